@@ -1,0 +1,525 @@
+/*
+ * dbmp_oracle.c -- plain, slow FP64 CPU reference of the DiffBMP rasterizer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle for the CUDA
+ * library: only the test suite, the smoke check and the benchmark's CPU-baseline
+ * leg may load it.  It shares no code, header, helper or constant generator with
+ * the CUDA path, and the CUDA path never calls it.
+ *
+ * What it computes (DiffBMP, "Differentiable Rendering with Bitmap Primitives"):
+ *   Eq. 1   canvas -> normalised primitive coords  [u v] = R(theta) [(x-xi)/s (y-yi)/s]
+ *   Eq. 2   normalised -> bitmap coords            U = (u+1)/2 (W-1), V = (v+1)/2 (H-1)
+ *   Eqs. S1-S3 (Sec. S1.1) bilinear sample M = w^T p over the four lattice taps
+ *   Eq. 3   alpha_i = alpha_max sigmoid(nu_i) M_i
+ *   Eqs. 4-5 front-to-back Porter-Duff over: T_k = prod_{j<k}(1-alpha_j),
+ *           I = sum_k T_k alpha_k sigmoid(c_k)
+ *   Eq. 8   background blend  I = I_FG + T_N b ;  I_alpha = 1 - T_N (Sec. 3.3.2)
+ *   Eq. 6, Eq. S4, Eq. S5 (Sec. 3.1.2, Sec. S1.2): exact gradients, written here as a
+ *           reverse recursion over the layers of one pixel (no division).
+ *   Sec. 3.1.1 "Parallelization": every primitive is listed in each tile its padded
+ *           bounding box overlaps, in front-to-back (index) order; oracle_bin is that
+ *           listing written out as a definition (fp32 bounding-box specification).
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - pixel (px,py) sits at canvas coordinate x = px, y = py (integer centres, as the
+ *     meshgrid of the naive baseline, Algorithm S3);
+ *   - taps outside the bitmap are zero (zero padding, as grid_sample in Algorithm S3);
+ *   - index 0 is the front layer;
+ *   - the "skip if M < eps" test of Algorithm 1 is read with eps = 0: a layer with
+ *     M == 0 has alpha == 0 and changes nothing, so skipping it is exact;
+ *   - early termination: a layer k is composited only while T_k >= T_stop
+ *     (T_stop = 0 composites every layer);
+ *   - a primitive with a non-finite parameter or s == 0 is skipped (no tiles, no
+ *     contribution, zero gradient).
+ *
+ * Parity pins: the tests check this file against closed forms (identity transform,
+ * one and two layer over, occlusion, zero opacity, rotation by pi/2), against
+ * torch.nn.functional.grid_sample + autograd in float64 (Algorithm S3), against
+ * central finite differences in FP64, against Eq. S5 for b = 0, and the binning
+ * against brute-force rectangle intersection and the sum_i tau_i = sum_t d_t identity.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_BG_NONE 0
+#define ORC_BG_CONST 1
+#define ORC_BG_BUFFER 2
+
+/* -------------------------------------------------------------------------- */
+/* Per-primitive quantities in FP64                                            */
+/* -------------------------------------------------------------------------- */
+typedef struct {
+    int valid;
+    double x, y, s, cs, sn;     /* position, scale, cos(theta), sin(theta) */
+    double amax, sig_nu, a;     /* alpha_max, sigmoid(nu), alpha_max*sigmoid(nu) */
+    double chat[3];             /* sigmoid(c)                                */
+    double xlo, xhi, ylo, yhi;  /* conservative canvas support box           */
+    const float *bmp;           /* bitmap P_i, row-major [H][W]              */
+} orc_prim;
+
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+static int finite_params(const float *p) {
+    for (int j = 0; j < 8; ++j)
+        if (!isfinite(p[j])) return 0;
+    return p[2] != 0.0f;
+}
+
+/* Fill one primitive record.  The support box is the canvas region where any of
+ * the four bilinear taps can be non-zero: U in (-1, W) and V in (-1, H), i.e.
+ * |u| < 1 + 2/(W-1), |v| < 1 + 2/(H-1), widened by one pixel.  It only skips work
+ * whose result is exactly zero; it never changes a value. */
+static void make_prim(orc_prim *q, const float *p, int32_t bid, const float *atlas,
+                      int32_t Hb, int32_t Wb, double alpha_max) {
+    q->valid = finite_params(p);
+    q->x = p[0];
+    q->y = p[1];
+    q->s = p[2];
+    double th = p[3];
+    q->cs = cos(th);
+    q->sn = sin(th);
+    q->amax = alpha_max;
+    q->sig_nu = sigmoid((double)p[4]);
+    q->a = alpha_max * q->sig_nu;
+    for (int j = 0; j < 3; ++j) q->chat[j] = sigmoid((double)p[5 + j]);
+    q->bmp = atlas + (size_t)bid * (size_t)Hb * (size_t)Wb;
+    double eu = 1.0 + 2.0 / (double)(Wb - 1), ev = 1.0 + 2.0 / (double)(Hb - 1);
+    double as = fabs(q->s);
+    double hx = as * (fabs(q->cs) * eu + fabs(q->sn) * ev) + 1.0;
+    double hy = as * (fabs(q->sn) * eu + fabs(q->cs) * ev) + 1.0;
+    q->xlo = q->x - hx;
+    q->xhi = q->x + hx;
+    q->ylo = q->y - hy;
+    q->yhi = q->y + hy;
+}
+
+/* One bitmap tap with zero padding outside [0,W-1] x [0,H-1]. */
+static double tap(const float *P, int32_t Hb, int32_t Wb, long v, long u) {
+    if (u < 0 || v < 0 || u >= Wb || v >= Hb) return 0.0;
+    return (double)P[(size_t)v * (size_t)Wb + (size_t)u];
+}
+
+/* Everything the backward needs about one (pixel, layer) evaluation. */
+typedef struct {
+    int k;
+    double u, v, wu, wv;
+    double p00, p01, p10, p11;
+    double M, alpha, T;  /* T = transmittance in front of this layer */
+} orc_layer;
+
+/* Eq. 1, Eq. 2 and Eqs. S1-S3 at canvas point (x, y). */
+static void sample(const orc_prim *q, int32_t Hb, int32_t Wb, double x, double y, orc_layer *L) {
+    double dx = x - q->x, dy = y - q->y;
+    L->u = (q->cs * dx + q->sn * dy) / q->s;
+    L->v = (-q->sn * dx + q->cs * dy) / q->s;
+    double U = (L->u + 1.0) / 2.0 * (double)(Wb - 1);
+    double V = (L->v + 1.0) / 2.0 * (double)(Hb - 1);
+    double u0 = floor(U), v0 = floor(V);
+    L->wu = U - u0;
+    L->wv = V - v0;
+    long iu = (long)u0, iv = (long)v0;
+    L->p00 = tap(q->bmp, Hb, Wb, iv, iu);
+    L->p01 = tap(q->bmp, Hb, Wb, iv, iu + 1);
+    L->p10 = tap(q->bmp, Hb, Wb, iv + 1, iu);
+    L->p11 = tap(q->bmp, Hb, Wb, iv + 1, iu + 1);
+    L->M = (1.0 - L->wu) * (1.0 - L->wv) * L->p00 + L->wu * (1.0 - L->wv) * L->p01 +
+           (1.0 - L->wu) * L->wv * L->p10 + L->wu * L->wv * L->p11;
+}
+
+static int in_box(const orc_prim *q, double x, double y) {
+    return q->valid && x > q->xlo && x < q->xhi && y > q->ylo && y < q->yhi;
+}
+
+/* Walk all layers of one pixel front to back (Eqs. 3-5).  Returns the number of
+ * contributing layers written to `Ls` (may be NULL), stores C, T_N, last index and
+ * the number of (pixel, primitive) pairs whose bitmap was sampled. */
+static int walk_pixel(const orc_prim *P, int32_t N, int32_t Hb, int32_t Wb, double x, double y,
+                      double T_stop, orc_layer *Ls, double C[3], double *T_out, int32_t *last,
+                      int64_t *pairs) {
+    double T = 1.0;
+    int n = 0;
+    C[0] = C[1] = C[2] = 0.0;
+    *last = -1;
+    for (int32_t k = 0; k < N; ++k) {
+        const orc_prim *q = &P[k];
+        if (!in_box(q, x, y)) continue;
+        if (T < T_stop) break;
+        orc_layer L;
+        sample(q, Hb, Wb, x, y, &L);
+        ++*pairs;
+        if (L.M == 0.0) continue;
+        L.k = k;
+        L.alpha = q->a * L.M;
+        L.T = T;
+        for (int j = 0; j < 3; ++j) C[j] += T * L.alpha * q->chat[j];
+        T *= (1.0 - L.alpha);
+        *last = k;
+        if (Ls) Ls[n] = L;
+        ++n;
+    }
+    *T_out = T;
+    return n;
+}
+
+static double bg_value(int32_t bg_mode, const double *bg_rgb, const float *bg_buf, int j,
+                       size_t pix, size_t HW) {
+    if (bg_mode == ORC_BG_CONST) return bg_rgb[j];
+    if (bg_mode == ORC_BG_BUFFER) return (double)bg_buf[(size_t)j * HW + pix];
+    return 0.0;
+}
+
+static orc_prim *make_prims(int32_t N, const float *params, const int32_t *bitmap_id,
+                            const float *atlas, int32_t Hb, int32_t Wb, double alpha_max) {
+    orc_prim *P = (orc_prim *)calloc((size_t)(N > 0 ? N : 1), sizeof(orc_prim));
+    for (int32_t k = 0; k < N; ++k)
+        make_prim(&P[k], params + 8 * (size_t)k, bitmap_id[k], atlas, Hb, Wb, alpha_max);
+    return P;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Forward: whole canvas, or a list of pixels                                  */
+/* -------------------------------------------------------------------------- */
+
+/* Renders the pixels (px[i], py[i]), i < n_pix.  If px == NULL, renders the whole
+ * H x W canvas in row-major order (n_pix ignored).  Outputs are indexed like the
+ * pixel list: image[j * n + i], T_final[i], n_last[i] (index of the last
+ * contributing primitive, -1 if none).  Returns the number of sampled pairs. */
+int64_t oracle_render(int32_t H, int32_t W, int32_t N, const float *params,
+                      const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
+                      int32_t Wb, double alpha_max, int32_t bg_mode, const double *bg_rgb,
+                      const float *bg_buf, double T_stop, int64_t n_pix, const int32_t *px,
+                      const int32_t *py, double *image, double *T_final, int32_t *n_last) {
+    (void)n_bmp;
+    orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
+    int64_t n = px ? n_pix : (int64_t)H * (int64_t)W;
+    size_t HW = (size_t)H * (size_t)W;
+    int64_t pairs = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : pairs)
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t x = px ? px[i] : (int32_t)(i % W);
+        int32_t y = px ? py[i] : (int32_t)(i / W);
+        double C[3], T;
+        int32_t last;
+        int64_t pr = 0;
+        walk_pixel(P, N, Hb, Wb, (double)x, (double)y, T_stop, NULL, C, &T, &last, &pr);
+        pairs += pr;
+        size_t pix = (size_t)y * (size_t)W + (size_t)x;
+        for (int j = 0; j < 3; ++j)
+            image[(size_t)j * (size_t)n + (size_t)i] =
+                C[j] + T * bg_value(bg_mode, bg_rgb, bg_buf, j, pix, HW);
+        T_final[i] = T;
+        n_last[i] = last;
+    }
+    free(P);
+    return pairs;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Backward                                                                    */
+/* -------------------------------------------------------------------------- */
+
+/* Adds the gradient of one pixel into G (N x 8, order x y s theta nu c_r c_g c_b).
+ * g[3] = dL/dI at the pixel, gA = dL/dI_alpha, b[3] = background at the pixel.
+ * Reverse recursion (exact derivative of Eqs. 3-5 and Eq. 8):
+ *   dL/dalpha_k = T_k [ sum_j g_j (chat_kj - R_j) + gA * B ],
+ *   with R = colour behind layer k normalised by T_{k+1} (starts at b), updated by
+ *   R <- alpha_k chat_k + (1 - alpha_k) R, and B = prod_{m>k} (1 - alpha_m).
+ * If `only` >= 0, only that primitive's row is accumulated. */
+static void pixel_grad(const orc_prim *P, int32_t Hb, int32_t Wb, const orc_layer *Ls, int n,
+                       const double g[3], double gA, const double b[3], double *G, int32_t only) {
+    double R[3] = {b[0], b[1], b[2]};
+    double B = 1.0;
+    double kw = 0.5 * (double)(Wb - 1), kv = 0.5 * (double)(Hb - 1);
+    for (int l = n - 1; l >= 0; --l) {
+        const orc_layer *L = &Ls[l];
+        const orc_prim *q = &P[L->k];
+        double dA = gA * B;
+        for (int j = 0; j < 3; ++j) dA += g[j] * (q->chat[j] - R[j]);
+        dA *= L->T;
+        if (only < 0 || only == L->k) {
+            double *Gk = G + 8 * (size_t)(only < 0 ? L->k : 0);
+            /* Eq. S4: colour logits */
+            for (int j = 0; j < 3; ++j)
+                Gk[5 + j] += g[j] * L->T * L->alpha * q->chat[j] * (1.0 - q->chat[j]);
+            /* Eq. 3: opacity logit */
+            Gk[4] += dA * q->amax * L->M * q->sig_nu * (1.0 - q->sig_nu);
+            /* Eq. 6: geometry through the bilinear sample and Eqs. 1-2 */
+            double dM = dA * q->a;
+            double dMdU = (1.0 - L->wv) * (L->p01 - L->p00) + L->wv * (L->p11 - L->p10);
+            double dMdV = (1.0 - L->wu) * (L->p10 - L->p00) + L->wu * (L->p11 - L->p01);
+            double gu = dM * dMdU * kw, gv = dM * dMdV * kv;
+            double s = q->s, cs = q->cs, sn = q->sn;
+            Gk[0] += gu * (-cs / s) + gv * (sn / s);
+            Gk[1] += gu * (-sn / s) + gv * (-cs / s);
+            Gk[2] += gu * (-L->u / s) + gv * (-L->v / s);
+            Gk[3] += gu * L->v + gv * (-L->u);
+        }
+        for (int j = 0; j < 3; ++j) R[j] = L->alpha * q->chat[j] + (1.0 - L->alpha) * R[j];
+        B *= (1.0 - L->alpha);
+    }
+}
+
+/* Gradient of L w.r.t. every primitive's raw parameters, summed over the whole
+ * canvas.  dL_dimage: 3 x H x W (planar), dL_dalpha: H x W or NULL.  dparams: N x 8,
+ * overwritten.  Same T_stop semantics as the forward. */
+void oracle_grad(int32_t H, int32_t W, int32_t N, const float *params, const int32_t *bitmap_id,
+                 const float *atlas, int32_t n_bmp, int32_t Hb, int32_t Wb, double alpha_max,
+                 int32_t bg_mode, const double *bg_rgb, const float *bg_buf, double T_stop,
+                 const double *dL_dimage, const double *dL_dalpha, double *dparams) {
+    (void)n_bmp;
+    orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
+    size_t HW = (size_t)H * (size_t)W;
+    memset(dparams, 0, sizeof(double) * 8 * (size_t)N);
+#pragma omp parallel
+    {
+        double *Gloc = (double *)calloc(8 * (size_t)(N > 0 ? N : 1), sizeof(double));
+        orc_layer *Ls = (orc_layer *)malloc(sizeof(orc_layer) * (size_t)(N > 0 ? N : 1));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < (int64_t)HW; ++i) {
+            int32_t x = (int32_t)(i % W), y = (int32_t)(i / W);
+            double C[3], T, g[3], b[3];
+            int32_t last;
+            int64_t pr = 0;
+            int n = walk_pixel(P, N, Hb, Wb, x, y, T_stop, Ls, C, &T, &last, &pr);
+            for (int j = 0; j < 3; ++j) {
+                g[j] = dL_dimage[(size_t)j * HW + (size_t)i];
+                b[j] = bg_value(bg_mode, bg_rgb, bg_buf, j, (size_t)i, HW);
+            }
+            double gA = dL_dalpha ? dL_dalpha[i] : 0.0;
+            pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gloc, -1);
+        }
+#pragma omp critical
+        for (size_t t = 0; t < 8 * (size_t)N; ++t) dparams[t] += Gloc[t];
+        free(Gloc);
+        free(Ls);
+    }
+    free(P);
+}
+
+/* Gradient of selected primitives only: for each sel[t], sums the per-pixel
+ * contributions over the pixels of its support box (all other pixels contribute
+ * exactly zero).  Used for sampled parity on canvases too large for oracle_grad.
+ * dparams_sel: n_sel x 8. */
+void oracle_grad_selected(int32_t H, int32_t W, int32_t N, const float *params,
+                          const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
+                          int32_t Wb, double alpha_max, int32_t bg_mode, const double *bg_rgb,
+                          const float *bg_buf, double T_stop, const float *dL_dimage,
+                          const float *dL_dalpha, int32_t n_sel, const int32_t *sel,
+                          double *dparams_sel) {
+    (void)n_bmp;
+    orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
+    size_t HW = (size_t)H * (size_t)W;
+    memset(dparams_sel, 0, sizeof(double) * 8 * (size_t)n_sel);
+    for (int32_t t = 0; t < n_sel; ++t) {
+        const orc_prim *q = &P[sel[t]];
+        if (!q->valid) continue;
+        long x0 = (long)floor(q->xlo), x1 = (long)ceil(q->xhi);
+        long y0 = (long)floor(q->ylo), y1 = (long)ceil(q->yhi);
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > W - 1) x1 = W - 1;
+        if (y1 > H - 1) y1 = H - 1;
+        if (x1 < x0 || y1 < y0) continue;
+        double G[8] = {0};
+        long bw = x1 - x0 + 1;
+        long nb = bw * (y1 - y0 + 1);
+#pragma omp parallel
+        {
+            double Gl[8] = {0};
+            orc_layer *Ls = (orc_layer *)malloc(sizeof(orc_layer) * (size_t)(N > 0 ? N : 1));
+#pragma omp for schedule(dynamic, 64)
+            for (long i = 0; i < nb; ++i) {
+                long x = x0 + i % bw, y = y0 + i / bw;
+                if (!in_box(q, (double)x, (double)y)) continue;
+                double C[3], T, g[3], b[3];
+                int32_t last;
+                int64_t pr = 0;
+                int n = walk_pixel(P, N, Hb, Wb, (double)x, (double)y, T_stop, Ls, C, &T, &last, &pr);
+                size_t pix = (size_t)y * (size_t)W + (size_t)x;
+                for (int j = 0; j < 3; ++j) {
+                    g[j] = (double)dL_dimage[(size_t)j * HW + pix];
+                    b[j] = bg_value(bg_mode, bg_rgb, bg_buf, j, pix, HW);
+                }
+                double gA = dL_dalpha ? (double)dL_dalpha[pix] : 0.0;
+                pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, sel[t]);
+            }
+#pragma omp critical
+            for (int j = 0; j < 8; ++j) G[j] += Gl[j];
+            free(Ls);
+        }
+        for (int j = 0; j < 8; ++j) dparams_sel[8 * (size_t)t + j] = G[j];
+    }
+    free(P);
+}
+
+/* Eq. S5 as printed (suffix sum S_j and back-product B, no background term), for
+ * one pixel: writes dL/dalpha_k of the pixel's contributing layers, front to back,
+ * into out[] and their primitive indices into ks[].  Returns the layer count.
+ * Used only to pin the reverse recursion above when b = 0. */
+int32_t oracle_eq_s5_dalpha(int32_t N, const float *params, const int32_t *bitmap_id,
+                            const float *atlas, int32_t Hb, int32_t Wb, double alpha_max, int32_t x,
+                            int32_t y, const double g[3], double gA, double *out, int32_t *ks) {
+    orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
+    orc_layer *Ls = (orc_layer *)malloc(sizeof(orc_layer) * (size_t)(N > 0 ? N : 1));
+    double C[3], T;
+    int32_t last;
+    int64_t pr = 0;
+    int n = walk_pixel(P, N, Hb, Wb, x, y, 0.0, Ls, C, &T, &last, &pr);
+    for (int l = 0; l < n; ++l) {
+        const orc_prim *q = &P[Ls[l].k];
+        double S[3] = {0, 0, 0}, B = 1.0;
+        for (int m = l + 1; m < n; ++m) {
+            for (int j = 0; j < 3; ++j) S[j] += P[Ls[m].k].chat[j] * Ls[m].alpha * Ls[m].T;
+            B *= (1.0 - Ls[m].alpha);
+        }
+        double d = gA * Ls[l].T * B;
+        for (int j = 0; j < 3; ++j) d += g[j] * (Ls[l].T * q->chat[j] - S[j] / (1.0 - Ls[l].alpha));
+        out[l] = d;
+        ks[l] = Ls[l].k;
+    }
+    free(Ls);
+    free(P);
+    return n;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Binning specification (Sec. 3.1.1 "Parallelization"; Sec. S1.3)             */
+/* -------------------------------------------------------------------------- */
+/* The tile lists are defined by an fp32 bounding box computed with the steps
+ * below, one IEEE single-precision operation at a time (this file is compiled
+ * with -ffp-contract=off, so no fused multiply-add).  Its sine and cosine come
+ * from Cody-Waite reduction by pi/2 (three-part constant) and the Taylor series
+ * of sin and cos to degree 9 / 8 on [-pi/4, pi/4]; they only size the box, which
+ * is widened by a one-pixel margin, so the box always contains the support of the
+ * primitive (|u| < 1 + 2/(W-1), |v| < 1 + 2/(H-1)).
+ *
+ * A primitive is listed in tile (tx, ty) iff tx0 <= tx <= tx1 and ty0 <= ty <= ty1
+ * with tx0 = floor((x - hx - 1)/T), tx1 = floor((x + hx + 1)/T) (same for y),
+ * clipped to the canvas' tiles.  Lists hold primitive indices in increasing order
+ * (front to back). */
+
+static void spec_abs_sincos(float th, float *as, float *ac) {
+    if (!(fabsf(th) <= 65536.0f)) { /* outside the reduction's exact range: bound by 1 */
+        *as = 1.0f;
+        *ac = 1.0f;
+        return;
+    }
+    const float two_over_pi = 0.636619772367581343f;
+    const float C1 = 1.5703125f;               /* pi/2 split in three parts */
+    const float C2 = 4.83751296997070312e-4f;
+    const float C3 = 7.54978995489188e-8f;
+    float k = rintf(th * two_over_pi);
+    float r = th - k * C1;
+    r = r - k * C2;
+    r = r - k * C3;
+    float r2 = r * r;
+    float sp = 1.0f / 362880.0f;
+    sp = sp * r2 + (-1.0f / 5040.0f);
+    sp = sp * r2 + (1.0f / 120.0f);
+    sp = sp * r2 + (-1.0f / 6.0f);
+    float sr = r + (r * r2) * sp;
+    float cp = 1.0f / 40320.0f;
+    cp = cp * r2 + (-1.0f / 720.0f);
+    cp = cp * r2 + (1.0f / 24.0f);
+    cp = cp * r2 + (-0.5f);
+    float cr = 1.0f + r2 * cp;
+    long ki = (long)k;
+    if (ki & 1) {
+        *as = fabsf(cr);
+        *ac = fabsf(sr);
+    } else {
+        *as = fabsf(sr);
+        *ac = fabsf(cr);
+    }
+}
+
+/* Tile rectangle of one primitive; returns 0 if it touches no tile. */
+static int spec_rect(const float *p, int32_t Hb, int32_t Wb, int32_t tile, int32_t ntx,
+                     int32_t nty, int32_t r[4]) {
+    for (int j = 0; j < 8; ++j)
+        if (!isfinite(p[j])) return 0;
+    if (p[2] == 0.0f) return 0;
+    float eu = 1.0f + 2.0f / (float)(Wb - 1);
+    float ev = 1.0f + 2.0f / (float)(Hb - 1);
+    float as, ac;
+    spec_abs_sincos(p[3], &as, &ac);
+    float s = fabsf(p[2]);
+    float hx = s * (ac * eu + as * ev);
+    float hy = s * (as * eu + ac * ev);
+    float inv_t = 1.0f / (float)tile;
+    float fx0 = floorf(((p[0] - hx) - 1.0f) * inv_t);
+    float fx1 = floorf(((p[0] + hx) + 1.0f) * inv_t);
+    float fy0 = floorf(((p[1] - hy) - 1.0f) * inv_t);
+    float fy1 = floorf(((p[1] + hy) + 1.0f) * inv_t);
+    if (!(fx1 >= 0.0f) || !(fy1 >= 0.0f)) return 0;
+    if (!(fx0 <= (float)(ntx - 1)) || !(fy0 <= (float)(nty - 1))) return 0;
+    r[0] = fx0 < 0.0f ? 0 : (int32_t)fx0;
+    r[1] = fy0 < 0.0f ? 0 : (int32_t)fy0;
+    r[2] = fx1 > (float)(ntx - 1) ? ntx - 1 : (int32_t)fx1;
+    r[3] = fy1 > (float)(nty - 1) ? nty - 1 : (int32_t)fy1;
+    return 1;
+}
+
+/* Per-primitive tile rectangles: rects[4*i] = {tx0, ty0, tx1, ty1} or {0,0,-1,-1}
+ * when the primitive touches no tile; tau[i] = number of tiles. */
+void oracle_bin_rects(int32_t H, int32_t W, int32_t tile, int32_t N, const float *params,
+                      int32_t Hb, int32_t Wb, int32_t *rects, int64_t *tau) {
+    int32_t ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
+    for (int32_t i = 0; i < N; ++i) {
+        int32_t r[4];
+        if (spec_rect(params + 8 * (size_t)i, Hb, Wb, tile, ntx, nty, r)) {
+            memcpy(rects + 4 * (size_t)i, r, sizeof r);
+            tau[i] = (int64_t)(r[2] - r[0] + 1) * (int64_t)(r[3] - r[1] + 1);
+        } else {
+            rects[4 * (size_t)i + 0] = 0;
+            rects[4 * (size_t)i + 1] = 0;
+            rects[4 * (size_t)i + 2] = -1;
+            rects[4 * (size_t)i + 3] = -1;
+            tau[i] = 0;
+        }
+    }
+}
+
+/* The tile lists as a definition: for every tile t (row-major), every primitive
+ * whose rectangle contains t, in increasing index order.  Writes the list
+ * boundaries (offsets[t] .. offsets[t+1]) and, if `list` is not NULL and K fits
+ * in `cap`, the concatenated lists.  Returns K = sum_t d_t. */
+int64_t oracle_bin(int32_t H, int32_t W, int32_t tile, int32_t N, const float *params,
+                   int32_t Hb, int32_t Wb, int64_t *offsets, int32_t *list, int64_t cap) {
+    int32_t ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
+    int32_t *rects = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(N > 0 ? N : 1));
+    int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    oracle_bin_rects(H, W, tile, N, params, Hb, Wb, rects, tau);
+    int64_t K = 0;
+    for (int32_t ty = 0; ty < nty; ++ty)
+        for (int32_t tx = 0; tx < ntx; ++tx) {
+            offsets[(size_t)ty * ntx + tx] = K;
+            for (int32_t i = 0; i < N; ++i) {
+                const int32_t *r = rects + 4 * (size_t)i;
+                if (tx >= r[0] && tx <= r[2] && ty >= r[1] && ty <= r[3]) {
+                    if (list && K < cap) list[K] = i;
+                    ++K;
+                }
+            }
+        }
+    offsets[(size_t)ntx * nty] = K;
+    free(rects);
+    free(tau);
+    return K;
+}
+
+/* The spec's |sin|, |cos| (exported so the tests can bound its error). */
+void oracle_spec_abs_sincos(float th, float *as, float *ac) { spec_abs_sincos(th, as, ac); }
+
+int32_t oracle_num_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,243 @@
+"""ctypes front of the FP64 C oracle, plus the optimiser and loss in numpy FP64.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, the benchmark's CPU-baseline leg).
+
+Conventions (shared with the library only through the documented ABI, not code):
+  params      float32 (N, 8): x, y, s, theta, nu, c_r, c_g, c_b  (nu and c are logits)
+  bitmap_id   int32 (N,)
+  atlas       float32 (n_bmp, Hb, Wb), P[v, u] = atlas[b, v, u], values in [0, 1]
+  image       (3, H, W) planar;  T_final (H, W);  index 0 = front layer
+  background  None (b = 0, Eq. 5), an RGB triple (constant), or a (3, H, W) buffer (Eq. 8)
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+BG_NONE, BG_CONST, BG_BUFFER = 0, 1, 2
+
+_f32p = ctypes.POINTER(ctypes.c_float)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.oracle_render.restype = ctypes.c_int64
+        L.oracle_render.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p, _i32p,
+                                    _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_double, ctypes.c_int32, _f64p, _f32p, ctypes.c_double,
+                                    ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _i32p]
+        L.oracle_grad.restype = None
+        L.oracle_grad.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p, _i32p,
+                                  _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_double, ctypes.c_int32, _f64p, _f32p, ctypes.c_double,
+                                  _f64p, _f64p, _f64p]
+        L.oracle_grad_selected.restype = None
+        L.oracle_grad_selected.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p,
+                                           _i32p, _f32p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p,
+                                           _f32p, ctypes.c_double, _f32p, _f32p, ctypes.c_int32,
+                                           _i32p, _f64p]
+        L.oracle_eq_s5_dalpha.restype = ctypes.c_int32
+        L.oracle_eq_s5_dalpha.argtypes = [ctypes.c_int32, _f32p, _i32p, _f32p, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                          ctypes.c_int32, _f64p, ctypes.c_double, _f64p, _i32p]
+        L.oracle_bin_rects.restype = None
+        L.oracle_bin_rects.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, _f32p, ctypes.c_int32, ctypes.c_int32,
+                                       _i32p, _i64p]
+        L.oracle_bin.restype = ctypes.c_int64
+        L.oracle_bin.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 _f32p, ctypes.c_int32, ctypes.c_int32, _i64p, _i32p,
+                                 ctypes.c_int64]
+        L.oracle_spec_abs_sincos.restype = None
+        L.oracle_spec_abs_sincos.argtypes = [ctypes.c_float, _f32p, _f32p]
+        L.oracle_num_threads.restype = ctypes.c_int32
+        L.oracle_num_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _prep(params, bitmap_id, atlas):
+    params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    bitmap_id = np.ascontiguousarray(bitmap_id, dtype=np.int32).reshape(-1)
+    atlas = np.ascontiguousarray(atlas, dtype=np.float32)
+    if atlas.ndim == 2:
+        atlas = atlas[None]
+    assert params.shape[0] == bitmap_id.shape[0]
+    if params.shape[0]:
+        assert bitmap_id.min() >= 0 and bitmap_id.max() < atlas.shape[0]
+    return params, bitmap_id, atlas
+
+
+def _bg(background, H, W):
+    if background is None:
+        return BG_NONE, np.zeros(3), None
+    b = np.asarray(background)
+    if b.size == 3:
+        return BG_CONST, np.ascontiguousarray(b, dtype=np.float64).reshape(3), None
+    return BG_BUFFER, np.zeros(3), np.ascontiguousarray(b, dtype=np.float32).reshape(3, H, W)
+
+
+def num_threads():
+    return int(lib().oracle_num_threads())
+
+
+def render(H, W, params, bitmap_id, atlas, alpha_max=1.0, background=(1.0, 1.0, 1.0),
+           T_stop=0.0, pixels=None):
+    """Forward (Eqs. 1-5, 8) in FP64.
+
+    Returns dict(image (3,H,W) or (3,n), T_final, n_last (index of last contributing
+    primitive, -1 if none), pairs (number of sampled (pixel, primitive) pairs)).
+    `pixels` = (px, py) int arrays renders only those pixels."""
+    params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
+    mode, rgb, buf = _bg(background, H, W)
+    N = params.shape[0]
+    if pixels is None:
+        n, px, py = H * W, None, None
+    else:
+        px = np.ascontiguousarray(pixels[0], dtype=np.int32)
+        py = np.ascontiguousarray(pixels[1], dtype=np.int32)
+        n = px.shape[0]
+    image = np.empty((3, n), np.float64)
+    T = np.empty(n, np.float64)
+    last = np.empty(n, np.int32)
+    pairs = lib().oracle_render(H, W, N, _p(params, _f32p), _p(bitmap_id, _i32p),
+                                _p(atlas, _f32p), atlas.shape[0], atlas.shape[1], atlas.shape[2],
+                                float(alpha_max), mode, _p(rgb, _f64p), _p(buf, _f32p),
+                                float(T_stop), n, _p(px, _i32p), _p(py, _i32p),
+                                _p(image, _f64p), _p(T, _f64p), _p(last, _i32p))
+    if pixels is None:
+        image, T, last = image.reshape(3, H, W), T.reshape(H, W), last.reshape(H, W)
+    return dict(image=image, T_final=T, n_last=last, pairs=int(pairs))
+
+
+def grad(H, W, params, bitmap_id, atlas, dL_dimage, dL_dalpha=None, alpha_max=1.0,
+         background=(1.0, 1.0, 1.0), T_stop=0.0):
+    """dL/dparams (N, 8) float64 for upstream gradients dL/dI (3,H,W) and dL/dI_alpha (H,W)."""
+    params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
+    mode, rgb, buf = _bg(background, H, W)
+    N = params.shape[0]
+    gI = np.ascontiguousarray(dL_dimage, dtype=np.float64).reshape(3, H, W)
+    gA = None if dL_dalpha is None else np.ascontiguousarray(dL_dalpha, np.float64).reshape(H, W)
+    out = np.zeros((N, 8), np.float64)
+    lib().oracle_grad(H, W, N, _p(params, _f32p), _p(bitmap_id, _i32p), _p(atlas, _f32p),
+                      atlas.shape[0], atlas.shape[1], atlas.shape[2], float(alpha_max), mode,
+                      _p(rgb, _f64p), _p(buf, _f32p), float(T_stop), _p(gI, _f64p),
+                      _p(gA, _f64p), _p(out, _f64p))
+    return out
+
+
+def grad_selected(H, W, params, bitmap_id, atlas, dL_dimage, sel, dL_dalpha=None, alpha_max=1.0,
+                  background=(1.0, 1.0, 1.0), T_stop=0.0):
+    """dL/dparams of the primitives `sel` only ((len(sel), 8) float64)."""
+    params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
+    mode, rgb, buf = _bg(background, H, W)
+    N = params.shape[0]
+    gI = np.ascontiguousarray(dL_dimage, dtype=np.float32).reshape(3, H, W)
+    gA = None if dL_dalpha is None else np.ascontiguousarray(dL_dalpha, np.float32).reshape(H, W)
+    sel = np.ascontiguousarray(sel, dtype=np.int32)
+    out = np.zeros((sel.shape[0], 8), np.float64)
+    lib().oracle_grad_selected(H, W, N, _p(params, _f32p), _p(bitmap_id, _i32p),
+                               _p(atlas, _f32p), atlas.shape[0], atlas.shape[1], atlas.shape[2],
+                               float(alpha_max), mode, _p(rgb, _f64p), _p(buf, _f32p),
+                               float(T_stop), _p(gI, _f32p), _p(gA, _f32p), sel.shape[0],
+                               _p(sel, _i32p), _p(out, _f64p))
+    return out
+
+
+def eq_s5_dalpha(params, bitmap_id, atlas, x, y, g, gA=0.0, alpha_max=1.0):
+    """Eq. S5 as printed (no background term) at one pixel: (dL/dalpha per layer, prim idx)."""
+    params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
+    N = params.shape[0]
+    out = np.zeros(max(N, 1), np.float64)
+    ks = np.zeros(max(N, 1), np.int32)
+    g = np.ascontiguousarray(g, np.float64).reshape(3)
+    n = lib().oracle_eq_s5_dalpha(N, _p(params, _f32p), _p(bitmap_id, _i32p), _p(atlas, _f32p),
+                                  atlas.shape[1], atlas.shape[2], float(alpha_max), int(x), int(y),
+                                  _p(g, _f64p), float(gA), _p(out, _f64p), _p(ks, _i32p))
+    return out[:n], ks[:n]
+
+
+def bin_rects(H, W, tile, params, Hb, Wb):
+    """Per-primitive tile rectangles (N, 4) {tx0, ty0, tx1, ty1} and tau (N,)."""
+    params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    N = params.shape[0]
+    rects = np.zeros((max(N, 1), 4), np.int32)
+    tau = np.zeros(max(N, 1), np.int64)
+    lib().oracle_bin_rects(H, W, tile, N, _p(params, _f32p), Hb, Wb, _p(rects, _i32p),
+                           _p(tau, _i64p))
+    return rects[:N], tau[:N]
+
+
+def bin(H, W, tile, params, Hb, Wb):
+    """Tile lists (Sec. 3.1.1): (offsets (n_tiles+1,) int64, list (K,) int32)."""
+    params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    N = params.shape[0]
+    ntx, nty = -(-W // tile), -(-H // tile)
+    offsets = np.zeros(ntx * nty + 1, np.int64)
+    K = lib().oracle_bin(H, W, tile, N, _p(params, _f32p), Hb, Wb, _p(offsets, _i64p), None, 0)
+    lst = np.zeros(max(K, 1), np.int32)
+    lib().oracle_bin(H, W, tile, N, _p(params, _f32p), Hb, Wb, _p(offsets, _i64p),
+                     _p(lst, _i32p), K)
+    return offsets, lst[:K]
+
+
+def spec_abs_sincos(theta):
+    a = ctypes.c_float()
+    b = ctypes.c_float()
+    lib().oracle_spec_abs_sincos(float(np.float32(theta)), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------------------
+# Loss and optimiser (Tab. S1: MSE loss, Adam-like optimiser with per-group gains
+# and exponential decay; PSNR of images in [0, 1]).
+# ---------------------------------------------------------------------------
+
+#: Tab. S1 learning-rate gains per parameter column: x, y, s (lr_gain_x/y/r = 10),
+#: theta (1), nu (lr_gain_v = 1.5), colour (1).
+LR_GAINS = (10.0, 10.0, 10.0, 1.0, 1.5, 1.0, 1.0, 1.0)
+
+
+def mse(image, target):
+    d = np.asarray(image, np.float64) - np.asarray(target, np.float64)
+    return float(np.mean(d * d))
+
+
+def mse_grad(image, target):
+    """dL/dI of L = mean over 3HW of (I - I*)^2."""
+    d = np.asarray(image, np.float64) - np.asarray(target, np.float64)
+    return 2.0 * d / d.size
+
+
+def psnr(image, target):
+    m = mse(image, target)
+    return float("inf") if m == 0 else 10.0 * math.log10(1.0 / m)
+
+
+def adam_step(p, g, m, v, t, lr, gains=LR_GAINS, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba) on (N, 8) arrays in FP64, bias-corrected, step t >= 1,
+    column j uses learning rate lr * gains[j].  Returns new (p, m, v)."""
+    p = np.asarray(p, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    lr_col = lr * np.asarray(gains, np.float64)[None, :]
+    return p - lr_col * mh / (np.sqrt(vh) + eps), m, v

@@ -1,0 +1,50 @@
+"""The oracle's pins must catch plausible mistakes (CPU only).
+
+Each case plants one mistake in a copy of the oracle's C source (a wrong sign,
+swapped taps, a dropped term, a wrong index or scale), builds it in a temporary
+directory and runs the pin tests against it; at least one pin must fail.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "rotation_sense": ("L->u = (q->cs * dx + q->sn * dy) / q->s;",
+                       "L->u = (q->cs * dx - q->sn * dy) / q->s;"),
+    "taps_transposed": ("L->p01 = tap(q->bmp, Hb, Wb, iv, iu + 1);\n    L->p10 = tap(q->bmp, Hb, Wb, iv + 1, iu);",
+                        "L->p10 = tap(q->bmp, Hb, Wb, iv, iu + 1);\n    L->p01 = tap(q->bmp, Hb, Wb, iv + 1, iu);"),
+    "background_dropped_in_backward": ("double R[3] = {b[0], b[1], b[2]};", "double R[3] = {0, 0, 0};"),
+    "sigmoid_derivative_dropped": ("q->chat[j] * (1.0 - q->chat[j]);", "q->chat[j];"),
+    "theta_gradient_sign": ("Gk[3] += gu * L->v + gv * (-L->u);", "Gk[3] += gu * L->v + gv * (L->u);"),
+    "bitmap_scale_W_not_W_minus_1": ("double U = (L->u + 1.0) / 2.0 * (double)(Wb - 1);",
+                                     "double U = (L->u + 1.0) / 2.0 * (double)(Wb);"),
+    "back_product_not_updated": ("B *= (1.0 - L->alpha);\n    }\n}", "}\n}"),
+    "transmittance_update": ("T *= (1.0 - L.alpha);", "T *= (1.0 - 0.5 * L.alpha);"),
+    "bin_margin_sign": ("float fx0 = floorf(((p[0] - hx) - 1.0f) * inv_t);",
+                        "float fx0 = floorf(((p[0] - hx) + 1.0f) * inv_t);"),
+    "bin_support_extension_dropped": ("float hx = s * (ac * eu + as * ev);", "float hx = s * (ac + as * ev);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "dbmp_oracle.c")).read()
+    a, b = MUTANTS[name]
+    assert a in src
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("_lib", "__pycache__"))
+    (tmp_path / "oracle" / "dbmp_oracle.c").write_text(src.replace(a, b, 1))
+    (tmp_path / "tests").mkdir()
+    for f in ("test_oracle_pins.py", "conftest.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    os.symlink(os.path.join(ROOT, "paper_2602_22625_gb300"), tmp_path / "paper_2602_22625_gb300")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=tmp_path, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "failed" in r.stdout
