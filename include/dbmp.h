@@ -1,0 +1,270 @@
+/*
+ * dbmp.h -- C ABI of libdbmp, a GB300 (sm_103a) differentiable rasterizer for
+ * bitmap primitives (DiffBMP, "Differentiable Rendering with Bitmap Primitives").
+ *
+ * The library draws N transformed bitmap primitives onto an RGB canvas,
+ * front-to-back, and differentiates the result w.r.t. every primitive's
+ * parameters.  One primitive i has eight float32 parameters, stored as one row
+ * of an N x 8 row-major array:
+ *
+ *     x_i, y_i, s_i, theta_i, nu_i, c_r, c_g, c_b
+ *
+ *   Eq. 1   [u v]^T = R(theta_i) [(x - x_i)/s_i, (y - y_i)/s_i]^T,
+ *           R = [[cos, sin], [-sin, cos]]; pixel (px, py) is the canvas point
+ *           x = px, y = py (row py, column px; y grows downwards)
+ *   Eq. 2   U = (u + 1)/2 (W_b - 1), V = (v + 1)/2 (H_b - 1)
+ *   Eqs. S1-S3 (Sec. S1.1)  M = bilinear sample of bitmap P at (U, V); taps
+ *           outside the bitmap read 0
+ *   Eq. 3   alpha_i = alpha_max sigmoid(nu_i) M_i           (nu: opacity logit)
+ *   Eqs. 4-5 T_k = prod_{j<k} (1 - alpha_j); I = sum_k T_k alpha_k sigmoid(c_k)
+ *           (index 0 is the front layer; c: colour logits)
+ *   Eq. 8   I += T_N b  (background b: none, a constant RGB, or a per-pixel buffer)
+ *
+ * Conventions for every call:
+ *   - Return value: DBMP_OK (0) or a negative DbmpStatus.  Argument errors are
+ *     detected on the host before any work is queued; dbmp_last_error() then
+ *     holds a one-line message (per thread).
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; they must
+ *     stay valid until the queued work has finished.  Host pointers are read
+ *     during the call only.
+ *   - Every call that takes a cudaStream_t only queues work on that stream and
+ *     never synchronises it, except where stated (dbmp_status_poll,
+ *     dbmp_workspace_create/destroy, dbmp_atlas_create/destroy, dbmp_autotune).
+ *   - Errors found on the device (tile-list capacity exceeded, degenerate
+ *     primitives) are recorded in the workspace's status block; read them with
+ *     dbmp_status_poll.  A kernel that finds the capacity error set does nothing.
+ *   - Images are planar float32: image[c][py][px], c = 0..2; per-pixel maps are
+ *     [py][px].  Canvases are any H, W >= 1 (ragged last tiles are handled).
+ */
+#ifndef DBMP_H
+#define DBMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *dbmp_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    DBMP_OK = 0,
+    DBMP_ERR_INVALID_ARG = -1, /* bad pointer, size, tile size or value */
+    DBMP_ERR_CAPACITY = -2,    /* tile lists exceed the workspace capacity */
+    DBMP_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    DBMP_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    DBMP_ERR_NOT_READY = -5,   /* required state missing (e.g. no prior dbmp_bin) */
+    DBMP_ERR_NO_MEMORY = -6    /* device allocation failed */
+} DbmpStatus;
+
+/* Background of Eq. 8 (Sec. 3.2.3). */
+typedef enum { DBMP_BG_NONE = 0, DBMP_BG_CONST = 1, DBMP_BG_BUFFER = 2 } DbmpBgMode;
+
+typedef struct {
+    int32_t mode;           /* DbmpBgMode */
+    float rgb[3];           /* DBMP_BG_CONST: b                          */
+    const float *buf_dev;   /* DBMP_BG_BUFFER: 3 x H x W planar, in [0,1] */
+} DbmpBackground;
+
+/* One-line description of the last error on this thread ("" if none). */
+const char *dbmp_last_error(void);
+
+/* ABI version of this header: 1. */
+int32_t dbmp_abi_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Bitmap atlas (the primitives P_i of Eq. 2 / Sec. S1.1)                     */
+/* ------------------------------------------------------------------------- */
+typedef struct DbmpAtlas DbmpAtlas;
+
+/* Builds the device-side sampling layout of n_bmp bitmaps of H_b x W_b texels
+ * (texels_dev: float32 [n_bmp][H_b][W_b], values in [0, 1]; H_b, W_b >= 2).
+ * The library stores, for every lattice cell (v0, u0) in [-1, H_b-1] x
+ * [-1, W_b-1], the four taps {P[v0,u0], P[v0,u0+1], P[v0+1,u0], P[v0+1,u0+1]}
+ * (zero outside the bitmap) as one 16-byte vector, so one bilinear sample is one
+ * 128-bit load.  Allocates (n_bmp (H_b+1)(W_b+1) 16 bytes) and synchronises
+ * `stream`.  texels_dev is not referenced after the call. */
+int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b,
+                          dbmp_stream_t stream, DbmpAtlas **out);
+int32_t dbmp_atlas_destroy(DbmpAtlas *atlas);
+/* Re-fills an existing atlas from new texels of the same shape (no allocation;
+ * stream-ordered). */
+int32_t dbmp_atlas_update(DbmpAtlas *atlas, const float *texels_dev, dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
+/* Workspace                                                                  */
+/* ------------------------------------------------------------------------- */
+typedef struct DbmpWorkspace DbmpWorkspace;
+
+typedef struct {
+    int32_t max_prims;    /* largest N (summed over canvases in batched mode) */
+    int32_t max_tiles;    /* largest tile count (summed over canvases)         */
+    int64_t max_pairs;    /* capacity of the tile lists: sum_t d_t (Sec. S4)    */
+    int32_t max_canvases; /* batched mode: largest number of canvases (>= 1)   */
+} DbmpLimits;
+
+/* Device bytes a workspace with these limits holds. */
+int32_t dbmp_workspace_bytes(const DbmpLimits *limits, size_t *bytes);
+/* Allocates a workspace (device memory: per-primitive records, tile lists,
+ * per-chunk histograms, gradient accumulators, status block). */
+int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out);
+int32_t dbmp_workspace_destroy(DbmpWorkspace *ws);
+
+/* Device-side status block, read (and cleared) by dbmp_status_poll. */
+typedef struct {
+    int32_t code;           /* DBMP_OK or DBMP_ERR_CAPACITY / DBMP_ERR_TIMEOUT   */
+    int32_t n_degenerate;   /* primitives with a bitmap id outside the atlas or a
+                               transform that overflows float32 (drawn as empty) */
+    int64_t pairs_required; /* sum_t d_t of the last binning                    */
+    int64_t pairs_evaluated;/* (pixel, list entry) pairs the last fwd evaluated  */
+    int64_t pairs_evaluated_bwd; /* same for the last bwd                       */
+} DbmpDeviceStatus;
+
+/* Synchronises `stream`, copies the status block to *out, clears the sticky
+ * error code and returns out->code. */
+int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStatus *out);
+
+/* ------------------------------------------------------------------------- */
+/* Binning (Sec. 3.1.1 "Parallelization"; Sec. S1.3)                          */
+/* ------------------------------------------------------------------------- */
+/* Per-primitive preprocessing and tile lists for one canvas H x W split into
+ * tile x tile pixel tiles (tile in {8, 16, 32}).  A primitive is listed in
+ * every tile its padded bounding box overlaps; each tile's list holds primitive
+ * indices in increasing (front-to-back) order.  The bounding box is the fp32
+ * specification below, evaluated one IEEE operation at a time (no fused
+ * multiply-add), so the lists are bit-exact and reproducible:
+ *     (|sin|, |cos|) of theta by Cody-Waite reduction by pi/2 and degree-9/8
+ *     Taylor polynomials (|theta| > 65536: both taken as 1);
+ *     e_u = 1 + 2/(W_b-1), e_v = 1 + 2/(H_b-1), s' = |s|;
+ *     hx = s' (|cos| e_u + |sin| e_v), hy = s' (|sin| e_u + |cos| e_v);
+ *     tx0 = floor(((x - hx) - 1) / tile), tx1 = floor(((x + hx) + 1) / tile),
+ *     likewise ty0, ty1, clipped to the canvas' tiles.
+ * Primitives with a non-finite parameter or s == 0 are not listed.
+ *   params_dev     float32 [N][8] (x, y, s, theta, nu, c_r, c_g, c_b)
+ *   bitmap_id_dev  int32 [N], each in [0, n_bmp); a primitive with an id
+ *                  outside the atlas is not listed and is counted in the status
+ *                  block's n_degenerate
+ *   alpha_max      in (0, 1] (Eq. 3)
+ * The tile lists are written by a stable counting sort keyed on the tile index
+ * (the primitive index is already the order inside a tile), so the result is
+ * identical to sorting (tile << 32 | index) keys.  If sum_t d_t exceeds
+ * limits.max_pairs nothing is written past the capacity, the status block gets
+ * DBMP_ERR_CAPACITY and pairs_required, and later fwd/bwd calls do nothing. */
+int32_t dbmp_bin(DbmpWorkspace *ws, int32_t H, int32_t W, int32_t tile, const float *params_dev,
+                 const int32_t *bitmap_id_dev, int32_t N, const DbmpAtlas *atlas, float alpha_max,
+                 dbmp_stream_t stream);
+
+/* Copies the tile lists of the last dbmp_bin to caller buffers:
+ * offsets_dev int64 [n_tiles + 1] (row-major tiles), list_dev int32 [cap].
+ * Writes min(K, cap) list entries; *n_tiles_out (host) gets the tile count. */
+int32_t dbmp_get_tile_lists(DbmpWorkspace *ws, int64_t *offsets_dev, int32_t *list_dev, int64_t cap,
+                            int32_t *n_tiles_out, dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
+/* Forward (Eqs. 1-5, 8; Algorithm 1)                                         */
+/* ------------------------------------------------------------------------- */
+/* Composites the binned primitives (requires a prior dbmp_bin on `ws`, with the
+ * same atlas).  One CTA per tile stages batches of primitive records in shared
+ * memory and walks the tile's list front to back, one pixel per thread.
+ *   T_stop   early termination: a layer is composited only while the pixel's
+ *            transmittance is >= max(T_stop, 2^-100); the image then differs from
+ *            the full composite by at most T_stop.  0 = every layer.
+ *   image_dev    out float32 [3][H][W]
+ *   T_final_dev  out float32 [H][W]  transmittance after the last composited
+ *                layer (I_alpha = 1 - T_final, Sec. 3.3.2)
+ *   n_last_dev   out int32 [H][W]  position, in the pixel's tile list, of the
+ *                last layer with alpha > 0 (-1: none); saved for the backward */
+int32_t dbmp_render_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg,
+                        float T_stop, float *image_dev, float *T_final_dev, int32_t *n_last_dev,
+                        dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
+/* Backward (Eq. 6; Eqs. S4-S5, Sec. S1.2)                                    */
+/* ------------------------------------------------------------------------- */
+/* Gradient of a scalar loss L w.r.t. the raw parameters (logits for nu and c),
+ * given dL/dI (3 x H x W) and optionally dL/dI_alpha (H x W, NULL = 0).
+ * Requires the dbmp_bin + dbmp_render_fwd of the same inputs (T_final and n_last
+ * are that forward's outputs).  Each tile is walked back to front from its
+ * largest n_last, recovering T_k = T_{k+1} / (1 - alpha_k) (the forward stores
+ * no per-layer state); the exact derivative is taken, including the background
+ * term Eq. S5 omits.  Per-(pixel, layer) terms are reduced across each warp by
+ * shuffles, then added with one atomic per primitive per warp, so dparams is
+ * exact up to float32 summation order.
+ *   dparams_dev  float32 [N][8], ACCUMULATED into (zero it first). */
+int32_t dbmp_render_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg,
+                        float T_stop, const float *dL_dimage_dev, const float *dL_dalpha_dev,
+                        const float *T_final_dev, const int32_t *n_last_dev, float *dparams_dev,
+                        dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
+/* Loss and optimiser (Tab. S1: MSE loss, Adam-like optimiser with per-group   */
+/* learning-rate gains and exponential decay; compute_psnr)                   */
+/* ------------------------------------------------------------------------- */
+/* L = mean((I - I*)^2) over n elements; dL_dI_dev = 2 (I - I*) / n; loss_dev
+ * (device double[1]) = L.  PSNR = 10 log10(1 / L) for images in [0, 1]. */
+int32_t dbmp_mse_grad(const float *image_dev, const float *target_dev, int64_t n,
+                      float *dL_dI_dev, double *loss_dev, dbmp_stream_t stream);
+
+typedef struct {
+    float lr;        /* base learning rate (Tab. S1: 0.1)                      */
+    float gamma;     /* exponential decay per step: lr_t = lr gamma^(t-1)      */
+    float beta1, beta2, eps;
+    float gains[8];  /* per parameter column (Tab. S1: 10 10 10 1 1.5 1 1 1)  */
+} DbmpAdamConfig;
+
+/* One bias-corrected Adam step on params/m/v (float32 [N][8]).  step_dev is a
+ * device int32 counter of completed steps: this call uses t = *step_dev + 1 and
+ * then increments it, so a captured CUDA graph replays correct steps. */
+int32_t dbmp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
+                       int32_t N, int32_t *step_dev, const DbmpAdamConfig *cfg,
+                       dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
+/* Batched, persistent rendering of many canvases                             */
+/* ------------------------------------------------------------------------- */
+/* A batch plan fixes the canvases of a step: canvas c is H[c] x W[c], owns the
+ * primitives [prim_offset[c], prim_offset[c+1]) of the concatenated parameter
+ * array, and its image / T_final / n_last / gradient maps start at pixel
+ * pix_offset[c] = sum_{c'<c} H[c'] W[c'] of concatenated per-canvas buffers
+ * (image: 3 planar channels per canvas, i.e. canvas c's image starts at
+ * 3 pix_offset[c]).  All host arrays have n_canvas (+1) entries.  The plan is
+ * uploaded to the workspace (synchronises `stream`); dbmp_batch_render then
+ * reads no host memory, so a whole optimisation step can be captured in a CUDA
+ * graph. */
+typedef struct {
+    int32_t tile;   /* 8, 16 or 32 */
+    int32_t batch;  /* records staged per shared-memory batch: 32, 64, 128 or 256 */
+} DbmpTuning;
+
+int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
+                        const int32_t *prim_offset, const DbmpTuning *tuning,
+                        dbmp_stream_t stream);
+
+typedef enum { DBMP_BATCH_BIN = 1, DBMP_BATCH_FWD = 2, DBMP_BATCH_BWD = 4 } DbmpBatchMode;
+
+/* Bins all canvases (one launch per stage), then renders every (canvas, tile)
+ * work item with one persistent forward launch (and one backward launch):
+ * resident CTAs pull items from an atomic queue ordered by decreasing list
+ * length (longest-processing-time first).  `mode` is an OR of DbmpBatchMode.
+ * Pointers follow the plan's concatenated layouts; bg must be NONE or CONST. */
+int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                          const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
+                          float T_stop, int32_t mode, float *image_dev, float *T_final_dev,
+                          int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
+                          dbmp_stream_t stream);
+
+/* Autotuner: times every (tile, batch) candidate on the planned batch (or a
+ * single canvas when n_canvas == 0 in the plan) with CUDA events, reps times
+ * each, and writes the fastest to *best.  Synchronises `stream`; re-plans the
+ * workspace with the winner. */
+int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                      const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
+                      float T_stop, int32_t mode, float *image_dev, float *T_final_dev,
+                      int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
+                      int32_t reps, DbmpTuning *best, float *best_ms, dbmp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBMP_H */

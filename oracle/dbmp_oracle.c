@@ -267,10 +267,26 @@ static void pixel_grad(const orc_prim *P, int32_t Hb, int32_t Wb, const orc_laye
 /* Gradient of L w.r.t. every primitive's raw parameters, summed over the whole
  * canvas.  dL_dimage: 3 x H x W (planar), dL_dalpha: H x W or NULL.  dparams: N x 8,
  * overwritten.  Same T_stop semantics as the forward. */
+void oracle_grad_rows(int32_t H, int32_t W, int32_t N, const float *params,
+                      const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
+                      int32_t Wb, double alpha_max, int32_t bg_mode, const double *bg_rgb,
+                      const float *bg_buf, double T_stop, const double *dL_dimage,
+                      const double *dL_dalpha, int32_t y0, int32_t y1, double *dparams);
+
 void oracle_grad(int32_t H, int32_t W, int32_t N, const float *params, const int32_t *bitmap_id,
                  const float *atlas, int32_t n_bmp, int32_t Hb, int32_t Wb, double alpha_max,
                  int32_t bg_mode, const double *bg_rgb, const float *bg_buf, double T_stop,
                  const double *dL_dimage, const double *dL_dalpha, double *dparams) {
+    oracle_grad_rows(H, W, N, params, bitmap_id, atlas, n_bmp, Hb, Wb, alpha_max, bg_mode, bg_rgb,
+                     bg_buf, T_stop, dL_dimage, dL_dalpha, 0, H, dparams);
+}
+
+/* The same sum restricted to the canvas rows y0 <= y < y1 (a bounded sample). */
+void oracle_grad_rows(int32_t H, int32_t W, int32_t N, const float *params,
+                      const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
+                      int32_t Wb, double alpha_max, int32_t bg_mode, const double *bg_rgb,
+                      const float *bg_buf, double T_stop, const double *dL_dimage,
+                      const double *dL_dalpha, int32_t y0, int32_t y1, double *dparams) {
     (void)n_bmp;
     orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
     size_t HW = (size_t)H * (size_t)W;
@@ -280,7 +296,7 @@ void oracle_grad(int32_t H, int32_t W, int32_t N, const float *params, const int
         double *Gloc = (double *)calloc(8 * (size_t)(N > 0 ? N : 1), sizeof(double));
         orc_layer *Ls = (orc_layer *)malloc(sizeof(orc_layer) * (size_t)(N > 0 ? N : 1));
 #pragma omp for schedule(dynamic, 64)
-        for (int64_t i = 0; i < (int64_t)HW; ++i) {
+        for (int64_t i = (int64_t)y0 * W; i < (int64_t)y1 * W; ++i) {
             int32_t x = (int32_t)(i % W), y = (int32_t)(i / W);
             double C[3], T, g[3], b[3];
             int32_t last;

@@ -42,6 +42,12 @@ def lib():
                                   _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_double, ctypes.c_int32, _f64p, _f32p, ctypes.c_double,
                                   _f64p, _f64p, _f64p]
+        L.oracle_grad_rows.restype = None
+        L.oracle_grad_rows.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p, _i32p,
+                                       _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_int32, _f64p, _f32p,
+                                       ctypes.c_double, _f64p, _f64p, ctypes.c_int32,
+                                       ctypes.c_int32, _f64p]
         L.oracle_grad_selected.restype = None
         L.oracle_grad_selected.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p,
                                            _i32p, _f32p, ctypes.c_int32, ctypes.c_int32,
@@ -139,6 +145,22 @@ def grad(H, W, params, bitmap_id, atlas, dL_dimage, dL_dalpha=None, alpha_max=1.
                       atlas.shape[0], atlas.shape[1], atlas.shape[2], float(alpha_max), mode,
                       _p(rgb, _f64p), _p(buf, _f32p), float(T_stop), _p(gI, _f64p),
                       _p(gA, _f64p), _p(out, _f64p))
+    return out
+
+
+def grad_rows(H, W, params, bitmap_id, atlas, dL_dimage, y0, y1, dL_dalpha=None, alpha_max=1.0,
+              background=(1.0, 1.0, 1.0), T_stop=0.0):
+    """dL/dparams (N, 8) summed over canvas rows y0 <= y < y1 only."""
+    params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
+    mode, rgb, buf = _bg(background, H, W)
+    N = params.shape[0]
+    gI = np.ascontiguousarray(dL_dimage, dtype=np.float64).reshape(3, H, W)
+    gA = None if dL_dalpha is None else np.ascontiguousarray(dL_dalpha, np.float64).reshape(H, W)
+    out = np.zeros((N, 8), np.float64)
+    lib().oracle_grad_rows(H, W, N, _p(params, _f32p), _p(bitmap_id, _i32p), _p(atlas, _f32p),
+                           atlas.shape[0], atlas.shape[1], atlas.shape[2], float(alpha_max), mode,
+                           _p(rgb, _f64p), _p(buf, _f32p), float(T_stop), _p(gI, _f64p),
+                           _p(gA, _f64p), int(y0), int(y1), _p(out, _f64p))
     return out
 
 

@@ -1,0 +1,611 @@
+// C ABI of libdbmp: argument checking, workspaces, plans, and the entry points
+// declared in include/dbmp.h.  No exception crosses the ABI.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dbmp_internal.cuh"
+
+using namespace dbmp;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int32_t fail(int32_t code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int32_t cuda_fail(cudaError_t e, const char *what) {
+    return fail(DBMP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define DBMP_CUDA(call, what)                          \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+constexpr int32_t kMaxTilesPerCanvas = 24576;  // scatter cursors: 8 B each in shared memory
+constexpr int64_t kHistCap = 16 << 20;         // chunk x tile histogram entries
+
+bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
+bool batch_ok(int32_t b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+
+}  // namespace
+
+struct DbmpAtlas {
+    float4 *quad = nullptr;
+    int32_t n_bmp = 0, Hb = 0, Wb = 0;
+    AtlasView view() const { return AtlasView{quad, n_bmp, Hb, Wb}; }
+};
+
+struct DbmpWorkspace {
+    DbmpLimits lim{};
+    // device
+    PrimRec *rec = nullptr;
+    int4 *rect = nullptr;
+    float *graw = nullptr;
+    int64_t *tile_off = nullptr;
+    int32_t *tile_order = nullptr;
+    int32_t *bucket = nullptr;
+    int32_t *list = nullptr;
+    int32_t *hist = nullptr;
+    CanvasDesc *canvas = nullptr;
+    DevStatus *status = nullptr;
+    // host copy of the current plan
+    std::vector<CanvasDesc> plan;
+    std::vector<int32_t> plan_H, plan_W, plan_off;
+    int32_t n_canvas = 0, n_tiles = 0, n_chunks = 0, N = 0, max_tpc = 0;
+    int64_t n_pix = 0;
+    RenderCfg cfg{16, 128};
+    bool persistent = false;
+    bool binned = false;
+    const float *params = nullptr;  // of the last binning (gradient finalisation)
+    int32_t Hb = 0, Wb = 0;
+    float alpha_max = 1.0f;
+};
+
+namespace {
+
+size_t ws_bytes(const DbmpLimits &l) {
+    size_t b = 0;
+    b += sizeof(PrimRec) * (size_t)l.max_prims;
+    b += sizeof(int4) * (size_t)l.max_prims;
+    b += sizeof(float) * 8 * (size_t)l.max_prims;
+    b += sizeof(int64_t) * ((size_t)l.max_tiles + 1);
+    b += sizeof(int32_t) * (size_t)l.max_tiles;
+    b += sizeof(int32_t) * 128;
+    b += sizeof(int32_t) * (size_t)l.max_pairs;
+    b += sizeof(int32_t) * (size_t)kHistCap;
+    b += sizeof(CanvasDesc) * (size_t)l.max_canvases;
+    b += sizeof(DevStatus);
+    return b;
+}
+
+int32_t check_limits(const DbmpLimits *l) {
+    if (!l) return fail(DBMP_ERR_INVALID_ARG, "limits is NULL");
+    if (l->max_prims < 0 || l->max_tiles < 1 || l->max_pairs < 1 || l->max_canvases < 1)
+        return fail(DBMP_ERR_INVALID_ARG, "limits: max_prims >= 0, max_tiles/max_pairs/max_canvases >= 1");
+    if (l->max_pairs > ((int64_t)1 << 31) - 1)
+        return fail(DBMP_ERR_INVALID_ARG, "limits: max_pairs must fit int32 list positions");
+    return DBMP_OK;
+}
+
+// Builds canvas descriptors for a plan (host), choosing the binning chunk size so
+// the chunk x tile histogram fits its capacity.
+int32_t build_plan(DbmpWorkspace *ws, int32_t n, const int32_t *H, const int32_t *W,
+                   const int32_t *off, int32_t tile) {
+    if (!tile_ok(tile)) return fail(DBMP_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", tile);
+    if (n < 1 || n > ws->lim.max_canvases)
+        return fail(DBMP_ERR_INVALID_ARG, "n_canvas %d outside [1, %d]", n, ws->lim.max_canvases);
+    std::vector<CanvasDesc> cv((size_t)n);
+    int64_t tiles = 0, pix = 0;
+    int32_t max_tpc = 0;
+    if (off[0] != 0) return fail(DBMP_ERR_INVALID_ARG, "prim_offset[0] must be 0");
+    for (int c = 0; c < n; ++c) {
+        if (H[c] < 1 || W[c] < 1) return fail(DBMP_ERR_INVALID_ARG, "canvas %d: H, W must be >= 1", c);
+        if (off[c + 1] < off[c]) return fail(DBMP_ERR_INVALID_ARG, "prim_offset must be non-decreasing");
+        CanvasDesc &d = cv[c];
+        d.H = H[c];
+        d.W = W[c];
+        d.ntx = (W[c] + tile - 1) / tile;
+        d.nty = (H[c] + tile - 1) / tile;
+        const int64_t t = (int64_t)d.ntx * d.nty;
+        if (t > kMaxTilesPerCanvas)
+            return fail(DBMP_ERR_INVALID_ARG, "canvas %d has %lld tiles of %d px (max %d per canvas)", c,
+                        (long long)t, tile, kMaxTilesPerCanvas);
+        max_tpc = std::max<int32_t>(max_tpc, (int32_t)t);
+        d.tile_base = (int32_t)tiles;
+        d.prim_base = off[c];
+        d.N = off[c + 1] - off[c];
+        d.pix_base = pix;
+        tiles += t;
+        pix += (int64_t)H[c] * W[c];
+    }
+    const int64_t N = off[n];
+    if (N > ws->lim.max_prims)
+        return fail(DBMP_ERR_INVALID_ARG, "%lld primitives exceed the workspace limit %d", (long long)N,
+                    ws->lim.max_prims);
+    if (tiles > ws->lim.max_tiles)
+        return fail(DBMP_ERR_INVALID_ARG, "%lld tiles exceed the workspace limit %d", (long long)tiles,
+                    ws->lim.max_tiles);
+    // smallest common chunk size (>= 128 primitives) whose histogram fits
+    int lg = 7;
+    for (;; ++lg) {
+        int64_t h = 0;
+        for (auto &d : cv) h += (int64_t)((d.N + (1 << lg) - 1) >> lg) * d.ntx * d.nty;
+        if (h <= kHistCap) break;
+        if (lg > 24) return fail(DBMP_ERR_INVALID_ARG, "binning histogram does not fit");
+    }
+    int64_t hb = 0;
+    int32_t chunks = 0;
+    for (auto &d : cv) {
+        d.chunk_log2 = lg;
+        d.n_chunks = (d.N + (1 << lg) - 1) >> lg;
+        d.chunk_base = chunks;
+        d.hist_base = hb;
+        chunks += d.n_chunks;
+        hb += (int64_t)d.n_chunks * d.ntx * d.nty;
+    }
+    ws->plan = cv;
+    ws->plan_H.assign(H, H + n);
+    ws->plan_W.assign(W, W + n);
+    ws->plan_off.assign(off, off + n + 1);
+    ws->n_canvas = n;
+    ws->n_tiles = (int32_t)tiles;
+    ws->n_chunks = chunks;
+    ws->N = (int32_t)N;
+    ws->max_tpc = max_tpc;
+    ws->n_pix = pix;
+    ws->cfg.tile = tile;
+    return DBMP_OK;
+}
+
+__global__ void k_set_canvas(CanvasDesc d, CanvasDesc *dst) { *dst = d; }
+
+int32_t check_atlas(const DbmpAtlas *atlas) {
+    if (!atlas || !atlas->quad) return fail(DBMP_ERR_INVALID_ARG, "atlas is NULL");
+    return DBMP_OK;
+}
+
+int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const DbmpAtlas *atlas,
+               float alpha_max, cudaStream_t st) {
+    BinBuffers b;
+    b.rec = ws->rec;
+    b.rect = ws->rect;
+    b.hist = ws->hist;
+    b.tile_off = ws->tile_off;
+    b.list = ws->list;
+    b.cap = ws->lim.max_pairs;
+    b.tile_order = ws->persistent ? ws->tile_order : nullptr;
+    b.bucket = ws->bucket;
+    b.status = ws->status;
+    b.canvas = ws->canvas;
+    b.n_canvas = ws->n_canvas;
+    b.n_tiles = ws->n_tiles;
+    b.n_chunks = ws->n_chunks;
+    b.N = ws->N;
+    b.max_tiles_per_canvas = ws->max_tpc;
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->n_degenerate, 0, sizeof(int32_t), st), "status reset");
+    DBMP_CUDA(launch_bin(b, params, bid, atlas->view(), alpha_max, ws->cfg.tile, st), "bin launch");
+    ws->params = params;
+    ws->Hb = atlas->Hb;
+    ws->Wb = atlas->Wb;
+    ws->alpha_max = alpha_max;
+    ws->binned = true;
+    return DBMP_OK;
+}
+
+RenderArgs make_args(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg, float T_stop) {
+    RenderArgs a{};
+    a.rec = ws->rec;
+    a.tile_off = ws->tile_off;
+    a.list = ws->list;
+    a.tile_order = ws->persistent ? ws->tile_order : nullptr;
+    a.canvas = ws->canvas;
+    a.n_canvas = ws->n_canvas;
+    a.n_tiles = ws->n_tiles;
+    a.status = ws->status;
+    a.atlas = atlas->view();
+    a.bg_mode = bg ? bg->mode : DBMP_BG_NONE;
+    if (bg && bg->mode == DBMP_BG_CONST) {
+        a.bg0 = bg->rgb[0];
+        a.bg1 = bg->rgb[1];
+        a.bg2 = bg->rgb[2];
+    }
+    a.bg_buf = bg ? bg->buf_dev : nullptr;
+    a.T_stop = T_stop;
+    a.graw = ws->graw;
+    return a;
+}
+
+int32_t check_bg(const DbmpBackground *bg) {
+    if (!bg) return DBMP_OK;
+    if (bg->mode != DBMP_BG_NONE && bg->mode != DBMP_BG_CONST && bg->mode != DBMP_BG_BUFFER)
+        return fail(DBMP_ERR_INVALID_ARG, "background mode %d unknown", bg->mode);
+    if (bg->mode == DBMP_BG_BUFFER && !bg->buf_dev)
+        return fail(DBMP_ERR_INVALID_ARG, "background buffer is NULL");
+    return DBMP_OK;
+}
+
+int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg, float T_stop,
+               float *image, float *T_final, int32_t *n_last, cudaStream_t st) {
+    RenderArgs a = make_args(ws, atlas, bg, T_stop);
+    a.image = image;
+    a.T_final = T_final;
+    a.n_last = n_last;
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(launch_fwd(a, ws->cfg, ws->persistent, st), "forward launch");
+    return DBMP_OK;
+}
+
+int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg, float T_stop,
+               const float *dL_dimage, const float *dL_dalpha, const float *T_final,
+               const int32_t *n_last, float *dparams, cudaStream_t st) {
+    RenderArgs a = make_args(ws, atlas, bg, T_stop);
+    a.T_final = const_cast<float *>(T_final);
+    a.n_last = const_cast<int32_t *>(n_last);
+    a.dL_dimage = dL_dimage;
+    a.dL_dalpha = dL_dalpha;
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, sizeof(int64_t), st), "status reset");
+    if (ws->N > 0)
+        DBMP_CUDA(cudaMemsetAsync(ws->graw, 0, sizeof(float) * 8 * (size_t)ws->N, st), "graw reset");
+    DBMP_CUDA(launch_bwd(a, ws->cfg, ws->persistent, st), "backward launch");
+    DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, ws->alpha_max,
+                                   ws->Hb, ws->Wb, st),
+              "gradient finalize");
+    return DBMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dbmp_last_error(void) { return g_err; }
+
+int32_t dbmp_abi_version(void) { return 1; }
+
+int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b,
+                          dbmp_stream_t stream, DbmpAtlas **out) {
+    if (!out) return fail(DBMP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!texels_dev) return fail(DBMP_ERR_INVALID_ARG, "texels_dev is NULL");
+    if (n_bmp < 1 || H_b < 2 || W_b < 2)
+        return fail(DBMP_ERR_INVALID_ARG, "atlas needs n_bmp >= 1 and H_b, W_b >= 2");
+    if ((int64_t)n_bmp * (H_b + 1) * (W_b + 1) > ((int64_t)1 << 31) - 1)
+        return fail(DBMP_ERR_INVALID_ARG, "atlas too large for int32 texel offsets");
+    DbmpAtlas *a = new DbmpAtlas;
+    a->n_bmp = n_bmp;
+    a->Hb = H_b;
+    a->Wb = W_b;
+    cudaError_t e = cudaMalloc(&a->quad, sizeof(float4) * (size_t)n_bmp * (H_b + 1) * (W_b + 1));
+    if (e != cudaSuccess) {
+        delete a;
+        return fail(DBMP_ERR_NO_MEMORY, "atlas allocation: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    e = launch_quad_build(texels_dev, a->quad, n_bmp, H_b, W_b, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(a->quad);
+        delete a;
+        return cuda_fail(e, "atlas build");
+    }
+    *out = a;
+    return DBMP_OK;
+}
+
+int32_t dbmp_atlas_update(DbmpAtlas *atlas, const float *texels_dev, dbmp_stream_t stream) {
+    if (int32_t r = check_atlas(atlas)) return r;
+    if (!texels_dev) return fail(DBMP_ERR_INVALID_ARG, "texels_dev is NULL");
+    DBMP_CUDA(launch_quad_build(texels_dev, atlas->quad, atlas->n_bmp, atlas->Hb, atlas->Wb,
+                                (cudaStream_t)stream),
+              "atlas update");
+    return DBMP_OK;
+}
+
+int32_t dbmp_atlas_destroy(DbmpAtlas *atlas) {
+    if (!atlas) return DBMP_OK;
+    cudaFree(atlas->quad);
+    delete atlas;
+    return DBMP_OK;
+}
+
+int32_t dbmp_workspace_bytes(const DbmpLimits *limits, size_t *bytes) {
+    if (int32_t r = check_limits(limits)) return r;
+    if (!bytes) return fail(DBMP_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = ws_bytes(*limits);
+    return DBMP_OK;
+}
+
+int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
+    if (!out) return fail(DBMP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (int32_t r = check_limits(limits)) return r;
+    DbmpWorkspace *ws = new DbmpWorkspace;
+    ws->lim = *limits;
+    const DbmpLimits &l = *limits;
+    struct Req {
+        void **p;
+        size_t n;
+    } reqs[] = {
+        {(void **)&ws->rec, sizeof(PrimRec) * (size_t)std::max(l.max_prims, 1)},
+        {(void **)&ws->rect, sizeof(int4) * (size_t)std::max(l.max_prims, 1)},
+        {(void **)&ws->graw, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1)},
+        {(void **)&ws->tile_off, sizeof(int64_t) * ((size_t)l.max_tiles + 1)},
+        {(void **)&ws->tile_order, sizeof(int32_t) * (size_t)l.max_tiles},
+        {(void **)&ws->bucket, sizeof(int32_t) * 128},
+        {(void **)&ws->list, sizeof(int32_t) * (size_t)l.max_pairs},
+        {(void **)&ws->hist, sizeof(int32_t) * (size_t)kHistCap},
+        {(void **)&ws->canvas, sizeof(CanvasDesc) * (size_t)l.max_canvases},
+        {(void **)&ws->status, sizeof(DevStatus)},
+    };
+    for (auto &r : reqs) {
+        cudaError_t e = cudaMalloc(r.p, r.n);
+        if (e != cudaSuccess) {
+            dbmp_workspace_destroy(ws);
+            return fail(DBMP_ERR_NO_MEMORY, "workspace allocation of %zu bytes: %s", r.n,
+                        cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaMemset(ws->status, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dbmp_workspace_destroy(ws);
+        return cuda_fail(e, "workspace init");
+    }
+    *out = ws;
+    return DBMP_OK;
+}
+
+int32_t dbmp_workspace_destroy(DbmpWorkspace *ws) {
+    if (!ws) return DBMP_OK;
+    void *ptrs[] = {ws->rec, ws->rect, ws->graw, ws->tile_off, ws->tile_order,
+                    ws->bucket, ws->list, ws->hist, ws->canvas, ws->status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ws;
+    return DBMP_OK;
+}
+
+int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStatus *out) {
+    if (!ws || !out) return fail(DBMP_ERR_INVALID_ARG, "ws/out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBMP_CUDA(cudaStreamSynchronize(st), "status sync");
+    DevStatus s;
+    DBMP_CUDA(cudaMemcpy(&s, ws->status, sizeof s, cudaMemcpyDeviceToHost), "status copy");
+    out->code = s.code;
+    out->n_degenerate = s.n_degenerate;
+    out->pairs_required = s.pairs_required;
+    out->pairs_evaluated = s.pairs_eval_fwd;
+    out->pairs_evaluated_bwd = s.pairs_eval_bwd;
+    const int32_t zero = 0;
+    DBMP_CUDA(cudaMemcpy(&ws->status->code, &zero, sizeof zero, cudaMemcpyHostToDevice), "status clear");
+    if (s.code == DBMP_ERR_CAPACITY)
+        fail(DBMP_ERR_CAPACITY, "tile lists need %lld entries, workspace holds %lld",
+             (long long)s.pairs_required, (long long)ws->lim.max_pairs);
+    return s.code;
+}
+
+int32_t dbmp_bin(DbmpWorkspace *ws, int32_t H, int32_t W, int32_t tile, const float *params_dev,
+                 const int32_t *bitmap_id_dev, int32_t N, const DbmpAtlas *atlas, float alpha_max,
+                 dbmp_stream_t stream) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    if (int32_t r = check_atlas(atlas)) return r;
+    if (N < 0) return fail(DBMP_ERR_INVALID_ARG, "N must be >= 0");
+    if (N > 0 && (!params_dev || !bitmap_id_dev))
+        return fail(DBMP_ERR_INVALID_ARG, "params_dev / bitmap_id_dev is NULL");
+    if (!(alpha_max > 0.0f && alpha_max <= 1.0f))
+        return fail(DBMP_ERR_INVALID_ARG, "alpha_max must be in (0, 1]");
+    if (N > 0 && (((uintptr_t)params_dev) & 15))
+        return fail(DBMP_ERR_INVALID_ARG, "params_dev must be 16-byte aligned");
+    const int32_t off[2] = {0, N};
+    if (int32_t r = build_plan(ws, 1, &H, &W, off, tile)) return r;
+    ws->persistent = false;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_set_canvas<<<1, 1, 0, st>>>(ws->plan[0], ws->canvas);
+    DBMP_CUDA(cudaGetLastError(), "plan upload");
+    return do_bin(ws, params_dev, bitmap_id_dev, atlas, alpha_max, st);
+}
+
+int32_t dbmp_get_tile_lists(DbmpWorkspace *ws, int64_t *offsets_dev, int32_t *list_dev, int64_t cap,
+                            int32_t *n_tiles_out, dbmp_stream_t stream) {
+    if (!ws || !offsets_dev || (!list_dev && cap > 0))
+        return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (!ws->binned) return fail(DBMP_ERR_NOT_READY, "no binning in this workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBMP_CUDA(cudaMemcpyAsync(offsets_dev, ws->tile_off, sizeof(int64_t) * ((size_t)ws->n_tiles + 1),
+                              cudaMemcpyDeviceToDevice, st),
+              "offsets copy");
+    const int64_t n = std::min<int64_t>(cap, ws->lim.max_pairs);
+    if (n > 0)
+        DBMP_CUDA(cudaMemcpyAsync(list_dev, ws->list, sizeof(int32_t) * (size_t)n,
+                                  cudaMemcpyDeviceToDevice, st),
+                  "list copy");
+    if (n_tiles_out) *n_tiles_out = ws->n_tiles;
+    return DBMP_OK;
+}
+
+int32_t dbmp_render_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg,
+                        float T_stop, float *image_dev, float *T_final_dev, int32_t *n_last_dev,
+                        dbmp_stream_t stream) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    if (int32_t r = check_atlas(atlas)) return r;
+    if (int32_t r = check_bg(bg)) return r;
+    if (!ws->binned) return fail(DBMP_ERR_NOT_READY, "dbmp_render_fwd needs a prior dbmp_bin");
+    if (atlas->Hb != ws->Hb || atlas->Wb != ws->Wb)
+        return fail(DBMP_ERR_INVALID_ARG, "atlas differs from the binned one");
+    if (!image_dev || !T_final_dev || !n_last_dev) return fail(DBMP_ERR_INVALID_ARG, "output is NULL");
+    if (!(T_stop >= 0.0f && T_stop < 1.0f)) return fail(DBMP_ERR_INVALID_ARG, "T_stop must be in [0, 1)");
+    return do_fwd(ws, atlas, bg, T_stop, image_dev, T_final_dev, n_last_dev, (cudaStream_t)stream);
+}
+
+int32_t dbmp_render_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg,
+                        float T_stop, const float *dL_dimage_dev, const float *dL_dalpha_dev,
+                        const float *T_final_dev, const int32_t *n_last_dev, float *dparams_dev,
+                        dbmp_stream_t stream) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    if (int32_t r = check_atlas(atlas)) return r;
+    if (int32_t r = check_bg(bg)) return r;
+    if (!ws->binned) return fail(DBMP_ERR_NOT_READY, "dbmp_render_bwd needs a prior dbmp_bin");
+    if (!dL_dimage_dev || !T_final_dev || !n_last_dev || (!dparams_dev && ws->N > 0))
+        return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (!(T_stop >= 0.0f && T_stop < 1.0f)) return fail(DBMP_ERR_INVALID_ARG, "T_stop must be in [0, 1)");
+    return do_bwd(ws, atlas, bg, T_stop, dL_dimage_dev, dL_dalpha_dev, T_final_dev, n_last_dev,
+                  dparams_dev, (cudaStream_t)stream);
+}
+
+int32_t dbmp_mse_grad(const float *image_dev, const float *target_dev, int64_t n, float *dL_dI_dev,
+                      double *loss_dev, dbmp_stream_t stream) {
+    if (n < 0) return fail(DBMP_ERR_INVALID_ARG, "n must be >= 0");
+    if (!loss_dev || (n > 0 && (!image_dev || !target_dev || !dL_dI_dev)))
+        return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    DBMP_CUDA(launch_mse_grad(image_dev, target_dev, n, dL_dI_dev, loss_dev, (cudaStream_t)stream),
+              "mse launch");
+    return DBMP_OK;
+}
+
+int32_t dbmp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
+                       int32_t N, int32_t *step_dev, const DbmpAdamConfig *cfg, dbmp_stream_t stream) {
+    if (!cfg || !step_dev) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (N < 0) return fail(DBMP_ERR_INVALID_ARG, "N must be >= 0");
+    if (N > 0 && (!params_dev || !grad_dev || !m_dev || !v_dev))
+        return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (!(cfg->beta1 >= 0 && cfg->beta1 < 1 && cfg->beta2 >= 0 && cfg->beta2 < 1 && cfg->eps > 0))
+        return fail(DBMP_ERR_INVALID_ARG, "Adam betas must be in [0, 1) and eps > 0");
+    DBMP_CUDA(launch_adam(params_dev, grad_dev, m_dev, v_dev, N, step_dev, *cfg, (cudaStream_t)stream),
+              "adam launch");
+    return DBMP_OK;
+}
+
+int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
+                        const int32_t *prim_offset, const DbmpTuning *tuning, dbmp_stream_t stream) {
+    if (!ws || !H || !W || !prim_offset) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    const int32_t tile = tuning ? tuning->tile : 16;
+    const int32_t batch = tuning ? tuning->batch : 128;
+    if (!batch_ok(batch)) return fail(DBMP_ERR_INVALID_ARG, "batch must be 32, 64, 128 or 256");
+    if (int32_t r = build_plan(ws, n_canvas, H, W, prim_offset, tile)) return r;
+    ws->cfg.batch = batch;
+    ws->persistent = true;
+    ws->binned = false;
+    cudaStream_t st = (cudaStream_t)stream;
+    DBMP_CUDA(cudaStreamSynchronize(st), "plan sync");
+    DBMP_CUDA(cudaMemcpy(ws->canvas, ws->plan.data(), sizeof(CanvasDesc) * ws->plan.size(),
+                         cudaMemcpyHostToDevice),
+              "plan upload");
+    return DBMP_OK;
+}
+
+int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                          const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
+                          float T_stop, int32_t mode, float *image_dev, float *T_final_dev,
+                          int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
+                          dbmp_stream_t stream) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    if (!ws->persistent || ws->n_canvas < 1)
+        return fail(DBMP_ERR_NOT_READY, "dbmp_batch_render needs dbmp_batch_plan first");
+    if (int32_t r = check_atlas(atlas)) return r;
+    if (int32_t r = check_bg(bg)) return r;
+    if (mode & ~(DBMP_BATCH_BIN | DBMP_BATCH_FWD | DBMP_BATCH_BWD) || mode == 0)
+        return fail(DBMP_ERR_INVALID_ARG, "mode must be an OR of BIN, FWD, BWD");
+    if (!(alpha_max > 0.0f && alpha_max <= 1.0f))
+        return fail(DBMP_ERR_INVALID_ARG, "alpha_max must be in (0, 1]");
+    if (!(T_stop >= 0.0f && T_stop < 1.0f)) return fail(DBMP_ERR_INVALID_ARG, "T_stop must be in [0, 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode & DBMP_BATCH_BIN) {
+        if (ws->N > 0 && (!params_dev || !bitmap_id_dev))
+            return fail(DBMP_ERR_INVALID_ARG, "params_dev / bitmap_id_dev is NULL");
+        if (ws->N > 0 && (((uintptr_t)params_dev) & 15))
+            return fail(DBMP_ERR_INVALID_ARG, "params_dev must be 16-byte aligned");
+        if (int32_t r = do_bin(ws, params_dev, bitmap_id_dev, atlas, alpha_max, st)) return r;
+    } else if (!ws->binned) {
+        return fail(DBMP_ERR_NOT_READY, "no binning for this plan yet (include DBMP_BATCH_BIN)");
+    }
+    if (mode & (DBMP_BATCH_FWD | DBMP_BATCH_BWD)) {
+        if (!T_final_dev || !n_last_dev) return fail(DBMP_ERR_INVALID_ARG, "T_final / n_last is NULL");
+    }
+    if (mode & DBMP_BATCH_FWD) {
+        if (!image_dev) return fail(DBMP_ERR_INVALID_ARG, "image is NULL");
+        if (int32_t r = do_fwd(ws, atlas, bg, T_stop, image_dev, T_final_dev, n_last_dev, st)) return r;
+    }
+    if (mode & DBMP_BATCH_BWD) {
+        if (!dL_dimage_dev || (!dparams_dev && ws->N > 0))
+            return fail(DBMP_ERR_INVALID_ARG, "dL_dimage / dparams is NULL");
+        if (int32_t r = do_bwd(ws, atlas, bg, T_stop, dL_dimage_dev, nullptr, T_final_dev, n_last_dev,
+                               dparams_dev, st))
+            return r;
+    }
+    return DBMP_OK;
+}
+
+int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                      const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg, float T_stop,
+                      int32_t mode, float *image_dev, float *T_final_dev, int32_t *n_last_dev,
+                      const float *dL_dimage_dev, float *dparams_dev, int32_t reps, DbmpTuning *best,
+                      float *best_ms, dbmp_stream_t stream) {
+    if (!ws || !best) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (!ws->persistent || ws->n_canvas < 1)
+        return fail(DBMP_ERR_NOT_READY, "dbmp_autotune needs dbmp_batch_plan first");
+    if (reps < 1) reps = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    const std::vector<int32_t> H = ws->plan_H, W = ws->plan_W, off = ws->plan_off;
+    const int n = ws->n_canvas;
+    cudaEvent_t e0, e1;
+    DBMP_CUDA(cudaEventCreate(&e0), "event");
+    DBMP_CUDA(cudaEventCreate(&e1), "event");
+    float best_t = 1e30f;
+    DbmpTuning bt{ws->cfg.tile, ws->cfg.batch};
+    const int32_t tiles[] = {8, 16, 32};
+    const int32_t batches[] = {32, 64, 128, 256};
+    int32_t rc = DBMP_OK;
+    for (int32_t t : tiles) {
+        for (int32_t b : batches) {
+            DbmpTuning cand{t, b};
+            if (dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &cand, stream) != DBMP_OK) continue;
+            // warm-up (also validates the capacity for this tile size)
+            rc = dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop,
+                                   mode | DBMP_BATCH_BIN, image_dev, T_final_dev, n_last_dev,
+                                   dL_dimage_dev, dparams_dev, stream);
+            if (rc != DBMP_OK) break;
+            DbmpDeviceStatus s;
+            if (dbmp_status_poll(ws, stream, &s) != DBMP_OK) continue;  // e.g. capacity: skip
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps; ++r)
+                dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop,
+                                  mode | DBMP_BATCH_BIN, image_dev, T_final_dev, n_last_dev,
+                                  dL_dimage_dev, dparams_dev, stream);
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "autotune timing");
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < best_t) {
+                best_t = ms;
+                bt = cand;
+            }
+        }
+        if (rc != DBMP_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DBMP_OK) return rc;
+    if (best_t >= 1e30f) return fail(DBMP_ERR_CAPACITY, "no (tile, batch) candidate fits the workspace");
+    *best = bt;
+    if (best_ms) *best_ms = best_t;
+    return dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &bt, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,360 @@
+// Tile binning (Sec. 3.1.1 "Parallelization", Sec. S1.3) on the GPU.
+//
+// The paper bins on the CPU.  Here every step runs on the device:
+//   k_prep     per primitive: FP64 transform coefficients rounded to a 48-byte record
+//              (Eqs. 1-3 folded), and the fp32 bounding-box rectangle of tiles;
+//   k_count    per chunk of primitives: a shared-memory histogram of tile hits;
+//   k_colscan  per tile: exclusive scan over chunks  -> each chunk's base in the tile;
+//   k_tilescan exclusive scan over tiles             -> tile offsets, K = sum_t d_t;
+//   k_scatter  per chunk: walks its primitives in index order and appends each to its
+//              tiles' lists at base + running count (shared-memory cursors).
+// Together this is a stable counting sort keyed on the tile id.  Because primitives
+// are appended in index order, each list comes out sorted front to back, which is
+// exactly the order of the keys (tile << 32 | index): no 64-bit keys are formed and
+// no radix passes over them are needed.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "dbmp_internal.cuh"
+
+namespace dbmp {
+
+namespace {
+
+constexpr int kBinThreads = 256;
+
+__device__ __forceinline__ int find_canvas_by(const CanvasDesc *cv, int n, int value, int which) {
+    // largest c with base(c) <= value; which: 0 = prim_base, 1 = chunk_base, 2 = tile_base
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int b = which == 0 ? cv[mid].prim_base : (which == 1 ? cv[mid].chunk_base : cv[mid].tile_base);
+        if (b <= value) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// |sin|, |cos| of the binning specification: Cody-Waite reduction by pi/2 with a
+// three-part constant, Taylor polynomials of degree 9 (sin) and 8 (cos) on
+// [-pi/4, pi/4].  Every operation rounds once (explicit intrinsics).
+__device__ __forceinline__ void spec_abs_sincos(float th, float &as, float &ac) {
+    if (!(fabsf(th) <= 65536.0f)) {
+        as = 1.0f;
+        ac = 1.0f;
+        return;
+    }
+    const float two_over_pi = 0.636619772367581343f;
+    const float C1 = 1.5703125f;
+    const float C2 = 4.83751296997070312e-4f;
+    const float C3 = 7.54978995489188e-8f;
+    const float k = rintf(__fmul_rn(th, two_over_pi));
+    float r = __fsub_rn(th, __fmul_rn(k, C1));
+    r = __fsub_rn(r, __fmul_rn(k, C2));
+    r = __fsub_rn(r, __fmul_rn(k, C3));
+    const float r2 = __fmul_rn(r, r);
+    float sp = 1.0f / 362880.0f;
+    sp = __fadd_rn(__fmul_rn(sp, r2), -1.0f / 5040.0f);
+    sp = __fadd_rn(__fmul_rn(sp, r2), 1.0f / 120.0f);
+    sp = __fadd_rn(__fmul_rn(sp, r2), -1.0f / 6.0f);
+    const float sr = __fadd_rn(r, __fmul_rn(__fmul_rn(r, r2), sp));
+    float cp = 1.0f / 40320.0f;
+    cp = __fadd_rn(__fmul_rn(cp, r2), -1.0f / 720.0f);
+    cp = __fadd_rn(__fmul_rn(cp, r2), 1.0f / 24.0f);
+    cp = __fadd_rn(__fmul_rn(cp, r2), -0.5f);
+    const float cr = __fadd_rn(1.0f, __fmul_rn(r2, cp));
+    const int ki = (int)k;
+    if (ki & 1) {
+        as = fabsf(cr);
+        ac = fabsf(sr);
+    } else {
+        as = fabsf(sr);
+        ac = fabsf(cr);
+    }
+}
+
+__device__ __forceinline__ bool all_finite8(const float *p) {
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ok = ok && isfinite(p[j]);
+    return ok;
+}
+
+__global__ void k_prep(const float *__restrict__ params, const int32_t *__restrict__ bitmap_id,
+                       const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t N,
+                       AtlasView atlas, float alpha_max, int32_t tile, PrimRec *__restrict__ rec,
+                       int4 *__restrict__ rect, DevStatus *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int c = find_canvas_by(cv, n_canvas, i, 0);
+    const CanvasDesc d = cv[c];
+    float p[8];
+    const float4 *p4 = reinterpret_cast<const float4 *>(params + 8 * (size_t)i);
+    const float4 lo = p4[0], hi = p4[1];
+    p[0] = lo.x; p[1] = lo.y; p[2] = lo.z; p[3] = lo.w;
+    p[4] = hi.x; p[5] = hi.y; p[6] = hi.z; p[7] = hi.w;
+
+    // ---- record (FP64, rounded once) ----
+    const double kw = 0.5 * (double)(atlas.Wb - 1), kv = 0.5 * (double)(atlas.Hb - 1);
+    double sn, cs;
+    sincos((double)p[3], &sn, &cs);
+    const double inv_s = 1.0 / (double)p[2];
+    PrimRec r;
+    r.x = p[0];
+    r.y = p[1];
+    r.A = (float)(kw * cs * inv_s);
+    r.B = (float)(kw * sn * inv_s);
+    r.C = (float)(-kv * sn * inv_s);
+    r.D = (float)(kv * cs * inv_s);
+    r.a = (float)((double)alpha_max / (1.0 + exp(-(double)p[4])));
+    r.quad_off = bitmap_id[i] * (atlas.Hb + 1) * (atlas.Wb + 1);  // checked below
+    r.cr = (float)(1.0 / (1.0 + exp(-(double)p[5])));
+    r.cg = (float)(1.0 / (1.0 + exp(-(double)p[6])));
+    r.cb = (float)(1.0 / (1.0 + exp(-(double)p[7])));
+    r.index = i;
+    const int32_t bid = bitmap_id[i];
+    const bool bid_ok = bid >= 0 && bid < atlas.n_bmp;
+    if (!bid_ok) {
+        r.quad_off = 0;
+        atomicAdd(&status->n_degenerate, 1);
+    }
+    const bool valid = bid_ok && all_finite8(p) && p[2] != 0.0f;
+    if (valid && !(isfinite(r.A) && isfinite(r.B) && isfinite(r.C) && isfinite(r.D))) {
+        // |s| below ~1e-37: the transform overflows float32; the primitive is drawn
+        // with zero opacity and counted.
+        r.a = 0.0f;
+        r.A = r.B = r.C = r.D = 0.0f;
+        atomicAdd(&status->n_degenerate, 1);
+    }
+    rec[i] = r;
+
+    // ---- tile rectangle: the fp32 binning specification ----
+    int4 rc = make_int4(0, 0, -1, -1);
+    if (valid) {
+        const float eu = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(atlas.Wb - 1)));
+        const float ev = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(atlas.Hb - 1)));
+        float as, ac;
+        spec_abs_sincos(p[3], as, ac);
+        const float s = fabsf(p[2]);
+        const float hx = __fmul_rn(s, __fadd_rn(__fmul_rn(ac, eu), __fmul_rn(as, ev)));
+        const float hy = __fmul_rn(s, __fadd_rn(__fmul_rn(as, eu), __fmul_rn(ac, ev)));
+        const float inv_t = __fdiv_rn(1.0f, (float)tile);
+        const float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(p[0], hx), 1.0f), inv_t));
+        const float fx1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(p[0], hx), 1.0f), inv_t));
+        const float fy0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(p[1], hy), 1.0f), inv_t));
+        const float fy1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(p[1], hy), 1.0f), inv_t));
+        const float mx = (float)(d.ntx - 1), my = (float)(d.nty - 1);
+        if (fx1 >= 0.0f && fy1 >= 0.0f && fx0 <= mx && fy0 <= my) {
+            rc.x = fx0 < 0.0f ? 0 : (int)fx0;
+            rc.y = fy0 < 0.0f ? 0 : (int)fy0;
+            rc.z = fx1 > mx ? d.ntx - 1 : (int)fx1;
+            rc.w = fy1 > my ? d.nty - 1 : (int)fy1;
+        }
+    }
+    rect[i] = rc;
+}
+
+__global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restrict__ cv,
+                        int32_t n_canvas, int32_t *__restrict__ hist) {
+    extern __shared__ int32_t sh[];
+    const int chunk = blockIdx.x;
+    const int c = find_canvas_by(cv, n_canvas, chunk, 1);
+    const CanvasDesc d = cv[c];
+    const int ntiles = d.ntx * d.nty;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) sh[t] = 0;
+    __syncthreads();
+    const int local = chunk - d.chunk_base;
+    const int p0 = d.prim_base + (local << d.chunk_log2);
+    const int p1 = min(p0 + (1 << d.chunk_log2), d.prim_base + d.N);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int p = p0 + warp; p < p1; p += nw) {
+        const int4 r = rect[p];
+        const int w = r.z - r.x + 1, h = r.w - r.y + 1;
+        if (w <= 0 || h <= 0) continue;
+        const int tau = w * h;
+        for (int k = lane; k < tau; k += 32) {
+            const int ty = r.y + k / w, tx = r.x + k % w;
+            atomicAdd(&sh[ty * d.ntx + tx], 1);
+        }
+    }
+    __syncthreads();
+    int32_t *row = hist + d.hist_base + (int64_t)local * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = sh[t];
+}
+
+__global__ void k_colscan(const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t n_tiles,
+                          int32_t *__restrict__ hist, int64_t *__restrict__ tile_cnt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const int c = find_canvas_by(cv, n_canvas, t, 2);
+    const CanvasDesc d = cv[c];
+    const int ntiles = d.ntx * d.nty;
+    const int lt = t - d.tile_base;
+    int32_t *col = hist + d.hist_base + lt;
+    int32_t run = 0;
+    for (int k = 0; k < d.n_chunks; ++k) {
+        const int32_t v = col[(int64_t)k * ntiles];
+        col[(int64_t)k * ntiles] = run;
+        run += v;
+    }
+    tile_cnt[t] = run;
+}
+
+// Exclusive scan of n tile counts in place (single CTA of 1024 threads), writes
+// off[n] = K and the capacity verdict.
+__global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, int32_t n,
+                                                   int64_t cap, DevStatus *status) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024 * 4) {
+        int64_t v[4];
+        int64_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = base + tid * 4 + k;
+            v[k] = i < n ? off[i] : 0;
+            s += v[k];
+        }
+        int64_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = warp_sums[lane];
+            int64_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_sums[lane] = wi - w;  // exclusive warp offsets
+        }
+        __syncthreads();
+        int64_t run = carry + warp_sums[warp] + incl - s;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = base + tid * 4 + k;
+            if (i < n) off[i] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == 1023) carry = run;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int64_t K = carry;
+        off[n] = K;
+        status->pairs_required = K;
+        status->lists_valid = K <= cap ? 1 : 0;
+        if (K > cap) status->code = (int32_t)DBMP_ERR_CAPACITY;
+    }
+}
+
+__global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__restrict__ cv,
+                          int32_t n_canvas, const int32_t *__restrict__ hist,
+                          const int64_t *__restrict__ tile_off, int32_t *__restrict__ list,
+                          const DevStatus *status) {
+    extern __shared__ int64_t cur[];
+    if (status->lists_valid == 0) return;
+    const int chunk = blockIdx.x;
+    const int c = find_canvas_by(cv, n_canvas, chunk, 1);
+    const CanvasDesc d = cv[c];
+    const int ntiles = d.ntx * d.nty;
+    const int local = chunk - d.chunk_base;
+    const int32_t *row = hist + d.hist_base + (int64_t)local * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        cur[t] = tile_off[d.tile_base + t] + row[t];
+    __syncthreads();
+    const int p0 = d.prim_base + (local << d.chunk_log2);
+    const int p1 = min(p0 + (1 << d.chunk_log2), d.prim_base + d.N);
+    for (int p = p0; p < p1; ++p) {
+        const int4 r = rect[p];
+        const int w = r.z - r.x + 1, h = r.w - r.y + 1;
+        if (w > 0 && h > 0) {
+            const int tau = w * h;
+            for (int k = threadIdx.x; k < tau; k += blockDim.x) {
+                const int ty = r.y + k / w, tx = r.x + k % w;
+                const int t = ty * d.ntx + tx;
+                list[cur[t]] = p;
+                cur[t] += 1;  // tiles of one primitive are distinct: no race
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- longest-list-first ordering of tiles for the persistent kernels ----
+__device__ __forceinline__ int len_bucket(int64_t len) {
+    // 0 for the longest lists ... 63 for empty
+    return len <= 0 ? 63 : 62 - (63 - __clzll((unsigned long long)len));
+}
+
+__global__ void k_order_count(const int64_t *__restrict__ off, int32_t n, int32_t *__restrict__ bucket) {
+    __shared__ int32_t h[64];
+    if (threadIdx.x < 64) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[len_bucket(off[t + 1] - off[t])], 1);
+    __syncthreads();
+    if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(&bucket[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_order_scan(int32_t *bucket) {
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 64; ++b) {
+            const int v = bucket[b];
+            bucket[b] = run;        // cursor
+            bucket[64 + b] = run;   // start (kept)
+            run += v;
+        }
+    }
+}
+
+__global__ void k_order_scatter(const int64_t *__restrict__ off, int32_t n, int32_t *bucket,
+                                int32_t *__restrict__ order) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int pos = atomicAdd(&bucket[len_bucket(off[t + 1] - off[t])], 1);
+        order[pos] = t;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,
+                       const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st) {
+    if (b.N > 0) {
+        k_prep<<<(b.N + 255) / 256, 256, 0, st>>>(params, bitmap_id, b.canvas, b.n_canvas, b.N, atlas,
+                                                   alpha_max, tile, b.rec, b.rect, b.status);
+    }
+    const size_t sh32 = sizeof(int32_t) * (size_t)b.max_tiles_per_canvas;
+    const size_t sh64 = sizeof(int64_t) * (size_t)b.max_tiles_per_canvas;
+    if (b.n_chunks > 0) {
+        cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32);
+        k_count<<<b.n_chunks, kBinThreads, sh32, st>>>(b.rect, b.canvas, b.n_canvas, b.hist);
+    }
+    k_colscan<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
+                                                       b.tile_off);
+    k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status);
+    if (b.n_chunks > 0) {
+        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64);
+        k_scatter<<<b.n_chunks, kBinThreads, sh64, st>>>(b.rect, b.canvas, b.n_canvas, b.hist,
+                                                         b.tile_off, b.list, b.status);
+    }
+    if (b.tile_order) {
+        cudaMemsetAsync(b.bucket, 0, sizeof(int32_t) * 128, st);
+        const int g = min(1024, (b.n_tiles + 255) / 256);
+        k_order_count<<<g, 256, 0, st>>>(b.tile_off, b.n_tiles, b.bucket);
+        k_order_scan<<<1, 32, 0, st>>>(b.bucket);
+        k_order_scatter<<<g, 256, 0, st>>>(b.tile_off, b.n_tiles, b.bucket, b.tile_order);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dbmp

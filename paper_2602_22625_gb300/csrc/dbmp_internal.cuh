@@ -1,0 +1,156 @@
+// Internal declarations of libdbmp (sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dbmp.h"
+
+namespace dbmp {
+
+// Per-primitive record staged in shared memory by the compositors (48 bytes).
+// U = A (x - x_i) + B (y - y_i) + kw,  V = C (x - x_i) + D (y - y_i) + kv  (Eqs. 1-2
+// folded: A = kw cos/s, B = kw sin/s, C = -kv sin/s, D = kv cos/s, kw = (W_b-1)/2,
+// kv = (H_b-1)/2), computed in FP64 and rounded once.
+struct __align__(16) PrimRec {
+    float x, y, A, B;
+    float C, D, a;       // a = alpha_max sigmoid(nu)  (Eq. 3 without M)
+    int32_t quad_off;    // offset of the primitive's bitmap in the quad atlas (float4 units)
+    float cr, cg, cb;    // sigmoid(c)
+    int32_t index;       // primitive index (row of params / dparams)
+};
+static_assert(sizeof(PrimRec) == 48, "PrimRec layout");
+
+// One canvas of a (possibly single-canvas) batch.
+struct CanvasDesc {
+    int32_t H, W, ntx, nty;
+    int32_t tile_base;   // first global tile id of this canvas
+    int32_t prim_base;   // first primitive of this canvas
+    int32_t N;           // primitives of this canvas
+    int32_t chunk_base;  // first global binning chunk of this canvas
+    int32_t n_chunks;
+    int32_t chunk_log2;  // primitives per binning chunk = 1 << chunk_log2
+    int64_t pix_base;    // first pixel of this canvas in concatenated per-pixel maps
+    int64_t hist_base;   // offset of this canvas' chunk x tile histogram
+};
+
+// Device status block (mirrors DbmpDeviceStatus, plus internal flags).
+struct DevStatus {
+    int32_t code;
+    int32_t n_degenerate;
+    int64_t pairs_required;
+    int64_t pairs_eval_fwd;
+    int64_t pairs_eval_bwd;
+    int32_t lists_valid;   // 1 after a binning that fit its capacity
+    int32_t pad;
+    uint32_t queue[4];     // persistent-kernel work counters
+};
+
+struct AtlasView {
+    const float4 *quad;    // [n_bmp][H_b+1][W_b+1] tap quads
+    int32_t n_bmp, Hb, Wb;
+};
+
+// Tile size and staging batch used by one render.
+struct RenderCfg {
+    int32_t tile;
+    int32_t batch;
+};
+
+// ---------------------------------------------------------------------------
+// The one bilinear sample both compositors use (Eq. 2, Eqs. S1-S3).  Every
+// operation is explicitly rounded (no contraction decided by the compiler), so
+// the forward and backward kernels compute bit-identical M and alpha.
+// Returns false when (U, V) lies outside (-1, W_b) x (-1, H_b), where every tap
+// is zero.  On true: M and the quantities the backward needs.
+// ---------------------------------------------------------------------------
+struct Sample {
+    float Up, Vp;        // U - kw, V - kv
+    float wu, wv;        // fractional parts
+    float d0, d1, m0, m1;
+    float M;
+};
+
+__device__ __forceinline__ bool sample_bitmap(const PrimRec &r, const float4 *__restrict__ quad,
+                                              int32_t Wq, float kw, float kv, float Wbf, float Hbf,
+                                              float px, float py, Sample &s) {
+    const float dx = __fsub_rn(px, r.x);
+    const float dy = __fsub_rn(py, r.y);
+    s.Up = __fmaf_rn(r.A, dx, __fmul_rn(r.B, dy));
+    s.Vp = __fmaf_rn(r.C, dx, __fmul_rn(r.D, dy));
+    const float U = __fadd_rn(s.Up, kw);
+    const float V = __fadd_rn(s.Vp, kv);
+    if (!(U >= -1.0f && U < Wbf && V >= -1.0f && V < Hbf)) return false;
+    const float fu = floorf(U), fv = floorf(V);
+    const int32_t iu = (int32_t)fu, iv = (int32_t)fv;   // in [-1, W_b-1] x [-1, H_b-1]
+    s.wu = __fsub_rn(U, fu);
+    s.wv = __fsub_rn(V, fv);
+    const float4 q = __ldg(quad + r.quad_off + (iv + 1) * Wq + (iu + 1));
+    s.d0 = __fsub_rn(q.y, q.x);                       // p01 - p00
+    s.d1 = __fsub_rn(q.w, q.z);                       // p11 - p10
+    s.m0 = __fmaf_rn(s.wu, s.d0, q.x);
+    s.m1 = __fmaf_rn(s.wu, s.d1, q.z);
+    s.M = __fmaf_rn(s.wv, __fsub_rn(s.m1, s.m0), s.m0);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one translation unit each).
+// ---------------------------------------------------------------------------
+struct BinBuffers {
+    PrimRec *rec;
+    int4 *rect;               // per primitive: tx0, ty0, tx1, ty1 (canvas-local); empty: tx1 < tx0
+    int32_t *hist;            // chunk x tile counts, then bases
+    int64_t *tile_off;        // [n_tiles + 1]
+    int32_t *list;            // [cap] primitive indices (global)
+    int64_t cap;
+    int32_t *tile_order;      // [n_tiles] processing order (longest lists first)
+    int32_t *bucket;          // scratch for the ordering
+    DevStatus *status;
+    const CanvasDesc *canvas; // [n_canvas]
+    int32_t n_canvas;
+    int32_t n_tiles;          // total tiles
+    int32_t n_chunks;         // total chunks
+    int32_t N;                // total primitives
+    int32_t max_tiles_per_canvas;
+};
+
+cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,
+                       const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st);
+
+struct RenderArgs {
+    const PrimRec *rec;
+    const int64_t *tile_off;
+    const int32_t *list;
+    const int32_t *tile_order;  // nullptr: tile id = work item
+    const CanvasDesc *canvas;
+    int32_t n_canvas;
+    int32_t n_tiles;
+    DevStatus *status;
+    AtlasView atlas;
+    int32_t bg_mode;
+    float bg0, bg1, bg2;
+    const float *bg_buf;
+    float T_stop;
+    // forward outputs / backward inputs
+    float *image;
+    float *T_final;
+    int32_t *n_last;
+    const float *dL_dimage;
+    const float *dL_dalpha;
+    float *graw;                // [N][8] raw per-primitive sums (backward)
+};
+
+cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st);
+cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st);
+cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
+                                 float *dparams, int32_t N, float alpha_max, int32_t Hb, int32_t Wb,
+                                 cudaStream_t st);
+cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t n_bmp, int32_t Hb,
+                              int32_t Wb, cudaStream_t st);
+cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
+                            double *loss, cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int32_t N, int32_t *step,
+                        const DbmpAdamConfig &cfg, cudaStream_t st);
+
+}  // namespace dbmp

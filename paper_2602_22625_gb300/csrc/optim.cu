@@ -1,0 +1,117 @@
+// Atlas layout, MSE loss gradient and the Adam update (Tab. S1).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "dbmp_internal.cuh"
+
+namespace dbmp {
+
+namespace {
+
+// quad[b][v0+1][u0+1] = {P[v0,u0], P[v0,u0+1], P[v0+1,u0], P[v0+1,u0+1]}, taps outside
+// the bitmap are 0 (zero padding of the bilinear sample, Sec. S1.1).
+__global__ void k_quad(const float *__restrict__ tex, float4 *__restrict__ quad, int32_t n_bmp,
+                       int32_t Hb, int32_t Wb) {
+    const int64_t cells = (int64_t)(Hb + 1) * (Wb + 1);
+    const int64_t total = cells * n_bmp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / cells);
+        const int c = (int)(i % cells);
+        const int v0 = c / (Wb + 1) - 1, u0 = c % (Wb + 1) - 1;
+        const float *P = tex + (int64_t)b * Hb * Wb;
+        auto tap = [&](int v, int u) -> float {
+            return (u >= 0 && v >= 0 && u < Wb && v < Hb) ? P[(int64_t)v * Wb + u] : 0.0f;
+        };
+        quad[i] = make_float4(tap(v0, u0), tap(v0, u0 + 1), tap(v0 + 1, u0), tap(v0 + 1, u0 + 1));
+    }
+}
+
+__global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg, int64_t n,
+                      float *__restrict__ dL, double *loss) {
+    __shared__ double red[32];
+    const float scale = (float)(2.0 / (double)n);
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = I[i] - Tg[i];
+        dL[i] = scale * d;
+        acc += (double)d * (double)d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(loss, acc / (double)n);
+    }
+}
+
+struct AdamArgs {
+    float lr, gamma, beta1, beta2, eps;
+    float gains[8];
+};
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int64_t n, const int32_t *step, AdamArgs c) {
+    const int t = *step + 1;
+    const float bc1 = 1.0f - powf(c.beta1, (float)t);
+    const float bc2 = 1.0f - powf(c.beta2, (float)t);
+    const float lr_t = c.lr * powf(c.gamma, (float)(t - 1));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = c.beta1 * m[i] + (1.0f - c.beta1) * gi;
+        const float vi = c.beta2 * v[i] + (1.0f - c.beta2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / bc1, vh = vi / bc2;
+        p[i] -= lr_t * c.gains[i & 7] * mh / (sqrtf(vh) + c.eps);
+    }
+}
+
+__global__ void k_step_inc(int32_t *step) { *step += 1; }
+
+int grid_for(int64_t n, int threads) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + threads - 1) / threads;
+    return (int)(want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8);
+}
+
+}  // namespace
+
+cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t n_bmp, int32_t Hb,
+                              int32_t Wb, cudaStream_t st) {
+    const int64_t total = (int64_t)n_bmp * (Hb + 1) * (Wb + 1);
+    k_quad<<<grid_for(total, 256), 256, 0, st>>>(texels, quad, n_bmp, Hb, Wb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
+                            double *loss, cudaStream_t st) {
+    cudaMemsetAsync(loss, 0, sizeof(double), st);
+    if (n > 0) k_mse<<<grid_for(n, 256), 256, 0, st>>>(image, target, n, dL, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int32_t N, int32_t *step,
+                        const DbmpAdamConfig &cfg, cudaStream_t st) {
+    AdamArgs c;
+    c.lr = cfg.lr;
+    c.gamma = cfg.gamma;
+    c.beta1 = cfg.beta1;
+    c.beta2 = cfg.beta2;
+    c.eps = cfg.eps;
+    for (int j = 0; j < 8; ++j) c.gains[j] = cfg.gains[j];
+    const int64_t n = (int64_t)N * 8;
+    if (n > 0) k_adam<<<grid_for(n, 256), 256, 0, st>>>(p, g, m, v, n, step, c);
+    k_step_inc<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError();
+}
+
+}  // namespace dbmp

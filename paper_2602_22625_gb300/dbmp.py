@@ -1,0 +1,279 @@
+"""Python binding of libdbmp (include/dbmp.h): argument marshalling only.
+
+Every function named dbmp_* here calls the C entry point of the same name with
+raw device pointers taken from torch tensors; all computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+DBMP_OK = 0
+DBMP_ERR_INVALID_ARG = -1
+DBMP_ERR_CAPACITY = -2
+DBMP_ERR_CUDA = -3
+DBMP_ERR_TIMEOUT = -4
+DBMP_ERR_NOT_READY = -5
+DBMP_ERR_NO_MEMORY = -6
+
+BG_NONE, BG_CONST, BG_BUFFER = 0, 1, 2
+BATCH_BIN, BATCH_FWD, BATCH_BWD = 1, 2, 4
+
+#: every entry point include/dbmp.h declares
+EXPORTS = (
+    "dbmp_last_error", "dbmp_abi_version", "dbmp_atlas_create", "dbmp_atlas_destroy",
+    "dbmp_atlas_update", "dbmp_workspace_bytes", "dbmp_workspace_create", "dbmp_workspace_destroy",
+    "dbmp_status_poll", "dbmp_bin", "dbmp_get_tile_lists", "dbmp_render_fwd", "dbmp_render_bwd",
+    "dbmp_mse_grad", "dbmp_adam_step", "dbmp_batch_plan", "dbmp_batch_render", "dbmp_autotune",
+)
+
+
+class DbmpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdbmp error {code}: {msg}")
+        self.code = code
+
+
+class DbmpBackground(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("rgb", ctypes.c_float * 3), ("buf_dev", ctypes.c_void_p)]
+
+
+class DbmpLimits(ctypes.Structure):
+    _fields_ = [("max_prims", ctypes.c_int32), ("max_tiles", ctypes.c_int32),
+                ("max_pairs", ctypes.c_int64), ("max_canvases", ctypes.c_int32)]
+
+
+class DbmpDeviceStatus(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("n_degenerate", ctypes.c_int32),
+                ("pairs_required", ctypes.c_int64), ("pairs_evaluated", ctypes.c_int64),
+                ("pairs_evaluated_bwd", ctypes.c_int64)]
+
+
+class DbmpAdamConfig(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("gamma", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("gains", ctypes.c_float * 8)]
+
+
+class DbmpTuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f32 = ctypes.c_float
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libdbmp.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdbmp.so not found at {path}; run paper_2602_22625_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    sig = {
+        "dbmp_last_error": (ctypes.c_char_p, []),
+        "dbmp_abi_version": (_i32, []),
+        "dbmp_atlas_create": (_i32, [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+        "dbmp_atlas_destroy": (_i32, [_vp]),
+        "dbmp_atlas_update": (_i32, [_vp, _vp, _vp]),
+        "dbmp_workspace_bytes": (_i32, [ctypes.POINTER(DbmpLimits), ctypes.POINTER(ctypes.c_size_t)]),
+        "dbmp_workspace_create": (_i32, [ctypes.POINTER(DbmpLimits), ctypes.POINTER(_vp)]),
+        "dbmp_workspace_destroy": (_i32, [_vp]),
+        "dbmp_status_poll": (_i32, [_vp, _vp, ctypes.POINTER(DbmpDeviceStatus)]),
+        "dbmp_bin": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _f32, _vp]),
+        "dbmp_get_tile_lists": (_i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(_i32), _vp]),
+        "dbmp_render_fwd": (_i32, [_vp, _vp, ctypes.POINTER(DbmpBackground), _f32, _vp, _vp, _vp, _vp]),
+        "dbmp_render_bwd": (_i32, [_vp, _vp, ctypes.POINTER(DbmpBackground), _f32, _vp, _vp, _vp, _vp,
+                                   _vp, _vp]),
+        "dbmp_mse_grad": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+        "dbmp_adam_step": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(DbmpAdamConfig), _vp]),
+        "dbmp_batch_plan": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(DbmpTuning), _vp]),
+        "dbmp_batch_render": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32,
+                                     _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "dbmp_autotune": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32, _i32,
+                                 _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
+                                 ctypes.POINTER(_f32), _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != DBMP_OK:
+        msg = load().dbmp_last_error().decode(errors="replace")
+        raise DbmpError(code, msg)
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_background(background, H=None, W=None):
+    """None -> no background (Eq. 5); 3 numbers -> constant; (3,H,W) CUDA tensor -> buffer."""
+    bg = DbmpBackground()
+    if background is None:
+        bg.mode = BG_NONE
+    elif isinstance(background, torch.Tensor) and background.numel() > 3:
+        bg.mode = BG_BUFFER
+        bg.buf_dev = _ptr(background)
+    else:
+        vals = [float(v) for v in (background.tolist() if isinstance(background, torch.Tensor) else background)]
+        bg.mode = BG_CONST
+        for j in range(3):
+            bg.rgb[j] = vals[j]
+    return bg
+
+
+# ----------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ----------------------------------------------------------------------------
+
+def dbmp_abi_version():
+    return load().dbmp_abi_version()
+
+
+def dbmp_atlas_create(texels, stream=None):
+    assert texels.dtype == torch.float32 and texels.dim() == 3
+    out = _vp()
+    _check(load().dbmp_atlas_create(_ptr(texels), texels.shape[0], texels.shape[1], texels.shape[2],
+                                    _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def dbmp_atlas_update(atlas, texels, stream=None):
+    _check(load().dbmp_atlas_update(atlas, _ptr(texels), _stream(stream)))
+
+
+def dbmp_atlas_destroy(atlas):
+    _check(load().dbmp_atlas_destroy(atlas))
+
+
+def dbmp_workspace_bytes(max_prims, max_tiles, max_pairs, max_canvases=1):
+    lim = DbmpLimits(max_prims, max_tiles, max_pairs, max_canvases)
+    n = ctypes.c_size_t()
+    _check(load().dbmp_workspace_bytes(ctypes.byref(lim), ctypes.byref(n)))
+    return n.value
+
+
+def dbmp_workspace_create(max_prims, max_tiles, max_pairs, max_canvases=1):
+    lim = DbmpLimits(max_prims, max_tiles, max_pairs, max_canvases)
+    out = _vp()
+    _check(load().dbmp_workspace_create(ctypes.byref(lim), ctypes.byref(out)))
+    return out.value
+
+
+def dbmp_workspace_destroy(ws):
+    _check(load().dbmp_workspace_destroy(ws))
+
+
+def dbmp_status_poll(ws, stream=None, raise_on_error=True):
+    st = DbmpDeviceStatus()
+    code = load().dbmp_status_poll(ws, _stream(stream), ctypes.byref(st))
+    if raise_on_error:
+        _check(code)
+    return st
+
+
+def dbmp_bin(ws, H, W, tile, params, bitmap_id, N, atlas, alpha_max, stream=None):
+    _check(load().dbmp_bin(ws, H, W, tile, _ptr(params), _ptr(bitmap_id), N, atlas, alpha_max,
+                           _stream(stream)))
+
+
+def dbmp_get_tile_lists(ws, offsets, lst, stream=None):
+    n = _i32()
+    _check(load().dbmp_get_tile_lists(ws, _ptr(offsets), _ptr(lst), lst.numel(), ctypes.byref(n),
+                                      _stream(stream)))
+    return n.value
+
+
+def dbmp_render_fwd(ws, atlas, bg, T_stop, image, T_final, n_last, stream=None):
+    _check(load().dbmp_render_fwd(ws, atlas, ctypes.byref(bg), T_stop, _ptr(image), _ptr(T_final),
+                                  _ptr(n_last), _stream(stream)))
+
+
+def dbmp_render_bwd(ws, atlas, bg, T_stop, dL_dimage, dL_dalpha, T_final, n_last, dparams, stream=None):
+    _check(load().dbmp_render_bwd(ws, atlas, ctypes.byref(bg), T_stop, _ptr(dL_dimage), _ptr(dL_dalpha),
+                                  _ptr(T_final), _ptr(n_last), _ptr(dparams), _stream(stream)))
+
+
+def dbmp_mse_grad(image, target, dL_dI, loss, stream=None):
+    _check(load().dbmp_mse_grad(_ptr(image), _ptr(target), image.numel(), _ptr(dL_dI), _ptr(loss),
+                                _stream(stream)))
+
+
+def adam_config(lr=0.1, gamma=1.0, beta1=0.9, beta2=0.999, eps=1e-8,
+                gains=(10.0, 10.0, 10.0, 1.0, 1.5, 1.0, 1.0, 1.0)):
+    c = DbmpAdamConfig()
+    c.lr, c.gamma, c.beta1, c.beta2, c.eps = lr, gamma, beta1, beta2, eps
+    for j in range(8):
+        c.gains[j] = gains[j]
+    return c
+
+
+def dbmp_adam_step(params, grad, m, v, step, cfg, stream=None):
+    _check(load().dbmp_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.shape[0], _ptr(step),
+                                 ctypes.byref(cfg), _stream(stream)))
+
+
+def dbmp_batch_plan(ws, H, W, prim_offset, tile=16, batch=128, stream=None):
+    n = len(H)
+    Ha = (_i32 * n)(*H)
+    Wa = (_i32 * n)(*W)
+    Oa = (_i32 * (n + 1))(*prim_offset)
+    t = DbmpTuning(tile, batch)
+    _check(load().dbmp_batch_plan(ws, n, Ha, Wa, Oa, ctypes.byref(t), _stream(stream)))
+
+
+def dbmp_batch_render(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, image=None, T_final=None,
+                      n_last=None, dL_dimage=None, dparams=None, stream=None):
+    _check(load().dbmp_batch_render(ws, _ptr(params), _ptr(bitmap_id), atlas, alpha_max, ctypes.byref(bg),
+                                    T_stop, mode, _ptr(image), _ptr(T_final), _ptr(n_last),
+                                    _ptr(dL_dimage), _ptr(dparams), _stream(stream)))
+
+
+def dbmp_autotune(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, image, T_final, n_last,
+                  dL_dimage=None, dparams=None, reps=3, stream=None):
+    best = DbmpTuning()
+    ms = _f32()
+    _check(load().dbmp_autotune(ws, _ptr(params), _ptr(bitmap_id), atlas, alpha_max, ctypes.byref(bg),
+                                T_stop, mode, _ptr(image), _ptr(T_final), _ptr(n_last), _ptr(dL_dimage),
+                                _ptr(dparams), reps, ctypes.byref(best), ctypes.byref(ms),
+                                _stream(stream)))
+    return (best.tile, best.batch), ms.value

@@ -1,0 +1,215 @@
+"""CUDA path vs the FP64 oracle: binning (bit-exact), forward (max-abs 1e-5) and
+backward (relative 1e-3 per parameter group), through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_22625_gb300 import dbmp as D
+from paper_2602_22625_gb300 import inputs
+from paper_2602_22625_gb300.render import Atlas, Renderer
+from _helpers import cuda, grad_close, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+
+
+def gpu_bin(sc, tile):
+    dev = cuda()
+    atlas = Atlas(to_dev(sc.atlas))
+    r = Renderer(sc.H, sc.W, atlas, max(sc.N, 1), tile=tile, background=sc.background)
+    p = to_dev(sc.params)
+    b = to_dev(sc.bitmap_id)
+    r.bin(p, b)
+    st = r.status()
+    K = st.pairs_required
+    n_tiles = (-(-sc.W // tile)) * (-(-sc.H // tile))
+    offs = torch.empty(n_tiles + 1, dtype=torch.int64, device=dev)
+    lst = torch.empty(max(K, 1), dtype=torch.int32, device=dev)
+    D.dbmp_get_tile_lists(r.ws.handle, offs, lst)
+    torch.cuda.synchronize()
+    return offs.cpu().numpy(), lst.cpu().numpy()[:K]
+
+
+def scene_ragged(seed=21, N=60, H=77, W=45):
+    sc = inputs.tiny(seed=seed, N=N, H=H, W=W)
+    sc.params[:, 2] = np.abs(sc.params[:, 2]) * 0.25
+    return sc
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_bit_exact_tiny(tile):
+    sc = inputs.tiny(seed=1)
+    offs, lst = gpu_bin(sc, tile)
+    ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, *sc.atlas.shape[1:])
+    np.testing.assert_array_equal(offs, ro)
+    np.testing.assert_array_equal(lst, rl)
+
+
+def test_bin_bit_exact_ragged_invalid_and_negative_scale():
+    sc = scene_ragged()
+    p = sc.params
+    p[3, 2] = 0.0
+    p[5, 0] = np.nan
+    p[7, 2] *= -1.0
+    p[9, 3] = 1e6  # beyond the reduction range: conservative box
+    for tile in (8, 16, 32):
+        offs, lst = gpu_bin(sc, tile)
+        ro, rl = oracle.bin(sc.H, sc.W, tile, p, *sc.atlas.shape[1:])
+        np.testing.assert_array_equal(offs, ro)
+        np.testing.assert_array_equal(lst, rl)
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_bin_bit_exact_main_workload(tile):
+    sc = inputs.main()
+    offs, lst = gpu_bin(sc, tile)
+    ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, *sc.atlas.shape[1:])
+    np.testing.assert_array_equal(offs, ro)
+    np.testing.assert_array_equal(lst, rl)
+
+
+def test_bin_empty():
+    sc = inputs.tiny(seed=2, N=0, H=40, W=50)
+    offs, lst = gpu_bin(sc, 16)
+    assert len(lst) == 0 and np.all(offs == 0)
+
+
+# ---------------------------------------------------------------------------
+# forward
+# ---------------------------------------------------------------------------
+
+def gpu_forward(sc, tile=16, T_stop=0.0, background="scene", alpha_max=1.0):
+    atlas = Atlas(to_dev(sc.atlas))
+    bg = sc.background if isinstance(background, str) else background
+    if isinstance(bg, np.ndarray) and bg.size > 3:
+        bg = to_dev(bg.astype(np.float32))
+    r = Renderer(sc.H, sc.W, atlas, max(sc.N, 1), tile=tile, background=bg, T_stop=T_stop,
+                 alpha_max=alpha_max)
+    p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
+    img, T, nl = r.forward(p, b)
+    st = r.status()
+    torch.cuda.synchronize()
+    return r, p, b, img, T, nl, st
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("T_stop", [0.0, 1e-6])
+def test_forward_tiny_matches_oracle(tile, T_stop):
+    sc = inputs.tiny(seed=1)
+    _, _, _, img, T, nl, st = gpu_forward(sc, tile, T_stop)
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background,
+                        T_stop=T_stop)
+    assert np.abs(img.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy() - ref["T_final"]).max() <= IMG_TOL
+    exact = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)
+    assert np.abs(img.cpu().numpy() - exact["image"]).max() <= IMG_TOL
+    assert st.pairs_evaluated > 0
+
+
+@pytest.mark.parametrize("bg", ["none", "const", "buffer"])
+@pytest.mark.parametrize("alpha_max", [1.0, 0.7])
+def test_forward_ragged_backgrounds(bg, alpha_max):
+    sc = scene_ragged()
+    background = {"none": None, "const": (0.2, 0.7, 0.4),
+                  "buffer": np.random.default_rng(3).uniform(0, 1, (3, sc.H, sc.W)).astype(np.float32)}[bg]
+    _, _, _, img, T, nl, _ = gpu_forward(sc, 16, 0.0, background=background, alpha_max=alpha_max)
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, alpha_max=alpha_max,
+                        background=background)
+    assert np.abs(img.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy() - ref["T_final"]).max() <= IMG_TOL
+    # n_last names the oracle's last contributing primitive
+    offs, lst = oracle.bin(sc.H, sc.W, 16, sc.params, *sc.atlas.shape[1:])
+    nl = nl.cpu().numpy()
+    ntx = -(-sc.W // 16)
+    yy, xx = np.mgrid[0:sc.H, 0:sc.W]
+    tid = (yy // 16) * ntx + xx // 16
+    prim = np.where(nl >= 0, lst[np.minimum(offs[tid] + np.maximum(nl, 0), len(lst) - 1)], -1)
+    assert np.mean(prim == ref["n_last"]) > 0.999
+
+
+def test_forward_empty_scene_is_background():
+    sc = inputs.tiny(seed=5, N=0, H=33, W=70)
+    _, _, _, img, T, nl, _ = gpu_forward(sc, 16, 0.0, background=(0.1, 0.2, 0.3))
+    img = img.cpu().numpy()
+    for j, v in enumerate((0.1, 0.2, 0.3)):
+        assert np.all(img[j] == np.float32(v))
+    assert np.all(T.cpu().numpy() == 1.0) and np.all(nl.cpu().numpy() == -1)
+
+
+def test_forward_main_workload_sampled_pixels():
+    sc = inputs.main()
+    _, _, _, img, T, _, st = gpu_forward(sc, 16, 1e-6)
+    rng = np.random.default_rng(0)
+    px = rng.integers(0, sc.W, 3000)
+    py = rng.integers(0, sc.H, 3000)
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background,
+                        pixels=(px, py))  # exact composite, no early termination
+    got = img.cpu().numpy()[:, py, px]
+    assert np.abs(got - ref["image"]).max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy()[py, px] - ref["T_final"]).max() <= IMG_TOL
+    assert st.pairs_required > 0
+
+
+# ---------------------------------------------------------------------------
+# backward
+# ---------------------------------------------------------------------------
+
+def gpu_grad(sc, gI, gA=None, tile=16, T_stop=0.0, background="scene", alpha_max=1.0):
+    r, p, b, img, T, nl, _ = gpu_forward(sc, tile, T_stop, background=background, alpha_max=alpha_max)
+    g = r.backward(to_dev(gI.astype(np.float32)), T, nl,
+                   None if gA is None else to_dev(gA.astype(np.float32)))
+    torch.cuda.synchronize()
+    return g.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_backward_tiny_matches_oracle(tile):
+    sc = inputs.tiny(seed=1)
+    rng = np.random.default_rng(11)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    g = gpu_grad(sc, gI, tile=tile)
+    ref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+    grad_close(g, ref, what=f"tile{tile}")
+
+
+@pytest.mark.parametrize("bg", ["none", "const", "buffer"])
+def test_backward_ragged_with_alpha_gradient(bg):
+    sc = scene_ragged(seed=23, N=80)
+    rng = np.random.default_rng(12)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    gA = rng.normal(size=(sc.H, sc.W)).astype(np.float32)
+    background = {"none": None, "const": (0.9, 0.1, 0.5),
+                  "buffer": rng.uniform(0, 1, (3, sc.H, sc.W)).astype(np.float32)}[bg]
+    g = gpu_grad(sc, gI, gA, background=background, alpha_max=0.8)
+    ref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, gA, alpha_max=0.8,
+                      background=background)
+    grad_close(g, ref, what=bg)
+
+
+def test_backward_opaque_layer_uses_rewalk():
+    """A layer with alpha = 1 exactly (alpha_max = 1, sigmoid(nu) = 1 in float32, M = 1)
+    leaves T = 0 behind it; the backward then recovers T in front of it by a re-walk."""
+    atlas = np.zeros((1, 16, 16), np.float32)
+    atlas[0, 2:14, 2:14] = 1.0
+    p = np.array([[20.0, 20.0, 6.0, 0.3, 0.5, 0.2, -0.3, 0.8],
+                  [24.0, 18.0, 12.0, 0.1, 60.0, 1.0, 0.5, -1.0],   # opaque
+                  [22.0, 22.0, 9.0, 0.7, 1.0, -0.4, 0.9, 0.1]], np.float32)
+    sc = inputs.Scene("opaque", 40, 40, p, np.zeros(3, np.int32), atlas)
+    rng = np.random.default_rng(4)
+    gI = rng.normal(size=(3, 40, 40)).astype(np.float32)
+    g = gpu_grad(sc, gI)
+    ref = oracle.grad(40, 40, p, sc.bitmap_id, atlas, gI, background=sc.background)
+    grad_close(g, ref, what="opaque")
+
+
+def test_backward_main_workload_sampled_primitives():
+    sc = inputs.main()
+    rng = np.random.default_rng(13)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32) * 1e-3
+    g = gpu_grad(sc, gI, T_stop=1e-6)
+    small = np.nonzero(np.abs(sc.params[:200, 2]) < 40)[0][:6]
+    sel = np.concatenate([small, [0, 1]])
+    ref = oracle.grad_selected(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, sel,
+                               background=sc.background, T_stop=1e-6)
+    grad_close(g[sel], ref, what="main")
