@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of one optimisation step of the bitmap-primitive rasterizer.
+
+Workload: 1024 x 1024 FP32 canvas, 20 000 primitives over 16 procedural stroke
+bitmaps of 128 x 128 (seeded Bezier strokes, Gaussian-blurred), scale
+LogNormal(-2, 0.7) of the canvas side, uniform rotation and colour, opacity
+U[0.2, 1], fixed depth order, MSE against a seeded target render.
+
+One step = the whole hot path: binning (preprocess, tile lists), forward
+composite, MSE gradient, backward composite, Adam update.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dbmp|reference]
+
+--impl reference times the FP64 CPU oracle (the correctness reference) on the
+host cores, one bounded sample of rows per step, scaled to the full canvas.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/step at 1024^2 x 20k prims"
+WORKLOAD = "main_1024sq_20k"
+L2_FLUSH_BYTES = 512 << 20
+T_STOP = 1e-6
+
+# Algorithmic FP32 operations (FMA = 2) per (pixel, list entry) pair; see the design doc.
+FLOPS_SAMPLE = 21       # Eqs. 1-2 and the bilinear sample (Eqs. S1-S3)
+FLOPS_COMPOSITE = 10    # Eqs. 3-5 for a pair with alpha > 0
+FLOPS_GRAD = 44         # Eq. 6, S4, S5 terms and the recursion for a pair with alpha > 0
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+# kernels one step launches (bin: prep, count, colscan, tilescan, scatter, 3 ordering;
+# fwd; mse; bwd, finalize; adam, step counter)
+LAUNCHES_PER_STEP = 14
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="dbmp", choices=["dbmp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--ppt", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "H": 1024, "W": 1024, "N": 20000, "atlas": "16 strokes 128x128",
+         "scale": "LogNormal(-2,0.7)*W", "T_stop": T_STOP, "background": "white",
+         "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB memset, outside the timed region)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+
+def oracle_band_step(sc, target, y0, y1):
+    """FP64 oracle forward + backward of the rows y0..y1 of the workload (MSE vs target)."""
+    import numpy as np
+    import oracle
+    ys, xs = np.mgrid[y0:y1, 0:sc.W]
+    out = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background,
+                        T_stop=T_STOP, pixels=(xs.ravel(), ys.ravel()))
+    img = out["image"].reshape(3, y1 - y0, sc.W)
+    gI = np.zeros((3, sc.H, sc.W))
+    gI[:, y0:y1] = 2.0 * (img - target[:, y0:y1]) / (3 * sc.H * sc.W)
+    oracle.grad_rows(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, y0, y1,
+                     background=sc.background, T_stop=T_STOP)
+
+
+def oracle_target(sc_t):
+    import numpy as np  # noqa: F401
+    import oracle
+    return oracle.render(sc_t.H, sc_t.W, sc_t.params, sc_t.bitmap_id, sc_t.atlas,
+                         background=sc_t.background)["image"]
+
+
+def cpu_baseline(rows=128):
+    import oracle
+    from paper_2602_22625_gb300 import inputs
+    sc = inputs.main(seed=2)
+    tgt_sc = inputs.main(seed=1002)
+    y0 = sc.H // 2 - rows // 2
+    import numpy as np
+    ys, xs = np.mgrid[y0:y0 + rows, 0:sc.W]
+    tgt = np.zeros((3, sc.H, sc.W))
+    tgt[:, y0:y0 + rows] = oracle.render(tgt_sc.H, tgt_sc.W, tgt_sc.params, tgt_sc.bitmap_id,
+                                         tgt_sc.atlas, background=tgt_sc.background,
+                                         pixels=(xs.ravel(), ys.ravel()))["image"].reshape(3, rows, sc.W)
+    t0 = time.perf_counter()
+    oracle_band_step(sc, tgt, y0, y0 + rows)
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3 * sc.H / rows, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"rows {y0}..{y0 + rows} of 1024 (fwd+bwd, FP64, T_stop={T_STOP}), "
+                      f"time x {sc.H // rows} to the full canvas; measured {dt:.2f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2602_22625_gb300 import inputs
+    sc = inputs.main(seed=2)
+    tgt_sc = inputs.main(seed=1002)
+    rows = 16
+    y0 = sc.H // 2 - rows // 2
+    ys, xs = np.mgrid[y0:y0 + rows, 0:sc.W]
+    tgt = np.zeros((3, sc.H, sc.W))
+    tgt[:, y0:y0 + rows] = oracle.render(tgt_sc.H, tgt_sc.W, tgt_sc.params, tgt_sc.bitmap_id,
+                                         tgt_sc.atlas, background=tgt_sc.background,
+                                         pixels=(xs.ravel(), ys.ravel()))["image"].reshape(3, rows, sc.W)
+    for _ in range(args.warmup):
+        oracle_band_step(sc, tgt, y0, y0 + rows)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_band_step(sc, tgt, y0, y0 + rows)
+        times.append((time.perf_counter() - t0) * 1e3 * sc.H / rows)
+    v = statistics.mean(times)
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config({"tile": None}),
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: rows {y0}..{y0 + rows} of 1024, fwd+bwd FP64, "
+                                       f"scaled x{sc.H // rows} to the full canvas"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi while the timed loop runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        busy = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel_key)
+        if not e:
+            return None
+        src = open(os.path.join(ROOT, "paper_2602_22625_gb300", "csrc", e["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != e["sha256"]:
+            return None
+        return e["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def run_dbmp(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_22625_gb300 import dbmp as D
+    from paper_2602_22625_gb300 import inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    D.load()
+
+    # inputs: each rank renders its own workload (weak scaling: no exchange)
+    sc = inputs.main(seed=2 + rank)
+    tgt = inputs.main(seed=1002 + rank)
+    atlas_t = torch.from_numpy(sc.atlas).to(dev)
+    atlas = D.dbmp_atlas_create(atlas_t)
+    N, H, W = sc.N, sc.H, sc.W
+    params0 = torch.from_numpy(sc.params).to(dev)
+    params = params0.clone()
+    bid = torch.from_numpy(sc.bitmap_id).to(dev)
+    image = torch.empty(3, H, W, device=dev)
+    T_final = torch.empty(H, W, device=dev)
+    n_last = torch.empty(H, W, device=dev, dtype=torch.int32)
+    target = torch.empty(3, H, W, device=dev)
+    dL = torch.empty(3, H, W, device=dev)
+    loss = torch.zeros(1, device=dev, dtype=torch.float64)
+    dparams = torch.zeros(N, 8, device=dev)
+    m = torch.zeros(N, 8, device=dev)
+    v = torch.zeros(N, 8, device=dev)
+    step = torch.zeros(1, device=dev, dtype=torch.int32)
+    bg = D.make_background(sc.background)
+    max_pairs = 96 << 20
+    ws = D.dbmp_workspace_create(N, (W // 8) * (H // 8), max_pairs, 1)
+    D.dbmp_batch_plan(ws, [H], [W], [0, N], tile=args.tile, batch=args.batch, ppt=args.ppt)
+
+    # target image: render of the target parameter set
+    tgt_p = torch.from_numpy(tgt.params).to(dev)
+    tgt_b = torch.from_numpy(tgt.bitmap_id).to(dev)
+    D.dbmp_batch_render(ws, tgt_p, tgt_b, atlas, 1.0, bg, 0.0, D.BATCH_BIN | D.BATCH_FWD, target, T_final,
+                        n_last)
+    D.dbmp_status_poll(ws)
+
+    # a real upstream gradient for the autotuner's backward
+    D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BIN | D.BATCH_FWD, image, T_final,
+                        n_last)
+    D.dbmp_mse_grad(image, target, dL, loss)
+    D.dbmp_status_poll(ws)
+    tuning = {"tile": args.tile, "batch": args.batch, "ppt": args.ppt, "autotuned": False}
+    if not args.no_autotune:
+        (t, b, pp), ms = D.dbmp_autotune(ws, params, bid, atlas, 1.0, bg, T_STOP,
+                                         D.BATCH_FWD | D.BATCH_BWD, image, T_final, n_last, dL, dparams,
+                                         reps=2)
+        tuning = {"tile": t, "batch": b, "ppt": pp, "autotuned": True, "autotune_ms_fwd_bwd": ms}
+        dparams.zero_()
+    adam = D.adam_config(lr=0.1, gamma=0.1 ** (1.0 / 500), zero_grad=True)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BIN, None, T_final, n_last)
+        if ev:
+            ev[1].record(stream)
+        D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_FWD, image, T_final, n_last)
+        if ev:
+            ev[2].record(stream)
+        D.dbmp_mse_grad(image, target, dL, loss)
+        if ev:
+            ev[3].record(stream)
+        D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BWD, image, T_final, n_last,
+                            dL, dparams)
+        if ev:
+            ev[4].record(stream)
+        D.dbmp_adam_step(params, dparams, m, v, step, adam)
+        if ev:
+            ev[5].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        one_step()
+    st = D.dbmp_status_poll(ws)
+    pairs = (st.pairs_evaluated, st.pairs_evaluated_bwd, st.pairs_contributing, st.pairs_required)
+
+    # ---- device-timed steps (inputs resident in HBM) ----
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            one_step(evs[k])
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    phase = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(5)] for k in range(args.steps)])
+    step_ms = phase.sum(1)
+    ms = float(step_ms.mean())
+    st = D.dbmp_status_poll(ws)
+    pairs_end = (st.pairs_evaluated, st.pairs_evaluated_bwd, st.pairs_contributing, st.pairs_required)
+
+    # ---- end to end through the C ABI with host buffers ----
+    h_params = params0.cpu().pin_memory()
+    h_bid = bid.cpu().pin_memory()
+    h_target = target.cpu().pin_memory()
+    h_loss = torch.zeros(1, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        params.copy_(h_params, non_blocking=True)
+        bid.copy_(h_bid, non_blocking=True)
+        target.copy_(h_target, non_blocking=True)
+        one_step()
+        h_loss.copy_(loss, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    h2d = h_params.numel() * 4 + h_bid.numel() * 4 + h_target.numel() * 4
+    d2h = 8
+
+    # ---- max over ranks ----
+    vals = torch.tensor([ms, float(np.mean(e2e_ms))], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms, e2e = float(vals[0]), float(vals[1])
+
+    fwd_ms = float(phase[:, 1].mean())
+    bwd_ms = float(phase[:, 3].mean())
+    ev_f, ev_b, contrib = pairs_end[0], pairs_end[1], pairs_end[2]
+    flops_f = FLOPS_SAMPLE * ev_f + FLOPS_COMPOSITE * contrib
+    flops_b = FLOPS_SAMPLE * ev_b + FLOPS_GRAD * contrib
+    if bwd_ms >= fwd_ms:
+        dom, flops, dms, key = "k_bwd (backward compositor)", flops_b, bwd_ms, "bwd"
+    else:
+        dom, flops, dms, key = "k_fwd (forward compositor)", flops_f, fwd_ms, "fwd"
+    achieved = flops / (dms * 1e-3) / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config({"tile": tuning["tile"], "batch": tuning["batch"], "ppt": tuning["ppt"],
+                          "autotuned": tuning["autotuned"],
+                          "parallelism": f"replicas x{world} (one canvas per GPU, no exchange)"}),
+        "breakdown_ms": {"bin": float(phase[:, 0].mean()), "fwd": fwd_ms, "mse": float(phase[:, 2].mean()),
+                         "bwd": bwd_ms, "adam": float(phase[:, 4].mean()),
+                         "step_min": float(step_ms.min()), "step_max": float(step_ms.max())},
+        "work": {"pairs_evaluated_fwd": ev_f, "pairs_evaluated_bwd": ev_b, "pairs_contributing": contrib,
+                 "tile_list_entries": pairs_end[3], "at_warmup_end": list(pairs)},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max clock (derived)",
+                     "algorithmic_flops_per_launch": flops, "kernel_ms": dms,
+                     "traffic": traffic_for(key)},
+        "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_dbmp(args)
+
+
+if __name__ == "__main__":
+    main()

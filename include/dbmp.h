@@ -119,6 +119,7 @@ typedef struct {
     int64_t pairs_required; /* sum_t d_t of the last binning                    */
     int64_t pairs_evaluated;/* (pixel, list entry) pairs the last fwd evaluated  */
     int64_t pairs_evaluated_bwd; /* same for the last bwd                       */
+    int64_t pairs_contributing;  /* pairs with alpha > 0 the last fwd composited  */
 } DbmpDeviceStatus;
 
 /* Synchronises `stream`, copies the status block to *out, clears the sticky
@@ -165,8 +166,10 @@ int32_t dbmp_get_tile_lists(DbmpWorkspace *ws, int64_t *offsets_dev, int32_t *li
 /* Forward (Eqs. 1-5, 8; Algorithm 1)                                         */
 /* ------------------------------------------------------------------------- */
 /* Composites the binned primitives (requires a prior dbmp_bin on `ws`, with the
- * same atlas).  One CTA per tile stages batches of primitive records in shared
- * memory and walks the tile's list front to back, one pixel per thread.
+ * same atlas).  Each warp composites one region of a tile (32 ppt pixels) as an
+ * independent worker: it stages batches of the tile's primitive records in its
+ * own shared-memory slice and walks the list front to back until all of its
+ * pixels are saturated.
  *   T_stop   early termination: a layer is composited only while the pixel's
  *            transmittance is >= max(T_stop, 2^-100); the image then differs from
  *            the full composite by at most T_stop.  0 = every layer.
@@ -211,12 +214,14 @@ typedef struct {
     float gamma;     /* exponential decay per step: lr_t = lr gamma^(t-1)      */
     float beta1, beta2, eps;
     float gains[8];  /* per parameter column (Tab. S1: 10 10 10 1 1.5 1 1 1)  */
+    int32_t zero_grad; /* non-zero: the step writes 0 to grad after reading it, so
+                          the next backward can accumulate into it directly    */
 } DbmpAdamConfig;
 
 /* One bias-corrected Adam step on params/m/v (float32 [N][8]).  step_dev is a
  * device int32 counter of completed steps: this call uses t = *step_dev + 1 and
  * then increments it, so a captured CUDA graph replays correct steps. */
-int32_t dbmp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
+int32_t dbmp_adam_step(float *params_dev, float *grad_dev, float *m_dev, float *v_dev,
                        int32_t N, int32_t *step_dev, const DbmpAdamConfig *cfg,
                        dbmp_stream_t stream);
 
@@ -234,7 +239,9 @@ int32_t dbmp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, f
  * graph. */
 typedef struct {
     int32_t tile;   /* 8, 16 or 32 */
-    int32_t batch;  /* records staged per shared-memory batch: 32, 64, 128 or 256 */
+    int32_t batch;  /* records each warp stages per shared-memory batch: 32 or 64 */
+    int32_t ppt;    /* pixels per lane: 1, 2 or 4 (4 needs tile >= 16); a warp owns
+                       a region of 32 ppt pixels of a tile */
 } DbmpTuning;
 
 int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
@@ -243,10 +250,10 @@ int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, c
 
 typedef enum { DBMP_BATCH_BIN = 1, DBMP_BATCH_FWD = 2, DBMP_BATCH_BWD = 4 } DbmpBatchMode;
 
-/* Bins all canvases (one launch per stage), then renders every (canvas, tile)
- * work item with one persistent forward launch (and one backward launch):
- * resident CTAs pull items from an atomic queue ordered by decreasing list
- * length (longest-processing-time first).  `mode` is an OR of DbmpBatchMode.
+/* Bins all canvases (one launch per stage), then renders every (canvas, tile,
+ * region) work item with one persistent forward launch (and one backward
+ * launch): resident warps pull items from an atomic queue, tiles ordered by
+ * decreasing list length (longest-processing-time first).  `mode` is an OR of DbmpBatchMode.
  * Pointers follow the plan's concatenated layouts; bg must be NONE or CONST. */
 int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
                           const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
@@ -254,7 +261,7 @@ int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int3
                           int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
                           dbmp_stream_t stream);
 
-/* Autotuner: times every (tile, batch) candidate on the planned batch (or a
+/* Autotuner: times every (tile, batch, ppt) candidate on the planned batch (or a
  * single canvas when n_canvas == 0 in the plan) with CUDA events, reps times
  * each, and writes the fastest to *best.  Synchronises `stream`; re-plans the
  * workspace with the winner. */

@@ -38,7 +38,6 @@ constexpr int32_t kMaxTilesPerCanvas = 24576;  // scatter cursors: 8 B each in s
 constexpr int64_t kHistCap = 16 << 20;         // chunk x tile histogram entries
 
 bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
-bool batch_ok(int32_t b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 
 }  // namespace
 
@@ -66,7 +65,7 @@ struct DbmpWorkspace {
     std::vector<int32_t> plan_H, plan_W, plan_off;
     int32_t n_canvas = 0, n_tiles = 0, n_chunks = 0, N = 0, max_tpc = 0;
     int64_t n_pix = 0;
-    RenderCfg cfg{16, 128};
+    RenderCfg cfg{16, 32, 2};
     bool persistent = false;
     bool binned = false;
     const float *params = nullptr;  // of the last binning (gradient finalisation)
@@ -244,7 +243,8 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     a.T_final = T_final;
     a.n_last = n_last;
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, sizeof(int64_t), st), "status reset");
-    DBMP_CUDA(launch_fwd(a, ws->cfg, ws->persistent, st), "forward launch");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_contrib, 0, sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
     return DBMP_OK;
 }
 
@@ -259,10 +259,8 @@ int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, sizeof(int64_t), st), "status reset");
     if (ws->N > 0)
         DBMP_CUDA(cudaMemsetAsync(ws->graw, 0, sizeof(float) * 8 * (size_t)ws->N, st), "graw reset");
-    DBMP_CUDA(launch_bwd(a, ws->cfg, ws->persistent, st), "backward launch");
-    DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, ws->alpha_max,
-                                   ws->Hb, ws->Wb, st),
-              "gradient finalize");
+    DBMP_CUDA(launch_bwd(a, ws->cfg, st), "backward launch");
+    DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, st), "gradient finalize");
     return DBMP_OK;
 }
 
@@ -358,6 +356,8 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         }
     }
     cudaError_t e = cudaMemset(ws->status, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = init_bin_kernels(kMaxTilesPerCanvas);
+    if (e == cudaSuccess) e = init_render_kernels();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dbmp_workspace_destroy(ws);
@@ -388,6 +388,7 @@ int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStat
     out->pairs_required = s.pairs_required;
     out->pairs_evaluated = s.pairs_eval_fwd;
     out->pairs_evaluated_bwd = s.pairs_eval_bwd;
+    out->pairs_contributing = s.pairs_contrib;
     const int32_t zero = 0;
     DBMP_CUDA(cudaMemcpy(&ws->status->code, &zero, sizeof zero, cudaMemcpyHostToDevice), "status clear");
     if (s.code == DBMP_ERR_CAPACITY)
@@ -474,7 +475,7 @@ int32_t dbmp_mse_grad(const float *image_dev, const float *target_dev, int64_t n
     return DBMP_OK;
 }
 
-int32_t dbmp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
+int32_t dbmp_adam_step(float *params_dev, float *grad_dev, float *m_dev, float *v_dev,
                        int32_t N, int32_t *step_dev, const DbmpAdamConfig *cfg, dbmp_stream_t stream) {
     if (!cfg || !step_dev) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
     if (N < 0) return fail(DBMP_ERR_INVALID_ARG, "N must be >= 0");
@@ -490,11 +491,12 @@ int32_t dbmp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, f
 int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
                         const int32_t *prim_offset, const DbmpTuning *tuning, dbmp_stream_t stream) {
     if (!ws || !H || !W || !prim_offset) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
-    const int32_t tile = tuning ? tuning->tile : 16;
-    const int32_t batch = tuning ? tuning->batch : 128;
-    if (!batch_ok(batch)) return fail(DBMP_ERR_INVALID_ARG, "batch must be 32, 64, 128 or 256");
-    if (int32_t r = build_plan(ws, n_canvas, H, W, prim_offset, tile)) return r;
-    ws->cfg.batch = batch;
+    const RenderCfg cfg{tuning ? tuning->tile : 16, tuning ? tuning->batch : 32, tuning ? tuning->ppt : 2};
+    if (!render_cfg_supported(cfg))
+        return fail(DBMP_ERR_INVALID_ARG, "unsupported tuning (tile %d, batch %d, ppt %d)", cfg.tile,
+                    cfg.batch, cfg.ppt);
+    if (int32_t r = build_plan(ws, n_canvas, H, W, prim_offset, cfg.tile)) return r;
+    ws->cfg = cfg;
     ws->persistent = true;
     ws->binned = false;
     cudaStream_t st = (cudaStream_t)stream;
@@ -563,13 +565,16 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     DBMP_CUDA(cudaEventCreate(&e0), "event");
     DBMP_CUDA(cudaEventCreate(&e1), "event");
     float best_t = 1e30f;
-    DbmpTuning bt{ws->cfg.tile, ws->cfg.batch};
+    DbmpTuning bt{ws->cfg.tile, ws->cfg.batch, ws->cfg.ppt};
     const int32_t tiles[] = {8, 16, 32};
-    const int32_t batches[] = {32, 64, 128, 256};
+    const int32_t batches[] = {32, 64};
+    const int32_t ppts[] = {1, 2, 4};
     int32_t rc = DBMP_OK;
     for (int32_t t : tiles) {
-        for (int32_t b : batches) {
-            DbmpTuning cand{t, b};
+        for (int32_t ci = 0; ci < 6; ++ci) {
+            const int32_t b = batches[ci / 3], p = ppts[ci % 3];
+            if (!render_cfg_supported(RenderCfg{t, b, p})) continue;
+            DbmpTuning cand{t, b, p};
             if (dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &cand, stream) != DBMP_OK) continue;
             // warm-up (also validates the capacity for this tile size)
             rc = dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop,

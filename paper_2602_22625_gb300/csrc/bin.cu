@@ -327,6 +327,15 @@ __global__ void k_order_scatter(const int64_t *__restrict__ off, int32_t n, int3
 
 }  // namespace
 
+cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas) {
+    const int sh64 = (int)(sizeof(int64_t) * (size_t)max_tiles_per_canvas);
+    const int sh32 = (int)(sizeof(int32_t) * (size_t)max_tiles_per_canvas);
+    cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, sh32);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, sh64);
+    return e;
+}
+
 cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,
                        const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st) {
     if (b.N > 0) {
@@ -336,14 +345,12 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
     const size_t sh32 = sizeof(int32_t) * (size_t)b.max_tiles_per_canvas;
     const size_t sh64 = sizeof(int64_t) * (size_t)b.max_tiles_per_canvas;
     if (b.n_chunks > 0) {
-        cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32);
         k_count<<<b.n_chunks, kBinThreads, sh32, st>>>(b.rect, b.canvas, b.n_canvas, b.hist);
     }
     k_colscan<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
                                                        b.tile_off);
     k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status);
     if (b.n_chunks > 0) {
-        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64);
         k_scatter<<<b.n_chunks, kBinThreads, sh64, st>>>(b.rect, b.canvas, b.n_canvas, b.hist,
                                                          b.tile_off, b.list, b.status);
     }

@@ -41,6 +41,7 @@ struct DevStatus {
     int64_t pairs_required;
     int64_t pairs_eval_fwd;
     int64_t pairs_eval_bwd;
+    int64_t pairs_contrib;  // (pixel, layer) pairs with alpha > 0 composited by the last fwd
     int32_t lists_valid;   // 1 after a binning that fit its capacity
     int32_t pad;
     uint32_t queue[4];     // persistent-kernel work counters
@@ -51,10 +52,11 @@ struct AtlasView {
     int32_t n_bmp, Hb, Wb;
 };
 
-// Tile size and staging batch used by one render.
+// Tile size, records per warp staging batch, pixels per lane.
 struct RenderCfg {
     int32_t tile;
     int32_t batch;
+    int32_t ppt;
 };
 
 // ---------------------------------------------------------------------------
@@ -115,6 +117,11 @@ struct BinBuffers {
     int32_t max_tiles_per_canvas;
 };
 
+// One-time kernel set-up (shared-memory opt-in, occupancy), called at workspace
+// creation so that later launches can be captured in CUDA graphs.
+cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas);
+cudaError_t init_render_kernels();
+
 cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,
                        const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st);
 
@@ -141,16 +148,16 @@ struct RenderArgs {
     float *graw;                // [N][8] raw per-primitive sums (backward)
 };
 
-cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st);
-cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st);
+bool render_cfg_supported(const RenderCfg &cfg);
+cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
+cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
-                                 float *dparams, int32_t N, float alpha_max, int32_t Hb, int32_t Wb,
-                                 cudaStream_t st);
+                                 float *dparams, int32_t N, cudaStream_t st);
 cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t n_bmp, int32_t Hb,
                               int32_t Wb, cudaStream_t st);
 cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
                             double *loss, cudaStream_t st);
-cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int32_t N, int32_t *step,
+cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32_t *step,
                         const DbmpAdamConfig &cfg, cudaStream_t st);
 
 }  // namespace dbmp

@@ -53,9 +53,10 @@ __global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg,
 struct AdamArgs {
     float lr, gamma, beta1, beta2, eps;
     float gains[8];
+    int32_t zero_grad;
 };
 
-__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, int64_t n, const int32_t *step, AdamArgs c) {
     const int t = *step + 1;
     const float bc1 = 1.0f - powf(c.beta1, (float)t);
@@ -64,6 +65,7 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
+        if (c.zero_grad) g[i] = 0.0f;
         const float mi = c.beta1 * m[i] + (1.0f - c.beta1) * gi;
         const float vi = c.beta2 * v[i] + (1.0f - c.beta2) * gi * gi;
         m[i] = mi;
@@ -99,7 +101,7 @@ cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int32_t N, int32_t *step,
+cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32_t *step,
                         const DbmpAdamConfig &cfg, cudaStream_t st) {
     AdamArgs c;
     c.lr = cfg.lr;
@@ -108,6 +110,7 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int32_t N,
     c.beta2 = cfg.beta2;
     c.eps = cfg.eps;
     for (int j = 0; j < 8; ++j) c.gains[j] = cfg.gains[j];
+    c.zero_grad = cfg.zero_grad;
     const int64_t n = (int64_t)N * 8;
     if (n > 0) k_adam<<<grid_for(n, 256), 256, 0, st>>>(p, g, m, v, n, step, c);
     k_step_inc<<<1, 1, 0, st>>>(step);

@@ -1,14 +1,23 @@
 // Forward and backward compositors (Eqs. 1-5, 8; Algorithm 1; Eq. 6, Eqs. S4-S5).
 //
-// One CTA owns one tile of TILE x TILE pixels; each thread owns PPT pixels of it.
-// The tile's list of primitive indices (front to back) is consumed in batches of
-// BATCH records, gathered from the per-primitive record array into shared memory
-// with cp.async (double-buffered: batch i+1 is in flight while batch i is
-// composited).  Bitmaps are read through L1 as 16-byte tap quads (one 128-bit
-// load per bilinear sample).  There is no per-layer state in global memory: the
-// forward keeps only T_final and the position of the last contributing layer, and
-// the backward walks the list back to front recovering T_k = T_{k+1} / (1 - a_k)
-// with exactly the arithmetic the forward used (sample_bitmap).
+// Work decomposition: a tile of TILE x TILE pixels is split into regions of
+// 32 * PPT pixels (TILE columns, 32 * PPT / TILE rows); one warp composites one
+// region, each lane owning PPT pixels of one column.  Warps are independent
+// workers: each pulls (tile, region) items from a global atomic queue (tiles in
+// longest-list-first order when the binning produced one), stages the tile's
+// primitive records into its own double-buffered shared-memory slice with
+// cp.async, walks the list, and stops as soon as all of its own pixels are
+// saturated (T < T_stop).  There is no CTA-wide barrier, so a region that
+// saturates early frees its warp for the next item instead of idling until the
+// slowest pixel of the tile is done.
+//
+// Bitmaps are read through L1 as 16-byte tap quads (one 128-bit load per bilinear
+// sample).  The forward keeps no per-layer state: it writes T_final and the list
+// position of the last contributing layer; the backward walks each region's list
+// back to front from the region's largest n_last, recovering
+// T_k = T_{k+1} / (1 - alpha_k) with exactly the arithmetic the forward used
+// (sample_bitmap), reduces the eight per-primitive sums across the warp with
+// shuffles and adds them with one atomic per primitive per warp.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -19,6 +28,8 @@ namespace dbmp {
 namespace {
 
 constexpr float kTFloor = 7.88860905e-31f;  // 2^-100: layers behind are never composited
+constexpr int kWarpsPerBlock = 4;
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int find_canvas_tile(const CanvasDesc *cv, int n, int t) {
     int lo = 0, hi = n - 1;
@@ -37,13 +48,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Gathers records list[l0 .. l0+n) into dst[0 .. n) (3 x 16-byte async copies each).
-template <int NT>
-__device__ __forceinline__ void stage_records(PrimRec *dst, const PrimRec *__restrict__ rec,
-                                              const int32_t *__restrict__ list, int64_t l0, int n) {
-    for (int j = threadIdx.x; j < n; j += NT) {
-        const PrimRec *src = rec + list[l0 + j];
-        const char *s = reinterpret_cast<const char *>(src);
+// One warp gathers records list[l0 .. l0+n) into dst[0 .. n) (3 x 16-byte async
+// copies per record) and commits them as one group.
+__device__ __forceinline__ void warp_stage(PrimRec *dst, const PrimRec *__restrict__ rec,
+                                           const int32_t *__restrict__ list, int64_t l0, int n, int lane) {
+    for (int j = lane; j < n; j += 32) {
+        const char *s = reinterpret_cast<const char *>(rec + list[l0 + j]);
         char *d = reinterpret_cast<char *>(dst + j);
         cp_async16(d, s);
         cp_async16(d + 16, s + 16);
@@ -52,20 +62,25 @@ __device__ __forceinline__ void stage_records(PrimRec *dst, const PrimRec *__res
     cp_async_commit();
 }
 
-struct TileGeom {
+struct Region {
     CanvasDesc d;
-    int tx, ty;
-    int64_t start;
-    int len;
+    int x0, y0;       // canvas coordinates of the region's top-left pixel
+    int64_t start;    // first list entry of the tile
+    int len;          // tile list length
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const RenderArgs &a, int tile_id) {
-    TileGeom g;
+template <int TILE, int PPT>
+__device__ __forceinline__ Region region_of(const RenderArgs &a, int item) {
+    constexpr int R = TILE * TILE / (32 * PPT);   // regions per tile
+    constexpr int RH = 32 * PPT / TILE;           // rows per region
+    const int ti = item / R, r = item - ti * R;
+    const int tile_id = a.tile_order ? a.tile_order[ti] : ti;
+    Region g;
     const int c = find_canvas_tile(a.canvas, a.n_canvas, tile_id);
     g.d = a.canvas[c];
     const int lt = tile_id - g.d.tile_base;
-    g.tx = lt % g.d.ntx;
-    g.ty = lt / g.d.ntx;
+    g.x0 = (lt % g.d.ntx) * TILE;
+    g.y0 = (lt / g.d.ntx) * TILE + r * RH;
     g.start = a.tile_off[tile_id];
     g.len = (int)(a.tile_off[tile_id + 1] - g.start);
     return g;
@@ -73,69 +88,70 @@ __device__ __forceinline__ TileGeom tile_geom(const RenderArgs &a, int tile_id) 
 
 __device__ __forceinline__ float bg_at(const RenderArgs &a, const CanvasDesc &d, int ch, int64_t pix) {
     if (a.bg_mode == DBMP_BG_CONST) return ch == 0 ? a.bg0 : (ch == 1 ? a.bg1 : a.bg2);
-    if (a.bg_mode == DBMP_BG_BUFFER)
-        return a.bg_buf[3 * d.pix_base + (int64_t)ch * d.H * d.W + pix];
+    if (a.bg_mode == DBMP_BG_BUFFER) return a.bg_buf[3 * d.pix_base + (int64_t)ch * d.H * d.W + pix];
     return 0.0f;
+}
+
+// Next work item for this warp (lane 0 pulls, all lanes get it).
+__device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
+    int it = 0;
+    if (lane == 0) it = (int)atomicAdd(queue, 1u);
+    return __shfl_sync(FULL, it, 0);
 }
 
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
 template <int TILE, int PPT, int BATCH>
-__device__ __forceinline__ void fwd_tile(const RenderArgs &a, int tile_id, PrimRec *sh) {
-    constexpr int NT = TILE * TILE / PPT;
-    constexpr int ROWS = NT / TILE;  // rows of the tile covered by one pass of the CTA
-    const TileGeom g = tile_geom(a, tile_id);
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32_t n_items) {
+    __shared__ PrimRec sh_all[kWarpsPerBlock][2][BATCH];
+    if (a.status->lists_valid == 0) return;
+    constexpr int LROWS = 32 / TILE;  // rows covered by the 32 lanes in one pass
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    PrimRec(*sh)[BATCH] = sh_all[warp];
     const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float tstop = fmaxf(a.T_stop, kTFloor);
+    int64_t ev_acc = 0, ct_acc = 0;
 
-    int px[PPT], py[PPT];
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    int last[PPT], evals[PPT];
-    bool done[PPT];
+    for (int item = next_item(&a.status->queue[0], lane); item < n_items;
+         item = next_item(&a.status->queue[0], lane)) {
+        const Region g = region_of<TILE, PPT>(a, item);
+        float px[PPT], py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+        int last[PPT];
+        bool inside[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        px[k] = g.tx * TILE + (threadIdx.x % TILE);
-        py[k] = g.ty * TILE + (threadIdx.x / TILE) + k * ROWS;
-        T[k] = 1.0f;
-        C0[k] = C1[k] = C2[k] = 0.0f;
-        last[k] = -1;
-        const bool inside = px[k] < g.d.W && py[k] < g.d.H;
-        done[k] = !inside;
-        evals[k] = inside ? g.len : 0;
-    }
-
-    if (g.len > 0) {
-        stage_records<NT>(sh, a.rec, a.list, g.start, min(BATCH, g.len));
-        for (int b0 = 0, it = 0; b0 < g.len; b0 += BATCH, ++it) {
-            const int n = min(BATCH, g.len - b0);
-            PrimRec *cur = sh + (it & 1) * BATCH;
-            if (b0 + BATCH < g.len)
-                stage_records<NT>(sh + ((it + 1) & 1) * BATCH, a.rec, a.list, g.start + b0 + BATCH,
-                                  min(BATCH, g.len - b0 - BATCH));
-            else
-                cp_async_commit();
-            cp_async_wait<1>();
-            __syncthreads();
-            bool warp_done = true;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) warp_done = warp_done && done[k];
-            if (!__all_sync(0xffffffffu, warp_done)) {
+        for (int k = 0; k < PPT; ++k) {
+            const int x = g.x0 + lane % TILE, y = g.y0 + lane / TILE + k * LROWS;
+            inside[k] = x < g.d.W && y < g.d.H;
+            px[k] = (float)x;
+            py[k] = (float)y;
+            T[k] = inside[k] ? 1.0f : 0.0f;   // pixels off the canvas never composite
+            C0[k] = C1[k] = C2[k] = 0.0f;
+            last[k] = -1;
+        }
+        if (g.len > 0) {
+            warp_stage(sh[0], a.rec, a.list, g.start, min(BATCH, g.len), lane);
+            bool alive = true;
+            for (int b0 = 0, it = 0; b0 < g.len && alive; b0 += BATCH, ++it) {
+                const int n = min(BATCH, g.len - b0);
+                const PrimRec *cur = sh[it & 1];
+                if (b0 + BATCH < g.len)
+                    warp_stage(sh[(it + 1) & 1], a.rec, a.list, g.start + b0 + BATCH,
+                               min(BATCH, g.len - b0 - BATCH), lane);
+                else
+                    cp_async_commit();
+                cp_async_wait<1>();
+                __syncwarp();
                 for (int j = 0; j < n; ++j) {
                     const PrimRec r = cur[j];
+                    bool any = false;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        if (done[k]) continue;
-                        if (T[k] < tstop) {
-                            done[k] = true;
-                            evals[k] = b0 + j;
-                            continue;
-                        }
+                        if (!(T[k] >= tstop)) continue;
                         Sample s;
-                        if (sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, (float)px[k],
-                                          (float)py[k], s) &&
+                        if (sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], s) &&
                             s.M > 0.0f) {
                             const float al = __fmul_rn(r.a, s.M);
                             const float q = __fsub_rn(1.0f, al);
@@ -145,67 +161,43 @@ __device__ __forceinline__ void fwd_tile(const RenderArgs &a, int tile_id, PrimR
                             C2[k] = __fmaf_rn(w, r.cb, C2[k]);
                             T[k] = __fmul_rn(T[k], q);
                             last[k] = b0 + j;
+                            ++ct_acc;
                         }
+                        any = any || T[k] >= tstop;
+                    }
+                    if (!__any_sync(FULL, any)) {
+                        alive = false;
+                        break;
                     }
                 }
+                __syncwarp();
             }
-            bool all = true;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) all = all && (done[k] || T[k] < tstop);
-            if (__syncthreads_and(all)) {
-#pragma unroll
-                for (int k = 0; k < PPT; ++k)
-                    if (!done[k]) {
-                        done[k] = true;
-                        evals[k] = b0 + n;
-                    }
-                break;
-            }
+            cp_async_wait<0>();
+            __syncwarp();
         }
-        cp_async_wait<0>();
-        __syncthreads();
-    }
-
-    int64_t ev = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (px[k] >= g.d.W || py[k] >= g.d.H) continue;
-        ev += evals[k];
-        const int64_t pix = (int64_t)py[k] * g.d.W + px[k];
         const int64_t HW = (int64_t)g.d.H * g.d.W;
-        float *img = a.image + 3 * g.d.pix_base;
-        img[pix] = __fmaf_rn(T[k], bg_at(a, g.d, 0, pix), C0[k]);
-        img[HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 1, pix), C1[k]);
-        img[2 * HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 2, pix), C2[k]);
-        a.T_final[g.d.pix_base + pix] = T[k];
-        a.n_last[g.d.pix_base + pix] = last[k];
-    }
-    // one counter update per warp
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    if ((threadIdx.x & 31) == 0 && ev) atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd,
-                                                 (unsigned long long)ev);
-}
-
-template <int TILE, int PPT, int BATCH>
-__global__ void __launch_bounds__(TILE * TILE / PPT) k_fwd(RenderArgs a) {
-    __shared__ PrimRec sh[2 * BATCH];
-    if (a.status->lists_valid == 0) return;
-    fwd_tile<TILE, PPT, BATCH>(a, blockIdx.x, sh);
-}
-
-template <int TILE, int PPT, int BATCH>
-__global__ void __launch_bounds__(TILE * TILE / PPT) k_fwd_persistent(RenderArgs a) {
-    __shared__ PrimRec sh[2 * BATCH];
-    __shared__ int item;
-    if (a.status->lists_valid == 0) return;
-    for (;;) {
-        if (threadIdx.x == 0) item = (int)atomicAdd(&a.status->queue[0], 1u);
-        __syncthreads();
-        const int it = item;
-        __syncthreads();
-        if (it >= a.n_tiles) break;
-        fwd_tile<TILE, PPT, BATCH>(a, a.tile_order ? a.tile_order[it] : it, sh);
+        for (int k = 0; k < PPT; ++k) {
+            if (!inside[k]) continue;
+            // a pixel evaluates entries up to its last layer, then finds T < T_stop
+            ev_acc += T[k] < tstop ? last[k] + 1 : g.len;
+            const int64_t pix = (int64_t)py[k] * g.d.W + (int64_t)px[k];
+            float *img = a.image + 3 * g.d.pix_base;
+            img[pix] = __fmaf_rn(T[k], bg_at(a, g.d, 0, pix), C0[k]);
+            img[HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 1, pix), C1[k]);
+            img[2 * HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 2, pix), C2[k]);
+            a.T_final[g.d.pix_base + pix] = T[k];
+            a.n_last[g.d.pix_base + pix] = last[k];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ev_acc += __shfl_xor_sync(FULL, ev_acc, o);
+        ct_acc += __shfl_xor_sync(FULL, ct_acc, o);
+    }
+    if (lane == 0 && ev_acc) {
+        atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd, (unsigned long long)ev_acc);
+        atomicAdd((unsigned long long *)&a.status->pairs_contrib, (unsigned long long)ct_acc);
     }
 }
 
@@ -215,9 +207,7 @@ __global__ void __launch_bounds__(TILE * TILE / PPT) k_fwd_persistent(RenderArgs
 
 // Sums v[0..7] over the 32 lanes of the warp (transpose reduction: 9 shuffles)
 // and adds the eight totals to dst[0..7] (lanes 0, 4, ..., 28 each add one).
-__device__ __forceinline__ void warp_reduce8_add(const float v[8], float *dst) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void warp_reduce8_add(const float v[8], float *dst, int lane) {
     float k1[4];
     {
         const bool up = lane & 16;
@@ -254,9 +244,9 @@ __device__ __forceinline__ void warp_reduce8_add(const float v[8], float *dst) {
 }
 
 // Transmittance in front of list position `upto` for one pixel, by a forward
-// re-walk (used only when the last contributing layer was exactly opaque, so
-// that dividing by (1 - alpha) = 0 cannot recover it).
-__device__ float rewalk_T(const RenderArgs &a, const TileGeom &g, int upto, float px, float py) {
+// re-walk (used only when the last contributing layer was exactly opaque, so that
+// dividing by (1 - alpha) = 0 cannot recover it).
+__device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float px, float py) {
     const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
@@ -271,65 +261,65 @@ __device__ float rewalk_T(const RenderArgs &a, const TileGeom &g, int upto, floa
 }
 
 template <int TILE, int PPT, int BATCH>
-__device__ __forceinline__ void bwd_tile(const RenderArgs &a, int tile_id, PrimRec *sh, int *sh_max) {
-    constexpr int NT = TILE * TILE / PPT;
-    constexpr int ROWS = NT / TILE;
-    const TileGeom g = tile_geom(a, tile_id);
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32_t n_items) {
+    __shared__ PrimRec sh_all[kWarpsPerBlock][2][BATCH];
+    if (a.status->lists_valid == 0) return;
+    constexpr int LROWS = 32 / TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    PrimRec(*sh)[BATCH] = sh_all[warp];
     const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float rho = kw / kv, irho = kv / kw;
+    int64_t ev_acc = 0;
 
-    int px[PPT], py[PPT], last[PPT];
-    float T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
-    int my_max = -1;
-    int64_t ev = 0;
+    for (int item = next_item(&a.status->queue[1], lane); item < n_items;
+         item = next_item(&a.status->queue[1], lane)) {
+        const Region g = region_of<TILE, PPT>(a, item);
+        float px[PPT], py[PPT], T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
+        int last[PPT];
+        int my_max = -1;
+        const int64_t HW = (int64_t)g.d.H * g.d.W;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        px[k] = g.tx * TILE + (threadIdx.x % TILE);
-        py[k] = g.ty * TILE + (threadIdx.x / TILE) + k * ROWS;
-        last[k] = -1;
-        T[k] = Y[k] = g0[k] = g1[k] = g2[k] = 0.0f;
-        if (px[k] < g.d.W && py[k] < g.d.H) {
-            const int64_t pix = (int64_t)py[k] * g.d.W + px[k];
-            const int64_t HW = (int64_t)g.d.H * g.d.W;
-            last[k] = min(a.n_last[g.d.pix_base + pix], g.len - 1);
-            T[k] = a.T_final[g.d.pix_base + pix];
-            const float *gI = a.dL_dimage + 3 * g.d.pix_base;
-            g0[k] = gI[pix];
-            g1[k] = gI[HW + pix];
-            g2[k] = gI[2 * HW + pix];
-            const float gA = a.dL_dalpha ? a.dL_dalpha[g.d.pix_base + pix] : 0.0f;
-            // Y = g . R - gA B, with R = b and B = 1 behind the last layer
-            Y[k] = g0[k] * bg_at(a, g.d, 0, pix) + g1[k] * bg_at(a, g.d, 1, pix) +
-                   g2[k] * bg_at(a, g.d, 2, pix) - gA;
-            my_max = max(my_max, last[k]);
-            ev += last[k] + 1;
+        for (int k = 0; k < PPT; ++k) {
+            const int x = g.x0 + lane % TILE, y = g.y0 + lane / TILE + k * LROWS;
+            px[k] = (float)x;
+            py[k] = (float)y;
+            last[k] = -1;
+            T[k] = Y[k] = g0[k] = g1[k] = g2[k] = 0.0f;
+            if (x < g.d.W && y < g.d.H) {
+                const int64_t pix = (int64_t)y * g.d.W + x;
+                last[k] = min(a.n_last[g.d.pix_base + pix], g.len - 1);
+                T[k] = a.T_final[g.d.pix_base + pix];
+                const float *gI = a.dL_dimage + 3 * g.d.pix_base;
+                g0[k] = gI[pix];
+                g1[k] = gI[HW + pix];
+                g2[k] = gI[2 * HW + pix];
+                const float gA = a.dL_dalpha ? a.dL_dalpha[g.d.pix_base + pix] : 0.0f;
+                // Y = g . R - gA B, with R = b and B = 1 behind the last layer
+                Y[k] = g0[k] * bg_at(a, g.d, 0, pix) + g1[k] * bg_at(a, g.d, 1, pix) +
+                       g2[k] * bg_at(a, g.d, 2, pix) - gA;
+                my_max = max(my_max, last[k]);
+                ev_acc += last[k] + 1;
+            }
         }
-    }
-    if (threadIdx.x == 0) *sh_max = -1;
-    __syncthreads();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(sh_max, my_max);
-    __syncthreads();
-    const int jmax = *sh_max;
-    __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(FULL, my_max, o));
+        if (my_max < 0) continue;
 
-    if (jmax >= 0) {
-        // batches [lo, hi) from the back
-        int hi = jmax + 1;
+        // batches [lo, hi) from the back of the region's walk
+        int hi = my_max + 1;
         int lo = max(0, hi - BATCH);
-        stage_records<NT>(sh, a.rec, a.list, g.start + lo, hi - lo);
+        warp_stage(sh[0], a.rec, a.list, g.start + lo, hi - lo, lane);
         for (int it = 0; hi > 0; ++it) {
             const int nlo = max(0, lo - BATCH);
-            PrimRec *cur = sh + (it & 1) * BATCH;
+            const PrimRec *cur = sh[it & 1];
             if (lo > 0)
-                stage_records<NT>(sh + ((it + 1) & 1) * BATCH, a.rec, a.list, g.start + nlo, lo - nlo);
+                warp_stage(sh[(it + 1) & 1], a.rec, a.list, g.start + nlo, lo - nlo, lane);
             else
                 cp_async_commit();
             cp_async_wait<1>();
-            __syncthreads();
+            __syncwarp();
             for (int j = hi - 1; j >= lo; --j) {
                 const PrimRec r = cur[j - lo];
                 float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -338,19 +328,13 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs &a, int tile_id, PrimR
                 for (int k = 0; k < PPT; ++k) {
                     if (j > last[k]) continue;
                     Sample s;
-                    if (!sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, (float)px[k],
-                                       (float)py[k], s) ||
+                    if (!sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], s) ||
                         !(s.M > 0.0f))
                         continue;
                     any = true;
                     const float al = __fmul_rn(r.a, s.M);
                     const float q = __fsub_rn(1.0f, al);
-                    float Tk;
-                    if (q > 0.0f) {
-                        Tk = __fdividef(T[k], q);
-                    } else {
-                        Tk = rewalk_T(a, g, j, (float)px[k], (float)py[k]);
-                    }
+                    const float Tk = q > 0.0f ? __fdividef(T[k], q) : rewalk_T(a, g, j, px[k], py[k]);
                     T[k] = Tk;
                     const float gc = g0[k] * r.cr + g1[k] * r.cg + g2[k] * r.cb;
                     const float dA = Tk * (gc - Y[k]);          // dL/dalpha_k
@@ -369,43 +353,19 @@ __device__ __forceinline__ void bwd_tile(const RenderArgs &a, int tile_id, PrimR
                     v[7] += g2[k] * w;
                     Y[k] = fmaf(q, Y[k], al * gc);
                 }
-                if (__any_sync(0xffffffffu, any)) warp_reduce8_add(v, a.graw + 8 * (int64_t)r.index);
+                if (__any_sync(FULL, any)) warp_reduce8_add(v, a.graw + 8 * (int64_t)r.index, lane);
             }
-            __syncthreads();
+            __syncwarp();
             hi = lo;
             lo = nlo;
         }
         cp_async_wait<0>();
-        __syncthreads();
+        __syncwarp();
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    if ((threadIdx.x & 31) == 0 && ev) atomicAdd((unsigned long long *)&a.status->pairs_eval_bwd,
-                                                 (unsigned long long)ev);
-}
-
-template <int TILE, int PPT, int BATCH>
-__global__ void __launch_bounds__(TILE * TILE / PPT) k_bwd(RenderArgs a) {
-    __shared__ PrimRec sh[2 * BATCH];
-    __shared__ int sh_max;
-    if (a.status->lists_valid == 0) return;
-    bwd_tile<TILE, PPT, BATCH>(a, blockIdx.x, sh, &sh_max);
-}
-
-template <int TILE, int PPT, int BATCH>
-__global__ void __launch_bounds__(TILE * TILE / PPT) k_bwd_persistent(RenderArgs a) {
-    __shared__ PrimRec sh[2 * BATCH];
-    __shared__ int sh_max;
-    __shared__ int item;
-    if (a.status->lists_valid == 0) return;
-    for (;;) {
-        if (threadIdx.x == 0) item = (int)atomicAdd(&a.status->queue[1], 1u);
-        __syncthreads();
-        const int it = item;
-        __syncthreads();
-        if (it >= a.n_tiles) break;
-        bwd_tile<TILE, PPT, BATCH>(a, a.tile_order ? a.tile_order[it] : it, sh, &sh_max);
-    }
+    for (int o = 16; o > 0; o >>= 1) ev_acc += __shfl_xor_sync(FULL, ev_acc, o);
+    if (lane == 0 && ev_acc)
+        atomicAdd((unsigned long long *)&a.status->pairs_eval_bwd, (unsigned long long)ev_acc);
 }
 
 // Per-primitive chain rule from the eight reduced sums to the raw parameters:
@@ -431,66 +391,99 @@ __global__ void k_finalize(const float *__restrict__ params, const PrimRec *__re
     o[7] += S[7] * r.cb * (1.0f - r.cb);
 }
 
-int persistent_grid(const void *kernel, int threads, cudaStream_t) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
-    return sms * (per > 0 ? per : 1);
+// Resident CTAs per SM of each instantiation, queried once (init_render_kernels)
+// so that launches inside a CUDA-graph capture make no occupancy queries.
+int g_sms = 0;
+struct OccEntry {
+    const void *fn;
+    int per_sm;
+};
+OccEntry g_occ[64];
+int g_n_occ = 0;
+
+int resident_ctas(const void *fn) {
+    for (int i = 0; i < g_n_occ; ++i)
+        if (g_occ[i].fn == fn) return g_occ[i].per_sm;
+    return 1;
+}
+
+int persistent_grid(const void *kernel, int32_t n_items) {
+    const int full = (g_sms > 0 ? g_sms : 1) * resident_ctas(kernel);
+    const int need = (n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return need < full ? (need > 0 ? need : 1) : full;
 }
 
 template <int TILE, int PPT, int BATCH>
-cudaError_t launch_fwd_t(const RenderArgs &a, bool persistent, cudaStream_t st) {
-    constexpr int NT = TILE * TILE / PPT;
-    if (persistent) {
-        const int grid = persistent_grid((const void *)k_fwd_persistent<TILE, PPT, BATCH>, NT, st);
-        k_fwd_persistent<TILE, PPT, BATCH><<<grid, NT, 0, st>>>(a);
+void register_occupancy() {
+    const void *fns[2] = {(const void *)k_fwd<TILE, PPT, BATCH>, (const void *)k_bwd<TILE, PPT, BATCH>};
+    for (const void *fn : fns) {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * kWarpsPerBlock, 0);
+        if (g_n_occ < 64) g_occ[g_n_occ++] = OccEntry{fn, per > 0 ? per : 1};
+    }
+}
+
+template <int TILE, int PPT, int BATCH>
+cudaError_t launch_t(const RenderArgs &a, bool fwd, cudaStream_t st) {
+    constexpr int R = TILE * TILE / (32 * PPT);
+    const int32_t n_items = a.n_tiles * R;
+    if (fwd) {
+        const int grid = persistent_grid((const void *)k_fwd<TILE, PPT, BATCH>, n_items);
+        k_fwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);
     } else {
-        k_fwd<TILE, PPT, BATCH><<<a.n_tiles, NT, 0, st>>>(a);
+        const int grid = persistent_grid((const void *)k_bwd<TILE, PPT, BATCH>, n_items);
+        k_bwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);
     }
     return cudaGetLastError();
 }
 
-template <int TILE, int PPT, int BATCH>
-cudaError_t launch_bwd_t(const RenderArgs &a, bool persistent, cudaStream_t st) {
-    constexpr int NT = TILE * TILE / PPT;
-    if (persistent) {
-        const int grid = persistent_grid((const void *)k_bwd_persistent<TILE, PPT, BATCH>, NT, st);
-        k_bwd_persistent<TILE, PPT, BATCH><<<grid, NT, 0, st>>>(a);
-    } else {
-        k_bwd<TILE, PPT, BATCH><<<a.n_tiles, NT, 0, st>>>(a);
-    }
-    return cudaGetLastError();
-}
-
-// (tile, batch) -> instantiation.  Pixels per thread: tile 8 -> 1 (64 threads),
-// tile 16 -> 2 (128 threads), tile 32 -> 4 (256 threads).
-template <bool FWD>
-cudaError_t dispatch(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st) {
-#define DBMP_CASE(T, P, B)                                                                  \
-    if (cfg.tile == T && cfg.batch == B)                                                    \
-        return FWD ? launch_fwd_t<T, P, B>(a, persistent, st) : launch_bwd_t<T, P, B>(a, persistent, st);
-    DBMP_CASE(8, 1, 32) DBMP_CASE(8, 1, 64) DBMP_CASE(8, 1, 128) DBMP_CASE(8, 1, 256)
-    DBMP_CASE(16, 2, 32) DBMP_CASE(16, 2, 64) DBMP_CASE(16, 2, 128) DBMP_CASE(16, 2, 256)
-    DBMP_CASE(32, 4, 32) DBMP_CASE(32, 4, 64) DBMP_CASE(32, 4, 128) DBMP_CASE(32, 4, 256)
+cudaError_t dispatch(const RenderArgs &a, const RenderCfg &cfg, bool fwd, cudaStream_t st) {
+#define DBMP_CASE(T, P, B) \
+    if (cfg.tile == T && cfg.ppt == P && cfg.batch == B) return launch_t<T, P, B>(a, fwd, st);
+    DBMP_CASE(8, 1, 32) DBMP_CASE(8, 2, 32) DBMP_CASE(8, 1, 64) DBMP_CASE(8, 2, 64)
+    DBMP_CASE(16, 1, 32) DBMP_CASE(16, 2, 32) DBMP_CASE(16, 4, 32)
+    DBMP_CASE(16, 1, 64) DBMP_CASE(16, 2, 64) DBMP_CASE(16, 4, 64)
+    DBMP_CASE(32, 1, 32) DBMP_CASE(32, 2, 32) DBMP_CASE(32, 4, 32)
+    DBMP_CASE(32, 1, 64) DBMP_CASE(32, 2, 64) DBMP_CASE(32, 4, 64)
 #undef DBMP_CASE
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st) {
-    if (persistent) cudaMemsetAsync(&a.status->queue[0], 0, sizeof(uint32_t), st);
-    return dispatch<true>(a, cfg, persistent, st);
+cudaError_t init_render_kernels() {
+    if (g_sms > 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    register_occupancy<8, 1, 32>(); register_occupancy<8, 2, 32>();
+    register_occupancy<8, 1, 64>(); register_occupancy<8, 2, 64>();
+    register_occupancy<16, 1, 32>(); register_occupancy<16, 2, 32>(); register_occupancy<16, 4, 32>();
+    register_occupancy<16, 1, 64>(); register_occupancy<16, 2, 64>(); register_occupancy<16, 4, 64>();
+    register_occupancy<32, 1, 32>(); register_occupancy<32, 2, 32>(); register_occupancy<32, 4, 32>();
+    register_occupancy<32, 1, 64>(); register_occupancy<32, 2, 64>(); register_occupancy<32, 4, 64>();
+    return cudaGetLastError();
 }
 
-cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, bool persistent, cudaStream_t st) {
-    if (persistent) cudaMemsetAsync(&a.status->queue[1], 0, sizeof(uint32_t), st);
-    return dispatch<false>(a, cfg, persistent, st);
+bool render_cfg_supported(const RenderCfg &cfg) {
+    const bool tile_ok = cfg.tile == 8 || cfg.tile == 16 || cfg.tile == 32;
+    const bool ppt_ok = cfg.ppt == 1 || cfg.ppt == 2 || (cfg.ppt == 4 && cfg.tile >= 16);
+    return tile_ok && ppt_ok && (cfg.batch == 32 || cfg.batch == 64);
+}
+
+cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
+    cudaMemsetAsync(&a.status->queue[0], 0, sizeof(uint32_t), st);
+    return dispatch(a, cfg, true, st);
+}
+
+cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
+    cudaMemsetAsync(&a.status->queue[1], 0, sizeof(uint32_t), st);
+    return dispatch(a, cfg, false, st);
 }
 
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
-                                 float *dparams, int32_t N, float, int32_t, int32_t, cudaStream_t st) {
+                                 float *dparams, int32_t N, cudaStream_t st) {
     if (N > 0) k_finalize<<<(N + 255) / 256, 256, 0, st>>>(params, rec, graw, dparams, N);
     return cudaGetLastError();
 }

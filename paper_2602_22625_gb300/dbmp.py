@@ -52,16 +52,17 @@ class DbmpLimits(ctypes.Structure):
 class DbmpDeviceStatus(ctypes.Structure):
     _fields_ = [("code", ctypes.c_int32), ("n_degenerate", ctypes.c_int32),
                 ("pairs_required", ctypes.c_int64), ("pairs_evaluated", ctypes.c_int64),
-                ("pairs_evaluated_bwd", ctypes.c_int64)]
+                ("pairs_evaluated_bwd", ctypes.c_int64), ("pairs_contributing", ctypes.c_int64)]
 
 
 class DbmpAdamConfig(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("gamma", ctypes.c_float), ("beta1", ctypes.c_float),
-                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("gains", ctypes.c_float * 8)]
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("gains", ctypes.c_float * 8),
+                ("zero_grad", ctypes.c_int32)]
 
 
 class DbmpTuning(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32)]
+    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("ppt", ctypes.c_int32)]
 
 
 _lib = None
@@ -239,9 +240,10 @@ def dbmp_mse_grad(image, target, dL_dI, loss, stream=None):
 
 
 def adam_config(lr=0.1, gamma=1.0, beta1=0.9, beta2=0.999, eps=1e-8,
-                gains=(10.0, 10.0, 10.0, 1.0, 1.5, 1.0, 1.0, 1.0)):
+                gains=(10.0, 10.0, 10.0, 1.0, 1.5, 1.0, 1.0, 1.0), zero_grad=False):
     c = DbmpAdamConfig()
     c.lr, c.gamma, c.beta1, c.beta2, c.eps = lr, gamma, beta1, beta2, eps
+    c.zero_grad = 1 if zero_grad else 0
     for j in range(8):
         c.gains[j] = gains[j]
     return c
@@ -252,12 +254,12 @@ def dbmp_adam_step(params, grad, m, v, step, cfg, stream=None):
                                  ctypes.byref(cfg), _stream(stream)))
 
 
-def dbmp_batch_plan(ws, H, W, prim_offset, tile=16, batch=128, stream=None):
+def dbmp_batch_plan(ws, H, W, prim_offset, tile=16, batch=32, ppt=2, stream=None):
     n = len(H)
     Ha = (_i32 * n)(*H)
     Wa = (_i32 * n)(*W)
     Oa = (_i32 * (n + 1))(*prim_offset)
-    t = DbmpTuning(tile, batch)
+    t = DbmpTuning(tile, batch, ppt)
     _check(load().dbmp_batch_plan(ws, n, Ha, Wa, Oa, ctypes.byref(t), _stream(stream)))
 
 
@@ -276,4 +278,4 @@ def dbmp_autotune(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, ima
                                 T_stop, mode, _ptr(image), _ptr(T_final), _ptr(n_last), _ptr(dL_dimage),
                                 _ptr(dparams), reps, ctypes.byref(best), ctypes.byref(ms),
                                 _stream(stream)))
-    return (best.tile, best.batch), ms.value
+    return (best.tile, best.batch, best.ppt), ms.value

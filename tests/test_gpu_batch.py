@@ -1,0 +1,300 @@
+"""Batched persistent rendering, every tuning instantiation, CUDA-graph capture of a
+whole optimisation step, the autotuner, the loss and Adam kernels, and device-side
+error reporting -- all through the C ABI, checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_22625_gb300 import dbmp as D
+from paper_2602_22625_gb300 import inputs
+from _helpers import cuda, grad_close, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+TUNINGS = [(t, b, p) for t in (8, 16, 32) for b in (32, 64) for p in (1, 2, 4) if not (p == 4 and t == 8)]
+
+
+def small_batch(seed=31, n=5):
+    g = np.random.default_rng(seed)
+    atlas = inputs.stroke_atlas(5, 4, 32, n_seg=24)
+    scenes = []
+    sizes = [(70, 53), (33, 90), (64, 64), (17, 21), (48, 100)][:n]
+    counts = [40, 0, 25, 7, 60][:n]
+    for c, ((H, W), N) in enumerate(zip(sizes, counts)):
+        p, b = inputs.primitives(seed * 1000 + c, N, H, W, atlas.shape[0], "uniform", (0.05, 0.3))
+        scenes.append(inputs.Scene(f"c{c}", H, W, p, b, atlas))
+    return scenes, atlas
+
+
+def concat(scenes):
+    params = np.concatenate([s.params for s in scenes]) if scenes else np.zeros((0, 8), np.float32)
+    bid = np.concatenate([s.bitmap_id for s in scenes]).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum([s.N for s in scenes])]).astype(np.int64)
+    pix = np.concatenate([[0], np.cumsum([s.H * s.W for s in scenes])]).astype(np.int64)
+    return params, bid, off, pix
+
+
+def run_batch(scenes, atlas_np, tuning, gI=None, T_stop=0.0, bg=(1.0, 1.0, 1.0)):
+    cuda()
+    params, bid, off, pix = concat(scenes)
+    N, P = int(off[-1]), int(pix[-1])
+    atlas = D.dbmp_atlas_create(to_dev(atlas_np))
+    n_tiles = sum(-(-s.W // 8) * -(-s.H // 8) for s in scenes)
+    ws = D.dbmp_workspace_create(max(N, 1), n_tiles, 1 << 24, len(scenes))
+    try:
+        D.dbmp_batch_plan(ws, [s.H for s in scenes], [s.W for s in scenes], off.tolist(), *tuning)
+        p, b = to_dev(params), to_dev(bid)
+        image = torch.full((3 * P,), -7.0, device="cuda")
+        T = torch.empty(P, device="cuda")
+        nl = torch.empty(P, dtype=torch.int32, device="cuda")
+        dparams = torch.zeros(max(N, 1), 8, device="cuda")
+        mode = D.BATCH_BIN | D.BATCH_FWD
+        gdev = None
+        if gI is not None:
+            mode |= D.BATCH_BWD
+            gdev = to_dev(gI.astype(np.float32))
+        bgs = D.make_background(bg)
+        D.dbmp_batch_render(ws, p, b, atlas, 1.0, bgs, T_stop, mode, image, T, nl, gdev, dparams)
+        st = D.dbmp_status_poll(ws)
+        torch.cuda.synchronize()
+        return image.cpu().numpy(), T.cpu().numpy(), dparams.cpu().numpy()[:N].astype(np.float64), st
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
+def split(flat, scenes, pix, channels):
+    out = []
+    for c, s in enumerate(scenes):
+        a = flat[channels * pix[c]: channels * pix[c + 1]]
+        out.append(a.reshape((channels, s.H, s.W)) if channels > 1 else a.reshape(s.H, s.W))
+    return out
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=lambda t: f"t{t[0]}b{t[1]}p{t[2]}")
+def test_every_tuning_matches_oracle(tuning):
+    sc = inputs.tiny(seed=3, N=120, H=72, W=88)
+    rng = np.random.default_rng(7)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    img, T, g, _ = run_batch([sc], sc.atlas, tuning, gI=gI)
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)
+    assert np.abs(img.reshape(3, sc.H, sc.W) - ref["image"]).max() <= IMG_TOL
+    assert np.abs(T.reshape(sc.H, sc.W) - ref["T_final"]).max() <= IMG_TOL
+    gref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+    grad_close(g, gref, what=str(tuning))
+
+
+@pytest.mark.parametrize("tuning", [(16, 32, 2), (8, 64, 1), (32, 32, 4)])
+def test_multi_canvas_batch_matches_oracle_per_canvas(tuning):
+    scenes, atlas = small_batch()
+    params, bid, off, pix = concat(scenes)
+    rng = np.random.default_rng(9)
+    gI = rng.normal(size=3 * int(pix[-1])).astype(np.float32)
+    img, T, g, st = run_batch(scenes, atlas, tuning, gI=gI, bg=(0.3, 0.6, 0.9))
+    imgs = split(img, scenes, pix, 3)
+    gIs = split(gI, scenes, pix, 3)
+    for c, s in enumerate(scenes):
+        ref = oracle.render(s.H, s.W, s.params, s.bitmap_id, atlas, background=(0.3, 0.6, 0.9))
+        assert np.abs(imgs[c] - ref["image"]).max() <= IMG_TOL, c
+        if s.N:
+            gref = oracle.grad(s.H, s.W, s.params, s.bitmap_id, atlas, gIs[c], background=(0.3, 0.6, 0.9))
+            grad_close(g[off[c]:off[c + 1]], gref, what=f"canvas {c}")
+    assert st.pairs_required > 0
+
+
+def test_batched_workload_sampled_against_oracle():
+    """The 64-canvas workload shape (sides 256..1024, 1k..50k primitives), scaled
+    down to 12 canvases so the oracle can check sampled pixels of every canvas."""
+    scenes = inputs.batched(seed=4, n_canvas=12, side=(96, 320), nprim=(200, 3000))
+    atlas = scenes[0].atlas
+    params, bid, off, pix = concat(scenes)
+    img, T, _, _ = run_batch(scenes, atlas, (16, 32, 2), T_stop=1e-6)
+    imgs = split(img, scenes, pix, 3)
+    rng = np.random.default_rng(1)
+    for c, s in enumerate(scenes):
+        px = rng.integers(0, s.W, 200)
+        py = rng.integers(0, s.H, 200)
+        ref = oracle.render(s.H, s.W, s.params, s.bitmap_id, atlas, background=s.background,
+                            pixels=(px, py))
+        assert np.abs(imgs[c][:, py, px] - ref["image"]).max() <= IMG_TOL, c
+
+
+def test_capacity_overflow_is_reported_and_nothing_is_written():
+    cuda()
+    sc = inputs.tiny(seed=4, N=200, H=64, W=64)
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, 64, 16, 1)  # room for 16 list entries only
+    try:
+        D.dbmp_bin(ws, sc.H, sc.W, 16, to_dev(sc.params), to_dev(sc.bitmap_id), sc.N, atlas, 1.0)
+        image = torch.full((3, 64, 64), -7.0, device="cuda")
+        T = torch.full((64, 64), -7.0, device="cuda")
+        nl = torch.zeros(64, 64, dtype=torch.int32, device="cuda")
+        D.dbmp_render_fwd(ws, atlas, D.make_background((1, 1, 1)), 0.0, image, T, nl)
+        with pytest.raises(D.DbmpError) as e:
+            D.dbmp_status_poll(ws)
+        assert e.value.code == D.DBMP_ERR_CAPACITY
+        st = D.dbmp_status_poll(ws, raise_on_error=False)  # cleared after the first poll
+        assert st.code == 0 and st.pairs_required > 16
+        assert torch.all(image == -7.0) and torch.all(T == -7.0)
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
+def test_out_of_range_bitmap_id_is_not_drawn():
+    cuda()
+    sc = inputs.tiny(seed=6, N=30, H=48, W=48)
+    bid = sc.bitmap_id.copy()
+    bid[4] = 5   # atlas has one bitmap
+    bid[9] = -1
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, 64, 1 << 16, 1)
+    try:
+        D.dbmp_bin(ws, 48, 48, 16, to_dev(sc.params), to_dev(bid), sc.N, atlas, 1.0)
+        image = torch.empty(3, 48, 48, device="cuda")
+        T = torch.empty(48, 48, device="cuda")
+        nl = torch.empty(48, 48, dtype=torch.int32, device="cuda")
+        D.dbmp_render_fwd(ws, atlas, D.make_background((1, 1, 1)), 0.0, image, T, nl)
+        st = D.dbmp_status_poll(ws)
+        assert st.n_degenerate == 2
+        keep = np.setdiff1d(np.arange(sc.N), [4, 9])
+        ref = oracle.render(48, 48, sc.params[keep], sc.bitmap_id[keep], sc.atlas)
+        assert np.abs(image.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
+def test_mse_kernel_matches_oracle():
+    cuda()
+    rng = np.random.default_rng(0)
+    a = rng.uniform(0, 1, (3, 77, 45)).astype(np.float32)
+    b = rng.uniform(0, 1, (3, 77, 45)).astype(np.float32)
+    dL = torch.empty(3, 77, 45, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    D.dbmp_mse_grad(to_dev(a), to_dev(b), dL, loss)
+    torch.cuda.synchronize()
+    # the kernel forms I - I* in float32 (one rounding, relative 6e-8 per element) and
+    # squares and sums in float64
+    assert loss.item() == pytest.approx(oracle.mse(a, b), rel=2e-7)
+    np.testing.assert_allclose(dL.cpu().numpy(), oracle.mse_grad(a, b), rtol=1e-6, atol=1e-12)
+
+
+def test_adam_kernel_matches_oracle():
+    cuda()
+    rng = np.random.default_rng(1)
+    N = 1000
+    p0 = rng.normal(size=(N, 8)).astype(np.float32)
+    p = to_dev(p0)
+    m = torch.zeros(N, 8, device="cuda")
+    v = torch.zeros(N, 8, device="cuda")
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cfg = D.adam_config(lr=0.1, gamma=0.95, zero_grad=True)
+    rp, rm, rv = p0.astype(np.float64), np.zeros((N, 8)), np.zeros((N, 8))
+    for t in range(1, 6):
+        g = rng.normal(size=(N, 8)).astype(np.float32)
+        gd = to_dev(g)
+        D.dbmp_adam_step(p, gd, m, v, step, cfg)
+        torch.cuda.synchronize()
+        assert torch.all(gd == 0)
+        rp, rm, rv = oracle.adam_step(rp, g, rm, rv, t, 0.1 * 0.95 ** (t - 1))
+    assert step.item() == 5
+    np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=2e-5)
+
+
+def test_cuda_graph_captures_a_whole_optimisation_step():
+    """bin + fwd + MSE + bwd captured once in a CUDA graph: replays at fixed
+    parameters accumulate exactly the gradient the eager calls accumulate (up to
+    atomic summation order).  With the Adam step inside the graph, the device step
+    counter advances once per replay and the loss falls."""
+    cuda()
+    sc = inputs.tiny(seed=8, N=300, H=128, W=128)
+    tg = inputs.tiny(seed=9, N=300, H=128, W=128)
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    bg = D.make_background((1, 1, 1))
+    ws = D.dbmp_workspace_create(sc.N, 256, 1 << 20, 1)
+    D.dbmp_batch_plan(ws, [128], [128], [0, sc.N], 16, 32, 2)
+    params = to_dev(sc.params)
+    bid = to_dev(sc.bitmap_id)
+    target = torch.empty(3, 128, 128, device="cuda")
+    T = torch.empty(128, 128, device="cuda")
+    nl = torch.empty(128, 128, dtype=torch.int32, device="cuda")
+    D.dbmp_batch_render(ws, to_dev(tg.params), to_dev(tg.bitmap_id), atlas, 1.0, bg, 0.0,
+                        D.BATCH_BIN | D.BATCH_FWD, target, T, nl)
+    image = torch.empty(3, 128, 128, device="cuda")
+    dL = torch.empty(3, 128, 128, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dparams = torch.zeros(sc.N, 8, device="cuda")
+    m = torch.zeros(sc.N, 8, device="cuda")
+    v = torch.zeros(sc.N, 8, device="cuda")
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cfg = D.adam_config(lr=0.02, gamma=0.99, zero_grad=True)
+
+    def grad_only():
+        D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, 1e-6, D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
+        D.dbmp_mse_grad(image, target, dL, loss)
+        D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, 1e-6, D.BATCH_BWD, image, T, nl, dL, dparams)
+
+    def full_step():
+        grad_only()
+        D.dbmp_adam_step(params, dparams, m, v, step, cfg)
+
+    try:
+        for _ in range(3):
+            grad_only()
+        torch.cuda.synchronize()
+        eager = dparams.clone()
+        loss0 = loss.item()
+        dparams.zero_()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            g1 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g1, stream=s):
+                grad_only()
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2, stream=s):
+                full_step()
+        torch.cuda.synchronize()
+        dparams.zero_()
+        for _ in range(3):
+            g1.replay()
+        torch.cuda.synchronize()
+        assert loss.item() == pytest.approx(loss0, rel=1e-12)
+        grad_close(dparams.cpu().numpy(), eager.cpu().numpy(), rel=1e-4, what="graph vs eager")
+        dparams.zero_()
+        losses = []
+        for _ in range(20):
+            g2.replay()
+            losses.append(loss.item())
+        assert step.item() == 20
+        assert losses[-1] < 0.9 * losses[0]
+    finally:
+        torch.cuda.synchronize()
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
+def test_autotune_picks_a_supported_tuning():
+    cuda()
+    sc = inputs.tiny(seed=10, N=500, H=200, W=160)
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, 25 * 20, 1 << 22, 1)
+    try:
+        D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N])
+        p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
+        image = torch.empty(3, sc.H, sc.W, device="cuda")
+        T = torch.empty(sc.H, sc.W, device="cuda")
+        nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+        dL = torch.zeros(3, sc.H, sc.W, device="cuda")
+        dp = torch.zeros(sc.N, 8, device="cuda")
+        best, ms = D.dbmp_autotune(ws, p, b, atlas, 1.0, D.make_background((1, 1, 1)), 1e-6,
+                                   D.BATCH_FWD | D.BATCH_BWD, image, T, nl, dL, dp, reps=1)
+        assert tuple(best) in TUNINGS and ms > 0
+        D.dbmp_batch_render(ws, p, b, atlas, 1.0, D.make_background((1, 1, 1)), 0.0,
+                            D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
+        ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas)
+        assert np.abs(image.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
