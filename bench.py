@@ -31,10 +31,14 @@ WORKLOAD = "main_1024sq_20k"
 L2_FLUSH_BYTES = 512 << 20
 T_STOP = 1e-6
 
-# Algorithmic FP32 operations (FMA = 2) per (pixel, list entry) pair; see the design doc.
+# Algorithmic FP32 operations (FMA = 2) per contributing (pixel, primitive) pair, the
+# unit of work: a pair with alpha > 0 composited before the pixel saturated.  Pairs
+# whose bitmap sample is zero change nothing and are not counted.
 FLOPS_SAMPLE = 21       # Eqs. 1-2 and the bilinear sample (Eqs. S1-S3)
-FLOPS_COMPOSITE = 10    # Eqs. 3-5 for a pair with alpha > 0
-FLOPS_GRAD = 44         # Eq. 6, S4, S5 terms and the recursion for a pair with alpha > 0
+FLOPS_COMPOSITE = 10    # Eqs. 3-5 (alpha, over, transmittance)
+FLOPS_GRAD = 44         # Eq. 6, S4, S5 terms and the reverse recursion
+FLOPS_FWD_PAIR = FLOPS_SAMPLE + FLOPS_COMPOSITE
+FLOPS_BWD_PAIR = FLOPS_SAMPLE + FLOPS_GRAD
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -371,8 +375,8 @@ def run_dbmp(args):
     fwd_ms = float(phase[:, 1].mean())
     bwd_ms = float(phase[:, 3].mean())
     ev_f, ev_b, contrib = pairs_end[0], pairs_end[1], pairs_end[2]
-    flops_f = FLOPS_SAMPLE * ev_f + FLOPS_COMPOSITE * contrib
-    flops_b = FLOPS_SAMPLE * ev_b + FLOPS_GRAD * contrib
+    flops_f = FLOPS_FWD_PAIR * contrib
+    flops_b = FLOPS_BWD_PAIR * contrib
     if bwd_ms >= fwd_ms:
         dom, flops, dms, key = "k_bwd (backward compositor)", flops_b, bwd_ms, "bwd"
     else:
@@ -396,11 +400,15 @@ def run_dbmp(args):
         "breakdown_ms": {"bin": float(phase[:, 0].mean()), "fwd": fwd_ms, "mse": float(phase[:, 2].mean()),
                          "bwd": bwd_ms, "adam": float(phase[:, 4].mean()),
                          "step_min": float(step_ms.min()), "step_max": float(step_ms.max())},
-        "work": {"pairs_evaluated_fwd": ev_f, "pairs_evaluated_bwd": ev_b, "pairs_contributing": contrib,
-                 "tile_list_entries": pairs_end[3], "at_warmup_end": list(pairs)},
+        "work": {"pairs_contributing": contrib, "pairs_in_walk_fwd": ev_f, "pairs_in_walk_bwd": ev_b,
+                 "tile_list_entries": pairs_end[3], "warp_steps_fwd": st.warp_steps,
+                 "warp_steps_bwd": st.warp_steps_bwd, "survivors_fwd": st.survivors,
+                 "survivors_bwd": st.survivors_bwd, "at_warmup_end": list(pairs)},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max clock (derived)",
+                     "unit_of_work": "contributing (pixel, primitive) pair",
+                     "flops_per_unit": FLOPS_BWD_PAIR if key == "bwd" else FLOPS_FWD_PAIR,
                      "algorithmic_flops_per_launch": flops, "kernel_ms": dms,
                      "traffic": traffic_for(key)},
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

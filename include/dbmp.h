@@ -83,8 +83,10 @@ typedef struct DbmpAtlas DbmpAtlas;
  * The library stores, for every lattice cell (v0, u0) in [-1, H_b-1] x
  * [-1, W_b-1], the four taps {P[v0,u0], P[v0,u0+1], P[v0+1,u0], P[v0+1,u0+1]}
  * (zero outside the bitmap) as one 16-byte vector, so one bilinear sample is one
- * 128-bit load.  Allocates (n_bmp (H_b+1)(W_b+1) 16 bytes) and synchronises
- * `stream`.  texels_dev is not referenced after the call. */
+ * 128-bit load, and a summed-area table of the non-zero texels, with which the
+ * compositors skip primitives whose bitmap is empty over a whole region of
+ * pixels.  Allocates n_bmp (H_b+1)(W_b+1) 20 bytes and synchronises `stream`.
+ * texels_dev is not referenced after the call. */
 int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b,
                           dbmp_stream_t stream, DbmpAtlas **out);
 int32_t dbmp_atlas_destroy(DbmpAtlas *atlas);
@@ -120,6 +122,10 @@ typedef struct {
     int64_t pairs_evaluated;/* (pixel, list entry) pairs the last fwd evaluated  */
     int64_t pairs_evaluated_bwd; /* same for the last bwd                       */
     int64_t pairs_contributing;  /* pairs with alpha > 0 the last fwd composited  */
+    int64_t warp_steps;          /* list entries walked by warps in the last fwd   */
+    int64_t warp_steps_bwd;      /* same for the last bwd                          */
+    int64_t survivors;           /* list entries that passed the region test (fwd) */
+    int64_t survivors_bwd;       /* same for the last bwd                          */
 } DbmpDeviceStatus;
 
 /* Synchronises `stream`, copies the status block to *out, clears the sticky

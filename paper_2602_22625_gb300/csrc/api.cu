@@ -43,8 +43,9 @@ bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
 
 struct DbmpAtlas {
     float4 *quad = nullptr;
+    int32_t *sat = nullptr;
     int32_t n_bmp = 0, Hb = 0, Wb = 0;
-    AtlasView view() const { return AtlasView{quad, n_bmp, Hb, Wb}; }
+    AtlasView view() const { return AtlasView{quad, sat, n_bmp, Hb, Wb}; }
 };
 
 struct DbmpWorkspace {
@@ -172,7 +173,7 @@ int32_t build_plan(DbmpWorkspace *ws, int32_t n, const int32_t *H, const int32_t
 __global__ void k_set_canvas(CanvasDesc d, CanvasDesc *dst) { *dst = d; }
 
 int32_t check_atlas(const DbmpAtlas *atlas) {
-    if (!atlas || !atlas->quad) return fail(DBMP_ERR_INVALID_ARG, "atlas is NULL");
+    if (!atlas || !atlas->quad || !atlas->sat) return fail(DBMP_ERR_INVALID_ARG, "atlas is NULL");
     return DBMP_OK;
 }
 
@@ -243,7 +244,8 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     a.T_final = T_final;
     a.n_last = n_last;
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, sizeof(int64_t), st), "status reset");
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_contrib, 0, sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_contrib, 0, 2 * sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->survivors_fwd, 0, sizeof(int64_t), st), "status reset");
     DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
     return DBMP_OK;
 }
@@ -257,6 +259,8 @@ int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     a.dL_dimage = dL_dimage;
     a.dL_dalpha = dL_dalpha;
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->warp_steps_bwd, 0, sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->survivors_bwd, 0, sizeof(int64_t), st), "status reset");
     if (ws->N > 0)
         DBMP_CUDA(cudaMemsetAsync(ws->graw, 0, sizeof(float) * 8 * (size_t)ws->N, st), "graw reset");
     DBMP_CUDA(launch_bwd(a, ws->cfg, st), "backward launch");
@@ -285,16 +289,20 @@ int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
     a->n_bmp = n_bmp;
     a->Hb = H_b;
     a->Wb = W_b;
-    cudaError_t e = cudaMalloc(&a->quad, sizeof(float4) * (size_t)n_bmp * (H_b + 1) * (W_b + 1));
+    const size_t cells = (size_t)n_bmp * (H_b + 1) * (W_b + 1);
+    cudaError_t e = cudaMalloc(&a->quad, sizeof(float4) * cells);
+    if (e == cudaSuccess) e = cudaMalloc(&a->sat, sizeof(int32_t) * cells);
     if (e != cudaSuccess) {
+        cudaFree(a->quad);
         delete a;
         return fail(DBMP_ERR_NO_MEMORY, "atlas allocation: %s", cudaGetErrorString(e));
     }
     cudaStream_t st = (cudaStream_t)stream;
-    e = launch_quad_build(texels_dev, a->quad, n_bmp, H_b, W_b, st);
+    e = launch_quad_build(texels_dev, a->quad, a->sat, n_bmp, H_b, W_b, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(a->quad);
+        cudaFree(a->sat);
         delete a;
         return cuda_fail(e, "atlas build");
     }
@@ -305,7 +313,7 @@ int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
 int32_t dbmp_atlas_update(DbmpAtlas *atlas, const float *texels_dev, dbmp_stream_t stream) {
     if (int32_t r = check_atlas(atlas)) return r;
     if (!texels_dev) return fail(DBMP_ERR_INVALID_ARG, "texels_dev is NULL");
-    DBMP_CUDA(launch_quad_build(texels_dev, atlas->quad, atlas->n_bmp, atlas->Hb, atlas->Wb,
+    DBMP_CUDA(launch_quad_build(texels_dev, atlas->quad, atlas->sat, atlas->n_bmp, atlas->Hb, atlas->Wb,
                                 (cudaStream_t)stream),
               "atlas update");
     return DBMP_OK;
@@ -314,6 +322,7 @@ int32_t dbmp_atlas_update(DbmpAtlas *atlas, const float *texels_dev, dbmp_stream
 int32_t dbmp_atlas_destroy(DbmpAtlas *atlas) {
     if (!atlas) return DBMP_OK;
     cudaFree(atlas->quad);
+    cudaFree(atlas->sat);
     delete atlas;
     return DBMP_OK;
 }
@@ -389,6 +398,10 @@ int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStat
     out->pairs_evaluated = s.pairs_eval_fwd;
     out->pairs_evaluated_bwd = s.pairs_eval_bwd;
     out->pairs_contributing = s.pairs_contrib;
+    out->warp_steps = s.warp_steps_fwd;
+    out->warp_steps_bwd = s.warp_steps_bwd;
+    out->survivors = s.survivors_fwd;
+    out->survivors_bwd = s.survivors_bwd;
     const int32_t zero = 0;
     DBMP_CUDA(cudaMemcpy(&ws->status->code, &zero, sizeof zero, cudaMemcpyHostToDevice), "status clear");
     if (s.code == DBMP_ERR_CAPACITY)

@@ -42,6 +42,10 @@ struct DevStatus {
     int64_t pairs_eval_fwd;
     int64_t pairs_eval_bwd;
     int64_t pairs_contrib;  // (pixel, layer) pairs with alpha > 0 composited by the last fwd
+    int64_t warp_steps_fwd; // list entries walked, summed over warps (last fwd)
+    int64_t warp_steps_bwd; // same for the last bwd
+    int64_t survivors_fwd;  // records that passed the region test (last fwd)
+    int64_t survivors_bwd;  // same for the last bwd
     int32_t lists_valid;   // 1 after a binning that fit its capacity
     int32_t pad;
     uint32_t queue[4];     // persistent-kernel work counters
@@ -49,6 +53,7 @@ struct DevStatus {
 
 struct AtlasView {
     const float4 *quad;    // [n_bmp][H_b+1][W_b+1] tap quads
+    const int32_t *sat;    // [n_bmp][H_b+1][W_b+1] summed-area table of (texel > 0)
     int32_t n_bmp, Hb, Wb;
 };
 
@@ -153,8 +158,8 @@ cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
 cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
                                  float *dparams, int32_t N, cudaStream_t st);
-cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t n_bmp, int32_t Hb,
-                              int32_t Wb, cudaStream_t st);
+cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t *sat, int32_t n_bmp,
+                              int32_t Hb, int32_t Wb, cudaStream_t st);
 cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
                             double *loss, cudaStream_t st);
 cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32_t *step,

@@ -27,6 +27,31 @@ __global__ void k_quad(const float *__restrict__ tex, float4 *__restrict__ quad,
     }
 }
 
+// sat[b][v][u] = number of texels P[v'][u'] > 0 with v' < v and u' < u
+// (v in [0, H_b], u in [0, W_b]); one CTA per bitmap: row prefix sums, then columns.
+__global__ void k_sat(const float *__restrict__ tex, int32_t *__restrict__ sat, int32_t Hb, int32_t Wb) {
+    const int b = blockIdx.x;
+    const float *P = tex + (int64_t)b * Hb * Wb;
+    int32_t *S = sat + (int64_t)b * (Hb + 1) * (Wb + 1);
+    for (int u = threadIdx.x; u <= Wb; u += blockDim.x) S[u] = 0;
+    for (int v = threadIdx.x; v < Hb; v += blockDim.x) {
+        int32_t run = 0;
+        S[(int64_t)(v + 1) * (Wb + 1)] = 0;
+        for (int u = 0; u < Wb; ++u) {
+            run += P[(int64_t)v * Wb + u] > 0.0f ? 1 : 0;
+            S[(int64_t)(v + 1) * (Wb + 1) + u + 1] = run;
+        }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u <= Wb; u += blockDim.x) {
+        int32_t run = 0;
+        for (int v = 1; v <= Hb; ++v) {
+            run += S[(int64_t)v * (Wb + 1) + u];
+            S[(int64_t)v * (Wb + 1) + u] = run;
+        }
+    }
+}
+
 __global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg, int64_t n,
                       float *__restrict__ dL, double *loss) {
     __shared__ double red[32];
@@ -87,10 +112,11 @@ int grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t n_bmp, int32_t Hb,
-                              int32_t Wb, cudaStream_t st) {
+cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t *sat, int32_t n_bmp,
+                              int32_t Hb, int32_t Wb, cudaStream_t st) {
     const int64_t total = (int64_t)n_bmp * (Hb + 1) * (Wb + 1);
     k_quad<<<grid_for(total, 256), 256, 0, st>>>(texels, quad, n_bmp, Hb, Wb);
+    k_sat<<<n_bmp, 256, 0, st>>>(texels, sat, Hb, Wb);
     return cudaGetLastError();
 }
 

@@ -40,26 +40,99 @@ __device__ __forceinline__ int find_canvas_tile(const CanvasDesc *cv, int n, int
     return lo;
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// Records of one batch held in registers: lane l holds entries l, l + 32, ...
+template <int RPL>
+struct Prefetch {
+    float4 q0[RPL], q1[RPL], q2[RPL];
+};
 
-// One warp gathers records list[l0 .. l0+n) into dst[0 .. n) (3 x 16-byte async
-// copies per record) and commits them as one group.
-__device__ __forceinline__ void warp_stage(PrimRec *dst, const PrimRec *__restrict__ rec,
-                                           const int32_t *__restrict__ list, int64_t l0, int n, int lane) {
-    for (int j = lane; j < n; j += 32) {
-        const char *s = reinterpret_cast<const char *>(rec + list[l0 + j]);
-        char *d = reinterpret_cast<char *>(dst + j);
-        cp_async16(d, s);
-        cp_async16(d + 16, s + 16);
-        cp_async16(d + 32, s + 32);
+// Issues the loads of list entries [l0, l0 + n) (lane l: entries l + 32 r).  The
+// loads are consumed by the next compaction, so their latency overlaps with the
+// compositing of the previous batch.
+template <int RPL>
+__device__ __forceinline__ void prefetch(Prefetch<RPL> &pf, const PrimRec *__restrict__ rec,
+                                         const int32_t *__restrict__ list, int64_t l0, int n, int lane) {
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int j = lane + 32 * r;
+        if (j < n) {
+            const float4 *p = reinterpret_cast<const float4 *>(rec + __ldg(list + l0 + j));
+            pf.q0[r] = __ldg(p);
+            pf.q1[r] = __ldg(p + 1);
+            pf.q2[r] = __ldg(p + 2);
+        }
     }
-    cp_async_commit();
+}
+
+__device__ __forceinline__ PrimRec as_rec(float4 a, float4 b, float4 c) {
+    PrimRec r;
+    r.x = a.x; r.y = a.y; r.A = a.z; r.B = a.w;
+    r.C = b.x; r.D = b.y; r.a = b.z; r.quad_off = __float_as_int(b.w);
+    r.cr = c.x; r.cg = c.y; r.cb = c.z; r.index = __float_as_int(c.w);
+    return r;
+}
+
+// Can primitive r be non-zero anywhere in the pixel rectangle [x0, x0+w] x [y0, y0+h]?
+// U and V are affine in (x, y), so the rectangle maps to a parallelogram whose
+// bounding box, widened by one texel (plus the bilinear neighbour), contains every
+// tap any of its pixels reads; the bitmap's summed-area table of non-zero texels
+// says whether that box holds a non-zero texel.  Never false for a primitive that
+// is non-zero at one of the pixels, so culling with it changes no result.
+__device__ __forceinline__ bool region_hits(const PrimRec &r, const AtlasView &at, float x0, float y0,
+                                            float w, float h, float kw, float kv) {
+    const float dx = x0 - r.x, dy = y0 - r.y;
+    const float U0 = fmaf(r.A, dx, r.B * dy) + kw;
+    const float V0 = fmaf(r.C, dx, r.D * dy) + kv;
+    const float aw = r.A * w, bh = r.B * h, cw = r.C * w, dh = r.D * h;
+    const float umin = U0 + fminf(aw, 0.0f) + fminf(bh, 0.0f);
+    const float umax = U0 + fmaxf(aw, 0.0f) + fmaxf(bh, 0.0f);
+    const float vmin = V0 + fminf(cw, 0.0f) + fminf(dh, 0.0f);
+    const float vmax = V0 + fmaxf(dh, 0.0f) + fmaxf(cw, 0.0f);
+    const float Wm = (float)(at.Wb - 1), Hm = (float)(at.Hb - 1);
+    // texels [floor(umin) - 1, floor(umax) + 2] x [floor(vmin) - 1, floor(vmax) + 2]
+    const float fu0 = floorf(umin) - 1.0f, fu1 = floorf(umax) + 2.0f;
+    const float fv0 = floorf(vmin) - 1.0f, fv1 = floorf(vmax) + 2.0f;
+    if (!(fu1 >= 0.0f && fv1 >= 0.0f && fu0 <= Wm && fv0 <= Hm)) return false;
+    const int u0 = (int)fmaxf(fu0, 0.0f), u1 = (int)fminf(fu1, Wm);
+    const int v0 = (int)fmaxf(fv0, 0.0f), v1 = (int)fminf(fv1, Hm);
+    const int Ws = at.Wb + 1;
+    const int32_t *S = at.sat + r.quad_off;
+    const int32_t n = __ldg(S + (v1 + 1) * Ws + u1 + 1) - __ldg(S + v0 * Ws + u1 + 1) -
+                      __ldg(S + (v1 + 1) * Ws + u0) + __ldg(S + v0 * Ws + u0);
+    return n > 0;
+}
+
+// Tests the prefetched records of list entries [e0, e0 + n) against the warp's
+// region and writes the survivors, in list order, to sh[0 .. m) with their list
+// positions in pos[]; returns m (same on every lane).
+template <int RPL>
+__device__ __forceinline__ int compact(const Prefetch<RPL> &pf, int e0, int n, PrimRec *sh, int *pos,
+                                       const AtlasView &at, float x0, float y0, float w, float h,
+                                       float kw, float kv, int lane) {
+    int base = 0;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int j = lane + 32 * r;
+        bool keep = false;
+        PrimRec rc;
+        if (j < n) {
+            rc = as_rec(pf.q0[r], pf.q1[r], pf.q2[r]);
+            keep = region_hits(rc, at, x0, y0, w, h, kw, kv);
+        }
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) {
+            const int slot = base + __popc(m & lt);
+            float4 *d = reinterpret_cast<float4 *>(sh + slot);
+            d[0] = pf.q0[r];
+            d[1] = pf.q1[r];
+            d[2] = pf.q2[r];
+            pos[slot] = e0 + j;
+        }
+        base += __popc(m);
+    }
+    __syncwarp();
+    return base;
 }
 
 struct Region {
@@ -104,16 +177,20 @@ __device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
 // ---------------------------------------------------------------------------
 template <int TILE, int PPT, int BATCH>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32_t n_items) {
-    __shared__ PrimRec sh_all[kWarpsPerBlock][2][BATCH];
-    if (a.status->lists_valid == 0) return;
+    constexpr int RPL = BATCH / 32;   // records per lane per batch
     constexpr int LROWS = 32 / TILE;  // rows covered by the 32 lanes in one pass
+    constexpr int RH = LROWS * PPT;   // rows of a region
+    __shared__ PrimRec sh_all[kWarpsPerBlock][BATCH];
+    __shared__ int pos_all[kWarpsPerBlock][BATCH];
+    if (a.status->lists_valid == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    PrimRec(*sh)[BATCH] = sh_all[warp];
+    PrimRec *sh = sh_all[warp];
+    int *pos = pos_all[warp];
     const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float tstop = fmaxf(a.T_stop, kTFloor);
-    int64_t ev_acc = 0, ct_acc = 0;
+    int64_t ev_acc = 0, ct_acc = 0, ws_acc = 0, sv_acc = 0;
 
     for (int item = next_item(&a.status->queue[0], lane); item < n_items;
          item = next_item(&a.status->queue[0], lane)) {
@@ -131,21 +208,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
             C0[k] = C1[k] = C2[k] = 0.0f;
             last[k] = -1;
         }
+        const float rx0 = (float)g.x0, ry0 = (float)g.y0;
+        const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
+        int walked = g.len;
         if (g.len > 0) {
-            warp_stage(sh[0], a.rec, a.list, g.start, min(BATCH, g.len), lane);
-            bool alive = true;
-            for (int b0 = 0, it = 0; b0 < g.len && alive; b0 += BATCH, ++it) {
+            Prefetch<RPL> pf;
+            prefetch<RPL>(pf, a.rec, a.list, g.start, min(BATCH, g.len), lane);
+            bool alive = __any_sync(FULL, T[0] >= tstop || (PPT > 1 && T[PPT - 1] >= tstop));
+            for (int b0 = 0; b0 < g.len && alive; b0 += BATCH) {
                 const int n = min(BATCH, g.len - b0);
-                const PrimRec *cur = sh[it & 1];
+                const int m = compact<RPL>(pf, b0, n, sh, pos, a.atlas, rx0, ry0, rw, rh, kw, kv, lane);
+                sv_acc += m;
                 if (b0 + BATCH < g.len)
-                    warp_stage(sh[(it + 1) & 1], a.rec, a.list, g.start + b0 + BATCH,
-                               min(BATCH, g.len - b0 - BATCH), lane);
-                else
-                    cp_async_commit();
-                cp_async_wait<1>();
-                __syncwarp();
-                for (int j = 0; j < n; ++j) {
-                    const PrimRec r = cur[j];
+                    prefetch<RPL>(pf, a.rec, a.list, g.start + b0 + BATCH, min(BATCH, g.len - b0 - BATCH),
+                                  lane);
+                for (int t = 0; t < m; ++t) {
+                    const PrimRec r = sh[t];
+                    const int j = pos[t];
                     bool any = false;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
@@ -160,21 +239,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
                             C1[k] = __fmaf_rn(w, r.cg, C1[k]);
                             C2[k] = __fmaf_rn(w, r.cb, C2[k]);
                             T[k] = __fmul_rn(T[k], q);
-                            last[k] = b0 + j;
+                            last[k] = j;
                             ++ct_acc;
                         }
                         any = any || T[k] >= tstop;
                     }
                     if (!__any_sync(FULL, any)) {
                         alive = false;
+                        walked = j + 1;
                         break;
                     }
                 }
                 __syncwarp();
             }
-            cp_async_wait<0>();
-            __syncwarp();
         }
+        ws_acc += walked;
         const int64_t HW = (int64_t)g.d.H * g.d.W;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -195,9 +274,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
         ev_acc += __shfl_xor_sync(FULL, ev_acc, o);
         ct_acc += __shfl_xor_sync(FULL, ct_acc, o);
     }
-    if (lane == 0 && ev_acc) {
-        atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd, (unsigned long long)ev_acc);
-        atomicAdd((unsigned long long *)&a.status->pairs_contrib, (unsigned long long)ct_acc);
+    if (lane == 0) {
+        if (ev_acc) {
+            atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd, (unsigned long long)ev_acc);
+            atomicAdd((unsigned long long *)&a.status->pairs_contrib, (unsigned long long)ct_acc);
+        }
+        if (ws_acc) atomicAdd((unsigned long long *)&a.status->warp_steps_fwd, (unsigned long long)ws_acc);
+        if (sv_acc) atomicAdd((unsigned long long *)&a.status->survivors_fwd, (unsigned long long)sv_acc);
     }
 }
 
@@ -262,16 +345,20 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
 
 template <int TILE, int PPT, int BATCH>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32_t n_items) {
-    __shared__ PrimRec sh_all[kWarpsPerBlock][2][BATCH];
-    if (a.status->lists_valid == 0) return;
+    constexpr int RPL = BATCH / 32;
     constexpr int LROWS = 32 / TILE;
+    constexpr int RH = LROWS * PPT;
+    __shared__ PrimRec sh_all[kWarpsPerBlock][BATCH];
+    __shared__ int pos_all[kWarpsPerBlock][BATCH];
+    if (a.status->lists_valid == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    PrimRec(*sh)[BATCH] = sh_all[warp];
+    PrimRec *sh = sh_all[warp];
+    int *pos = pos_all[warp];
     const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float rho = kw / kv, irho = kv / kw;
-    int64_t ev_acc = 0;
+    int64_t ev_acc = 0, ws_acc = 0, sv_acc = 0;
 
     for (int item = next_item(&a.status->queue[1], lane); item < n_items;
          item = next_item(&a.status->queue[1], lane)) {
@@ -306,22 +393,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(FULL, my_max, o));
         if (my_max < 0) continue;
+        ws_acc += my_max + 1;
+        const float rx0 = (float)g.x0, ry0 = (float)g.y0;
+        const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
 
         // batches [lo, hi) from the back of the region's walk
         int hi = my_max + 1;
         int lo = max(0, hi - BATCH);
-        warp_stage(sh[0], a.rec, a.list, g.start + lo, hi - lo, lane);
-        for (int it = 0; hi > 0; ++it) {
+        Prefetch<RPL> pf;
+        prefetch<RPL>(pf, a.rec, a.list, g.start + lo, hi - lo, lane);
+        while (hi > 0) {
+            const int m = compact<RPL>(pf, lo, hi - lo, sh, pos, a.atlas, rx0, ry0, rw, rh, kw, kv, lane);
+            sv_acc += m;
             const int nlo = max(0, lo - BATCH);
-            const PrimRec *cur = sh[it & 1];
-            if (lo > 0)
-                warp_stage(sh[(it + 1) & 1], a.rec, a.list, g.start + nlo, lo - nlo, lane);
-            else
-                cp_async_commit();
-            cp_async_wait<1>();
-            __syncwarp();
-            for (int j = hi - 1; j >= lo; --j) {
-                const PrimRec r = cur[j - lo];
+            if (lo > 0) prefetch<RPL>(pf, a.rec, a.list, g.start + nlo, lo - nlo, lane);
+            for (int t = m - 1; t >= 0; --t) {
+                const PrimRec r = sh[t];
+                const int j = pos[t];
                 float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 bool any = false;
 #pragma unroll
@@ -359,13 +447,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
             hi = lo;
             lo = nlo;
         }
-        cp_async_wait<0>();
-        __syncwarp();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ev_acc += __shfl_xor_sync(FULL, ev_acc, o);
-    if (lane == 0 && ev_acc)
-        atomicAdd((unsigned long long *)&a.status->pairs_eval_bwd, (unsigned long long)ev_acc);
+    if (lane == 0) {
+        if (ev_acc) atomicAdd((unsigned long long *)&a.status->pairs_eval_bwd, (unsigned long long)ev_acc);
+        if (ws_acc) atomicAdd((unsigned long long *)&a.status->warp_steps_bwd, (unsigned long long)ws_acc);
+        if (sv_acc) atomicAdd((unsigned long long *)&a.status->survivors_bwd, (unsigned long long)sv_acc);
+    }
 }
 
 // Per-primitive chain rule from the eight reduced sums to the raw parameters:

@@ -52,7 +52,9 @@ class DbmpLimits(ctypes.Structure):
 class DbmpDeviceStatus(ctypes.Structure):
     _fields_ = [("code", ctypes.c_int32), ("n_degenerate", ctypes.c_int32),
                 ("pairs_required", ctypes.c_int64), ("pairs_evaluated", ctypes.c_int64),
-                ("pairs_evaluated_bwd", ctypes.c_int64), ("pairs_contributing", ctypes.c_int64)]
+                ("pairs_evaluated_bwd", ctypes.c_int64), ("pairs_contributing", ctypes.c_int64),
+                ("warp_steps", ctypes.c_int64), ("warp_steps_bwd", ctypes.c_int64),
+                ("survivors", ctypes.c_int64), ("survivors_bwd", ctypes.c_int64)]
 
 
 class DbmpAdamConfig(ctypes.Structure):
