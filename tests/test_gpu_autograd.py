@@ -1,0 +1,150 @@
+"""torch.autograd.Function over the C ABI: gradients against the oracle's FP64
+analytic gradient and against central finite differences (small canvas, and the
+2048^2 x 200k heavy-overlap workload with FD localised to each primitive's box)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_22625_gb300 import dbmp as D
+from paper_2602_22625_gb300 import inputs
+from paper_2602_22625_gb300.render import Atlas, Renderer, render
+from _helpers import cuda, grad_close, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def small_scene():
+    sc = inputs.tiny(seed=14, N=10, H=40, W=36)
+    sc.params[:, 2] = np.abs(sc.params[:, 2]) * 0.3
+    return sc
+
+
+def test_autograd_matches_oracle_gradient():
+    cuda()
+    sc = small_scene()
+    rng = np.random.default_rng(2)
+    wI = rng.normal(size=(3, sc.H, sc.W))
+    wA = rng.normal(size=(sc.H, sc.W))
+    r = Renderer(sc.H, sc.W, Atlas(to_dev(sc.atlas)), sc.N, tile=16, background=(0.4, 0.5, 0.6), T_stop=0.0)
+    p = to_dev(sc.params).requires_grad_(True)
+    img, alpha = render(p, to_dev(sc.bitmap_id), r)
+    loss = (img * to_dev(wI.astype(np.float32))).sum() + (alpha * to_dev(wA.astype(np.float32))).sum()
+    loss.backward()
+    ref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, wI, wA, background=(0.4, 0.5, 0.6))
+    grad_close(p.grad.cpu().numpy(), ref, what="autograd vs oracle")
+
+
+def test_autograd_matches_central_finite_differences():
+    """Central differences of the oracle's FP64 forward on the same loss."""
+    cuda()
+    sc = small_scene()
+    rng = np.random.default_rng(3)
+    wI = rng.normal(size=(3, sc.H, sc.W))
+    r = Renderer(sc.H, sc.W, Atlas(to_dev(sc.atlas)), sc.N, tile=8, background=(1, 1, 1), T_stop=0.0)
+    p = to_dev(sc.params).requires_grad_(True)
+    img, _ = render(p, to_dev(sc.bitmap_id), r)
+    (img * to_dev(wI.astype(np.float32))).sum().backward()
+    g = p.grad.cpu().numpy().astype(np.float64)
+
+    def L(params):
+        return float((oracle.render(sc.H, sc.W, params, sc.bitmap_id, sc.atlas)["image"] * wI).sum())
+
+    steps = [2 ** -10, 2 ** -10, 2 ** -10, 2 ** -12, 2 ** -10, 2 ** -10, 2 ** -10, 2 ** -10]
+    fd = np.zeros_like(g)
+    for i in range(sc.N):
+        for j in range(8):
+            pp, pm = sc.params.copy(), sc.params.copy()
+            pp[i, j] += np.float32(steps[j])
+            pm[i, j] -= np.float32(steps[j])
+            fd[i, j] = (L(pp) - L(pm)) / (np.float64(pp[i, j]) - np.float64(pm[i, j]))
+    # bilinear kinks inside the step bound the agreement of a few entries
+    scale = np.abs(fd).max(0)
+    err = np.abs(g - fd) / np.maximum(scale, 1e-12)
+    assert np.median(err) < 1e-3 and err.max() < 2e-2, err
+
+
+def test_autograd_rebins_after_another_forward():
+    cuda()
+    a = small_scene()
+    b = inputs.tiny(seed=15, N=10, H=40, W=36)
+    r = Renderer(a.H, a.W, Atlas(to_dev(a.atlas)), a.N, tile=16, T_stop=0.0)
+    pa = to_dev(a.params).requires_grad_(True)
+    img_a, _ = render(pa, to_dev(a.bitmap_id), r)
+    pb = to_dev(b.params).requires_grad_(True)
+    img_b, _ = render(pb, to_dev(b.bitmap_id), r)   # re-bins the shared workspace
+    wI = np.random.default_rng(5).normal(size=(3, a.H, a.W))
+    (img_a * to_dev(wI.astype(np.float32))).sum().backward()
+    ref = oracle.grad(a.H, a.W, a.params, a.bitmap_id, a.atlas, wI)
+    grad_close(pa.grad.cpu().numpy(), ref, what="rebinned")
+
+
+@pytest.fixture(scope="module")
+def stress():
+    return inputs.stress()
+
+
+def test_stress_workload_dense_tiles_and_localized_fd(stress):
+    """2048^2 canvas, 64 bitmaps, 200k primitives with Pareto(1.5) scales: some
+    tiles list more than 5000 primitives.  Gradients of the autograd render are
+    checked, for sampled small primitives, against central differences of the
+    oracle restricted to the pixels of each primitive's box (a perturbation
+    changes no other pixel)."""
+    cuda()
+    sc = stress
+    r = Renderer(sc.H, sc.W, Atlas(to_dev(sc.atlas)), sc.N, tile=32, background=sc.background, T_stop=1e-6)
+    p = to_dev(sc.params).requires_grad_(True)
+    bid = to_dev(sc.bitmap_id)
+    rng = np.random.default_rng(6)
+    # the smallest primitives (Pareto scales start at 0.015 W = 30.7 px), front layers
+    cand = np.nonzero((np.abs(sc.params[:, 2]) < 34) & (np.arange(sc.N) < 3000))[0]
+    sel = rng.choice(cand, 3, replace=False)
+    # loss weights: random over the union of the selected primitives' boxes
+    wI = np.zeros((3, sc.H, sc.W), np.float32)
+    boxes = []
+    for i in sel:
+        x, y, s = sc.params[i, :3]
+        h = int(abs(s) * 1.5 + 4)
+        x0, x1 = max(int(x) - h, 0), min(int(x) + h, sc.W - 1)
+        y0, y1 = max(int(y) - h, 0), min(int(y) + h, sc.H - 1)
+        boxes.append((x0, x1, y0, y1))
+        wI[:, y0:y1 + 1, x0:x1 + 1] = rng.normal(size=(3, y1 - y0 + 1, x1 - x0 + 1))
+    img, _ = render(p, bid, r)
+    st = r.status()
+    (img * to_dev(wI)).sum().backward()
+    g = p.grad.cpu().numpy().astype(np.float64)
+    # tile density: the longest list has more than 5000 primitives
+    n_tiles = (sc.W // 32) * (sc.H // 32)
+    offs = torch.empty(n_tiles + 1, dtype=torch.int64, device="cuda")
+    lst = torch.empty(1, dtype=torch.int32, device="cuda")
+    D.dbmp_get_tile_lists(r.ws.handle, offs, lst)
+    assert int(torch.diff(offs).max()) > 5000
+    assert st.pairs_required == int(offs[-1])
+
+    def L(params, box):
+        x0, x1, y0, y1 = box
+        ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
+        o = oracle.render(sc.H, sc.W, params, sc.bitmap_id, sc.atlas, background=sc.background, T_stop=1e-6,
+                          pixels=(xs.ravel(), ys.ravel()))["image"]
+        return float((o * wI[:, ys.ravel(), xs.ravel()]).sum())
+
+    # 1) the oracle's FP64 analytic gradient of the same loss (exact up to rounding)
+    ref = oracle.grad_selected(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, wI, sel,
+                               background=sc.background, T_stop=1e-6)
+    grad_close(g[sel], ref, what="stress vs oracle")
+    # 2) central differences of the oracle's forward over each primitive's box.  The
+    # parameters are float32, so the smallest step is a few ulps (2^-12 px for
+    # y ~ 1600); with texels 0.5 px apart a few pixels then cross a bilinear kink
+    # (integer U or V) inside the step, which biases single entries.  So the check
+    # is on the median over the 24 entries, with a loose bound on the worst one.
+    steps = [2 ** -12, 2 ** -12, 2 ** -12, 2 ** -14, 2 ** -12, 2 ** -12, 2 ** -12, 2 ** -12]
+    errs = []
+    for i, box in zip(sel, boxes):
+        fd = np.zeros(8)
+        for j in range(8):
+            pp, pm = sc.params.copy(), sc.params.copy()
+            pp[i, j] += np.float32(steps[j])
+            pm[i, j] -= np.float32(steps[j])
+            fd[j] = (L(pp, box) - L(pm, box)) / (np.float64(pp[i, j]) - np.float64(pm[i, j]))
+        errs.append(np.abs(g[i] - fd) / max(np.abs(fd).max(), 1e-12))
+    errs = np.concatenate(errs)
+    assert np.median(errs) < 1e-3 and errs.max() < 0.5, errs
