@@ -277,6 +277,49 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
                       int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
                       int32_t reps, DbmpTuning *best, float *best_ms, dbmp_stream_t stream);
 
+/* ------------------------------------------------------------------------- */
+/* Forward render without device allocation                                   */
+/* ------------------------------------------------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory.  Examples: a host application or plugin
+ * sandbox that owns a fixed device-memory budget, and real-time loops where
+ * cudaMalloc/cudaFree cannot be afforded because they may synchronise the whole
+ * device and can fail with out-of-memory partway through a long run.
+ *
+ * It renders one canvas exactly like dbmp_bin (tile 16) followed by
+ * dbmp_render_fwd (default tuning), from the plain atlas texels
+ * (float32 [n_bmp][H_b][W_b]), with no DbmpWorkspace and no DbmpAtlas.  All
+ * intermediate state lives in one scratch array compiled into the library
+ * (about 5.1 MB of device memory).  Every GPU that loads the library holds it
+ * until the process exits.  Maximum sizes:
+ *     H, W <= 512;  N <= 4096;  n_bmp (H_b + 1)(W_b + 1) <= 32768;
+ *     tile-list entries (sum_t d_t) <= 1 048 576.
+ * Larger sizes are rejected on the host with DBMP_ERR_INVALID_ARG; exceeding
+ * the tile-list capacity can only be seen on the device (see status_out).
+ *
+ * The caller passes inputs and outputs as for dbmp_bin / dbmp_render_fwd
+ * (params_dev 16-byte aligned; image 3 x H x W, T_final and n_last H x W).
+ * This call calls no cudaMalloc, cudaFree or allocating library routine.  The
+ * first call on each device does a one-time set-up with that device current: it
+ * resolves the scratch array's device address and sets kernel attributes.  Make
+ * that first call before any stream capture.
+ *
+ * All calls share the one scratch array, which keeps the last call's contents.
+ * The call itself clears what must start at zero.  Calls whose GPU work
+ * overlaps (different streams without ordering between them, or several host
+ * threads) race on the array and give wrong results: order them on one stream.
+ *
+ * status_out: NULL -> the call only queues work on `stream` and returns; if the
+ * tile lists exceed the capacity, the outputs are left unwritten.  Non-NULL ->
+ * the call synchronises `stream`, fills *status_out, and returns
+ * DBMP_ERR_CAPACITY if the lists did not fit. */
+int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *params_dev,
+                               const int32_t *bitmap_id_dev, int32_t N, const float *texels_dev,
+                               int32_t n_bmp, int32_t H_b, int32_t W_b, float alpha_max,
+                               const DbmpBackground *bg, float T_stop, float *image_dev,
+                               float *T_final_dev, int32_t *n_last_dev, dbmp_stream_t stream,
+                               DbmpDeviceStatus *status_out);
+
 #ifdef __cplusplus
 }
 #endif

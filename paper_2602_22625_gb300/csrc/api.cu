@@ -41,6 +41,8 @@ bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
 
 }  // namespace
 
+int32_t dbmp::record_error(int32_t code, const char *msg) { return fail(code, "%s", msg); }
+
 struct DbmpAtlas {
     float4 *quad = nullptr;
     int32_t *sat = nullptr;

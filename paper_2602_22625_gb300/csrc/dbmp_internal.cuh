@@ -122,6 +122,9 @@ struct BinBuffers {
     int32_t max_tiles_per_canvas;
 };
 
+// Stores a one-line message for dbmp_last_error() on this thread; returns code.
+int32_t record_error(int32_t code, const char *msg);
+
 // One-time kernel set-up (shared-memory opt-in, occupancy), called at workspace
 // creation so that later launches can be captured in CUDA graphs.
 cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas);

@@ -31,6 +31,7 @@ EXPORTS = (
     "dbmp_atlas_update", "dbmp_workspace_bytes", "dbmp_workspace_create", "dbmp_workspace_destroy",
     "dbmp_status_poll", "dbmp_bin", "dbmp_get_tile_lists", "dbmp_render_fwd", "dbmp_render_bwd",
     "dbmp_mse_grad", "dbmp_adam_step", "dbmp_batch_plan", "dbmp_batch_render", "dbmp_autotune",
+    "dbmp_render_fwd_static",
 )
 
 
@@ -112,6 +113,9 @@ def load(build_if_missing: bool = True):
         "dbmp_autotune": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32, _i32,
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
+        "dbmp_render_fwd_static": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp, _i32, _i32, _i32, _f32,
+                                          ctypes.POINTER(DbmpBackground), _f32, _vp, _vp, _vp, _vp,
+                                          ctypes.POINTER(DbmpDeviceStatus)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -281,3 +285,15 @@ def dbmp_autotune(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, ima
                                 _ptr(dparams), reps, ctypes.byref(best), ctypes.byref(ms),
                                 _stream(stream)))
     return (best.tile, best.batch, best.ppt), ms.value
+
+
+def dbmp_render_fwd_static(H, W, params, bitmap_id, texels, alpha_max, bg, T_stop, image, T_final, n_last,
+                           stream=None, with_status=True):
+    """Forward render from the library's built-in scratch area (no device allocation).
+    Returns the device status when with_status (the call then synchronises)."""
+    st = DbmpDeviceStatus() if with_status else None
+    _check(load().dbmp_render_fwd_static(H, W, _ptr(params), _ptr(bitmap_id), params.shape[0], _ptr(texels),
+                                         texels.shape[0], texels.shape[1], texels.shape[2], alpha_max,
+                                         ctypes.byref(bg), T_stop, _ptr(image), _ptr(T_final), _ptr(n_last),
+                                         _stream(stream), ctypes.byref(st) if st is not None else None))
+    return st
