@@ -278,6 +278,25 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
                       int32_t reps, DbmpTuning *best, float *best_ms, dbmp_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
+/* BF16 tensor-core GEMM (tcgen05, FP32 accumulation), used by the proposal    */
+/* network below and exposed for testing                                      */
+/* ------------------------------------------------------------------------- */
+/* C[m][n] (op)= sum_k A[m][k] B[n][k] for m < M, n < N, k < K.
+ *   A_dev, B_dev  bf16 (raw 16-bit), row-major M x K and N x K (K contiguous),
+ *                 16-byte aligned, lda and ldb multiples of 8, K a multiple of 64
+ *   mode 0: Cf[m][n] = acc            (float32, row stride ldc)
+ *   mode 1: Cf[m][n] += acc           (float32 atomics; allows split_k > 1)
+ *   mode 2: Cb[m][n] = bf16(max(acc + bias[n], 0))   (bf16, row stride ldc)
+ *   mode 3: Cf[m][n] = acc + bias[n]
+ *   split_k  number of CTAs sharing the K range of a tile (mode 1 only if > 1)
+ *   status_dev  optional device int32 set to DBMP_ERR_TIMEOUT if a bounded
+ *               wait on the tensor-core pipeline gave up (nullable) */
+int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev, int32_t ldb,
+                       int32_t M, int32_t N, int32_t K, int32_t mode, float *Cf_dev,
+                       uint16_t *Cb_dev, int32_t ldc, const float *bias_dev, int32_t split_k,
+                       int32_t *status_dev, dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
 /* Forward render without device allocation                                   */
 /* ------------------------------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers that

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "dbmp_internal.cuh"
@@ -626,6 +627,27 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     *best = bt;
     if (best_ms) *best_ms = best_t;
     return dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &bt, stream);
+}
+
+int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev, int32_t ldb, int32_t M,
+                       int32_t N, int32_t K, int32_t mode, float *Cf_dev, uint16_t *Cb_dev, int32_t ldc,
+                       const float *bias_dev, int32_t split_k, int32_t *status_dev, dbmp_stream_t stream) {
+    if (!A_dev || !B_dev) return fail(DBMP_ERR_INVALID_ARG, "A / B is NULL");
+    if (M < 1 || N < 1 || K < 64 || K % 64) return fail(DBMP_ERR_INVALID_ARG, "need M, N >= 1 and K a multiple of 64");
+    if (lda < K || ldb < K || (lda & 7) || (ldb & 7) || (((uintptr_t)A_dev) & 15) || (((uintptr_t)B_dev) & 15))
+        return fail(DBMP_ERR_INVALID_ARG, "A / B rows must be 16-byte aligned with lda, ldb >= K, multiples of 8");
+    if (mode < 0 || mode > 3) return fail(DBMP_ERR_INVALID_ARG, "mode must be 0..3");
+    if (ldc < N) return fail(DBMP_ERR_INVALID_ARG, "ldc < N");
+    if ((mode == 2 && !Cb_dev) || (mode != 2 && !Cf_dev)) return fail(DBMP_ERR_INVALID_ARG, "output is NULL");
+    if ((mode == 2 || mode == 3) && !bias_dev) return fail(DBMP_ERR_INVALID_ARG, "bias is NULL");
+    if (split_k < 1 || (split_k > 1 && mode != 1)) return fail(DBMP_ERR_INVALID_ARG, "split_k > 1 needs mode 1");
+    static std::once_flag once;
+    static cudaError_t init_err = cudaSuccess;
+    std::call_once(once, [] { init_err = init_gemm_kernels(); });
+    DBMP_CUDA(init_err, "gemm set-up");
+    GemmArgs g{A_dev, B_dev, M, N, K, lda, ldb, ldc, mode, Cf_dev, Cb_dev, bias_dev, status_dev};
+    DBMP_CUDA(launch_gemm(g, split_k, (cudaStream_t)stream), "gemm launch");
+    return DBMP_OK;
 }
 
 }  // extern "C"

@@ -168,4 +168,25 @@ cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, 
 cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32_t *step,
                         const DbmpAdamConfig &cfg, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM (gemm_tc.cu): C[m][n] (op)= sum_k A[m][k] B[n][k], BF16 in, FP32
+// accumulation.  A, B are raw bf16 bits, K-contiguous, 16-byte aligned rows
+// (lda, ldb multiples of 8), K a multiple of 64.
+// ---------------------------------------------------------------------------
+enum GemmMode { GEMM_STORE_F32 = 0, GEMM_ATOMIC_F32 = 1, GEMM_BIAS_RELU_BF16 = 2, GEMM_BIAS_F32 = 3 };
+
+struct GemmArgs {
+    const uint16_t *A;
+    const uint16_t *B;
+    int32_t M, N, K, lda, ldb, ldc;
+    int32_t mode;
+    float *Cf;          // GEMM_STORE_F32, GEMM_ATOMIC_F32, GEMM_BIAS_F32
+    uint16_t *Cb;       // GEMM_BIAS_RELU_BF16
+    const float *bias;  // [N] for the bias modes
+    int32_t *status;    // set to DBMP_ERR_TIMEOUT if a bounded wait gives up (may be null)
+};
+
+cudaError_t init_gemm_kernels();
+cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st);
+
 }  // namespace dbmp
