@@ -206,3 +206,71 @@ def batched(seed: int = 4, n_canvas: int = 64, side=(256, 1024), nprim=(1000, 50
         p, b = primitives(seed * 100003 + c, N, S, S, atlas.shape[0], "lognormal", (-2.0, 0.7))
         scenes.append(Scene(f"batch{c}_{S}sq_{N}", S, S, p, b, atlas))
     return scenes
+
+
+# ---------------------------------------------------------------------------
+# Anchored scenes for the learned proposal network
+# ---------------------------------------------------------------------------
+#: anchored scene geometry: 8 x 8 cells of 32 px on a 256^2 canvas, 8 slots per cell;
+#: slot k sits in sub-cell (k % 4, k // 4) of 8 x 16 px; primitive index
+#: (cy * 8 + cx) * 8 + k (cells in raster order, slots in order, index 0 in front)
+ANCHOR_CANVAS, ANCHOR_CELLS, ANCHOR_SLOTS = 256, 8, 8
+ANCHOR_SCALE = (6.0, 14.0)       # half-extent in pixels
+ANCHOR_OPACITY = (0.5, 1.0)
+
+
+def anchored(seed: int, B: int = 1) -> np.ndarray:
+    """B scenes of 512 soft-disc primitives placed by the anchored generator:
+    x = cell_x + sub_x + U[0, 8), y = cell_y + sub_y + U[0, 16), s ~ U[6, 14] px,
+    theta ~ U[0, 2 pi), opacity ~ U[0.5, 1], RGB ~ U[0, 1] (stored as logits).
+    Returns float32 (B, 512, 8)."""
+    g = rng(seed)
+    C, S = ANCHOR_CELLS, ANCHOR_SLOTS
+    cell = ANCHOR_CANVAS // C
+    idx = np.arange(C * C * S)
+    cy, cx, k = idx // (C * S), (idx // S) % C, idx % S
+    base_x = cx * cell + (k % 4) * 8
+    base_y = cy * cell + (k // 4) * 16
+    p = np.empty((B, C * C * S, 8), np.float64)
+    p[..., 0] = base_x[None] + g.uniform(0.0, 8.0, (B, C * C * S))
+    p[..., 1] = base_y[None] + g.uniform(0.0, 16.0, (B, C * C * S))
+    p[..., 2] = g.uniform(ANCHOR_SCALE[0], ANCHOR_SCALE[1], (B, C * C * S))
+    p[..., 3] = g.uniform(0.0, 2.0 * math.pi, (B, C * C * S))
+    p[..., 4] = _logit(g.uniform(ANCHOR_OPACITY[0], ANCHOR_OPACITY[1], (B, C * C * S)))
+    p[..., 5:8] = _logit(g.uniform(0.0, 1.0, (B, C * C * S, 3)))
+    return p.astype(np.float32)
+
+
+def random_init(seed: int, B: int = 1, N: int = 512, H: int = 256, W: int = 256) -> np.ndarray:
+    """The plain method's random initialisation for the same scenes: positions
+    uniform over the canvas, scales, opacities and colours from the same ranges."""
+    g = rng(seed)
+    p = np.empty((B, N, 8), np.float64)
+    p[..., 0] = g.uniform(0.0, W, (B, N))
+    p[..., 1] = g.uniform(0.0, H, (B, N))
+    p[..., 2] = g.uniform(ANCHOR_SCALE[0], ANCHOR_SCALE[1], (B, N))
+    p[..., 3] = g.uniform(0.0, 2.0 * math.pi, (B, N))
+    p[..., 4] = _logit(g.uniform(ANCHOR_OPACITY[0], ANCHOR_OPACITY[1], (B, N)))
+    p[..., 5:8] = _logit(g.uniform(0.0, 1.0, (B, N, 3)))
+    return p.astype(np.float32)
+
+
+def cnn_init(seed: int = 0) -> np.ndarray:
+    """He-normal initial weights (zero biases) of the proposal network, flattened in
+    the library's parameter order: for each layer, W (Cout x K row-major), then b."""
+    g = rng(seed)
+    chunks = []
+    for cin_pad, cin_real, cout, ksz in CNN_LAYERS:
+        K = ksz * ksz * cin_pad
+        w = g.normal(0.0, math.sqrt(2.0 / (ksz * ksz * cin_real)), (cout, ksz * ksz, cin_pad))
+        w[:, :, cin_real:] = 0.0
+        if cout == CNN_LAYERS[-1][2]:
+            w *= 0.1  # small head: initial proposals near the anchors' centres
+        chunks += [w.reshape(cout, K).ravel(), np.zeros(cout)]
+    return np.concatenate(chunks).astype(np.float32)
+
+
+#: (input channels padded, input channels used, output channels, kernel size):
+#: five 4x4 stride-2 convolutions with ReLU, then a 1x1 head (8 slots x 8 outputs)
+CNN_LAYERS = ((8, 3, 32, 4), (32, 32, 64, 4), (64, 64, 128, 4), (128, 128, 256, 4),
+              (256, 256, 256, 4), (256, 256, 64, 1))
