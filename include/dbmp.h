@@ -297,6 +297,57 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
                        int32_t *status_dev, dbmp_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
+/* Learned proposal network                                                   */
+/* ------------------------------------------------------------------------- */
+/* A small CNN that maps a target image to initial parameters of 512 primitives,
+ * to be refined by the plain optimisation (Eqs. 1-5 + Adam).  The paper names
+ * learned (autoregressive / RL) initialisation as future work (Sec. S5) and
+ * shows that initialisation matters (Sec. 3.2.2); the network here is this
+ * library's own design:
+ *   input   256 x 256 RGB in [0, 1] -> bf16 NHWC, 2 (I - 0.5), channels padded to 8
+ *   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 8 -> 32 -> 64 -> 128 -> 256 -> 256
+ *   head    1x1 conv 256 -> 64 on the 8 x 8 map = 8 slots x 8 outputs per cell
+ *   decode  cell (cy, cx), slot k, outputs o: x = 32 cx + 8 (k % 4) + 8 s(o0),
+ *           y = 32 cy + 16 (k / 4) + 16 s(o1), s = 6 + 8 s(o2), theta = 0,
+ *           nu = o4, c = (o5, o6, o7); primitive index (8 cy + cx) 8 + k
+ *   loss    mean squared error of the raw outputs against the targets of the
+ *           anchored parameterisation (logit of the clipped in-cell offset and
+ *           scale, nu and c clipped to [-6, 6]; theta not learned)
+ * All products run on the tcgen05 tensor cores (BF16 operands, FP32
+ * accumulation); weights are FP32 masters with BF16 copies.  Parameters are one
+ * flat float32 vector: for each layer, W (Cout x K, K ordered (ky, kx, ci)) then
+ * b (Cout).  A proposer owns its buffers for batches of up to max_batch images.
+ * images_dev: B x 3 x 256 x 256 float32 planar (the concatenated per-canvas
+ * images dbmp_batch_render writes for 256 x 256 canvases). */
+typedef struct DbmpProposer DbmpProposer;
+
+typedef struct {
+    float lr, beta1, beta2, eps;
+} DbmpProposerAdam;
+
+int64_t dbmp_proposer_num_params(void);
+/* Allocates (synchronises the device). */
+int32_t dbmp_proposer_create(int32_t max_batch, DbmpProposer **out);
+int32_t dbmp_proposer_destroy(DbmpProposer *p);
+/* Uploads host float32 parameters (n = dbmp_proposer_num_params()), resets Adam.
+ * Synchronous. */
+int32_t dbmp_proposer_set_params(DbmpProposer *p, const float *host, int64_t n);
+/* Downloads the parameters (which = 0) or the last gradient (which = 1);
+ * synchronises the device; DBMP_ERR_TIMEOUT if a tensor-core wait gave up. */
+int32_t dbmp_proposer_get(DbmpProposer *p, int32_t which, float *host, int64_t n);
+/* Decoded proposals: params_out_dev float32 B x 512 x 8 (same layout as dbmp_bin's
+ * params, primitive order as above).  Stream-ordered. */
+int32_t dbmp_propose(DbmpProposer *p, const float *images_dev, int32_t B, float *params_out_dev,
+                     dbmp_stream_t stream);
+/* One training step on (image, target parameters) pairs: forward, loss
+ * (loss_dev: device double, overwritten), gradient of every parameter, and, if
+ * adam is not NULL, one Adam step on the FP32 masters.  target_params_dev:
+ * B x 512 x 8 float32.  Stream-ordered. */
+int32_t dbmp_proposer_train_step(DbmpProposer *p, const float *images_dev, const float *target_params_dev,
+                                 int32_t B, const DbmpProposerAdam *adam, double *loss_dev,
+                                 dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
 /* Forward render without device allocation                                   */
 /* ------------------------------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers that

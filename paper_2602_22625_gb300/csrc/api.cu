@@ -650,4 +650,90 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
     return DBMP_OK;
 }
 
+struct DbmpProposer {
+    CnnBuffers c;
+    int32_t step = 0;
+};
+
+int64_t dbmp_proposer_num_params(void) { return cnn_num_params(); }
+
+int32_t dbmp_proposer_create(int32_t max_batch, DbmpProposer **out) {
+    if (!out) return fail(DBMP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_batch < 1) return fail(DBMP_ERR_INVALID_ARG, "max_batch must be >= 1");
+    DbmpProposer *p = new DbmpProposer;
+    cudaError_t e = cnn_alloc(p->c, max_batch);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cnn_free(p->c);
+        delete p;
+        return fail(DBMP_ERR_NO_MEMORY, "proposer allocation (%zu bytes): %s", cnn_bytes(max_batch),
+                    cudaGetErrorString(e));
+    }
+    *out = p;
+    return DBMP_OK;
+}
+
+int32_t dbmp_proposer_destroy(DbmpProposer *p) {
+    if (!p) return DBMP_OK;
+    cudaDeviceSynchronize();
+    cnn_free(p->c);
+    delete p;
+    return DBMP_OK;
+}
+
+int32_t dbmp_proposer_set_params(DbmpProposer *p, const float *host, int64_t n) {
+    if (!p || !host) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    const int64_t np = cnn_num_params();
+    if (n != np) return fail(DBMP_ERR_INVALID_ARG, "expected %lld parameters, got %lld", (long long)np, (long long)n);
+    DBMP_CUDA(cudaMemcpy(p->c.theta, host, sizeof(float) * np, cudaMemcpyHostToDevice), "params upload");
+    DBMP_CUDA(cudaMemset(p->c.m, 0, sizeof(float) * np), "adam reset");
+    DBMP_CUDA(cudaMemset(p->c.v, 0, sizeof(float) * np), "adam reset");
+    DBMP_CUDA(cnn_sync_weights(p->c, 0), "bf16 copies");
+    DBMP_CUDA(cudaDeviceSynchronize(), "params sync");
+    p->step = 0;
+    return DBMP_OK;
+}
+
+int32_t dbmp_proposer_get(DbmpProposer *p, int32_t which, float *host, int64_t n) {
+    if (!p || !host) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    const int64_t np = cnn_num_params();
+    if (n != np) return fail(DBMP_ERR_INVALID_ARG, "expected %lld values, got %lld", (long long)np, (long long)n);
+    if (which != 0 && which != 1) return fail(DBMP_ERR_INVALID_ARG, "which must be 0 (params) or 1 (grads)");
+    DBMP_CUDA(cudaDeviceSynchronize(), "sync");
+    DBMP_CUDA(cudaMemcpy(host, which == 0 ? p->c.theta : p->c.grad, sizeof(float) * np, cudaMemcpyDeviceToHost),
+              "download");
+    int32_t st = 0;
+    DBMP_CUDA(cudaMemcpy(&st, p->c.status, sizeof st, cudaMemcpyDeviceToHost), "status");
+    if (st) return fail(st, "a tensor-core wait gave up");
+    return DBMP_OK;
+}
+
+int32_t dbmp_propose(DbmpProposer *p, const float *images_dev, int32_t B, float *params_out_dev,
+                     dbmp_stream_t stream) {
+    if (!p || !images_dev || !params_out_dev) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (B < 1 || B > p->c.max_batch) return fail(DBMP_ERR_INVALID_ARG, "B = %d outside 1..%d", B, p->c.max_batch);
+    cudaStream_t st = (cudaStream_t)stream;
+    DBMP_CUDA(cnn_forward(p->c, images_dev, B, st), "proposer forward");
+    DBMP_CUDA(cnn_decode(p->c, B, params_out_dev, st), "proposer decode");
+    return DBMP_OK;
+}
+
+int32_t dbmp_proposer_train_step(DbmpProposer *p, const float *images_dev, const float *target_params_dev,
+                                 int32_t B, const DbmpProposerAdam *adam, double *loss_dev, dbmp_stream_t stream) {
+    if (!p || !images_dev || !target_params_dev || !loss_dev) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (B < 1 || B > p->c.max_batch) return fail(DBMP_ERR_INVALID_ARG, "B = %d outside 1..%d", B, p->c.max_batch);
+    if (adam && !(adam->lr >= 0 && adam->beta1 >= 0 && adam->beta1 < 1 && adam->beta2 >= 0 && adam->beta2 < 1 &&
+                  adam->eps > 0))
+        return fail(DBMP_ERR_INVALID_ARG, "bad Adam settings");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBMP_CUDA(cnn_forward(p->c, images_dev, B, st), "proposer forward");
+    DBMP_CUDA(cnn_backward(p->c, target_params_dev, B, loss_dev, st), "proposer backward");
+    if (adam) {
+        p->step += 1;
+        DBMP_CUDA(cnn_adam(p->c, adam->lr, adam->beta1, adam->beta2, adam->eps, p->step, st), "proposer adam");
+    }
+    return DBMP_OK;
+}
+
 }  // extern "C"

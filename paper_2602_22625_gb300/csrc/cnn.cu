@@ -1,0 +1,436 @@
+// The learned proposal network: a small CNN that maps a 256 x 256 target image to
+// initial parameters of 512 primitives, refined afterwards by the plain gradient
+// optimisation.  (The paper leaves learned initialisation to future work, Sec. S5,
+// and shows that initialisation matters, Sec. 3.2.2.)
+//
+//   input   B x 256 x 256 x 8 bf16 (NHWC; channels 0-2 = 2 (I - 0.5), 3-7 = 0)
+//   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 8 -> 32 -> 64 -> 128 -> 256 -> 256
+//   head    1x1 conv 256 -> 64 on the 8 x 8 map: 8 slots x 8 outputs per cell
+//
+// Every product is the tcgen05 GEMM of gemm_tc.cu (BF16 operands, FP32 accumulation):
+//   forward  X_l = relu(im2col(X_{l-1}) W_l^T + b_l)   (bias + ReLU fused, bf16 out)
+//   wgrad    dW_l = dZ_l^T im2col(X_{l-1})               (operands transposed to K-major,
+//                                                          split-K with fp32 atomics)
+//   dgrad    dX_{l-1} = col2im(dZ_l W_l) masked by X_{l-1} > 0
+// Weights are FP32 masters with BF16 copies; Adam updates the masters.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dbmp_internal.cuh"
+
+namespace dbmp {
+
+namespace {
+
+__device__ __forceinline__ uint16_t f2bf(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf2f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+
+__global__ void k_pack_input(const float *__restrict__ img, int32_t B, uint16_t *__restrict__ X0) {
+    const int64_t n = (int64_t)B * 65536;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i >> 16, pix = i & 65535;
+        const float *I = img + b * 3 * 65536 + pix;
+        __align__(16) uint16_t h[8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[c] = f2bf(2.0f * (I[c * 65536] - 0.5f));
+#pragma unroll
+        for (int c = 3; c < 8; ++c) h[c] = 0;
+        reinterpret_cast<uint4 *>(X0)[i] = *reinterpret_cast<const uint4 *>(h);
+    }
+}
+
+// col[m][(ky*4 + kx)*C + c] = X[b][2oy-1+ky][2ox-1+kx][c] (0 outside), m = (b, oy, ox);
+// one 16-byte chunk (8 channels) per thread.
+__global__ void k_im2col(const uint16_t *__restrict__ X, int32_t B, int32_t H, int32_t W, int32_t C,
+                         uint16_t *__restrict__ col) {
+    const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+    const int64_t n = (int64_t)B * Ho * Wo * 16 * C8;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        const int64_t r = i / C8;
+        const int kk = (int)(r % 16);
+        const int64_t m = r / 16;
+        const int ox = (int)(m % Wo), oy = (int)((m / Wo) % Ho);
+        const int64_t b = m / ((int64_t)Wo * Ho);
+        const int y = 2 * oy - 1 + kk / 4, x = 2 * ox - 1 + kk % 4;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (y >= 0 && y < H && x >= 0 && x < W)
+            v = reinterpret_cast<const uint4 *>(X + ((b * H + y) * W + x) * C)[c8];
+        reinterpret_cast<uint4 *>(col)[i] = v;
+    }
+}
+
+// dX[b][y][x][c] = sum over (ky, kx) with 2oy-1+ky = y, 2ox-1+kx = x of
+// dcol[(b,oy,ox)][(ky*4+kx)*C + c]; then dZ = X > 0 ? bf16(dX) : 0.
+__global__ void k_col2im_mask(const float *__restrict__ dcol, const uint16_t *__restrict__ X, int32_t B,
+                              int32_t H, int32_t W, int32_t C, uint16_t *__restrict__ dZ) {
+    const int Ho = H / 2, Wo = W / 2;
+    const int64_t n = (int64_t)B * H * W * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t p = i / C;
+        const int x = (int)(p % W), y = (int)((p / W) % H);
+        const int64_t b = p / ((int64_t)W * H);
+        float acc = 0.0f;
+        // ky = y + 1 - 2 oy in [0, 4): two candidates of matching parity
+        for (int ky = (y + 1) & 1; ky < 4; ky += 2) {
+            const int oy = (y + 1 - ky) / 2;
+            if (oy < 0 || oy >= Ho) continue;
+            for (int kx = (x + 1) & 1; kx < 4; kx += 2) {
+                const int ox = (x + 1 - kx) / 2;
+                if (ox < 0 || ox >= Wo) continue;
+                acc += dcol[((b * Ho + oy) * Wo + ox) * (16 * (int64_t)C) + (ky * 4 + kx) * C + c];
+            }
+        }
+        dZ[i] = bf2f(X[i]) > 0.0f ? f2bf(acc) : (uint16_t)0;
+    }
+}
+
+__global__ void k_transpose(const uint16_t *__restrict__ in, int32_t R, int32_t C, uint16_t *__restrict__ out) {
+    __shared__ uint16_t t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[k][threadIdx.x] = in[(int64_t)r * C + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < C && r < R) out[(int64_t)c * R + r] = t[threadIdx.x][k];
+    }
+}
+
+// out[n] += sum_m in[m][n] (in: bf16 or fp32); out must be zeroed by the caller.
+template <typename T>
+__global__ void k_colsum(const T *__restrict__ in, int32_t M, int32_t N, float *__restrict__ out) {
+    __shared__ float part[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    float acc = 0.0f;
+    if (n < N)
+        for (int m = blockIdx.y * 8 + threadIdx.y; m < M; m += gridDim.y * 8) {
+            if constexpr (sizeof(T) == 2)
+                acc += bf2f(in[(int64_t)m * N + n]);
+            else
+                acc += in[(int64_t)m * N + n];
+        }
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float s = 0.0f;
+        for (int k = 0; k < 8; ++k) s += part[k][threadIdx.x];
+        atomicAdd(out + n, s);
+    }
+}
+
+__global__ void k_mask_to_bf16(const float *__restrict__ dX, const uint16_t *__restrict__ X, int64_t n,
+                               uint16_t *__restrict__ dZ) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dZ[i] = bf2f(X[i]) > 0.0f ? f2bf(dX[i]) : (uint16_t)0;
+}
+
+__global__ void k_to_bf16(const float *__restrict__ in, int64_t n, uint16_t *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = f2bf(in[i]);
+}
+
+__device__ __forceinline__ float logit_clip(float p) {
+    p = fminf(fmaxf(p, 0.02f), 0.98f);
+    return logf(p / (1.0f - p));
+}
+
+// Anchored decoding of the head outputs: cell (cy, cx) = row m % 64 of scene m / 64,
+// slot k = column / 8.  Loss over the raw outputs (see k_head_decode for the map).
+__global__ void k_head_loss(const float *__restrict__ O, const float *__restrict__ tp, int32_t B,
+                            float *__restrict__ dO, double *loss) {
+    __shared__ double red[8];
+    const int64_t n = (int64_t)B * 512 * 8;
+    const double inv = 1.0 / ((double)B * 512.0 * 7.0);
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i & 7);
+        const int64_t bp = i >> 3;
+        const int p = (int)(bp & 511);
+        const int64_t b = bp >> 9;
+        const int cell = p >> 3, k = p & 7;
+        const int cy = cell >> 3, cx = cell & 7;
+        const int64_t oi = (b * 64 + cell) * 64 + k * 8 + j;
+        const float *q = tp + bp * 8;
+        float t = 0.0f, w = 1.0f;
+        if (j == 0) t = logit_clip((q[0] - (float)(cx * 32 + (k & 3) * 8)) / 8.0f);
+        else if (j == 1) t = logit_clip((q[1] - (float)(cy * 32 + (k >> 2) * 16)) / 16.0f);
+        else if (j == 2) t = logit_clip((q[2] - 6.0f) / 8.0f);
+        else if (j == 3) w = 0.0f;
+        else t = fminf(fmaxf(q[j], -6.0f), 6.0f);
+        const float d = (O[oi] - t) * w;
+        dO[oi] = (float)(2.0 * (double)d * inv);
+        acc += (double)d * (double)d * inv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(loss, s);
+    }
+}
+
+// params[b][p] = (cx*32 + (k%4)*8 + 8 s(o0), cy*32 + (k/4)*16 + 16 s(o1), 6 + 8 s(o2), 0, o4, o5, o6, o7)
+__global__ void k_head_decode(const float *__restrict__ O, int32_t B, float *__restrict__ params) {
+    const int64_t n = (int64_t)B * 512;
+    for (int64_t bp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; bp < n; bp += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(bp & 511);
+        const int64_t b = bp >> 9;
+        const int cell = p >> 3, k = p & 7;
+        const int cy = cell >> 3, cx = cell & 7;
+        const float *o = O + (b * 64 + cell) * 64 + k * 8;
+        float *out = params + bp * 8;
+        out[0] = (float)(cx * 32 + (k & 3) * 8) + 8.0f / (1.0f + expf(-o[0]));
+        out[1] = (float)(cy * 32 + (k >> 2) * 16) + 16.0f / (1.0f + expf(-o[1]));
+        out[2] = 6.0f + 8.0f / (1.0f + expf(-o[2]));
+        out[3] = 0.0f;
+        out[4] = o[4];
+        out[5] = o[5];
+        out[6] = o[6];
+        out[7] = o[7];
+    }
+}
+
+__global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, int32_t t,
+                            uint16_t *__restrict__ pbf) {
+    const float bc1 = 1.0f - powf(b1, (float)t), bc2 = 1.0f - powf(b2, (float)t);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        p[i] = pi;
+        pbf[i] = f2bf(pi);
+    }
+}
+
+int grid1d(int64_t n, int threads = 256) {
+    const int64_t g = (n + threads - 1) / threads;
+    return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Layer table
+// ---------------------------------------------------------------------------
+struct CnnLayer {
+    int cin, cout, k, hin;   // padded input channels, output channels, kernel, input side
+    int64_t K, w_off, b_off;
+};
+
+static void layer_table(CnnLayer L[6], int64_t *n_params) {
+    const int cin[6] = {8, 32, 64, 128, 256, 256}, cout[6] = {32, 64, 128, 256, 256, 64};
+    const int ks[6] = {4, 4, 4, 4, 4, 1}, hin[6] = {256, 128, 64, 32, 16, 8};
+    int64_t o = 0;
+    for (int l = 0; l < 6; ++l) {
+        L[l].cin = cin[l];
+        L[l].cout = cout[l];
+        L[l].k = ks[l];
+        L[l].hin = hin[l];
+        L[l].K = (int64_t)ks[l] * ks[l] * cin[l];
+        L[l].w_off = o;
+        o += L[l].K * cout[l];
+        L[l].b_off = o;
+        o += cout[l];
+    }
+    *n_params = o;
+}
+
+int64_t cnn_num_params() {
+    CnnLayer L[6];
+    int64_t n;
+    layer_table(L, &n);
+    return n;
+}
+
+// sizes in elements for a given max batch
+struct CnnSizes {
+    int64_t X[6], col, dx, dz;
+};
+
+static CnnSizes cnn_sizes(int32_t B) {
+    CnnLayer L[6];
+    int64_t np;
+    layer_table(L, &np);
+    CnnSizes s{};
+    s.X[0] = (int64_t)B * 256 * 256 * 8;
+    for (int l = 0; l < 5; ++l) s.X[l + 1] = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2) * L[l].cout;
+    s.col = 0;
+    s.dx = (int64_t)B * 64 * 256;
+    s.dz = (int64_t)B * 64 * 64;
+    for (int l = 0; l < 5; ++l) {
+        const int64_t M = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2);
+        s.col = s.col > M * L[l].K ? s.col : M * L[l].K;
+        if (l > 0) s.dx = s.dx > M * L[l].K ? s.dx : M * L[l].K;
+        s.dz = s.dz > M * L[l].cout ? s.dz : M * L[l].cout;
+    }
+    return s;
+}
+
+size_t cnn_bytes(int32_t B) {
+    const CnnSizes s = cnn_sizes(B);
+    int64_t np = cnn_num_params();
+    size_t b = 4 * sizeof(float) * np + 2 * sizeof(uint16_t) * np;
+    for (int l = 0; l < 6; ++l) b += sizeof(uint16_t) * s.X[l];
+    b += 2 * sizeof(float) * (size_t)B * 64 * 64 + sizeof(float) * s.dx;
+    b += 2 * sizeof(uint16_t) * s.col + 3 * sizeof(uint16_t) * s.dz + sizeof(int32_t) * 4;
+    return b;
+}
+
+cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
+    const CnnSizes s = cnn_sizes(B);
+    const int64_t np = cnn_num_params();
+    c = CnnBuffers{};
+    c.max_batch = B;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **p, size_t n) {
+        if (e == cudaSuccess) e = cudaMalloc(p, n > 0 ? n : 16);
+    };
+    A((void **)&c.theta, sizeof(float) * np);
+    A((void **)&c.grad, sizeof(float) * np);
+    A((void **)&c.m, sizeof(float) * np);
+    A((void **)&c.v, sizeof(float) * np);
+    A((void **)&c.wbf, sizeof(uint16_t) * np);
+    A((void **)&c.wT, sizeof(uint16_t) * np);
+    for (int l = 0; l < 6; ++l) A((void **)&c.X[l], sizeof(uint16_t) * s.X[l]);
+    A((void **)&c.O, sizeof(float) * B * 64 * 64);
+    A((void **)&c.dO, sizeof(float) * B * 64 * 64);
+    A((void **)&c.dx, sizeof(float) * s.dx);
+    A((void **)&c.col, sizeof(uint16_t) * s.col);
+    A((void **)&c.colT, sizeof(uint16_t) * s.col);
+    A((void **)&c.dz, sizeof(uint16_t) * s.dz);
+    A((void **)&c.dzT, sizeof(uint16_t) * s.dz);
+    A((void **)&c.dzp, sizeof(uint16_t) * s.dz);
+    A((void **)&c.status, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c.status, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c.m, 0, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMemset(c.v, 0, sizeof(float) * np);
+    if (e == cudaSuccess) e = init_gemm_kernels();
+    return e;
+}
+
+void cnn_free(CnnBuffers &c) {
+    void *ps[] = {c.theta, c.grad, c.m, c.v, c.wbf, c.wT, c.X[0], c.X[1], c.X[2], c.X[3], c.X[4], c.X[5],
+                  c.O, c.dO, c.dx, c.col, c.colT, c.dz, c.dzT, c.dzp, c.status};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    c = CnnBuffers{};
+}
+
+// After new master weights: bf16 copies for the products.
+cudaError_t cnn_sync_weights(CnnBuffers &c, cudaStream_t st) {
+    const int64_t np = cnn_num_params();
+    k_to_bf16<<<grid1d(np), 256, 0, st>>>(c.theta, np, c.wbf);
+    return cudaGetLastError();
+}
+
+static cudaError_t gemm(const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N, int K, int mode,
+                        float *Cf, uint16_t *Cb, int ldc, const float *bias, int split, int32_t *status,
+                        cudaStream_t st) {
+    GemmArgs g{A, B, M, N, K, lda, ldb, ldc, mode, Cf, Cb, bias, status};
+    return launch_gemm(g, split, st);
+}
+
+static void transpose(const uint16_t *in, int R, int C, uint16_t *out, cudaStream_t st) {
+    dim3 grid((C + 31) / 32, (R + 31) / 32);
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, R, C, out);
+}
+
+// Forward of B images (fp32, 3 x 256 x 256 each, concatenated) into c.O.
+cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStream_t st) {
+    CnnLayer L[6];
+    int64_t np;
+    layer_table(L, &np);
+    k_pack_input<<<grid1d((int64_t)B * 65536), 256, 0, st>>>(images, B, c.X[0]);
+    cudaError_t e = cudaGetLastError();
+    for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
+        const int H = L[l].hin, Ho = H / 2;
+        const int M = B * Ho * Ho;
+        k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, H, H, L[l].cin, c.col);
+        e = gemm(c.col, (int)L[l].K, c.wbf + L[l].w_off, (int)L[l].K, M, L[l].cout, (int)L[l].K,
+                 GEMM_BIAS_RELU_BF16, nullptr, c.X[l + 1], L[l].cout, c.theta + L[l].b_off, 1, c.status, st);
+    }
+    if (e == cudaSuccess)
+        e = gemm(c.X[5], 256, c.wbf + L[5].w_off, 256, B * 64, 64, 256, GEMM_BIAS_F32, c.O, nullptr, 64,
+                 c.theta + L[5].b_off, 1, c.status, st);
+    return e;
+}
+
+cudaError_t cnn_decode(CnnBuffers &c, int32_t B, float *params, cudaStream_t st) {
+    k_head_decode<<<grid1d((int64_t)B * 512), 256, 0, st>>>(c.O, B, params);
+    return cudaGetLastError();
+}
+
+static int split_for(int M, int N, int K) {
+    const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
+    int s = (2 * 152 + tiles - 1) / tiles;
+    const int kt = K / 64;
+    if (s > kt / 2) s = kt / 2 > 0 ? kt / 2 : 1;
+    return s < 1 ? 1 : s;
+}
+
+// Loss and gradient w.r.t. all parameters into c.grad (overwritten).
+cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, double *loss, cudaStream_t st) {
+    CnnLayer L[6];
+    int64_t np;
+    layer_table(L, &np);
+    cudaMemsetAsync(loss, 0, sizeof(double), st);
+    cudaMemsetAsync(c.grad, 0, sizeof(float) * np, st);
+    const int M6 = B * 64;
+    k_head_loss<<<grid1d((int64_t)B * 4096), 256, 0, st>>>(c.O, target_params, B, c.dO, loss);
+    k_to_bf16<<<grid1d((int64_t)M6 * 64), 256, 0, st>>>(c.dO, (int64_t)M6 * 64, c.dz);
+    // head: wgrad, bias, dgrad
+    transpose(c.dz, M6, 64, c.dzT, st);
+    transpose(c.X[5], M6, 256, c.colT, st);
+    cudaError_t e = gemm(c.dzT, M6, c.colT, M6, 64, 256, M6, GEMM_ATOMIC_F32, c.grad + L[5].w_off, nullptr, 256,
+                         nullptr, split_for(64, 256, M6), c.status, st);
+    k_colsum<float><<<dim3(2, 64), dim3(32, 8), 0, st>>>(c.dO, M6, 64, c.grad + L[5].b_off);
+    transpose(c.wbf + L[5].w_off, 64, 256, c.wT + L[5].w_off, st);
+    if (e == cudaSuccess)
+        e = gemm(c.dz, 64, c.wT + L[5].w_off, 64, M6, 256, 64, GEMM_STORE_F32, c.dx, nullptr, 256, nullptr, 1,
+                 c.status, st);
+    k_mask_to_bf16<<<grid1d((int64_t)M6 * 256), 256, 0, st>>>(c.dx, c.X[5], (int64_t)M6 * 256, c.dz);
+    for (int l = 4; l >= 0 && e == cudaSuccess; --l) {
+        const int H = L[l].hin, Ho = H / 2, M = B * Ho * Ho;
+        const int K = (int)L[l].K, Co = L[l].cout;
+        k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, H, H, L[l].cin, c.col);
+        transpose(c.dz, M, Co, c.dzT, st);
+        transpose(c.col, M, K, c.colT, st);
+        e = gemm(c.dzT, M, c.colT, M, Co, K, M, GEMM_ATOMIC_F32, c.grad + L[l].w_off, nullptr, K, nullptr,
+                 split_for(Co, K, M), c.status, st);
+        k_colsum<uint16_t><<<dim3((Co + 31) / 32, 64), dim3(32, 8), 0, st>>>(c.dz, M, Co, c.grad + L[l].b_off);
+        if (l == 0 || e != cudaSuccess) break;
+        transpose(c.wbf + L[l].w_off, Co, K, c.wT + L[l].w_off, st);
+        e = gemm(c.dz, Co, c.wT + L[l].w_off, Co, M, K, Co, GEMM_STORE_F32, c.dx, nullptr, K, nullptr, 1, c.status,
+                 st);
+        k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin), 256, 0, st>>>(c.dx, c.X[l], B, H, H, L[l].cin,
+                                                                               c.dzp);
+        uint16_t *t = c.dz;
+        c.dz = c.dzp;
+        c.dzp = t;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
+cudaError_t cnn_adam(CnnBuffers &c, float lr, float b1, float b2, float eps, int32_t t, cudaStream_t st) {
+    const int64_t np = cnn_num_params();
+    k_adam_flat<<<grid1d(np), 256, 0, st>>>(c.theta, c.grad, c.m, c.v, np, lr, b1, b2, eps, t, c.wbf);
+    return cudaGetLastError();
+}
+
+}  // namespace dbmp

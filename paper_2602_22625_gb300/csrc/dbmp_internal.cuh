@@ -189,4 +189,27 @@ struct GemmArgs {
 cudaError_t init_gemm_kernels();
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Proposal network (cnn.cu)
+// ---------------------------------------------------------------------------
+struct CnnBuffers {
+    int32_t max_batch;
+    float *theta, *grad, *m, *v;   // fp32 master parameters, gradient, Adam moments
+    uint16_t *wbf, *wT;            // bf16 copies of the weights, transposed copies
+    uint16_t *X[6];                // activations (NHWC bf16): input and five conv outputs
+    float *O, *dO, *dx;            // head outputs, their gradient, fp32 product buffer
+    uint16_t *col, *colT, *dz, *dzT, *dzp;
+    int32_t *status;
+};
+
+int64_t cnn_num_params();
+size_t cnn_bytes(int32_t max_batch);
+cudaError_t cnn_alloc(CnnBuffers &c, int32_t max_batch);
+void cnn_free(CnnBuffers &c);
+cudaError_t cnn_sync_weights(CnnBuffers &c, cudaStream_t st);
+cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStream_t st);
+cudaError_t cnn_decode(CnnBuffers &c, int32_t B, float *params, cudaStream_t st);
+cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, double *loss, cudaStream_t st);
+cudaError_t cnn_adam(CnnBuffers &c, float lr, float b1, float b2, float eps, int32_t t, cudaStream_t st);
+
 }  // namespace dbmp

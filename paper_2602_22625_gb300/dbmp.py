@@ -31,7 +31,9 @@ EXPORTS = (
     "dbmp_atlas_update", "dbmp_workspace_bytes", "dbmp_workspace_create", "dbmp_workspace_destroy",
     "dbmp_status_poll", "dbmp_bin", "dbmp_get_tile_lists", "dbmp_render_fwd", "dbmp_render_bwd",
     "dbmp_mse_grad", "dbmp_adam_step", "dbmp_batch_plan", "dbmp_batch_render", "dbmp_autotune",
-    "dbmp_render_fwd_static",
+    "dbmp_render_fwd_static", "dbmp_gemm_bf16", "dbmp_proposer_num_params", "dbmp_proposer_create",
+    "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
+    "dbmp_proposer_train_step",
 )
 
 
@@ -62,6 +64,11 @@ class DbmpAdamConfig(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("gamma", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("gains", ctypes.c_float * 8),
                 ("zero_grad", ctypes.c_int32)]
+
+
+class DbmpProposerAdam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
 
 
 class DbmpTuning(ctypes.Structure):
@@ -113,6 +120,15 @@ def load(build_if_missing: bool = True):
         "dbmp_autotune": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32, _i32,
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
+        "dbmp_gemm_bf16": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _i32,
+                                  _vp, _vp]),
+        "dbmp_proposer_num_params": (_i64, []),
+        "dbmp_proposer_create": (_i32, [_i32, ctypes.POINTER(_vp)]),
+        "dbmp_proposer_destroy": (_i32, [_vp]),
+        "dbmp_proposer_set_params": (_i32, [_vp, _vp, _i64]),
+        "dbmp_proposer_get": (_i32, [_vp, _i32, _vp, _i64]),
+        "dbmp_propose": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+        "dbmp_proposer_train_step": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(DbmpProposerAdam), _vp, _vp]),
         "dbmp_render_fwd_static": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp, _i32, _i32, _i32, _f32,
                                           ctypes.POINTER(DbmpBackground), _f32, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(DbmpDeviceStatus)]),
@@ -297,3 +313,49 @@ def dbmp_render_fwd_static(H, W, params, bitmap_id, texels, alpha_max, bg, T_sto
                                          ctypes.byref(bg), T_stop, _ptr(image), _ptr(T_final), _ptr(n_last),
                                          _stream(stream), ctypes.byref(st) if st is not None else None))
     return st
+
+
+def dbmp_gemm_bf16(A, B, M, N, K, mode, Cf=None, Cb=None, ldc=None, bias=None, split_k=1, status=None,
+                   stream=None):
+    _check(load().dbmp_gemm_bf16(_ptr(A), A.shape[-1], _ptr(B), B.shape[-1], M, N, K, mode, _ptr(Cf), _ptr(Cb),
+                                 N if ldc is None else ldc, _ptr(bias), split_k, _ptr(status), _stream(stream)))
+
+
+def dbmp_proposer_num_params():
+    return int(load().dbmp_proposer_num_params())
+
+
+def dbmp_proposer_create(max_batch):
+    out = _vp()
+    _check(load().dbmp_proposer_create(max_batch, ctypes.byref(out)))
+    return out.value
+
+
+def dbmp_proposer_destroy(p):
+    _check(load().dbmp_proposer_destroy(p))
+
+
+def dbmp_proposer_set_params(p, theta):
+    import numpy as np
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(load().dbmp_proposer_set_params(p, theta.ctypes.data, theta.size))
+
+
+def dbmp_proposer_get(p, which):
+    import numpy as np
+    out = np.empty(dbmp_proposer_num_params(), np.float32)
+    _check(load().dbmp_proposer_get(p, which, out.ctypes.data, out.size))
+    return out
+
+
+def dbmp_propose(p, images, params_out, stream=None):
+    _check(load().dbmp_propose(p, _ptr(images), images.shape[0], _ptr(params_out), _stream(stream)))
+
+
+def dbmp_proposer_train_step(p, images, target_params, loss, adam=None, stream=None):
+    cfg = None
+    if adam is not None:
+        cfg = DbmpProposerAdam(*adam)
+    _check(load().dbmp_proposer_train_step(p, _ptr(images), _ptr(target_params), images.shape[0],
+                                           ctypes.byref(cfg) if cfg is not None else None, _ptr(loss),
+                                           _stream(stream)))

@@ -1,0 +1,110 @@
+"""The proposal network on the tensor cores against its FP64 oracle (same bfloat16
+rounding points), and what a briefly trained network gains over random
+initialisation before and after the plain refinement."""
+import numpy as np
+import pytest
+
+from oracle import cnn
+from paper_2602_22625_gb300 import dbmp as D
+from paper_2602_22625_gb300 import inputs, proposer
+from _helpers import cuda, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def layer_slices():
+    out, o = [], 0
+    for cin_pad, _, cout, k in cnn.LAYERS:
+        nw = cout * k * k * cin_pad
+        out.append((slice(o, o + nw), slice(o + nw, o + nw + cout)))
+        o += nw + cout
+    return out
+
+
+@pytest.fixture(scope="module")
+def case():
+    rng = np.random.default_rng(0)
+    theta = inputs.cnn_init(1)
+    # positive biases keep most units active; random ones exercise both ReLU sides
+    for w, b in layer_slices():
+        theta[b] = rng.normal(0.05, 0.05, theta[b].shape[0])
+    images = rng.uniform(0, 1, (2, 3, 256, 256)).astype(np.float32)
+    tp = inputs.anchored(11, 2)
+    return theta, images, tp
+
+
+def test_proposer_gradient_matches_oracle(case):
+    cuda()
+    theta, images, tp = case
+    P = proposer.Proposer(max_batch=2)
+    try:
+        P.set_params(theta)
+        loss = P.train_step(to_dev(images), to_dev(tp))
+        g = P.grads()
+        L = loss.item()
+    finally:
+        P.close()
+    O, cache = cnn.forward(theta.astype(np.float64), images)
+    Lr, dO = cnn.loss_and_grad(O, tp)
+    gr = cnn.backward(dO, cache)
+    assert L == pytest.approx(Lr, rel=1e-4)
+    # bf16 roundings happen at the same points on both sides; what remains is the
+    # accumulation: a product accumulated in fp32 rounds to a neighbouring bf16 value
+    # now and then, and these flips compound along the backward chain.  Re-running the
+    # oracle itself with fp32 matmuls moves its gradient by 0.02% (head) to 0.32%
+    # (first layer); tensor-core accumulation roughly triples that.  The bound, 2% per
+    # tensor, is about twice the largest difference seen; a wrong index or operand
+    # gives errors of order one.
+    errs = {}
+    for li, (w, b) in enumerate(layer_slices()):
+        for sl, what in ((w, "W"), (b, "b")):
+            ref = gr[sl]
+            errs[f"{li}{what}"] = float(np.linalg.norm(g[sl] - ref) / np.linalg.norm(ref))
+    print(errs)
+    assert max(errs.values()) < 2e-2, errs
+
+
+def test_propose_matches_oracle_decode(case):
+    cuda()
+    theta, images, _ = case
+    P = proposer.Proposer(max_batch=2)
+    try:
+        P.set_params(theta)
+        got = P.propose(to_dev(images)).cpu().numpy()
+    finally:
+        P.close()
+    O, _ = cnn.forward(theta.astype(np.float64), images)
+    ref = cnn.decode(O)
+    assert np.abs(got - ref).max() <= 2e-3 * max(1.0, np.abs(ref).max())
+
+
+def test_trained_proposals_beat_random_init():
+    """Train on 16384 freshly rendered pairs, then compare on held-out scenes: PSNR
+    of the proposal itself, and after 60 steps of the plain refinement.  (The loss
+    has a floor: colours and opacities of slots hidden behind others cannot be
+    read from the image.)"""
+    cuda()
+    scenes = proposer.SceneRenderer(max_batch=64)
+    P = proposer.Proposer(max_batch=64, seed=2)
+    try:
+        losses = proposer.train(P, scenes, n_pairs=16384, batch=64, seed=5000, lr=2e-3, lr_end=2e-4,
+                                log_every=32)
+        print("training loss", losses)
+        assert losses[-1] < 0.8 * losses[0], losses
+        held = torch.from_numpy(inputs.anchored(999_001, 4)).cuda()
+        targets = torch.empty(4, 3, 256, 256, device="cuda")
+        scenes.render(held, targets)
+        learned = P.propose(targets)
+        rand = torch.from_numpy(inputs.random_init(999_002, 4)).cuda()
+        gains0, gains60 = [], []
+        for i in range(4):
+            pl, _, _, _ = proposer.refine(learned[i], targets[i], scenes.atlas, steps=60)
+            pr, _, _, _ = proposer.refine(rand[i], targets[i], scenes.atlas, steps=60)
+            gains0.append(pl[0] - pr[0])
+            gains60.append(pl[-1] - pr[-1])
+        print("PSNR gain of the learned init at step 0:", gains0, "after 60 steps:", gains60)
+        assert min(gains0) > 1.0, gains0
+        assert np.mean(gains60) > 0.0, gains60
+    finally:
+        P.close()
+        scenes.close()
