@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--impl", default="dbmp", choices=["dbmp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-pairs", type=int, default=100_000)
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--ppt", type=int, default=2)
@@ -236,6 +238,69 @@ def traffic_for(kernel_key):
         return None
 
 
+def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
+    """Trains the proposal network on n_pairs freshly rendered anchored scenes, then
+    for held-out targets times both arms to 30 dB (and 25, 20 dB): learned = propose +
+    refinement, plain = random init + refinement.  Also times the network's training
+    step on the tensor cores."""
+    import numpy as np
+    import torch
+    from paper_2602_22625_gb300 import inputs, proposer
+
+    scenes = proposer.SceneRenderer(max_batch=batch)
+    P = proposer.Proposer(max_batch=batch, seed=0)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = proposer.train(P, scenes, n_pairs, batch, seed=10_000, lr=2e-3, lr_end=1e-4,
+                                log_every=max(1, n_pairs // batch // 8))
+        train_s = time.perf_counter() - t0
+        # tensor-core training step alone (images already rendered)
+        imgs = torch.empty(batch, 3, 256, 256, device="cuda")
+        tp = torch.from_numpy(inputs.anchored(123, batch)).cuda()
+        scenes.render(tp, imgs)
+        for _ in range(3):
+            P.train_step(imgs, tp, 1e-6)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 20
+        for _ in range(reps):
+            P.train_step(imgs, tp, 1e-6)
+        e1.record()
+        e1.synchronize()
+        step_ms = e0.elapsed_time(e1) / reps
+        flops = proposer.cnn_train_flops(batch)
+        held = torch.from_numpy(inputs.anchored(777_001, n_targets)).cuda()
+        targets = torch.empty(n_targets, 3, 256, 256, device="cuda")
+        scenes.render(held, targets)
+        rand = torch.from_numpy(inputs.random_init(777_002, n_targets)).cuda()
+        arms = {"learned": [], "plain": []}
+        for i in range(n_targets):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            init = P.propose(targets[i:i + 1])[0]
+            arms["learned"].append(proposer.refine(init, targets[i], scenes.atlas, steps, t0=t0)[:2])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            arms["plain"].append(proposer.refine(rand[i], targets[i], scenes.atlas, steps, t0=t0)[:2])
+        out = {"pairs": n_pairs, "batch": batch, "train_s": train_s, "train_loss": [losses[0], losses[-1]],
+               "targets": n_targets, "refine_steps": steps,
+               "cnn_train_step_ms": step_ms, "cnn_train_tflops": flops / (step_ms * 1e-3) / 1e12,
+               "cnn_train_frac_of_bf16_peak": flops / (step_ms * 1e-3) / 1e12 / 1964.1}
+        for arm, runs in arms.items():
+            for goal in (20.0, 25.0, 30.0):
+                ts = [proposer.time_to(ps, tm, goal) for ps, tm in runs]
+                hit = [t for t in ts if t is not None]
+                out[f"{arm}_reached_{int(goal)}db"] = f"{len(hit)}/{len(ts)}"
+                out[f"{arm}_median_s_to_{int(goal)}db"] = float(np.median(hit)) if len(hit) == len(ts) else None
+            out[f"{arm}_psnr_start"] = float(np.median([ps[0] for ps, _ in runs]))
+            out[f"{arm}_psnr_final"] = float(np.median([ps[-1] for ps, _ in runs]))
+        return out
+    finally:
+        P.close()
+        scenes.close()
+
+
 def run_dbmp(args):
     import numpy as np
     import torch
@@ -385,6 +450,9 @@ def run_dbmp(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+    learned = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        learned = learned_vs_plain(args.learned_pairs)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -417,6 +485,8 @@ def run_dbmp(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if learned is not None:
+        line["time_to_30db"] = learned
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

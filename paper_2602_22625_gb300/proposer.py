@@ -105,6 +105,13 @@ def train(prop: Proposer, scenes: SceneRenderer, n_pairs, batch, seed=1000, lr=1
     return losses
 
 
+def time_to(psnrs, times, goal):
+    for p, t in zip(psnrs, times):
+        if p >= goal:
+            return t
+    return None
+
+
 def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0, 1.0, 1.0), t0=None,
            psnr_goal=30.0):
     """The plain method: Adam on all primitive parameters of one 256^2 canvas against
@@ -145,3 +152,17 @@ def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0,
         torch.cuda.synchronize()
         D.dbmp_workspace_destroy(ws)
     return psnrs, times, hit, params
+
+
+def cnn_train_flops(batch):
+    """Algorithmic FLOPs of one training step of the network (forward, input and
+    weight gradients; no input gradient for the first layer), with the 3 real
+    input channels of the first layer."""
+    f = 0
+    side = 256
+    for li, (cin_pad, cin, cout, k) in enumerate(inputs.CNN_LAYERS):
+        so = side // 2 if k == 4 else side
+        macs = batch * so * so * cout * k * k * cin
+        f += 2 * macs * (2 if li == 0 else 3)
+        side = so
+    return f
