@@ -252,7 +252,7 @@ def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
     try:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        losses = proposer.train(P, scenes, n_pairs, batch, seed=10_000, lr=2e-3, lr_end=1e-4,
+        losses = proposer.train(P, scenes, n_pairs, batch, seed=10_000, lr=5e-4, lr_end=5e-5,
                                 log_every=max(1, n_pairs // batch // 8))
         train_s = time.perf_counter() - t0
         # tensor-core training step alone (images already rendered)
