@@ -181,22 +181,38 @@ __global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restr
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = sh[t];
 }
 
+// Per tile: exclusive scan of the chunk counts down the tile's column.  A CTA covers
+// 32 tiles (x) with 8 groups (y) that each scan one eighth of the chunks, so the
+// dependent chain per thread is an eighth of the column.
 __global__ void k_colscan(const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t n_tiles,
                           int32_t *__restrict__ hist, int64_t *__restrict__ tile_cnt) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const int c = find_canvas_by(cv, n_canvas, t, 2);
-    const CanvasDesc d = cv[c];
-    const int ntiles = d.ntx * d.nty;
-    const int lt = t - d.tile_base;
-    int32_t *col = hist + d.hist_base + lt;
+    __shared__ int32_t part[8][33];
+    const int t = blockIdx.x * 32 + threadIdx.x;
+    const int g = threadIdx.y;
     int32_t run = 0;
-    for (int k = 0; k < d.n_chunks; ++k) {
-        const int32_t v = col[(int64_t)k * ntiles];
-        col[(int64_t)k * ntiles] = run;
-        run += v;
+    int ntiles = 0, k0 = 0, k1 = 0;
+    int32_t *col = nullptr;
+    if (t < n_tiles) {
+        const CanvasDesc d = cv[find_canvas_by(cv, n_canvas, t, 2)];
+        ntiles = d.ntx * d.nty;
+        const int per = (d.n_chunks + 7) / 8;
+        k0 = min(g * per, d.n_chunks);
+        k1 = min(k0 + per, d.n_chunks);
+        col = hist + d.hist_base + (t - d.tile_base);
+        for (int k = k0; k < k1; ++k) run += col[(int64_t)k * ntiles];
     }
-    tile_cnt[t] = run;
+    part[g][threadIdx.x] = run;
+    __syncthreads();
+    if (t < n_tiles) {
+        int32_t base = 0;
+        for (int h = 0; h < g; ++h) base += part[h][threadIdx.x];
+        for (int k = k0; k < k1; ++k) {
+            const int32_t v = col[(int64_t)k * ntiles];
+            col[(int64_t)k * ntiles] = base;
+            base += v;
+        }
+        if (g == 7) tile_cnt[t] = base;
+    }
 }
 
 // Exclusive scan of n tile counts in place (single CTA of 1024 threads), writes
@@ -347,7 +363,7 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
     if (b.n_chunks > 0) {
         k_count<<<b.n_chunks, kBinThreads, sh32, st>>>(b.rect, b.canvas, b.n_canvas, b.hist);
     }
-    k_colscan<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
+    k_colscan<<<(b.n_tiles + 31) / 32, dim3(32, 8), 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
                                                        b.tile_off);
     k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status);
     if (b.n_chunks > 0) {
