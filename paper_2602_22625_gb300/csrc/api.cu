@@ -35,7 +35,7 @@ int32_t cuda_fail(cudaError_t e, const char *what) {
         if (_e != cudaSuccess) return cuda_fail(_e, what); \
     } while (0)
 
-constexpr int32_t kMaxTilesPerCanvas = 24576;  // scatter cursors: 8 B each in shared memory
+constexpr int32_t kMaxTilesPerCanvas = 65536;  // tile index range of one canvas
 constexpr int64_t kHistCap = 16 << 20;         // chunk x tile histogram entries
 
 bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
@@ -144,10 +144,10 @@ int32_t build_plan(DbmpWorkspace *ws, int32_t n, const int32_t *H, const int32_t
     // smallest common chunk size (>= 128 primitives) whose histogram fits
     int lg = 7;
     for (;; ++lg) {
+        if (lg > 24) return fail(DBMP_ERR_INVALID_ARG, "binning histogram does not fit");
         int64_t h = 0;
         for (auto &d : cv) h += (int64_t)((d.N + (1 << lg) - 1) >> lg) * d.ntx * d.nty;
         if (h <= kHistCap) break;
-        if (lg > 24) return fail(DBMP_ERR_INVALID_ARG, "binning histogram does not fit");
     }
     int64_t hb = 0;
     int32_t chunks = 0;
@@ -158,6 +158,12 @@ int32_t build_plan(DbmpWorkspace *ws, int32_t n, const int32_t *H, const int32_t
         d.hist_base = hb;
         chunks += d.n_chunks;
         hb += (int64_t)d.n_chunks * d.ntx * d.nty;
+    }
+    for (auto &d : cv) {
+        if (!bin_slab_ok(d.ntx, lg))
+            return fail(DBMP_ERR_INVALID_ARG, "canvas too wide for binning (%d tiles per row)", d.ntx);
+        d.slab_rows = bin_slab_rows(d.ntx, d.nty, lg, chunks);
+        d.n_slabs = (d.nty + d.slab_rows - 1) / d.slab_rows;
     }
     ws->plan = cv;
     ws->plan_H.assign(H, H + n);
@@ -198,6 +204,15 @@ int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const
     b.n_chunks = ws->n_chunks;
     b.N = ws->N;
     b.max_tiles_per_canvas = ws->max_tpc;
+    b.chunk_log2 = ws->plan.empty() ? 7 : ws->plan[0].chunk_log2;
+    b.max_slabs = 1;
+    b.smem_count = 16;
+    b.smem_scatter = 16;
+    for (const auto &d : ws->plan) {
+        b.max_slabs = std::max(b.max_slabs, d.n_slabs);
+        b.smem_count = std::max<int32_t>(b.smem_count, (int32_t)bin_smem_bytes(d.ntx, d.slab_rows, d.chunk_log2, false));
+        b.smem_scatter = std::max<int32_t>(b.smem_scatter, (int32_t)bin_smem_bytes(d.ntx, d.slab_rows, d.chunk_log2, true));
+    }
     DBMP_CUDA(cudaMemsetAsync(&ws->status->n_degenerate, 0, sizeof(int32_t), st), "status reset");
     DBMP_CUDA(launch_bin(b, params, bid, atlas->view(), alpha_max, ws->cfg.tile, st), "bin launch");
     ws->params = params;

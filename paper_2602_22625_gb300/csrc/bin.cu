@@ -3,13 +3,14 @@
 // The paper bins on the CPU.  Here every step runs on the device:
 //   k_prep     per primitive: FP64 transform coefficients rounded to a 48-byte record
 //              (Eqs. 1-3 folded), and the fp32 bounding-box rectangle of tiles;
-//   k_count    per chunk of primitives: a shared-memory histogram of tile hits;
+//   k_count    per (chunk of primitives, slab of tile rows): per-tile hit counts from
+//              column and row bit masks (a tile's mask is their AND);
 //   k_colscan  per tile: exclusive scan over chunks  -> each chunk's base in the tile;
 //   k_tilescan exclusive scan over tiles             -> tile offsets, K = sum_t d_t;
-//   k_scatter  per chunk: walks its primitives in index order and appends each to its
-//              tiles' lists at base + running count (shared-memory cursors).
-// Together this is a stable counting sort keyed on the tile id.  Because primitives
-// are appended in index order, each list comes out sorted front to back, which is
+//   k_scatter  per (chunk, slab), one warp per tile: the set bits of the tile's mask,
+//              in index order, written as one contiguous run at the chunk's base.
+// Together this is a stable counting sort keyed on the tile id.  Because each run
+// holds its primitives in index order, each list comes out sorted front to back, which is
 // exactly the order of the keys (tile << 32 | index): no 64-bit keys are formed and
 // no radix passes over them are needed.
 #include <cuda_runtime.h>
@@ -21,7 +22,6 @@ namespace dbmp {
 
 namespace {
 
-constexpr int kBinThreads = 256;
 
 __device__ __forceinline__ int find_canvas_by(const CanvasDesc *cv, int n, int value, int which) {
     // largest c with base(c) <= value; which: 0 = prim_base, 1 = chunk_base, 2 = tile_base
@@ -153,32 +153,90 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     rect[i] = rc;
 }
 
-__global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restrict__ cv,
-                        int32_t n_canvas, int32_t *__restrict__ hist) {
-    extern __shared__ int32_t sh[];
-    const int chunk = blockIdx.x;
-    const int c = find_canvas_by(cv, n_canvas, chunk, 1);
-    const CanvasDesc d = cv[c];
-    const int ntiles = d.ntx * d.nty;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) sh[t] = 0;
-    __syncthreads();
-    const int local = chunk - d.chunk_base;
-    const int p0 = d.prim_base + (local << d.chunk_log2);
-    const int p1 = min(p0 + (1 << d.chunk_log2), d.prim_base + d.N);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int p = p0 + warp; p < p1; p += nw) {
-        const int4 r = rect[p];
-        const int w = r.z - r.x + 1, h = r.w - r.y + 1;
-        if (w <= 0 || h <= 0) continue;
-        const int tau = w * h;
-        for (int k = lane; k < tau; k += 32) {
-            const int ty = r.y + k / w, tx = r.x + k % w;
-            atomicAdd(&sh[ty * d.ntx + tx], 1);
+// Binning work unit: one CTA per (chunk of 2^chunk_log2 primitives, slab of tile
+// rows), taking the chunk in passes of blockDim.x primitives, one warp per 32.
+// A primitive's tiles form a rectangle, so primitive (w, q) of a pass overlaps tile
+// (tx, ty) iff bit q is set in both colw[tx][w] (tx0 <= tx <= tx1) and
+// roww[ty][w] (ty0 <= ty <= ty1): the CTA keeps (columns + slab rows) x warps
+// words instead of a mask per tile, and a tile's mask is their AND.
+struct SlabWork {
+    int local, p0, p1, sy0, sy1, rows, slab_tiles, ntiles, nw;
+    uint32_t *colw, *roww;   // [ntx][nw], [rows][nw] words in shared memory
+};
+
+__device__ __forceinline__ bool slab_work(const CanvasDesc &d, uint32_t *smem, SlabWork &s) {
+    if ((int)blockIdx.y >= d.n_slabs) return false;
+    s.ntiles = d.ntx * d.nty;
+    s.nw = blockDim.x >> 5;
+    s.local = (int)blockIdx.x - d.chunk_base;
+    s.p0 = d.prim_base + (s.local << d.chunk_log2);
+    s.p1 = d.prim_base + (int)min((int64_t)d.N, ((int64_t)s.local + 1) << d.chunk_log2);
+    s.sy0 = blockIdx.y * d.slab_rows;
+    s.sy1 = min(s.sy0 + d.slab_rows, d.nty);
+    s.rows = s.sy1 - s.sy0;
+    s.slab_tiles = s.rows * d.ntx;
+    s.colw = smem;
+    s.roww = smem + d.ntx * s.nw;
+    return true;
+}
+
+// Builds colw / roww for the pass starting at primitive q0: lane q of warp w holds
+// the rectangle of primitive q0 + 32 w + q, each lane then assembles the words of
+// its columns (rows) bit by bit.  No atomics: every word has one writer.
+__device__ __forceinline__ void build_masks(const int4 *__restrict__ rect, int q0, const SlabWork &s, int ntx) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();   // readers of the previous pass' words are done
+    const int p = q0 + warp * 32 + lane;
+    int4 r = make_int4(0, 0, -1, -1);
+    if (p < s.p1) r = rect[p];
+    for (int c0 = 0; c0 < ntx; c0 += 32) {
+        const int c = c0 + lane;
+        uint32_t word = 0u;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            const int x0 = __shfl_sync(0xffffffffu, r.x, q), x1 = __shfl_sync(0xffffffffu, r.z, q);
+            word |= (uint32_t)(x0 <= c && c <= x1) << q;
         }
+        if (c < ntx) s.colw[c * s.nw + warp] = word;
+    }
+    for (int y0 = 0; y0 < s.rows; y0 += 32) {
+        const int y = s.sy0 + y0 + lane;
+        uint32_t word = 0u;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            const int a = __shfl_sync(0xffffffffu, r.y, q), b = __shfl_sync(0xffffffffu, r.w, q);
+            word |= (uint32_t)(a <= y && y <= b) << q;
+        }
+        if (y0 + lane < s.rows) s.roww[(y0 + lane) * s.nw + warp] = word;
     }
     __syncthreads();
-    int32_t *row = hist + d.hist_base + (int64_t)local * ntiles;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = sh[t];
+}
+
+// Number of the pass' primitives overlapping slab tile t (nw is a multiple of 4,
+// the word arrays 16-byte aligned).
+__device__ __forceinline__ int tile_count(const SlabWork &s, int ntx, int t) {
+    const uint4 *cw = reinterpret_cast<const uint4 *>(s.colw + (t % ntx) * s.nw);
+    const uint4 *rw = reinterpret_cast<const uint4 *>(s.roww + (t / ntx) * s.nw);
+    int n = 0;
+    for (int i = 0; i < (s.nw >> 2); ++i) {
+        const uint4 a = cw[i], b = rw[i];
+        n += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+    }
+    return n;
+}
+
+__global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restrict__ cv,
+                        int32_t n_canvas, int32_t *__restrict__ hist) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const CanvasDesc d = cv[find_canvas_by(cv, n_canvas, blockIdx.x, 1)];
+    SlabWork s;
+    if (!slab_work(d, smem, s)) return;
+    int32_t *row = hist + d.hist_base + (int64_t)s.local * s.ntiles + s.sy0 * d.ntx;
+    for (int q0 = s.p0; q0 < s.p1; q0 += blockDim.x) {
+        build_masks(rect, q0, s, d.ntx);
+        for (int t = threadIdx.x; t < s.slab_tiles; t += blockDim.x)
+            row[t] = (q0 == s.p0 ? 0 : row[t]) + tile_count(s, d.ntx, t);
+    }
 }
 
 // Per tile: exclusive scan of the chunk counts down the tile's column.  A CTA covers
@@ -272,36 +330,56 @@ __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, in
     }
 }
 
+// Writes the entries of one (chunk, slab), one warp per tile: lane l owns the nw
+// consecutive bits [l nw, (l + 1) nw) of the tile's 32 nw-bit mask (primitives
+// q0 + l nw + j), a warp scan of the lanes' bit counts places them, and the run of
+// the tile's entries from this pass is written contiguously at
+//   tile_off[t] + (entries of earlier chunks) + (entries of earlier passes),
+// so each list comes out in index (front-to-back) order.
 __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__restrict__ cv,
                           int32_t n_canvas, const int32_t *__restrict__ hist,
                           const int64_t *__restrict__ tile_off, int32_t *__restrict__ list,
                           const DevStatus *status) {
-    extern __shared__ int64_t cur[];
+    extern __shared__ __align__(16) uint32_t smem[];
     if (status->lists_valid == 0) return;
-    const int chunk = blockIdx.x;
-    const int c = find_canvas_by(cv, n_canvas, chunk, 1);
-    const CanvasDesc d = cv[c];
-    const int ntiles = d.ntx * d.nty;
-    const int local = chunk - d.chunk_base;
-    const int32_t *row = hist + d.hist_base + (int64_t)local * ntiles;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-        cur[t] = tile_off[d.tile_base + t] + row[t];
-    __syncthreads();
-    const int p0 = d.prim_base + (local << d.chunk_log2);
-    const int p1 = min(p0 + (1 << d.chunk_log2), d.prim_base + d.N);
-    for (int p = p0; p < p1; ++p) {
-        const int4 r = rect[p];
-        const int w = r.z - r.x + 1, h = r.w - r.y + 1;
-        if (w > 0 && h > 0) {
-            const int tau = w * h;
-            for (int k = threadIdx.x; k < tau; k += blockDim.x) {
-                const int ty = r.y + k / w, tx = r.x + k % w;
-                const int t = ty * d.ntx + tx;
-                list[cur[t]] = p;
-                cur[t] += 1;  // tiles of one primitive are distinct: no race
+    const CanvasDesc d = cv[find_canvas_by(cv, n_canvas, blockIdx.x, 1)];
+    SlabWork s;
+    if (!slab_work(d, smem, s)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *done = reinterpret_cast<int32_t *>(s.roww + s.rows * s.nw);   // entries of earlier passes
+    const int32_t *row = hist + d.hist_base + (int64_t)s.local * s.ntiles + s.sy0 * d.ntx;
+    const int64_t *toff = tile_off + d.tile_base + s.sy0 * d.ntx;
+    const int bit0 = lane * s.nw;              // first bit of this lane
+    const int wi = bit0 >> 5, sh = bit0 & 31;  // its word and offset (nw divides 32)
+    const uint32_t keep = s.nw == 32 ? 0xffffffffu : ((1u << s.nw) - 1u);
+    for (int q0 = s.p0; q0 < s.p1; q0 += blockDim.x) {
+        build_masks(rect, q0, s, d.ntx);
+        const bool first = q0 == s.p0, last = q0 + (int)blockDim.x >= s.p1;
+        for (int t = warp; t < s.slab_tiles; t += s.nw) {
+            const int tx = t % d.ntx, ty = t / d.ntx;
+            uint32_t v = (s.colw[tx * s.nw + wi] & s.roww[ty * s.nw + wi]) >> sh & keep;
+            const int c = __popc(v);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
             }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) {
+                if (first && !last && lane == 0) done[t] = 0;
+                continue;
+            }
+            const int prev = first ? 0 : done[t];
+            int64_t pos = toff[t] + row[t] + prev + (incl - c);
+            const int pbase = q0 + bit0;
+            while (v) {
+                const int j = __ffs(v) - 1;
+                list[pos++] = pbase + j;
+                v &= v - 1u;
+            }
+            if (!last && lane == 0) done[t] = prev + total;
         }
-        __syncthreads();
     }
 }
 
@@ -343,12 +421,10 @@ __global__ void k_order_scatter(const int64_t *__restrict__ off, int32_t n, int3
 
 }  // namespace
 
-cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas) {
-    const int sh64 = (int)(sizeof(int64_t) * (size_t)max_tiles_per_canvas);
-    const int sh32 = (int)(sizeof(int32_t) * (size_t)max_tiles_per_canvas);
-    cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, sh32);
+cudaError_t init_bin_kernels(int32_t) {
+    cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemCap);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, sh64);
+        e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemCap);
     return e;
 }
 
@@ -358,16 +434,16 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
         k_prep<<<(b.N + 255) / 256, 256, 0, st>>>(params, bitmap_id, b.canvas, b.n_canvas, b.N, atlas,
                                                    alpha_max, tile, b.rec, b.rect, b.status);
     }
-    const size_t sh32 = sizeof(int32_t) * (size_t)b.max_tiles_per_canvas;
-    const size_t sh64 = sizeof(int64_t) * (size_t)b.max_tiles_per_canvas;
+    const int chunk_threads = bin_threads(b.chunk_log2);
+    const dim3 grid_cs(b.n_chunks, b.max_slabs);
     if (b.n_chunks > 0) {
-        k_count<<<b.n_chunks, kBinThreads, sh32, st>>>(b.rect, b.canvas, b.n_canvas, b.hist);
+        k_count<<<grid_cs, chunk_threads, b.smem_count, st>>>(b.rect, b.canvas, b.n_canvas, b.hist);
     }
     k_colscan<<<(b.n_tiles + 31) / 32, dim3(32, 8), 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
-                                                       b.tile_off);
+                                                             b.tile_off);
     k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status);
     if (b.n_chunks > 0) {
-        k_scatter<<<b.n_chunks, kBinThreads, sh64, st>>>(b.rect, b.canvas, b.n_canvas, b.hist,
+        k_scatter<<<grid_cs, chunk_threads, b.smem_scatter, st>>>(b.rect, b.canvas, b.n_canvas, b.hist,
                                                          b.tile_off, b.list, b.status);
     }
     if (b.tile_order) {

@@ -32,6 +32,8 @@ struct CanvasDesc {
     int32_t chunk_log2;  // primitives per binning chunk = 1 << chunk_log2
     int64_t pix_base;    // first pixel of this canvas in concatenated per-pixel maps
     int64_t hist_base;   // offset of this canvas' chunk x tile histogram
+    int32_t slab_rows;   // tile rows per binning slab
+    int32_t n_slabs;     // ceil(nty / slab_rows)
 };
 
 // Device status block (mirrors DbmpDeviceStatus, plus internal flags).
@@ -120,6 +122,10 @@ struct BinBuffers {
     int32_t n_chunks;         // total chunks
     int32_t N;                // total primitives
     int32_t max_tiles_per_canvas;
+    int32_t chunk_log2;       // primitives per binning chunk (all canvases), 7..10
+    int32_t max_slabs;        // largest n_slabs over the canvases
+    int32_t smem_count;       // dynamic shared memory of k_count / k_scatter (largest
+    int32_t smem_scatter;     //   over the canvases)
 };
 
 // Stores a one-line message for dbmp_last_error() on this thread; returns code.
@@ -128,6 +134,28 @@ int32_t record_error(int32_t code, const char *msg);
 // One-time kernel set-up (shared-memory opt-in, occupancy), called at workspace
 // creation so that later launches can be captured in CUDA graphs.
 cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas);
+// Binning slab geometry.  One CTA of min(2^chunk_log2, 1024) threads takes a chunk
+// in passes of one primitive per thread and covers a slab of tile rows.  Shared
+// memory: one mask word per (tile column, warp) and per (slab row, warp), plus a
+// running count per slab tile (scatter only).
+constexpr int32_t kBinSmemCap = 96 * 1024;
+constexpr int32_t kBinTargetCtas = 8 * 152;   // enough CTAs to fill every SM several times
+inline int32_t bin_threads(int32_t chunk_log2) { return chunk_log2 >= 10 ? 1024 : (1 << chunk_log2); }
+inline int64_t bin_smem_bytes(int32_t ntx, int32_t rows, int32_t chunk_log2, bool scatter) {
+    const int64_t nw = bin_threads(chunk_log2) / 32;
+    return ((int64_t)ntx + rows) * nw * 4 + (scatter ? 4 * (int64_t)rows * ntx : 0);
+}
+inline bool bin_slab_ok(int32_t ntx, int32_t chunk_log2) {
+    return bin_smem_bytes(ntx, 1, chunk_log2, true) <= kBinSmemCap;
+}
+// Rows per slab: enough slabs that all chunks x slabs reach kBinTargetCtas, within
+// the shared-memory cap.
+inline int32_t bin_slab_rows(int32_t ntx, int32_t nty, int32_t chunk_log2, int64_t total_chunks) {
+    const int64_t want = (kBinTargetCtas + total_chunks - 1) / (total_chunks > 0 ? total_chunks : 1);
+    int32_t rows = want >= nty ? 1 : (int32_t)((nty + want - 1) / want);
+    while (rows > 1 && bin_smem_bytes(ntx, rows, chunk_log2, true) > kBinSmemCap) --rows;
+    return rows;
+}
 cudaError_t init_render_kernels();
 
 cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,

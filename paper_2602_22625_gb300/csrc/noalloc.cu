@@ -129,6 +129,8 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
     d.chunk_base = 0;
     d.chunk_log2 = kChunkLog2;
     d.n_chunks = (N + (1 << kChunkLog2) - 1) >> kChunkLog2;
+    d.slab_rows = bin_slab_rows(d.ntx, d.nty, kChunkLog2, d.n_chunks);
+    d.n_slabs = (d.nty + d.slab_rows - 1) / d.slab_rows;
     d.pix_base = 0;
     d.hist_base = 0;
 
@@ -163,6 +165,10 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
         b.n_chunks = d.n_chunks;
         b.N = N;
         b.max_tiles_per_canvas = d.ntx * d.nty;
+        b.chunk_log2 = kChunkLog2;
+        b.max_slabs = d.n_slabs;
+        b.smem_count = (int32_t)bin_smem_bytes(d.ntx, d.slab_rows, kChunkLog2, false);
+        b.smem_scatter = (int32_t)bin_smem_bytes(d.ntx, d.slab_rows, kChunkLog2, true);
         e = launch_bin(b, params_dev, bitmap_id_dev, atlas, alpha_max, kTile, st);
     }
     if (e == cudaSuccess) {

@@ -7,7 +7,7 @@ import oracle
 from paper_2602_22625_gb300 import dbmp as D
 from paper_2602_22625_gb300 import inputs
 from paper_2602_22625_gb300.render import Atlas, Renderer
-from _helpers import cuda, grad_close, to_dev, torch
+from _helpers import cuda, grad_close, lists_from_rects, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +65,22 @@ def test_bin_bit_exact_main_workload(tile):
     sc = inputs.main()
     offs, lst = gpu_bin(sc, tile)
     ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, *sc.atlas.shape[1:])
+    np.testing.assert_array_equal(offs, ro)
+    np.testing.assert_array_equal(lst, rl)
+
+
+def test_bin_bit_exact_multi_pass_chunks():
+    """300k primitives on a 2048 x 2048 canvas at tile 8 (65,536 tiles): the
+    histogram needs chunks of 2048 primitives, so each binning CTA takes its chunk
+    in two passes, and rows of 256 tiles give one-row slabs."""
+    atlas = inputs.stroke_atlas(seed=32, n=8, size=64)
+    p, b = inputs.primitives(31, 300_000, 2048, 2048, atlas.shape[0], "uniform", (0.001, 0.004))
+    sc = inputs.Scene("small_2048sq_300k", 2048, 2048, p, b, atlas)
+    offs, lst = gpu_bin(sc, 8)
+    # the oracle's definition tests every primitive against every tile (2e10 tests
+    # here); the expected lists come from its rectangles expanded and stably sorted
+    rects, _ = oracle.bin_rects(sc.H, sc.W, 8, sc.params, *sc.atlas.shape[1:])
+    ro, rl = lists_from_rects(rects, 256, 256)
     np.testing.assert_array_equal(offs, ro)
     np.testing.assert_array_equal(lst, rl)
 

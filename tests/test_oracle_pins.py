@@ -317,6 +317,21 @@ def test_binning_conservation_order_and_rects(tile):
         np.testing.assert_array_equal(seg, np.nonzero(inside)[0])
 
 
+@pytest.mark.parametrize("tile", [8, 32])
+def test_lists_from_rects_reproduce_the_oracle_binning(tile):
+    """The rectangle expansion + stable sort used as the expected value for binning
+    cases too large for the oracle's tile-by-tile definition gives the same lists."""
+    from _helpers import lists_from_rects
+    sc = inputs.tiny(seed=10, N=500, H=150, W=230)
+    Hb, Wb = sc.atlas.shape[1:]
+    sc.params[::7, 2] = 0.0   # unlisted primitives in the mix
+    offs, lst = oracle.bin(sc.H, sc.W, tile, sc.params, Hb, Wb)
+    rects, _ = oracle.bin_rects(sc.H, sc.W, tile, sc.params, Hb, Wb)
+    o2, l2 = lists_from_rects(rects, -(-sc.W // tile), -(-sc.H // tile))
+    np.testing.assert_array_equal(o2, offs)
+    np.testing.assert_array_equal(l2, lst)
+
+
 def test_binning_rect_is_tight_and_conservative():
     """The fp32 spec box lies between the exact (FP64) support box widened by
     0.99 px and by 1.01 px, and every pixel where a primitive is non-zero lies in
