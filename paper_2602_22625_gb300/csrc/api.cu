@@ -141,8 +141,9 @@ int32_t build_plan(DbmpWorkspace *ws, int32_t n, const int32_t *H, const int32_t
     if (tiles > ws->lim.max_tiles)
         return fail(DBMP_ERR_INVALID_ARG, "%lld tiles exceed the workspace limit %d", (long long)tiles,
                     ws->lim.max_tiles);
-    // smallest common chunk size (>= 128 primitives) whose histogram fits
-    int lg = 7;
+    // smallest common chunk size (>= 512 primitives: fewer, longer runs per tile in the
+    // scatter) whose histogram fits
+    int lg = 9;
     for (;; ++lg) {
         if (lg > 24) return fail(DBMP_ERR_INVALID_ARG, "binning histogram does not fit");
         int64_t h = 0;

@@ -80,27 +80,56 @@ struct Sample {
     float M;
 };
 
+// The sample in two halves, so that a compositor can issue the tap-quad load of
+// its next layer before it composites the current one: tap_issue transforms the
+// pixel, tests the range and issues the load; tap_finish blends.  Together they
+// are exactly sample_bitmap.
+struct Tap {
+    float4 q;            // (p00, p01, p10, p11); zero when !ok
+    float Up, Vp, wu, wv;
+    bool ok;
+};
+
+__device__ __forceinline__ void tap_issue(const PrimRec &r, const float4 *__restrict__ quad, int32_t Wq,
+                                          float kw, float kv, float Wbf, float Hbf, float px, float py,
+                                          Tap &t) {
+    const float dx = __fsub_rn(px, r.x);
+    const float dy = __fsub_rn(py, r.y);
+    t.Up = __fmaf_rn(r.A, dx, __fmul_rn(r.B, dy));
+    t.Vp = __fmaf_rn(r.C, dx, __fmul_rn(r.D, dy));
+    const float U = __fadd_rn(t.Up, kw);
+    const float V = __fadd_rn(t.Vp, kv);
+    t.ok = U >= -1.0f && U < Wbf && V >= -1.0f && V < Hbf;
+    const float fu = floorf(U), fv = floorf(V);
+    t.wu = __fsub_rn(U, fu);
+    t.wv = __fsub_rn(V, fv);
+    t.q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (t.ok) {
+        const int32_t iu = (int32_t)fu, iv = (int32_t)fv;   // in [-1, W_b-1] x [-1, H_b-1]
+        t.q = __ldg(quad + r.quad_off + (iv + 1) * Wq + (iu + 1));
+    }
+}
+
+__device__ __forceinline__ bool tap_finish(const Tap &t, Sample &s) {
+    if (!t.ok) return false;
+    s.Up = t.Up;
+    s.Vp = t.Vp;
+    s.wu = t.wu;
+    s.wv = t.wv;
+    s.d0 = __fsub_rn(t.q.y, t.q.x);                     // p01 - p00
+    s.d1 = __fsub_rn(t.q.w, t.q.z);                     // p11 - p10
+    s.m0 = __fmaf_rn(s.wu, s.d0, t.q.x);
+    s.m1 = __fmaf_rn(s.wu, s.d1, t.q.z);
+    s.M = __fmaf_rn(s.wv, __fsub_rn(s.m1, s.m0), s.m0);
+    return true;
+}
+
 __device__ __forceinline__ bool sample_bitmap(const PrimRec &r, const float4 *__restrict__ quad,
                                               int32_t Wq, float kw, float kv, float Wbf, float Hbf,
                                               float px, float py, Sample &s) {
-    const float dx = __fsub_rn(px, r.x);
-    const float dy = __fsub_rn(py, r.y);
-    s.Up = __fmaf_rn(r.A, dx, __fmul_rn(r.B, dy));
-    s.Vp = __fmaf_rn(r.C, dx, __fmul_rn(r.D, dy));
-    const float U = __fadd_rn(s.Up, kw);
-    const float V = __fadd_rn(s.Vp, kv);
-    if (!(U >= -1.0f && U < Wbf && V >= -1.0f && V < Hbf)) return false;
-    const float fu = floorf(U), fv = floorf(V);
-    const int32_t iu = (int32_t)fu, iv = (int32_t)fv;   // in [-1, W_b-1] x [-1, H_b-1]
-    s.wu = __fsub_rn(U, fu);
-    s.wv = __fsub_rn(V, fv);
-    const float4 q = __ldg(quad + r.quad_off + (iv + 1) * Wq + (iu + 1));
-    s.d0 = __fsub_rn(q.y, q.x);                       // p01 - p00
-    s.d1 = __fsub_rn(q.w, q.z);                       // p11 - p10
-    s.m0 = __fmaf_rn(s.wu, s.d0, q.x);
-    s.m1 = __fmaf_rn(s.wu, s.d1, q.z);
-    s.M = __fmaf_rn(s.wv, __fsub_rn(s.m1, s.m0), s.m0);
-    return true;
+    Tap t;
+    tap_issue(r, quad, Wq, kw, kv, Wbf, Hbf, px, py, t);
+    return tap_finish(t, s);
 }
 
 // ---------------------------------------------------------------------------

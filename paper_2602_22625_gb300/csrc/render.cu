@@ -29,6 +29,15 @@ namespace {
 
 constexpr float kTFloor = 7.88860905e-31f;  // 2^-100: layers behind are never composited
 constexpr int kWarpsPerBlock = 4;
+
+// Resident CTAs per SM each compositor instantiation is compiled for (register
+// budget 65536 / (128 x blocks)).  Both kernels hide the latency of their tap
+// loads with warps, so occupancy beats registers; these are the largest counts
+// at which ptxas spills at most a few words.
+constexpr int fwd_blocks(int ppt, int batch) { return ppt == 4 ? 5 : (ppt == 2 && batch == 64 ? 7 : 8); }
+constexpr int bwd_blocks(int ppt, int batch) {
+    return ppt == 1 ? (batch == 32 ? 6 : 5) : (ppt == 2 ? (batch == 32 ? 5 : 4) : (batch == 32 ? 4 : 3));
+}
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int find_canvas_tile(const CanvasDesc *cv, int n, int t) {
@@ -165,6 +174,19 @@ __device__ __forceinline__ float bg_at(const RenderArgs &a, const CanvasDesc &d,
     return 0.0f;
 }
 
+// Work counters of one warp, kept in shared memory rather than registers (the
+// compositors are register-limited): per item each lane's counts are summed over
+// the warp and lane 0 adds them here; flushed to the status block at exit.
+struct WarpStats {
+    unsigned long long v[4];
+};
+
+__device__ __forceinline__ int warp_sum(int x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
 // Next work item for this warp (lane 0 pulls, all lanes get it).
 __device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
     int it = 0;
@@ -176,7 +198,7 @@ __device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
 // Forward
 // ---------------------------------------------------------------------------
 template <int TILE, int PPT, int BATCH>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32_t n_items) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k_fwd(RenderArgs a, int32_t n_items) {
     constexpr int RPL = BATCH / 32;   // records per lane per batch
     constexpr int LROWS = 32 / TILE;  // rows covered by the 32 lanes in one pass
     constexpr int RH = LROWS * PPT;   // rows of a region
@@ -190,7 +212,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float tstop = fmaxf(a.T_stop, kTFloor);
-    int64_t ev_acc = 0, ct_acc = 0, ws_acc = 0, sv_acc = 0;
+    __shared__ WarpStats stats_all[kWarpsPerBlock];
+    WarpStats &stats = stats_all[warp];   // pairs evaluated, contributing, walked, survivors
+    if (lane < 4) stats.v[lane] = 0ull;
+    __syncwarp();
 
     for (int item = next_item(&a.status->queue[0], lane); item < n_items;
          item = next_item(&a.status->queue[0], lane)) {
@@ -210,7 +235,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
         }
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
         const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
-        int walked = g.len;
+        int walked = g.len, sv_it = 0, ct_it = 0;
         if (g.len > 0) {
             Prefetch<RPL> pf;
             prefetch<RPL>(pf, a.rec, a.list, g.start, min(BATCH, g.len), lane);
@@ -218,7 +243,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
             for (int b0 = 0; b0 < g.len && alive; b0 += BATCH) {
                 const int n = min(BATCH, g.len - b0);
                 const int m = compact<RPL>(pf, b0, n, sh, pos, a.atlas, rx0, ry0, rw, rh, kw, kv, lane);
-                sv_acc += m;
+                sv_it += m;
                 if (b0 + BATCH < g.len)
                     prefetch<RPL>(pf, a.rec, a.list, g.start + b0 + BATCH, min(BATCH, g.len - b0 - BATCH),
                                   lane);
@@ -226,12 +251,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
                     const PrimRec r = sh[t];
                     const int j = pos[t];
                     bool any = false;
+                    Tap tp[PPT];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        tp[k].ok = false;
+                        if (T[k] >= tstop) tap_issue(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], tp[k]);
+                    }
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         if (!(T[k] >= tstop)) continue;
                         Sample s;
-                        if (sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], s) &&
-                            s.M > 0.0f) {
+                        if (tap_finish(tp[k], s) && s.M > 0.0f) {
                             const float al = __fmul_rn(r.a, s.M);
                             const float q = __fsub_rn(1.0f, al);
                             const float w = __fmul_rn(T[k], al);
@@ -240,7 +270,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
                             C2[k] = __fmaf_rn(w, r.cb, C2[k]);
                             T[k] = __fmul_rn(T[k], q);
                             last[k] = j;
-                            ++ct_acc;
+                            ++ct_it;
                         }
                         any = any || T[k] >= tstop;
                     }
@@ -253,13 +283,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
                 __syncwarp();
             }
         }
-        ws_acc += walked;
         const int64_t HW = (int64_t)g.d.H * g.d.W;
+        int ev_it = 0;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             if (!inside[k]) continue;
             // a pixel evaluates entries up to its last layer, then finds T < T_stop
-            ev_acc += T[k] < tstop ? last[k] + 1 : g.len;
+            ev_it += T[k] < tstop ? last[k] + 1 : g.len;
             const int64_t pix = (int64_t)py[k] * g.d.W + (int64_t)px[k];
             float *img = a.image + 3 * g.d.pix_base;
             img[pix] = __fmaf_rn(T[k], bg_at(a, g.d, 0, pix), C0[k]);
@@ -268,19 +298,24 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_fwd(RenderArgs a, int32
             a.T_final[g.d.pix_base + pix] = T[k];
             a.n_last[g.d.pix_base + pix] = last[k];
         }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ev_acc += __shfl_xor_sync(FULL, ev_acc, o);
-        ct_acc += __shfl_xor_sync(FULL, ct_acc, o);
-    }
-    if (lane == 0) {
-        if (ev_acc) {
-            atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd, (unsigned long long)ev_acc);
-            atomicAdd((unsigned long long *)&a.status->pairs_contrib, (unsigned long long)ct_acc);
+        // per item each lane's counts fit 32 bits (<= PPT x list length)
+        ev_it = warp_sum(ev_it);
+        ct_it = warp_sum(ct_it);
+        if (lane == 0) {
+            stats.v[0] += (unsigned)ev_it;
+            stats.v[1] += (unsigned)ct_it;
+            stats.v[2] += (unsigned)walked;
+            stats.v[3] += (unsigned)sv_it;
         }
-        if (ws_acc) atomicAdd((unsigned long long *)&a.status->warp_steps_fwd, (unsigned long long)ws_acc);
-        if (sv_acc) atomicAdd((unsigned long long *)&a.status->survivors_fwd, (unsigned long long)sv_acc);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (stats.v[0]) {
+            atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd, stats.v[0]);
+            atomicAdd((unsigned long long *)&a.status->pairs_contrib, stats.v[1]);
+        }
+        if (stats.v[2]) atomicAdd((unsigned long long *)&a.status->warp_steps_fwd, stats.v[2]);
+        if (stats.v[3]) atomicAdd((unsigned long long *)&a.status->survivors_fwd, stats.v[3]);
     }
 }
 
@@ -344,7 +379,7 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
 }
 
 template <int TILE, int PPT, int BATCH>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32_t n_items) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k_bwd(RenderArgs a, int32_t n_items) {
     constexpr int RPL = BATCH / 32;
     constexpr int LROWS = 32 / TILE;
     constexpr int RH = LROWS * PPT;
@@ -358,14 +393,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float rho = kw / kv, irho = kv / kw;
-    int64_t ev_acc = 0, ws_acc = 0, sv_acc = 0;
+    __shared__ WarpStats stats_all[kWarpsPerBlock];
+    WarpStats &stats = stats_all[warp];   // pairs evaluated, -, walked, survivors
+    if (lane < 4) stats.v[lane] = 0ull;
+    __syncwarp();
 
     for (int item = next_item(&a.status->queue[1], lane); item < n_items;
          item = next_item(&a.status->queue[1], lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
         float px[PPT], py[PPT], T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
         int last[PPT];
-        int my_max = -1;
+        int my_max = -1, ev_it = 0, sv_it = 0;
         const int64_t HW = (int64_t)g.d.H * g.d.W;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -387,13 +425,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
                 Y[k] = g0[k] * bg_at(a, g.d, 0, pix) + g1[k] * bg_at(a, g.d, 1, pix) +
                        g2[k] * bg_at(a, g.d, 2, pix) - gA;
                 my_max = max(my_max, last[k]);
-                ev_acc += last[k] + 1;
+                ev_it += last[k] + 1;
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(FULL, my_max, o));
+        ev_it = warp_sum(ev_it);
+        if (lane == 0) {
+            stats.v[0] += (unsigned)ev_it;
+            stats.v[2] += (unsigned)(my_max + 1);
+        }
         if (my_max < 0) continue;
-        ws_acc += my_max + 1;
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
         const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
 
@@ -404,7 +446,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
         prefetch<RPL>(pf, a.rec, a.list, g.start + lo, hi - lo, lane);
         while (hi > 0) {
             const int m = compact<RPL>(pf, lo, hi - lo, sh, pos, a.atlas, rx0, ry0, rw, rh, kw, kv, lane);
-            sv_acc += m;
+            sv_it += m;
             const int nlo = max(0, lo - BATCH);
             if (lo > 0) prefetch<RPL>(pf, a.rec, a.list, g.start + nlo, lo - nlo, lane);
             for (int t = m - 1; t >= 0; --t) {
@@ -412,13 +454,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
                 const int j = pos[t];
                 float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 bool any = false;
+                Tap tp[PPT];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    tp[k].ok = false;
+                    if (j <= last[k]) tap_issue(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], tp[k]);
+                }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (j > last[k]) continue;
                     Sample s;
-                    if (!sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], s) ||
-                        !(s.M > 0.0f))
-                        continue;
+                    if (!tap_finish(tp[k], s) || !(s.M > 0.0f)) continue;
                     any = true;
                     const float al = __fmul_rn(r.a, s.M);
                     const float q = __fsub_rn(1.0f, al);
@@ -447,13 +493,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_bwd(RenderArgs a, int32
             hi = lo;
             lo = nlo;
         }
+        if (lane == 0) stats.v[3] += (unsigned)sv_it;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ev_acc += __shfl_xor_sync(FULL, ev_acc, o);
+    __syncwarp();
     if (lane == 0) {
-        if (ev_acc) atomicAdd((unsigned long long *)&a.status->pairs_eval_bwd, (unsigned long long)ev_acc);
-        if (ws_acc) atomicAdd((unsigned long long *)&a.status->warp_steps_bwd, (unsigned long long)ws_acc);
-        if (sv_acc) atomicAdd((unsigned long long *)&a.status->survivors_bwd, (unsigned long long)sv_acc);
+        if (stats.v[0]) atomicAdd((unsigned long long *)&a.status->pairs_eval_bwd, stats.v[0]);
+        if (stats.v[2]) atomicAdd((unsigned long long *)&a.status->warp_steps_bwd, stats.v[2]);
+        if (stats.v[3]) atomicAdd((unsigned long long *)&a.status->survivors_bwd, stats.v[3]);
     }
 }
 
