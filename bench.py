@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--ppt", type=int, default=2)
+    ap.add_argument("--ppt-bwd", type=int, default=0, help="pixels per lane of the backward (0: --ppt)")
     return ap.parse_args()
 
 
@@ -106,24 +107,23 @@ def oracle_target(sc_t):
                          background=sc_t.background)["image"]
 
 
-def cpu_baseline(rows=128):
+def cpu_baseline(min_s=10.0, max_reps=40):
+    """The oracle as it stands on the host cores: fwd + bwd of the whole canvas in
+    FP64, repeated until at least min_s seconds of CPU work (bounded sample)."""
     import oracle
     from paper_2602_22625_gb300 import inputs
     sc = inputs.main(seed=2)
-    tgt_sc = inputs.main(seed=1002)
-    y0 = sc.H // 2 - rows // 2
-    import numpy as np
-    ys, xs = np.mgrid[y0:y0 + rows, 0:sc.W]
-    tgt = np.zeros((3, sc.H, sc.W))
-    tgt[:, y0:y0 + rows] = oracle.render(tgt_sc.H, tgt_sc.W, tgt_sc.params, tgt_sc.bitmap_id,
-                                         tgt_sc.atlas, background=tgt_sc.background,
-                                         pixels=(xs.ravel(), ys.ravel()))["image"].reshape(3, rows, sc.W)
-    t0 = time.perf_counter()
-    oracle_band_step(sc, tgt, y0, y0 + rows)
-    dt = time.perf_counter() - t0
-    return {"value": dt * 1e3 * sc.H / rows, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"rows {y0}..{y0 + rows} of 1024 (fwd+bwd, FP64, T_stop={T_STOP}), "
-                      f"time x {sc.H // rows} to the full canvas; measured {dt:.2f} s"}
+    ts = inputs.main(seed=1002)
+    tgt = oracle.render(ts.H, ts.W, ts.params, ts.bitmap_id, ts.atlas, background=ts.background,
+                        T_stop=T_STOP)["image"]   # input data only: not timed
+    times = []
+    while sum(times) < min_s and len(times) < max_reps:
+        t0 = time.perf_counter()
+        oracle_band_step(sc, tgt, 0, sc.H)
+        times.append(time.perf_counter() - t0)
+    return {"value": statistics.mean(times) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the whole {sc.H}x{sc.W} canvas, fwd+bwd in FP64 (T_stop={T_STOP}), {len(times)} "
+                      f"repetitions, {sum(times):.1f} s of CPU work"}
 
 
 def run_reference(args):
@@ -219,8 +219,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it still matches the source."""
+def traffic_for(kernel_key, tile, batch, ppt):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the
+    source and was taken at this tuning (tile, batch, the pass' pixels per lane)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -228,7 +229,7 @@ def traffic_for(kernel_key):
     try:
         d = json.load(open(p))
         e = d.get(kernel_key)
-        if not e:
+        if not e or (e.get("tile"), e.get("batch"), e.get("ppt")) != (tile, batch, ppt):
             return None
         src = open(os.path.join(ROOT, "paper_2602_22625_gb300", "csrc", e["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != e["sha256"]:
@@ -338,7 +339,8 @@ def run_dbmp(args):
     bg = D.make_background(sc.background)
     max_pairs = 96 << 20
     ws = D.dbmp_workspace_create(N, (W // 8) * (H // 8), max_pairs, 1)
-    D.dbmp_batch_plan(ws, [H], [W], [0, N], tile=args.tile, batch=args.batch, ppt=args.ppt)
+    D.dbmp_batch_plan(ws, [H], [W], [0, N], tile=args.tile, batch=args.batch, ppt=args.ppt,
+                      ppt_bwd=args.ppt_bwd)
 
     # target image: render of the target parameter set
     tgt_p = torch.from_numpy(tgt.params).to(dev)
@@ -352,12 +354,14 @@ def run_dbmp(args):
                         n_last)
     D.dbmp_mse_grad(image, target, dL, loss)
     D.dbmp_status_poll(ws)
-    tuning = {"tile": args.tile, "batch": args.batch, "ppt": args.ppt, "autotuned": False}
+    tuning = {"tile": args.tile, "batch": args.batch, "ppt": args.ppt, "ppt_bwd": args.ppt_bwd or args.ppt,
+              "autotuned": False}
     if not args.no_autotune:
-        (t, b, pp), ms = D.dbmp_autotune(ws, params, bid, atlas, 1.0, bg, T_STOP,
+        (t, b, pp, pb), ms = D.dbmp_autotune(ws, params, bid, atlas, 1.0, bg, T_STOP,
                                          D.BATCH_FWD | D.BATCH_BWD, image, T_final, n_last, dL, dparams,
                                          reps=2)
-        tuning = {"tile": t, "batch": b, "ppt": pp, "autotuned": True, "autotune_ms_fwd_bwd": ms}
+        tuning = {"tile": t, "batch": b, "ppt": pp, "ppt_bwd": pb, "autotuned": True,
+                  "autotune_ms_bin_fwd_bwd": ms}
         dparams.zero_()
     adam = D.adam_config(lr=0.1, gamma=0.1 ** (1.0 / 500), zero_grad=True)
 
@@ -443,9 +447,9 @@ def run_dbmp(args):
     flops_f = FLOPS_FWD_PAIR * contrib
     flops_b = FLOPS_BWD_PAIR * contrib
     if bwd_ms >= fwd_ms:
-        dom, flops, dms, key = "k_bwd (backward compositor)", flops_b, bwd_ms, "bwd"
+        dom, flops, dms, key, kppt = "k_bwd (backward compositor)", flops_b, bwd_ms, "bwd", tuning["ppt_bwd"]
     else:
-        dom, flops, dms, key = "k_fwd (forward compositor)", flops_f, fwd_ms, "fwd"
+        dom, flops, dms, key, kppt = "k_fwd (forward compositor)", flops_f, fwd_ms, "fwd", tuning["ppt"]
     achieved = flops / (dms * 1e-3) / 1e12
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -463,6 +467,7 @@ def run_dbmp(args):
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config({"tile": tuning["tile"], "batch": tuning["batch"], "ppt": tuning["ppt"],
+                          "ppt_bwd": tuning["ppt_bwd"],
                           "autotuned": tuning["autotuned"],
                           "parallelism": f"replicas x{world} (one canvas per GPU, no exchange)"}),
         "breakdown_ms": {"bin": float(phase[:, 0].mean()), "fwd": fwd_ms, "mse": float(phase[:, 2].mean()),
@@ -478,7 +483,7 @@ def run_dbmp(args):
                      "unit_of_work": "contributing (pixel, primitive) pair",
                      "flops_per_unit": FLOPS_BWD_PAIR if key == "bwd" else FLOPS_FWD_PAIR,
                      "algorithmic_flops_per_launch": flops, "kernel_ms": dms,
-                     "traffic": traffic_for(key)},
+                     "traffic": traffic_for(key, tuning["tile"], tuning["batch"], kppt)},
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clk.summary(),

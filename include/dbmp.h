@@ -246,8 +246,10 @@ int32_t dbmp_adam_step(float *params_dev, float *grad_dev, float *m_dev, float *
 typedef struct {
     int32_t tile;   /* 8, 16 or 32 */
     int32_t batch;  /* records each warp stages per shared-memory batch: 32 or 64 */
-    int32_t ppt;    /* pixels per lane: 1, 2 or 4 (4 needs tile >= 16); a warp owns
-                       a region of 32 ppt pixels of a tile */
+    int32_t ppt;    /* pixels per lane of the forward: 1, 2 or 4 (4 needs tile >= 16);
+                       a warp owns a region of 32 ppt pixels of a tile */
+    int32_t ppt_bwd;/* pixels per lane of the backward, same values; 0 = ppt.  The
+                       passes share only per-pixel maps, so their regions may differ */
 } DbmpTuning;
 
 int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
@@ -267,10 +269,11 @@ int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int3
                           int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
                           dbmp_stream_t stream);
 
-/* Autotuner: times every (tile, batch, ppt) candidate on the planned batch (or a
- * single canvas when n_canvas == 0 in the plan) with CUDA events, reps times
- * each, and writes the fastest to *best.  Synchronises `stream`; re-plans the
- * workspace with the winner. */
+/* Autotuner: for every (tile, batch) it times, with CUDA events and reps times
+ * each, the binning once and the forward and the backward (those `mode` asks
+ * for) at every supported ppt; the tuning with the smallest bin + best forward +
+ * best backward time, each pass at its own ppt, goes to *best and its time to
+ * *best_ms.  Synchronises `stream`; re-plans the workspace with the winner. */
 int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
                       const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
                       float T_stop, int32_t mode, float *image_dev, float *T_final_dev,

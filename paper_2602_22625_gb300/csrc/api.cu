@@ -69,7 +69,7 @@ struct DbmpWorkspace {
     std::vector<int32_t> plan_H, plan_W, plan_off;
     int32_t n_canvas = 0, n_tiles = 0, n_chunks = 0, N = 0, max_tpc = 0;
     int64_t n_pix = 0;
-    RenderCfg cfg{16, 32, 2};
+    RenderCfg cfg{16, 32, 2, 2};
     bool persistent = false;
     bool binned = false;
     const float *params = nullptr;  // of the last binning (gradient finalisation)
@@ -523,10 +523,11 @@ int32_t dbmp_adam_step(float *params_dev, float *grad_dev, float *m_dev, float *
 int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
                         const int32_t *prim_offset, const DbmpTuning *tuning, dbmp_stream_t stream) {
     if (!ws || !H || !W || !prim_offset) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
-    const RenderCfg cfg{tuning ? tuning->tile : 16, tuning ? tuning->batch : 32, tuning ? tuning->ppt : 2};
+    RenderCfg cfg{16, 32, 2, 2};
+    if (tuning) cfg = RenderCfg{tuning->tile, tuning->batch, tuning->ppt, tuning->ppt_bwd ? tuning->ppt_bwd : tuning->ppt};
     if (!render_cfg_supported(cfg))
-        return fail(DBMP_ERR_INVALID_ARG, "unsupported tuning (tile %d, batch %d, ppt %d)", cfg.tile,
-                    cfg.batch, cfg.ppt);
+        return fail(DBMP_ERR_INVALID_ARG, "unsupported tuning (tile %d, batch %d, ppt %d, ppt_bwd %d)", cfg.tile,
+                    cfg.batch, cfg.ppt, cfg.ppt_bwd);
     if (int32_t r = build_plan(ws, n_canvas, H, W, prim_offset, cfg.tile)) return r;
     ws->cfg = cfg;
     ws->persistent = true;
@@ -597,41 +598,63 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     DBMP_CUDA(cudaEventCreate(&e0), "event");
     DBMP_CUDA(cudaEventCreate(&e1), "event");
     float best_t = 1e30f;
-    DbmpTuning bt{ws->cfg.tile, ws->cfg.batch, ws->cfg.ppt};
+    DbmpTuning bt{ws->cfg.tile, ws->cfg.batch, ws->cfg.ppt, ws->cfg.ppt_bwd};
     const int32_t tiles[] = {8, 16, 32};
     const int32_t batches[] = {32, 64};
     const int32_t ppts[] = {1, 2, 4};
+    const bool want_f = (mode & DBMP_BATCH_FWD) != 0, want_b = (mode & DBMP_BATCH_BWD) != 0;
     int32_t rc = DBMP_OK;
+    // mean time of `reps` renders of `m`; < 0 on a launch error (rc set)
+    auto time_mode = [&](int32_t m) -> float {
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+            dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop, m, image_dev,
+                              T_final_dev, n_last_dev, dL_dimage_dev, dparams_dev, stream);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            return -1.0f;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / (float)reps;
+    };
     for (int32_t t : tiles) {
-        for (int32_t ci = 0; ci < 6; ++ci) {
-            const int32_t b = batches[ci / 3], p = ppts[ci % 3];
-            if (!render_cfg_supported(RenderCfg{t, b, p})) continue;
-            DbmpTuning cand{t, b, p};
-            if (dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &cand, stream) != DBMP_OK) continue;
-            // warm-up (also validates the capacity for this tile size)
-            rc = dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop,
-                                   mode | DBMP_BATCH_BIN, image_dev, T_final_dev, n_last_dev,
-                                   dL_dimage_dev, dparams_dev, stream);
-            if (rc != DBMP_OK) break;
-            DbmpDeviceStatus s;
-            if (dbmp_status_poll(ws, stream, &s) != DBMP_OK) continue;  // e.g. capacity: skip
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < reps; ++r)
-                dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop,
-                                  mode | DBMP_BATCH_BIN, image_dev, T_final_dev, n_last_dev,
-                                  dL_dimage_dev, dparams_dev, stream);
-            cudaEventRecord(e1, st);
-            cudaError_t e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) {
-                rc = cuda_fail(e, "autotune timing");
-                break;
+        for (int32_t b : batches) {
+            float bin_ms = -1.0f, f_best = 1e30f, g_best = 1e30f;
+            int32_t pf = 0, pb = 0;
+            for (int32_t p : ppts) {
+                if (!render_cfg_supported(RenderCfg{t, b, p, p})) continue;
+                DbmpTuning cand{t, b, p, p};
+                if (dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &cand, stream) != DBMP_OK) continue;
+                // warm-up (also validates the capacity for this tile size)
+                rc = dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop,
+                                       mode | DBMP_BATCH_BIN, image_dev, T_final_dev, n_last_dev,
+                                       dL_dimage_dev, dparams_dev, stream);
+                if (rc != DBMP_OK) break;
+                DbmpDeviceStatus s;
+                if (dbmp_status_poll(ws, stream, &s) != DBMP_OK) break;  // e.g. capacity: skip the tile
+                if (bin_ms < 0.0f && (bin_ms = time_mode(DBMP_BATCH_BIN)) < 0.0f) break;
+                if (want_f) {
+                    const float f = time_mode(DBMP_BATCH_FWD);
+                    if (f < 0.0f) break;
+                    if (f < f_best) f_best = f, pf = p;
+                }
+                if (want_b) {
+                    const float g = time_mode(DBMP_BATCH_BWD);
+                    if (g < 0.0f) break;
+                    if (g < g_best) g_best = g, pb = p;
+                }
             }
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= (float)reps;
-            if (ms < best_t) {
-                best_t = ms;
-                bt = cand;
+            if (rc != DBMP_OK) break;
+            if (bin_ms < 0.0f) continue;
+            if (!want_f) pf = pb ? pb : 2;
+            if (!want_b) pb = pf;
+            const float total = bin_ms + (want_f ? f_best : 0.0f) + (want_b ? g_best : 0.0f);
+            if (total < best_t) {
+                best_t = total;
+                bt = DbmpTuning{t, b, pf, pb};
             }
         }
         if (rc != DBMP_OK) break;

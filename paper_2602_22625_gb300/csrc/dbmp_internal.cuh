@@ -59,11 +59,14 @@ struct AtlasView {
     int32_t n_bmp, Hb, Wb;
 };
 
-// Tile size, records per warp staging batch, pixels per lane.
+// Tile size, records per warp staging batch, pixels per lane of the forward and
+// of the backward (0: same as the forward).
 struct RenderCfg {
     int32_t tile;
     int32_t batch;
     int32_t ppt;
+    int32_t ppt_bwd;
+    int32_t bwd_ppt() const { return ppt_bwd ? ppt_bwd : ppt; }
 };
 
 // ---------------------------------------------------------------------------

@@ -193,7 +193,7 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
         a.image = image_dev;
         a.T_final = T_final_dev;
         a.n_last = n_last_dev;
-        e = launch_fwd(a, RenderCfg{kTile, 32, 2}, st);
+        e = launch_fwd(a, RenderCfg{kTile, 32, 2, 2}, st);
     }
     if (e != cudaSuccess) return fail_static(DBMP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
 

@@ -52,17 +52,51 @@ __global__ void k_sat(const float *__restrict__ tex, int32_t *__restrict__ sat, 
     }
 }
 
+// Adds d^2 to the compensated sum (s, c) with error-free transformations (the
+// exact product d^2 = p + pe by one FMA, the exact sum s + p = t + se by TwoSum),
+// as in Ogita, Rump and Oishi's compensated dot product: s + c carries about twice
+// fp32 precision, so the loss needs no FP64 arithmetic per element (FP64 throughput
+// is a small fraction of FP32 on this GPU).  Explicitly rounded operations keep the
+// compiler from contracting or reassociating the transformations.
+__device__ __forceinline__ void acc_sq(float d, float &s, float &c) {
+    const float p = __fmul_rn(d, d);
+    const float pe = __fmaf_rn(d, d, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(se, pe));
+}
+
+// dL/dI = 2 (I - I*) / n and the loss sum (I - I*)^2 / n.  The differences are
+// formed in fp32 (the upstream gradient's precision), the squares summed per thread
+// with acc_sq and across threads in FP64.  Four elements per thread and load when
+// all pointers are 16-byte aligned; the tail and unaligned buffers take the scalar
+// loop.
 __global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg, int64_t n,
                       float *__restrict__ dL, double *loss) {
     __shared__ double red[32];
     const float scale = (float)(2.0 / (double)n);
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f, c = 0.0f;
+    const bool vec = ((((uintptr_t)I) | ((uintptr_t)Tg) | ((uintptr_t)dL)) & 15) == 0;
+    const int64_t n4 = vec ? n / 4 : 0;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n4; i += nth) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(I) + i);
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(Tg) + i);
+        const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+        reinterpret_cast<float4 *>(dL)[i] = make_float4(scale * d.x, scale * d.y, scale * d.z, scale * d.w);
+        acc_sq(d.x, s, c);
+        acc_sq(d.y, s, c);
+        acc_sq(d.z, s, c);
+        acc_sq(d.w, s, c);
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += nth) {
         const float d = I[i] - Tg[i];
         dL[i] = scale * d;
-        acc += (double)d * (double)d;
+        acc_sq(d, s, c);
     }
+    double acc = (double)s + (double)c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -123,7 +157,7 @@ cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t *sat, i
 cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
                             double *loss, cudaStream_t st) {
     cudaMemsetAsync(loss, 0, sizeof(double), st);
-    if (n > 0) k_mse<<<grid_for(n, 256), 256, 0, st>>>(image, target, n, dL, loss);
+    if (n > 0) k_mse<<<grid_for((n + 3) / 4, 256), 256, 0, st>>>(image, target, n, dL, loss);
     return cudaGetLastError();
 }
 

@@ -603,8 +603,8 @@ cudaError_t init_render_kernels() {
 
 bool render_cfg_supported(const RenderCfg &cfg) {
     const bool tile_ok = cfg.tile == 8 || cfg.tile == 16 || cfg.tile == 32;
-    const bool ppt_ok = cfg.ppt == 1 || cfg.ppt == 2 || (cfg.ppt == 4 && cfg.tile >= 16);
-    return tile_ok && ppt_ok && (cfg.batch == 32 || cfg.batch == 64);
+    auto ppt_ok = [&](int p) { return p == 1 || p == 2 || (p == 4 && cfg.tile >= 16); };
+    return tile_ok && ppt_ok(cfg.ppt) && ppt_ok(cfg.bwd_ppt()) && (cfg.batch == 32 || cfg.batch == 64);
 }
 
 cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
@@ -614,7 +614,9 @@ cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
 
 cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
     cudaMemsetAsync(&a.status->queue[1], 0, sizeof(uint32_t), st);
-    return dispatch(a, cfg, false, st);
+    RenderCfg b = cfg;
+    b.ppt = cfg.bwd_ppt();
+    return dispatch(a, b, false, st);
 }
 
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,

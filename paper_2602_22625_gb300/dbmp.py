@@ -72,7 +72,8 @@ class DbmpProposerAdam(ctypes.Structure):
 
 
 class DbmpTuning(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("ppt", ctypes.c_int32)]
+    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("ppt", ctypes.c_int32),
+                ("ppt_bwd", ctypes.c_int32)]
 
 
 _lib = None
@@ -276,12 +277,12 @@ def dbmp_adam_step(params, grad, m, v, step, cfg, stream=None):
                                  ctypes.byref(cfg), _stream(stream)))
 
 
-def dbmp_batch_plan(ws, H, W, prim_offset, tile=16, batch=32, ppt=2, stream=None):
+def dbmp_batch_plan(ws, H, W, prim_offset, tile=16, batch=32, ppt=2, ppt_bwd=0, stream=None):
     n = len(H)
     Ha = (_i32 * n)(*H)
     Wa = (_i32 * n)(*W)
     Oa = (_i32 * (n + 1))(*prim_offset)
-    t = DbmpTuning(tile, batch, ppt)
+    t = DbmpTuning(tile, batch, ppt, ppt_bwd)
     _check(load().dbmp_batch_plan(ws, n, Ha, Wa, Oa, ctypes.byref(t), _stream(stream)))
 
 
@@ -300,7 +301,7 @@ def dbmp_autotune(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, ima
                                 T_stop, mode, _ptr(image), _ptr(T_final), _ptr(n_last), _ptr(dL_dimage),
                                 _ptr(dparams), reps, ctypes.byref(best), ctypes.byref(ms),
                                 _stream(stream)))
-    return (best.tile, best.batch, best.ppt), ms.value
+    return (best.tile, best.batch, best.ppt, best.ppt_bwd), ms.value
 
 
 def dbmp_render_fwd_static(H, W, params, bitmap_id, texels, alpha_max, bg, T_stop, image, T_final, n_last,

@@ -85,6 +85,13 @@ def test_every_tuning_matches_oracle(tuning):
     grad_close(g, gref, what=str(tuning))
 
 
+@pytest.mark.parametrize("tuning", [(16, 32, 2, 4), (32, 64, 4, 1), (8, 32, 1, 2)],
+                         ids=lambda t: f"t{t[0]}b{t[1]}p{t[2]}pb{t[3]}")
+def test_forward_and_backward_at_different_ppt_match_oracle(tuning):
+    """The backward's regions may differ from the forward's (own pixels per lane)."""
+    test_every_tuning_matches_oracle(tuning)
+
+
 @pytest.mark.parametrize("tuning", [(16, 32, 2), (8, 64, 1), (32, 32, 4)])
 def test_multi_canvas_batch_matches_oracle_per_canvas(tuning):
     scenes, atlas = small_batch()
@@ -166,15 +173,25 @@ def test_out_of_range_bitmap_id_is_not_drawn():
         D.dbmp_atlas_destroy(atlas)
 
 
-def test_mse_kernel_matches_oracle():
+@pytest.mark.parametrize("offset", [0, 1])
+def test_mse_kernel_matches_oracle(offset):
+    """offset 0: 16-byte aligned buffers (four elements per load, a 3-element tail);
+    offset 1: buffers one float past the boundary (the scalar path)."""
     cuda()
     rng = np.random.default_rng(0)
     a = rng.uniform(0, 1, (3, 77, 45)).astype(np.float32)
     b = rng.uniform(0, 1, (3, 77, 45)).astype(np.float32)
-    dL = torch.empty(3, 77, 45, device="cuda")
+    n = a.size
+    ab = torch.zeros(n + 4, device="cuda")
+    bb = torch.zeros(n + 4, device="cuda")
+    gb = torch.zeros(n + 4, device="cuda")
+    ab[offset:offset + n] = to_dev(a).reshape(-1)
+    bb[offset:offset + n] = to_dev(b).reshape(-1)
+    dL = gb[offset:offset + n].view(3, 77, 45)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    D.dbmp_mse_grad(to_dev(a), to_dev(b), dL, loss)
+    D.dbmp_mse_grad(ab[offset:offset + n], bb[offset:offset + n], dL, loss)
     torch.cuda.synchronize()
+    assert float(gb[:offset].abs().sum()) == 0.0 and float(gb[offset + n:].abs().sum()) == 0.0
     # the kernel forms I - I* in float32 (one rounding, relative 6e-8 per element) and
     # squares and sums in float64
     assert loss.item() == pytest.approx(oracle.mse(a, b), rel=2e-7)
@@ -290,7 +307,7 @@ def test_autotune_picks_a_supported_tuning():
         dp = torch.zeros(sc.N, 8, device="cuda")
         best, ms = D.dbmp_autotune(ws, p, b, atlas, 1.0, D.make_background((1, 1, 1)), 1e-6,
                                    D.BATCH_FWD | D.BATCH_BWD, image, T, nl, dL, dp, reps=1)
-        assert tuple(best) in TUNINGS and ms > 0
+        assert tuple(best[:3]) in TUNINGS and (best[0], best[1], best[3]) in TUNINGS and ms > 0
         D.dbmp_batch_render(ws, p, b, atlas, 1.0, D.make_background((1, 1, 1)), 0.0,
                             D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
         ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas)
