@@ -180,9 +180,32 @@ __device__ __forceinline__ bool slab_work(const CanvasDesc &d, uint32_t *smem, S
     return true;
 }
 
-// Builds colw / roww for the pass starting at primitive q0: lane q of warp w holds
-// the rectangle of primitive q0 + 32 w + q, each lane then assembles the words of
-// its columns (rows) bit by bit.  No atomics: every word has one writer.
+// Bits [lo, hi] of the 32 positions [p0, p0 + 32) covered by the inclusive run [a, b].
+__device__ __forceinline__ uint32_t run_bits(int a, int b, int p0) {
+    if (b < p0 || a > p0 + 31) return 0u;
+    const int lo = max(a - p0, 0), hi = min(b - p0, 31);
+    return (0xffffffffu >> (31 - hi)) & (0xffffffffu << lo);
+}
+
+// Transposes the warp's 32 x 32 bit matrix held one row per lane (bit c of lane q)
+// into one column per lane (bit q of lane c): five butterfly stages, stage j
+// exchanging the off-diagonal j x j blocks between lanes l and l ^ j.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    const uint32_t lowmask[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const uint32_t m = lowmask[s];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+// Builds colw / roww for the pass starting at primitive q0: lane q of warp w takes
+// the rectangle of primitive q0 + 32 w + q, forms its run of covered columns (rows)
+// in each group of 32 as a row of bits, and a warp transpose turns the 32 rows
+// into the group's 32 column (row) words.  No atomics: every word has one writer.
 __device__ __forceinline__ void build_masks(const int4 *__restrict__ rect, int q0, const SlabWork &s, int ntx) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();   // readers of the previous pass' words are done
@@ -190,23 +213,11 @@ __device__ __forceinline__ void build_masks(const int4 *__restrict__ rect, int q
     int4 r = make_int4(0, 0, -1, -1);
     if (p < s.p1) r = rect[p];
     for (int c0 = 0; c0 < ntx; c0 += 32) {
-        const int c = c0 + lane;
-        uint32_t word = 0u;
-#pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-            const int x0 = __shfl_sync(0xffffffffu, r.x, q), x1 = __shfl_sync(0xffffffffu, r.z, q);
-            word |= (uint32_t)(x0 <= c && c <= x1) << q;
-        }
-        if (c < ntx) s.colw[c * s.nw + warp] = word;
+        const uint32_t word = transpose32(run_bits(r.x, r.z, c0), lane);
+        if (c0 + lane < ntx) s.colw[(c0 + lane) * s.nw + warp] = word;
     }
     for (int y0 = 0; y0 < s.rows; y0 += 32) {
-        const int y = s.sy0 + y0 + lane;
-        uint32_t word = 0u;
-#pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-            const int a = __shfl_sync(0xffffffffu, r.y, q), b = __shfl_sync(0xffffffffu, r.w, q);
-            word |= (uint32_t)(a <= y && y <= b) << q;
-        }
+        const uint32_t word = transpose32(run_bits(r.y, r.w, s.sy0 + y0), lane);
         if (y0 + lane < s.rows) s.roww[(y0 + lane) * s.nw + warp] = word;
     }
     __syncthreads();
