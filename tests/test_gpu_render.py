@@ -203,6 +203,26 @@ def test_backward_ragged_with_alpha_gradient(bg):
     grad_close(g, ref, what=bg)
 
 
+def test_backward_takes_its_state_from_the_given_maps_not_the_last_forward():
+    """The backward depends only on the binning and the T_final / n_last it is
+    given: after an exact forward (T_stop = 0) another forward of the same binning
+    terminates early (T_stop = 0.3, far fewer list entries walked); the backward
+    with the exact forward's maps still gives the exact gradient."""
+    sc = inputs.tiny(seed=5, N=1500, H=96, W=80)
+    r, p, b, img, T, nl, st0 = gpu_forward(sc, tile=16, T_stop=0.0)
+    img2, T2, nl2 = torch.empty_like(img), torch.empty_like(T), torch.empty_like(nl)
+    D.dbmp_render_fwd(r.ws.handle, r.atlas.handle, r.bg, 0.3, img2, T2, nl2)
+    st1 = r.status()
+    torch.cuda.synchronize()
+    assert int(nl.max()) >= 64 and st1.warp_steps < 0.5 * st0.warp_steps   # fewer batches visited
+    rng = np.random.default_rng(13)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    g = r.backward(to_dev(gI), T, nl)
+    torch.cuda.synchronize()
+    ref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+    grad_close(g.cpu().numpy().astype(np.float64), ref, what="maps of the exact forward")
+
+
 def test_backward_opaque_layer_uses_rewalk():
     """A layer with alpha = 1 exactly (alpha_max = 1, sigmoid(nu) = 1 in float32, M = 1)
     leaves T = 0 behind it; the backward then recovers T in front of it by a re-walk."""
