@@ -16,6 +16,9 @@
  *   Eq. 8   background blend  I = I_FG + T_N b ;  I_alpha = 1 - T_N (Sec. 3.3.2)
  *   Eq. 6, Eq. S4, Eq. S5 (Sec. 3.1.2, Sec. S1.2): exact gradients, written here as a
  *           reverse recursion over the layers of one pixel (no division).
+ *   Sec. 3.2 "Structure-aware Initialization" (Tab. S1 window 7, base probability 0.1):
+ *           local variance, its normalisation, weighted draws of lattice points and the
+ *           initial parameters at them (oracle_local_variance, oracle_structure_init).
  *   Sec. 3.1.1 "Parallelization": every primitive is listed in each tile its padded
  *           bounding box overlaps, in front-to-back (index) order; oracle_bin is that
  *           listing written out as a definition (fp32 bounding-box specification).
@@ -30,13 +33,22 @@
  *   - early termination: a layer k is composited only while T_k >= T_stop
  *     (T_stop = 0 composites every layer);
  *   - a primitive with a non-finite parameter or s == 0 is skipped (no tiles, no
- *     contribution, zero gradient).
+ *     contribution, zero gradient);
+ *   - structure-aware initialisation: "lattice points" are the pixel centres; the local
+ *     variance is the population variance over the 7 x 7 window clipped to the canvas,
+ *     averaged over R, G, B; NLV is its min-max normalisation over the canvas; draws
+ *     are with replacement, with weights quantised to multiples of 2^-20 so that the
+ *     cumulative weights are exact; the colour draw is on the activated colour
+ *     (clamped to [1e-4, 1 - 1e-4], stored as its logit); the random numbers are inputs.
  *
  * Parity pins: the tests check this file against closed forms (identity transform,
  * one and two layer over, occlusion, zero opacity, rotation by pi/2), against
  * torch.nn.functional.grid_sample + autograd in float64 (Algorithm S3), against
  * central finite differences in FP64, against Eq. S5 for b = 0, and the binning
  * against brute-force rectangle intersection and the sum_i tau_i = sum_t d_t identity.
+ * The initialisation: brute-force windows (numpy) and the checkerboard closed form for
+ * the variance, inverse-CDF hits and the law of large numbers for the draws, and the
+ * parameter formulas at the drawn pixels.
  */
 #include <math.h>
 #include <stdint.h>
@@ -527,6 +539,98 @@ int64_t oracle_bin(int32_t H, int32_t W, int32_t tile, int32_t N, const float *p
     free(rects);
     free(tau);
     return K;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Structure-aware initialisation (Sec. 3.2, "Structure-aware Initialization";  */
+/* Tab. S1: variance window 7, base probability 0.1, colour noise std 0.02)    */
+/* -------------------------------------------------------------------------- */
+/* LV(p): for each channel, the population variance of the image over the 7 x 7
+ * window centred on p (clipped to the canvas), averaged over the three channels.
+ * The sums run over the window in row-major order, mean first, then the squared
+ * deviations. */
+void oracle_local_variance(int32_t H, int32_t W, const float *image, double *lv) {
+    const size_t HW = (size_t)H * W;
+    for (int32_t y = 0; y < H; ++y)
+        for (int32_t x = 0; x < W; ++x) {
+            const int32_t y0 = y - 3 < 0 ? 0 : y - 3, y1 = y + 3 > H - 1 ? H - 1 : y + 3;
+            const int32_t x0 = x - 3 < 0 ? 0 : x - 3, x1 = x + 3 > W - 1 ? W - 1 : x + 3;
+            const double n = (double)((y1 - y0 + 1) * (x1 - x0 + 1));
+            double acc = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const float *P = image + (size_t)c * HW;
+                double sum = 0.0;
+                for (int32_t yy = y0; yy <= y1; ++yy)
+                    for (int32_t xx = x0; xx <= x1; ++xx) sum += (double)P[(size_t)yy * W + xx];
+                const double mean = sum / n;
+                double ss = 0.0;
+                for (int32_t yy = y0; yy <= y1; ++yy)
+                    for (int32_t xx = x0; xx <= x1; ++xx) {
+                        const double d = (double)P[(size_t)yy * W + xx] - mean;
+                        ss += d * d;
+                    }
+                acc += ss / n;
+            }
+            lv[(size_t)y * W + x] = acc / 3.0;
+        }
+}
+
+/* The initialisation itself.  NLV = (LV - min LV) / (max LV - min LV) (0 where the
+ * variance is constant over the canvas).  Pixel p is drawn with probability
+ * proportional to w(p) = 0.1 + 0.9 NLV(p), quantised to q(p) = floor(w(p) 2^20) so
+ * that cumulative weights are exact integers: primitive i takes the pixel p with
+ * Q(p) <= floor(u_pos[i] Q_total) < Q(p) + q(p), Q the exclusive prefix sum of q
+ * (draws with replacement).  Its parameters: (x, y) = (px, py), the pixel centre;
+ * s = s_max - (s_max - s_min) NLV(p); theta = 2 pi u_theta[i]; nu fixed; colour
+ * channel j: c_hat = I_j(p) + sigma_c n_color[3i+j] clamped to [1e-4, 1 - 1e-4],
+ * stored as the logit.  params_out is [N][8] FP64; nlv_out [H][W] and pix_out [N]
+ * may be NULL.  Returns Q_total. */
+int64_t oracle_structure_init(int32_t H, int32_t W, const float *image, int32_t N, const double *u_pos,
+                              const double *u_theta, const double *n_color, double s_min, double s_max,
+                              double sigma_c, double nu, double *params_out, double *nlv_out,
+                              int32_t *pix_out) {
+    const size_t HW = (size_t)H * W;
+    double *lv = (double *)malloc(sizeof(double) * HW);
+    int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (HW + 1));
+    oracle_local_variance(H, W, image, lv);
+    double mn = lv[0], mx = lv[0];
+    for (size_t p = 1; p < HW; ++p) {
+        if (lv[p] < mn) mn = lv[p];
+        if (lv[p] > mx) mx = lv[p];
+    }
+    Q[0] = 0;
+    for (size_t p = 0; p < HW; ++p) {
+        lv[p] = mx > mn ? (lv[p] - mn) / (mx - mn) : 0.0; /* NLV */
+        const double w = 0.1 + 0.9 * lv[p];
+        Q[p + 1] = Q[p] + (int64_t)floor(w * 1048576.0);
+    }
+    const int64_t total = Q[HW];
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int32_t i = 0; i < N; ++i) {
+        const int64_t t = (int64_t)floor(u_pos[i] * (double)total);
+        size_t lo = 0, hi = HW - 1; /* largest p with Q[p] <= t */
+        while (lo < hi) {
+            const size_t mid = (lo + hi + 1) / 2;
+            if (Q[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const size_t p = lo;
+        double *o = params_out + 8 * (size_t)i;
+        o[0] = (double)(p % (size_t)W);
+        o[1] = (double)(p / (size_t)W);
+        o[2] = s_max - (s_max - s_min) * lv[p];
+        o[3] = two_pi * u_theta[i];
+        o[4] = nu;
+        for (int j = 0; j < 3; ++j) {
+            double c = (double)image[(size_t)j * HW + p] + sigma_c * n_color[3 * (size_t)i + j];
+            c = c < 1e-4 ? 1e-4 : (c > 1.0 - 1e-4 ? 1.0 - 1e-4 : c);
+            o[5 + j] = log(c / (1.0 - c));
+        }
+        if (pix_out) pix_out[i] = (int32_t)p;
+    }
+    if (nlv_out) memcpy(nlv_out, lv, sizeof(double) * HW);
+    free(lv);
+    free(Q);
+    return total;
 }
 
 /* The spec's |sin|, |cos| (exported so the tests can bound its error). */

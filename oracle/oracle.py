@@ -70,6 +70,12 @@ def lib():
         L.oracle_spec_abs_sincos.argtypes = [ctypes.c_float, _f32p, _f32p]
         L.oracle_num_threads.restype = ctypes.c_int32
         L.oracle_num_threads.argtypes = []
+        L.oracle_local_variance.restype = None
+        L.oracle_local_variance.argtypes = [ctypes.c_int32, ctypes.c_int32, _f32p, _f64p]
+        L.oracle_structure_init.restype = ctypes.c_int64
+        L.oracle_structure_init.argtypes = [ctypes.c_int32, ctypes.c_int32, _f32p, ctypes.c_int32, _f64p, _f64p,
+                                            _f64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _f64p, _f64p, _i32p]
         _lib = L
     return _lib
 
@@ -263,3 +269,37 @@ def adam_step(p, g, m, v, t, lr, gains=LR_GAINS, beta1=0.9, beta2=0.999, eps=1e-
     vh = v / (1.0 - beta2 ** t)
     lr_col = lr * np.asarray(gains, np.float64)[None, :]
     return p - lr_col * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# Structure-aware initialisation (Sec. 3.2 "Structure-aware Initialization", Tab. S1)
+# ---------------------------------------------------------------------------
+
+def local_variance(image):
+    """LV (H, W): per channel the population variance over the 7 x 7 window clipped
+    to the canvas, averaged over the three channels.  image (3, H, W)."""
+    image = np.ascontiguousarray(image, dtype=np.float32)
+    _, H, W = image.shape
+    lv = np.zeros((H, W))
+    lib().oracle_local_variance(H, W, _p(image, _f32p), _p(lv, _f64p))
+    return lv
+
+
+def structure_init(image, u_pos, u_theta, n_color, s_range, sigma_c=0.02, nu=-2.0):
+    """Primitive parameters (N, 8) FP64 drawn by the structure-aware initialisation
+    from image (3, H, W) with the given random draws (u_pos, u_theta in [0, 1), n_color
+    (N, 3) standard normal).  Returns (params, NLV (H, W), pixel index (N,), Q_total)."""
+    image = np.ascontiguousarray(image, dtype=np.float32)
+    _, H, W = image.shape
+    u_pos = np.ascontiguousarray(u_pos, dtype=np.float64)
+    u_theta = np.ascontiguousarray(u_theta, dtype=np.float64)
+    n_color = np.ascontiguousarray(n_color, dtype=np.float64).reshape(-1, 3)
+    N = u_pos.shape[0]
+    params = np.zeros((N, 8))
+    nlv = np.zeros((H, W))
+    pix = np.zeros(max(N, 1), np.int32)
+    total = lib().oracle_structure_init(H, W, _p(image, _f32p), N, _p(u_pos, _f64p), _p(u_theta, _f64p),
+                                        _p(n_color, _f64p), float(s_range[0]), float(s_range[1]),
+                                        float(sigma_c), float(nu), _p(params, _f64p), _p(nlv, _f64p),
+                                        _p(pix, _i32p))
+    return params, nlv, pix[:N], int(total)

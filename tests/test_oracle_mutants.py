@@ -28,6 +28,12 @@ MUTANTS = {
     "bin_margin_sign": ("float fx0 = floorf(((p[0] - hx) - 1.0f) * inv_t);",
                         "float fx0 = floorf(((p[0] - hx) + 1.0f) * inv_t);"),
     "bin_support_extension_dropped": ("float hx = s * (ac * eu + as * ev);", "float hx = s * (ac + as * ev);"),
+    "variance_window_5_wide": ("const int32_t x0 = x - 3 < 0 ? 0 : x - 3, x1 = x + 3 > W - 1 ? W - 1 : x + 3;",
+                               "const int32_t x0 = x - 2 < 0 ? 0 : x - 2, x1 = x + 2 > W - 1 ? W - 1 : x + 2;"),
+    "variance_not_centred": ("const double d = (double)P[(size_t)yy * W + xx] - mean;",
+                             "const double d = (double)P[(size_t)yy * W + xx];"),
+    "base_probability_dropped": ("const double w = 0.1 + 0.9 * lv[p];", "const double w = lv[p];"),
+    "scale_rule_reversed": ("o[2] = s_max - (s_max - s_min) * lv[p];", "o[2] = s_min + (s_max - s_min) * lv[p];"),
 }
 
 
@@ -40,11 +46,11 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                     ignore=shutil.ignore_patterns("_lib", "__pycache__"))
     (tmp_path / "oracle" / "dbmp_oracle.c").write_text(src.replace(a, b, 1))
     (tmp_path / "tests").mkdir()
-    for f in ("test_oracle_pins.py", "conftest.py"):
+    for f in ("test_oracle_pins.py", "test_oracle_init.py", "conftest.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     os.symlink(os.path.join(ROOT, "paper_2602_22625_gb300"), tmp_path / "paper_2602_22625_gb300")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], cwd=tmp_path, capture_output=True, text=True,
-                       timeout=300)
+                        "tests/test_oracle_pins.py", "tests/test_oracle_init.py"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
     assert "failed" in r.stdout
