@@ -241,11 +241,13 @@ def traffic_for(kernel_key, tile, batch, ppt):
 
 def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
     """Trains the proposal network on n_pairs freshly rendered anchored scenes, then
-    for held-out targets times both arms to 30 dB (and 25, 20 dB): learned = propose +
-    refinement, plain = random init + refinement.  Also times the network's training
-    step on the tensor cores."""
+    for held-out targets times three arms to 30 dB (and 25, 20 dB): learned = propose +
+    refinement, plain = random init + refinement, structure = the paper's
+    structure-aware initialisation + refinement.  Also times the network's training
+    step on the tensor cores and the initialisation kernels."""
     import numpy as np
     import torch
+    from paper_2602_22625_gb300 import dbmp as D
     from paper_2602_22625_gb300 import inputs, proposer
 
     scenes = proposer.SceneRenderer(max_batch=batch)
@@ -275,7 +277,17 @@ def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
         targets = torch.empty(n_targets, 3, 256, 256, device="cuda")
         scenes.render(held, targets)
         rand = torch.from_numpy(inputs.random_init(777_002, n_targets)).cuda()
-        arms = {"learned": [], "plain": []}
+        arms = {"learned": [], "plain": [], "structure": []}
+        # the structure-aware initialisation kernels alone (one 256^2 target, 512 draws)
+        scratch = torch.empty(D.dbmp_structure_init_scratch_bytes(256, 256), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            proposer.structure_init(targets[0], 1, scratch=scratch)
+        e0.record()
+        for _ in range(reps):
+            proposer.structure_init(targets[0], 1, scratch=scratch)
+        e1.record()
+        e1.synchronize()
+        init_ms = e0.elapsed_time(e1) / reps
         for i in range(n_targets):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -284,10 +296,17 @@ def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             arms["plain"].append(proposer.refine(rand[i], targets[i], scenes.atlas, steps, t0=t0)[:2])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            init = proposer.structure_init(targets[i], 777_100 + i)
+            arms["structure"].append(proposer.refine(init, targets[i], scenes.atlas, steps, t0=t0)[:2])
         out = {"pairs": n_pairs, "batch": batch, "train_s": train_s, "train_loss": [losses[0], losses[-1]],
                "targets": n_targets, "refine_steps": steps,
                "cnn_train_step_ms": step_ms, "cnn_train_tflops": flops / (step_ms * 1e-3) / 1e12,
-               "cnn_train_frac_of_bf16_peak": flops / (step_ms * 1e-3) / 1e12 / 1964.1}
+               "cnn_train_frac_of_bf16_peak": flops / (step_ms * 1e-3) / 1e12 / 1964.1,
+               "structure_init_ms": init_ms,
+               "structure_init": "Sec. 3.2 structure-aware: 7x7 local variance, draws ~ 0.1 + 0.9 NLV, "
+                                 "s in [6, 14] by NLV, nu = -2, colour std 0.02 (includes the draws' upload)"}
         for arm, runs in arms.items():
             for goal in (20.0, 25.0, 30.0):
                 ts = [proposer.time_to(ps, tm, goal) for ps, tm in runs]

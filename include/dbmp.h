@@ -351,6 +351,42 @@ int32_t dbmp_proposer_train_step(DbmpProposer *p, const float *images_dev, const
                                  dbmp_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
+/* Structure-aware initialisation (Sec. 3.2 "Structure-aware Initialization"; */
+/* Tab. S1: variance window 7, base probability 0.1, colour noise std 0.02)   */
+/* ------------------------------------------------------------------------- */
+/* Draws N initial primitives from a target image, dense and fine where the
+ * image varies locally, sparse and coarse where it is flat:
+ *   LV(p)   per channel the population variance of the image over the 7 x 7
+ *           window centred on pixel p (clipped to the canvas), averaged over
+ *           R, G, B, in FP64;
+ *   NLV(p)  (LV(p) - min LV) / (max LV - min LV), 0 if LV is constant;
+ *   draw    primitive i takes pixel p with probability proportional to
+ *           w(p) = 0.1 + 0.9 NLV(p) (with replacement): w is quantised to
+ *           q(p) = floor(w(p) 2^20) and i takes the p with
+ *           Q(p) <= floor(u_pos[i] Q_total) < Q(p) + q(p), Q the exclusive prefix
+ *           sum of q (exact integers, so the draw is reproducible bit for bit);
+ *   params  x = px, y = py (the pixel centre), s = s_max - (s_max - s_min) NLV(p),
+ *           theta = 2 pi u_theta[i], nu fixed, colour channel j: the logit of
+ *           I_j(p) + sigma_c n_color[3 i + j] clamped to [1e-4, 1 - 1e-4].
+ * Readings of the paper: the lattice points are the pixel centres, the colour
+ * draw is on the activated colour, and the random numbers are inputs (the
+ * caller's seeded generator).  The paper fixes nu = -2 in its text and lists
+ * v_init_bias = -4 in Tab. S1; nu is an argument here.
+ *   image_dev    float32 3 x H x W planar, values in [0, 1] (read only)
+ *   u_pos_dev, u_theta_dev   double [N] in [0, 1);  n_color_dev  double [N][3]
+ *   scratch_dev  dbmp_structure_init_scratch_bytes(H, W) bytes, 256-byte aligned,
+ *                caller-owned; overwritten
+ *   params_dev   float32 [N][8] (out);  nlv_dev  double [H][W] (out, nullable)
+ * Returns DBMP_ERR_INVALID_ARG for H, W < 1, H W > 2^31 - 1, N < 0, a NULL
+ * required pointer, a misaligned scratch, s_min > s_max or sigma_c < 0.
+ * Stream-ordered, no allocation, capturable in a CUDA graph. */
+int32_t dbmp_structure_init_scratch_bytes(int32_t H, int32_t W, size_t *bytes);
+int32_t dbmp_structure_init(const float *image_dev, int32_t H, int32_t W, int32_t N, const double *u_pos_dev,
+                            const double *u_theta_dev, const double *n_color_dev, double s_min, double s_max,
+                            double sigma_c, double nu, void *scratch_dev, float *params_dev, double *nlv_dev,
+                            dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
 /* Forward render without device allocation                                   */
 /* ------------------------------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers that

@@ -668,6 +668,32 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     return dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &bt, stream);
 }
 
+int32_t dbmp_structure_init_scratch_bytes(int32_t H, int32_t W, size_t *bytes) {
+    if (!bytes) return fail(DBMP_ERR_INVALID_ARG, "bytes is NULL");
+    if (H < 1 || W < 1 || (int64_t)H * W > 2147483647LL)
+        return fail(DBMP_ERR_INVALID_ARG, "H, W must be >= 1 with H W < 2^31");
+    *bytes = structure_init_scratch((int64_t)H * W);
+    return DBMP_OK;
+}
+
+int32_t dbmp_structure_init(const float *image_dev, int32_t H, int32_t W, int32_t N, const double *u_pos_dev,
+                            const double *u_theta_dev, const double *n_color_dev, double s_min, double s_max,
+                            double sigma_c, double nu, void *scratch_dev, float *params_dev, double *nlv_dev,
+                            dbmp_stream_t stream) {
+    if (H < 1 || W < 1 || (int64_t)H * W > 2147483647LL)
+        return fail(DBMP_ERR_INVALID_ARG, "H, W must be >= 1 with H W < 2^31");
+    if (N < 0) return fail(DBMP_ERR_INVALID_ARG, "N must be >= 0");
+    if (!image_dev || !scratch_dev) return fail(DBMP_ERR_INVALID_ARG, "image / scratch is NULL");
+    if (N > 0 && (!u_pos_dev || !u_theta_dev || !n_color_dev || !params_dev))
+        return fail(DBMP_ERR_INVALID_ARG, "random draws / params is NULL");
+    if (((uintptr_t)scratch_dev) & 255) return fail(DBMP_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    if (!(s_min <= s_max) || !(sigma_c >= 0.0)) return fail(DBMP_ERR_INVALID_ARG, "need s_min <= s_max, sigma_c >= 0");
+    DBMP_CUDA(launch_structure_init(image_dev, H, W, N, u_pos_dev, u_theta_dev, n_color_dev, s_min, s_max, sigma_c,
+                                    nu, scratch_dev, params_dev, nlv_dev, (cudaStream_t)stream),
+              "structure init launch");
+    return DBMP_OK;
+}
+
 int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev, int32_t ldb, int32_t M,
                        int32_t N, int32_t K, int32_t mode, float *Cf_dev, uint16_t *Cb_dev, int32_t ldc,
                        const float *bias_dev, int32_t split_k, int32_t *status_dev, dbmp_stream_t stream) {

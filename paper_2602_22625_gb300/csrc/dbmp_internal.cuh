@@ -166,6 +166,12 @@ int32_t record_error(int32_t code, const char *msg);
 // One-time kernel set-up (shared-memory opt-in, occupancy), called at workspace
 // creation so that later launches can be captured in CUDA graphs.
 cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas);
+// Structure-aware initialisation (init.cu).
+size_t structure_init_scratch(int64_t n_pixels);
+cudaError_t launch_structure_init(const float *image, int32_t H, int32_t W, int32_t N, const double *u_pos,
+                                  const double *u_theta, const double *n_color, double s_min, double s_max,
+                                  double sigma_c, double nu, void *scratch, float *params, double *nlv_out,
+                                  cudaStream_t st);
 // Binning slab geometry.  One CTA of min(2^chunk_log2, 1024) threads takes a chunk
 // in passes of one primitive per thread and covers a slab of tile rows.  Shared
 // memory: one mask word per (tile column, warp) and per (slab row, warp), plus a

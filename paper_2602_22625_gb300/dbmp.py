@@ -33,7 +33,7 @@ EXPORTS = (
     "dbmp_mse_grad", "dbmp_adam_step", "dbmp_batch_plan", "dbmp_batch_render", "dbmp_autotune",
     "dbmp_render_fwd_static", "dbmp_gemm_bf16", "dbmp_proposer_num_params", "dbmp_proposer_create",
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
-    "dbmp_proposer_train_step",
+    "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
 )
 
 
@@ -130,6 +130,9 @@ def load(build_if_missing: bool = True):
         "dbmp_proposer_get": (_i32, [_vp, _i32, _vp, _i64]),
         "dbmp_propose": (_i32, [_vp, _vp, _i32, _vp, _vp]),
         "dbmp_proposer_train_step": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(DbmpProposerAdam), _vp, _vp]),
+        "dbmp_structure_init_scratch_bytes": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+        "dbmp_structure_init": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp]),
         "dbmp_render_fwd_static": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp, _i32, _i32, _i32, _f32,
                                           ctypes.POINTER(DbmpBackground), _f32, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(DbmpDeviceStatus)]),
@@ -360,3 +363,22 @@ def dbmp_proposer_train_step(p, images, target_params, loss, adam=None, stream=N
     _check(load().dbmp_proposer_train_step(p, _ptr(images), _ptr(target_params), images.shape[0],
                                            ctypes.byref(cfg) if cfg is not None else None, _ptr(loss),
                                            _stream(stream)))
+
+
+def dbmp_structure_init_scratch_bytes(H, W):
+    n = ctypes.c_size_t()
+    _check(load().dbmp_structure_init_scratch_bytes(H, W, ctypes.byref(n)))
+    return n.value
+
+
+def dbmp_structure_init(image, u_pos, u_theta, n_color, s_min, s_max, sigma_c, nu, params, nlv=None,
+                        scratch=None, stream=None):
+    """Structure-aware initialisation of params (N, 8) from image (3, H, W) with the
+    given random draws (float64 device tensors).  scratch: a uint8 device tensor of
+    dbmp_structure_init_scratch_bytes(H, W) bytes (allocated here when None)."""
+    _, H, W = image.shape
+    if scratch is None:
+        scratch = torch.empty(dbmp_structure_init_scratch_bytes(H, W), dtype=torch.uint8, device=image.device)
+    _check(load().dbmp_structure_init(_ptr(image), H, W, params.shape[0], _ptr(u_pos), _ptr(u_theta),
+                                      _ptr(n_color), float(s_min), float(s_max), float(sigma_c), float(nu),
+                                      _ptr(scratch), _ptr(params), _ptr(nlv), _stream(stream)))

@@ -255,6 +255,13 @@ def random_init(seed: int, B: int = 1, N: int = 512, H: int = 256, W: int = 256)
     return p.astype(np.float32)
 
 
+def init_draws(seed: int, N: int):
+    """The random numbers the structure-aware initialisation consumes for N
+    primitives: u_pos, u_theta ~ U[0, 1) (N,), n_color ~ N(0, 1) (N, 3), float64."""
+    g = rng(seed)
+    return g.uniform(0.0, 1.0, N), g.uniform(0.0, 1.0, N), g.normal(0.0, 1.0, (N, 3))
+
+
 def cnn_init(seed: int = 0) -> np.ndarray:
     """He-normal initial weights (zero biases) of the proposal network, flattened in
     the library's parameter order: for each layer, W (Cout x K row-major), then b."""

@@ -154,6 +154,19 @@ def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0,
     return psnrs, times, hit, params
 
 
+def structure_init(target, seed, N=N_PRIMS, s_range=inputs.ANCHOR_SCALE, sigma_c=0.02, nu=-2.0, scratch=None):
+    """The paper's structure-aware initialisation of N primitives from target
+    (3, H, W) on the GPU (Sec. 3.2; Tab. S1 window 7, base probability 0.1,
+    colour std 0.02; nu = -2 as in the text), with seeded random draws."""
+    u, ut, nc = inputs.init_draws(seed, N)
+    dev = target.device
+    params = torch.empty(N, 8, device=dev)
+    D.dbmp_structure_init(target.contiguous(), torch.from_numpy(u).to(dev), torch.from_numpy(ut).to(dev),
+                          torch.from_numpy(nc).to(dev), s_range[0], s_range[1], sigma_c, nu, params,
+                          scratch=scratch)
+    return params
+
+
 def cnn_train_flops(batch):
     """Algorithmic FLOPs of one training step of the network (forward, input and
     weight gradients; no input gradient for the first layer), with the 3 real
