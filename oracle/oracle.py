@@ -303,3 +303,34 @@ def structure_init(image, u_pos, u_theta, n_color, s_range, sigma_c=0.02, nu=-2.
                                         float(sigma_c), float(nu), _p(params, _f64p), _p(nlv, _f64p),
                                         _p(pix, _i32p))
     return params, nlv, pix[:N], int(total)
+
+
+# ---------------------------------------------------------------------------
+# Gaussian blur of the primitive bitmaps (Sec. 3.2 "Blurring Primitives for
+# Enriching Gradients"; Tab. S1 do_gaussian_blur, blur_sigma = 1.0)
+# ---------------------------------------------------------------------------
+
+def blur_radius(sigma):
+    """Support of the kernel: r = ceil(3 sigma) texels on each side."""
+    return int(math.ceil(3.0 * sigma))
+
+
+def gaussian_blur(texels, sigma):
+    """Each bitmap convolved with the 2-D Gaussian exp(-(dy^2 + dx^2) / (2 sigma^2)),
+    |dy|, |dx| <= r, normalised to sum 1, texels outside the bitmap zero; FP64,
+    the 2-D sum written out.  texels (n_bmp, H_b, W_b) -> same shape."""
+    t = np.asarray(texels, np.float64)
+    if t.ndim == 2:
+        t = t[None]
+    r = blur_radius(sigma)
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2.0 * sigma * sigma))
+    w /= w.sum()
+    n, H, W = t.shape
+    pad = np.zeros((n, H + 2 * r, W + 2 * r))
+    pad[:, r:r + H, r:r + W] = t
+    out = np.zeros_like(t)
+    for dy in range(2 * r + 1):
+        for dx in range(2 * r + 1):
+            out += w[dy, dx] * pad[:, dy:dy + H, dx:dx + W]
+    return out
