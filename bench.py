@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the soft-rasterisation ablation")
     ap.add_argument("--learned-pairs", type=int, default=100_000)
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=32)
@@ -321,6 +322,56 @@ def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
         scenes.close()
 
 
+def blur_ablation(n_targets=4, steps=300, sigma=1.0):
+    """Soft rasterisation (Sec. 3.2, Tab. S1 blur_sigma 1.0) on and off: targets are
+    256^2 renders of 512 primitives with 16 hard-edged stroke bitmaps; the same random
+    initialisation is refined against them with the hard atlas and with the atlas
+    blurred on the GPU.  Reports the final PSNR of both arms and the blur kernel time."""
+    import numpy as np
+    import torch
+    from paper_2602_22625_gb300 import dbmp as D
+    from paper_2602_22625_gb300 import inputs, proposer
+
+    hard_np = inputs.stroke_atlas(21, 16, 128, blur_sigma=0.0)
+    hard_dev = torch.from_numpy(hard_np).cuda()
+    soft_dev = D.dbmp_blur_bitmaps(hard_dev, sigma)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        D.dbmp_blur_bitmaps(hard_dev, sigma, out=soft_dev)
+    e1.record()
+    e1.synchronize()
+    blur_ms = e0.elapsed_time(e1) / 20
+    hard = D.dbmp_atlas_create(hard_dev)
+    soft = D.dbmp_atlas_create(soft_dev)
+    N, S = proposer.N_PRIMS, proposer.SIDE
+    ws = D.dbmp_workspace_create(N, (S // 16) ** 2, N * 256, 1)
+    bg = D.make_background((1.0, 1.0, 1.0))
+    res = {"hard": [], "blurred": []}
+    try:
+        for k in range(n_targets):
+            tp, tb = inputs.primitives(31_000 + k, N, S, S, 16, "uniform", (0.03, 0.08))
+            tbid = torch.from_numpy(tb).cuda()
+            tgt = torch.empty(3, S, S, device="cuda")
+            T = torch.empty(S, S, device="cuda")
+            nl = torch.empty(S, S, dtype=torch.int32, device="cuda")
+            D.dbmp_bin(ws, S, S, 16, torch.from_numpy(tp).cuda(), tbid, N, hard, 1.0)
+            D.dbmp_render_fwd(ws, hard, bg, 1e-6, tgt, T, nl)
+            init = torch.from_numpy(inputs.random_init(32_000 + k, 1, N, S, S)[0]).cuda()
+            bid = torch.from_numpy(inputs.rng(33_000 + k).integers(0, 16, N).astype(np.int32)).cuda()
+            for arm, atlas in (("hard", hard), ("blurred", soft)):
+                ps = proposer.refine(init, tgt, atlas, steps, bitmap_id=bid)[0]
+                res[arm].append(ps[-1])
+    finally:
+        torch.cuda.synchronize()
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(hard)
+        D.dbmp_atlas_destroy(soft)
+    return {"targets": n_targets, "steps": steps, "sigma": sigma, "blur_ms_16x128sq": blur_ms,
+            "psnr_final_hard": res["hard"], "psnr_final_blurred": res["blurred"],
+            "median_gain_db": float(np.median(np.array(res["blurred"]) - np.array(res["hard"])))}
+
+
 def run_dbmp(args):
     import numpy as np
     import torch
@@ -476,6 +527,9 @@ def run_dbmp(args):
     learned = None
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_vs_plain(args.learned_pairs)
+    ablation = None
+    if rank == 0 and world == 1 and not args.no_ablation:
+        ablation = blur_ablation()
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -511,6 +565,8 @@ def run_dbmp(args):
         line["cpu_baseline"] = cpu
     if learned is not None:
         line["time_to_30db"] = learned
+    if ablation is not None:
+        line["blur_ablation"] = ablation
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

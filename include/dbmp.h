@@ -351,6 +351,21 @@ int32_t dbmp_proposer_train_step(DbmpProposer *p, const float *images_dev, const
                                  dbmp_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
+/* Gaussian blur of the primitive bitmaps (Sec. 3.2 "Blurring Primitives for  */
+/* Enriching Gradients"; Tab. S1 do_gaussian_blur, blur_sigma = 1.0)          */
+/* ------------------------------------------------------------------------- */
+/* Soft rasterisation applied once before optimisation: out = each bitmap
+ * convolved with the Gaussian exp(-(dy^2 + dx^2) / (2 sigma^2)), |dy|, |dx| <=
+ * r = ceil(3 sigma), normalised to sum 1, with texels outside the bitmap taken as
+ * zero (the radius is this library's reading; the paper gives sigma only).  Build
+ * the atlas from `out` (dbmp_atlas_create / dbmp_atlas_update).
+ *   texels_dev  float32 [n_bmp][H_b][W_b] (read only);  out_dev  same shape, must
+ *               not overlap texels_dev;  sigma in (0, 5];  1 <= n_bmp <= 65535
+ * FP32 arithmetic (separable passes), stream-ordered, no allocation. */
+int32_t dbmp_blur_bitmaps(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b, float sigma,
+                          float *out_dev, dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
 /* Structure-aware initialisation (Sec. 3.2 "Structure-aware Initialization"; */
 /* Tab. S1: variance window 7, base probability 0.1, colour noise std 0.02)   */
 /* ------------------------------------------------------------------------- */

@@ -668,6 +668,20 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     return dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &bt, stream);
 }
 
+int32_t dbmp_blur_bitmaps(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b, float sigma,
+                          float *out_dev, dbmp_stream_t stream) {
+    if (!texels_dev || !out_dev) return fail(DBMP_ERR_INVALID_ARG, "texels / out is NULL");
+    if (n_bmp < 1 || n_bmp > 65535 || H_b < 1 || W_b < 1)
+        return fail(DBMP_ERR_INVALID_ARG, "need 1 <= n_bmp <= 65535 and H_b, W_b >= 1");
+    if (!(sigma > 0.0f && sigma <= 5.0f)) return fail(DBMP_ERR_INVALID_ARG, "sigma must be in (0, 5]");
+    const size_t bytes = sizeof(float) * (size_t)n_bmp * H_b * W_b;
+    const char *a = reinterpret_cast<const char *>(texels_dev), *b = reinterpret_cast<const char *>(out_dev);
+    if (a < b + bytes && b < a + bytes) return fail(DBMP_ERR_INVALID_ARG, "out overlaps texels");
+    DBMP_CUDA(launch_blur(texels_dev, out_dev, n_bmp, H_b, W_b, blur_taps(sigma), (cudaStream_t)stream),
+              "blur launch");
+    return DBMP_OK;
+}
+
 int32_t dbmp_structure_init_scratch_bytes(int32_t H, int32_t W, size_t *bytes) {
     if (!bytes) return fail(DBMP_ERR_INVALID_ARG, "bytes is NULL");
     if (H < 1 || W < 1 || (int64_t)H * W > 2147483647LL)

@@ -166,6 +166,15 @@ int32_t record_error(int32_t code, const char *msg);
 // One-time kernel set-up (shared-memory opt-in, occupancy), called at workspace
 // creation so that later launches can be captured in CUDA graphs.
 cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas);
+// Gaussian blur of the bitmaps (blur.cu): normalised 1-D taps of radius r.
+constexpr int32_t kMaxBlurRadius = 15;
+struct BlurTaps {
+    int32_t r;
+    float w[2 * kMaxBlurRadius + 1];
+};
+BlurTaps blur_taps(double sigma);
+cudaError_t launch_blur(const float *in, float *out, int32_t n_bmp, int32_t Hb, int32_t Wb, const BlurTaps &taps,
+                        cudaStream_t st);
 // Structure-aware initialisation (init.cu).
 size_t structure_init_scratch(int64_t n_pixels);
 cudaError_t launch_structure_init(const float *image, int32_t H, int32_t W, int32_t N, const double *u_pos,

@@ -34,6 +34,7 @@ EXPORTS = (
     "dbmp_render_fwd_static", "dbmp_gemm_bf16", "dbmp_proposer_num_params", "dbmp_proposer_create",
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
+    "dbmp_blur_bitmaps",
 )
 
 
@@ -130,6 +131,7 @@ def load(build_if_missing: bool = True):
         "dbmp_proposer_get": (_i32, [_vp, _i32, _vp, _i64]),
         "dbmp_propose": (_i32, [_vp, _vp, _i32, _vp, _vp]),
         "dbmp_proposer_train_step": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(DbmpProposerAdam), _vp, _vp]),
+        "dbmp_blur_bitmaps": (_i32, [_vp, _i32, _i32, _i32, _f32, _vp, _vp]),
         "dbmp_structure_init_scratch_bytes": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
         "dbmp_structure_init": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp]),
@@ -382,3 +384,15 @@ def dbmp_structure_init(image, u_pos, u_theta, n_color, s_min, s_max, sigma_c, n
     _check(load().dbmp_structure_init(_ptr(image), H, W, params.shape[0], _ptr(u_pos), _ptr(u_theta),
                                       _ptr(n_color), float(s_min), float(s_max), float(sigma_c), float(nu),
                                       _ptr(scratch), _ptr(params), _ptr(nlv), _stream(stream)))
+
+
+def dbmp_blur_bitmaps(texels, sigma, out=None, stream=None):
+    """Gaussian blur (radius ceil(3 sigma), zero padding) of every bitmap of
+    texels (n_bmp, H_b, W_b) float32 CUDA; returns out."""
+    if texels.dim() == 2:
+        texels = texels[None]
+    if out is None:
+        out = torch.empty_like(texels)
+    n, H, W = texels.shape
+    _check(load().dbmp_blur_bitmaps(_ptr(texels), n, H, W, float(sigma), _ptr(out), _stream(stream)))
+    return out

@@ -113,12 +113,12 @@ def time_to(psnrs, times, goal):
 
 
 def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0, 1.0, 1.0), t0=None,
-           psnr_goal=30.0):
+           psnr_goal=30.0, bitmap_id=None):
     """The plain method: Adam on all primitive parameters of one 256^2 canvas against
     target_image (3, 256, 256).  Returns (psnr per step, seconds per step since t0,
     seconds to reach psnr_goal or None, final params)."""
     params = init_params.reshape(N_PRIMS, 8).contiguous().clone()
-    bid = torch.zeros(N_PRIMS, dtype=torch.int32, device="cuda")
+    bid = torch.zeros(N_PRIMS, dtype=torch.int32, device="cuda") if bitmap_id is None else bitmap_id
     ws = D.dbmp_workspace_create(N_PRIMS, (SIDE // 16) ** 2, N_PRIMS * 256, 1)
     bg = D.make_background(background)
     image = torch.empty(3, SIDE, SIDE, device="cuda")
