@@ -481,6 +481,12 @@ def run_dbmp(args):
     ms = float(step_ms.mean())
     st = D.dbmp_status_poll(ws)
     pairs_end = (st.pairs_evaluated, st.pairs_evaluated_bwd, st.pairs_contributing, st.pairs_required)
+    # Sec. S4 scaling statistics of the last step's binning (histograms: log2 bins)
+    sstats = D.dbmp_bin_stats(ws)
+    for k in ("tau_hist", "d_hist", "foot_hist"):
+        h = sstats[k]
+        nz = [i for i, v in enumerate(h) if v]
+        sstats[k] = {"first_bin": nz[0], "counts": h[nz[0]:nz[-1] + 1]} if nz else {"first_bin": 0, "counts": []}
 
     # ---- end to end through the C ABI with host buffers ----
     h_params = params0.cpu().pin_memory()
@@ -567,6 +573,9 @@ def run_dbmp(args):
         line["time_to_30db"] = learned
     if ablation is not None:
         line["blur_ablation"] = ablation
+    line["scaling_stats"] = dict(sstats, note="tau: tiles per primitive, d: primitives per tile, foot: padded "
+                                              "box area / canvas area; bin b = [2^b, 2^(b+1)) (foot: "
+                                              "[2^-(b+1), 2^-b))")
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

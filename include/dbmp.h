@@ -132,6 +132,25 @@ typedef struct {
  * error code and returns out->code. */
 int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStatus *out);
 
+/* Scaling statistics of the workspace's last binning (Sec. S4, "Additional scaling
+ * statistics": normalised footprint A_i / (H W), tile-hit degree tau_i, per-tile
+ * density d_t), summed over the plan's canvases.  A_i is the padded box area
+ * (2 hx + 2)(2 hy + 2) of the binning specification below (FP64 from its fp32
+ * half-extents), normalised by its own canvas.  Histograms have 32 bins:
+ *   tau_hist[b]   listed primitives (tau_i >= 1) with floor(log2 tau_i) = b
+ *   d_hist[b]     tiles with d_t >= 1 and floor(log2 d_t) = b
+ *   foot_hist[b]  listed primitives with A_i / (H W) in [2^-(b+1), 2^-b) (b = 0
+ *                 also takes ratios >= 1; smaller ratios go to b = 31)
+ * pairs = sum_i tau_i = sum_t d_t.  Needs a binning in the workspace (else
+ * DBMP_ERR_NOT_READY) with its params still valid; synchronises `stream`. */
+typedef struct {
+    int64_t n_listed, pairs, tau_max, d_max, n_tiles, empty_tiles;
+    int64_t tau_hist[32];
+    int64_t d_hist[32];
+    int64_t foot_hist[32];
+} DbmpBinStats;
+int32_t dbmp_bin_stats(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpBinStats *out);
+
 /* ------------------------------------------------------------------------- */
 /* Binning (Sec. 3.1.1 "Parallelization"; Sec. S1.3)                          */
 /* ------------------------------------------------------------------------- */

@@ -493,6 +493,30 @@ static int spec_rect(const float *p, int32_t Hb, int32_t Wb, int32_t tile, int32
     return 1;
 }
 
+/* Padded screen-space box area of each primitive, (2 hx + 2)(2 hy + 2) in FP64 from
+ * the fp32 half-extents of the binning specification (the footprint A_i of the
+ * scaling analysis, Sec. S4); -1 for a primitive the binning skips. */
+void oracle_bin_footprint(int32_t N, const float *params, int32_t Hb, int32_t Wb, double *area) {
+    for (int32_t i = 0; i < N; ++i) {
+        const float *p = params + 8 * (size_t)i;
+        int ok = p[2] != 0.0f;
+        for (int j = 0; j < 8; ++j)
+            if (!isfinite(p[j])) ok = 0;
+        if (!ok) {
+            area[i] = -1.0;
+            continue;
+        }
+        float eu = 1.0f + 2.0f / (float)(Wb - 1);
+        float ev = 1.0f + 2.0f / (float)(Hb - 1);
+        float as, ac;
+        spec_abs_sincos(p[3], &as, &ac);
+        float s = fabsf(p[2]);
+        float hx = s * (ac * eu + as * ev);
+        float hy = s * (as * eu + ac * ev);
+        area[i] = (2.0 * (double)hx + 2.0) * (2.0 * (double)hy + 2.0);
+    }
+}
+
 /* Per-primitive tile rectangles: rects[4*i] = {tx0, ty0, tx1, ty1} or {0,0,-1,-1}
  * when the primitive touches no tile; tau[i] = number of tiles. */
 void oracle_bin_rects(int32_t H, int32_t W, int32_t tile, int32_t N, const float *params,

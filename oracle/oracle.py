@@ -70,6 +70,8 @@ def lib():
         L.oracle_spec_abs_sincos.argtypes = [ctypes.c_float, _f32p, _f32p]
         L.oracle_num_threads.restype = ctypes.c_int32
         L.oracle_num_threads.argtypes = []
+        L.oracle_bin_footprint.restype = None
+        L.oracle_bin_footprint.argtypes = [ctypes.c_int32, _f32p, ctypes.c_int32, ctypes.c_int32, _f64p]
         L.oracle_local_variance.restype = None
         L.oracle_local_variance.argtypes = [ctypes.c_int32, ctypes.c_int32, _f32p, _f64p]
         L.oracle_structure_init.restype = ctypes.c_int64
@@ -333,4 +335,40 @@ def gaussian_blur(texels, sigma):
     for dy in range(2 * r + 1):
         for dx in range(2 * r + 1):
             out += w[dy, dx] * pad[:, dy:dy + H, dx:dx + W]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Scaling statistics of a binning (Sec. S4: footprint A_i / (H W), tile-hit
+# degree tau_i, per-tile density d_t)
+# ---------------------------------------------------------------------------
+
+def _log2_bin(v):
+    """floor(log2 v) for integers v >= 1."""
+    return np.array([int(x).bit_length() - 1 for x in np.asarray(v).ravel()], np.int64)
+
+
+def bin_stats(H, W, tile, params, Hb, Wb):
+    """Histograms of one canvas' binning, 32 bins each: tau_hist[b] = listed primitives
+    with floor(log2 tau_i) = b; d_hist[b] = tiles with floor(log2 d_t) = b (empty tiles
+    counted apart); foot_hist[b] = listed primitives with A_i / (H W) in
+    [2^-(b+1), 2^-b) (b = 0 also takes ratios >= 1; b capped at 31)."""
+    params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    N = params.shape[0]
+    _, tau = bin_rects(H, W, tile, params, Hb, Wb)
+    offs, _ = bin(H, W, tile, params, Hb, Wb)
+    d = np.diff(offs)
+    area = np.zeros(max(N, 1))
+    lib().oracle_bin_footprint(N, _p(params, _f32p), Hb, Wb, _p(area, _f64p))
+    area = area[:N]
+    listed = tau > 0
+    out = {"n_listed": int(listed.sum()), "pairs": int(tau.sum()), "tau_max": int(tau.max(initial=0)),
+           "d_max": int(d.max(initial=0)), "n_tiles": int(d.size), "empty_tiles": int((d == 0).sum()),
+           "tau_hist": np.bincount(_log2_bin(tau[listed]), minlength=32)[:32],
+           "d_hist": np.bincount(_log2_bin(d[d > 0]), minlength=32)[:32]}
+    fb = []
+    for a in area[listed]:
+        m, e = math.frexp(a / float(H * W))   # ratio in [2^(e-1), 2^e)
+        fb.append(min(31, max(0, -e)))
+    out["foot_hist"] = np.bincount(np.array(fb, np.int64), minlength=32)[:32]
     return out

@@ -64,6 +64,7 @@ struct DbmpWorkspace {
     int32_t *hist = nullptr;
     CanvasDesc *canvas = nullptr;
     DevStatus *status = nullptr;
+    unsigned long long *stats = nullptr;   // scaling statistics counters
     // host copy of the current plan
     std::vector<CanvasDesc> plan;
     std::vector<int32_t> plan_H, plan_W, plan_off;
@@ -91,6 +92,7 @@ size_t ws_bytes(const DbmpLimits &l) {
     b += sizeof(int32_t) * (size_t)kHistCap;
     b += sizeof(CanvasDesc) * (size_t)l.max_canvases;
     b += sizeof(DevStatus);
+    b += sizeof(unsigned long long) * kBinStatsWords;
     return b;
 }
 
@@ -187,8 +189,7 @@ int32_t check_atlas(const DbmpAtlas *atlas) {
     return DBMP_OK;
 }
 
-int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const DbmpAtlas *atlas,
-               float alpha_max, cudaStream_t st) {
+BinBuffers bin_buffers(DbmpWorkspace *ws) {
     BinBuffers b;
     b.rec = ws->rec;
     b.rect = ws->rect;
@@ -214,6 +215,12 @@ int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const
         b.smem_count = std::max<int32_t>(b.smem_count, (int32_t)bin_smem_bytes(d.ntx, d.slab_rows, d.chunk_log2, false));
         b.smem_scatter = std::max<int32_t>(b.smem_scatter, (int32_t)bin_smem_bytes(d.ntx, d.slab_rows, d.chunk_log2, true));
     }
+    return b;
+}
+
+int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const DbmpAtlas *atlas,
+               float alpha_max, cudaStream_t st) {
+    const BinBuffers b = bin_buffers(ws);
     DBMP_CUDA(cudaMemsetAsync(&ws->status->n_degenerate, 0, sizeof(int32_t), st), "status reset");
     DBMP_CUDA(launch_bin(b, params, bid, atlas->view(), alpha_max, ws->cfg.tile, st), "bin launch");
     ws->params = params;
@@ -374,6 +381,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         {(void **)&ws->hist, sizeof(int32_t) * (size_t)kHistCap},
         {(void **)&ws->canvas, sizeof(CanvasDesc) * (size_t)l.max_canvases},
         {(void **)&ws->status, sizeof(DevStatus)},
+        {(void **)&ws->stats, sizeof(unsigned long long) * kBinStatsWords},
     };
     for (auto &r : reqs) {
         cudaError_t e = cudaMalloc(r.p, r.n);
@@ -397,8 +405,8 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
 
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws) {
     if (!ws) return DBMP_OK;
-    void *ptrs[] = {ws->rec, ws->rect, ws->graw, ws->tile_off, ws->tile_order,
-                    ws->bucket, ws->list, ws->hist, ws->canvas, ws->status};
+    void *ptrs[] = {ws->rec,  ws->rect, ws->graw,   ws->tile_off, ws->tile_order, ws->bucket,
+                    ws->list, ws->hist, ws->canvas, ws->status,   ws->stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ws;
@@ -666,6 +674,28 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     *best = bt;
     if (best_ms) *best_ms = best_t;
     return dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &bt, stream);
+}
+
+int32_t dbmp_bin_stats(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpBinStats *out) {
+    if (!ws || !out) return fail(DBMP_ERR_INVALID_ARG, "ws / out is NULL");
+    if (!ws->binned || (ws->N > 0 && !ws->params)) return fail(DBMP_ERR_NOT_READY, "no binning in this workspace yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBMP_CUDA(launch_bin_stats(bin_buffers(ws), ws->params, ws->Hb, ws->Wb, ws->stats, st), "stats launch");
+    unsigned long long h[kBinStatsWords];
+    DBMP_CUDA(cudaMemcpyAsync(h, ws->stats, sizeof h, cudaMemcpyDeviceToHost, st), "stats copy");
+    DBMP_CUDA(cudaStreamSynchronize(st), "stats sync");
+    out->n_listed = (int64_t)h[0];
+    out->pairs = (int64_t)h[1];
+    out->tau_max = (int64_t)h[2];
+    out->d_max = (int64_t)h[3];
+    out->n_tiles = (int64_t)h[4];
+    out->empty_tiles = (int64_t)h[5];
+    for (int b = 0; b < 32; ++b) {
+        out->tau_hist[b] = (int64_t)h[8 + b];
+        out->d_hist[b] = (int64_t)h[40 + b];
+        out->foot_hist[b] = (int64_t)h[72 + b];
+    }
+    return DBMP_OK;
 }
 
 int32_t dbmp_blur_bitmaps(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b, float sigma,

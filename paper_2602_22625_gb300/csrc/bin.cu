@@ -79,6 +79,19 @@ __device__ __forceinline__ bool all_finite8(const float *p) {
     return ok;
 }
 
+// Half-extents of the padded box of the binning specification: the bitmap's
+// support with its zero-padding ring (e_u = 1 + 2/(W_b-1), e_v likewise) rotated by
+// theta and scaled by |s|, one IEEE operation at a time.
+__device__ __forceinline__ void spec_halfext(float s_raw, float theta, int32_t Hb, int32_t Wb, float &hx, float &hy) {
+    const float eu = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(Wb - 1)));
+    const float ev = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(Hb - 1)));
+    float as, ac;
+    spec_abs_sincos(theta, as, ac);
+    const float s = fabsf(s_raw);
+    hx = __fmul_rn(s, __fadd_rn(__fmul_rn(ac, eu), __fmul_rn(as, ev)));
+    hy = __fmul_rn(s, __fadd_rn(__fmul_rn(as, eu), __fmul_rn(ac, ev)));
+}
+
 __global__ void k_prep(const float *__restrict__ params, const int32_t *__restrict__ bitmap_id,
                        const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t N,
                        AtlasView atlas, float alpha_max, int32_t tile, PrimRec *__restrict__ rec,
@@ -130,13 +143,8 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     // ---- tile rectangle: the fp32 binning specification ----
     int4 rc = make_int4(0, 0, -1, -1);
     if (valid) {
-        const float eu = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(atlas.Wb - 1)));
-        const float ev = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(atlas.Hb - 1)));
-        float as, ac;
-        spec_abs_sincos(p[3], as, ac);
-        const float s = fabsf(p[2]);
-        const float hx = __fmul_rn(s, __fadd_rn(__fmul_rn(ac, eu), __fmul_rn(as, ev)));
-        const float hy = __fmul_rn(s, __fadd_rn(__fmul_rn(as, eu), __fmul_rn(ac, ev)));
+        float hx, hy;
+        spec_halfext(p[2], p[3], atlas.Hb, atlas.Wb, hx, hy);
         const float inv_t = __fdiv_rn(1.0f, (float)tile);
         const float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(p[0], hx), 1.0f), inv_t));
         const float fx1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(p[0], hx), 1.0f), inv_t));
@@ -430,7 +438,84 @@ __global__ void k_order_scatter(const int64_t *__restrict__ off, int32_t n, int3
     }
 }
 
+// ---- scaling statistics of a binning (Sec. S4) ----
+// st: [0] listed primitives, [1] sum tau, [2] max tau, [3] max d, [4] tiles,
+// [5] empty tiles, [8 + b] tau histogram, [40 + b] d histogram, [72 + b] footprint
+// histogram (b = 0..31, see DbmpBinStats).
+__global__ void k_stats_prims(const int4 *__restrict__ rect, const float *__restrict__ params,
+                              const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t N, int32_t Hb, int32_t Wb,
+                              unsigned long long *st) {
+    __shared__ unsigned long long h[64];
+    __shared__ unsigned long long listed, pairs, tmax;
+    if (threadIdx.x < 64) h[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) listed = pairs = tmax = 0ull;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int4 r = rect[i];
+        if (r.z < r.x || r.w < r.y) continue;
+        const unsigned long long tau = (unsigned long long)(r.z - r.x + 1) * (unsigned long long)(r.w - r.y + 1);
+        atomicAdd(&listed, 1ull);
+        atomicAdd(&pairs, tau);
+        atomicMax(&tmax, tau);
+        atomicAdd(&h[63 - __clzll(tau)], 1ull);
+        float hx, hy;
+        const float *p = params + 8 * (int64_t)i;
+        spec_halfext(p[2], p[3], Hb, Wb, hx, hy);
+        const double area = __dmul_rn(__dadd_rn(__dmul_rn(2.0, (double)hx), 2.0),
+                                      __dadd_rn(__dmul_rn(2.0, (double)hy), 2.0));
+        const CanvasDesc d = cv[find_canvas_by(cv, n_canvas, i, 0)];
+        int e;
+        frexp(__ddiv_rn(area, (double)d.H * (double)d.W), &e);   // ratio in [2^(e-1), 2^e)
+        atomicAdd(&h[32 + min(31, max(0, -e))], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        if (h[threadIdx.x]) atomicAdd(&st[8 + threadIdx.x], h[threadIdx.x]);
+        if (h[32 + threadIdx.x]) atomicAdd(&st[72 + threadIdx.x], h[32 + threadIdx.x]);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&st[0], listed);
+        atomicAdd(&st[1], pairs);
+        atomicMax(&st[2], tmax);
+    }
+}
+
+__global__ void k_stats_tiles(const int64_t *__restrict__ off, int32_t n, unsigned long long *st) {
+    __shared__ unsigned long long h[32];
+    __shared__ unsigned long long empty, dmax;
+    if (threadIdx.x < 32) h[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) empty = dmax = 0ull;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const unsigned long long d = (unsigned long long)(off[t + 1] - off[t]);
+        if (d == 0) {
+            atomicAdd(&empty, 1ull);
+            continue;
+        }
+        atomicMax(&dmax, d);
+        atomicAdd(&h[63 - __clzll(d)], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&st[40 + threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        atomicAdd(&st[5], empty);
+        atomicMax(&st[3], dmax);
+        if (blockIdx.x == 0) atomicAdd(&st[4], (unsigned long long)n);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_bin_stats(const BinBuffers &b, const float *params, int32_t Hb, int32_t Wb,
+                             unsigned long long *st, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(unsigned long long) * kBinStatsWords, s);
+    if (e != cudaSuccess) return e;
+    if (b.N > 0)
+        k_stats_prims<<<min(1216, (b.N + 255) / 256), 256, 0, s>>>(b.rect, params, b.canvas, b.n_canvas, b.N, Hb,
+                                                                   Wb, st);
+    if (b.n_tiles > 0) k_stats_tiles<<<min(1216, (b.n_tiles + 255) / 256), 256, 0, s>>>(b.tile_off, b.n_tiles, st);
+    return cudaGetLastError();
+}
 
 cudaError_t init_bin_kernels(int32_t) {
     cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemCap);

@@ -166,6 +166,10 @@ int32_t record_error(int32_t code, const char *msg);
 // One-time kernel set-up (shared-memory opt-in, occupancy), called at workspace
 // creation so that later launches can be captured in CUDA graphs.
 cudaError_t init_bin_kernels(int32_t max_tiles_per_canvas);
+// Scaling statistics of the last binning (bin.cu); st holds kBinStatsWords counters.
+constexpr int32_t kBinStatsWords = 104;
+cudaError_t launch_bin_stats(const BinBuffers &b, const float *params, int32_t Hb, int32_t Wb,
+                             unsigned long long *st, cudaStream_t s);
 // Gaussian blur of the bitmaps (blur.cu): normalised 1-D taps of radius r.
 constexpr int32_t kMaxBlurRadius = 15;
 struct BlurTaps {

@@ -34,8 +34,15 @@ EXPORTS = (
     "dbmp_render_fwd_static", "dbmp_gemm_bf16", "dbmp_proposer_num_params", "dbmp_proposer_create",
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
-    "dbmp_blur_bitmaps",
+    "dbmp_blur_bitmaps", "dbmp_bin_stats",
 )
+
+
+class DbmpBinStats(ctypes.Structure):
+    _fields_ = [("n_listed", ctypes.c_int64), ("pairs", ctypes.c_int64), ("tau_max", ctypes.c_int64),
+                ("d_max", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("empty_tiles", ctypes.c_int64),
+                ("tau_hist", ctypes.c_int64 * 32), ("d_hist", ctypes.c_int64 * 32),
+                ("foot_hist", ctypes.c_int64 * 32)]
 
 
 class DbmpError(RuntimeError):
@@ -132,6 +139,7 @@ def load(build_if_missing: bool = True):
         "dbmp_propose": (_i32, [_vp, _vp, _i32, _vp, _vp]),
         "dbmp_proposer_train_step": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(DbmpProposerAdam), _vp, _vp]),
         "dbmp_blur_bitmaps": (_i32, [_vp, _i32, _i32, _i32, _f32, _vp, _vp]),
+        "dbmp_bin_stats": (_i32, [_vp, _vp, ctypes.POINTER(DbmpBinStats)]),
         "dbmp_structure_init_scratch_bytes": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
         "dbmp_structure_init": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp]),
@@ -395,4 +403,14 @@ def dbmp_blur_bitmaps(texels, sigma, out=None, stream=None):
         out = torch.empty_like(texels)
     n, H, W = texels.shape
     _check(load().dbmp_blur_bitmaps(_ptr(texels), n, H, W, float(sigma), _ptr(out), _stream(stream)))
+    return out
+
+
+def dbmp_bin_stats(ws, stream=None):
+    """Scaling statistics of the workspace's last binning as a dict (histograms as lists)."""
+    st = DbmpBinStats()
+    _check(load().dbmp_bin_stats(ws, _stream(stream), ctypes.byref(st)))
+    out = {f: getattr(st, f) for f in ("n_listed", "pairs", "tau_max", "d_max", "n_tiles", "empty_tiles")}
+    for f in ("tau_hist", "d_hist", "foot_hist"):
+        out[f] = list(getattr(st, f))
     return out
