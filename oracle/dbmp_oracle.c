@@ -608,10 +608,12 @@ void oracle_local_variance(int32_t H, int32_t W, const float *image, double *lv)
  * s = s_max - (s_max - s_min) NLV(p); theta = 2 pi u_theta[i]; nu fixed; colour
  * channel j: c_hat = I_j(p) + sigma_c n_color[3i+j] clamped to [1e-4, 1 - 1e-4],
  * stored as the logit.  params_out is [N][8] FP64; nlv_out [H][W] and pix_out [N]
- * may be NULL.  Returns Q_total. */
-int64_t oracle_structure_init(int32_t H, int32_t W, const float *image, int32_t N, const double *u_pos,
-                              const double *u_theta, const double *n_color, double s_min, double s_max,
-                              double sigma_c, double nu, double *params_out, double *nlv_out,
+ * may be NULL.  mask (nullable, [H][W]): the spatially constrained variant (Sec.
+ * 3.3.2, Sec. S3 "Re-initialization Mechanism") draws only pixels with mask > 0;
+ * with an empty mask nothing is drawn (params_out untouched).  Returns Q_total. */
+int64_t oracle_structure_init(int32_t H, int32_t W, const float *image, const float *mask, int32_t N,
+                              const double *u_pos, const double *u_theta, const double *n_color, double s_min,
+                              double s_max, double sigma_c, double nu, double *params_out, double *nlv_out,
                               int32_t *pix_out) {
     const size_t HW = (size_t)H * W;
     double *lv = (double *)malloc(sizeof(double) * HW);
@@ -626,9 +628,10 @@ int64_t oracle_structure_init(int32_t H, int32_t W, const float *image, int32_t 
     for (size_t p = 0; p < HW; ++p) {
         lv[p] = mx > mn ? (lv[p] - mn) / (mx - mn) : 0.0; /* NLV */
         const double w = 0.1 + 0.9 * lv[p];
-        Q[p + 1] = Q[p] + (int64_t)floor(w * 1048576.0);
+        Q[p + 1] = Q[p] + (mask && !(mask[p] > 0.0f) ? 0 : (int64_t)floor(w * 1048576.0));
     }
     const int64_t total = Q[HW];
+    if (total == 0) N = 0; /* an empty mask draws nothing */
     const double two_pi = 6.283185307179586476925286766559;
     for (int32_t i = 0; i < N; ++i) {
         const int64_t t = (int64_t)floor(u_pos[i] * (double)total);

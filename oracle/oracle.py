@@ -75,8 +75,8 @@ def lib():
         L.oracle_local_variance.restype = None
         L.oracle_local_variance.argtypes = [ctypes.c_int32, ctypes.c_int32, _f32p, _f64p]
         L.oracle_structure_init.restype = ctypes.c_int64
-        L.oracle_structure_init.argtypes = [ctypes.c_int32, ctypes.c_int32, _f32p, ctypes.c_int32, _f64p, _f64p,
-                                            _f64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+        L.oracle_structure_init.argtypes = [ctypes.c_int32, ctypes.c_int32, _f32p, _f32p, ctypes.c_int32, _f64p,
+                                            _f64p, _f64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, _f64p, _f64p, _i32p]
         _lib = L
     return _lib
@@ -287,11 +287,14 @@ def local_variance(image):
     return lv
 
 
-def structure_init(image, u_pos, u_theta, n_color, s_range, sigma_c=0.02, nu=-2.0):
+def structure_init(image, u_pos, u_theta, n_color, s_range, sigma_c=0.02, nu=-2.0, mask=None):
     """Primitive parameters (N, 8) FP64 drawn by the structure-aware initialisation
     from image (3, H, W) with the given random draws (u_pos, u_theta in [0, 1), n_color
-    (N, 3) standard normal).  Returns (params, NLV (H, W), pixel index (N,), Q_total)."""
+    (N, 3) standard normal); mask (H, W): draw only where mask > 0 (an empty mask
+    draws nothing: params zero, pixel -1).  Returns (params, NLV (H, W), pixel index
+    (N,), Q_total)."""
     image = np.ascontiguousarray(image, dtype=np.float32)
+    mask_a = None if mask is None else np.ascontiguousarray(mask, dtype=np.float32)
     _, H, W = image.shape
     u_pos = np.ascontiguousarray(u_pos, dtype=np.float64)
     u_theta = np.ascontiguousarray(u_theta, dtype=np.float64)
@@ -299,8 +302,9 @@ def structure_init(image, u_pos, u_theta, n_color, s_range, sigma_c=0.02, nu=-2.
     N = u_pos.shape[0]
     params = np.zeros((N, 8))
     nlv = np.zeros((H, W))
-    pix = np.zeros(max(N, 1), np.int32)
-    total = lib().oracle_structure_init(H, W, _p(image, _f32p), N, _p(u_pos, _f64p), _p(u_theta, _f64p),
+    pix = np.full(max(N, 1), -1, np.int32)
+    total = lib().oracle_structure_init(H, W, _p(image, _f32p), _p(mask_a, _f32p), N, _p(u_pos, _f64p),
+                                        _p(u_theta, _f64p),
                                         _p(n_color, _f64p), float(s_range[0]), float(s_range[1]),
                                         float(sigma_c), float(nu), _p(params, _f64p), _p(nlv, _f64p),
                                         _p(pix, _i32p))
@@ -372,3 +376,36 @@ def bin_stats(H, W, tile, params, Hb, Wb):
         fb.append(min(31, max(0, -e)))
     out["foot_hist"] = np.bincount(np.array(fb, np.int64), minlength=32)[:32]
     return out
+
+
+
+def structure_reinit(params, image, mask, u_pos, u_theta, n_color, s_range, threshold=0.3, sigma_c=0.02,
+                     nu=-2.0):
+    """Re-initialisation (Sec. 3.3.2; Sec. S3 "Re-initialization Mechanism"): every
+    primitive i with sigmoid(nu_i) < threshold takes the structure-aware draw i
+    (restricted to mask > 0 when mask is given).  Returns (new params FP64, indices)."""
+    p = np.asarray(params, np.float64).reshape(-1, 8).copy()
+    drawn, _, pix, total = structure_init(image, u_pos, u_theta, n_color, s_range, sigma_c, nu, mask)
+    low = np.nonzero(1.0 / (1.0 + np.exp(-p[:, 4])) < threshold)[0] if total > 0 else np.zeros(0, np.int64)
+    p[low] = drawn[low]
+    return p, low
+
+
+# ---------------------------------------------------------------------------
+# Spatially constrained loss (Eq. 9, Sec. 3.3.2)
+# ---------------------------------------------------------------------------
+
+def alpha_loss(image, T_final, target, target_alpha, lam):
+    """L = mean over 3 H W of [alpha* > 0] (I - I*)^2 + lam * mean over H W of
+    (I_alpha - alpha*)^2, I_alpha = 1 - T_N (Eq. 9 with both norms read as means).
+    Returns (L, dL/dI (3, H, W), dL/dI_alpha (H, W)) in FP64."""
+    I = np.asarray(image, np.float64)
+    T = np.asarray(T_final, np.float64)
+    It = np.asarray(target, np.float64)
+    a = np.asarray(target_alpha, np.float64)
+    m = (a > 0).astype(np.float64)[None]
+    n3, n1 = I.size, T.size
+    d = m * (I - It)
+    Ia = 1.0 - T
+    L = float((d * d).sum() / n3 + lam * ((Ia - a) ** 2).sum() / n1)
+    return L, 2.0 * d / n3, 2.0 * lam * (Ia - a) / n1

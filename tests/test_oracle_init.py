@@ -101,3 +101,64 @@ def test_parameters_at_the_drawn_pixels():
     c2 = 1 / (1 + np.exp(-p2[:, 5:8]))
     inside = (chat + 0.02 * nc > 2e-4) & (chat + 0.02 * nc < 1 - 2e-4)
     np.testing.assert_allclose(c2[inside], (chat + 0.02 * nc)[inside], rtol=0, atol=1e-12)
+
+
+def test_masked_draws_stay_inside_the_mask_and_an_all_ones_mask_changes_nothing():
+    g = np.random.default_rng(7)
+    img = g.uniform(0, 1, (3, 30, 40)).astype(np.float32)
+    yy, xx = np.mgrid[0:30, 0:40]
+    mask = (((yy - 15) ** 2 + (xx - 20) ** 2) < 100).astype(np.float32)
+    u, ut, nc = draws(8, 4000)
+    p, _, pix, total = oracle.structure_init(img, u, ut, nc, (2.0, 8.0), mask=mask)
+    assert total > 0 and np.all(mask.ravel()[pix] > 0)
+    p1, _, pix1, _ = oracle.structure_init(img, u, ut, nc, (2.0, 8.0), mask=np.ones((30, 40), np.float32))
+    p0, _, pix0, _ = oracle.structure_init(img, u, ut, nc, (2.0, 8.0))
+    np.testing.assert_array_equal(pix1, pix0)
+    np.testing.assert_array_equal(p1, p0)
+    pe, _, pixe, te = oracle.structure_init(img, u, ut, nc, (2.0, 8.0), mask=np.zeros((30, 40), np.float32))
+    assert te == 0 and np.all(pixe == -1) and np.all(pe == 0)
+
+
+def test_reinit_replaces_exactly_the_transparent_primitives():
+    """Sec. S3 "Re-initialization Mechanism": sigmoid(nu) < 0.3 -> redrawn."""
+    g = np.random.default_rng(9)
+    img = g.uniform(0, 1, (3, 32, 32)).astype(np.float32)
+    N = 300
+    params = g.normal(size=(N, 8))
+    params[:, 4] = g.uniform(-3, 3, N)
+    u, ut, nc = draws(10, N)
+    new, idx = oracle.structure_reinit(params, img, None, u, ut, nc, (2.0, 8.0), threshold=0.3)
+    low = 1 / (1 + np.exp(-params[:, 4])) < 0.3
+    np.testing.assert_array_equal(np.sort(idx), np.nonzero(low)[0])
+    np.testing.assert_array_equal(new[~low], params[~low])
+    drawn = oracle.structure_init(img, u, ut, nc, (2.0, 8.0))[0]
+    np.testing.assert_array_equal(new[low], drawn[low])
+
+
+def test_alpha_loss_reduces_to_mse_and_its_gradients_match_finite_differences():
+    g = np.random.default_rng(11)
+    I = g.uniform(0, 1, (3, 9, 11))
+    It = g.uniform(0, 1, (3, 9, 11))
+    T = g.uniform(0, 1, (9, 11))
+    a = g.uniform(0, 1, (9, 11))
+    L, dI, dA = oracle.alpha_loss(I, T, It, np.ones_like(a), 0.0)
+    assert L == pytest.approx(oracle.mse(I, It), rel=1e-14)
+    np.testing.assert_allclose(dI, oracle.mse_grad(I, It), rtol=1e-14)
+    assert np.all(dA == 0)
+    a[a < 0.3] = 0.0                           # some pixels outside the object
+    L, dI, dA = oracle.alpha_loss(I, T, It, a, 0.3)
+    assert np.all(dI[:, a == 0] == 0)
+    h = 1e-6
+    for (c, y, x) in [(0, 2, 3), (2, 8, 10), (1, 0, 0)]:
+        Ip, Im = I.copy(), I.copy()
+        Ip[c, y, x] += h
+        Im[c, y, x] -= h
+        fd = (oracle.alpha_loss(Ip, T, It, a, 0.3)[0] - oracle.alpha_loss(Im, T, It, a, 0.3)[0]) / (2 * h)
+        assert fd == pytest.approx(dI[c, y, x], rel=1e-6, abs=1e-12)
+    for (y, x) in [(1, 1), (4, 7), (8, 0)]:
+        # I_alpha = 1 - T: dL/dI_alpha = -dL/dT
+        Tp, Tm = T.copy(), T.copy()
+        Tp[y, x] += h
+        Tm[y, x] -= h
+        fd = (oracle.alpha_loss(I, Tp, It, a, 0.3)[0] - oracle.alpha_loss(I, Tm, It, a, 0.3)[0]) / (2 * h)
+        assert -fd == pytest.approx(dA[y, x], rel=1e-6, abs=1e-12)

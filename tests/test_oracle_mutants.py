@@ -34,6 +34,8 @@ MUTANTS = {
                              "const double d = (double)P[(size_t)yy * W + xx];"),
     "base_probability_dropped": ("const double w = 0.1 + 0.9 * lv[p];", "const double w = lv[p];"),
     "scale_rule_reversed": ("o[2] = s_max - (s_max - s_min) * lv[p];", "o[2] = s_min + (s_max - s_min) * lv[p];"),
+    "mask_ignored": ("Q[p + 1] = Q[p] + (mask && !(mask[p] > 0.0f) ? 0 : (int64_t)floor(w * 1048576.0));",
+                     "Q[p + 1] = Q[p] + (int64_t)floor(w * 1048576.0);"),
 }
 
 
