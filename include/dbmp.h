@@ -407,6 +407,9 @@ int32_t dbmp_blur_bitmaps(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
  * caller's seeded generator).  The paper fixes nu = -2 in its text and lists
  * v_init_bias = -4 in Tab. S1; nu is an argument here.
  *   image_dev    float32 3 x H x W planar, values in [0, 1] (read only)
+ *   mask_dev     float32 H x W or NULL: the spatially constrained variant (Sec.
+ *                3.3.2) draws only pixels with mask > 0 (the target's alpha); an
+ *                empty mask draws nothing and leaves params_dev untouched
  *   u_pos_dev, u_theta_dev   double [N] in [0, 1);  n_color_dev  double [N][3]
  *   scratch_dev  dbmp_structure_init_scratch_bytes(H, W) bytes, 256-byte aligned,
  *                caller-owned; overwritten
@@ -415,10 +418,35 @@ int32_t dbmp_blur_bitmaps(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
  * required pointer, a misaligned scratch, s_min > s_max or sigma_c < 0.
  * Stream-ordered, no allocation, capturable in a CUDA graph. */
 int32_t dbmp_structure_init_scratch_bytes(int32_t H, int32_t W, size_t *bytes);
-int32_t dbmp_structure_init(const float *image_dev, int32_t H, int32_t W, int32_t N, const double *u_pos_dev,
-                            const double *u_theta_dev, const double *n_color_dev, double s_min, double s_max,
-                            double sigma_c, double nu, void *scratch_dev, float *params_dev, double *nlv_dev,
-                            dbmp_stream_t stream);
+int32_t dbmp_structure_init(const float *image_dev, const float *mask_dev, int32_t H, int32_t W, int32_t N,
+                            const double *u_pos_dev, const double *u_theta_dev, const double *n_color_dev,
+                            double s_min, double s_max, double sigma_c, double nu, void *scratch_dev,
+                            float *params_dev, double *nlv_dev, dbmp_stream_t stream);
+
+/* Re-initialisation of transparent primitives (Sec. 3.3.2; Sec. S3 "Re-initialization
+ * Mechanism": opacity sigmoid(nu) below prune_threshold = 0.3, every 50 iterations
+ * after a warm-up).  Every primitive i of params_dev (in/out, [N][8]) with
+ * sigmoid(nu_i) < threshold (evaluated in FP64) takes draw i of
+ * dbmp_structure_init with the same arguments; its Adam moments adam_m_dev /
+ * adam_v_dev ([N][8], nullable) are zeroed (a reading: the redrawn primitive
+ * starts afresh) and *count_dev (int32, nullable, not reset here) is incremented.
+ * threshold in [0, 1].  Other arguments, errors and ordering as dbmp_structure_init. */
+int32_t dbmp_structure_reinit(const float *image_dev, const float *mask_dev, int32_t H, int32_t W, int32_t N,
+                              const double *u_pos_dev, const double *u_theta_dev, const double *n_color_dev,
+                              double s_min, double s_max, double sigma_c, double nu, double threshold,
+                              void *scratch_dev, float *params_dev, float *adam_m_dev, float *adam_v_dev,
+                              int32_t *count_dev, dbmp_stream_t stream);
+
+/* Spatially constrained loss (Eq. 9, Sec. 3.3.2), both squared norms read as means:
+ *   L = sum_p [a*_p > 0] |I_p - I*_p|^2 / (3 n) + lambda_alpha sum_p (I_alpha,p - a*_p)^2 / n
+ * with I_alpha = 1 - T_N (T_final of the forward), n = n_pix pixels; writes
+ * dL/dI (3 planes) and dL/dI_alpha, the inputs of dbmp_render_bwd, and overwrites
+ * *loss_dev (device double).  The paper weights the opacity term 0.3 (Sec. S3).
+ *   image_dev, target_dev  float32 3 x n planar;  T_final_dev, target_alpha_dev
+ *   float32 n;  outputs float32 3 x n and n.  lambda_alpha >= 0.  Stream-ordered. */
+int32_t dbmp_alpha_loss_grad(const float *image_dev, const float *T_final_dev, const float *target_dev,
+                             const float *target_alpha_dev, int64_t n_pix, float lambda_alpha, float *dL_dimage_dev,
+                             float *dL_dalpha_dev, double *loss_dev, dbmp_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
 /* Forward render without device allocation                                   */

@@ -720,10 +720,10 @@ int32_t dbmp_structure_init_scratch_bytes(int32_t H, int32_t W, size_t *bytes) {
     return DBMP_OK;
 }
 
-int32_t dbmp_structure_init(const float *image_dev, int32_t H, int32_t W, int32_t N, const double *u_pos_dev,
-                            const double *u_theta_dev, const double *n_color_dev, double s_min, double s_max,
-                            double sigma_c, double nu, void *scratch_dev, float *params_dev, double *nlv_dev,
-                            dbmp_stream_t stream) {
+namespace {
+int32_t check_structure_args(const float *image_dev, int32_t H, int32_t W, int32_t N, const double *u_pos_dev,
+                             const double *u_theta_dev, const double *n_color_dev, double s_min, double s_max,
+                             double sigma_c, void *scratch_dev, float *params_dev) {
     if (H < 1 || W < 1 || (int64_t)H * W > 2147483647LL)
         return fail(DBMP_ERR_INVALID_ARG, "H, W must be >= 1 with H W < 2^31");
     if (N < 0) return fail(DBMP_ERR_INVALID_ARG, "N must be >= 0");
@@ -732,8 +732,49 @@ int32_t dbmp_structure_init(const float *image_dev, int32_t H, int32_t W, int32_
         return fail(DBMP_ERR_INVALID_ARG, "random draws / params is NULL");
     if (((uintptr_t)scratch_dev) & 255) return fail(DBMP_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
     if (!(s_min <= s_max) || !(sigma_c >= 0.0)) return fail(DBMP_ERR_INVALID_ARG, "need s_min <= s_max, sigma_c >= 0");
-    DBMP_CUDA(launch_structure_init(image_dev, H, W, N, u_pos_dev, u_theta_dev, n_color_dev, s_min, s_max, sigma_c,
-                                    nu, scratch_dev, params_dev, nlv_dev, (cudaStream_t)stream),
+    return DBMP_OK;
+}
+}  // namespace
+
+int32_t dbmp_structure_reinit(const float *image_dev, const float *mask_dev, int32_t H, int32_t W, int32_t N,
+                              const double *u_pos_dev, const double *u_theta_dev, const double *n_color_dev,
+                              double s_min, double s_max, double sigma_c, double nu, double threshold,
+                              void *scratch_dev, float *params_dev, float *adam_m_dev, float *adam_v_dev,
+                              int32_t *count_dev, dbmp_stream_t stream) {
+    if (int32_t r = check_structure_args(image_dev, H, W, N, u_pos_dev, u_theta_dev, n_color_dev, s_min, s_max,
+                                         sigma_c, scratch_dev, params_dev))
+        return r;
+    if (!(threshold >= 0.0 && threshold <= 1.0)) return fail(DBMP_ERR_INVALID_ARG, "threshold must be in [0, 1]");
+    DBMP_CUDA(launch_structure_init(image_dev, mask_dev, H, W, N, u_pos_dev, u_theta_dev, n_color_dev, s_min, s_max,
+                                    sigma_c, nu, scratch_dev, params_dev, nullptr, threshold, adam_m_dev,
+                                    adam_v_dev, count_dev, (cudaStream_t)stream),
+              "structure reinit launch");
+    return DBMP_OK;
+}
+
+int32_t dbmp_alpha_loss_grad(const float *image_dev, const float *T_final_dev, const float *target_dev,
+                             const float *target_alpha_dev, int64_t n_pix, float lambda_alpha, float *dL_dimage_dev,
+                             float *dL_dalpha_dev, double *loss_dev, dbmp_stream_t stream) {
+    if (n_pix < 0) return fail(DBMP_ERR_INVALID_ARG, "n_pix must be >= 0");
+    if (!image_dev || !T_final_dev || !target_dev || !target_alpha_dev || !dL_dimage_dev || !dL_dalpha_dev || !loss_dev)
+        return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (!(lambda_alpha >= 0.0f)) return fail(DBMP_ERR_INVALID_ARG, "lambda_alpha must be >= 0");
+    DBMP_CUDA(launch_alpha_loss(image_dev, T_final_dev, target_dev, target_alpha_dev, n_pix, lambda_alpha,
+                                dL_dimage_dev, dL_dalpha_dev, loss_dev, (cudaStream_t)stream),
+              "alpha loss launch");
+    return DBMP_OK;
+}
+
+int32_t dbmp_structure_init(const float *image_dev, const float *mask_dev, int32_t H, int32_t W, int32_t N,
+                            const double *u_pos_dev, const double *u_theta_dev, const double *n_color_dev,
+                            double s_min, double s_max, double sigma_c, double nu, void *scratch_dev,
+                            float *params_dev, double *nlv_dev, dbmp_stream_t stream) {
+    if (int32_t r = check_structure_args(image_dev, H, W, N, u_pos_dev, u_theta_dev, n_color_dev, s_min, s_max,
+                                         sigma_c, scratch_dev, params_dev))
+        return r;
+    DBMP_CUDA(launch_structure_init(image_dev, mask_dev, H, W, N, u_pos_dev, u_theta_dev, n_color_dev, s_min, s_max,
+                                    sigma_c, nu, scratch_dev, params_dev, nlv_dev, -1.0, nullptr, nullptr, nullptr,
+                                    (cudaStream_t)stream),
               "structure init launch");
     return DBMP_OK;
 }

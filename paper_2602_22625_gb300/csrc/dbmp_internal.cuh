@@ -181,10 +181,15 @@ cudaError_t launch_blur(const float *in, float *out, int32_t n_bmp, int32_t Hb, 
                         cudaStream_t st);
 // Structure-aware initialisation (init.cu).
 size_t structure_init_scratch(int64_t n_pixels);
-cudaError_t launch_structure_init(const float *image, int32_t H, int32_t W, int32_t N, const double *u_pos,
-                                  const double *u_theta, const double *n_color, double s_min, double s_max,
-                                  double sigma_c, double nu, void *scratch, float *params, double *nlv_out,
-                                  cudaStream_t st);
+cudaError_t launch_structure_init(const float *image, const float *mask, int32_t H, int32_t W, int32_t N,
+                                  const double *u_pos, const double *u_theta, const double *n_color, double s_min,
+                                  double s_max, double sigma_c, double nu, void *scratch, float *params,
+                                  double *nlv_out, double reinit_thr, float *adam_m, float *adam_v,
+                                  int32_t *count, cudaStream_t st);
+// Spatially constrained loss, Eq. 9 (optim.cu).
+cudaError_t launch_alpha_loss(const float *image, const float *T_final, const float *target,
+                              const float *target_alpha, int64_t n_pix, float lam, float *dL_dimage,
+                              float *dL_dalpha, double *loss, cudaStream_t st);
 // Binning slab geometry.  One CTA of min(2^chunk_log2, 1024) threads takes a chunk
 // in passes of one primitive per thread and covers a slab of tile rows.  Shared
 // memory: one mask word per (tile column, warp) and per (slab row, warp), plus a

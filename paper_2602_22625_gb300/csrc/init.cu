@@ -10,7 +10,9 @@
 //   k_seg_*     exclusive prefix sum of the integer weights (exact, so the draw of a
 //               pixel does not depend on the order of a parallel sum);
 //   k_sample    per primitive: the pixel whose cumulative-weight interval holds
-//               floor(u Q_total), and its initial parameters.
+//               floor(u Q_total), and its initial parameters (or, re-initialising,
+//               only for primitives whose opacity sigmoid(nu) fell below a threshold).
+// An optional mask (the target's alpha) restricts the draws to its support.
 // Every FP64 operation that decides a pixel is explicitly rounded and taken in a
 // fixed order (the window row-major, mean first), so the draws are reproducible
 // bit for bit by any implementation of the same definition.
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kLvTile * kLvTile) k_lvar(const float *__restr
 }
 
 __global__ void k_qweights(double *__restrict__ lv, int64_t n, const unsigned long long *minmax,
-                           int32_t *__restrict__ q, double *__restrict__ nlv_out) {
+                           const float *__restrict__ mask, int32_t *__restrict__ q, double *__restrict__ nlv_out) {
     const double mn = __longlong_as_double((long long)minmax[0]);
     const double mx = __longlong_as_double((long long)minmax[1]);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
@@ -99,7 +101,8 @@ __global__ void k_qweights(double *__restrict__ lv, int64_t n, const unsigned lo
         lv[p] = nlv;
         if (nlv_out) nlv_out[p] = nlv;
         const double w = __dadd_rn(0.1, __dmul_rn(0.9, nlv));
-        q[p] = (int32_t)floor(__dmul_rn(w, 1048576.0));   // w in [0.1, 1]: q <= 2^20
+        // w in [0.1, 1]: q <= 2^20; pixels outside the mask are never drawn
+        q[p] = (mask && !(mask[p] > 0.0f)) ? 0 : (int32_t)floor(__dmul_rn(w, 1048576.0));
     }
 }
 
@@ -159,14 +162,29 @@ __global__ void k_seg_scan(const int32_t *__restrict__ q, int64_t n, int64_t seg
     }
 }
 
+// reinit_thr < 0: every primitive takes its draw; else only those with
+// sigmoid(nu_i) < reinit_thr (evaluated in FP64), whose Adam moments (if given) are
+// cleared and which are counted in *count.
 __global__ void k_sample(const float *__restrict__ image, int32_t H, int32_t W, int32_t N,
                          const double *__restrict__ u_pos, const double *__restrict__ u_theta,
                          const double *__restrict__ n_color, double s_min, double s_max, double sigma_c, double nu,
-                         const double *__restrict__ nlv, const int64_t *__restrict__ Q, float *__restrict__ params) {
+                         const double *__restrict__ nlv, const int64_t *__restrict__ Q, float *__restrict__ params,
+                         double reinit_thr, float *__restrict__ adam_m, float *__restrict__ adam_v,
+                         int32_t *__restrict__ count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t n = (int64_t)H * W;
     const int64_t total = Q[n];
+    if (total == 0) return;   // empty mask: nothing is drawn
+    if (reinit_thr >= 0.0) {
+        const double sig = 1.0 / (1.0 + exp(-(double)params[8 * (int64_t)i + 4]));
+        if (!(sig < reinit_thr)) return;
+        for (int j = 0; j < 8; ++j) {
+            if (adam_m) adam_m[8 * (int64_t)i + j] = 0.0f;
+            if (adam_v) adam_v[8 * (int64_t)i + j] = 0.0f;
+        }
+        if (count) atomicAdd(count, 1);
+    }
     const int64_t t = (int64_t)floor(__dmul_rn(u_pos[i], (double)total));
     int64_t lo = 0, hi = n - 1;   // largest p with Q[p] <= t
     while (lo < hi) {
@@ -196,10 +214,11 @@ size_t structure_init_scratch(int64_t n) {
            align256(sizeof(int64_t) * kScanMaxSegs) + align256(2 * sizeof(unsigned long long));
 }
 
-cudaError_t launch_structure_init(const float *image, int32_t H, int32_t W, int32_t N, const double *u_pos,
-                                  const double *u_theta, const double *n_color, double s_min, double s_max,
-                                  double sigma_c, double nu, void *scratch, float *params, double *nlv_out,
-                                  cudaStream_t st) {
+cudaError_t launch_structure_init(const float *image, const float *mask, int32_t H, int32_t W, int32_t N,
+                                  const double *u_pos, const double *u_theta, const double *n_color, double s_min,
+                                  double s_max, double sigma_c, double nu, void *scratch, float *params,
+                                  double *nlv_out, double reinit_thr, float *adam_m, float *adam_v,
+                                  int32_t *count, cudaStream_t st) {
     const int64_t n = (int64_t)H * W;
     char *b = static_cast<char *>(scratch);
     double *lv = reinterpret_cast<double *>(b);
@@ -215,7 +234,7 @@ cudaError_t launch_structure_init(const float *image, int32_t H, int32_t W, int3
     const dim3 g((W + kLvTile - 1) / kLvTile, (H + kLvTile - 1) / kLvTile);
     k_lvar<<<g, dim3(kLvTile, kLvTile), 0, st>>>(image, H, W, lv, minmax);
     const int64_t qblocks = (n + 255) / 256;
-    k_qweights<<<(int)(qblocks < 152 * 16 ? qblocks : 152 * 16), 256, 0, st>>>(lv, n, minmax, q, nlv_out);
+    k_qweights<<<(int)(qblocks < 152 * 16 ? qblocks : 152 * 16), 256, 0, st>>>(lv, n, minmax, mask, q, nlv_out);
     const int64_t want = (n + 4095) / 4096;
     const int32_t segs = (int32_t)(want < 1 ? 1 : (want > kScanMaxSegs ? kScanMaxSegs : want));
     const int64_t seg = (n + segs - 1) / segs;
@@ -224,7 +243,7 @@ cudaError_t launch_structure_init(const float *image, int32_t H, int32_t W, int3
     k_seg_scan<<<segs, 256, 0, st>>>(q, n, seg, bsum, Q);
     if (N > 0)
         k_sample<<<(N + 255) / 256, 256, 0, st>>>(image, H, W, N, u_pos, u_theta, n_color, s_min, s_max, sigma_c,
-                                                  nu, lv, Q, params);
+                                                  nu, lv, Q, params, reinit_thr, adam_m, adam_v, count);
     return cudaGetLastError();
 }
 

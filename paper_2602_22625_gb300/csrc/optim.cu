@@ -109,6 +109,43 @@ __global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg,
     }
 }
 
+// Eq. 9 (Sec. 3.3.2), both squared norms read as means: over the pixels p (planar
+// images of n1 pixels, n3 = 3 n1 values), m_p = [alpha*_p > 0],
+//   L = sum m_p (I - I*)^2 / n3 + lam sum (I_alpha - alpha*)^2 / n1,  I_alpha = 1 - T_N,
+//   dL/dI = 2 m_p (I - I*) / n3,  dL/dI_alpha = 2 lam (I_alpha - alpha*) / n1.
+// Per-thread sums are compensated (acc_sq), cross-thread sums FP64.
+__global__ void k_alpha_loss(const float *__restrict__ I, const float *__restrict__ T, const float *__restrict__ It,
+                             const float *__restrict__ at, int64_t n1, float lam, float *__restrict__ dI,
+                             float *__restrict__ dA, double *loss) {
+    __shared__ double red[32];
+    const float s3 = (float)(2.0 / (3.0 * (double)n1)), s1 = (float)(2.0 * (double)lam / (double)n1);
+    float c0 = 0.0f, e0 = 0.0f, c1 = 0.0f, e1 = 0.0f;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n1; p += (int64_t)gridDim.x * blockDim.x) {
+        const float a = at[p];
+        const bool in = a > 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float d = in ? I[ch * n1 + p] - It[ch * n1 + p] : 0.0f;
+            dI[ch * n1 + p] = s3 * d;
+            acc_sq(d, c0, e0);
+        }
+        const float r = (1.0f - T[p]) - a;
+        dA[p] = s1 * r;
+        acc_sq(r, c1, e1);
+    }
+    double acc = ((double)c0 + (double)e0) / (3.0 * (double)n1) + (double)lam * ((double)c1 + (double)e1) / (double)n1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(loss, acc);
+    }
+}
+
 struct AdamArgs {
     float lr, gamma, beta1, beta2, eps;
     float gains[8];
@@ -158,6 +195,16 @@ cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, 
                             double *loss, cudaStream_t st) {
     cudaMemsetAsync(loss, 0, sizeof(double), st);
     if (n > 0) k_mse<<<grid_for((n + 3) / 4, 256), 256, 0, st>>>(image, target, n, dL, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_loss(const float *image, const float *T_final, const float *target,
+                              const float *target_alpha, int64_t n_pix, float lam, float *dL_dimage,
+                              float *dL_dalpha, double *loss, cudaStream_t st) {
+    cudaMemsetAsync(loss, 0, sizeof(double), st);
+    if (n_pix > 0)
+        k_alpha_loss<<<grid_for(n_pix, 256), 256, 0, st>>>(image, T_final, target, target_alpha, n_pix, lam,
+                                                            dL_dimage, dL_dalpha, loss);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ EXPORTS = (
     "dbmp_render_fwd_static", "dbmp_gemm_bf16", "dbmp_proposer_num_params", "dbmp_proposer_create",
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
-    "dbmp_blur_bitmaps", "dbmp_bin_stats",
+    "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
 )
 
 
@@ -141,8 +141,12 @@ def load(build_if_missing: bool = True):
         "dbmp_blur_bitmaps": (_i32, [_vp, _i32, _i32, _i32, _f32, _vp, _vp]),
         "dbmp_bin_stats": (_i32, [_vp, _vp, ctypes.POINTER(DbmpBinStats)]),
         "dbmp_structure_init_scratch_bytes": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
-        "dbmp_structure_init": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+        "dbmp_structure_init": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp]),
+        "dbmp_structure_reinit": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp,
+                                         _vp, _vp, _vp, _vp, _vp]),
+        "dbmp_alpha_loss_grad": (_i32, [_vp, _vp, _vp, _vp, _i64, _f32, _vp, _vp, _vp, _vp]),
         "dbmp_render_fwd_static": (_i32, [_i32, _i32, _vp, _vp, _i32, _vp, _i32, _i32, _i32, _f32,
                                           ctypes.POINTER(DbmpBackground), _f32, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(DbmpDeviceStatus)]),
@@ -382,16 +386,36 @@ def dbmp_structure_init_scratch_bytes(H, W):
 
 
 def dbmp_structure_init(image, u_pos, u_theta, n_color, s_min, s_max, sigma_c, nu, params, nlv=None,
-                        scratch=None, stream=None):
+                        scratch=None, mask=None, stream=None):
     """Structure-aware initialisation of params (N, 8) from image (3, H, W) with the
-    given random draws (float64 device tensors).  scratch: a uint8 device tensor of
-    dbmp_structure_init_scratch_bytes(H, W) bytes (allocated here when None)."""
+    given random draws (float64 device tensors); mask (H, W) restricts the draws.
+    scratch: a uint8 device tensor of dbmp_structure_init_scratch_bytes(H, W) bytes
+    (allocated here when None)."""
     _, H, W = image.shape
     if scratch is None:
         scratch = torch.empty(dbmp_structure_init_scratch_bytes(H, W), dtype=torch.uint8, device=image.device)
-    _check(load().dbmp_structure_init(_ptr(image), H, W, params.shape[0], _ptr(u_pos), _ptr(u_theta),
+    _check(load().dbmp_structure_init(_ptr(image), _ptr(mask), H, W, params.shape[0], _ptr(u_pos), _ptr(u_theta),
                                       _ptr(n_color), float(s_min), float(s_max), float(sigma_c), float(nu),
                                       _ptr(scratch), _ptr(params), _ptr(nlv), _stream(stream)))
+
+
+def dbmp_structure_reinit(image, u_pos, u_theta, n_color, s_min, s_max, sigma_c, nu, threshold, params,
+                          adam_m=None, adam_v=None, count=None, scratch=None, mask=None, stream=None):
+    """Redraws every primitive of params (N, 8, in place) whose sigmoid(nu) < threshold."""
+    _, H, W = image.shape
+    if scratch is None:
+        scratch = torch.empty(dbmp_structure_init_scratch_bytes(H, W), dtype=torch.uint8, device=image.device)
+    _check(load().dbmp_structure_reinit(_ptr(image), _ptr(mask), H, W, params.shape[0], _ptr(u_pos), _ptr(u_theta),
+                                        _ptr(n_color), float(s_min), float(s_max), float(sigma_c), float(nu),
+                                        float(threshold), _ptr(scratch), _ptr(params), _ptr(adam_m), _ptr(adam_v),
+                                        _ptr(count), _stream(stream)))
+
+
+def dbmp_alpha_loss_grad(image, T_final, target, target_alpha, lambda_alpha, dL_dimage, dL_dalpha, loss,
+                         stream=None):
+    _check(load().dbmp_alpha_loss_grad(_ptr(image), _ptr(T_final), _ptr(target), _ptr(target_alpha),
+                                       T_final.numel(), float(lambda_alpha), _ptr(dL_dimage), _ptr(dL_dalpha),
+                                       _ptr(loss), _stream(stream)))
 
 
 def dbmp_blur_bitmaps(texels, sigma, out=None, stream=None):
