@@ -13,6 +13,8 @@
 //                                                          split-K with fp32 atomics)
 //   dgrad    dX_{l-1} = col2im(dZ_l W_l) masked by X_{l-1} > 0
 // Weights are FP32 masters with BF16 copies; Adam updates the masters.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -124,6 +126,14 @@ __global__ void k_colsum(const T *__restrict__ in, int32_t M, int32_t N, float *
         for (int k = 0; k < 8; ++k) s += part[k][threadIdx.x];
         atomicAdd(out + n, s);
     }
+}
+
+// Row-blocks of k_colsum: about 8 CTAs per SM over all column groups, each CTA
+// taking at least 64 rows.
+inline int colsum_rows(int64_t M, int col_groups) {
+    const int64_t want = (8 * 152 + col_groups - 1) / col_groups;
+    const int64_t cap = (M + 63) / 64;
+    return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
 __global__ void k_mask_to_bf16(const float *__restrict__ dX, const uint16_t *__restrict__ X, int64_t n,
@@ -398,7 +408,7 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
     transpose(c.X[5], M6, 256, c.colT, st);
     cudaError_t e = gemm(c.dzT, M6, c.colT, M6, 64, 256, M6, GEMM_ATOMIC_F32, c.grad + L[5].w_off, nullptr, 256,
                          nullptr, split_for(64, 256, M6), c.status, st);
-    k_colsum<float><<<dim3(2, 64), dim3(32, 8), 0, st>>>(c.dO, M6, 64, c.grad + L[5].b_off);
+    k_colsum<float><<<dim3(2, colsum_rows(M6, 2)), dim3(32, 8), 0, st>>>(c.dO, M6, 64, c.grad + L[5].b_off);
     transpose(c.wbf + L[5].w_off, 64, 256, c.wT + L[5].w_off, st);
     if (e == cudaSuccess)
         e = gemm(c.dz, 64, c.wT + L[5].w_off, 64, M6, 256, 64, GEMM_STORE_F32, c.dx, nullptr, 256, nullptr, 1,
@@ -412,7 +422,8 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
         transpose(c.col, M, K, c.colT, st);
         e = gemm(c.dzT, M, c.colT, M, Co, K, M, GEMM_ATOMIC_F32, c.grad + L[l].w_off, nullptr, K, nullptr,
                  split_for(Co, K, M), c.status, st);
-        k_colsum<uint16_t><<<dim3((Co + 31) / 32, 64), dim3(32, 8), 0, st>>>(c.dz, M, Co, c.grad + L[l].b_off);
+        k_colsum<uint16_t><<<dim3((Co + 31) / 32, colsum_rows(M, (Co + 31) / 32)), dim3(32, 8), 0, st>>>(
+            c.dz, M, Co, c.grad + L[l].b_off);
         if (l == 0 || e != cudaSuccess) break;
         transpose(c.wbf + L[l].w_off, Co, K, c.wT + L[l].w_off, st);
         e = gemm(c.dz, Co, c.wT + L[l].w_off, Co, M, K, Co, GEMM_STORE_F32, c.dx, nullptr, K, nullptr, 1, c.status,

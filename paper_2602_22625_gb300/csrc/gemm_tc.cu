@@ -1,23 +1,34 @@
-// BF16 GEMM on the sm_103a tensor cores (tcgen05 + TMEM), FP32 accumulation.
+// BF16 GEMM on the sm_103a tensor cores (tcgen05 + TMEM + TMA), FP32 accumulation.
 //
 //   C[m][n] (op)= sum_k A[m][k] * B[n][k]      A: M x K, B: N x K, both K-contiguous BF16
 //
-// One CTA computes a 128 x BN tile.  128 threads stream K in stages of 64 with
-// cp.async (16-byte chunks, zero-filled outside M / N) into shared memory laid out
-// as the canonical no-swizzle K-major core-matrix layout: a core matrix is 8 rows
-// x 16 bytes, core matrices adjacent in K are 128 bytes apart (leading byte offset)
-// and those adjacent in M/N 1024 bytes apart (stride byte offset).  One elected
-// thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a TMEM
-// accumulator of BN fp32 columns and commits each stage to an mbarrier, so loads of
-// later stages overlap the tensor-core work.  The epilogue reads TMEM with
-// tcgen05.ld (32 lanes x 32 bit per warp), applies the requested operation and
-// writes C.  Split-K over gridDim.z adds partial tiles with fp32 atomics.
+// One CTA computes a 128 x BN tile (BN = 32 ... 256) with three warp roles:
+//   warp 0      producer: one thread issues the TMA tensor copies of the A and B
+//               K-slabs (64 wide) into a ring of shared-memory stages, each stage
+//               announced on its `full` mbarrier with the bytes it expects;
+//   warp 1      allocates BN TMEM columns; one thread issues tcgen05.mma (M = 128,
+//               N = BN, K = 16 per instruction) for each stage and commits it to the
+//               stage's `empty` mbarrier, which returns the slot to the producer;
+//               a last commit signals that the accumulator is complete;
+//   warps 2-5   epilogue: each reads the TMEM lane quarter it may access
+//               (32 (warp % 4) ...) with tcgen05.ld, applies the mode, writes C.
+// TMA writes each stage in the 128-byte swizzled K-major layout (rows of 64 bf16,
+// eight-row atoms of 1024 bytes), which the shared-memory matrix descriptors
+// describe with layout type SWIZZLE_128B; one MMA's K step of 16 elements advances
+// the descriptor's start address by 32 bytes.  Rows past M or N are zero-filled by
+// the tensor copy; K must be a multiple of 64.  Split-K over gridDim.z adds
+// partial tiles with fp32 atomics.
 //
-// Every mbarrier wait is bounded; a wait that gives up sets the status flag, the
-// CTA drains its own copies, frees its TMEM and returns.
+// Every mbarrier wait is bounded.  A wait that gives up sets the status flag; the
+// producer still waits (bounded) for the copies it issued, the accumulator's last
+// commit is still made, and TMEM is freed before the CTA exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "dbmp_internal.cuh"
 
@@ -27,24 +38,28 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kStages = 3;
+constexpr int kThreads = 192;
 constexpr uint32_t kWaitLimit = 1u << 26;  // polls before a wait gives up
+
+template <int BN>
+struct TileCfg {
+    static constexpr int A_BYTES = kBM * kBK * 2;   // 16 KB
+    static constexpr int B_BYTES = BN * kBK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = 196608 / STAGE > 8 ? 8 : 196608 / STAGE;
+    static constexpr int SMEM = STAGES * STAGE + 1024;   // + alignment slack
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 // Waits for the phase of parity `parity` to complete; false if it gave up.
@@ -61,18 +76,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// 2-D tensor copy global -> shared (coordinates: x along K, y along rows),
+// completing `bar`'s transaction count.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// Shared-memory matrix descriptor: no swizzle, K-major, version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor (sm_100 family): K-major, 128-byte swizzle, eight-
+// row atoms 1024 bytes apart (stride byte offset); the leading byte offset is not
+// used by swizzled K-major layouts and is set to one 16-byte unit.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version
-    // base offset 0, lbo mode 0, layout type 0 (no swizzle)
+    d |= (uint64_t)1 << 16;                      // leading byte offset: 16 B
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 1024 B
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // layout: 128-byte swizzle
     return d;
 }
 
@@ -112,39 +138,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Byte offset of row r, 16-byte K-chunk kc inside one operand stage.
-__device__ __forceinline__ uint32_t core_off(int r, int kc) {
-    return (uint32_t)((r >> 3) * 1024 + kc * 128 + (r & 7) * 16);
-}
-
 template <int BN>
-__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    using C = TileCfg<BN>;
+    constexpr int S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[kStages];
+    __shared__ __align__(8) uint64_t full[S], empty[S], acc_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
-    constexpr int A_BYTES = kBM * kBK * 2;   // 16 KB
-    constexpr int B_BYTES = BN * kBK * 2;
-    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    // align the dynamic buffer to 1024 bytes
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     const uint32_t sbase = smem_u32(smem);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    (void)STAGE_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     const int kt_total = g.K / kBK;
     const int kt_per = (kt_total + gridDim.z - 1) / gridDim.z;
     const int kt0 = blockIdx.z * kt_per;
-    const int T = min(kt_per, kt_total - kt0);
+    const int T = max(0, min(kt_per, kt_total - kt0));
 
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(&acc_done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
                      "r"((uint32_t)BN)
                      : "memory");
@@ -155,143 +179,164 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    auto load_stage = [&](int slot, int kt) {
-        const uint32_t sa = sbase + slot * STAGE_BYTES, sb = sa + A_BYTES;
-        const int kbase = (kt0 + kt) * kBK;
-        // A: 128 rows x 8 chunks
-        for (int c = tid; c < kBM * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7;
-            const int m = m0 + r;
-            const bool ok = m < g.M;
-            const __nv_bfloat16 *src =
-                reinterpret_cast<const __nv_bfloat16 *>(g.A) + (size_t)(ok ? m : 0) * g.lda + kbase + kc * 8;
-            cp_async16_zfill(sa + core_off(r, kc), src, ok);
-        }
-        for (int c = tid; c < BN * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7;
-            const int n = n0 + r;
-            const bool ok = n < g.N;
-            const __nv_bfloat16 *src =
-                reinterpret_cast<const __nv_bfloat16 *>(g.B) + (size_t)(ok ? n : 0) * g.ldb + kbase + kc * 8;
-            cp_async16_zfill(sb + core_off(r, kc), src, ok);
-        }
-    };
-
-    bool ok = T > 0;
-    if (ok) {
-        for (int t = 0; t < kStages - 1; ++t) {
-            if (t < T) load_stage(t, t);
-            cp_async_commit();
-        }
-        const uint32_t idesc = instr_desc<BN>();
-        for (int t = 0; t < T; ++t) {
-            const int s = t % kStages;
-            const int tp = t + kStages - 1;
-            if (tp < T) {
-                if (t >= 1) {
-                    // the slot being refilled was read by MMA t-1
-                    if (!mbar_wait(smem_u32(&mbar[(t - 1) % kStages]), ((t - 1) / kStages) & 1)) abort_flag = 1;
-                }
-                load_stage(tp % kStages, tp);
-            }
-            cp_async_commit();
-            cp_async_wait<kStages - 1>();
-            fence_async_smem();
-            __syncthreads();
-            if (abort_flag) {
-                ok = false;
+    if (warp == 0 && lane == 0 && T > 0) {
+        // ---- producer ----
+        int issued = 0;
+        for (int i = 0; i < T; ++i) {
+            const int s = i % S;
+            if (i >= S && !mbar_wait(smem_u32(&empty[s]), ((i / S) & 1) ^ 1)) {
+                abort_flag = 1;
                 break;
             }
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t sa = sbase + s * STAGE_BYTES, sb = sa + A_BYTES;
-#pragma unroll
-                for (int ks = 0; ks < kBK / 16; ++ks) {
-                    const uint64_t ad = smem_desc(sa + ks * 256, 128, 1024);
-                    const uint64_t bd = smem_desc(sb + ks * 256, 128, 1024);
-                    mma_bf16(tmem, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-                }
-                mma_commit(smem_u32(&mbar[s]));
-            }
+            if (*(volatile int *)&abort_flag) break;
+            const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);
+            mbar_expect_tx(fb, C::STAGE);
+            tma_load_2d(sa, &tmA, (kt0 + i) * kBK, m0, fb);
+            tma_load_2d(sa + C::A_BYTES, &tmB, (kt0 + i) * kBK, n0, fb);
+            issued = i + 1;
         }
-        if (ok && !mbar_wait(smem_u32(&mbar[(T - 1) % kStages]), ((T - 1) / kStages) & 1)) abort_flag = 1;
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    ok = ok && !abort_flag;  // uniform over the CTA: the epilogue's TMEM loads are warp-collective
-    if (!ok && T > 0 && tid == 0 && g.status) atomicExch(g.status, (int)DBMP_ERR_TIMEOUT);
-    tc_fence_after();
-
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tmem_ld16(trow + c0, v);
-            if (row >= g.M) continue;
-            const int nb = n0 + c0;
-            if (g.mode == GEMM_STORE_F32 || g.mode == GEMM_BIAS_F32) {
-                float *out = g.Cf + (size_t)row * g.ldc + nb;
+        // every issued copy lands before the CTA can exit
+        for (int i = issued > S ? issued - S : 0; i < issued; ++i)
+            if (!mbar_wait(smem_u32(&full[i % S]), (i / S) & 1)) abort_flag = 1;
+    } else if (warp == 1 && lane == 0 && T > 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = instr_desc<BN>();
+        for (int i = 0; i < T; ++i) {
+            const int s = i % S;
+            if (!mbar_wait(smem_u32(&full[s]), (i / S) & 1)) {
+                abort_flag = 1;
+                break;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            tc_fence_after();
+            const uint32_t sa = sbase + s * C::STAGE, sb = sa + C::A_BYTES;
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (nb + i < g.N) out[i] = v[i] + (g.mode == GEMM_BIAS_F32 ? g.bias[nb + i] : 0.0f);
-            } else if (g.mode == GEMM_ATOMIC_F32) {
-                float *out = g.Cf + (size_t)row * g.ldc + nb;
+            for (int kk = 0; kk < kBK / 16; ++kk)
+                mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(smem_u32(&empty[s]));
+        }
+        mma_commit(smem_u32(&acc_done));   // arrives once every issued MMA has completed
+    } else if (warp >= 2) {
+        // ---- epilogue ----
+        bool ok = T > 0 && mbar_wait(smem_u32(&acc_done), 0);
+        ok = __all_sync(0xffffffffu, ok);
+        ok = ok && !*(volatile int *)&abort_flag;
+        ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+        tc_fence_after();
+        if (ok) {
+            const int q = warp & 3;                        // TMEM lanes 32 q .. 32 q + 31
+            const int row = m0 + q * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(trow + c0, v);
+                if (row >= g.M) continue;
+                const int nb = n0 + c0;
+                const bool full16 = nb + 16 <= g.N;
+                if (g.mode == GEMM_STORE_F32 || g.mode == GEMM_BIAS_F32) {
+                    float *out = g.Cf + (size_t)row * g.ldc + nb;
+                    if (g.mode == GEMM_BIAS_F32) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (nb + i < g.N) atomicAdd(out + i, v[i]);
-            } else {  // GEMM_BIAS_RELU_BF16
-                __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + (size_t)row * g.ldc + nb;
-                __align__(16) __nv_bfloat16 h[16];
+                        for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                    }
+                    if (full16 && ((g.ldc & 3) == 0) && ((nb & 3) == 0)) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float b = nb + i < g.N ? g.bias[nb + i] : 0.0f;
-                    h[i] = __float2bfloat16_rn(fmaxf(v[i] + b, 0.0f));
-                }
-                if (nb + 16 <= g.N && ((g.ldc & 7) == 0) && ((nb & 7) == 0)) {
-                    reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
-                    reinterpret_cast<uint4 *>(out)[1] = reinterpret_cast<const uint4 *>(h)[1];
-                } else {
+                        for (int i = 0; i < 4; ++i)
+                            reinterpret_cast<float4 *>(out)[i] =
+                                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (nb + i < g.N) out[i] = v[i];
+                    }
+                } else if (g.mode == GEMM_ATOMIC_F32) {
+                    float *out = g.Cf + (size_t)row * g.ldc + nb;
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        if (nb + i < g.N) out[i] = h[i];
+                        if (nb + i < g.N) atomicAdd(out + i, v[i]);
+                } else {  // GEMM_BIAS_RELU_BF16
+                    __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + (size_t)row * g.ldc + nb;
+                    __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float b = nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                        h[i] = __float2bfloat16_rn(fmaxf(v[i] + b, 0.0f));
+                    }
+                    if (full16 && ((g.ldc & 7) == 0) && ((nb & 7) == 0)) {
+                        reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                        reinterpret_cast<uint4 *>(out)[1] = reinterpret_cast<const uint4 *>(h)[1];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (nb + i < g.N) out[i] = h[i];
+                    }
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (threadIdx.x == 0 && abort_flag && g.status) atomicExch(g.status, (int)DBMP_ERR_TIMEOUT);
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)BN)
                      : "memory");
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+// Tensor map of a rows x K row-major bf16 matrix (row stride ld elements), copied
+// in boxes of 64 (K) x box_rows with the 128-byte swizzle; out-of-range rows read 0.
+bool make_map(CUtensorMap *m, const uint16_t *base, int rows, int K, int ld, int box_rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN>
 cudaError_t launch_gemm_t(const GemmArgs &g, int split_k, cudaStream_t st) {
-    constexpr int smem = kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
-    dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, split_k);
-    k_gemm_tc<BN><<<grid, 128, smem, st>>>(g);
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, g.A, g.M, g.K, g.lda, kBM) || !make_map(&tb, g.B, g.N, g.K, g.ldb, BN))
+        return cudaErrorInvalidValue;
+    const dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, split_k);
+    k_gemm_tma<BN><<<grid, kThreads, TileCfg<BN>::SMEM, st>>>(ta, tb, g);
     return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_gemm_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<BN>::SMEM);
 }
 
 }  // namespace
 
 cudaError_t init_gemm_kernels() {
-    constexpr int s32 = kStages * (kBM * kBK * 2 + 32 * kBK * 2) + 1024;
-    constexpr int s64 = kStages * (kBM * kBK * 2 + 64 * kBK * 2) + 1024;
-    constexpr int s128 = kStages * (kBM * kBK * 2 + 128 * kBK * 2) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (err == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn)) err = cudaErrorNotSupported;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    cudaError_t e = err;
+    if (e == cudaSuccess) e = set_smem<32>();
+    if (e == cudaSuccess) e = set_smem<64>();
+    if (e == cudaSuccess) e = set_smem<128>();
+    if (e == cudaSuccess) e = set_smem<256>();
     return e;
 }
 
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
-    if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1) return cudaErrorInvalidValue;
+    if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
     if (g.N <= 32) return launch_gemm_t<32>(g, split_k, st);
     if (g.N <= 64) return launch_gemm_t<64>(g, split_k, st);
-    return launch_gemm_t<128>(g, split_k, st);
+    if (g.N <= 128) return launch_gemm_t<128>(g, split_k, st);
+    return launch_gemm_t<256>(g, split_k, st);
 }
 
 }  // namespace dbmp

@@ -1,5 +1,6 @@
 """The tcgen05 BF16 GEMM (FP32 accumulation) against float64 matmuls of the same
-bf16 values: ragged M and N, several K, every epilogue mode, split-K."""
+bf16 values: ragged M and N (N up to several 256-wide tiles), K from one stage to
+many trips around the stage ring, every epilogue mode, split-K."""
 import ctypes
 
 import numpy as np
@@ -44,7 +45,7 @@ def operands(M, N, K, seed):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 32, 64), (300, 70, 192), (1000, 256, 512),
-                                   (77, 5, 128), (4096, 64, 2048)])
+                                   (77, 5, 128), (4096, 64, 2048), (512, 600, 1024), (256, 1024, 4096)])
 def test_gemm_store_f32(M, N, K):
     cuda()
     A, B, ref = operands(M, N, K, M + N + K)
