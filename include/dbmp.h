@@ -305,7 +305,9 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
 /* ------------------------------------------------------------------------- */
 /* C[m][n] (op)= sum_k A[m][k] B[n][k] for m < M, n < N, k < K.
  *   A_dev, B_dev  bf16 (raw 16-bit), row-major M x K and N x K (K contiguous),
- *                 16-byte aligned, lda and ldb multiples of 8, K a multiple of 64
+ *                 16-byte aligned, lda and ldb multiples of 8, K a multiple of 64;
+ *                 with mode flag 16 (32) A (B) is given MN-major instead: the
+ *                 K x M (K x N) row-major matrix, lda >= M (ldb >= N)
  *   mode 0: Cf[m][n] = acc            (float32, row stride ldc)
  *   mode 1: Cf[m][n] += acc           (float32 atomics; allows split_k > 1)
  *   mode 2: Cb[m][n] = bf16(max(acc + bias[n], 0))   (bf16, row stride ldc)

@@ -9,9 +9,9 @@
 //
 // Every product is the tcgen05 GEMM of gemm_tc.cu (BF16 operands, FP32 accumulation):
 //   forward  X_l = relu(im2col(X_{l-1}) W_l^T + b_l)   (bias + ReLU fused, bf16 out)
-//   wgrad    dW_l = dZ_l^T im2col(X_{l-1})               (operands transposed to K-major,
+//   wgrad    dW_l = dZ_l^T im2col(X_{l-1})               (both operands read MN-major,
 //                                                          split-K with fp32 atomics)
-//   dgrad    dX_{l-1} = col2im(dZ_l W_l) masked by X_{l-1} > 0
+//   dgrad    dX_{l-1} = col2im(dZ_l W_l) masked by X_{l-1} > 0   (W_l read MN-major)
 // Weights are FP32 masters with BF16 copies; Adam updates the masters.
 #include <algorithm>
 
@@ -89,20 +89,6 @@ __global__ void k_col2im_mask(const float *__restrict__ dcol, const uint16_t *__
             }
         }
         dZ[i] = bf2f(X[i]) > 0.0f ? f2bf(acc) : (uint16_t)0;
-    }
-}
-
-__global__ void k_transpose(const uint16_t *__restrict__ in, int32_t R, int32_t C, uint16_t *__restrict__ out) {
-    __shared__ uint16_t t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < R && c < C) t[k][threadIdx.x] = in[(int64_t)r * C + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (c < C && r < R) out[(int64_t)c * R + r] = t[threadIdx.x][k];
     }
 }
 
@@ -297,7 +283,7 @@ size_t cnn_bytes(int32_t B) {
     size_t b = 4 * sizeof(float) * np + 2 * sizeof(uint16_t) * np;
     for (int l = 0; l < 6; ++l) b += sizeof(uint16_t) * s.X[l];
     b += 2 * sizeof(float) * (size_t)B * 64 * 64 + sizeof(float) * s.dx;
-    b += 2 * sizeof(uint16_t) * s.col + 3 * sizeof(uint16_t) * s.dz + sizeof(int32_t) * 4;
+    b += sizeof(uint16_t) * s.col + 2 * sizeof(uint16_t) * s.dz + sizeof(int32_t) * 4;
     return b;
 }
 
@@ -315,15 +301,12 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
     A((void **)&c.m, sizeof(float) * np);
     A((void **)&c.v, sizeof(float) * np);
     A((void **)&c.wbf, sizeof(uint16_t) * np);
-    A((void **)&c.wT, sizeof(uint16_t) * np);
     for (int l = 0; l < 6; ++l) A((void **)&c.X[l], sizeof(uint16_t) * s.X[l]);
     A((void **)&c.O, sizeof(float) * B * 64 * 64);
     A((void **)&c.dO, sizeof(float) * B * 64 * 64);
     A((void **)&c.dx, sizeof(float) * s.dx);
     A((void **)&c.col, sizeof(uint16_t) * s.col);
-    A((void **)&c.colT, sizeof(uint16_t) * s.col);
     A((void **)&c.dz, sizeof(uint16_t) * s.dz);
-    A((void **)&c.dzT, sizeof(uint16_t) * s.dz);
     A((void **)&c.dzp, sizeof(uint16_t) * s.dz);
     A((void **)&c.status, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(c.status, 0, sizeof(int32_t) * 4);
@@ -334,8 +317,8 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
 }
 
 void cnn_free(CnnBuffers &c) {
-    void *ps[] = {c.theta, c.grad, c.m, c.v, c.wbf, c.wT, c.X[0], c.X[1], c.X[2], c.X[3], c.X[4], c.X[5],
-                  c.O, c.dO, c.dx, c.col, c.colT, c.dz, c.dzT, c.dzp, c.status};
+    void *ps[] = {c.theta, c.grad, c.m, c.v, c.wbf, c.X[0], c.X[1], c.X[2], c.X[3], c.X[4], c.X[5],
+                  c.O, c.dO, c.dx, c.col, c.dz, c.dzp, c.status};
     for (void *p : ps)
         if (p) cudaFree(p);
     c = CnnBuffers{};
@@ -348,16 +331,13 @@ cudaError_t cnn_sync_weights(CnnBuffers &c, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// mode: a GemmMode, plus GEMM_A_MN / GEMM_B_MN when an operand is given MN-major.
 static cudaError_t gemm(const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N, int K, int mode,
                         float *Cf, uint16_t *Cb, int ldc, const float *bias, int split, int32_t *status,
                         cudaStream_t st) {
-    GemmArgs g{A, B, M, N, K, lda, ldb, ldc, mode, Cf, Cb, bias, status};
+    GemmArgs g{A,    B,    M,  N,  K,   lda,  ldb,   ldc, mode & 15, (mode & GEMM_A_MN) != 0, (mode & GEMM_B_MN) != 0,
+               Cf,   Cb,   bias, status};
     return launch_gemm(g, split, st);
-}
-
-static void transpose(const uint16_t *in, int R, int C, uint16_t *out, cudaStream_t st) {
-    dim3 grid((C + 31) / 32, (R + 31) / 32);
-    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, R, C, out);
 }
 
 // Forward of B images (fp32, 3 x 256 x 256 each, concatenated) into c.O.
@@ -403,31 +383,25 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
     const int M6 = B * 64;
     k_head_loss<<<grid1d((int64_t)B * 4096), 256, 0, st>>>(c.O, target_params, B, c.dO, loss);
     k_to_bf16<<<grid1d((int64_t)M6 * 64), 256, 0, st>>>(c.dO, (int64_t)M6 * 64, c.dz);
-    // head: wgrad, bias, dgrad
-    transpose(c.dz, M6, 64, c.dzT, st);
-    transpose(c.X[5], M6, 256, c.colT, st);
-    cudaError_t e = gemm(c.dzT, M6, c.colT, M6, 64, 256, M6, GEMM_ATOMIC_F32, c.grad + L[5].w_off, nullptr, 256,
-                         nullptr, split_for(64, 256, M6), c.status, st);
+    // head: wgrad (dZ^T X5: both operands read MN-major), bias, dgrad (dZ W: W read MN-major)
+    cudaError_t e = gemm(c.dz, 64, c.X[5], 256, 64, 256, M6, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN,
+                         c.grad + L[5].w_off, nullptr, 256, nullptr, split_for(64, 256, M6), c.status, st);
     k_colsum<float><<<dim3(2, colsum_rows(M6, 2)), dim3(32, 8), 0, st>>>(c.dO, M6, 64, c.grad + L[5].b_off);
-    transpose(c.wbf + L[5].w_off, 64, 256, c.wT + L[5].w_off, st);
     if (e == cudaSuccess)
-        e = gemm(c.dz, 64, c.wT + L[5].w_off, 64, M6, 256, 64, GEMM_STORE_F32, c.dx, nullptr, 256, nullptr, 1,
-                 c.status, st);
+        e = gemm(c.dz, 64, c.wbf + L[5].w_off, 256, M6, 256, 64, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, 256,
+                 nullptr, 1, c.status, st);
     k_mask_to_bf16<<<grid1d((int64_t)M6 * 256), 256, 0, st>>>(c.dx, c.X[5], (int64_t)M6 * 256, c.dz);
     for (int l = 4; l >= 0 && e == cudaSuccess; --l) {
         const int H = L[l].hin, Ho = H / 2, M = B * Ho * Ho;
         const int K = (int)L[l].K, Co = L[l].cout;
         k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, H, H, L[l].cin, c.col);
-        transpose(c.dz, M, Co, c.dzT, st);
-        transpose(c.col, M, K, c.colT, st);
-        e = gemm(c.dzT, M, c.colT, M, Co, K, M, GEMM_ATOMIC_F32, c.grad + L[l].w_off, nullptr, K, nullptr,
-                 split_for(Co, K, M), c.status, st);
+        e = gemm(c.dz, Co, c.col, K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off, nullptr,
+                 K, nullptr, split_for(Co, K, M), c.status, st);
         k_colsum<uint16_t><<<dim3((Co + 31) / 32, colsum_rows(M, (Co + 31) / 32)), dim3(32, 8), 0, st>>>(
             c.dz, M, Co, c.grad + L[l].b_off);
         if (l == 0 || e != cudaSuccess) break;
-        transpose(c.wbf + L[l].w_off, Co, K, c.wT + L[l].w_off, st);
-        e = gemm(c.dz, Co, c.wT + L[l].w_off, Co, M, K, Co, GEMM_STORE_F32, c.dx, nullptr, K, nullptr, 1, c.status,
-                 st);
+        e = gemm(c.dz, Co, c.wbf + L[l].w_off, K, M, K, Co, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, K, nullptr, 1,
+                 c.status, st);
         k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin), 256, 0, st>>>(c.dx, c.X[l], B, H, H, L[l].cin,
                                                                                c.dzp);
         uint16_t *t = c.dz;

@@ -258,12 +258,16 @@ cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32
 // (lda, ldb multiples of 8), K a multiple of 64.
 // ---------------------------------------------------------------------------
 enum GemmMode { GEMM_STORE_F32 = 0, GEMM_ATOMIC_F32 = 1, GEMM_BIAS_RELU_BF16 = 2, GEMM_BIAS_F32 = 3 };
+// Operand layout flags of dbmp_gemm_bf16's mode: A (B) given MN-major, i.e. as the
+// K x M (K x N) matrix with M (N) contiguous.
+constexpr int32_t GEMM_A_MN = 16, GEMM_B_MN = 32;
 
 struct GemmArgs {
     const uint16_t *A;
     const uint16_t *B;
     int32_t M, N, K, lda, ldb, ldc;
-    int32_t mode;
+    int32_t mode;       // GemmMode (the epilogue)
+    int32_t a_mn, b_mn; // operands MN-major (A: K x M, B: K x N, lda / ldb their row strides)
     float *Cf;          // GEMM_STORE_F32, GEMM_ATOMIC_F32, GEMM_BIAS_F32
     uint16_t *Cb;       // GEMM_BIAS_RELU_BF16
     const float *bias;  // [N] for the bias modes
@@ -279,10 +283,10 @@ cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st);
 struct CnnBuffers {
     int32_t max_batch;
     float *theta, *grad, *m, *v;   // fp32 master parameters, gradient, Adam moments
-    uint16_t *wbf, *wT;            // bf16 copies of the weights, transposed copies
+    uint16_t *wbf;                 // bf16 copies of the weights
     uint16_t *X[6];                // activations (NHWC bf16): input and five conv outputs
     float *O, *dO, *dx;            // head outputs, their gradient, fp32 product buffer
-    uint16_t *col, *colT, *dz, *dzT, *dzp;
+    uint16_t *col, *dz, *dzp;      // im2col matrix, conv output gradients (two buffers)
     int32_t *status;
 };
 

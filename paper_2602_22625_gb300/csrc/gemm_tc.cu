@@ -12,12 +12,17 @@
 //               a last commit signals that the accumulator is complete;
 //   warps 2-5   epilogue: each reads the TMEM lane quarter it may access
 //               (32 (warp % 4) ...) with tcgen05.ld, applies the mode, writes C.
-// TMA writes each stage in the 128-byte swizzled K-major layout (rows of 64 bf16,
-// eight-row atoms of 1024 bytes), which the shared-memory matrix descriptors
-// describe with layout type SWIZZLE_128B; one MMA's K step of 16 elements advances
-// the descriptor's start address by 32 bytes.  Rows past M or N are zero-filled by
-// the tensor copy; K must be a multiple of 64.  Split-K over gridDim.z adds
-// partial tiles with fp32 atomics.
+// TMA writes each stage with the 128-byte swizzle, whose eight-row atoms of 1024
+// bytes the shared-memory matrix descriptors describe (layout type SWIZZLE_128B):
+//   K-major operand   one box of 64 (K) x rows: 128-byte rows along K, atoms 1024
+//                     bytes apart along M/N; an MMA's K step of 16 advances the
+//                     start address by 32 bytes;
+//   MN-major operand  boxes of 64 (M/N) x 64 (K), 8 KB each: 128-byte rows along
+//                     M/N, atoms 1024 bytes apart along K (stride byte offset),
+//                     boxes 8 KB apart along M/N (leading byte offset); a K step of
+//                     16 advances the start address by 2048 bytes.
+// Rows past M or N are zero-filled by the tensor copy; K must be a multiple of 64.
+// Split-K over gridDim.z adds partial tiles with fp32 atomics.
 //
 // Every mbarrier wait is bounded.  A wait that gives up sets the status flag; the
 // producer still waits (bounded) for the copies it issued, the accumulator's last
@@ -89,25 +94,28 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// Shared-memory matrix descriptor (sm_100 family): K-major, 128-byte swizzle, eight-
-// row atoms 1024 bytes apart (stride byte offset); the leading byte offset is not
-// used by swizzled K-major layouts and is set to one 16-byte unit.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+// Shared-memory matrix descriptor (sm_100 family) with the 128-byte swizzle:
+// stride byte offset 1024 (eight-row atoms); the leading byte offset is the
+// distance between 64-element M/N boxes of an MN-major operand (not used by a
+// swizzled K-major operand, which gets one 16-byte unit).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t lbo) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;                      // leading byte offset: 16 B
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;  // leading byte offset
     d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 1024 B
     d |= (uint64_t)1 << 46;                      // descriptor version
     d |= (uint64_t)2 << 61;                      // layout: 128-byte swizzle
     return d;
 }
 
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = BN.
+// Instruction descriptor of kind::f16: D f32, A and B bf16, M = 128, N = BN; bits 15
+// and 16 mark A / B as MN-major.
 template <int BN>
-__device__ __forceinline__ uint32_t instr_desc() {
+__device__ __forceinline__ uint32_t instr_desc(bool a_mn, bool b_mn) {
     return (1u << 4)                 // D format: f32
            | (1u << 7)               // A format: bf16
            | (1u << 10)              // B format: bf16
+           | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16)
            | ((uint32_t)(BN >> 3) << 17)
            | ((uint32_t)(kBM >> 4) << 24);
 }
@@ -190,9 +198,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (*(volatile int *)&abort_flag) break;
             const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);
+            const int k = (kt0 + i) * kBK;
             mbar_expect_tx(fb, C::STAGE);
-            tma_load_2d(sa, &tmA, (kt0 + i) * kBK, m0, fb);
-            tma_load_2d(sa + C::A_BYTES, &tmB, (kt0 + i) * kBK, n0, fb);
+            if (g.a_mn) {
+                for (int j = 0; j < kBM / 64; ++j) tma_load_2d(sa + j * 8192, &tmA, m0 + 64 * j, k, fb);
+            } else {
+                tma_load_2d(sa, &tmA, k, m0, fb);
+            }
+            if (g.b_mn) {
+                for (int j = 0; j < BN / 64; ++j) tma_load_2d(sa + C::A_BYTES + j * 8192, &tmB, n0 + 64 * j, k, fb);
+            } else {
+                tma_load_2d(sa + C::A_BYTES, &tmB, k, n0, fb);
+            }
             issued = i + 1;
         }
         // every issued copy lands before the CTA can exit
@@ -200,7 +217,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(smem_u32(&full[i % S]), (i / S) & 1)) abort_flag = 1;
     } else if (warp == 1 && lane == 0 && T > 0) {
         // ---- MMA issuer ----
-        const uint32_t idesc = instr_desc<BN>();
+        const uint32_t idesc = instr_desc<BN>(g.a_mn != 0, g.b_mn != 0);
+        // per K step of 16: +32 B (K-major) or +2048 B (MN-major); leading byte offsets
+        const uint32_t a_step = g.a_mn ? 2048u : 32u, b_step = g.b_mn ? 2048u : 32u;
+        const uint32_t a_lbo = g.a_mn ? 8192u : 16u, b_lbo = g.b_mn ? 8192u : 16u;
         for (int i = 0; i < T; ++i) {
             const int s = i % S;
             if (!mbar_wait(smem_u32(&full[s]), (i / S) & 1)) {
@@ -212,7 +232,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sa = sbase + s * C::STAGE, sb = sa + C::A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
-                mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(tmem, sw128_desc(sa + kk * a_step, a_lbo), sw128_desc(sb + kk * b_step, b_lbo), idesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
             mma_commit(smem_u32(&empty[s]));
         }
         mma_commit(smem_u32(&acc_done));   // arrives once every issued MMA has completed
@@ -284,12 +305,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-// Tensor map of a rows x K row-major bf16 matrix (row stride ld elements), copied
-// in boxes of 64 (K) x box_rows with the 128-byte swizzle; out-of-range rows read 0.
-bool make_map(CUtensorMap *m, const uint16_t *base, int rows, int K, int ld, int box_rows) {
-    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+// Tensor map of a row-major bf16 matrix with `inner` contiguous elements per row and
+// `outer` rows (row stride ld elements), copied in boxes of 64 (inner) x box_outer
+// with the 128-byte swizzle; out-of-range elements read 0.  K-major operands have
+// inner = K, MN-major operands inner = M (or N).
+bool make_map(CUtensorMap *m, const uint16_t *base, int outer, int inner, int ld, int box_outer) {
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
     const cuuint32_t estr[2] = {1, 1};
     return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -299,8 +322,9 @@ bool make_map(CUtensorMap *m, const uint16_t *base, int rows, int K, int ld, int
 template <int BN>
 cudaError_t launch_gemm_t(const GemmArgs &g, int split_k, cudaStream_t st) {
     CUtensorMap ta, tb;
-    if (!make_map(&ta, g.A, g.M, g.K, g.lda, kBM) || !make_map(&tb, g.B, g.N, g.K, g.ldb, BN))
-        return cudaErrorInvalidValue;
+    const bool ok_a = g.a_mn ? make_map(&ta, g.A, g.K, g.M, g.lda, kBK) : make_map(&ta, g.A, g.M, g.K, g.lda, kBM);
+    const bool ok_b = g.b_mn ? make_map(&tb, g.B, g.K, g.N, g.ldb, kBK) : make_map(&tb, g.B, g.N, g.K, g.ldb, BN);
+    if (!ok_a || !ok_b) return cudaErrorInvalidValue;
     const dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, split_k);
     k_gemm_tma<BN><<<grid, kThreads, TileCfg<BN>::SMEM, st>>>(ta, tb, g);
     return cudaGetLastError();
@@ -333,7 +357,7 @@ cudaError_t init_gemm_kernels() {
 
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
-    if (g.N <= 32) return launch_gemm_t<32>(g, split_k, st);
+    if (g.N <= 32 && !g.b_mn) return launch_gemm_t<32>(g, split_k, st);   // MN-major boxes are 64 wide
     if (g.N <= 64) return launch_gemm_t<64>(g, split_k, st);
     if (g.N <= 128) return launch_gemm_t<128>(g, split_k, st);
     return launch_gemm_t<256>(g, split_k, st);

@@ -71,3 +71,37 @@ def test_gemm_bias_modes():
     assert torch.all(C2.float() >= 0)
     C3 = gemm(A, B, 3, bias=bias)
     assert (C3.double() - (ref + bias.double())).abs().max().item() <= 2e-3
+
+
+def gemm_mn(A, B, M, N, K, mode, a_mn, b_mn, lda, ldb, split_k=1):
+    """A, B given as stored (K-major: M x K / N x K; MN-major: K x M / K x N)."""
+    L = D.load()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    flags = (16 if a_mn else 0) | (32 if b_mn else 0)
+    D._check(L.dbmp_gemm_bf16(A.data_ptr(), lda, B.data_ptr(), ldb, M, N, K, mode | flags, C.data_ptr(), None,
+                              N, None, split_k, status.data_ptr(), torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    return C
+
+
+@pytest.mark.parametrize("a_mn,b_mn", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 128), (300, 200, 320), (64, 512, 1024), (32, 128, 4096)])
+def test_gemm_mn_major_operands(M, N, K, a_mn, b_mn):
+    """Operands given MN-major (A as K x M, B as K x N, M / N contiguous), as the
+    proposal network's weight and input gradients read them."""
+    cuda()
+    A, B, ref = operands(M, N, K, 7 * M + N + K)
+    At = A.T.contiguous() if a_mn else A
+    Bt = B.T.contiguous() if b_mn else B
+    lda = M if a_mn else K
+    ldb = N if b_mn else K
+    if (a_mn and lda % 8) or (b_mn and ldb % 8):
+        pytest.skip("row stride must be a multiple of 8")
+    C = gemm_mn(At, Bt, M, N, K, 0, a_mn, b_mn, lda, ldb)
+    err = (C.double() - ref).abs().max().item()
+    assert err <= 2e-6 * K * 4, err
+    if K >= 1024:   # split-K with atomics on the same layouts
+        C1 = gemm_mn(At, Bt, M, N, K, 1, a_mn, b_mn, lda, ldb, split_k=4)
+        assert (C1.double() - ref).abs().max().item() <= 2e-6 * K * 4
