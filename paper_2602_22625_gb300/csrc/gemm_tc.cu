@@ -2,7 +2,8 @@
 //
 //   C[m][n] (op)= sum_k A[m][k] * B[n][k]      A: M x K, B: N x K, both K-contiguous BF16
 //
-// One CTA computes a 128 x BN tile (BN = 32 ... 256) with three warp roles:
+// One CTA computes a 128 x BN tile (BN = 32 ... 256) with three warp roles (the
+// stage ring has as many stages as the CTA's K steps, at most 4-8 by BN):
 //   warp 0      producer: one thread issues the TMA tensor copies of the A and B
 //               K-slabs (64 wide) into a ring of shared-memory stages, each stage
 //               announced on its `full` mbarrier with the bytes it expects;
@@ -146,13 +147,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Stages a CTA uses: as many as it has K steps, up to the ring's capacity, so short-K
+// products keep several CTAs resident per SM.
+template <int BN>
+__host__ __device__ __forceinline__ int stages_for(int kt_per) {
+    return kt_per < TileCfg<BN>::STAGES ? (kt_per > 0 ? kt_per : 1) : TileCfg<BN>::STAGES;
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
     using C = TileCfg<BN>;
-    constexpr int S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[S], empty[S], acc_done;
+    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], acc_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -164,6 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int kt_per = (kt_total + gridDim.z - 1) / gridDim.z;
     const int kt0 = blockIdx.z * kt_per;
     const int T = max(0, min(kt_per, kt_total - kt0));
+    const int S = stages_for<BN>(kt_per);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -189,10 +197,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0 && lane == 0 && T > 0) {
         // ---- producer ----
-        int issued = 0;
+        int issued = 0, s = 0;
+        uint32_t ph = 0;   // parity of the current use of slot s
         for (int i = 0; i < T; ++i) {
-            const int s = i % S;
-            if (i >= S && !mbar_wait(smem_u32(&empty[s]), ((i / S) & 1) ^ 1)) {
+            if (i >= S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1)) {
                 abort_flag = 1;
                 break;
             }
@@ -211,6 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tma_load_2d(sa + C::A_BYTES, &tmB, k, n0, fb);
             }
             issued = i + 1;
+            if (++s == S) s = 0, ph ^= 1;
         }
         // every issued copy lands before the CTA can exit
         for (int i = issued > S ? issued - S : 0; i < issued; ++i)
@@ -221,9 +230,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // per K step of 16: +32 B (K-major) or +2048 B (MN-major); leading byte offsets
         const uint32_t a_step = g.a_mn ? 2048u : 32u, b_step = g.b_mn ? 2048u : 32u;
         const uint32_t a_lbo = g.a_mn ? 8192u : 16u, b_lbo = g.b_mn ? 8192u : 16u;
+        int s = 0;
+        uint32_t ph = 0;
         for (int i = 0; i < T; ++i) {
-            const int s = i % S;
-            if (!mbar_wait(smem_u32(&full[s]), (i / S) & 1)) {
+            if (!mbar_wait(smem_u32(&full[s]), ph)) {
                 abort_flag = 1;
                 break;
             }
@@ -235,6 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma_bf16(tmem, sw128_desc(sa + kk * a_step, a_lbo), sw128_desc(sb + kk * b_step, b_lbo), idesc,
                          (i > 0 || kk > 0) ? 1u : 0u);
             mma_commit(smem_u32(&empty[s]));
+            if (++s == S) s = 0, ph ^= 1;
         }
         mma_commit(smem_u32(&acc_done));   // arrives once every issued MMA has completed
     } else if (warp >= 2) {
@@ -326,7 +337,9 @@ cudaError_t launch_gemm_t(const GemmArgs &g, int split_k, cudaStream_t st) {
     const bool ok_b = g.b_mn ? make_map(&tb, g.B, g.K, g.N, g.ldb, kBK) : make_map(&tb, g.B, g.N, g.K, g.ldb, BN);
     if (!ok_a || !ok_b) return cudaErrorInvalidValue;
     const dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, split_k);
-    k_gemm_tma<BN><<<grid, kThreads, TileCfg<BN>::SMEM, st>>>(ta, tb, g);
+    const int kt_total = g.K / kBK, kt_per = (kt_total + split_k - 1) / split_k;
+    const int smem = stages_for<BN>(kt_per) * TileCfg<BN>::STAGE + 1024;
+    k_gemm_tma<BN><<<grid, kThreads, smem, st>>>(ta, tb, g);
     return cudaGetLastError();
 }
 
