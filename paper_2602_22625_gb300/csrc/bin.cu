@@ -131,9 +131,13 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
         atomicAdd(&status->n_degenerate, 1);
     }
     const bool valid = bid_ok && all_finite8(p) && p[2] != 0.0f;
-    if (valid && !(isfinite(r.A) && isfinite(r.B) && isfinite(r.C) && isfinite(r.D))) {
-        // |s| below ~1e-37: the transform overflows float32; the primitive is drawn
-        // with zero opacity and counted.
+    // |A|, |B|, |C|, |D| <= 2^100 keeps every bitmap coordinate a compositor forms
+    // for a pixel the primitive's tile rectangle covers finite in float32.
+    const float kMaxCoef = 1.2676506e30f;   // 2^100
+    if (valid && !(fabsf(r.A) <= kMaxCoef && fabsf(r.B) <= kMaxCoef && fabsf(r.C) <= kMaxCoef &&
+                   fabsf(r.D) <= kMaxCoef)) {
+        // |s| below ~1e-28 of the bitmap's half-width: the primitive is drawn with
+        // zero opacity and counted.
         r.a = 0.0f;
         r.A = r.B = r.C = r.D = 0.0f;
         atomicAdd(&status->n_degenerate, 1);

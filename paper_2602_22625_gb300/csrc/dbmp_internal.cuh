@@ -70,69 +70,74 @@ struct RenderCfg {
 };
 
 // ---------------------------------------------------------------------------
-// The one bilinear sample both compositors use (Eq. 2, Eqs. S1-S3).  Every
+// The one bilinear sample every compositor uses (Eq. 2, Eqs. S1-S3).  Every
 // operation is explicitly rounded (no contraction decided by the compiler), so
-// the forward and backward kernels compute bit-identical M and alpha.
-// Returns false when (U, V) lies outside (-1, W_b) x (-1, H_b), where every tap
-// is zero.  On true: M and the quantities the backward needs.
+// the forward, the backward and the backward's re-walk compute bit-identical M
+// and alpha for the same (pixel, primitive).
+//
+// The transform is split by what it depends on.  Its column part depends on the
+// primitive and the pixel's x only, so a lane that owns several pixels of one
+// column evaluates it once per primitive:
+//     dx = px - x,   au = A dx + kw,   cv = C dx + kv            (col_xf)
+// and each pixel adds its row part:
+//     dy = py - y,   U = B dy + au,    V = D dy + cv             (tap_issue)
+// (U, V) outside (-1, W_b) x (-1, H_b) reads only zero taps; there, and for a
+// pixel that no longer composites, no load is issued and tap_M returns 0.
 // ---------------------------------------------------------------------------
-struct Sample {
-    float Up, Vp;        // U - kw, V - kv
-    float wu, wv;        // fractional parts
-    float d0, d1, m0, m1;
-    float M;
+struct ColXf {
+    float au, cv;              // A dx + kw, C dx + kv
+    const float4 *base;        // quad of texel (0, 0): quad + quad_off + (W_b + 1) + 1
 };
 
-// The sample in two halves, so that a compositor can issue the tap-quad load of
-// its next layer before it composites the current one: tap_issue transforms the
-// pixel, tests the range and issues the load; tap_finish blends.  Together they
-// are exactly sample_bitmap.
+__device__ __forceinline__ ColXf col_xf(const PrimRec &r, const float4 *__restrict__ quad, int32_t Wq,
+                                        float kw, float kv, float px) {
+    const float dx = __fsub_rn(px, r.x);
+    ColXf c;
+    c.au = __fmaf_rn(r.A, dx, kw);
+    c.cv = __fmaf_rn(r.C, dx, kv);
+    c.base = quad + r.quad_off + Wq + 1;
+    return c;
+}
+
+// The per-pixel half of a sample.  tap_issue transforms the pixel, tests the range
+// and issues the 128-bit tap load; tap_M blends.  Splitting them lets a lane have
+// the loads of all its pixels in flight before it blends.  q keeps its previous
+// contents when no load is issued (ok false); tap_M then returns 0 without
+// reading it, and every other quantity computed from q stays finite.
 struct Tap {
-    float4 q;            // (p00, p01, p10, p11); zero when !ok
-    float Up, Vp, wu, wv;
+    float4 q;                  // (p00, p01, p10, p11)
+    float U, V, wu, wv;        // bitmap coordinates and their fractional parts
     bool ok;
 };
 
-__device__ __forceinline__ void tap_issue(const PrimRec &r, const float4 *__restrict__ quad, int32_t Wq,
-                                          float kw, float kv, float Wbf, float Hbf, float px, float py,
-                                          Tap &t) {
-    const float dx = __fsub_rn(px, r.x);
+__device__ __forceinline__ void tap_issue(const PrimRec &r, const ColXf &c, int32_t Wq, float Wbf, float Hbf,
+                                          float py, bool live, Tap &t) {
     const float dy = __fsub_rn(py, r.y);
-    t.Up = __fmaf_rn(r.A, dx, __fmul_rn(r.B, dy));
-    t.Vp = __fmaf_rn(r.C, dx, __fmul_rn(r.D, dy));
-    const float U = __fadd_rn(t.Up, kw);
-    const float V = __fadd_rn(t.Vp, kv);
-    t.ok = U >= -1.0f && U < Wbf && V >= -1.0f && V < Hbf;
-    const float fu = floorf(U), fv = floorf(V);
-    t.wu = __fsub_rn(U, fu);
-    t.wv = __fsub_rn(V, fv);
-    t.q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (t.ok) {
-        const int32_t iu = (int32_t)fu, iv = (int32_t)fv;   // in [-1, W_b-1] x [-1, H_b-1]
-        t.q = __ldg(quad + r.quad_off + (iv + 1) * Wq + (iu + 1));
-    }
+    t.U = __fmaf_rn(r.B, dy, c.au);
+    t.V = __fmaf_rn(r.D, dy, c.cv);
+    t.ok = live && t.U >= -1.0f && t.U < Wbf && t.V >= -1.0f && t.V < Hbf;
+    const float fu = floorf(t.U), fv = floorf(t.V);
+    t.wu = __fsub_rn(t.U, fu);
+    t.wv = __fsub_rn(t.V, fv);
+    if (t.ok) t.q = __ldg(c.base + (int32_t)fv * Wq + (int32_t)fu);   // fu, fv in [-1, W_b-1] x [-1, H_b-1]
 }
 
-__device__ __forceinline__ bool tap_finish(const Tap &t, Sample &s) {
-    if (!t.ok) return false;
-    s.Up = t.Up;
-    s.Vp = t.Vp;
-    s.wu = t.wu;
-    s.wv = t.wv;
-    s.d0 = __fsub_rn(t.q.y, t.q.x);                     // p01 - p00
-    s.d1 = __fsub_rn(t.q.w, t.q.z);                     // p11 - p10
-    s.m0 = __fmaf_rn(s.wu, s.d0, t.q.x);
-    s.m1 = __fmaf_rn(s.wu, s.d1, t.q.z);
-    s.M = __fmaf_rn(s.wv, __fsub_rn(s.m1, s.m0), s.m0);
-    return true;
+// Bilinear value M (0 when !ok) and the two tap differences the backward needs:
+// dMdU = d0 + wv (d1 - d0), dMdV = m1 - m0.  M >= 0 whenever the texels are.
+__device__ __forceinline__ float tap_M(const Tap &t, float &dMdU, float &dMdV) {
+    const float d0 = __fsub_rn(t.q.y, t.q.x);          // p01 - p00
+    const float d1 = __fsub_rn(t.q.w, t.q.z);          // p11 - p10
+    const float m0 = __fmaf_rn(t.wu, d0, t.q.x);
+    const float m1 = __fmaf_rn(t.wu, d1, t.q.z);
+    dMdV = __fsub_rn(m1, m0);
+    dMdU = __fmaf_rn(t.wv, __fsub_rn(d1, d0), d0);
+    const float M = __fmaf_rn(t.wv, dMdV, m0);
+    return t.ok ? M : 0.0f;
 }
 
-__device__ __forceinline__ bool sample_bitmap(const PrimRec &r, const float4 *__restrict__ quad,
-                                              int32_t Wq, float kw, float kv, float Wbf, float Hbf,
-                                              float px, float py, Sample &s) {
-    Tap t;
-    tap_issue(r, quad, Wq, kw, kv, Wbf, Hbf, px, py, t);
-    return tap_finish(t, s);
+__device__ __forceinline__ float tap_M(const Tap &t) {
+    float du, dv;
+    return tap_M(t, du, dv);
 }
 
 // ---------------------------------------------------------------------------

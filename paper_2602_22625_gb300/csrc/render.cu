@@ -220,18 +220,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     for (int item = next_item(&a.status->queue[0], lane); item < n_items;
          item = next_item(&a.status->queue[0], lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
-        float px[PPT], py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+        const int x = g.x0 + lane % TILE;
+        const float px = (float)x;
+        float py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
         int last[PPT];
         bool inside[PPT];
+        Tap tp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int x = g.x0 + lane % TILE, y = g.y0 + lane / TILE + k * LROWS;
+            const int y = g.y0 + lane / TILE + k * LROWS;
             inside[k] = x < g.d.W && y < g.d.H;
-            px[k] = (float)x;
             py[k] = (float)y;
             T[k] = inside[k] ? 1.0f : 0.0f;   // pixels off the canvas never composite
             C0[k] = C1[k] = C2[k] = 0.0f;
             last[k] = -1;
+            tp[k].q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
         const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
@@ -250,28 +253,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
                 for (int t = 0; t < m; ++t) {
                     const PrimRec r = sh[t];
                     const int j = pos[t];
+                    const ColXf cx = col_xf(r, a.atlas.quad, Wq, kw, kv, px);
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) tap_issue(r, cx, Wq, Wbf, Hbf, py[k], T[k] >= tstop, tp[k]);
+                    // Branch-free per pixel: a pixel that does not composite this layer
+                    // has M = 0, so alpha = 0, q = 1 and every update below is an exact
+                    // no-op (T * 1 = T, fma(0, c, C) = C).
                     bool any = false;
-                    Tap tp[PPT];
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        tp[k].ok = false;
-                        if (T[k] >= tstop) tap_issue(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], tp[k]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        if (!(T[k] >= tstop)) continue;
-                        Sample s;
-                        if (tap_finish(tp[k], s) && s.M > 0.0f) {
-                            const float al = __fmul_rn(r.a, s.M);
-                            const float q = __fsub_rn(1.0f, al);
-                            const float w = __fmul_rn(T[k], al);
-                            C0[k] = __fmaf_rn(w, r.cr, C0[k]);
-                            C1[k] = __fmaf_rn(w, r.cg, C1[k]);
-                            C2[k] = __fmaf_rn(w, r.cb, C2[k]);
-                            T[k] = __fmul_rn(T[k], q);
-                            last[k] = j;
-                            ++ct_it;
-                        }
+                        const float M = tap_M(tp[k]);
+                        const float al = __fmul_rn(r.a, M);
+                        const float q = __fsub_rn(1.0f, al);
+                        const float w = __fmul_rn(T[k], al);
+                        C0[k] = __fmaf_rn(w, r.cr, C0[k]);
+                        C1[k] = __fmaf_rn(w, r.cg, C1[k]);
+                        C2[k] = __fmaf_rn(w, r.cb, C2[k]);
+                        T[k] = __fmul_rn(T[k], q);
+                        const bool c = M > 0.0f;
+                        last[k] = c ? j : last[k];
+                        ct_it += c ? 1 : 0;
                         any = any || T[k] >= tstop;
                     }
                     if (!__any_sync(FULL, any)) {
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
             if (!inside[k]) continue;
             // a pixel evaluates entries up to its last layer, then finds T < T_stop
             ev_it += T[k] < tstop ? last[k] + 1 : g.len;
-            const int64_t pix = (int64_t)py[k] * g.d.W + (int64_t)px[k];
+            const int64_t pix = (int64_t)py[k] * g.d.W + x;
             float *img = a.image + 3 * g.d.pix_base;
             img[pix] = __fmaf_rn(T[k], bg_at(a, g.d, 0, pix), C0[k]);
             img[HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 1, pix), C1[k]);
@@ -369,11 +370,12 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     float T = 1.0f;
+    Tap tp;
+    tp.q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int j = 0; j < upto; ++j) {
         const PrimRec r = a.rec[a.list[g.start + j]];
-        Sample s;
-        if (sample_bitmap(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px, py, s) && s.M > 0.0f)
-            T = __fmul_rn(T, __fsub_rn(1.0f, __fmul_rn(r.a, s.M)));
+        tap_issue(r, col_xf(r, a.atlas.quad, Wq, kw, kv, px), Wq, Wbf, Hbf, py, true, tp);
+        T = __fmul_rn(T, __fsub_rn(1.0f, __fmul_rn(r.a, tap_M(tp))));
     }
     return T;
 }
@@ -401,17 +403,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     for (int item = next_item(&a.status->queue[1], lane); item < n_items;
          item = next_item(&a.status->queue[1], lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
-        float px[PPT], py[PPT], T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
+        const int x = g.x0 + lane % TILE;
+        const float px = (float)x;
+        float py[PPT], T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
         int last[PPT];
+        Tap tp[PPT];
         int my_max = -1, ev_it = 0, sv_it = 0;
         const int64_t HW = (int64_t)g.d.H * g.d.W;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int x = g.x0 + lane % TILE, y = g.y0 + lane / TILE + k * LROWS;
-            px[k] = (float)x;
+            const int y = g.y0 + lane / TILE + k * LROWS;
             py[k] = (float)y;
             last[k] = -1;
             T[k] = Y[k] = g0[k] = g1[k] = g2[k] = 0.0f;
+            tp[k].q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (x < g.d.W && y < g.d.H) {
                 const int64_t pix = (int64_t)y * g.d.W + x;
                 last[k] = min(a.n_last[g.d.pix_base + pix], g.len - 1);
@@ -452,42 +457,70 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
             for (int t = m - 1; t >= 0; --t) {
                 const PrimRec r = sh[t];
                 const int j = pos[t];
-                float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                const ColXf cx = col_xf(r, a.atlas.quad, Wq, kw, kv, px);
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) tap_issue(r, cx, Wq, Wbf, Hbf, py[k], j <= last[k], tp[k]);
+                // Phase 1: alpha and the recovered transmittance in front of the layer.
+                // A pixel that does not composite this layer (behind its last layer,
+                // outside the bitmap, zero texels) has M = 0 and keeps T and Y.
+                float M[PPT], al[PPT], q[PPT], Tk[PPT];
+                bool redo = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    M[k] = tap_M(tp[k]);
+                    al[k] = __fmul_rn(r.a, M[k]);
+                    q[k] = __fsub_rn(1.0f, al[k]);
+                    Tk[k] = M[k] > 0.0f ? __fdividef(T[k], q[k]) : T[k];
+                    redo = redo || (M[k] > 0.0f && !(q[k] > 0.0f));
+                }
+                if (__any_sync(FULL, redo)) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k)
+                        if (M[k] > 0.0f && !(q[k] > 0.0f)) Tk[k] = rewalk_T(a, g, j, px, py[k]);
+                }
+                // Phase 2: the eight per-primitive sums.  The factor a (opacity) common
+                // to the geometric sums is applied once per primitive, and the
+                // centring of U, V (Up = U - kw, Vp = V - kv) is undone on the sums:
+                //   sum dM dMdU Up  = a (sum dA dMdU U - kw sum dA dMdU), and so on.
+                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3u = 0.0f, s3v = 0.0f, s4 = 0.0f;
+                float s5 = 0.0f, s6 = 0.0f, s7 = 0.0f;
                 bool any = false;
-                Tap tp[PPT];
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    tp[k].ok = false;
-                    if (j <= last[k]) tap_issue(r, a.atlas.quad, Wq, kw, kv, Wbf, Hbf, px[k], py[k], tp[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (j > last[k]) continue;
-                    Sample s;
-                    if (!tap_finish(tp[k], s) || !(s.M > 0.0f)) continue;
-                    any = true;
-                    const float al = __fmul_rn(r.a, s.M);
-                    const float q = __fsub_rn(1.0f, al);
-                    const float Tk = q > 0.0f ? __fdividef(T[k], q) : rewalk_T(a, g, j, px[k], py[k]);
-                    T[k] = Tk;
+                    float dMdU, dMdV;
+                    tap_M(tp[k], dMdU, dMdV);
+                    const bool c = M[k] > 0.0f;
+                    any = any || c;
+                    T[k] = Tk[k];
                     const float gc = g0[k] * r.cr + g1[k] * r.cg + g2[k] * r.cb;
-                    const float dA = Tk * (gc - Y[k]);          // dL/dalpha_k
-                    const float w = Tk * al;
-                    const float dM = dA * r.a;                  // dL/dM
-                    const float dMdU = fmaf(s.wv, s.d1 - s.d0, s.d0);
-                    const float dMdV = s.m1 - s.m0;
-                    const float gU = dM * dMdU, gV = dM * dMdV;
-                    v[0] += gU;
-                    v[1] += gV;
-                    v[2] += gU * s.Up + gV * s.Vp;
-                    v[3] += rho * gU * s.Vp - irho * gV * s.Up;
-                    v[4] += dA * al;
-                    v[5] += g0[k] * w;
-                    v[6] += g1[k] * w;
-                    v[7] += g2[k] * w;
-                    Y[k] = fmaf(q, Y[k], al * gc);
+                    const float dA = c ? Tk[k] * (gc - Y[k]) : 0.0f;   // dL/dalpha_k
+                    const float gU = dA * dMdU, gV = dA * dMdV;        // / a
+                    s0 += gU;
+                    s1 += gV;
+                    s2 = fmaf(gU, tp[k].U, s2);
+                    s2 = fmaf(gV, tp[k].V, s2);
+                    s3u = fmaf(gU, tp[k].V, s3u);
+                    s3v = fmaf(gV, tp[k].U, s3v);
+                    s4 = fmaf(dA, M[k], s4);                           // / a
+                    const float w = Tk[k] * al[k];
+                    s5 = fmaf(g0[k], w, s5);
+                    s6 = fmaf(g1[k], w, s6);
+                    s7 = fmaf(g2[k], w, s7);
+                    Y[k] = fmaf(q[k], Y[k], al[k] * gc);
                 }
-                if (__any_sync(FULL, any)) warp_reduce8_add(v, a.graw + 8 * (int64_t)r.index, lane);
+                if (__any_sync(FULL, any)) {
+                    const float ra = r.a;
+                    float v[8];
+                    v[0] = ra * s0;
+                    v[1] = ra * s1;
+                    v[2] = ra * fmaf(-kv, s1, fmaf(-kw, s0, s2));
+                    v[3] = ra * (fmaf(rho, s3u, fmaf(-kw, s0, kv * s1)) - irho * s3v);
+                    v[4] = ra * s4;
+                    v[5] = s5;
+                    v[6] = s6;
+                    v[7] = s7;
+                    warp_reduce8_add(v, a.graw + 8 * (int64_t)r.index, lane);
+                }
             }
             __syncwarp();
             hi = lo;
