@@ -80,13 +80,16 @@ typedef struct DbmpAtlas DbmpAtlas;
 
 /* Builds the device-side sampling layout of n_bmp bitmaps of H_b x W_b texels
  * (texels_dev: float32 [n_bmp][H_b][W_b], values in [0, 1]; H_b, W_b >= 2).
- * The library stores, for every lattice cell (v0, u0) in [-1, H_b-1] x
- * [-1, W_b-1], the four taps {P[v0,u0], P[v0,u0+1], P[v0+1,u0], P[v0+1,u0+1]}
- * (zero outside the bitmap) as one 16-byte vector, so one bilinear sample is one
- * 128-bit load, and a summed-area table of the non-zero texels, with which the
- * compositors skip primitives whose bitmap is empty over a whole region of
- * pixels.  Allocates n_bmp (H_b+1)(W_b+1) 20 bytes and synchronises `stream`.
- * texels_dev is not referenced after the call. */
+ * The library stacks the bitmaps in one pitch-linear float plane, each followed
+ * by a zero row, and reads it through a 2-D texture object with a zero border,
+ * so that one texture gather returns the four taps of a bilinear sample (zero
+ * outside the bitmap).  It also builds a summed-area table of the non-zero
+ * texels, with which the compositors skip primitives whose bitmap is empty over
+ * a whole region of pixels.  The plane must fit the device's pitch-linear
+ * texture limits (GB300: n_bmp (H_b + 1) <= 65000 rows, W_b <= 131072);
+ * otherwise DBMP_ERR_INVALID_ARG.  Allocates about n_bmp (H_b+1)(W_b+1) 8 bytes,
+ * creates one texture object and synchronises `stream`.  texels_dev is not
+ * referenced after the call. */
 int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, int32_t W_b,
                           dbmp_stream_t stream, DbmpAtlas **out);
 int32_t dbmp_atlas_destroy(DbmpAtlas *atlas);
@@ -463,7 +466,7 @@ int32_t dbmp_alpha_loss_grad(const float *image_dev, const float *T_final_dev, c
  * dbmp_render_fwd (default tuning), from the plain atlas texels
  * (float32 [n_bmp][H_b][W_b]), with no DbmpWorkspace and no DbmpAtlas.  All
  * intermediate state lives in one scratch array compiled into the library
- * (about 5.1 MB of device memory).  Every GPU that loads the library holds it
+ * (about 6.1 MB of device memory).  Every GPU that loads the library holds it
  * until the process exits.  Maximum sizes:
  *     H, W <= 512;  N <= 4096;  n_bmp (H_b + 1)(W_b + 1) <= 32768;
  *     tile-list entries (sum_t d_t) <= 1 048 576.
@@ -474,8 +477,10 @@ int32_t dbmp_alpha_loss_grad(const float *image_dev, const float *T_final_dev, c
  * (params_dev 16-byte aligned; image 3 x H x W, T_final and n_last H x W).
  * This call calls no cudaMalloc, cudaFree or allocating library routine.  The
  * first call on each device does a one-time set-up with that device current: it
- * resolves the scratch array's device address and sets kernel attributes.  Make
- * that first call before any stream capture.
+ * resolves the scratch array's device address and sets kernel attributes.  The
+ * first call with each atlas shape (W_b, n_bmp (H_b + 1)) on a device creates a
+ * texture object over the scratch texel plane, kept until the process exits (at
+ * most 64 shapes).  Make those first calls before any stream capture.
  *
  * All calls share the one scratch array, which keeps the last call's contents.
  * The call itself clears what must start at zero.  Calls whose GPU work

@@ -45,10 +45,13 @@ bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
 int32_t dbmp::record_error(int32_t code, const char *msg) { return fail(code, "%s", msg); }
 
 struct DbmpAtlas {
-    float4 *quad = nullptr;
+    void *plane_alloc = nullptr;
+    float *plane = nullptr;     // stacked texel plane (row pitch `pitch` bytes), 512-byte aligned
+    size_t pitch = 0;
+    cudaTextureObject_t tex = 0;
     int32_t *sat = nullptr;
     int32_t n_bmp = 0, Hb = 0, Wb = 0;
-    AtlasView view() const { return AtlasView{quad, sat, n_bmp, Hb, Wb}; }
+    AtlasView view() const { return AtlasView{tex, sat, n_bmp, Hb, Wb}; }
 };
 
 struct DbmpWorkspace {
@@ -185,7 +188,7 @@ int32_t build_plan(DbmpWorkspace *ws, int32_t n, const int32_t *H, const int32_t
 __global__ void k_set_canvas(CanvasDesc d, CanvasDesc *dst) { *dst = d; }
 
 int32_t check_atlas(const DbmpAtlas *atlas) {
-    if (!atlas || !atlas->quad || !atlas->sat) return fail(DBMP_ERR_INVALID_ARG, "atlas is NULL");
+    if (!atlas || !atlas->plane || !atlas->sat) return fail(DBMP_ERR_INVALID_ARG, "atlas is NULL");
     return DBMP_OK;
 }
 
@@ -311,23 +314,36 @@ int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
         return fail(DBMP_ERR_INVALID_ARG, "atlas needs n_bmp >= 1 and H_b, W_b >= 2");
     if ((int64_t)n_bmp * (H_b + 1) * (W_b + 1) > ((int64_t)1 << 31) - 1)
         return fail(DBMP_ERR_INVALID_ARG, "atlas too large for int32 texel offsets");
+    bool fits = false;
+    if (cudaError_t e = atlas_texture_fits(n_bmp, H_b, W_b, &fits)) return cuda_fail(e, "texture limits");
+    if (!fits)
+        return fail(DBMP_ERR_INVALID_ARG,
+                    "atlas %d x %dx%d exceeds the device's 2-D texture limits (n_bmp (H_b + 1) rows of W_b texels)",
+                    n_bmp, H_b, W_b);
     DbmpAtlas *a = new DbmpAtlas;
     a->n_bmp = n_bmp;
     a->Hb = H_b;
     a->Wb = W_b;
-    const size_t cells = (size_t)n_bmp * (H_b + 1) * (W_b + 1);
-    cudaError_t e = cudaMalloc(&a->quad, sizeof(float4) * cells);
+    a->pitch = atlas_plane_pitch(W_b);
+    const size_t rows = (size_t)n_bmp * (H_b + 1);
+    const size_t cells = rows * (W_b + 1);
+    cudaError_t e = cudaMalloc(&a->plane_alloc, a->pitch * rows + kTexAlign);
     if (e == cudaSuccess) e = cudaMalloc(&a->sat, sizeof(int32_t) * cells);
     if (e != cudaSuccess) {
-        cudaFree(a->quad);
+        cudaFree(a->plane_alloc);
         delete a;
         return fail(DBMP_ERR_NO_MEMORY, "atlas allocation: %s", cudaGetErrorString(e));
     }
+    a->plane = reinterpret_cast<float *>(((uintptr_t)a->plane_alloc + kTexAlign - 1) & ~(uintptr_t)(kTexAlign - 1));
     cudaStream_t st = (cudaStream_t)stream;
-    e = launch_quad_build(texels_dev, a->quad, a->sat, n_bmp, H_b, W_b, st);
+    e = atlas_texture_create(a->plane, a->pitch, n_bmp, H_b, W_b, &a->tex);
+    if (e == cudaSuccess)
+        e = launch_atlas_build(texels_dev, a->plane, (int64_t)(a->pitch / sizeof(float)), a->sat, n_bmp, H_b,
+                               W_b, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-        cudaFree(a->quad);
+        if (a->tex) cudaDestroyTextureObject(a->tex);
+        cudaFree(a->plane_alloc);
         cudaFree(a->sat);
         delete a;
         return cuda_fail(e, "atlas build");
@@ -339,15 +355,16 @@ int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
 int32_t dbmp_atlas_update(DbmpAtlas *atlas, const float *texels_dev, dbmp_stream_t stream) {
     if (int32_t r = check_atlas(atlas)) return r;
     if (!texels_dev) return fail(DBMP_ERR_INVALID_ARG, "texels_dev is NULL");
-    DBMP_CUDA(launch_quad_build(texels_dev, atlas->quad, atlas->sat, atlas->n_bmp, atlas->Hb, atlas->Wb,
-                                (cudaStream_t)stream),
+    DBMP_CUDA(launch_atlas_build(texels_dev, atlas->plane, (int64_t)(atlas->pitch / sizeof(float)), atlas->sat,
+                                 atlas->n_bmp, atlas->Hb, atlas->Wb, (cudaStream_t)stream),
               "atlas update");
     return DBMP_OK;
 }
 
 int32_t dbmp_atlas_destroy(DbmpAtlas *atlas) {
     if (!atlas) return DBMP_OK;
-    cudaFree(atlas->quad);
+    if (atlas->tex) cudaDestroyTextureObject(atlas->tex);
+    cudaFree(atlas->plane_alloc);
     cudaFree(atlas->sat);
     delete atlas;
     return DBMP_OK;

@@ -119,7 +119,7 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     r.C = (float)(-kv * sn * inv_s);
     r.D = (float)(kv * cs * inv_s);
     r.a = (float)((double)alpha_max / (1.0 + exp(-(double)p[4])));
-    r.quad_off = bitmap_id[i] * (atlas.Hb + 1) * (atlas.Wb + 1);  // checked below
+    r.bmp_row = bitmap_id[i] * (atlas.Hb + 1);  // checked below
     r.cr = (float)(1.0 / (1.0 + exp(-(double)p[5])));
     r.cg = (float)(1.0 / (1.0 + exp(-(double)p[6])));
     r.cb = (float)(1.0 / (1.0 + exp(-(double)p[7])));
@@ -127,7 +127,7 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     const int32_t bid = bitmap_id[i];
     const bool bid_ok = bid >= 0 && bid < atlas.n_bmp;
     if (!bid_ok) {
-        r.quad_off = 0;
+        r.bmp_row = 0;
         atomicAdd(&status->n_degenerate, 1);
     }
     const bool valid = bid_ok && all_finite8(p) && p[2] != 0.0f;

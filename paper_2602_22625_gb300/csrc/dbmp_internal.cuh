@@ -15,7 +15,7 @@ namespace dbmp {
 struct __align__(16) PrimRec {
     float x, y, A, B;
     float C, D, a;       // a = alpha_max sigmoid(nu)  (Eq. 3 without M)
-    int32_t quad_off;    // offset of the primitive's bitmap in the quad atlas (float4 units)
+    int32_t bmp_row;     // first row of the primitive's bitmap in the texel plane: id x (H_b + 1)
     float cr, cg, cb;    // sigmoid(c)
     int32_t index;       // primitive index (row of params / dparams)
 };
@@ -53,9 +53,15 @@ struct DevStatus {
     uint32_t queue[4];     // persistent-kernel work counters
 };
 
+// The bitmap atlas as the kernels see it.  The texels of all bitmaps are stacked in
+// one pitch-linear float plane, bitmap b in rows b (H_b + 1) .. b (H_b + 1) + H_b - 1
+// followed by one zero row, read through a 2-D texture object (border address mode,
+// border value 0; point sampling, unnormalised coordinates).  A bilinear sample
+// fetches its four taps with one gather, so taps outside the bitmap read 0 (zero
+// padding, Sec. S1.1) from the border or the zero row.
 struct AtlasView {
-    const float4 *quad;    // [n_bmp][H_b+1][W_b+1] tap quads
-    const int32_t *sat;    // [n_bmp][H_b+1][W_b+1] summed-area table of (texel > 0)
+    cudaTextureObject_t tex;  // texel plane
+    const int32_t *sat;       // [n_bmp][H_b+1][W_b+1] summed-area table of (texel > 0)
     int32_t n_bmp, Hb, Wb;
 };
 
@@ -86,16 +92,15 @@ struct RenderCfg {
 // ---------------------------------------------------------------------------
 struct ColXf {
     float au, cv;              // A dx + kw, C dx + kv
-    const float4 *base;        // quad of texel (0, 0): quad + quad_off + (W_b + 1) + 1
+    float row;                 // bmp_row + 1: gather y of the bitmap's row -1
 };
 
-__device__ __forceinline__ ColXf col_xf(const PrimRec &r, const float4 *__restrict__ quad, int32_t Wq,
-                                        float kw, float kv, float px) {
+__device__ __forceinline__ ColXf col_xf(const PrimRec &r, float kw, float kv, float px) {
     const float dx = __fsub_rn(px, r.x);
     ColXf c;
     c.au = __fmaf_rn(r.A, dx, kw);
     c.cv = __fmaf_rn(r.C, dx, kv);
-    c.base = quad + r.quad_off + Wq + 1;
+    c.row = (float)(r.bmp_row + 1);
     return c;
 }
 
@@ -110,8 +115,8 @@ struct Tap {
     bool ok;
 };
 
-__device__ __forceinline__ void tap_issue(const PrimRec &r, const ColXf &c, int32_t Wq, float Wbf, float Hbf,
-                                          float py, bool live, Tap &t) {
+__device__ __forceinline__ void tap_issue(const PrimRec &r, const ColXf &c, cudaTextureObject_t tex, float Wbf,
+                                          float Hbf, float py, bool live, Tap &t) {
     const float dy = __fsub_rn(py, r.y);
     t.U = __fmaf_rn(r.B, dy, c.au);
     t.V = __fmaf_rn(r.D, dy, c.cv);
@@ -119,7 +124,14 @@ __device__ __forceinline__ void tap_issue(const PrimRec &r, const ColXf &c, int3
     const float fu = floorf(t.U), fv = floorf(t.V);
     t.wu = __fsub_rn(t.U, fu);
     t.wv = __fsub_rn(t.V, fv);
-    if (t.ok) t.q = __ldg(c.base + (int32_t)fv * Wq + (int32_t)fu);   // fu, fv in [-1, W_b-1] x [-1, H_b-1]
+    if (t.ok) {
+        // Texel centres sit at half-integers, so a gather at (fu + 1, row + fv) has
+        // its 2 x 2 footprint at texels fu, fu + 1 of plane rows bmp_row + fv,
+        // bmp_row + fv + 1 with no rounding to decide: exact integers, fu, fv in
+        // [-1, W_b-1] x [-1, H_b-1].  Gather order: (u0,v1), (u1,v1), (u1,v0), (u0,v0).
+        const float4 g = tex2Dgather<float4>(tex, __fadd_rn(fu, 1.0f), __fadd_rn(fv, c.row), 0);
+        t.q = make_float4(g.w, g.z, g.x, g.y);
+    }
 }
 
 // Bilinear value M (0 when !ok) and the two tap differences the backward needs:
@@ -250,8 +262,18 @@ cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
 cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
                                  float *dparams, int32_t N, cudaStream_t st);
-cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t *sat, int32_t n_bmp,
-                              int32_t Hb, int32_t Wb, cudaStream_t st);
+// Texel plane (row pitch `pitch` floats) and summed-area tables of an atlas from
+// its dense texels [n_bmp][H_b][W_b].
+cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int32_t n_bmp,
+                               int32_t Hb, int32_t Wb, cudaStream_t st);
+// Row pitch (bytes) of an atlas texel plane, and the texture object over it (the
+// plane's base must be kTexAlign-aligned).
+constexpr size_t kTexAlign = 512;
+size_t atlas_plane_pitch(int32_t Wb);
+cudaError_t atlas_texture_create(float *plane, size_t pitch_bytes, int32_t n_bmp, int32_t Hb, int32_t Wb,
+                                 cudaTextureObject_t *out);
+// Whether an n_bmp x H_b x W_b atlas fits the device's pitch-linear texture limits.
+cudaError_t atlas_texture_fits(int32_t n_bmp, int32_t Hb, int32_t Wb, bool *fits);
 cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
                             double *loss, cudaStream_t st);
 cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32_t *step,

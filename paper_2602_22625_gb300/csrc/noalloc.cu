@@ -37,12 +37,28 @@ constexpr size_t kOffRect = kOffRec + align256(sizeof(PrimRec) * kMaxPrims);
 constexpr size_t kOffHist = kOffRect + align256(sizeof(int4) * kMaxPrims);
 constexpr size_t kOffTileOff = kOffHist + align256(sizeof(int32_t) * kMaxChunks * kMaxTiles);
 constexpr size_t kOffList = kOffTileOff + align256(sizeof(int64_t) * (kMaxTiles + 1));
-constexpr size_t kOffQuad = kOffList + align256(sizeof(int32_t) * kMaxPairs);
-constexpr size_t kOffSat = kOffQuad + align256(sizeof(float4) * kMaxAtlasCells);
-constexpr size_t kScratchBytes = kOffSat + align256(sizeof(int32_t) * kMaxAtlasCells);  // ~5.1 MB
+// texel plane: n_bmp (H_b+1) rows of atlas_plane_pitch(W_b) <= 4 W_b + 124 bytes, and
+// n_bmp (H_b+1) <= cells / 3; plus room to align its base to kTexAlign
+constexpr size_t kPlaneBytes = 4 * kMaxAtlasCells + 124 * (kMaxAtlasCells / 3 + 1) + kTexAlign;
+constexpr size_t kOffPlane = kOffList + align256(sizeof(int32_t) * kMaxPairs);
+constexpr size_t kOffSat = kOffPlane + align256(kPlaneBytes);
+constexpr size_t kScratchBytes = kOffSat + align256(sizeof(int32_t) * kMaxAtlasCells);  // ~6.1 MB
 
 // The scratch area: every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Texture objects over the scratch texel plane, one per atlas shape (W_b, plane rows)
+// and device, created on first use and kept until the process exits (a launch still
+// queued may read one).
+struct TexEntry {
+    int dev;
+    int32_t Wb;
+    int64_t rows;
+    cudaTextureObject_t tex;
+};
+constexpr int kMaxTexEntries = 64;
+TexEntry g_tex[kMaxTexEntries];
+int g_n_tex = 0;
 
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
@@ -79,6 +95,28 @@ int32_t scratch_for_current_device(unsigned char **out) {
         g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_scratch_ptr[dev];
+    return DBMP_OK;
+}
+
+// The texture object for an n_bmp x H_b x W_b atlas in the scratch plane at `plane`.
+int32_t scratch_texture(float *plane, int32_t n_bmp, int32_t Hb, int32_t Wb, cudaTextureObject_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_static(DBMP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    const int64_t rows = (int64_t)n_bmp * (Hb + 1);
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    for (int i = 0; i < g_n_tex; ++i)
+        if (g_tex[i].dev == dev && g_tex[i].Wb == Wb && g_tex[i].rows == rows) {
+            *out = g_tex[i].tex;
+            return DBMP_OK;
+        }
+    if (g_n_tex == kMaxTexEntries)
+        return fail_static(DBMP_ERR_INVALID_ARG, "more than %d distinct atlas shapes", kMaxTexEntries);
+    cudaTextureObject_t t = 0;
+    e = atlas_texture_create(plane, atlas_plane_pitch(Wb), n_bmp, Hb, Wb, &t);
+    if (e != cudaSuccess) return fail_static(DBMP_ERR_CUDA, "texture object: %s", cudaGetErrorString(e));
+    g_tex[g_n_tex++] = TexEntry{dev, Wb, rows, t};
+    *out = t;
     return DBMP_OK;
 }
 
@@ -134,8 +172,11 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
     d.pix_base = 0;
     d.hist_base = 0;
 
-    AtlasView atlas{reinterpret_cast<const float4 *>(base + kOffQuad),
-                    reinterpret_cast<const int32_t *>(base + kOffSat), n_bmp, H_b, W_b};
+    float *plane = reinterpret_cast<float *>(((uintptr_t)(base + kOffPlane) + kTexAlign - 1) &
+                                             ~(uintptr_t)(kTexAlign - 1));
+    cudaTextureObject_t tex = 0;
+    if (int32_t r = scratch_texture(plane, n_bmp, H_b, W_b, &tex)) return r;
+    AtlasView atlas{tex, reinterpret_cast<const int32_t *>(base + kOffSat), n_bmp, H_b, W_b};
 
     // The previous call's contents are still in the array: the status block (error
     // code, counters, work queues) must start at zero; everything else read later is
@@ -146,8 +187,8 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
-        e = launch_quad_build(texels_dev, reinterpret_cast<float4 *>(base + kOffQuad),
-                              reinterpret_cast<int32_t *>(base + kOffSat), n_bmp, H_b, W_b, st);
+        e = launch_atlas_build(texels_dev, plane, (int64_t)(atlas_plane_pitch(W_b) / sizeof(float)),
+                               reinterpret_cast<int32_t *>(base + kOffSat), n_bmp, H_b, W_b, st);
     if (e == cudaSuccess) {
         BinBuffers b{};
         b.rec = reinterpret_cast<PrimRec *>(base + kOffRec);

@@ -8,22 +8,17 @@ namespace dbmp {
 
 namespace {
 
-// quad[b][v0+1][u0+1] = {P[v0,u0], P[v0,u0+1], P[v0+1,u0], P[v0+1,u0+1]}, taps outside
-// the bitmap are 0 (zero padding of the bilinear sample, Sec. S1.1).
-__global__ void k_quad(const float *__restrict__ tex, float4 *__restrict__ quad, int32_t n_bmp,
-                       int32_t Hb, int32_t Wb) {
-    const int64_t cells = (int64_t)(Hb + 1) * (Wb + 1);
-    const int64_t total = cells * n_bmp;
+// plane row b (H_b + 1) + v = bitmap b's row v for v < H_b, zero for v = H_b.
+__global__ void k_plane(const float *__restrict__ tex, float *__restrict__ plane, int64_t pitch, int32_t n_bmp,
+                        int32_t Hb, int32_t Wb) {
+    const int64_t rows = (int64_t)n_bmp * (Hb + 1);
+    const int64_t total = rows * Wb;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / cells);
-        const int c = (int)(i % cells);
-        const int v0 = c / (Wb + 1) - 1, u0 = c % (Wb + 1) - 1;
-        const float *P = tex + (int64_t)b * Hb * Wb;
-        auto tap = [&](int v, int u) -> float {
-            return (u >= 0 && v >= 0 && u < Wb && v < Hb) ? P[(int64_t)v * Wb + u] : 0.0f;
-        };
-        quad[i] = make_float4(tap(v0, u0), tap(v0, u0 + 1), tap(v0 + 1, u0), tap(v0 + 1, u0 + 1));
+        const int64_t row = i / Wb;
+        const int u = (int)(i - row * Wb);
+        const int b = (int)(row / (Hb + 1)), v = (int)(row - (int64_t)b * (Hb + 1));
+        plane[row * pitch + u] = v < Hb ? tex[((int64_t)b * Hb + v) * Wb + u] : 0.0f;
     }
 }
 
@@ -183,12 +178,43 @@ int grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_quad_build(const float *texels, float4 *quad, int32_t *sat, int32_t n_bmp,
-                              int32_t Hb, int32_t Wb, cudaStream_t st) {
-    const int64_t total = (int64_t)n_bmp * (Hb + 1) * (Wb + 1);
-    k_quad<<<grid_for(total, 256), 256, 0, st>>>(texels, quad, n_bmp, Hb, Wb);
+cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int32_t n_bmp,
+                               int32_t Hb, int32_t Wb, cudaStream_t st) {
+    const int64_t total = (int64_t)n_bmp * (Hb + 1) * Wb;
+    k_plane<<<grid_for(total, 256), 256, 0, st>>>(texels, plane, pitch, n_bmp, Hb, Wb);
     k_sat<<<n_bmp, 256, 0, st>>>(texels, sat, Hb, Wb);
     return cudaGetLastError();
+}
+
+size_t atlas_plane_pitch(int32_t Wb) { return ((size_t)Wb * sizeof(float) + 127) & ~(size_t)127; }
+
+cudaError_t atlas_texture_fits(int32_t n_bmp, int32_t Hb, int32_t Wb, bool *fits) {
+    int dev = 0, maxw = 0, maxh = 0, maxp = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLinearWidth, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLinearHeight, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxTexture2DLinearPitch, dev);
+    if (e != cudaSuccess) return e;
+    *fits = Wb <= maxw && (int64_t)n_bmp * (Hb + 1) <= maxh && atlas_plane_pitch(Wb) <= (size_t)maxp;
+    return cudaSuccess;
+}
+
+cudaError_t atlas_texture_create(float *plane, size_t pitch_bytes, int32_t n_bmp, int32_t Hb, int32_t Wb,
+                                 cudaTextureObject_t *out) {
+    cudaResourceDesc rd{};
+    rd.resType = cudaResourceTypePitch2D;
+    rd.res.pitch2D.devPtr = plane;
+    rd.res.pitch2D.desc = cudaCreateChannelDesc<float>();
+    rd.res.pitch2D.width = (size_t)Wb;
+    rd.res.pitch2D.height = (size_t)n_bmp * (Hb + 1);
+    rd.res.pitch2D.pitchInBytes = pitch_bytes;
+    cudaTextureDesc td{};
+    td.addressMode[0] = cudaAddressModeBorder;
+    td.addressMode[1] = cudaAddressModeBorder;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;   // border colour: zero-initialised
+    return cudaCreateTextureObject(out, &rd, &td, nullptr);
 }
 
 cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,

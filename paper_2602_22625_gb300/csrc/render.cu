@@ -11,8 +11,8 @@
 // saturates early frees its warp for the next item instead of idling until the
 // slowest pixel of the tile is done.
 //
-// Bitmaps are read through L1 as 16-byte tap quads (one 128-bit load per bilinear
-// sample).  The forward keeps no per-layer state: it writes T_final and the list
+// Bitmaps are read through the texture path: one gather fetches the four taps of a
+// bilinear sample from the stacked texel plane.  The forward keeps no per-layer state: it writes T_final and the list
 // position of the last contributing layer; the backward walks each region's list
 // back to front from the region's largest n_last, recovering
 // T_k = T_{k+1} / (1 - alpha_k) with exactly the arithmetic the forward used
@@ -76,7 +76,7 @@ __device__ __forceinline__ void prefetch(Prefetch<RPL> &pf, const PrimRec *__res
 __device__ __forceinline__ PrimRec as_rec(float4 a, float4 b, float4 c) {
     PrimRec r;
     r.x = a.x; r.y = a.y; r.A = a.z; r.B = a.w;
-    r.C = b.x; r.D = b.y; r.a = b.z; r.quad_off = __float_as_int(b.w);
+    r.C = b.x; r.D = b.y; r.a = b.z; r.bmp_row = __float_as_int(b.w);
     r.cr = c.x; r.cg = c.y; r.cb = c.z; r.index = __float_as_int(c.w);
     return r;
 }
@@ -105,7 +105,7 @@ __device__ __forceinline__ bool region_hits(const PrimRec &r, const AtlasView &a
     const int u0 = (int)fmaxf(fu0, 0.0f), u1 = (int)fminf(fu1, Wm);
     const int v0 = (int)fmaxf(fv0, 0.0f), v1 = (int)fminf(fv1, Hm);
     const int Ws = at.Wb + 1;
-    const int32_t *S = at.sat + r.quad_off;
+    const int32_t *S = at.sat + r.bmp_row * Ws;
     const int32_t n = __ldg(S + (v1 + 1) * Ws + u1 + 1) - __ldg(S + v0 * Ws + u1 + 1) -
                       __ldg(S + (v1 + 1) * Ws + u0) + __ldg(S + v0 * Ws + u0);
     return n > 0;
@@ -208,7 +208,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     PrimRec *sh = sh_all[warp];
     int *pos = pos_all[warp];
-    const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float tstop = fmaxf(a.T_stop, kTFloor);
@@ -253,9 +252,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
                 for (int t = 0; t < m; ++t) {
                     const PrimRec r = sh[t];
                     const int j = pos[t];
-                    const ColXf cx = col_xf(r, a.atlas.quad, Wq, kw, kv, px);
+                    const ColXf cx = col_xf(r, kw, kv, px);
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) tap_issue(r, cx, Wq, Wbf, Hbf, py[k], T[k] >= tstop, tp[k]);
+                    for (int k = 0; k < PPT; ++k) tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], T[k] >= tstop, tp[k]);
                     // Branch-free per pixel: a pixel that does not composite this layer
                     // has M = 0, so alpha = 0, q = 1 and every update below is an exact
                     // no-op (T * 1 = T, fma(0, c, C) = C).
@@ -366,7 +365,6 @@ __device__ __forceinline__ void warp_reduce8_add(const float v[8], float *dst, i
 // re-walk (used only when the last contributing layer was exactly opaque, so that
 // dividing by (1 - alpha) = 0 cannot recover it).
 __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float px, float py) {
-    const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     float T = 1.0f;
@@ -374,7 +372,7 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
     tp.q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int j = 0; j < upto; ++j) {
         const PrimRec r = a.rec[a.list[g.start + j]];
-        tap_issue(r, col_xf(r, a.atlas.quad, Wq, kw, kv, px), Wq, Wbf, Hbf, py, true, tp);
+        tap_issue(r, col_xf(r, kw, kv, px), a.atlas.tex, Wbf, Hbf, py, true, tp);
         T = __fmul_rn(T, __fsub_rn(1.0f, __fmul_rn(r.a, tap_M(tp))));
     }
     return T;
@@ -391,7 +389,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     PrimRec *sh = sh_all[warp];
     int *pos = pos_all[warp];
-    const int Wq = a.atlas.Wb + 1;
     const float kw = 0.5f * (float)(a.atlas.Wb - 1), kv = 0.5f * (float)(a.atlas.Hb - 1);
     const float Wbf = (float)a.atlas.Wb, Hbf = (float)a.atlas.Hb;
     const float rho = kw / kv, irho = kv / kw;
@@ -457,9 +454,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
             for (int t = m - 1; t >= 0; --t) {
                 const PrimRec r = sh[t];
                 const int j = pos[t];
-                const ColXf cx = col_xf(r, a.atlas.quad, Wq, kw, kv, px);
+                const ColXf cx = col_xf(r, kw, kv, px);
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) tap_issue(r, cx, Wq, Wbf, Hbf, py[k], j <= last[k], tp[k]);
+                for (int k = 0; k < PPT; ++k) tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], j <= last[k], tp[k]);
                 // Phase 1: alpha and the recovered transmittance in front of the layer.
                 // A pixel that does not composite this layer (behind its last layer,
                 // outside the bitmap, zero texels) has M = 0 and keeps T and Y.
