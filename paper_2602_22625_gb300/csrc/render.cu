@@ -468,12 +468,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                     al[k] = __fmul_rn(r.a, M[k]);
                     q[k] = __fsub_rn(1.0f, al[k]);
                     Tk[k] = M[k] > 0.0f ? __fdividef(T[k], q[k]) : T[k];
-                    redo = redo || (M[k] > 0.0f && !(q[k] > 0.0f));
+                    redo = redo || al[k] >= 1.0f;   // 1 - alpha rounds to a positive float iff alpha < 1
                 }
                 if (__any_sync(FULL, redo)) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
-                        if (M[k] > 0.0f && !(q[k] > 0.0f)) Tk[k] = rewalk_T(a, g, j, px, py[k]);
+                        if (al[k] >= 1.0f) Tk[k] = rewalk_T(a, g, j, px, py[k]);
                 }
                 // Phase 2: the eight per-primitive sums.  The factor a (opacity) common
                 // to the geometric sums is applied once per primitive, and the
