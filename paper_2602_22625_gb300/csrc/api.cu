@@ -62,7 +62,6 @@ struct DbmpWorkspace {
     float *graw = nullptr;
     int64_t *tile_off = nullptr;
     int32_t *tile_order = nullptr;
-    int32_t *bucket = nullptr;
     int32_t *list = nullptr;
     int32_t *hist = nullptr;
     CanvasDesc *canvas = nullptr;
@@ -90,7 +89,6 @@ size_t ws_bytes(const DbmpLimits &l) {
     b += sizeof(float) * 8 * (size_t)l.max_prims;
     b += sizeof(int64_t) * ((size_t)l.max_tiles + 1);
     b += sizeof(int32_t) * (size_t)l.max_tiles;
-    b += sizeof(int32_t) * 128;
     b += sizeof(int32_t) * (size_t)l.max_pairs;
     b += sizeof(int32_t) * (size_t)kHistCap;
     b += sizeof(CanvasDesc) * (size_t)l.max_canvases;
@@ -201,7 +199,6 @@ BinBuffers bin_buffers(DbmpWorkspace *ws) {
     b.list = ws->list;
     b.cap = ws->lim.max_pairs;
     b.tile_order = ws->persistent ? ws->tile_order : nullptr;
-    b.bucket = ws->bucket;
     b.status = ws->status;
     b.canvas = ws->canvas;
     b.n_canvas = ws->n_canvas;
@@ -393,7 +390,6 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         {(void **)&ws->graw, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1)},
         {(void **)&ws->tile_off, sizeof(int64_t) * ((size_t)l.max_tiles + 1)},
         {(void **)&ws->tile_order, sizeof(int32_t) * (size_t)l.max_tiles},
-        {(void **)&ws->bucket, sizeof(int32_t) * 128},
         {(void **)&ws->list, sizeof(int32_t) * (size_t)l.max_pairs},
         {(void **)&ws->hist, sizeof(int32_t) * (size_t)kHistCap},
         {(void **)&ws->canvas, sizeof(CanvasDesc) * (size_t)l.max_canvases},
@@ -422,7 +418,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
 
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws) {
     if (!ws) return DBMP_OK;
-    void *ptrs[] = {ws->rec,  ws->rect, ws->graw,   ws->tile_off, ws->tile_order, ws->bucket,
+    void *ptrs[] = {ws->rec,  ws->rect, ws->graw,   ws->tile_off, ws->tile_order,
                     ws->list, ws->hist, ws->canvas, ws->status,   ws->stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -106,7 +106,7 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     p[0] = lo.x; p[1] = lo.y; p[2] = lo.z; p[3] = lo.w;
     p[4] = hi.x; p[5] = hi.y; p[6] = hi.z; p[7] = hi.w;
 
-    // ---- record (FP64, rounded once) ----
+    // ---- record: transform coefficients in FP64, rounded once ----
     const double kw = 0.5 * (double)(atlas.Wb - 1), kv = 0.5 * (double)(atlas.Hb - 1);
     double sn, cs;
     sincos((double)p[3], &sn, &cs);
@@ -118,11 +118,12 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     r.B = (float)(kw * sn * inv_s);
     r.C = (float)(-kv * sn * inv_s);
     r.D = (float)(kv * cs * inv_s);
-    r.a = (float)((double)alpha_max / (1.0 + exp(-(double)p[4])));
+    // opacity and colour sigmoids in fp32 (a few ulps; they enter the image linearly)
+    r.a = alpha_max / (1.0f + expf(-p[4]));
     r.bmp_row = bitmap_id[i] * (atlas.Hb + 1);  // checked below
-    r.cr = (float)(1.0 / (1.0 + exp(-(double)p[5])));
-    r.cg = (float)(1.0 / (1.0 + exp(-(double)p[6])));
-    r.cb = (float)(1.0 / (1.0 + exp(-(double)p[7])));
+    r.cr = 1.0f / (1.0f + expf(-p[5]));
+    r.cg = 1.0f / (1.0f + expf(-p[6]));
+    r.cb = 1.0f / (1.0f + expf(-p[7]));
     r.index = i;
     const int32_t bid = bitmap_id[i];
     const bool bid_ok = bid >= 0 && bid < atlas.n_bmp;
@@ -296,14 +297,24 @@ __global__ void k_colscan(const CanvasDesc *__restrict__ cv, int32_t n_canvas, i
     }
 }
 
+// Longest-list-first ordering key of a tile: 0 for the longest lists ... 63 for empty
+// (power-of-two buckets of the list length).
+__device__ __forceinline__ int len_bucket(int64_t len) {
+    return len <= 0 ? 63 : 62 - (63 - __clzll((unsigned long long)len));
+}
+
 // Exclusive scan of n tile counts in place (single CTA of 1024 threads), writes
-// off[n] = K and the capacity verdict.
+// off[n] = K and the capacity verdict.  With `order` non-null it then lists the tiles
+// longest list first (a counting sort on len_bucket; ties in any order) for the
+// persistent compositors.
 __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, int32_t n,
-                                                   int64_t cap, DevStatus *status) {
+                                                   int64_t cap, DevStatus *status, int32_t *__restrict__ order) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t carry;
+    __shared__ int32_t bucket[64];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) carry = 0;
+    if (tid < 64) bucket[tid] = 0;
     __syncthreads();
     for (int base = 0; base < n; base += 1024 * 4) {
         int64_t v[4];
@@ -313,6 +324,7 @@ __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, in
             const int i = base + tid * 4 + k;
             v[k] = i < n ? off[i] : 0;
             s += v[k];
+            if (order && i < n) atomicAdd(&bucket[len_bucket(v[k])], 1);
         }
         int64_t incl = s;
 #pragma unroll
@@ -351,6 +363,23 @@ __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, in
         status->lists_valid = K <= cap ? 1 : 0;
         if (K > cap) status->code = (int32_t)DBMP_ERR_CAPACITY;
     }
+    if (!order) return;
+    if (warp == 0) {   // bucket counts -> exclusive cursors (64 buckets, two per lane)
+        const int c0 = bucket[2 * lane], c1 = bucket[2 * lane + 1];
+        int incl = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        bucket[2 * lane] = incl - c0 - c1;
+        bucket[2 * lane + 1] = incl - c1;
+    }
+    __syncthreads();   // also orders the offsets written above before the reads below
+    for (int i = tid; i < n; i += 1024) {
+        const int64_t len = (i + 1 < n ? off[i + 1] : carry) - off[i];
+        order[atomicAdd(&bucket[len_bucket(len)], 1)] = i;
+    }
 }
 
 // Writes the entries of one (chunk, slab), one warp per tile: lane l owns the nw
@@ -378,7 +407,15 @@ __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__res
     for (int q0 = s.p0; q0 < s.p1; q0 += blockDim.x) {
         build_masks(rect, q0, s, d.ntx);
         const bool first = q0 == s.p0, last = q0 + (int)blockDim.x >= s.p1;
-        for (int t = warp; t < s.slab_tiles; t += s.nw) {
+        // lane l fetches the list base (tile offset + earlier chunks) of the warp's
+        // tile 32 i + l ahead of time; tile i takes it from lane i % 32
+        int64_t base_ahead = 0;
+        for (int t = warp, it = 0; t < s.slab_tiles; t += s.nw, ++it) {
+            if ((it & 31) == 0) {
+                const int tl = t + lane * s.nw;
+                base_ahead = tl < s.slab_tiles ? toff[tl] + row[tl] : 0;
+            }
+            const int64_t tile_base = __shfl_sync(0xffffffffu, base_ahead, it & 31);
             const int tx = t % d.ntx, ty = t / d.ntx;
             uint32_t v = (s.colw[tx * s.nw + wi] & s.roww[ty * s.nw + wi]) >> sh & keep;
             const int c = __popc(v);
@@ -394,7 +431,7 @@ __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__res
                 continue;
             }
             const int prev = first ? 0 : done[t];
-            int64_t pos = toff[t] + row[t] + prev + (incl - c);
+            int64_t pos = tile_base + prev + (incl - c);
             const int pbase = q0 + bit0;
             while (v) {
                 const int j = __ffs(v) - 1;
@@ -406,41 +443,6 @@ __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__res
     }
 }
 
-// ---- longest-list-first ordering of tiles for the persistent kernels ----
-__device__ __forceinline__ int len_bucket(int64_t len) {
-    // 0 for the longest lists ... 63 for empty
-    return len <= 0 ? 63 : 62 - (63 - __clzll((unsigned long long)len));
-}
-
-__global__ void k_order_count(const int64_t *__restrict__ off, int32_t n, int32_t *__restrict__ bucket) {
-    __shared__ int32_t h[64];
-    if (threadIdx.x < 64) h[threadIdx.x] = 0;
-    __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        atomicAdd(&h[len_bucket(off[t + 1] - off[t])], 1);
-    __syncthreads();
-    if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(&bucket[threadIdx.x], h[threadIdx.x]);
-}
-
-__global__ void k_order_scan(int32_t *bucket) {
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int b = 0; b < 64; ++b) {
-            const int v = bucket[b];
-            bucket[b] = run;        // cursor
-            bucket[64 + b] = run;   // start (kept)
-            run += v;
-        }
-    }
-}
-
-__global__ void k_order_scatter(const int64_t *__restrict__ off, int32_t n, int32_t *bucket,
-                                int32_t *__restrict__ order) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int pos = atomicAdd(&bucket[len_bucket(off[t + 1] - off[t])], 1);
-        order[pos] = t;
-    }
-}
 
 // ---- scaling statistics of a binning (Sec. S4) ----
 // st: [0] listed primitives, [1] sum tau, [2] max tau, [3] max d, [4] tiles,
@@ -541,17 +543,10 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
     }
     k_colscan<<<(b.n_tiles + 31) / 32, dim3(32, 8), 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
                                                              b.tile_off);
-    k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status);
+    k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status, b.tile_order);
     if (b.n_chunks > 0) {
         k_scatter<<<grid_cs, chunk_threads, b.smem_scatter, st>>>(b.rect, b.canvas, b.n_canvas, b.hist,
                                                          b.tile_off, b.list, b.status);
-    }
-    if (b.tile_order) {
-        cudaMemsetAsync(b.bucket, 0, sizeof(int32_t) * 128, st);
-        const int g = min(1024, (b.n_tiles + 255) / 256);
-        k_order_count<<<g, 256, 0, st>>>(b.tile_off, b.n_tiles, b.bucket);
-        k_order_scan<<<1, 32, 0, st>>>(b.bucket);
-        k_order_scatter<<<g, 256, 0, st>>>(b.tile_off, b.n_tiles, b.bucket, b.tile_order);
     }
     return cudaGetLastError();
 }

@@ -163,7 +163,6 @@ struct BinBuffers {
     int32_t *list;            // [cap] primitive indices (global)
     int64_t cap;
     int32_t *tile_order;      // [n_tiles] processing order (longest lists first)
-    int32_t *bucket;          // scratch for the ordering
     DevStatus *status;
     const CanvasDesc *canvas; // [n_canvas]
     int32_t n_canvas;

@@ -198,7 +198,6 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
         b.list = reinterpret_cast<int32_t *>(base + kOffList);
         b.cap = kMaxPairs;
         b.tile_order = nullptr;
-        b.bucket = nullptr;
         b.status = status;
         b.canvas = canvas;
         b.n_canvas = 1;
