@@ -44,9 +44,9 @@ FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
-# kernels one step launches (bin: prep, count, colscan, tilescan, scatter, 3 ordering;
+# kernels one step launches (bin: prep, count, colscan, tilescan with the tile ordering, scatter;
 # fwd; mse; bwd, finalize; adam, step counter)
-LAUNCHES_PER_STEP = 14
+LAUNCHES_PER_STEP = 11
 
 
 def parse():

@@ -76,15 +76,29 @@ __global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg,
     const bool vec = ((((uintptr_t)I) | ((uintptr_t)Tg) | ((uintptr_t)dL)) & 15) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n4; i += nth) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(I) + i);
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(Tg) + i);
-        const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-        reinterpret_cast<float4 *>(dL)[i] = make_float4(scale * d.x, scale * d.y, scale * d.z, scale * d.w);
-        acc_sq(d.x, s, c);
-        acc_sq(d.y, s, c);
-        acc_sq(d.z, s, c);
-        acc_sq(d.w, s, c);
+    const float4 *I4 = reinterpret_cast<const float4 *>(I), *T4 = reinterpret_cast<const float4 *>(Tg);
+    for (int64_t i0 = tid; i0 < n4; i0 += 2 * nth) {
+        // two independent float4 pairs in flight per thread
+        float4 a[2], b[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t i = i0 + u * nth;
+            if (i < n4) {
+                a[u] = __ldg(I4 + i);
+                b[u] = __ldg(T4 + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t i = i0 + u * nth;
+            if (i >= n4) continue;
+            const float4 d = make_float4(a[u].x - b[u].x, a[u].y - b[u].y, a[u].z - b[u].z, a[u].w - b[u].w);
+            reinterpret_cast<float4 *>(dL)[i] = make_float4(scale * d.x, scale * d.y, scale * d.z, scale * d.w);
+            acc_sq(d.x, s, c);
+            acc_sq(d.y, s, c);
+            acc_sq(d.z, s, c);
+            acc_sq(d.w, s, c);
+        }
     }
     for (int64_t i = 4 * n4 + tid; i < n; i += nth) {
         const float d = I[i] - Tg[i];
@@ -168,12 +182,14 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ g, float *__re
 
 __global__ void k_step_inc(int32_t *step) { *step += 1; }
 
-int grid_for(int64_t n, int threads) {
+// Blocks for n work items of `threads` threads, at most `per_sm` resident blocks
+// per SM (grid-stride loops take the rest).
+int grid_for(int64_t n, int threads, int per_sm = 8) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = (n + threads - 1) / threads;
-    return (int)(want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8);
+    return (int)(want < (int64_t)sms * per_sm ? (want > 0 ? want : 1) : (int64_t)sms * per_sm);
 }
 
 }  // namespace
@@ -220,7 +236,9 @@ cudaError_t atlas_texture_create(float *plane, size_t pitch_bytes, int32_t n_bmp
 cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, float *dL,
                             double *loss, cudaStream_t st) {
     cudaMemsetAsync(loss, 0, sizeof(double), st);
-    if (n > 0) k_mse<<<grid_for((n + 3) / 4, 256), 256, 0, st>>>(image, target, n, dL, loss);
+    // four resident blocks per SM: enough loads in flight for HBM with two float4
+    // pairs per thread, and half the FP64 atomics of a full grid
+    if (n > 0) k_mse<<<grid_for((n + 3) / 4, 256, 4), 256, 0, st>>>(image, target, n, dL, loss);
     return cudaGetLastError();
 }
 
