@@ -249,3 +249,41 @@ def test_backward_main_workload_sampled_primitives():
     ref = oracle.grad_selected(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, sel,
                                background=sc.background, T_stop=1e-6)
     grad_close(g[sel], ref, what="main")
+
+
+def scene_lattice():
+    """Primitives placed so that every pixel's bitmap coordinates (U, V) are exact
+    integers or half-integers in both fp32 and FP64 (theta = 0, |A| = |D| in {1/2, 1, 2},
+    centres on the matching lattice): samples sit exactly on texel boundaries, on the
+    bitmap's first and last lattice cells (U or V = -1 and W_b - 1) and just outside.
+    The atlas has no zero texels, so a bitmap read past its last row would pick up the
+    next bitmap's first row."""
+    Hb = Wb = 16                     # kw = kv = 7.5
+    atlas = np.random.default_rng(5).uniform(0.05, 1.0, (3, Hb, Wb)).astype(np.float32)
+    rows = [  # x, y, s, bitmap: U = (7.5 / s)(px - x) + 7.5
+        (50.5, 40.5, 7.5, 0), (60.0, 45.0, 15.0, 1), (55.5, 50.5, -7.5, 2), (52.25, 47.75, 3.75, 0),
+        (44.5, 58.5, 7.5, 1), (70.0, 30.0, 15.0, 2), (38.5, 35.5, -7.5, 0), (64.25, 60.25, 3.75, 1),
+    ]
+    rng = np.random.default_rng(6)
+    p = np.zeros((len(rows), 8), np.float32)
+    for i, (x, y, s, _) in enumerate(rows):
+        p[i, :4] = (x, y, s, 0.0)
+        p[i, 4] = rng.uniform(-0.5, 1.5)           # opacity logit
+        p[i, 5:] = rng.normal(size=3)              # colour logits
+    bid = np.array([r[3] for r in rows], np.int32)
+    return inputs.Scene("lattice_96sq", 96, 96, p, bid, atlas, recipe="lattice-aligned samples")
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_lattice_aligned_samples_match_oracle(tile):
+    """The texture gather's 2 x 2 footprint and its zero border against the FP64
+    bilinear sample exactly at texel boundaries and bitmap edges."""
+    sc = scene_lattice()
+    _, _, _, img, T, nl, _ = gpu_forward(sc, tile, 0.0)
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)
+    assert np.abs(img.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy() - ref["T_final"]).max() <= IMG_TOL
+    gI = np.random.default_rng(13).normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    g = gpu_grad(sc, gI, tile=tile)
+    grad_ref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+    grad_close(g, grad_ref, what=f"lattice tile{tile}")
