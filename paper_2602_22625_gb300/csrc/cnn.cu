@@ -45,50 +45,69 @@ __global__ void k_pack_input(const float *__restrict__ img, int32_t B, uint16_t 
     }
 }
 
-// col[m][(ky*4 + kx)*C + c] = X[b][2oy-1+ky][2ox-1+kx][c] (0 outside), m = (b, oy, ox);
-// one 16-byte chunk (8 channels) per thread.
-__global__ void k_im2col(const uint16_t *__restrict__ X, int32_t B, int32_t H, int32_t W, int32_t C,
+// The network's sides and channel counts are powers of two; the index arithmetic
+// below uses their log2 (shifts and masks instead of 64-bit divisions).
+//
+// col[m][(ky*4 + kx)*C + c] = X[b][2oy-1+ky][2ox-1+kx][c] (0 outside), m = (b, oy, ox),
+// H = W = 2^lh, C = 8 * 2^lc8; one 16-byte chunk (8 channels) per thread.
+__global__ void k_im2col(const uint16_t *__restrict__ X, int32_t B, int32_t lh, int32_t lc8,
                          uint16_t *__restrict__ col) {
-    const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
-    const int64_t n = (int64_t)B * Ho * Wo * 16 * C8;
+    const int lo = lh - 1;   // log2 of the output side
+    const int H = 1 << lh, C8 = 1 << lc8;
+    const int64_t n = ((int64_t)B << (2 * lo + 4 + lc8));
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c8 = (int)(i % C8);
-        const int64_t r = i / C8;
-        const int kk = (int)(r % 16);
-        const int64_t m = r / 16;
-        const int ox = (int)(m % Wo), oy = (int)((m / Wo) % Ho);
-        const int64_t b = m / ((int64_t)Wo * Ho);
-        const int y = 2 * oy - 1 + kk / 4, x = 2 * ox - 1 + kk % 4;
+        const int c8 = (int)(i & (C8 - 1));
+        const int kk = (int)((i >> lc8) & 15);
+        const int64_t m = i >> (lc8 + 4);
+        const int ox = (int)(m & ((1 << lo) - 1)), oy = (int)((m >> lo) & ((1 << lo) - 1));
+        const int64_t b = m >> (2 * lo);
+        const int y = 2 * oy - 1 + (kk >> 2), x = 2 * ox - 1 + (kk & 3);
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (y >= 0 && y < H && x >= 0 && x < W)
-            v = reinterpret_cast<const uint4 *>(X + ((b * H + y) * W + x) * C)[c8];
+        if (y >= 0 && y < H && x >= 0 && x < H)
+            v = reinterpret_cast<const uint4 *>(X + ((((b << lh) + y) << lh) + x) * (8 << lc8))[c8];
         reinterpret_cast<uint4 *>(col)[i] = v;
     }
 }
 
 // dX[b][y][x][c] = sum over (ky, kx) with 2oy-1+ky = y, 2ox-1+kx = x of
-// dcol[(b,oy,ox)][(ky*4+kx)*C + c]; then dZ = X > 0 ? bf16(dX) : 0.
+// dcol[(b,oy,ox)][(ky*4+kx)*C + c]; then dZ = X > 0 ? bf16(dX) : 0.  H = W = 2^lh,
+// C = 2^lc (>= 4); four channels per thread (16-byte loads of dcol).
 __global__ void k_col2im_mask(const float *__restrict__ dcol, const uint16_t *__restrict__ X, int32_t B,
-                              int32_t H, int32_t W, int32_t C, uint16_t *__restrict__ dZ) {
-    const int Ho = H / 2, Wo = W / 2;
-    const int64_t n = (int64_t)B * H * W * C;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int64_t p = i / C;
-        const int x = (int)(p % W), y = (int)((p / W) % H);
-        const int64_t b = p / ((int64_t)W * H);
-        float acc = 0.0f;
+                              int32_t lh, int32_t lc, uint16_t *__restrict__ dZ) {
+    const int lo = lh - 1, Ho = 1 << lo, C = 1 << lc;
+    const int64_t n4 = ((int64_t)B << (2 * lh + lc)) >> 2;
+    for (int64_t i4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i4 < n4;
+         i4 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i4 << 2;
+        const int c = (int)(i & (C - 1));
+        const int64_t p = i >> lc;
+        const int x = (int)(p & ((1 << lh) - 1)), y = (int)((p >> lh) & ((1 << lh) - 1));
+        const int64_t b = p >> (2 * lh);
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         // ky = y + 1 - 2 oy in [0, 4): two candidates of matching parity
         for (int ky = (y + 1) & 1; ky < 4; ky += 2) {
-            const int oy = (y + 1 - ky) / 2;
+            const int oy = (y + 1 - ky) >> 1;
             if (oy < 0 || oy >= Ho) continue;
             for (int kx = (x + 1) & 1; kx < 4; kx += 2) {
-                const int ox = (x + 1 - kx) / 2;
-                if (ox < 0 || ox >= Wo) continue;
-                acc += dcol[((b * Ho + oy) * Wo + ox) * (16 * (int64_t)C) + (ky * 4 + kx) * C + c];
+                const int ox = (x + 1 - kx) >> 1;
+                if (ox < 0 || ox >= Ho) continue;
+                const float4 d = *reinterpret_cast<const float4 *>(
+                    dcol + ((((b << lo) + oy) << lo) + ox) * ((int64_t)16 << lc) + ((ky * 4 + kx) << lc) + c);
+                acc.x += d.x;
+                acc.y += d.y;
+                acc.z += d.z;
+                acc.w += d.w;
             }
         }
-        dZ[i] = bf2f(X[i]) > 0.0f ? f2bf(acc) : (uint16_t)0;
+        const uint2 xv = *reinterpret_cast<const uint2 *>(X + i);
+        const float a[4] = {acc.x, acc.y, acc.z, acc.w};
+        const uint16_t xs[4] = {(uint16_t)(xv.x & 0xffffu), (uint16_t)(xv.x >> 16), (uint16_t)(xv.y & 0xffffu),
+                                (uint16_t)(xv.y >> 16)};
+        uint16_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = bf2f(xs[k]) > 0.0f ? f2bf(a[k]) : (uint16_t)0;
+        *reinterpret_cast<uint2 *>(dZ + i) = make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                                                        (uint32_t)o[2] | ((uint32_t)o[3] << 16));
     }
 }
 
@@ -213,6 +232,13 @@ __global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, 
     }
 }
 
+// log2 of a power of two
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
 int grid1d(int64_t n, int threads = 256) {
     const int64_t g = (n + threads - 1) / threads;
     return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
@@ -265,12 +291,12 @@ static CnnSizes cnn_sizes(int32_t B) {
     CnnSizes s{};
     s.X[0] = (int64_t)B * 256 * 256 * 8;
     for (int l = 0; l < 5; ++l) s.X[l + 1] = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2) * L[l].cout;
-    s.col = 0;
+    s.col = 0;   // all five layers' im2col matrices (kept from the forward for the weight gradients)
     s.dx = (int64_t)B * 64 * 256;
     s.dz = (int64_t)B * 64 * 64;
     for (int l = 0; l < 5; ++l) {
         const int64_t M = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2);
-        s.col = s.col > M * L[l].K ? s.col : M * L[l].K;
+        s.col += M * L[l].K;
         if (l > 0) s.dx = s.dx > M * L[l].K ? s.dx : M * L[l].K;
         s.dz = s.dz > M * L[l].cout ? s.dz : M * L[l].cout;
     }
@@ -347,11 +373,14 @@ cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStrea
     layer_table(L, &np);
     k_pack_input<<<grid1d((int64_t)B * 65536), 256, 0, st>>>(images, B, c.X[0]);
     cudaError_t e = cudaGetLastError();
+    uint16_t *col = c.col;
     for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
         const int H = L[l].hin, Ho = H / 2;
         const int M = B * Ho * Ho;
-        k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, H, H, L[l].cin, c.col);
-        e = gemm(c.col, (int)L[l].K, c.wbf + L[l].w_off, (int)L[l].K, M, L[l].cout, (int)L[l].K,
+        if (l > 0) col += (int64_t)B * (L[l - 1].hin / 2) * (L[l - 1].hin / 2) * L[l - 1].K;
+        k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, ilog2(H), ilog2(L[l].cin / 8),
+                                                                       col);
+        e = gemm(col, (int)L[l].K, c.wbf + L[l].w_off, (int)L[l].K, M, L[l].cout, (int)L[l].K,
                  GEMM_BIAS_RELU_BF16, nullptr, c.X[l + 1], L[l].cout, c.theta + L[l].b_off, 1, c.status, st);
     }
     if (e == cudaSuccess)
@@ -373,7 +402,8 @@ static int split_for(int M, int N, int K) {
     return s < 1 ? 1 : s;
 }
 
-// Loss and gradient w.r.t. all parameters into c.grad (overwritten).
+// Loss and gradient w.r.t. all parameters into c.grad (overwritten).  Reads the
+// activations and im2col matrices the forward of the same batch left in c.
 cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, double *loss, cudaStream_t st) {
     CnnLayer L[6];
     int64_t np;
@@ -391,19 +421,22 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
         e = gemm(c.dz, 64, c.wbf + L[5].w_off, 256, M6, 256, 64, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, 256,
                  nullptr, 1, c.status, st);
     k_mask_to_bf16<<<grid1d((int64_t)M6 * 256), 256, 0, st>>>(c.dx, c.X[5], (int64_t)M6 * 256, c.dz);
+    int64_t col_off[5];
+    col_off[0] = 0;
+    for (int l = 1; l < 5; ++l) col_off[l] = col_off[l - 1] + (int64_t)B * (L[l - 1].hin / 2) * (L[l - 1].hin / 2) * L[l - 1].K;
     for (int l = 4; l >= 0 && e == cudaSuccess; --l) {
         const int H = L[l].hin, Ho = H / 2, M = B * Ho * Ho;
         const int K = (int)L[l].K, Co = L[l].cout;
-        k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, H, H, L[l].cin, c.col);
-        e = gemm(c.dz, Co, c.col, K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off, nullptr,
+        // the forward of this batch left im2col(X_{l-1}) at col + col_off[l]
+        e = gemm(c.dz, Co, c.col + col_off[l], K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off, nullptr,
                  K, nullptr, split_for(Co, K, M), c.status, st);
         k_colsum<uint16_t><<<dim3((Co + 31) / 32, colsum_rows(M, (Co + 31) / 32)), dim3(32, 8), 0, st>>>(
             c.dz, M, Co, c.grad + L[l].b_off);
         if (l == 0 || e != cudaSuccess) break;
         e = gemm(c.dz, Co, c.wbf + L[l].w_off, K, M, K, Co, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, K, nullptr, 1,
                  c.status, st);
-        k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin), 256, 0, st>>>(c.dx, c.X[l], B, H, H, L[l].cin,
-                                                                               c.dzp);
+        k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin / 4), 256, 0, st>>>(c.dx, c.X[l], B, ilog2(H),
+                                                                                   ilog2(L[l].cin), c.dzp);
         uint16_t *t = c.dz;
         c.dz = c.dzp;
         c.dzp = t;

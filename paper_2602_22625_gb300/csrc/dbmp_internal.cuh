@@ -312,7 +312,7 @@ struct CnnBuffers {
     uint16_t *wbf;                 // bf16 copies of the weights
     uint16_t *X[6];                // activations (NHWC bf16): input and five conv outputs
     float *O, *dO, *dx;            // head outputs, their gradient, fp32 product buffer
-    uint16_t *col, *dz, *dzp;      // im2col matrix, conv output gradients (two buffers)
+    uint16_t *col, *dz, *dzp;      // im2col matrices of the five convs, conv output gradients (two buffers)
     int32_t *status;
 };
 
