@@ -238,9 +238,9 @@ __device__ __forceinline__ void build_masks(const int4 *__restrict__ rect, int q
 
 // Number of the pass' primitives overlapping slab tile t (nw is a multiple of 4,
 // the word arrays 16-byte aligned).
-__device__ __forceinline__ int tile_count(const SlabWork &s, int ntx, int t) {
-    const uint4 *cw = reinterpret_cast<const uint4 *>(s.colw + (t % ntx) * s.nw);
-    const uint4 *rw = reinterpret_cast<const uint4 *>(s.roww + (t / ntx) * s.nw);
+__device__ __forceinline__ int tile_count(const SlabWork &s, int tx, int ty) {
+    const uint4 *cw = reinterpret_cast<const uint4 *>(s.colw + tx * s.nw);
+    const uint4 *rw = reinterpret_cast<const uint4 *>(s.roww + ty * s.nw);
     int n = 0;
     for (int i = 0; i < (s.nw >> 2); ++i) {
         const uint4 a = cw[i], b = rw[i];
@@ -258,8 +258,15 @@ __global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restr
     int32_t *row = hist + d.hist_base + (int64_t)s.local * s.ntiles + s.sy0 * d.ntx;
     for (int q0 = s.p0; q0 < s.p1; q0 += blockDim.x) {
         build_masks(rect, q0, s, d.ntx);
-        for (int t = threadIdx.x; t < s.slab_tiles; t += blockDim.x)
-            row[t] = (q0 == s.p0 ? 0 : row[t]) + tile_count(s, d.ntx, t);
+        // (tx, ty) of tile t, advanced by (blockDim % ntx, blockDim / ntx) per step
+        const int dtx = (int)blockDim.x % d.ntx, dty = (int)blockDim.x / d.ntx;
+        int tx = (int)threadIdx.x % d.ntx, ty = (int)threadIdx.x / d.ntx;
+        for (int t = threadIdx.x; t < s.slab_tiles; t += blockDim.x) {
+            row[t] = (q0 == s.p0 ? 0 : row[t]) + tile_count(s, tx, ty);
+            tx += dtx;
+            ty += dty;
+            if (tx >= d.ntx) tx -= d.ntx, ++ty;
+        }
     }
 }
 
@@ -410,13 +417,20 @@ __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__res
         // lane l fetches the list base (tile offset + earlier chunks) of the warp's
         // tile 32 i + l ahead of time; tile i takes it from lane i % 32
         int64_t base_ahead = 0;
+        // (tx, ty) of tile t, advanced by (nw % ntx, nw / ntx) per step without divisions
+        const int dtx = s.nw % d.ntx, dty = s.nw / d.ntx;
+        int tx = warp % d.ntx, ty = warp / d.ntx;
         for (int t = warp, it = 0; t < s.slab_tiles; t += s.nw, ++it) {
+            if (it > 0) {
+                tx += dtx;
+                ty += dty;
+                if (tx >= d.ntx) tx -= d.ntx, ++ty;
+            }
             if ((it & 31) == 0) {
                 const int tl = t + lane * s.nw;
                 base_ahead = tl < s.slab_tiles ? toff[tl] + row[tl] : 0;
             }
             const int64_t tile_base = __shfl_sync(0xffffffffu, base_ahead, it & 31);
-            const int tx = t % d.ntx, ty = t / d.ntx;
             uint32_t v = (s.colw[tx * s.nw + wi] & s.roww[ty * s.nw + wi]) >> sh & keep;
             const int c = __popc(v);
             int incl = c;
