@@ -111,34 +111,55 @@ __global__ void k_col2im_mask(const float *__restrict__ dcol, const uint16_t *__
     }
 }
 
-// out[n] += sum_m in[m][n] (in: bf16 or fp32); out must be zeroed by the caller.
+// out[n] += sum_m in[m][n] (in: bf16 or fp32; N a multiple of VEC = 16 / sizeof(T), at
+// most 256 VEC); out must be zeroed by the caller.  Each thread
+// reads 16 bytes (VEC consecutive columns) of a row, so a warp reads whole rows
+// contiguously; the block's 256 threads cover N / VEC column groups x R rows per step,
+// accumulate in registers over a grid-stride loop on rows, and reduce over their R row
+// slots in shared memory before one atomic per column.
 template <typename T>
-__global__ void k_colsum(const T *__restrict__ in, int32_t M, int32_t N, float *__restrict__ out) {
-    __shared__ float part[8][33];
-    const int n = blockIdx.x * 32 + threadIdx.x;
-    float acc = 0.0f;
-    if (n < N)
-        for (int m = blockIdx.y * 8 + threadIdx.y; m < M; m += gridDim.y * 8) {
-            if constexpr (sizeof(T) == 2)
-                acc += bf2f(in[(int64_t)m * N + n]);
-            else
-                acc += in[(int64_t)m * N + n];
+__global__ void __launch_bounds__(256) k_colsum(const T *__restrict__ in, int32_t M, int32_t N,
+                                                float *__restrict__ out) {
+    constexpr int VEC = 16 / sizeof(T);
+    __shared__ float part[256][VEC + 1];
+    const int G = N / VEC, R = 256 / G;          // column groups, row slots
+    const int gi = threadIdx.x % G, ri = threadIdx.x / G;
+    float acc[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) acc[k] = 0.0f;
+    if (ri < R) {
+        for (int64_t m = (int64_t)blockIdx.x * R + ri; m < M; m += (int64_t)gridDim.x * R) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(in + m * N + gi * VEC);
+            if constexpr (sizeof(T) == 2) {
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc[2 * k] += bf2f((uint16_t)(w[k] & 0xffffu));
+                    acc[2 * k + 1] += bf2f((uint16_t)(w[k] >> 16));
+                }
+            } else {
+                acc[0] += __uint_as_float(v.x);
+                acc[1] += __uint_as_float(v.y);
+                acc[2] += __uint_as_float(v.z);
+                acc[3] += __uint_as_float(v.w);
+            }
         }
-    part[threadIdx.y][threadIdx.x] = acc;
+    }
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) part[threadIdx.x][k] = acc[k];
     __syncthreads();
-    if (threadIdx.y == 0 && n < N) {
-        float s = 0.0f;
-        for (int k = 0; k < 8; ++k) s += part[k][threadIdx.x];
-        atomicAdd(out + n, s);
+    for (int c = threadIdx.x; c < N; c += 256) {   // column c = group c / VEC, element c % VEC
+        float sum = 0.0f;
+        for (int r = 0; r < R; ++r) sum += part[r * G + c / VEC][c % VEC];
+        atomicAdd(out + c, sum);
     }
 }
 
-// Row-blocks of k_colsum: about 8 CTAs per SM over all column groups, each CTA
-// taking at least 64 rows.
-inline int colsum_rows(int64_t M, int col_groups) {
-    const int64_t want = (8 * 152 + col_groups - 1) / col_groups;
-    const int64_t cap = (M + 63) / 64;
-    return (int)std::max<int64_t>(1, std::min(want, cap));
+// Blocks of k_colsum: about 4 per SM, each taking at least 16 steps of rows.
+inline int colsum_blocks(int64_t M, int N, int elem_bytes) {
+    const int R = 256 / (N / (16 / elem_bytes));
+    const int64_t cap = (M + 16 * R - 1) / (16 * R);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4 * 152, cap));
 }
 
 __global__ void k_mask_to_bf16(const float *__restrict__ dX, const uint16_t *__restrict__ X, int64_t n,
@@ -416,7 +437,7 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
     // head: wgrad (dZ^T X5: both operands read MN-major), bias, dgrad (dZ W: W read MN-major)
     cudaError_t e = gemm(c.dz, 64, c.X[5], 256, 64, 256, M6, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN,
                          c.grad + L[5].w_off, nullptr, 256, nullptr, split_for(64, 256, M6), c.status, st);
-    k_colsum<float><<<dim3(2, colsum_rows(M6, 2)), dim3(32, 8), 0, st>>>(c.dO, M6, 64, c.grad + L[5].b_off);
+    k_colsum<float><<<colsum_blocks(M6, 64, 4), 256, 0, st>>>(c.dO, M6, 64, c.grad + L[5].b_off);
     if (e == cudaSuccess)
         e = gemm(c.dz, 64, c.wbf + L[5].w_off, 256, M6, 256, 64, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, 256,
                  nullptr, 1, c.status, st);
@@ -430,8 +451,7 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
         // the forward of this batch left im2col(X_{l-1}) at col + col_off[l]
         e = gemm(c.dz, Co, c.col + col_off[l], K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off, nullptr,
                  K, nullptr, split_for(Co, K, M), c.status, st);
-        k_colsum<uint16_t><<<dim3((Co + 31) / 32, colsum_rows(M, (Co + 31) / 32)), dim3(32, 8), 0, st>>>(
-            c.dz, M, Co, c.grad + L[l].b_off);
+        k_colsum<uint16_t><<<colsum_blocks(M, Co, 2), 256, 0, st>>>(c.dz, M, Co, c.grad + L[l].b_off);
         if (l == 0 || e != cudaSuccess) break;
         e = gemm(c.dz, Co, c.wbf + L[l].w_off, K, M, K, Co, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, K, nullptr, 1,
                  c.status, st);

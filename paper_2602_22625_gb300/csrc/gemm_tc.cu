@@ -370,9 +370,17 @@ cudaError_t init_gemm_kernels() {
 
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
-    if (g.N <= 32 && !g.b_mn) return launch_gemm_t<32>(g, split_k, st);   // MN-major boxes are 64 wide
-    if (g.N <= 64) return launch_gemm_t<64>(g, split_k, st);
-    if (g.N <= 128) return launch_gemm_t<128>(g, split_k, st);
+    // tile width: the narrowest of {32 (K-major B only: MN-major boxes are 64 wide), 64,
+    // 128, 256} covering N, halved (down to 64) while the grid has fewer CTAs than SMs
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+        sms = 152;
+    int bn = g.N <= 32 && !g.b_mn ? 32 : g.N <= 64 ? 64 : g.N <= 128 ? 128 : 256;
+    const int64_t rows = (g.M + kBM - 1) / kBM;
+    while (bn > 64 && rows * ((g.N + bn - 1) / bn) * split_k < sms) bn /= 2;
+    if (bn == 32) return launch_gemm_t<32>(g, split_k, st);
+    if (bn == 64) return launch_gemm_t<64>(g, split_k, st);
+    if (bn == 128) return launch_gemm_t<128>(g, split_k, st);
     return launch_gemm_t<256>(g, split_k, st);
 }
 
