@@ -298,6 +298,7 @@ struct GemmArgs {
     uint16_t *Cb;       // GEMM_BIAS_RELU_BF16
     const float *bias;  // [N] for the bias modes
     int32_t *status;    // set to DBMP_ERR_TIMEOUT if a bounded wait gives up (may be null)
+    int32_t tma_c;      // set by the launcher: C written by TMA tensor stores (aligned C)
 };
 
 cudaError_t init_gemm_kernels();

@@ -12,7 +12,11 @@
 //               stage's `empty` mbarrier, which returns the slot to the producer;
 //               a last commit signals that the accumulator is complete;
 //   warps 2-5   epilogue: each reads the TMEM lane quarter it may access
-//               (32 (warp % 4) ...) with tcgen05.ld, applies the mode, writes C.
+//               (32 (warp % 4) ...) with tcgen05.ld and applies the mode.  When C's
+//               rows are 16-byte aligned, each warp writes 128-byte row pieces of its
+//               32 rows into a double-buffered shared-memory box in the 128-byte
+//               swizzled layout and one lane issues a TMA tensor store of the box (a
+//               TMA reduce-add for split-K); otherwise every lane stores its own row.
 // TMA writes each stage with the 128-byte swizzle, whose eight-row atoms of 1024
 // bytes the shared-memory matrix descriptors describe (layout type SWIZZLE_128B):
 //   K-major operand   one box of 64 (K) x rows: 128-byte rows along K, atoms 1024
@@ -33,6 +37,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -47,13 +52,17 @@ constexpr int kBK = 64;
 constexpr int kThreads = 192;
 constexpr uint32_t kWaitLimit = 1u << 26;  // polls before a wait gives up
 
+// Epilogue staging: per epilogue warp two boxes of 32 rows x 128 bytes.
+constexpr int kStageBox = 32 * 128;
+constexpr int kEpiBytes = 4 * 2 * kStageBox;   // 32 KB
+
 template <int BN>
 struct TileCfg {
     static constexpr int A_BYTES = kBM * kBK * 2;   // 16 KB
     static constexpr int B_BYTES = BN * kBK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int STAGES = 196608 / STAGE > 8 ? 8 : 196608 / STAGE;
-    static constexpr int SMEM = STAGES * STAGE + 1024;   // + alignment slack
+    static constexpr int SMEM = STAGES * STAGE + kEpiBytes + 1024;   // + alignment slack
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -90,6 +99,33 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
             "r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+
+// 2-D tensor store / reduce-add shared -> global of one box (bulk async-group).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// at most one of this thread's bulk groups still reading shared memory
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory"); }
+// all of this thread's bulk groups complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
@@ -156,7 +192,8 @@ __host__ __device__ __forceinline__ int stages_for(int kt_per) {
 
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmC, GemmArgs g) {
     using C = TileCfg<BN>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], acc_done;
@@ -183,6 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+        if (g.tma_c) asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
@@ -255,10 +293,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = ok && !*(volatile int *)&abort_flag;
         ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
         tc_fence_after();
-        if (ok) {
-            const int q = warp & 3;                        // TMEM lanes 32 q .. 32 q + 31
+        const int q = warp & 3;                        // TMEM lanes 32 q .. 32 q + 31
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        if (ok && g.tma_c) {
+            // 128-byte row pieces: 32 fp32 or 64 bf16 columns.  Row `lane` of the box
+            // holds its eight 16-byte chunks at chunk ^ (lane % 8) (128-byte swizzle:
+            // conflict-free for the warp, the layout the tensor map's swizzle reads).
+            const bool bf = g.mode == GEMM_BIAS_RELU_BF16;
+            const int ecols = bf ? 64 : 32;
+            const uint32_t box0 = sbase + S * C::STAGE + (uint32_t)(q * 2 * kStageBox);
+            unsigned char *box0p = smem + S * C::STAGE + q * 2 * kStageBox;
+            int buf = 0;
+            for (int c0 = 0; c0 < BN; c0 += ecols, buf ^= 1) {
+                uint32_t w[32];   // this lane's 128 bytes of the piece
+                for (int h = 0; h < ecols; h += 16) {
+                    float v[16];
+                    if (c0 + h < BN) {   // a 64-column bf16 piece of a 32-wide tile: the rest is
+                        tmem_ld16(trow + c0 + h, v);   // past N (the store clips it) and never read
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+                    }
+                    const int nb = n0 + c0 + h;
+                    if (g.mode == GEMM_BIAS_F32 || g.mode == GEMM_BIAS_RELU_BF16) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                    }
+                    if (bf) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) w[h / 2 + i] = pack_bf16x2(fmaxf(v[2 * i], 0.0f), fmaxf(v[2 * i + 1], 0.0f));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) w[h + i] = __float_as_uint(v[i]);
+                    }
+                }
+                if (lane == 0) bulk_wait_read1();   // the store issued from this buffer two pieces ago
+                __syncwarp();
+                unsigned char *rowp = box0p + buf * kStageBox + lane * 128;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<uint4 *>(rowp + ((j ^ (lane & 7)) << 4)) =
+                        make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t src = box0 + (uint32_t)(buf * kStageBox);
+                    if (g.mode == GEMM_ATOMIC_F32)
+                        tma_reduce_add_2d(&tmC, n0 + c0, m0 + q * 32, src);
+                    else
+                        tma_store_2d(&tmC, n0 + c0, m0 + q * 32, src);
+                    bulk_commit();
+                }
+            }
+            if (lane == 0) bulk_wait_all();
+        } else if (ok) {
             const int row = m0 + q * 32 + lane;
-            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float v[16];
                 tmem_ld16(trow + c0, v);
@@ -330,16 +419,40 @@ bool make_map(CUtensorMap *m, const uint16_t *base, int outer, int inner, int ld
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of the output C (M rows of N elements, row stride ldc) for the
+// epilogue's TMA stores: boxes of 128 bytes (32 fp32 or 64 bf16) x 32 rows, 128-byte
+// swizzle.  False when C's base or row stride is not 16-byte aligned, and for rows of
+// under 256 bytes: there one lane per row already stores a warp's rows contiguously,
+// and the staging buffers would only cost resident CTAs.
+bool make_map_c(CUtensorMap *m, const GemmArgs &g) {
+    const bool bf = g.mode == GEMM_BIAS_RELU_BF16;
+    const void *base = bf ? (const void *)g.Cb : (const void *)g.Cf;
+    const size_t esz = bf ? 2 : 4;
+    if (!base || ((uintptr_t)base & 15) || (((size_t)g.ldc * esz) & 15) || g.ldc < g.N) return false;
+    if ((size_t)g.ldc * esz < 256) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.ldc * esz};
+    const cuuint32_t box[2] = {bf ? 64u : 32u, 32u};
+    const cuuint32_t estr[2] = {1, 1};
+    return g_encode(m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN>
-cudaError_t launch_gemm_t(const GemmArgs &g, int split_k, cudaStream_t st) {
-    CUtensorMap ta, tb;
+cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, cudaStream_t st) {
+    CUtensorMap ta, tb, tc;
+    GemmArgs g = g0;
     const bool ok_a = g.a_mn ? make_map(&ta, g.A, g.K, g.M, g.lda, kBK) : make_map(&ta, g.A, g.M, g.K, g.lda, kBM);
     const bool ok_b = g.b_mn ? make_map(&tb, g.B, g.K, g.N, g.ldb, kBK) : make_map(&tb, g.B, g.N, g.K, g.ldb, BN);
     if (!ok_a || !ok_b) return cudaErrorInvalidValue;
+    memset(&tc, 0, sizeof tc);
+    g.tma_c = make_map_c(&tc, g) ? 1 : 0;
     const dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, split_k);
     const int kt_total = g.K / kBK, kt_per = (kt_total + split_k - 1) / split_k;
-    const int smem = stages_for<BN>(kt_per) * TileCfg<BN>::STAGE + 1024;
-    k_gemm_tma<BN><<<grid, kThreads, smem, st>>>(ta, tb, g);
+    const int smem = stages_for<BN>(kt_per) * TileCfg<BN>::STAGE + (g.tma_c ? kEpiBytes : 0) + 1024;
+    k_gemm_tma<BN><<<grid, kThreads, smem, st>>>(ta, tb, tc, g);
     return cudaGetLastError();
 }
 
@@ -371,13 +484,13 @@ cudaError_t init_gemm_kernels() {
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
     // tile width: the narrowest of {32 (K-major B only: MN-major boxes are 64 wide), 64,
-    // 128, 256} covering N, halved (down to 64) while the grid has fewer CTAs than SMs
+    // 128, 256} covering N, halved (down to 64) while twice the CTAs still fit one wave
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
         sms = 152;
     int bn = g.N <= 32 && !g.b_mn ? 32 : g.N <= 64 ? 64 : g.N <= 128 ? 128 : 256;
     const int64_t rows = (g.M + kBM - 1) / kBM;
-    while (bn > 64 && rows * ((g.N + bn - 1) / bn) * split_k < sms) bn /= 2;
+    while (bn > 64 && 2 * rows * ((g.N + bn - 1) / bn) * split_k <= sms) bn /= 2;
     if (bn == 32) return launch_gemm_t<32>(g, split_k, st);
     if (bn == 64) return launch_gemm_t<64>(g, split_k, st);
     if (bn == 128) return launch_gemm_t<128>(g, split_k, st);
