@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                 // A pixel that does not composite this layer (behind its last layer,
                 // outside the bitmap, zero texels) has M = 0 and keeps T and Y.
                 float M[PPT], al[PPT], q[PPT], Tk[PPT];
-                bool redo = false;
+                bool redo = false, any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     M[k] = tap_M(tp[k]);
@@ -469,7 +469,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                     q[k] = __fsub_rn(1.0f, al[k]);
                     Tk[k] = M[k] > 0.0f ? __fdividef(T[k], q[k]) : T[k];
                     redo = redo || al[k] >= 1.0f;   // 1 - alpha rounds to a positive float iff alpha < 1
+                    any = any || M[k] > 0.0f;
                 }
+                // no pixel of the warp composites this layer: T, Y and the sums are unchanged
+                if (!__any_sync(FULL, any)) continue;
                 if (__any_sync(FULL, redo)) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
@@ -481,13 +484,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                 //   sum dM dMdU Up  = a (sum dA dMdU U - kw sum dA dMdU), and so on.
                 float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3u = 0.0f, s3v = 0.0f, s4 = 0.0f;
                 float s5 = 0.0f, s6 = 0.0f, s7 = 0.0f;
-                bool any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     float dMdU, dMdV;
                     tap_M(tp[k], dMdU, dMdV);
                     const bool c = M[k] > 0.0f;
-                    any = any || c;
                     T[k] = Tk[k];
                     const float gc = g0[k] * r.cr + g1[k] * r.cg + g2[k] * r.cb;
                     const float dA = c ? Tk[k] * (gc - Y[k]) : 0.0f;   // dL/dalpha_k
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                     s7 = fmaf(g2[k], w, s7);
                     Y[k] = fmaf(q[k], Y[k], al[k] * gc);
                 }
-                if (__any_sync(FULL, any)) {
+                {
                     const float ra = r.a;
                     float v[8];
                     v[0] = ra * s0;
