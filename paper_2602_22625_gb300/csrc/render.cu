@@ -4,20 +4,23 @@
 // 32 * PPT pixels (TILE columns, 32 * PPT / TILE rows); one warp composites one
 // region, each lane owning PPT pixels of one column.  Warps are independent
 // workers: each pulls (tile, region) items from a global atomic queue (tiles in
-// longest-list-first order when the binning produced one), stages the tile's
-// primitive records into its own double-buffered shared-memory slice with
-// cp.async, walks the list, and stops as soon as all of its own pixels are
-// saturated (T < T_stop).  There is no CTA-wide barrier, so a region that
-// saturates early frees its warp for the next item instead of idling until the
-// slowest pixel of the tile is done.
+// longest-list-first order when the binning produced one), gathers the tile's
+// primitive records into registers one batch ahead, keeps those whose bitmap is
+// non-empty over the region in its own shared-memory slice, walks them, and stops
+// as soon as all of its own pixels are saturated (T < T_stop).  There is no
+// CTA-wide barrier, so a region that saturates early frees its warp for the next
+// item instead of idling until the slowest pixel of the tile is done.
 //
 // Bitmaps are read through the texture path: one gather fetches the four taps of a
-// bilinear sample from the stacked texel plane.  The forward keeps no per-layer state: it writes T_final and the list
-// position of the last contributing layer; the backward walks each region's list
-// back to front from the region's largest n_last, recovering
-// T_k = T_{k+1} / (1 - alpha_k) with exactly the arithmetic the forward used
-// (sample_bitmap), reduces the eight per-primitive sums across the warp with
-// shuffles and adds them with one atomic per primitive per warp.
+// bilinear sample from the stacked texel plane.  Every pixel runs the same
+// straight-line blend for every record (a pixel that does not composite it has
+// M = 0, which makes each update an exact no-op).  The forward keeps no per-layer
+// state: it writes T_final and the list position of the last contributing layer;
+// the backward walks each region's list back to front from the region's largest
+// n_last, recovering T_k = T_{k+1} / (1 - alpha_k) with exactly the arithmetic the
+// forward used (col_xf, tap_issue, tap_M), reduces the eight per-primitive sums
+// across the warp with shuffles and adds them with one atomic per primitive per
+// warp.
 #include <cuda_runtime.h>
 #include <math.h>
 
