@@ -65,3 +65,25 @@ def test_static_forward_rejects_sizes_beyond_its_maximum():
         D.dbmp_render_fwd_static(600, 600, to_dev(sc.params), to_dev(sc.bitmap_id), to_dev(sc.atlas), 1.0,
                                  D.make_background((1, 1, 1)), 0.0, img, T, nl)
     assert e.value.code == D.DBMP_ERR_INVALID_ARG and "512" in str(e.value)
+
+
+def test_static_forward_alternating_atlas_shapes():
+    """The entry point keeps one texture object per atlas shape over its scratch texel
+    plane: shapes A, B, A in a row (the third call reuses A's object, with the plane
+    rewritten by B in between) all match the regular entry points."""
+    cuda()
+    a = inputs.tiny(seed=44, N=120, H=96, W=112)                  # 1 x 64 x 64 soft disc
+    b = inputs.tiny(seed=45, N=80, H=90, W=90)
+    b.atlas = np.random.default_rng(9).uniform(0.05, 1.0, (3, 16, 24)).astype(np.float32)
+    b.bitmap_id = (np.arange(b.N) % 3).astype(np.int32)
+    bg = D.make_background((1.0, 1.0, 1.0))
+    for sc in (a, b, a):
+        img = torch.full((3, sc.H, sc.W), -5.0, device="cuda")
+        T = torch.full((sc.H, sc.W), -5.0, device="cuda")
+        nl = torch.full((sc.H, sc.W), -5, dtype=torch.int32, device="cuda")
+        st = D.dbmp_render_fwd_static(sc.H, sc.W, to_dev(sc.params), to_dev(sc.bitmap_id),
+                                      to_dev(sc.atlas), 1.0, bg, 0.0, img, T, nl)
+        assert st.code == 0 and st.pairs_required > 0
+        ref_img, ref_T, _ = regular_forward(sc, bg, 0.0)
+        assert np.abs(img.cpu().numpy() - ref_img).max() <= IMG_TOL
+        assert np.abs(T.cpu().numpy() - ref_T).max() <= IMG_TOL
