@@ -299,6 +299,7 @@ struct GemmArgs {
     const float *bias;  // [N] for the bias modes
     int32_t *status;    // set to DBMP_ERR_TIMEOUT if a bounded wait gives up (may be null)
     int32_t tma_c;      // set by the launcher: C written by TMA tensor stores (aligned C)
+    int32_t split;      // set by the launcher: K splits (partial tiles added into C)
 };
 
 cudaError_t init_gemm_kernels();

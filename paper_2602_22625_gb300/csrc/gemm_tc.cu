@@ -2,15 +2,16 @@
 //
 //   C[m][n] (op)= sum_k A[m][k] * B[n][k]      A: M x K, B: N x K, both K-contiguous BF16
 //
-// One CTA computes a 128 x BN tile (BN = 32 ... 256) with three warp roles (the
-// stage ring has as many stages as the CTA's K steps, at most 4-8 by BN):
+// A persistent CTA per SM computes 128 x BN tiles (BN = 32 ... 256) in turn, with
+// three warp roles:
 //   warp 0      producer: one thread issues the TMA tensor copies of the A and B
 //               K-slabs (64 wide) into a ring of shared-memory stages, each stage
 //               announced on its `full` mbarrier with the bytes it expects;
-//   warp 1      allocates BN TMEM columns; one thread issues tcgen05.mma (M = 128,
-//               N = BN, K = 16 per instruction) for each stage and commits it to the
-//               stage's `empty` mbarrier, which returns the slot to the producer;
-//               a last commit signals that the accumulator is complete;
+//   warp 1      allocates 2 BN TMEM columns (two accumulators); one thread issues
+//               tcgen05.mma (M = 128, N = BN, K = 16 per instruction) for each stage
+//               and commits it to the stage's `empty` mbarrier, which returns the slot
+//               to the producer; a commit after a tile's last stage marks its
+//               accumulator full;
 //   warps 2-5   epilogue: each reads the TMEM lane quarter it may access
 //               (32 (warp % 4) ...) with tcgen05.ld and applies the mode.  When C's
 //               rows are 16-byte aligned, each warp writes 128-byte row pieces of its
@@ -27,11 +28,11 @@
 //                     boxes 8 KB apart along M/N (leading byte offset); a K step of
 //                     16 advances the start address by 2048 bytes.
 // Rows past M or N are zero-filled by the tensor copy; K must be a multiple of 64.
-// Split-K over gridDim.z adds partial tiles with fp32 atomics.
+// Split-K adds partial tiles into C (TMA reduce-add, or fp32 atomics).
 //
-// Every mbarrier wait is bounded.  A wait that gives up sets the status flag; the
-// producer still waits (bounded) for the copies it issued, the accumulator's last
-// commit is still made, and TMEM is freed before the CTA exits.
+// Every mbarrier wait is bounded.  A wait that gives up sets the status flag and every
+// role stops at its next check; the producer still waits (bounded) for the copies it
+// issued, the MMA thread for the MMAs it issued, and TMEM is freed before the CTA exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -39,6 +40,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "dbmp_internal.cuh"
@@ -183,32 +185,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stages a CTA uses: as many as it has K steps, up to the ring's capacity, so short-K
-// products keep several CTAs resident per SM.
-template <int BN>
-__host__ __device__ __forceinline__ int stages_for(int kt_per) {
-    return kt_per < TileCfg<BN>::STAGES ? (kt_per > 0 ? kt_per : 1) : TileCfg<BN>::STAGES;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
+// Persistent kernel: CTA c takes tiles c, c + gridDim.x, ... of the tiles_m x tiles_n
+// x split schedule (m fastest, so that concurrent CTAs share the B tile).  The stage
+// ring runs across tile boundaries, and the accumulator is double-buffered in TMEM
+// (2 BN columns): the MMA thread fills buffer lt & 1 of the CTA's tile lt while the
+// epilogue warps drain the other.
+//   acc_full[b]   completed by the MMA commit after a tile's last K step;
+//   acc_empty[b]  completed when the four epilogue warps have read the buffer.
+// Tiles of a split with no K steps are skipped by every role alike.
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, GemmArgs g) {
     using C = TileCfg<BN>;
+    constexpr int S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], acc_done;
+    __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int tiles_m = (g.M + kBM - 1) / kBM, tiles_n = (g.N + BN - 1) / BN;
     const int kt_total = g.K / kBK;
-    const int kt_per = (kt_total + gridDim.z - 1) / gridDim.z;
-    const int kt0 = blockIdx.z * kt_per;
-    const int T = max(0, min(kt_per, kt_total - kt0));
-    const int S = stages_for<BN>(kt_per);
+    const int kt_per = (kt_total + g.split - 1) / g.split;
+    const int n_tiles = tiles_m * tiles_n * g.split;
+    // tile t -> output origin (m0, n0) and K steps [kt0, kt0 + T)
+    auto decode = [&](int t, int &m0, int &n0, int &kt0, int &T) {
+        const int tm = t % tiles_m, r = t / tiles_m;
+        m0 = tm * kBM;
+        n0 = (r % tiles_n) * BN;
+        kt0 = (r / tiles_n) * kt_per;
+        T = max(0, min(kt_per, kt_total - kt0));
+    };
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -216,7 +230,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(&acc_done), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 4);
+        }
+        mbar_init(smem_u32(&drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -224,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                     "r"((uint32_t)BN)
+                     "r"((uint32_t)(2 * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -233,173 +251,202 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0 && T > 0) {
+    if (warp == 0 && lane == 0) {
         // ---- producer ----
-        int issued = 0, s = 0;
-        uint32_t ph = 0;   // parity of the current use of slot s
-        for (int i = 0; i < T; ++i) {
-            if (i >= S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1)) {
-                abort_flag = 1;
-                break;
+        uint32_t u = 0;   // stage uses issued: slot u % S, its (u / S)-th use
+        int s = 0;
+        uint32_t ph = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            int m0, n0, kt0, T;
+            decode(t, m0, n0, kt0, T);
+            for (int i = 0; i < T; ++i) {
+                if (u >= (uint32_t)S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1)) abort_flag = 1;
+                if (*(volatile int *)&abort_flag) break;
+                const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);
+                const int k = (kt0 + i) * kBK;
+                mbar_expect_tx(fb, C::STAGE);
+                if (g.a_mn) {
+                    for (int j = 0; j < kBM / 64; ++j) tma_load_2d(sa + j * 8192, &tmA, m0 + 64 * j, k, fb);
+                } else {
+                    tma_load_2d(sa, &tmA, k, m0, fb);
+                }
+                if (g.b_mn) {
+                    for (int j = 0; j < BN / 64; ++j)
+                        tma_load_2d(sa + C::A_BYTES + j * 8192, &tmB, n0 + 64 * j, k, fb);
+                } else {
+                    tma_load_2d(sa + C::A_BYTES, &tmB, k, n0, fb);
+                }
+                ++u;
+                if (++s == S) s = 0, ph ^= 1;
             }
             if (*(volatile int *)&abort_flag) break;
-            const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);
-            const int k = (kt0 + i) * kBK;
-            mbar_expect_tx(fb, C::STAGE);
-            if (g.a_mn) {
-                for (int j = 0; j < kBM / 64; ++j) tma_load_2d(sa + j * 8192, &tmA, m0 + 64 * j, k, fb);
-            } else {
-                tma_load_2d(sa, &tmA, k, m0, fb);
-            }
-            if (g.b_mn) {
-                for (int j = 0; j < BN / 64; ++j) tma_load_2d(sa + C::A_BYTES + j * 8192, &tmB, n0 + 64 * j, k, fb);
-            } else {
-                tma_load_2d(sa + C::A_BYTES, &tmB, k, n0, fb);
-            }
-            issued = i + 1;
-            if (++s == S) s = 0, ph ^= 1;
         }
         // every issued copy lands before the CTA can exit
-        for (int i = issued > S ? issued - S : 0; i < issued; ++i)
-            if (!mbar_wait(smem_u32(&full[i % S]), (i / S) & 1)) abort_flag = 1;
-    } else if (warp == 1 && lane == 0 && T > 0) {
+        for (uint32_t v = u > (uint32_t)S ? u - S : 0; v < u; ++v)
+            if (!mbar_wait(smem_u32(&full[v % S]), (v / S) & 1)) abort_flag = 1;
+    } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         const uint32_t idesc = instr_desc<BN>(g.a_mn != 0, g.b_mn != 0);
         // per K step of 16: +32 B (K-major) or +2048 B (MN-major); leading byte offsets
         const uint32_t a_step = g.a_mn ? 2048u : 32u, b_step = g.b_mn ? 2048u : 32u;
         const uint32_t a_lbo = g.a_mn ? 8192u : 16u, b_lbo = g.b_mn ? 8192u : 16u;
-        int s = 0;
+        int s = 0, lt = 0;
         uint32_t ph = 0;
-        for (int i = 0; i < T; ++i) {
-            if (!mbar_wait(smem_u32(&full[s]), ph)) {
-                abort_flag = 1;
-                break;
-            }
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            int m0, n0, kt0, T;
+            decode(t, m0, n0, kt0, T);
+            if (T == 0) continue;
+            const int b = lt & 1;
+            if (lt >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1)) abort_flag = 1;
             if (*(volatile int *)&abort_flag) break;
             tc_fence_after();
-            const uint32_t sa = sbase + s * C::STAGE, sb = sa + C::A_BYTES;
+            const uint32_t d = tmem + (uint32_t)(b * BN);
+            for (int i = 0; i < T; ++i) {
+                if (!mbar_wait(smem_u32(&full[s]), ph)) abort_flag = 1;
+                if (*(volatile int *)&abort_flag) break;
+                tc_fence_after();
+                const uint32_t sa = sbase + s * C::STAGE, sb = sa + C::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-                mma_bf16(tmem, sw128_desc(sa + kk * a_step, a_lbo), sw128_desc(sb + kk * b_step, b_lbo), idesc,
-                         (i > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(smem_u32(&empty[s]));
-            if (++s == S) s = 0, ph ^= 1;
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                    mma_bf16(d, sw128_desc(sa + kk * a_step, a_lbo), sw128_desc(sb + kk * b_step, b_lbo), idesc,
+                             (i > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(smem_u32(&empty[s]));
+                if (++s == S) s = 0, ph ^= 1;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            mma_commit(smem_u32(&acc_full[b]));   // arrives once the tile's MMAs have completed
+            ++lt;
         }
-        mma_commit(smem_u32(&acc_done));   // arrives once every issued MMA has completed
+        mma_commit(smem_u32(&drain));             // every MMA issued by this thread
+        if (!mbar_wait(smem_u32(&drain), 0)) abort_flag = 1;
     } else if (warp >= 2) {
         // ---- epilogue ----
-        bool ok = T > 0 && mbar_wait(smem_u32(&acc_done), 0);
-        ok = __all_sync(0xffffffffu, ok);
-        ok = ok && !*(volatile int *)&abort_flag;
-        ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
-        tc_fence_after();
-        const int q = warp & 3;                        // TMEM lanes 32 q .. 32 q + 31
-        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-        if (ok && g.tma_c) {
-            // 128-byte row pieces: 32 fp32 or 64 bf16 columns.  Row `lane` of the box
-            // holds its eight 16-byte chunks at chunk ^ (lane % 8) (128-byte swizzle:
-            // conflict-free for the warp, the layout the tensor map's swizzle reads).
-            const bool bf = g.mode == GEMM_BIAS_RELU_BF16;
-            const int ecols = bf ? 64 : 32;
-            const uint32_t box0 = sbase + S * C::STAGE + (uint32_t)(q * 2 * kStageBox);
-            unsigned char *box0p = smem + S * C::STAGE + q * 2 * kStageBox;
-            int buf = 0;
-            for (int c0 = 0; c0 < BN; c0 += ecols, buf ^= 1) {
-                uint32_t w[32];   // this lane's 128 bytes of the piece
-                for (int h = 0; h < ecols; h += 16) {
+        const int q = warp & 3;                   // TMEM lanes 32 q .. 32 q + 31
+        const bool bf = g.mode == GEMM_BIAS_RELU_BF16;
+        const int ecols = bf ? 64 : 32;           // columns of a 128-byte row piece
+        const uint32_t box0 = sbase + S * C::STAGE + (uint32_t)(q * 2 * kStageBox);
+        unsigned char *box0p = smem + S * C::STAGE + q * 2 * kStageBox;
+        int buf = 0, lt = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            int m0, n0, kt0, T;
+            decode(t, m0, n0, kt0, T);
+            if (T == 0) continue;
+            const int b = lt & 1;
+            bool ok = mbar_wait(smem_u32(&acc_full[b]), (lt >> 1) & 1);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) abort_flag = 1;
+            ok = ok && !*(volatile int *)&abort_flag;
+            ok = __all_sync(0xffffffffu, ok);     // tcgen05.ld below is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t trow = tmem + (uint32_t)(b * BN) + ((uint32_t)(q * 32) << 16);
+            if (g.tma_c) {
+                // Row `lane` of a staging box holds its eight 16-byte chunks at
+                // chunk ^ (lane % 8) (128-byte swizzle: conflict-free for the warp,
+                // the layout the tensor map's swizzle reads).
+                for (int c0 = 0; c0 < BN; c0 += ecols, buf ^= 1) {
+                    uint32_t w[32];   // this lane's 128 bytes of the piece
+                    for (int h = 0; h < ecols; h += 16) {
+                        float v[16];
+                        if (c0 + h < BN) {   // a 64-column bf16 piece of a 32-wide tile: the rest is
+                            tmem_ld16(trow + c0 + h, v);   // past N (the store clips it) and never read
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+                        }
+                        const int nb = n0 + c0 + h;
+                        if (g.mode == GEMM_BIAS_F32 || g.mode == GEMM_BIAS_RELU_BF16) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                        }
+                        if (bf) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                w[h / 2 + i] = pack_bf16x2(fmaxf(v[2 * i], 0.0f), fmaxf(v[2 * i + 1], 0.0f));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) w[h + i] = __float_as_uint(v[i]);
+                        }
+                    }
+                    if (lane == 0) bulk_wait_read1();   // the store issued from this buffer two pieces ago
+                    __syncwarp();
+                    unsigned char *rowp = box0p + buf * kStageBox + lane * 128;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<uint4 *>(rowp + ((j ^ (lane & 7)) << 4)) =
+                            make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        const uint32_t src = box0 + (uint32_t)(buf * kStageBox);
+                        if (g.mode == GEMM_ATOMIC_F32)
+                            tma_reduce_add_2d(&tmC, n0 + c0, m0 + q * 32, src);
+                        else
+                            tma_store_2d(&tmC, n0 + c0, m0 + q * 32, src);
+                        bulk_commit();
+                    }
+                }
+            } else {
+                const int row = m0 + q * 32 + lane;
+                for (int c0 = 0; c0 < BN; c0 += 16) {
                     float v[16];
-                    if (c0 + h < BN) {   // a 64-column bf16 piece of a 32-wide tile: the rest is
-                        tmem_ld16(trow + c0 + h, v);   // past N (the store clips it) and never read
-                    } else {
+                    tmem_ld16(trow + c0, v);
+                    if (row >= g.M) continue;
+                    const int nb = n0 + c0;
+                    const bool full16 = nb + 16 <= g.N;
+                    if (g.mode == GEMM_STORE_F32 || g.mode == GEMM_BIAS_F32) {
+                        float *out = g.Cf + (size_t)row * g.ldc + nb;
+                        if (g.mode == GEMM_BIAS_F32) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = 0.0f;
-                    }
-                    const int nb = n0 + c0 + h;
-                    if (g.mode == GEMM_BIAS_F32 || g.mode == GEMM_BIAS_RELU_BF16) {
+                            for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                        }
+                        if (full16 && ((g.ldc & 3) == 0) && ((nb & 3) == 0)) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
-                    }
-                    if (bf) {
+                            for (int i = 0; i < 4; ++i)
+                                reinterpret_cast<float4 *>(out)[i] =
+                                    make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) w[h / 2 + i] = pack_bf16x2(fmaxf(v[2 * i], 0.0f), fmaxf(v[2 * i + 1], 0.0f));
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) w[h + i] = __float_as_uint(v[i]);
-                    }
-                }
-                if (lane == 0) bulk_wait_read1();   // the store issued from this buffer two pieces ago
-                __syncwarp();
-                unsigned char *rowp = box0p + buf * kStageBox + lane * 128;
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    *reinterpret_cast<uint4 *>(rowp + ((j ^ (lane & 7)) << 4)) =
-                        make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    const uint32_t src = box0 + (uint32_t)(buf * kStageBox);
-                    if (g.mode == GEMM_ATOMIC_F32)
-                        tma_reduce_add_2d(&tmC, n0 + c0, m0 + q * 32, src);
-                    else
-                        tma_store_2d(&tmC, n0 + c0, m0 + q * 32, src);
-                    bulk_commit();
-                }
-            }
-            if (lane == 0) bulk_wait_all();
-        } else if (ok) {
-            const int row = m0 + q * 32 + lane;
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                tmem_ld16(trow + c0, v);
-                if (row >= g.M) continue;
-                const int nb = n0 + c0;
-                const bool full16 = nb + 16 <= g.N;
-                if (g.mode == GEMM_STORE_F32 || g.mode == GEMM_BIAS_F32) {
-                    float *out = g.Cf + (size_t)row * g.ldc + nb;
-                    if (g.mode == GEMM_BIAS_F32) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
-                    }
-                    if (full16 && ((g.ldc & 3) == 0) && ((nb & 3) == 0)) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            reinterpret_cast<float4 *>(out)[i] =
-                                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                    } else {
+                            for (int i = 0; i < 16; ++i)
+                                if (nb + i < g.N) out[i] = v[i];
+                        }
+                    } else if (g.mode == GEMM_ATOMIC_F32) {
+                        float *out = g.Cf + (size_t)row * g.ldc + nb;
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (nb + i < g.N) out[i] = v[i];
-                    }
-                } else if (g.mode == GEMM_ATOMIC_F32) {
-                    float *out = g.Cf + (size_t)row * g.ldc + nb;
+                            if (nb + i < g.N) atomicAdd(out + i, v[i]);
+                    } else {  // GEMM_BIAS_RELU_BF16
+                        __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + (size_t)row * g.ldc + nb;
+                        __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (nb + i < g.N) atomicAdd(out + i, v[i]);
-                } else {  // GEMM_BIAS_RELU_BF16
-                    __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + (size_t)row * g.ldc + nb;
-                    __align__(16) __nv_bfloat16 h[16];
+                        for (int i = 0; i < 16; ++i) {
+                            const float bb = nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                            h[i] = __float2bfloat16_rn(fmaxf(v[i] + bb, 0.0f));
+                        }
+                        if (full16 && ((g.ldc & 7) == 0) && ((nb & 7) == 0)) {
+                            reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
+                            reinterpret_cast<uint4 *>(out)[1] = reinterpret_cast<const uint4 *>(h)[1];
+                        } else {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float b = nb + i < g.N ? g.bias[nb + i] : 0.0f;
-                        h[i] = __float2bfloat16_rn(fmaxf(v[i] + b, 0.0f));
-                    }
-                    if (full16 && ((g.ldc & 7) == 0) && ((nb & 7) == 0)) {
-                        reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
-                        reinterpret_cast<uint4 *>(out)[1] = reinterpret_cast<const uint4 *>(h)[1];
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (nb + i < g.N) out[i] = h[i];
+                            for (int i = 0; i < 16; ++i)
+                                if (nb + i < g.N) out[i] = h[i];
+                        }
                     }
                 }
             }
+            // this warp's reads of buffer b are complete: release it to the MMA thread
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+            ++lt;
         }
+        if (lane == 0) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0 && abort_flag && g.status) atomicExch(g.status, (int)DBMP_ERR_TIMEOUT);
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)BN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)(2 * BN))
                      : "memory");
 }
 
@@ -441,7 +488,7 @@ bool make_map_c(CUtensorMap *m, const GemmArgs &g) {
 }
 
 template <int BN>
-cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, cudaStream_t st) {
+cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, int sms, cudaStream_t st) {
     CUtensorMap ta, tb, tc;
     GemmArgs g = g0;
     const bool ok_a = g.a_mn ? make_map(&ta, g.A, g.K, g.M, g.lda, kBK) : make_map(&ta, g.A, g.M, g.K, g.lda, kBM);
@@ -449,9 +496,14 @@ cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, cudaStream_t st) {
     if (!ok_a || !ok_b) return cudaErrorInvalidValue;
     memset(&tc, 0, sizeof tc);
     g.tma_c = make_map_c(&tc, g) ? 1 : 0;
-    const dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, split_k);
-    const int kt_total = g.K / kBK, kt_per = (kt_total + split_k - 1) / split_k;
-    const int smem = stages_for<BN>(kt_per) * TileCfg<BN>::STAGE + (g.tma_c ? kEpiBytes : 0) + 1024;
+    g.split = split_k;
+    const int64_t tiles = (int64_t)((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN) * split_k;
+    if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
+    // One CTA per SM: the ring and the staging boxes take most of the SM's shared
+    // memory, the double-buffered accumulator 2 BN of its 512 TMEM columns.  The ring
+    // runs across tiles, so a short-K product still has several tiles' operands in flight.
+    const int smem = TileCfg<BN>::SMEM - (g.tma_c ? 0 : kEpiBytes);
+    const int grid = (int)(tiles < sms ? tiles : sms);
     k_gemm_tma<BN><<<grid, kThreads, smem, st>>>(ta, tb, tc, g);
     return cudaGetLastError();
 }
@@ -491,10 +543,10 @@ cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     int bn = g.N <= 32 && !g.b_mn ? 32 : g.N <= 64 ? 64 : g.N <= 128 ? 128 : 256;
     const int64_t rows = (g.M + kBM - 1) / kBM;
     while (bn > 64 && 2 * rows * ((g.N + bn - 1) / bn) * split_k <= sms) bn /= 2;
-    if (bn == 32) return launch_gemm_t<32>(g, split_k, st);
-    if (bn == 64) return launch_gemm_t<64>(g, split_k, st);
-    if (bn == 128) return launch_gemm_t<128>(g, split_k, st);
-    return launch_gemm_t<256>(g, split_k, st);
+    if (bn == 32) return launch_gemm_t<32>(g, split_k, sms, st);
+    if (bn == 64) return launch_gemm_t<64>(g, split_k, sms, st);
+    if (bn == 128) return launch_gemm_t<128>(g, split_k, sms, st);
+    return launch_gemm_t<256>(g, split_k, sms, st);
 }
 
 }  // namespace dbmp
