@@ -123,9 +123,23 @@ def cpu_baseline(min_s=10.0, max_reps=40):
         t0 = time.perf_counter()
         oracle_band_step(sc, tgt, 0, sc.H)
         times.append(time.perf_counter() - t0)
-    return {"value": statistics.mean(times) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # one core: a band of rows through the canvas centre, scaled to the whole canvas
+    rows = 32
+    y0 = sc.H // 2 - rows // 2
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle_band_step(sc, tgt, y0, y0 + rows)
+        one = (time.perf_counter() - t0) * sc.H / rows
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": statistics.mean(times) * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
             "sample": f"the whole {sc.H}x{sc.W} canvas, fwd+bwd in FP64 (T_stop={T_STOP}), {len(times)} "
-                      f"repetitions, {sum(times):.1f} s of CPU work"}
+                      f"repetitions, {sum(times):.1f} s of CPU work",
+            "one_core": {"value": one * 1e3, "unit": "ms", "cores": 1,
+                         "sample": f"rows {y0}..{y0 + rows} of {sc.H}, fwd+bwd in FP64, scaled x{sc.H // rows} "
+                                   f"to the whole canvas"}}
 
 
 def run_reference(args):

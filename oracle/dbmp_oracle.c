@@ -670,3 +670,13 @@ int32_t oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the calling thread's later parallel regions (n >= 1); for timing the
+ * oracle on one core and on all of them.  Changes no result. */
+void oracle_set_num_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads((int)n);
+#else
+    (void)n;
+#endif
+}

@@ -70,6 +70,8 @@ def lib():
         L.oracle_spec_abs_sincos.argtypes = [ctypes.c_float, _f32p, _f32p]
         L.oracle_num_threads.restype = ctypes.c_int32
         L.oracle_num_threads.argtypes = []
+        L.oracle_set_num_threads.restype = None
+        L.oracle_set_num_threads.argtypes = [ctypes.c_int32]
         L.oracle_bin_footprint.restype = None
         L.oracle_bin_footprint.argtypes = [ctypes.c_int32, _f32p, ctypes.c_int32, ctypes.c_int32, _f64p]
         L.oracle_local_variance.restype = None
@@ -109,6 +111,11 @@ def _bg(background, H, W):
 
 def num_threads():
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n):
+    """Threads of the oracle's later parallel loops (timing only; results unchanged)."""
+    lib().oracle_set_num_threads(int(n))
 
 
 def render(H, W, params, bitmap_id, atlas, alpha_max=1.0, background=(1.0, 1.0, 1.0),
