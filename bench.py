@@ -235,6 +235,27 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def binning_hbm(N, K, n_tiles, bin_ms):
+    """The binning pass against the HBM roofline: its algorithmic bytes are the
+    parameters and bitmap ids read (36 B per primitive), the records written for the
+    compositors (48 B per primitive), the tile lists (4 B per entry) and the tile
+    offsets (8 B per tile)."""
+    peak = hbm_peak_gbs()
+    nbytes = 36 * N + 48 * N + 4 * K + 8 * (n_tiles + 1)
+    achieved = nbytes / (bin_ms * 1e-3) / 1e9
+    return {"bytes": nbytes, "ms": bin_ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
+
+
+def hbm_peak_gbs():
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0   # fallback: one earlier measurement on a GB300
+
+
 def traffic_for(kernel_key, tile, batch, ppt):
     """DRAM bytes per launch from the committed ncu summary, if it still matches the
     source and was taken at this tuning (tile, batch, the pass' pixels per lane)."""
@@ -668,6 +689,8 @@ def run_dbmp(args):
                      "flops_per_unit": FLOPS_BWD_PAIR if key == "bwd" else FLOPS_FWD_PAIR,
                      "algorithmic_flops_per_launch": flops, "kernel_ms": dms,
                      "traffic": traffic_for(key, tuning["tile"], tuning["batch"], kppt)},
+        "binning_hbm": binning_hbm(N, pairs_end[3], (H // tuning["tile"]) * (W // tuning["tile"]),
+                                   float(phase[:, 0].mean())),
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clk.summary(),
