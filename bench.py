@@ -75,6 +75,23 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seeds(rank):
+    """Seeds of a rank's own canvas and target: every rank renders a workload of the
+    same shape and distribution (weak scaling, no exchange)."""
+    return 2 + rank, 1002 + rank
+
+
+def max_over_ranks(values, device, world):
+    """Element-wise maximum of `values` (floats) over all ranks (the slowest rank's
+    time); a plain copy when world == 1."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def config(extra=None):
     c = {"workload": WORKLOAD, "H": 1024, "W": 1024, "N": 20000, "atlas": "16 strokes 128x128",
          "scale": "LogNormal(-2,0.7)*W", "T_stop": T_STOP, "background": "white",
@@ -513,8 +530,9 @@ def run_dbmp(args):
     D.load()
 
     # inputs: each rank renders its own workload (weak scaling: no exchange)
-    sc = inputs.main(seed=2 + rank)
-    tgt = inputs.main(seed=1002 + rank)
+    seed, tgt_seed = rank_seeds(rank)
+    sc = inputs.main(seed=seed)
+    tgt = inputs.main(seed=tgt_seed)
     atlas_t = torch.from_numpy(sc.atlas).to(dev)
     atlas = D.dbmp_atlas_create(atlas_t)
     N, H, W = sc.N, sc.H, sc.W
@@ -637,10 +655,7 @@ def run_dbmp(args):
     d2h = 8
 
     # ---- max over ranks ----
-    vals = torch.tensor([ms, float(np.mean(e2e_ms))], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms, e2e = float(vals[0]), float(vals[1])
+    ms, e2e = max_over_ranks([ms, float(np.mean(e2e_ms))], dev, world)
 
     fwd_ms = float(phase[:, 1].mean())
     bwd_ms = float(phase[:, 3].mean())
