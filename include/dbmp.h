@@ -316,8 +316,11 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
  *   mode 2: Cb[m][n] = bf16(max(acc + bias[n], 0))   (bf16, row stride ldc)
  *   mode 3: Cf[m][n] = acc + bias[n]
  *   split_k  number of CTAs sharing the K range of a tile (mode 1 only if > 1)
+ *   mode flag 64: failure-detection test only: no operand copy is issued, so the
+ *               pipeline's waits run out (2 s each) and status_dev is set to
+ *               DBMP_ERR_TIMEOUT; C is not written; the context stays usable
  *   status_dev  optional device int32 set to DBMP_ERR_TIMEOUT if a bounded
- *               wait on the tensor-core pipeline gave up (nullable) */
+ *               wait on the tensor-core pipeline gave up after 2 s (nullable) */
 int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev, int32_t ldb,
                        int32_t M, int32_t N, int32_t K, int32_t mode, float *Cf_dev,
                        uint16_t *Cb_dev, int32_t ldc, const float *bias_dev, int32_t split_k,

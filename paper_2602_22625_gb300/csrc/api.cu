@@ -798,12 +798,13 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
     if (!A_dev || !B_dev) return fail(DBMP_ERR_INVALID_ARG, "A / B is NULL");
     if (M < 1 || N < 1 || K < 64 || K % 64) return fail(DBMP_ERR_INVALID_ARG, "need M, N >= 1 and K a multiple of 64");
     const int a_mn = (mode & GEMM_A_MN) != 0, b_mn = (mode & GEMM_B_MN) != 0;
-    mode &= ~(GEMM_A_MN | GEMM_B_MN);
+    const int stall = (mode & GEMM_TEST_STALL) != 0;
+    mode &= ~(GEMM_A_MN | GEMM_B_MN | GEMM_TEST_STALL);
     if (lda < (a_mn ? M : K) || ldb < (b_mn ? N : K) || (lda & 7) || (ldb & 7) || (((uintptr_t)A_dev) & 15) ||
         (((uintptr_t)B_dev) & 15))
         return fail(DBMP_ERR_INVALID_ARG,
                     "A / B rows must be 16-byte aligned, lda / ldb multiples of 8 and >= the contiguous extent");
-    if (mode < 0 || mode > 3) return fail(DBMP_ERR_INVALID_ARG, "mode must be 0..3 (+ layout flags 16, 32)");
+    if (mode < 0 || mode > 3) return fail(DBMP_ERR_INVALID_ARG, "mode must be 0..3 (+ flags 16, 32, 64)");
     if (ldc < N) return fail(DBMP_ERR_INVALID_ARG, "ldc < N");
     if ((mode == 2 && !Cb_dev) || (mode != 2 && !Cf_dev)) return fail(DBMP_ERR_INVALID_ARG, "output is NULL");
     if ((mode == 2 || mode == 3) && !bias_dev) return fail(DBMP_ERR_INVALID_ARG, "bias is NULL");
@@ -813,6 +814,7 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
     std::call_once(once, [] { init_err = init_gemm_kernels(); });
     DBMP_CUDA(init_err, "gemm set-up");
     GemmArgs g{A_dev, B_dev, M, N, K, lda, ldb, ldc, mode, a_mn, b_mn, Cf_dev, Cb_dev, bias_dev, status_dev};
+    g.stall = stall;
     DBMP_CUDA(launch_gemm(g, split_k, (cudaStream_t)stream), "gemm launch");
     return DBMP_OK;
 }

@@ -287,6 +287,8 @@ enum GemmMode { GEMM_STORE_F32 = 0, GEMM_ATOMIC_F32 = 1, GEMM_BIAS_RELU_BF16 = 2
 // Operand layout flags of dbmp_gemm_bf16's mode: A (B) given MN-major, i.e. as the
 // K x M (K x N) matrix with M (N) contiguous.
 constexpr int32_t GEMM_A_MN = 16, GEMM_B_MN = 32;
+// dbmp_gemm_bf16 mode flag of the timeout test (see GemmArgs::stall)
+constexpr int32_t GEMM_TEST_STALL = 64;
 
 struct GemmArgs {
     const uint16_t *A;
@@ -300,6 +302,8 @@ struct GemmArgs {
     int32_t *status;    // set to DBMP_ERR_TIMEOUT if a bounded wait gives up (may be null)
     int32_t tma_c;      // set by the launcher: C written by TMA tensor stores (aligned C)
     int32_t split;      // set by the launcher: K splits (partial tiles added into C)
+    int32_t stall;      // test hook: the producer issues no copies, so the MMA and
+                        // epilogue waits run out and status becomes DBMP_ERR_TIMEOUT
 };
 
 cudaError_t init_gemm_kernels();

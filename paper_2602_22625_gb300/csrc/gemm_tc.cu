@@ -52,7 +52,7 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;
 constexpr int kThreads = 192;
-constexpr uint32_t kWaitLimit = 1u << 26;  // polls before a wait gives up
+constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait gives up after 2 s
 
 // Epilogue staging: per epilogue warp two boxes of 32 rows x 128 bytes.
 constexpr int kStageBox = 32 * 128;
@@ -79,9 +79,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Waits for the phase of parity `parity` to complete; false if it gave up.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of parity `parity` to complete; false if it gave up after
+// kWaitNs of the global timer.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0;; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -89,8 +97,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((i & 63) == 0) {
+            const unsigned long long t = global_ns();
+            if (i == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
+        }
     }
-    return false;
 }
 
 // 2-D tensor copy global -> shared (coordinates: x along K, y along rows),
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
             int m0, n0, kt0, T;
             decode(t, m0, n0, kt0, T);
-            for (int i = 0; i < T; ++i) {
+            for (int i = 0; i < T && !g.stall; ++i) {
                 if (u >= (uint32_t)S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1)) abort_flag = 1;
                 if (*(volatile int *)&abort_flag) break;
                 const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);

@@ -105,3 +105,22 @@ def test_gemm_mn_major_operands(M, N, K, a_mn, b_mn):
     if K >= 1024:   # split-K with atomics on the same layouts
         C1 = gemm_mn(At, Bt, M, N, K, 1, a_mn, b_mn, lda, ldb, split_k=4)
         assert (C1.double() - ref).abs().max().item() <= 2e-6 * K * 4
+
+
+def test_gemm_wait_timeout_sets_status_and_leaves_the_context_usable():
+    """Failure detection without a fault: with the test flag the producer issues no
+    copies, the pipeline's bounded waits run out after 2 s, the kernel returns and the
+    status word reads DBMP_ERR_TIMEOUT; C is not written and the next GEMM runs."""
+    cuda()
+    L = D.load()
+    A, B, ref = operands(256, 128, 128, 7)
+    C = torch.full((256, 128), -7.0, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gemm(A, B, 0)   # declares the argument types
+    D._check(L.dbmp_gemm_bf16(A.data_ptr(), 128, B.data_ptr(), 128, 256, 128, 128, 0 | 64, C.data_ptr(), None,
+                              128, None, 1, status.data_ptr(), torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert status.item() == D.DBMP_ERR_TIMEOUT
+    assert bool((C == -7.0).all())
+    C2 = gemm(A, B, 0)
+    assert (C2.double() - ref).abs().max().item() <= 2e-6 * 128 * 4
