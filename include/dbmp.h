@@ -115,6 +115,13 @@ int32_t dbmp_workspace_bytes(const DbmpLimits *limits, size_t *bytes);
  * per-chunk histograms, gradient accumulators, status block). */
 int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out);
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws);
+/* Testing aid, in place of a memory sanitizer: fills every scratch buffer of the
+ * workspace (records, rectangles, gradient sums, tile offsets, order and lists,
+ * histograms, canvas descriptors, statistics; not the status block) with 0xFF
+ * bytes, i.e. NaN floats and -1 integers, stream-ordered.  A later call that read a
+ * buffer before writing it would then return different results.  Call it before
+ * dbmp_batch_plan / dbmp_bin: it also erases a stored plan. */
+int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream);
 
 /* Device-side status block, read (and cleared) by dbmp_status_poll. */
 typedef struct {
@@ -221,7 +228,8 @@ int32_t dbmp_render_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBac
  * no per-layer state); the exact derivative is taken, including the background
  * term Eq. S5 omits.  Per-(pixel, layer) terms are reduced across each warp by
  * shuffles, then added with one atomic per primitive per warp, so dparams is
- * exact up to float32 summation order.
+ * exact up to float32 summation order.  The chain rule to s and nu reads the
+ * params_dev given to dbmp_bin: that buffer must still hold the same values.
  *   dparams_dev  float32 [N][8], ACCUMULATED into (zero it first). */
 int32_t dbmp_render_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg,
                         float T_stop, const float *dL_dimage_dev, const float *dL_dalpha_dev,

@@ -416,6 +416,28 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
     return DBMP_OK;
 }
 
+int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "workspace is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DbmpLimits &l = ws->lim;
+    struct {
+        void *p;
+        size_t n;
+    } bufs[] = {
+        {ws->rec, sizeof(PrimRec) * (size_t)std::max(l.max_prims, 1)},
+        {ws->rect, sizeof(int4) * (size_t)std::max(l.max_prims, 1)},
+        {ws->graw, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1)},
+        {ws->tile_off, sizeof(int64_t) * ((size_t)l.max_tiles + 1)},
+        {ws->tile_order, sizeof(int32_t) * (size_t)l.max_tiles},
+        {ws->list, sizeof(int32_t) * (size_t)l.max_pairs},
+        {ws->hist, sizeof(int32_t) * (size_t)kHistCap},
+        {ws->canvas, sizeof(CanvasDesc) * (size_t)l.max_canvases},
+        {ws->stats, sizeof(unsigned long long) * kBinStatsWords},
+    };
+    for (auto &b : bufs) DBMP_CUDA(cudaMemsetAsync(b.p, 0xFF, b.n, st), "poison");
+    return DBMP_OK;
+}
+
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws) {
     if (!ws) return DBMP_OK;
     void *ptrs[] = {ws->rec,  ws->rect, ws->graw,   ws->tile_off, ws->tile_order,

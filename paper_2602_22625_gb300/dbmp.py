@@ -35,6 +35,7 @@ EXPORTS = (
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
     "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
+    "dbmp_workspace_poison",
 )
 
 
@@ -115,6 +116,7 @@ def load(build_if_missing: bool = True):
         "dbmp_workspace_bytes": (_i32, [ctypes.POINTER(DbmpLimits), ctypes.POINTER(ctypes.c_size_t)]),
         "dbmp_workspace_create": (_i32, [ctypes.POINTER(DbmpLimits), ctypes.POINTER(_vp)]),
         "dbmp_workspace_destroy": (_i32, [_vp]),
+        "dbmp_workspace_poison": (_i32, [_vp, _vp]),
         "dbmp_status_poll": (_i32, [_vp, _vp, ctypes.POINTER(DbmpDeviceStatus)]),
         "dbmp_bin": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _f32, _vp]),
         "dbmp_get_tile_lists": (_i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(_i32), _vp]),
@@ -242,6 +244,10 @@ def dbmp_workspace_create(max_prims, max_tiles, max_pairs, max_canvases=1):
 
 def dbmp_workspace_destroy(ws):
     _check(load().dbmp_workspace_destroy(ws))
+
+
+def dbmp_workspace_poison(ws, stream=None):
+    _check(load().dbmp_workspace_poison(ws, _stream(stream)))
 
 
 def dbmp_status_poll(ws, stream=None, raise_on_error=True):

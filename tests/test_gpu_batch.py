@@ -35,13 +35,15 @@ def concat(scenes):
     return params, bid, off, pix
 
 
-def run_batch(scenes, atlas_np, tuning, gI=None, T_stop=0.0, bg=(1.0, 1.0, 1.0)):
+def run_batch(scenes, atlas_np, tuning, gI=None, T_stop=0.0, bg=(1.0, 1.0, 1.0), poison=False):
     cuda()
     params, bid, off, pix = concat(scenes)
     N, P = int(off[-1]), int(pix[-1])
     atlas = D.dbmp_atlas_create(to_dev(atlas_np))
     n_tiles = sum(-(-s.W // 8) * -(-s.H // 8) for s in scenes)
     ws = D.dbmp_workspace_create(max(N, 1), n_tiles, 1 << 24, len(scenes))
+    if poison:
+        D.dbmp_workspace_poison(ws)
     try:
         D.dbmp_batch_plan(ws, [s.H for s in scenes], [s.W for s in scenes], off.tolist(), *tuning)
         p, b = to_dev(params), to_dev(bid)
@@ -312,6 +314,108 @@ def test_autotune_picks_a_supported_tuning():
                             D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
         ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas)
         assert np.abs(image.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
+@pytest.mark.parametrize("tuning", [(16, 32, 4), (8, 64, 1), (32, 32, 2)], ids=lambda t: f"t{t[0]}b{t[1]}p{t[2]}")
+def test_poisoned_workspace_changes_nothing(tuning):
+    """Every scratch buffer of the workspace filled with NaN / -1 before planning:
+    binning, forward and backward must read nothing they did not write, so the images
+    are bit-identical to a clean workspace's and the gradients equal up to the order of
+    their float atomics."""
+    scenes, atlas = small_batch(seed=37)
+    params, bid, off, pix = concat(scenes)
+    rng = np.random.default_rng(5)
+    gI = rng.normal(size=3 * int(pix[-1])).astype(np.float32)
+    img0, T0, g0, _ = run_batch(scenes, atlas, tuning, gI=gI)
+    img1, T1, g1, st = run_batch(scenes, atlas, tuning, gI=gI, poison=True)
+    assert st.code == 0
+    assert np.array_equal(img0, img1) and np.array_equal(T0, T1)
+    assert np.all(np.isfinite(g1))
+    grad_close(g1, g0, rel=1e-5, what="poisoned")
+
+
+def test_poisoned_single_canvas_workspace_matches_oracle():
+    cuda()
+    sc = inputs.tiny(seed=8, N=70, H=61, W=83)
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, 16 * 16, 1 << 20, 1)
+    D.dbmp_workspace_poison(ws)
+    try:
+        bg = D.make_background(sc.background)
+        params, bid = to_dev(sc.params), to_dev(sc.bitmap_id)   # the backward reads params again
+        D.dbmp_bin(ws, sc.H, sc.W, 16, params, bid, sc.N, atlas, 1.0)
+        image = torch.empty(3, sc.H, sc.W, device="cuda")
+        T = torch.empty(sc.H, sc.W, device="cuda")
+        nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+        D.dbmp_render_fwd(ws, atlas, bg, 0.0, image, T, nl)
+        gI = np.random.default_rng(6).normal(size=(3, sc.H, sc.W)).astype(np.float32)
+        dp = torch.zeros(sc.N, 8, device="cuda")
+        D.dbmp_render_bwd(ws, atlas, bg, 0.0, to_dev(gI), None, T, nl, dp)
+        st = D.dbmp_status_poll(ws)
+        assert st.code == 0
+        ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)
+        assert np.abs(image.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+        gref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+        grad_close(dp.cpu().numpy().astype(np.float64), gref, what="poisoned single")
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
+def test_gpu_optimisation_resumes_from_a_checkpoint(tmp_path):
+    """Six optimisation steps in one go against three, a checkpoint (parameters, Adam
+    moments, step counter) written and read back into fresh device buffers, and three
+    more.  The file is exact; the gradients' float atomics sum in any order, so the two
+    runs agree to rounding, not bit for bit."""
+    from paper_2602_22625_gb300 import checkpoint
+    cuda()
+    sc = inputs.tiny(seed=9, N=60, H=64, W=64)
+    tg = inputs.tiny(seed=10, N=60, H=64, W=64)
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, 64, 1 << 20, 1)
+    try:
+        D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N], tile=16, batch=32, ppt=2)
+        bg = D.make_background(sc.background)
+        bid = to_dev(sc.bitmap_id)
+        image = torch.empty(3, sc.H, sc.W, device="cuda")
+        T = torch.empty(sc.H, sc.W, device="cuda")
+        nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+        target = torch.empty(3, sc.H, sc.W, device="cuda")
+        D.dbmp_batch_render(ws, to_dev(tg.params), to_dev(tg.bitmap_id), atlas, 1.0, bg, 0.0,
+                            D.BATCH_BIN | D.BATCH_FWD, target, T, nl)
+        dL = torch.empty(3, sc.H, sc.W, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dp = torch.zeros(sc.N, 8, device="cuda")
+        cfg = D.adam_config(lr=0.05, gamma=0.99, zero_grad=True)
+
+        def steps(p, m, v, step, n):
+            for _ in range(n):
+                D.dbmp_batch_render(ws, p, bid, atlas, 1.0, bg, 0.0, D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
+                D.dbmp_mse_grad(image, target, dL, loss)
+                D.dbmp_batch_render(ws, p, bid, atlas, 1.0, bg, 0.0, D.BATCH_BWD, image, T, nl, dL, dp)
+                D.dbmp_adam_step(p, dp, m, v, step, cfg)
+
+        def fresh():
+            return (to_dev(sc.params), torch.zeros(sc.N, 8, device="cuda"), torch.zeros(sc.N, 8, device="cuda"),
+                    torch.zeros(1, dtype=torch.int32, device="cuda"))
+
+        p, m, v, step = fresh()
+        steps(p, m, v, step, 6)
+        ref = p.cpu().numpy()
+        p, m, v, step = fresh()
+        steps(p, m, v, step, 3)
+        ck = tmp_path / "gpu.ckpt"
+        checkpoint.save(ck, {"params": p, "m": m, "v": v, "step": step}, step=int(step.item()))
+        a, s, _ = checkpoint.load(ck)
+        assert s == 3 and np.array_equal(a["params"], p.cpu().numpy())
+        p2, m2, v2, step2 = (to_dev(a["params"]), to_dev(a["m"]), to_dev(a["v"]), to_dev(a["step"]))
+        steps(p2, m2, v2, step2, 3)
+        assert int(step2.item()) == 6
+        got = p2.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)

@@ -251,13 +251,14 @@ def test_backward_main_workload_sampled_primitives():
     grad_close(g[sel], ref, what="main")
 
 
-def scene_lattice():
+
+def scene_lattice(shift=0.0):
     """Primitives placed so that every pixel's bitmap coordinates (U, V) are exact
-    integers or half-integers in both fp32 and FP64 (theta = 0, |A| = |D| in {1/2, 1, 2},
-    centres on the matching lattice): samples sit exactly on texel boundaries, on the
-    bitmap's first and last lattice cells (U or V = -1 and W_b - 1) and just outside.
-    The atlas has no zero texels, so a bitmap read past its last row would pick up the
-    next bitmap's first row."""
+    integers or half-integers (theta = 0, |A| = |D| in {1/2, 1, 2}, centres on the
+    matching lattice), moved by `shift` px in x and y: samples sit on texel boundaries
+    (shift 0) or |A| shift to one side of them, on the bitmap's first and last lattice
+    cells (U or V = -1 and W_b - 1) and just outside.  The atlas has no zero texels, so
+    a bitmap read past its last row would pick up the next bitmap's first row."""
     Hb = Wb = 16                     # kw = kv = 7.5
     atlas = np.random.default_rng(5).uniform(0.05, 1.0, (3, Hb, Wb)).astype(np.float32)
     rows = [  # x, y, s, bitmap: U = (7.5 / s)(px - x) + 7.5
@@ -267,7 +268,7 @@ def scene_lattice():
     rng = np.random.default_rng(6)
     p = np.zeros((len(rows), 8), np.float32)
     for i, (x, y, s, _) in enumerate(rows):
-        p[i, :4] = (x, y, s, 0.0)
+        p[i, :4] = (x + shift, y + shift, s, 0.0)
         p[i, 4] = rng.uniform(-0.5, 1.5)           # opacity logit
         p[i, 5:] = rng.normal(size=3)              # colour logits
     bid = np.array([r[3] for r in rows], np.int32)
@@ -275,10 +276,15 @@ def scene_lattice():
 
 
 @pytest.mark.parametrize("tile", [8, 16])
-def test_lattice_aligned_samples_match_oracle(tile):
+@pytest.mark.parametrize("shift", [0.0, 2.0 ** -12, -(2.0 ** -12)])
+def test_lattice_aligned_samples_match_oracle(tile, shift):
     """The texture gather's 2 x 2 footprint and its zero border against the FP64
-    bilinear sample exactly at texel boundaries and bitmap edges."""
-    sc = scene_lattice()
+    bilinear sample at texel boundaries and bitmap edges.  M is continuous across a
+    texel boundary, so on the lattice (shift 0) the image and the opacity and colour
+    gradients are compared; the geometric gradients are one-sided there (which side
+    is decided by each side's rounding of U) and are compared on the shifted lattices,
+    where U = k -/+ |A| 2^-12 is exact in fp32 and far from k in FP64."""
+    sc = scene_lattice(shift)
     _, _, _, img, T, nl, _ = gpu_forward(sc, tile, 0.0)
     ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)
     assert np.abs(img.cpu().numpy() - ref["image"]).max() <= IMG_TOL
@@ -286,4 +292,7 @@ def test_lattice_aligned_samples_match_oracle(tile):
     gI = np.random.default_rng(13).normal(size=(3, sc.H, sc.W)).astype(np.float32)
     g = gpu_grad(sc, gI, tile=tile)
     grad_ref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
-    grad_close(g, grad_ref, what=f"lattice tile{tile}")
+    cols = slice(4, 8) if shift == 0.0 else slice(0, 8)
+    gz, rz = np.zeros_like(g), np.zeros_like(grad_ref)
+    gz[:, cols], rz[:, cols] = g[:, cols], grad_ref[:, cols]
+    grad_close(gz, rz, what=f"lattice tile{tile} shift{shift}")
