@@ -4,6 +4,7 @@ batched rasterizer from seeded anchored parameter sets (100k pairs would be ~79 
 of images if stored)."""
 from __future__ import annotations
 
+import json
 import math
 import time
 
@@ -113,10 +114,11 @@ def time_to(psnrs, times, goal):
 
 
 def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0, 1.0, 1.0), t0=None,
-           psnr_goal=30.0, bitmap_id=None):
+           psnr_goal=30.0, bitmap_id=None, log=None):
     """The plain method: Adam on all primitive parameters of one 256^2 canvas against
     target_image (3, 256, 256).  Returns (psnr per step, seconds per step since t0,
-    seconds to reach psnr_goal or None, final params)."""
+    seconds to reach psnr_goal or None, final params).  With `log` (a writable text
+    file) each step appends one JSON line {"step", "loss", "psnr", "s"}."""
     params = init_params.reshape(N_PRIMS, 8).contiguous().clone()
     bid = torch.zeros(N_PRIMS, dtype=torch.int32, device="cuda") if bitmap_id is None else bitmap_id
     ws = D.dbmp_workspace_create(N_PRIMS, (SIDE // 16) ** 2, N_PRIMS * 256, 1)
@@ -142,6 +144,8 @@ def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0,
             ps = 10.0 * math.log10(1.0 / max(mse, 1e-30))
             psnrs.append(ps)
             times.append(time.perf_counter() - t0)
+            if log is not None:
+                log.write(json.dumps({"step": len(psnrs) - 1, "loss": mse, "psnr": ps, "s": times[-1]}) + "\n")
             if hit is None and ps >= psnr_goal:
                 hit = times[-1]
             if len(psnrs) > steps:

@@ -1,6 +1,9 @@
 """The proposal network on the tensor cores against its FP64 oracle (same bfloat16
 rounding points), and what a briefly trained network gains over random
 initialisation before and after the plain refinement."""
+import io
+import json
+
 import numpy as np
 import pytest
 
@@ -98,7 +101,10 @@ def test_trained_proposals_beat_random_init():
         rand = torch.from_numpy(inputs.random_init(999_002, 4)).cuda()
         gains0, gains60 = [], []
         for i in range(4):
-            pl, _, _, _ = proposer.refine(learned[i], targets[i], scenes.atlas, steps=60)
+            log = io.StringIO()
+            pl, _, _, _ = proposer.refine(learned[i], targets[i], scenes.atlas, steps=60, log=log)
+            rows = [json.loads(r) for r in log.getvalue().splitlines()]   # one JSON line per step
+            assert [r["step"] for r in rows] == list(range(61)) and [r["psnr"] for r in rows] == pl
             pr, _, _, _ = proposer.refine(rand[i], targets[i], scenes.atlas, steps=60)
             gains0.append(pl[0] - pr[0])
             gains60.append(pl[-1] - pr[-1])
