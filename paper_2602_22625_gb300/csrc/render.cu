@@ -1,8 +1,8 @@
 // Forward and backward compositors (Eqs. 1-5, 8; Algorithm 1; Eq. 6, Eqs. S4-S5).
 //
 // Work decomposition: a tile of TILE x TILE pixels is split into regions of
-// 32 * PPT pixels (TILE columns, 32 * PPT / TILE rows); one warp composites one
-// region, each lane owning PPT pixels of one column.  Warps are independent
+// 32 * PPT pixels (RW = min(TILE, 16) columns, 32 * PPT / RW rows); one warp
+// composites one region, each lane owning PPT pixels of one column.  Warps are independent
 // workers: each pulls (tile, region) items from a global atomic queue (tiles in
 // longest-list-first order when the binning produced one), gathers the tile's
 // primitive records into registers one batch ahead, keeps those whose bitmap is
@@ -154,18 +154,25 @@ struct Region {
     int len;          // tile list length
 };
 
+// Width of a warp's region: the tile's width up to 16 pixels, so that a 32-pixel
+// tile (shorter lists in total, cheaper binning) still gives each warp a compact
+// 16-pixel-wide region to cull against.
+constexpr int region_w(int tile) { return tile < 16 ? tile : 16; }
+
 template <int TILE, int PPT>
 __device__ __forceinline__ Region region_of(const RenderArgs &a, int item) {
-    constexpr int R = TILE * TILE / (32 * PPT);   // regions per tile
-    constexpr int RH = 32 * PPT / TILE;           // rows per region
+    constexpr int RW = region_w(TILE);            // columns per region
+    constexpr int RH = 32 * PPT / RW;             // rows per region
+    constexpr int RX = TILE / RW;                 // regions across a tile
+    constexpr int R = RX * (TILE / RH);           // regions per tile
     const int ti = item / R, r = item - ti * R;
     const int tile_id = a.tile_order ? a.tile_order[ti] : ti;
     Region g;
     const int c = find_canvas_tile(a.canvas, a.n_canvas, tile_id);
     g.d = a.canvas[c];
     const int lt = tile_id - g.d.tile_base;
-    g.x0 = (lt % g.d.ntx) * TILE;
-    g.y0 = (lt / g.d.ntx) * TILE + r * RH;
+    g.x0 = (lt % g.d.ntx) * TILE + (r % RX) * RW;
+    g.y0 = (lt / g.d.ntx) * TILE + (r / RX) * RH;
     g.start = a.tile_off[tile_id];
     g.len = (int)(a.tile_off[tile_id + 1] - g.start);
     return g;
@@ -203,7 +210,8 @@ __device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
 template <int TILE, int PPT, int BATCH>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k_fwd(RenderArgs a, int32_t n_items) {
     constexpr int RPL = BATCH / 32;   // records per lane per batch
-    constexpr int LROWS = 32 / TILE;  // rows covered by the 32 lanes in one pass
+    constexpr int RW = region_w(TILE);
+    constexpr int LROWS = 32 / RW;    // rows covered by the 32 lanes in one pass
     constexpr int RH = LROWS * PPT;   // rows of a region
     __shared__ PrimRec sh_all[kWarpsPerBlock][BATCH];
     __shared__ int pos_all[kWarpsPerBlock][BATCH];
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     for (int item = next_item(&a.status->queue[0], lane); item < n_items;
          item = next_item(&a.status->queue[0], lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
-        const int x = g.x0 + lane % TILE;
+        const int x = g.x0 + lane % RW;
         const float px = (float)x;
         float py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
         int last[PPT];
@@ -230,7 +238,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
         Tap tp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int y = g.y0 + lane / TILE + k * LROWS;
+            const int y = g.y0 + lane / RW + k * LROWS;
             inside[k] = x < g.d.W && y < g.d.H;
             py[k] = (float)y;
             T[k] = inside[k] ? 1.0f : 0.0f;   // pixels off the canvas never composite
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
             tp[k].q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
-        const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
+        const float rw = (float)(RW - 1), rh = (float)(RH - 1);
         int walked = g.len, sv_it = 0, ct_it = 0;
         if (g.len > 0) {
             Prefetch<RPL> pf;
@@ -384,7 +392,8 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
 template <int TILE, int PPT, int BATCH>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k_bwd(RenderArgs a, int32_t n_items) {
     constexpr int RPL = BATCH / 32;
-    constexpr int LROWS = 32 / TILE;
+    constexpr int RW = region_w(TILE);
+    constexpr int LROWS = 32 / RW;
     constexpr int RH = LROWS * PPT;
     __shared__ PrimRec sh_all[kWarpsPerBlock][BATCH];
     __shared__ int pos_all[kWarpsPerBlock][BATCH];
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     for (int item = next_item(&a.status->queue[1], lane); item < n_items;
          item = next_item(&a.status->queue[1], lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
-        const int x = g.x0 + lane % TILE;
+        const int x = g.x0 + lane % RW;
         const float px = (float)x;
         float py[PPT], T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
         int last[PPT];
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
         const int64_t HW = (int64_t)g.d.H * g.d.W;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int y = g.y0 + lane / TILE + k * LROWS;
+            const int y = g.y0 + lane / RW + k * LROWS;
             py[k] = (float)y;
             last[k] = -1;
             T[k] = Y[k] = g0[k] = g1[k] = g2[k] = 0.0f;
@@ -442,7 +451,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
         }
         if (my_max < 0) continue;
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
-        const float rw = (float)(TILE - 1), rh = (float)(RH - 1);
+        const float rw = (float)(RW - 1), rh = (float)(RH - 1);
 
         // batches [lo, hi) from the back of the region's walk
         int hi = my_max + 1;
@@ -594,7 +603,7 @@ void register_occupancy() {
 
 template <int TILE, int PPT, int BATCH>
 cudaError_t launch_t(const RenderArgs &a, bool fwd, cudaStream_t st) {
-    constexpr int R = TILE * TILE / (32 * PPT);
+    constexpr int R = TILE * TILE / (32 * PPT);   // regions per tile (any region shape)
     const int32_t n_items = a.n_tiles * R;
     if (fwd) {
         const int grid = persistent_grid((const void *)k_fwd<TILE, PPT, BATCH>, n_items);
