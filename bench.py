@@ -570,9 +570,11 @@ def run_dbmp(args):
     tuning = {"tile": args.tile, "batch": args.batch, "ppt": args.ppt, "ppt_bwd": args.ppt_bwd or args.ppt,
               "autotuned": False}
     if not args.no_autotune:
+        # five renders per candidate and phase: steps vary by a few per cent, about the
+        # margin between the best two tile sizes
         (t, b, pp, pb), ms = D.dbmp_autotune(ws, params, bid, atlas, 1.0, bg, T_STOP,
                                          D.BATCH_FWD | D.BATCH_BWD, image, T_final, n_last, dL, dparams,
-                                         reps=2)
+                                         reps=5)
         tuning = {"tile": t, "batch": b, "ppt": pp, "ppt_bwd": pb, "autotuned": True,
                   "autotune_ms_bin_fwd_bwd": ms}
         dparams.zero_()
@@ -689,6 +691,7 @@ def run_dbmp(args):
         "config": config({"tile": tuning["tile"], "batch": tuning["batch"], "ppt": tuning["ppt"],
                           "ppt_bwd": tuning["ppt_bwd"],
                           "autotuned": tuning["autotuned"],
+                          "autotune_ms_bin_fwd_bwd": tuning.get("autotune_ms_bin_fwd_bwd"),
                           "parallelism": f"replicas x{world} (one canvas per GPU, no exchange)"}),
         "breakdown_ms": {"bin": float(phase[:, 0].mean()), "fwd": fwd_ms, "mse": float(phase[:, 2].mean()),
                          "bwd": bwd_ms, "adam": float(phase[:, 4].mean()),
