@@ -116,8 +116,9 @@ int32_t dbmp_workspace_bytes(const DbmpLimits *limits, size_t *bytes);
 int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out);
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws);
 /* Testing aid, in place of a memory sanitizer: fills every scratch buffer of the
- * workspace (records, rectangles, gradient sums, tile offsets, order and lists,
- * histograms, canvas descriptors, statistics; not the status block) with 0xFF
+ * workspace (records, rectangles, tile offsets, order and lists, histograms,
+ * canvas descriptors, statistics; not the status block, nor the per-primitive
+ * gradient sums, which every backward leaves zero for the next) with 0xFF
  * bytes, i.e. NaN floats and -1 integers, stream-ordered.  A later call that read a
  * buffer before writing it would then return different results.  Call it before
  * dbmp_batch_plan / dbmp_bin: it also erases a stored plan. */

@@ -269,9 +269,7 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     a.image = image;
     a.T_final = T_final;
     a.n_last = n_last;
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, sizeof(int64_t), st), "status reset");
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_contrib, 0, 2 * sizeof(int64_t), st), "status reset");
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->survivors_fwd, 0, sizeof(int64_t), st), "status reset");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, kFwdGroupBytes, st), "status reset");
     DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
     return DBMP_OK;
 }
@@ -284,11 +282,7 @@ int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     a.n_last = const_cast<int32_t *>(n_last);
     a.dL_dimage = dL_dimage;
     a.dL_dalpha = dL_dalpha;
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, sizeof(int64_t), st), "status reset");
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->warp_steps_bwd, 0, sizeof(int64_t), st), "status reset");
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->survivors_bwd, 0, sizeof(int64_t), st), "status reset");
-    if (ws->N > 0)
-        DBMP_CUDA(cudaMemsetAsync(ws->graw, 0, sizeof(float) * 8 * (size_t)ws->N, st), "graw reset");
+    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, kBwdGroupBytes, st), "status reset");
     DBMP_CUDA(launch_bwd(a, ws->cfg, st), "backward launch");
     DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, st), "gradient finalize");
     return DBMP_OK;
@@ -405,6 +399,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         }
     }
     cudaError_t e = cudaMemset(ws->status, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMemset(ws->graw, 0, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1));
     if (e == cudaSuccess) e = init_bin_kernels(kMaxTilesPerCanvas);
     if (e == cudaSuccess) e = init_render_kernels();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -426,7 +421,6 @@ int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream) {
     } bufs[] = {
         {ws->rec, sizeof(PrimRec) * (size_t)std::max(l.max_prims, 1)},
         {ws->rect, sizeof(int4) * (size_t)std::max(l.max_prims, 1)},
-        {ws->graw, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1)},
         {ws->tile_off, sizeof(int64_t) * ((size_t)l.max_tiles + 1)},
         {ws->tile_order, sizeof(int32_t) * (size_t)l.max_tiles},
         {ws->list, sizeof(int32_t) * (size_t)l.max_pairs},

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/dbmp.h"
@@ -41,17 +42,27 @@ struct DevStatus {
     int32_t code;
     int32_t n_degenerate;
     int64_t pairs_required;
+    int32_t lists_valid;    // 1 after a binning that fit its capacity
+    int32_t pad;
+    // forward counters and work queue, reset together before each forward
     int64_t pairs_eval_fwd;
-    int64_t pairs_eval_bwd;
     int64_t pairs_contrib;  // (pixel, layer) pairs with alpha > 0 composited by the last fwd
     int64_t warp_steps_fwd; // list entries walked, summed over warps (last fwd)
-    int64_t warp_steps_bwd; // same for the last bwd
     int64_t survivors_fwd;  // records that passed the region test (last fwd)
+    uint32_t queue_fwd;     // persistent-kernel work counter
+    uint32_t pad_fwd;
+    // backward counters and work queue, reset together before each backward
+    int64_t pairs_eval_bwd;
+    int64_t warp_steps_bwd; // same for the last bwd
     int64_t survivors_bwd;  // same for the last bwd
-    int32_t lists_valid;   // 1 after a binning that fit its capacity
-    int32_t pad;
-    uint32_t queue[4];     // persistent-kernel work counters
+    uint32_t queue_bwd;
+    uint32_t pad_bwd;
 };
+// Byte lengths of the two groups, each reset by one memset from its first field.
+constexpr size_t kFwdGroupBytes = offsetof(DevStatus, pairs_eval_bwd) - offsetof(DevStatus, pairs_eval_fwd);
+constexpr size_t kBwdGroupBytes = sizeof(DevStatus) - offsetof(DevStatus, pairs_eval_bwd);
+static_assert(kFwdGroupBytes == 4 * sizeof(int64_t) + 2 * sizeof(uint32_t), "forward group layout");
+static_assert(kBwdGroupBytes == 3 * sizeof(int64_t) + 2 * sizeof(uint32_t), "backward group layout");
 
 // The bitmap atlas as the kernels see it.  The texels of all bitmaps are stacked in
 // one pitch-linear float plane, bitmap b in rows b (H_b + 1) .. b (H_b + 1) + H_b - 1
@@ -253,13 +264,15 @@ struct RenderArgs {
     int32_t *n_last;
     const float *dL_dimage;
     const float *dL_dalpha;
-    float *graw;                // [N][8] raw per-primitive sums (backward)
+    float *graw;                // [N][8] raw per-primitive sums (backward; zero between calls)
 };
 
 bool render_cfg_supported(const RenderCfg &cfg);
 cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
 cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
-cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
+// dparams += chain rule of the raw sums graw, which are zeroed after reading (graw is
+// zero before every backward: zeroed at workspace creation, left zero by this kernel).
+cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
                                  float *dparams, int32_t N, cudaStream_t st);
 // Texel plane (row pitch `pitch` floats) and summed-area tables of an atlas from
 // its dense texels [n_bmp][H_b][W_b].

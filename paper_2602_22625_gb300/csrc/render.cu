@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     if (lane < 4) stats.v[lane] = 0ull;
     __syncwarp();
 
-    for (int item = next_item(&a.status->queue[0], lane); item < n_items;
-         item = next_item(&a.status->queue[0], lane)) {
+    for (int item = next_item(&a.status->queue_fwd, lane); item < n_items;
+         item = next_item(&a.status->queue_fwd, lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
         const int x = g.x0 + lane % RW;
         const float px = (float)x;
@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     if (lane < 4) stats.v[lane] = 0ull;
     __syncwarp();
 
-    for (int item = next_item(&a.status->queue[1], lane); item < n_items;
-         item = next_item(&a.status->queue[1], lane)) {
+    for (int item = next_item(&a.status->queue_bwd, lane); item < n_items;
+         item = next_item(&a.status->queue_bwd, lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
         const int x = g.x0 + lane % RW;
         const float px = (float)x;
@@ -549,12 +549,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
 // Per-primitive chain rule from the eight reduced sums to the raw parameters:
 //   x: -(A S0 + C S1)    y: -(B S0 + D S1)    s: -S2 / s    theta: S3
 //   nu: S4 (1 - sigmoid(nu))    c_j: S_{5+j} chat_j (1 - chat_j)
+// The sums are read and then zeroed, so graw is zero again for the next backward.
 __global__ void k_finalize(const float *__restrict__ params, const PrimRec *__restrict__ rec,
-                           const float *__restrict__ graw, float *__restrict__ dparams, int32_t N) {
+                           float *__restrict__ graw, float *__restrict__ dparams, int32_t N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const PrimRec r = rec[i];
-    const float *S = graw + 8 * (size_t)i;
+    float4 *g4 = reinterpret_cast<float4 *>(graw + 8 * (size_t)i);
+    const float4 lo = g4[0], hi = g4[1];
+    g4[0] = g4[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float S[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
     const float *p = params + 8 * (size_t)i;
     float *o = dparams + 8 * (size_t)i;
     const float s = p[2];
@@ -650,19 +654,19 @@ bool render_cfg_supported(const RenderCfg &cfg) {
     return tile_ok && ppt_ok(cfg.ppt) && ppt_ok(cfg.bwd_ppt()) && (cfg.batch == 32 || cfg.batch == 64);
 }
 
+// The caller resets the status block's forward (backward) group, work queue included,
+// before each launch.
 cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
-    cudaMemsetAsync(&a.status->queue[0], 0, sizeof(uint32_t), st);
     return dispatch(a, cfg, true, st);
 }
 
 cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
-    cudaMemsetAsync(&a.status->queue[1], 0, sizeof(uint32_t), st);
     RenderCfg b = cfg;
     b.ppt = cfg.bwd_ppt();
     return dispatch(a, b, false, st);
 }
 
-cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, const float *graw,
+cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
                                  float *dparams, int32_t N, cudaStream_t st) {
     if (N > 0) k_finalize<<<(N + 255) / 256, 256, 0, st>>>(params, rec, graw, dparams, N);
     return cudaGetLastError();
