@@ -300,6 +300,22 @@ int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int3
                           int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
                           dbmp_stream_t stream);
 
+/* dbmp_batch_render with the MSE loss (Tab. S1 `mse`, mean over 3 H W) fused into
+ * the forward's epilogue: mode must include DBMP_BATCH_FWD.  The forward writes the
+ * image as usual and, per pixel, dL/dI = 2 (I - I*) / n into dL_dimage_dev (the
+ * same values dbmp_mse_grad would write) and adds its (I - I*)^2 / n into
+ * *loss_dev (zeroed by the call; summation order unspecified), n = 3 x the planned
+ * canvases' pixels; with DBMP_BATCH_BWD the backward then runs on that dL/dI.  This
+ * saves the separate pass over the image that dbmp_mse_grad makes.
+ *   target_dev     float32, the plan's concatenated planar 3 x H x W targets
+ *   dL_dimage_dev  float32, same layout (out; the backward's input)
+ *   loss_dev       double [1] (out) */
+int32_t dbmp_batch_render_mse(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                              const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg, float T_stop,
+                              int32_t mode, const float *target_dev, float *image_dev, float *T_final_dev,
+                              int32_t *n_last_dev, float *dL_dimage_dev, float *dparams_dev, double *loss_dev,
+                              dbmp_stream_t stream);
+
 /* Autotuner: for every (tile, batch) it times, with CUDA events and reps times
  * each, the binning once and the forward and the backward (those `mode` asks
  * for) at every supported ppt; the tuning with the smallest bin + best forward +

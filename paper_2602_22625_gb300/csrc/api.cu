@@ -264,11 +264,23 @@ int32_t check_bg(const DbmpBackground *bg) {
 }
 
 int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg, float T_stop,
-               float *image, float *T_final, int32_t *n_last, cudaStream_t st) {
+               float *image, float *T_final, int32_t *n_last, cudaStream_t st,
+               const float *mse_target = nullptr, float *mse_dL = nullptr, double *mse_loss = nullptr) {
     RenderArgs a = make_args(ws, atlas, bg, T_stop);
     a.image = image;
     a.T_final = T_final;
     a.n_last = n_last;
+    if (mse_target) {
+        int64_t pixels = 0;
+        for (int c = 0; c < ws->n_canvas; ++c) pixels += (int64_t)ws->plan_H[c] * ws->plan_W[c];
+        const double n = 3.0 * (double)pixels;
+        a.mse_target = mse_target;
+        a.mse_dL = mse_dL;
+        a.mse_loss = mse_loss;
+        a.mse_scale = (float)(2.0 / n);
+        a.mse_inv_n = 1.0 / n;
+        DBMP_CUDA(cudaMemsetAsync(mse_loss, 0, sizeof(double), st), "loss reset");
+    }
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, kFwdGroupBytes, st), "status reset");
     DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
     return DBMP_OK;
@@ -577,11 +589,16 @@ int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, c
     return DBMP_OK;
 }
 
-int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
-                          const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
-                          float T_stop, int32_t mode, float *image_dev, float *T_final_dev,
-                          int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
-                          dbmp_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// dbmp_batch_render, and with target_dev the MSE loss fused into the forward.
+int32_t batch_render(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                     const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg, float T_stop,
+                     int32_t mode, float *image_dev, float *T_final_dev, int32_t *n_last_dev,
+                     const float *dL_dimage_dev, float *dparams_dev, const float *target_dev, float *dL_out_dev,
+                     double *loss_dev, dbmp_stream_t stream) {
     if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
     if (!ws->persistent || ws->n_canvas < 1)
         return fail(DBMP_ERR_NOT_READY, "dbmp_batch_render needs dbmp_batch_plan first");
@@ -607,7 +624,9 @@ int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int3
     }
     if (mode & DBMP_BATCH_FWD) {
         if (!image_dev) return fail(DBMP_ERR_INVALID_ARG, "image is NULL");
-        if (int32_t r = do_fwd(ws, atlas, bg, T_stop, image_dev, T_final_dev, n_last_dev, st)) return r;
+        if (int32_t r = do_fwd(ws, atlas, bg, T_stop, image_dev, T_final_dev, n_last_dev, st, target_dev,
+                               dL_out_dev, loss_dev))
+            return r;
     }
     if (mode & DBMP_BATCH_BWD) {
         if (!dL_dimage_dev || (!dparams_dev && ws->N > 0))
@@ -617,6 +636,31 @@ int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int3
             return r;
     }
     return DBMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t dbmp_batch_render(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                          const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg,
+                          float T_stop, int32_t mode, float *image_dev, float *T_final_dev,
+                          int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
+                          dbmp_stream_t stream) {
+    return batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop, mode, image_dev, T_final_dev,
+                        n_last_dev, dL_dimage_dev, dparams_dev, nullptr, nullptr, nullptr, stream);
+}
+
+int32_t dbmp_batch_render_mse(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
+                              const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg, float T_stop,
+                              int32_t mode, const float *target_dev, float *image_dev, float *T_final_dev,
+                              int32_t *n_last_dev, float *dL_dimage_dev, float *dparams_dev, double *loss_dev,
+                              dbmp_stream_t stream) {
+    if (!(mode & DBMP_BATCH_FWD)) return fail(DBMP_ERR_INVALID_ARG, "dbmp_batch_render_mse needs DBMP_BATCH_FWD");
+    if (!target_dev || !dL_dimage_dev || !loss_dev)
+        return fail(DBMP_ERR_INVALID_ARG, "target / dL_dimage / loss is NULL");
+    return batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop, mode, image_dev, T_final_dev,
+                        n_last_dev, dL_dimage_dev, dparams_dev, target_dev, dL_dimage_dev, loss_dev, stream);
 }
 
 int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,

@@ -163,6 +163,22 @@ __device__ __forceinline__ float tap_M(const Tap &t) {
     return tap_M(t, du, dv);
 }
 
+// Adds d^2 to the compensated sum (s, c) with error-free transformations (the
+// exact product d^2 = p + pe by one FMA, the exact sum s + p = t + se by TwoSum),
+// as in Ogita, Rump and Oishi's compensated dot product: s + c carries about twice
+// fp32 precision, so the loss needs no FP64 arithmetic per element (FP64 throughput
+// is a small fraction of FP32 on this GPU).  Explicitly rounded operations keep the
+// compiler from contracting or reassociating the transformations.
+__device__ __forceinline__ void acc_sq(float d, float &s, float &c) {
+    const float p = __fmul_rn(d, d);
+    const float pe = __fmaf_rn(d, d, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(se, pe));
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (one translation unit each).
 // ---------------------------------------------------------------------------
@@ -265,6 +281,13 @@ struct RenderArgs {
     const float *dL_dimage;
     const float *dL_dalpha;
     float *graw;                // [N][8] raw per-primitive sums (backward; zero between calls)
+    // forward with the MSE loss fused (null target: off): dL/dI = mse_scale (I - I*)
+    // into mse_dL, and L = sum (I - I*)^2 / n added into *mse_loss (zeroed by the caller)
+    const float *mse_target;
+    float *mse_dL;
+    double *mse_loss;
+    float mse_scale;            // float(2 / n)
+    double mse_inv_n;           // 1 / n, n = 3 x pixels of all canvases
 };
 
 bool render_cfg_supported(const RenderCfg &cfg);

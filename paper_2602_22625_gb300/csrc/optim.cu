@@ -47,22 +47,6 @@ __global__ void k_sat(const float *__restrict__ tex, int32_t *__restrict__ sat, 
     }
 }
 
-// Adds d^2 to the compensated sum (s, c) with error-free transformations (the
-// exact product d^2 = p + pe by one FMA, the exact sum s + p = t + se by TwoSum),
-// as in Ogita, Rump and Oishi's compensated dot product: s + c carries about twice
-// fp32 precision, so the loss needs no FP64 arithmetic per element (FP64 throughput
-// is a small fraction of FP32 on this GPU).  Explicitly rounded operations keep the
-// compiler from contracting or reassociating the transformations.
-__device__ __forceinline__ void acc_sq(float d, float &s, float &c) {
-    const float p = __fmul_rn(d, d);
-    const float pe = __fmaf_rn(d, d, -p);
-    const float t = __fadd_rn(s, p);
-    const float z = __fsub_rn(t, s);
-    const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(se, pe));
-}
-
 // dL/dI = 2 (I - I*) / n and the loss sum (I - I*)^2 / n.  The differences are
 // formed in fp32 (the upstream gradient's precision), the squares summed per thread
 // with acc_sq and across threads in FP64.  Four elements per thread and load when

@@ -157,7 +157,7 @@ struct Region {
 // Width of a warp's region: the tile's width up to 16 pixels, so that a 32-pixel
 // tile (shorter lists in total, cheaper binning) still gives each warp a compact
 // 16-pixel-wide region to cull against.
-constexpr int region_w(int tile) { return tile < 16 ? tile : 16; }
+__host__ __device__ constexpr int region_w(int tile) { return tile < 16 ? tile : 16; }
 
 template <int TILE, int PPT>
 __device__ __forceinline__ Region region_of(const RenderArgs &a, int item) {
@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     WarpStats &stats = stats_all[warp];   // pairs evaluated, contributing, walked, survivors
     if (lane < 4) stats.v[lane] = 0ull;
     __syncwarp();
+    float mse_s = 0.0f, mse_c = 0.0f;     // this lane's compensated sum of (I - I*)^2
 
     for (int item = next_item(&a.status->queue_fwd, lane); item < n_items;
          item = next_item(&a.status->queue_fwd, lane)) {
@@ -303,11 +304,25 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
             ev_it += T[k] < tstop ? last[k] + 1 : g.len;
             const int64_t pix = (int64_t)py[k] * g.d.W + x;
             float *img = a.image + 3 * g.d.pix_base;
-            img[pix] = __fmaf_rn(T[k], bg_at(a, g.d, 0, pix), C0[k]);
-            img[HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 1, pix), C1[k]);
-            img[2 * HW + pix] = __fmaf_rn(T[k], bg_at(a, g.d, 2, pix), C2[k]);
+            const float I0 = __fmaf_rn(T[k], bg_at(a, g.d, 0, pix), C0[k]);
+            const float I1 = __fmaf_rn(T[k], bg_at(a, g.d, 1, pix), C1[k]);
+            const float I2 = __fmaf_rn(T[k], bg_at(a, g.d, 2, pix), C2[k]);
+            img[pix] = I0;
+            img[HW + pix] = I1;
+            img[2 * HW + pix] = I2;
             a.T_final[g.d.pix_base + pix] = T[k];
             a.n_last[g.d.pix_base + pix] = last[k];
+            if (a.mse_target) {   // the loss of the pixel (the same arithmetic as k_mse)
+                const float *tg = a.mse_target + 3 * g.d.pix_base;
+                float *dl = a.mse_dL + 3 * g.d.pix_base;
+                const float d0 = I0 - tg[pix], d1 = I1 - tg[HW + pix], d2 = I2 - tg[2 * HW + pix];
+                dl[pix] = a.mse_scale * d0;
+                dl[HW + pix] = a.mse_scale * d1;
+                dl[2 * HW + pix] = a.mse_scale * d2;
+                acc_sq(d0, mse_s, mse_c);
+                acc_sq(d1, mse_s, mse_c);
+                acc_sq(d2, mse_s, mse_c);
+            }
         }
         // per item each lane's counts fit 32 bits (<= PPT x list length)
         ev_it = warp_sum(ev_it);
@@ -320,6 +335,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
         }
     }
     __syncwarp();
+    if (a.mse_target) {
+        double acc = (double)mse_s + (double)mse_c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (lane == 0 && acc != 0.0) atomicAdd(a.mse_loss, acc * a.mse_inv_n);
+    }
     if (lane == 0) {
         if (stats.v[0]) {
             atomicAdd((unsigned long long *)&a.status->pairs_eval_fwd, stats.v[0]);

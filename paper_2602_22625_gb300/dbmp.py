@@ -35,7 +35,7 @@ EXPORTS = (
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
     "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
-    "dbmp_workspace_poison",
+    "dbmp_workspace_poison", "dbmp_batch_render_mse",
 )
 
 
@@ -128,6 +128,8 @@ def load(build_if_missing: bool = True):
         "dbmp_batch_plan": (_i32, [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(DbmpTuning), _vp]),
         "dbmp_batch_render": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32,
                                      _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "dbmp_batch_render_mse": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32,
+                                         _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "dbmp_autotune": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32, _i32,
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
@@ -314,6 +316,15 @@ def dbmp_batch_render(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode,
     _check(load().dbmp_batch_render(ws, _ptr(params), _ptr(bitmap_id), atlas, alpha_max, ctypes.byref(bg),
                                     T_stop, mode, _ptr(image), _ptr(T_final), _ptr(n_last),
                                     _ptr(dL_dimage), _ptr(dparams), _stream(stream)))
+
+
+def dbmp_batch_render_mse(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, target, image, T_final,
+                          n_last, dL_dimage, loss, dparams=None, stream=None):
+    """dbmp_batch_render with the MSE loss fused into the forward: dL/dI into dL_dimage
+    and the loss into loss (float64 [1]); mode must include BATCH_FWD."""
+    _check(load().dbmp_batch_render_mse(ws, _ptr(params), _ptr(bitmap_id), atlas, alpha_max, ctypes.byref(bg),
+                                        T_stop, mode, _ptr(target), _ptr(image), _ptr(T_final), _ptr(n_last),
+                                        _ptr(dL_dimage), _ptr(dparams), _ptr(loss), _stream(stream)))
 
 
 def dbmp_autotune(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, image, T_final, n_last,

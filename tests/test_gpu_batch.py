@@ -419,3 +419,51 @@ def test_gpu_optimisation_resumes_from_a_checkpoint(tmp_path):
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)
+
+
+@pytest.mark.parametrize("tuning", [(16, 32, 4), (32, 32, 4), (8, 32, 1)], ids=lambda t: f"t{t[0]}b{t[1]}p{t[2]}")
+def test_fused_mse_matches_the_separate_passes(tuning):
+    """dbmp_batch_render_mse (the loss in the forward's epilogue) against the forward,
+    dbmp_mse_grad and the backward run one after another on a ragged multi-canvas
+    batch: images and dL/dI bit for bit, the loss to FP64 rounding (summation order),
+    the gradients to float32 atomics' rounding; and the loss against the oracle's."""
+    cuda()
+    scenes, atlas_np = small_batch(seed=41)
+    params, bid, off, pix = concat(scenes)
+    N, P = int(off[-1]), int(pix[-1])
+    target = to_dev(np.random.default_rng(8).uniform(0, 1, 3 * P).astype(np.float32))
+    atlas = D.dbmp_atlas_create(to_dev(atlas_np))
+    n_tiles = sum(-(-s.W // 8) * -(-s.H // 8) for s in scenes)
+    ws = D.dbmp_workspace_create(max(N, 1), n_tiles, 1 << 24, len(scenes))
+    try:
+        D.dbmp_batch_plan(ws, [s.H for s in scenes], [s.W for s in scenes], off.tolist(), *tuning)
+        p, b = to_dev(params), to_dev(bid)
+        bg = D.make_background((1.0, 1.0, 1.0))
+        out = []
+        for fused in (False, True):
+            image = torch.empty(3 * P, device="cuda")
+            T = torch.empty(P, device="cuda")
+            nl = torch.empty(P, dtype=torch.int32, device="cuda")
+            dL = torch.empty(3 * P, device="cuda")
+            loss = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+            dp = torch.zeros(max(N, 1), 8, device="cuda")
+            mode = D.BATCH_BIN | D.BATCH_FWD | D.BATCH_BWD
+            if fused:
+                D.dbmp_batch_render_mse(ws, p, b, atlas, 1.0, bg, 0.0, mode, target, image, T, nl, dL, loss, dp)
+            else:
+                D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 0.0, D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
+                D.dbmp_mse_grad(image, target, dL, loss)
+                D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 0.0, D.BATCH_BWD, image, T, nl, dL, dp)
+            assert D.dbmp_status_poll(ws).code == 0
+            torch.cuda.synchronize()
+            out.append([x.cpu().numpy() for x in (image, T, nl, dL, loss, dp)])
+        (i0, t0, n0, d0, l0, g0), (i1, t1, n1, d1, l1, g1) = out
+        assert np.array_equal(i0, i1) and np.array_equal(t0, t1) and np.array_equal(n0, n1)
+        assert np.array_equal(d0, d1)
+        assert abs(l1[0] - l0[0]) <= 1e-12 * abs(l0[0])
+        grad_close(g1[:N].astype(np.float64), g0[:N].astype(np.float64), rel=1e-5, what="fused mse")
+        ref = oracle.mse(i0, target.cpu().numpy())
+        assert abs(l1[0] - ref) <= 1e-9 * ref
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
