@@ -375,6 +375,105 @@ def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
         scenes.close()
 
 
+def other_workload(name, steps=5, warmup=3):
+    """One optimisation step (bin, forward with the fused MSE, backward, Adam) of the
+    batched workload (64 canvases, side U{256..1024}, N log-uniform [1k, 50k], one
+    plan and one persistent launch per pass) or the stress workload (2048^2, 200k
+    primitives, Pareto scales), autotuned, L2 flushed between timed steps; the target
+    is a render of other seeds.  Returns ms per step, the phases, the work and the
+    backward against the derived FP32 peak."""
+    import numpy as np
+    import torch
+    from paper_2602_22625_gb300 import dbmp as D
+    from paper_2602_22625_gb300 import inputs
+    dev = torch.device("cuda")
+    if name == "batched":
+        scenes = inputs.batched(seed=4)
+        # targets: the same canvases and primitive counts, other seeds (so one plan serves both)
+        tparts = [inputs.primitives(7000 + c, s.N, s.H, s.W, s.atlas.shape[0], "lognormal", (-2.0, 0.7))
+                  for c, s in enumerate(scenes)]
+    else:
+        scenes = [inputs.stress(seed=3)]
+        t = inputs.stress(seed=1003)
+        tparts = [(t.params, t.bitmap_id)]
+    atlas_np = scenes[0].atlas
+    P = np.concatenate([s.params for s in scenes])
+    B = np.concatenate([s.bitmap_id for s in scenes]).astype(np.int32)
+    tP = np.concatenate([p for p, _ in tparts])
+    tB = np.concatenate([b for _, b in tparts]).astype(np.int32)
+    off = [0] + [int(v) for v in np.cumsum([s.N for s in scenes])]
+    Hs, Ws = [s.H for s in scenes], [s.W for s in scenes]
+    N, pix = off[-1], sum(h * w for h, w in zip(Hs, Ws))
+    atlas = D.dbmp_atlas_create(torch.from_numpy(atlas_np).to(dev))
+    ws = D.dbmp_workspace_create(N, sum((h // 8) * (w // 8) for h, w in zip(Hs, Ws)), 400 << 20, len(Hs))
+    try:
+        bg = D.make_background((1.0, 1.0, 1.0))
+        image = torch.empty(3 * pix, device=dev)
+        T = torch.empty(pix, device=dev)
+        nl = torch.empty(pix, dtype=torch.int32, device=dev)
+        target = torch.empty(3 * pix, device=dev)
+        dL = torch.empty(3 * pix, device=dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        D.dbmp_batch_plan(ws, Hs, Ws, off, tile=32, batch=32, ppt=4)
+        D.dbmp_batch_render(ws, torch.from_numpy(tP).to(dev), torch.from_numpy(tB).to(dev), atlas, 1.0, bg, 0.0,
+                            D.BATCH_BIN | D.BATCH_FWD, target, T, nl)
+        params = torch.from_numpy(P).to(dev)
+        bid = torch.from_numpy(B).to(dev)
+        dp = torch.zeros(N, 8, device=dev)
+        m = torch.zeros_like(dp)
+        v = torch.zeros_like(dp)
+        step = torch.zeros(1, dtype=torch.int32, device=dev)
+        D.dbmp_batch_render_mse(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BIN | D.BATCH_FWD, target, image,
+                                T, nl, dL, loss)
+        (t, b, pp, pb), _ = D.dbmp_autotune(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_FWD | D.BATCH_BWD,
+                                            image, T, nl, dL, dp, reps=3)
+        dp.zero_()
+        adam = D.adam_config(lr=0.1, gamma=0.1 ** (1.0 / 500), zero_grad=True)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+        st = torch.cuda.current_stream()
+
+        def one(ev=None):
+            if ev:
+                ev[0].record(st)
+            D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BIN, None, T, nl)
+            if ev:
+                ev[1].record(st)
+            D.dbmp_batch_render_mse(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_FWD, target, image, T, nl,
+                                    dL, loss)
+            if ev:
+                ev[2].record(st)
+            D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BWD, image, T, nl, dL, dp)
+            if ev:
+                ev[3].record(st)
+            D.dbmp_adam_step(params, dp, m, v, step, adam)
+            if ev:
+                ev[4].record(st)
+
+        for _ in range(warmup):
+            one()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            one(evs[k])
+        torch.cuda.synchronize()
+        ph = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(steps)])
+        s_ = D.dbmp_status_poll(ws)
+        bwd = float(ph[:, 2].mean())
+        bwd_tf = FLOPS_BWD_PAIR * s_.pairs_contributing / (bwd * 1e-3) / 1e12
+        return {"workload": "batched_64_canvases" if name == "batched" else "stress_2048sq_200k",
+                "canvases": len(Hs), "pixels": pix, "primitives": N, "tuning": [t, b, pp, pb],
+                "ms_per_step": float(ph.sum(1).mean()),
+                "breakdown_ms": {"bin": float(ph[:, 0].mean()), "fwd_with_mse": float(ph[:, 1].mean()),
+                                 "bwd": bwd, "adam": float(ph[:, 3].mean())},
+                "pairs_contributing": s_.pairs_contributing, "tile_list_entries": s_.pairs_required,
+                "bwd_tflops": bwd_tf, "bwd_frac_of_fp32_peak": bwd_tf / FP32_PEAK_TFLOPS,
+                "steps": steps, "l2": "flushed between timed steps"}
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
 def blur_ablation(n_targets=4, steps=300, sigma=1.0):
     """Soft rasterisation (Sec. 3.2, Tab. S1 blur_sigma 1.0) on and off: targets are
     256^2 renders of 512 primitives with 16 hard-edged stroke bitmaps; the same random
@@ -676,9 +775,11 @@ def run_dbmp(args):
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_vs_plain(args.learned_pairs)
     ablation = constrained = None
+    others = None
     if rank == 0 and world == 1 and not args.no_ablation:
         ablation = blur_ablation()
         constrained = spatial_constraint()
+        others = [other_workload("batched"), other_workload("stress")]
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -722,6 +823,8 @@ def run_dbmp(args):
         line["blur_ablation"] = ablation
     if constrained is not None:
         line["spatial_constraint"] = constrained
+    if others is not None:
+        line["other_workloads"] = others
     line["scaling_stats"] = dict(sstats, note="tau: tiles per primitive, d: primitives per tile, foot: padded "
                                               "box area / canvas area; bin b = [2^b, 2^(b+1)) (foot: "
                                               "[2^-(b+1), 2^-b))")
