@@ -200,20 +200,31 @@ def test_mse_kernel_matches_oracle(offset):
     np.testing.assert_allclose(dL.cpu().numpy(), oracle.mse_grad(a, b), rtol=1e-6, atol=1e-12)
 
 
-def test_adam_kernel_matches_oracle():
+@pytest.mark.parametrize("offset", [0, 1], ids=["aligned", "unaligned"])
+def test_adam_kernel_matches_oracle(offset):
+    """offset 1 shifts every array by one float: the element-wise kernel instead of the
+    one with 16-byte vectors."""
     cuda()
     rng = np.random.default_rng(1)
     N = 1000
+
+    def buf(init=None):
+        b = torch.zeros(N * 8 + 1, device="cuda")
+        t = b[offset:offset + N * 8].view(N, 8)
+        if init is not None:
+            t.copy_(torch.from_numpy(init))
+        return t
+
     p0 = rng.normal(size=(N, 8)).astype(np.float32)
-    p = to_dev(p0)
-    m = torch.zeros(N, 8, device="cuda")
-    v = torch.zeros(N, 8, device="cuda")
+    p = buf(p0)
+    m = buf()
+    v = buf()
     step = torch.zeros(1, dtype=torch.int32, device="cuda")
     cfg = D.adam_config(lr=0.1, gamma=0.95, zero_grad=True)
     rp, rm, rv = p0.astype(np.float64), np.zeros((N, 8)), np.zeros((N, 8))
     for t in range(1, 6):
         g = rng.normal(size=(N, 8)).astype(np.float32)
-        gd = to_dev(g)
+        gd = buf(g)
         D.dbmp_adam_step(p, gd, m, v, step, cfg)
         torch.cuda.synchronize()
         assert torch.all(gd == 0)
