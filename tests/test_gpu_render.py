@@ -296,3 +296,16 @@ def test_lattice_aligned_samples_match_oracle(tile, shift):
     gz, rz = np.zeros_like(g), np.zeros_like(grad_ref)
     gz[:, cols], rz[:, cols] = g[:, cols], grad_ref[:, cols]
     grad_close(gz, rz, what=f"lattice tile{tile} shift{shift}")
+
+
+def test_atlas_beyond_the_texture_height_is_rejected():
+    """The texel plane stacks n_bmp (H_b + 1) rows; past the device's pitch-linear
+    texture height (65000 rows on GB300) the atlas is refused on the host."""
+    cuda()
+    ok = to_dev(np.zeros((503, 128, 128), np.float32))     # 503 x 129 = 64887 rows
+    a = D.dbmp_atlas_create(ok)
+    D.dbmp_atlas_destroy(a)
+    big = to_dev(np.zeros((504, 128, 128), np.float32))    # 65016 rows
+    with pytest.raises(D.DbmpError) as e:
+        D.dbmp_atlas_create(big)
+    assert e.value.code == D.DBMP_ERR_INVALID_ARG and "texture" in str(e.value)
