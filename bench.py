@@ -725,6 +725,32 @@ def run_dbmp(args):
     ms = float(step_ms.mean())
     st = D.dbmp_status_poll(ws)
     pairs_end = (st.pairs_evaluated, st.pairs_evaluated_bwd, st.pairs_contributing, st.pairs_required)
+
+    # ---- the same step captured once as a CUDA graph and replayed ----
+    graph_ms = None
+    try:
+        cap = torch.cuda.Stream(device=dev)
+        cap.wait_stream(stream)
+        with torch.cuda.stream(cap):
+            g_step = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_step, stream=cap):
+                one_step()
+        torch.cuda.synchronize()
+        for _ in range(3):
+            g_step.replay()
+        gts = []
+        for k in range(args.steps):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            g_step.replay()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            gts.append(a0.elapsed_time(a1))
+        graph_ms = float(np.mean(gts))
+    except RuntimeError as e:   # capture refused: report the eager step only
+        print(f"graph capture: {e}", file=sys.stderr)
     # Sec. S4 scaling statistics of the last step's binning (histograms: log2 bins)
     sstats = D.dbmp_bin_stats(ws)
     for k in ("tau_hist", "d_hist", "foot_hist"):
@@ -812,6 +838,7 @@ def run_dbmp(args):
         "binning_hbm": binning_hbm(N, pairs_end[3], (H // tuning["tile"]) * (W // tuning["tile"]),
                                    float(phase[:, 0].mean())),
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "graph_ms_per_step": graph_ms,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clk.summary(),
     }
