@@ -297,6 +297,8 @@ cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
 // zero before every backward: zeroed at workspace creation, left zero by this kernel).
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
                                  float *dparams, int32_t N, cudaStream_t st);
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
 // Texel plane (row pitch `pitch` floats) and summed-area tables of an atlas from
 // its dense texels [n_bmp][H_b][W_b].
 cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int32_t n_bmp,

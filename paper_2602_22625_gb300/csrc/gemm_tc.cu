@@ -549,9 +549,7 @@ cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
     // tile width: the narrowest of {32 (K-major B only: MN-major boxes are 64 wide), 64,
     // 128, 256} covering N, halved (down to 64) while twice the CTAs still fit one wave
-    int sms = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
-        sms = 152;
+    const int sms = sm_count();
     int bn = g.N <= 32 && !g.b_mn ? 32 : g.N <= 64 ? 64 : g.N <= 128 ? 128 : 256;
     const int64_t rows = (g.M + kBM - 1) / kBM;
     while (bn > 64 && 2 * rows * ((g.N + bn - 1) / bn) * split_k <= sms) bn /= 2;

@@ -200,14 +200,23 @@ __global__ void k_step_inc(int32_t *step) { *step += 1; }
 // Blocks for n work items of `threads` threads, at most `per_sm` resident blocks
 // per SM (grid-stride loops take the rest).
 int grid_for(int64_t n, int threads, int per_sm = 8) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     const int64_t want = (n + threads - 1) / threads;
     return (int)(want < (int64_t)sms * per_sm ? (want > 0 ? want : 1) : (int64_t)sms * per_sm);
 }
 
 }  // namespace
+
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 152;
+    if (dev < 64) cached[dev] = n;   // the same value from any racing thread
+    return n;
+}
 
 cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int32_t n_bmp,
                                int32_t Hb, int32_t Wb, cudaStream_t st) {
