@@ -309,3 +309,64 @@ def test_atlas_beyond_the_texture_height_is_rejected():
     with pytest.raises(D.DbmpError) as e:
         D.dbmp_atlas_create(big)
     assert e.value.code == D.DBMP_ERR_INVALID_ARG and "texture" in str(e.value)
+
+
+
+def test_main_workload_in_the_benchmarked_configuration():
+    """One optimisation step as the benchmark times it, at full size (1024^2 canvas,
+    20k primitives, tile 32, batch 32, 4 pixels per lane forward and backward, T_stop
+    1e-6): dbmp_batch_render(BIN), dbmp_batch_render_mse(FWD) with the loss in the
+    forward's epilogue, dbmp_batch_render(BWD), dbmp_adam_step.  Against the FP64
+    oracle: every pixel, the loss, dL/dI, the gradient of every primitive (the oracle's
+    backward takes the GPU's dL/dI, itself checked) and the updated parameters."""
+    cuda()
+    sc = inputs.main()
+    tg = inputs.main(seed=1002)
+    target = to_dev(oracle.render(tg.H, tg.W, tg.params, tg.bitmap_id, tg.atlas,
+                                  background=tg.background)["image"].astype(np.float32))
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, (sc.W // 8) * (sc.H // 8), 96 << 20, 1)
+    try:
+        D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N], tile=32, batch=32, ppt=4, ppt_bwd=4)
+        bg = D.make_background(sc.background)
+        p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
+        image = torch.empty(3, sc.H, sc.W, device="cuda")
+        T = torch.empty(sc.H, sc.W, device="cuda")
+        nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+        dL = torch.empty(3, sc.H, sc.W, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dp = torch.zeros(sc.N, 8, device="cuda")
+        m = torch.zeros(sc.N, 8, device="cuda")
+        v = torch.zeros(sc.N, 8, device="cuda")
+        step = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cfg = D.adam_config(lr=0.1, gamma=0.1 ** (1.0 / 500), zero_grad=True)
+        D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BIN, None, T, nl)
+        D.dbmp_batch_render_mse(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_FWD, target, image, T, nl, dL, loss)
+        D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BWD, image, T, nl, dL, dp)
+        assert D.dbmp_status_poll(ws).code == 0
+        grad = dp.cpu().numpy().astype(np.float64)
+        D.dbmp_adam_step(p, dp, m, v, step, cfg)
+        torch.cuda.synchronize()
+        img, tgt = image.cpu().numpy(), target.cpu().numpy()
+        ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background,
+                            T_stop=1e-6)
+        assert np.abs(img - ref["image"]).max() <= IMG_TOL
+        assert np.abs(T.cpu().numpy() - ref["T_final"]).max() <= IMG_TOL
+        # the loss of the GPU's own image to summation order; against the oracle's image,
+        # |mean(d1^2) - mean(d2^2)| <= max|d1 - d2| * mean|d1 + d2| bounds the difference
+        L = loss.item()
+        assert abs(L - oracle.mse(img, tgt)) <= 1e-6 * L
+        assert abs(L - oracle.mse(ref["image"], tgt)) <= IMG_TOL * (2.0 * np.sqrt(L) + IMG_TOL)
+        gI = dL.cpu().numpy()
+        np.testing.assert_allclose(gI, oracle.mse_grad(img, tgt), rtol=1e-6, atol=1e-12)
+        gref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background,
+                           T_stop=1e-6)
+        grad_close(grad, gref, what="benchmarked configuration")
+        # Adam at step 1 takes the GPU's gradient; zero_grad clears it for the next step
+        rp, _, _ = oracle.adam_step(sc.params, grad, np.zeros((sc.N, 8)), np.zeros((sc.N, 8)), 1, 0.1)
+        # positions reach 1024, where a float32 ulp is 6e-5: allow 2 ulp beside the step's error
+        assert np.all(np.abs(p.cpu().numpy() - rp) <= 2e-5 + 2.4e-7 * np.abs(rp))
+        assert step.item() == 1 and torch.all(dp == 0)
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
