@@ -145,6 +145,31 @@ __device__ __forceinline__ void tap_issue(const PrimRec &r, const ColXf &c, cuda
     }
 }
 
+// tap_issue for two pixels of one column (rows py2.x, py2.y), with the transform and
+// the fractional parts in packed FP32x2 instructions.  Lane-wise the roundings are
+// those of tap_issue: a - b is computed as fma(b, -1, a), which rounds a - b once.
+__device__ __forceinline__ void tap_issue2(const PrimRec &r, const ColXf &c, cudaTextureObject_t tex, float Wbf,
+                                           float Hbf, float2 py2, bool live0, bool live1, Tap &t0, Tap &t1) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 dy = __ffma2_rn(make_float2(r.y, r.y), m1, py2);
+    const float2 U = __ffma2_rn(make_float2(r.B, r.B), dy, make_float2(c.au, c.au));
+    const float2 V = __ffma2_rn(make_float2(r.D, r.D), dy, make_float2(c.cv, c.cv));
+    const float2 fu = make_float2(floorf(U.x), floorf(U.y)), fv = make_float2(floorf(V.x), floorf(V.y));
+    const float2 wu = __ffma2_rn(fu, m1, U), wv = __ffma2_rn(fv, m1, V);
+    t0.U = U.x; t0.V = V.x; t0.wu = wu.x; t0.wv = wv.x;
+    t1.U = U.y; t1.V = V.y; t1.wu = wu.y; t1.wv = wv.y;
+    t0.ok = live0 && U.x >= -1.0f && U.x < Wbf && V.x >= -1.0f && V.x < Hbf;
+    t1.ok = live1 && U.y >= -1.0f && U.y < Wbf && V.y >= -1.0f && V.y < Hbf;
+    if (t0.ok) {
+        const float4 g = tex2Dgather<float4>(tex, __fadd_rn(fu.x, 1.0f), __fadd_rn(fv.x, c.row), 0);
+        t0.q = make_float4(g.w, g.z, g.x, g.y);
+    }
+    if (t1.ok) {
+        const float4 g = tex2Dgather<float4>(tex, __fadd_rn(fu.y, 1.0f), __fadd_rn(fv.y, c.row), 0);
+        t1.q = make_float4(g.w, g.z, g.x, g.y);
+    }
+}
+
 // Bilinear value M (0 when !ok) and the two tap differences the backward needs:
 // dMdU = d0 + wv (d1 - d0), dMdV = m1 - m0.  M >= 0 whenever the texels are.
 __device__ __forceinline__ float tap_M(const Tap &t, float &dMdU, float &dMdV) {

@@ -265,23 +265,57 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
                     const PrimRec r = sh[t];
                     const int j = pos[t];
                     const ColXf cx = col_xf(r, kw, kv, px);
+                    if constexpr (PPT % 2 == 0) {
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], T[k] >= tstop, tp[k]);
+                        for (int k = 0; k < PPT; k += 2)
+                            tap_issue2(r, cx, a.atlas.tex, Wbf, Hbf, make_float2(py[k], py[k + 1]), T[k] >= tstop,
+                                       T[k + 1] >= tstop, tp[k], tp[k + 1]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k)
+                            tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], T[k] >= tstop, tp[k]);
+                    }
                     // Branch-free per pixel: a pixel that does not composite this layer
                     // has M = 0, so alpha = 0, q = 1 and every update below is an exact
                     // no-op (T * 1 = T, fma(0, c, C) = C).
                     bool any = false;
+                    float M[PPT];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) M[k] = tap_M(tp[k]);
+                    if constexpr (PPT % 2 == 0) {
+                        // two pixels per packed FP32x2 instruction (lane-wise the same
+                        // rounding as the scalar form below)
+                        const float2 a2 = make_float2(r.a, r.a), na2 = make_float2(-r.a, -r.a);
+                        const float2 one2 = make_float2(1.0f, 1.0f);
+                        const float2 cr2 = make_float2(r.cr, r.cr), cg2 = make_float2(r.cg, r.cg),
+                                     cb2 = make_float2(r.cb, r.cb);
+#pragma unroll
+                        for (int k = 0; k < PPT; k += 2) {
+                            const float2 M2 = make_float2(M[k], M[k + 1]);
+                            float2 T2 = make_float2(T[k], T[k + 1]);
+                            const float2 w = __fmul2_rn(T2, __fmul2_rn(a2, M2));
+                            T2 = __fmul2_rn(T2, __ffma2_rn(na2, M2, one2));
+                            const float2 c0 = __ffma2_rn(w, cr2, make_float2(C0[k], C0[k + 1]));
+                            const float2 c1 = __ffma2_rn(w, cg2, make_float2(C1[k], C1[k + 1]));
+                            const float2 c2 = __ffma2_rn(w, cb2, make_float2(C2[k], C2[k + 1]));
+                            T[k] = T2.x; T[k + 1] = T2.y;
+                            C0[k] = c0.x; C0[k + 1] = c0.y;
+                            C1[k] = c1.x; C1[k + 1] = c1.y;
+                            C2[k] = c2.x; C2[k + 1] = c2.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            const float w = __fmul_rn(T[k], __fmul_rn(r.a, M[k]));
+                            C0[k] = __fmaf_rn(w, r.cr, C0[k]);
+                            C1[k] = __fmaf_rn(w, r.cg, C1[k]);
+                            C2[k] = __fmaf_rn(w, r.cb, C2[k]);
+                            T[k] = __fmul_rn(T[k], __fmaf_rn(-r.a, M[k], 1.0f));
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float M = tap_M(tp[k]);
-                        const float al = __fmul_rn(r.a, M);
-                        const float q = __fsub_rn(1.0f, al);
-                        const float w = __fmul_rn(T[k], al);
-                        C0[k] = __fmaf_rn(w, r.cr, C0[k]);
-                        C1[k] = __fmaf_rn(w, r.cg, C1[k]);
-                        C2[k] = __fmaf_rn(w, r.cb, C2[k]);
-                        T[k] = __fmul_rn(T[k], q);
-                        const bool c = M > 0.0f;
+                        const bool c = M[k] > 0.0f;
                         last[k] = c ? j : last[k];
                         ct_it += c ? 1 : 0;
                         any = any || T[k] >= tstop;
@@ -405,7 +439,7 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
     for (int j = 0; j < upto; ++j) {
         const PrimRec r = a.rec[a.list[g.start + j]];
         tap_issue(r, col_xf(r, kw, kv, px), a.atlas.tex, Wbf, Hbf, py, true, tp);
-        T = __fmul_rn(T, __fsub_rn(1.0f, __fmul_rn(r.a, tap_M(tp))));
+        T = __fmul_rn(T, __fmaf_rn(-r.a, tap_M(tp), 1.0f));
     }
     return T;
 }
@@ -488,20 +522,46 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                 const PrimRec r = sh[t];
                 const int j = pos[t];
                 const ColXf cx = col_xf(r, kw, kv, px);
+                if constexpr (PPT % 2 == 0) {
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], j <= last[k], tp[k]);
+                    for (int k = 0; k < PPT; k += 2)
+                        tap_issue2(r, cx, a.atlas.tex, Wbf, Hbf, make_float2(py[k], py[k + 1]), j <= last[k],
+                                   j <= last[k + 1], tp[k], tp[k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], j <= last[k], tp[k]);
+                }
                 // Phase 1: alpha and the recovered transmittance in front of the layer.
                 // A pixel that does not composite this layer (behind its last layer,
-                // outside the bitmap, zero texels) has M = 0 and keeps T and Y.
-                float M[PPT], al[PPT], q[PPT], Tk[PPT];
+                // outside the bitmap, zero texels) has M = 0 and keeps T and Y.  The
+                // packed form keeps nal = -alpha; q = 1 - a M is rounded once (fma), as
+                // in the forward, so T_{k+1} = T_k q is undone by the same q.
+                const float2 na2 = make_float2(-r.a, -r.a);
+                float M[PPT], nal[PPT], q[PPT], Tk[PPT];
                 bool redo = false, any = false;
 #pragma unroll
+                for (int k = 0; k < PPT; ++k) M[k] = tap_M(tp[k]);
+                if constexpr (PPT % 2 == 0) {
+#pragma unroll
+                    for (int k = 0; k < PPT; k += 2) {
+                        const float2 M2 = make_float2(M[k], M[k + 1]);
+                        const float2 n2 = __fmul2_rn(na2, M2);
+                        const float2 q2 = __ffma2_rn(na2, M2, make_float2(1.0f, 1.0f));
+                        nal[k] = n2.x; nal[k + 1] = n2.y;
+                        q[k] = q2.x; q[k + 1] = q2.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        nal[k] = __fmul_rn(-r.a, M[k]);
+                        q[k] = __fmaf_rn(-r.a, M[k], 1.0f);
+                    }
+                }
+#pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    M[k] = tap_M(tp[k]);
-                    al[k] = __fmul_rn(r.a, M[k]);
-                    q[k] = __fsub_rn(1.0f, al[k]);
                     Tk[k] = M[k] > 0.0f ? __fdividef(T[k], q[k]) : T[k];
-                    redo = redo || al[k] >= 1.0f;   // 1 - alpha rounds to a positive float iff alpha < 1
+                    // alpha rounds below 1 only if a M < 1 - 2^-25, and then q > 0
+                    redo = redo || nal[k] <= -1.0f;
                     any = any || M[k] > 0.0f;
                 }
                 // no pixel of the warp composites this layer: T, Y and the sums are unchanged
@@ -509,38 +569,107 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                 if (__any_sync(FULL, redo)) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k)
-                        if (al[k] >= 1.0f) Tk[k] = rewalk_T(a, g, j, px, py[k]);
+                        if (nal[k] <= -1.0f) Tk[k] = rewalk_T(a, g, j, px, py[k]);
                 }
                 // Phase 2: the eight per-primitive sums.  The factor a (opacity) common
                 // to the geometric sums is applied once per primitive, and the
                 // centring of U, V (Up = U - kw, Vp = V - kv) is undone on the sums:
                 //   sum dM dMdU Up  = a (sum dA dMdU U - kw sum dA dMdU), and so on.
-                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3u = 0.0f, s3v = 0.0f, s4 = 0.0f;
-                float s5 = 0.0f, s6 = 0.0f, s7 = 0.0f;
+                // The packed form accumulates the negated sums (with -dL/dalpha and
+                // -T alpha) and applies the sign with the factor -a and in s5..s7.
+                float s0, s1, s2, s3u, s3v, s4, s5, s6, s7, ra;
+                if constexpr (PPT % 2 == 0) {
+                    const float2 ncr = make_float2(-r.cr, -r.cr), ncg = make_float2(-r.cg, -r.cg),
+                                 ncb = make_float2(-r.cb, -r.cb);
+                    float2 S0, S1, S2, S3u, S3v, S4, S5, S6, S7;
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    float dMdU, dMdV;
-                    tap_M(tp[k], dMdU, dMdV);
-                    const bool c = M[k] > 0.0f;
-                    T[k] = Tk[k];
-                    const float gc = g0[k] * r.cr + g1[k] * r.cg + g2[k] * r.cb;
-                    const float dA = c ? Tk[k] * (gc - Y[k]) : 0.0f;   // dL/dalpha_k
-                    const float gU = dA * dMdU, gV = dA * dMdV;        // / a
-                    s0 += gU;
-                    s1 += gV;
-                    s2 = fmaf(gU, tp[k].U, s2);
-                    s2 = fmaf(gV, tp[k].V, s2);
-                    s3u = fmaf(gU, tp[k].V, s3u);
-                    s3v = fmaf(gV, tp[k].U, s3v);
-                    s4 = fmaf(dA, M[k], s4);                           // / a
-                    const float w = Tk[k] * al[k];
-                    s5 = fmaf(g0[k], w, s5);
-                    s6 = fmaf(g1[k], w, s6);
-                    s7 = fmaf(g2[k], w, s7);
-                    Y[k] = fmaf(q[k], Y[k], al[k] * gc);
+                    for (int k = 0; k < PPT; k += 2) {
+                        float du0, dv0, du1, dv1;
+                        tap_M(tp[k], du0, dv0);
+                        tap_M(tp[k + 1], du1, dv1);
+                        T[k] = Tk[k];
+                        T[k + 1] = Tk[k + 1];
+                        const float2 G0 = make_float2(g0[k], g0[k + 1]), G1 = make_float2(g1[k], g1[k + 1]),
+                                     G2 = make_float2(g2[k], g2[k + 1]);
+                        float2 ngc = __fmul2_rn(G0, ncr);                  // -g . c
+                        ngc = __ffma2_rn(G1, ncg, ngc);
+                        ngc = __ffma2_rn(G2, ncb, ngc);
+                        const float2 Tk2 = make_float2(Tk[k], Tk[k + 1]);
+                        const float2 Y2 = make_float2(Y[k], Y[k + 1]);
+                        float2 ndA = __fmul2_rn(Tk2, __fadd2_rn(ngc, Y2));  // -dL/dalpha_k
+                        ndA.x = M[k] > 0.0f ? ndA.x : 0.0f;
+                        ndA.y = M[k + 1] > 0.0f ? ndA.y : 0.0f;
+                        const float2 gU = __fmul2_rn(ndA, make_float2(du0, du1));
+                        const float2 gV = __fmul2_rn(ndA, make_float2(dv0, dv1));
+                        const float2 U2 = make_float2(tp[k].U, tp[k + 1].U), V2 = make_float2(tp[k].V, tp[k + 1].V);
+                        const float2 M2 = make_float2(M[k], M[k + 1]);
+                        const float2 nal2 = make_float2(nal[k], nal[k + 1]);
+                        const float2 nw = __fmul2_rn(Tk2, nal2);            // -T_k alpha_k
+                        if (k == 0) {
+                            S0 = gU;
+                            S1 = gV;
+                            S2 = __fmul2_rn(gU, U2);
+                            S3u = __fmul2_rn(gU, V2);
+                            S3v = __fmul2_rn(gV, U2);
+                            S4 = __fmul2_rn(ndA, M2);
+                            S5 = __fmul2_rn(G0, nw);
+                            S6 = __fmul2_rn(G1, nw);
+                            S7 = __fmul2_rn(G2, nw);
+                        } else {
+                            S0 = __fadd2_rn(S0, gU);
+                            S1 = __fadd2_rn(S1, gV);
+                            S2 = __ffma2_rn(gU, U2, S2);
+                            S3u = __ffma2_rn(gU, V2, S3u);
+                            S3v = __ffma2_rn(gV, U2, S3v);
+                            S4 = __ffma2_rn(ndA, M2, S4);
+                            S5 = __ffma2_rn(G0, nw, S5);
+                            S6 = __ffma2_rn(G1, nw, S6);
+                            S7 = __ffma2_rn(G2, nw, S7);
+                        }
+                        S2 = __ffma2_rn(gV, V2, S2);
+                        // Y = q Y + alpha (g . c), with alpha (g . c) = (-alpha)(-g . c)
+                        const float2 Yn = __ffma2_rn(make_float2(q[k], q[k + 1]), Y2, __fmul2_rn(nal2, ngc));
+                        Y[k] = Yn.x;
+                        Y[k + 1] = Yn.y;
+                    }
+                    s0 = S0.x + S0.y;
+                    s1 = S1.x + S1.y;
+                    s2 = S2.x + S2.y;
+                    s3u = S3u.x + S3u.y;
+                    s3v = S3v.x + S3v.y;
+                    s4 = S4.x + S4.y;
+                    s5 = -S5.x - S5.y;
+                    s6 = -S6.x - S6.y;
+                    s7 = -S7.x - S7.y;
+                    ra = -r.a;
+                } else {
+                    s0 = s1 = s2 = s3u = s3v = s4 = s5 = s6 = s7 = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        float dMdU, dMdV;
+                        tap_M(tp[k], dMdU, dMdV);
+                        const bool c = M[k] > 0.0f;
+                        T[k] = Tk[k];
+                        const float al = -nal[k];
+                        const float gc = g0[k] * r.cr + g1[k] * r.cg + g2[k] * r.cb;
+                        const float dA = c ? Tk[k] * (gc - Y[k]) : 0.0f;   // dL/dalpha_k
+                        const float gU = dA * dMdU, gV = dA * dMdV;        // / a
+                        s0 += gU;
+                        s1 += gV;
+                        s2 = fmaf(gU, tp[k].U, s2);
+                        s2 = fmaf(gV, tp[k].V, s2);
+                        s3u = fmaf(gU, tp[k].V, s3u);
+                        s3v = fmaf(gV, tp[k].U, s3v);
+                        s4 = fmaf(dA, M[k], s4);                           // / a
+                        const float w = Tk[k] * al;
+                        s5 = fmaf(g0[k], w, s5);
+                        s6 = fmaf(g1[k], w, s6);
+                        s7 = fmaf(g2[k], w, s7);
+                        Y[k] = fmaf(q[k], Y[k], al * gc);
+                    }
+                    ra = r.a;
                 }
                 {
-                    const float ra = r.a;
                     float v[8];
                     v[0] = ra * s0;
                     v[1] = ra * s1;
