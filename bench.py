@@ -285,7 +285,9 @@ def traffic_for(kernel_key, tile, batch, ppt):
         e = d.get(kernel_key)
         if not e or (e.get("tile"), e.get("batch"), e.get("ppt")) != (tile, batch, ppt):
             return None
-        src = open(os.path.join(ROOT, "paper_2602_22625_gb300", "csrc", e["source"]), "rb").read()
+        # the kernel's source files (the compositor and the header with its sample helpers)
+        names = e.get("sources") or [e["source"]]
+        src = b"".join(open(os.path.join(ROOT, "paper_2602_22625_gb300", "csrc", n), "rb").read() for n in names)
         if hashlib.sha256(src).hexdigest() != e["sha256"]:
             return None
         return e["bytes_per_launch"]
