@@ -96,6 +96,7 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
                        const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t N,
                        AtlasView atlas, float alpha_max, int32_t tile, PrimRec *__restrict__ rec,
                        int4 *__restrict__ rect, DevStatus *status) {
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int c = find_canvas_by(cv, n_canvas, i, 0);
@@ -251,6 +252,8 @@ __device__ __forceinline__ int tile_count(const SlabWork &s, int tx, int ty) {
 
 __global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restrict__ cv,
                         int32_t n_canvas, int32_t *__restrict__ hist) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) uint32_t smem[];
     const CanvasDesc d = cv[find_canvas_by(cv, n_canvas, blockIdx.x, 1)];
     SlabWork s;
@@ -275,6 +278,8 @@ __global__ void k_count(const int4 *__restrict__ rect, const CanvasDesc *__restr
 // dependent chain per thread is an eighth of the column.
 __global__ void k_colscan(const CanvasDesc *__restrict__ cv, int32_t n_canvas, int32_t n_tiles,
                           int32_t *__restrict__ hist, int64_t *__restrict__ tile_cnt) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int32_t part[8][33];
     const int t = blockIdx.x * 32 + threadIdx.x;
     const int g = threadIdx.y;
@@ -316,6 +321,8 @@ __device__ __forceinline__ int len_bucket(int64_t len) {
 // persistent compositors.
 __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, int32_t n,
                                                    int64_t cap, DevStatus *status, int32_t *__restrict__ order) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t carry;
     __shared__ int32_t bucket[64];
@@ -399,6 +406,7 @@ __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__res
                           int32_t n_canvas, const int32_t *__restrict__ hist,
                           const int64_t *__restrict__ tile_off, int32_t *__restrict__ list,
                           const DevStatus *status) {
+    pdl_wait();
     extern __shared__ __align__(16) uint32_t smem[];
     if (status->lists_valid == 0) return;
     const CanvasDesc d = cv[find_canvas_by(cv, n_canvas, blockIdx.x, 1)];
@@ -553,15 +561,19 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
     const int chunk_threads = bin_threads(b.chunk_log2);
     const dim3 grid_cs(b.n_chunks, b.max_slabs);
     if (b.n_chunks > 0) {
-        k_count<<<grid_cs, chunk_threads, b.smem_count, st>>>(b.rect, b.canvas, b.n_canvas, b.hist);
+        cudaError_t e = launch_pdl(k_count, grid_cs, dim3(chunk_threads), b.smem_count, st, b.rect, b.canvas,
+                                   b.n_canvas, b.hist);
+        if (e != cudaSuccess) return e;
     }
-    k_colscan<<<(b.n_tiles + 31) / 32, dim3(32, 8), 0, st>>>(b.canvas, b.n_canvas, b.n_tiles, b.hist,
-                                                             b.tile_off);
-    k_tilescan<<<1, 1024, 0, st>>>(b.tile_off, b.n_tiles, b.cap, b.status, b.tile_order);
-    if (b.n_chunks > 0) {
-        k_scatter<<<grid_cs, chunk_threads, b.smem_scatter, st>>>(b.rect, b.canvas, b.n_canvas, b.hist,
-                                                         b.tile_off, b.list, b.status);
-    }
+    cudaError_t e = launch_pdl(k_colscan, dim3((b.n_tiles + 31) / 32), dim3(32, 8), 0, st, b.canvas, b.n_canvas,
+                               b.n_tiles, b.hist, b.tile_off);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_tilescan, dim3(1), dim3(1024), 0, st, b.tile_off, b.n_tiles, b.cap, b.status,
+                       b.tile_order);
+    if (e == cudaSuccess && b.n_chunks > 0)
+        e = launch_pdl(k_scatter, grid_cs, dim3(chunk_threads), b.smem_scatter, st, b.rect, b.canvas, b.n_canvas,
+                       b.hist, b.tile_off, b.list, b.status);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

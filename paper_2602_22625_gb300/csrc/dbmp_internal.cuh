@@ -204,6 +204,31 @@ __device__ __forceinline__ void acc_sq(float d, float &s, float &c) {
     c = __fadd_rn(c, __fadd_rn(se, pe));
 }
 
+// Programmatic dependent launch (PDL).  A kernel launched with launch_pdl may start
+// while the previous kernel of the stream is still running; pdl_wait(), its first
+// statement, returns once that kernel has completed and its writes are visible
+// (hardware-managed, no spin of ours).  pdl_trigger() lets the next kernel launch
+// as soon as every CTA of this one has issued it, instead of after the last exits.
+// A kernel launched without the attribute passes pdl_wait() at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (one translation unit each).
 // ---------------------------------------------------------------------------

@@ -147,6 +147,8 @@ struct AdamArgs {
 
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, int64_t n, const int32_t *step, AdamArgs c) {
+    pdl_wait();
+    pdl_trigger();
     const int t = *step + 1;
     const float bc1 = 1.0f - powf(c.beta1, (float)t);
     const float bc2 = 1.0f - powf(c.beta2, (float)t);
@@ -168,6 +170,8 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ g, float *__re
 // thread, with the column gains in registers; for 16-byte aligned arrays.
 __global__ void k_adam8(float4 *__restrict__ p, float4 *__restrict__ g, float4 *__restrict__ m,
                         float4 *__restrict__ v, int32_t N, const int32_t *step, AdamArgs c) {
+    pdl_wait();
+    pdl_trigger();
     const int t = *step + 1;
     const float bc1 = 1.0f - powf(c.beta1, (float)t);
     const float bc2 = 1.0f - powf(c.beta2, (float)t);
@@ -195,7 +199,10 @@ __global__ void k_adam8(float4 *__restrict__ p, float4 *__restrict__ g, float4 *
     }
 }
 
-__global__ void k_step_inc(int32_t *step) { *step += 1; }
+__global__ void k_step_inc(int32_t *step) {
+    pdl_wait();
+    *step += 1;
+}
 
 // Blocks for n work items of `threads` threads, at most `per_sm` resident blocks
 // per SM (grid-stride loops take the rest).
@@ -288,13 +295,16 @@ cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32
     c.zero_grad = cfg.zero_grad;
     const int64_t n = (int64_t)N * 8;
     const bool aligned = ((((uintptr_t)p) | ((uintptr_t)g) | ((uintptr_t)m) | ((uintptr_t)v)) & 15) == 0;
+    cudaError_t e = cudaSuccess;
     if (n > 0 && aligned)
-        k_adam8<<<grid_for(N, 128), 128, 0, st>>>(reinterpret_cast<float4 *>(p), reinterpret_cast<float4 *>(g),
-                                                 reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), N, step,
-                                                 c);
+        e = launch_pdl(k_adam8, dim3(grid_for(N, 128)), dim3(128), 0, st, reinterpret_cast<float4 *>(p),
+                       reinterpret_cast<float4 *>(g), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), N,
+                       static_cast<const int32_t *>(step), c);
     else if (n > 0)
-        k_adam<<<grid_for(n, 256), 256, 0, st>>>(p, g, m, v, n, step, c);
-    k_step_inc<<<1, 1, 0, st>>>(step);
+        e = launch_pdl(k_adam, dim3(grid_for(n, 256)), dim3(256), 0, st, p, g, m, v, n,
+                       static_cast<const int32_t *>(step), c);
+    if (e == cudaSuccess) e = launch_pdl(k_step_inc, dim3(1), dim3(1), 0, st, step);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

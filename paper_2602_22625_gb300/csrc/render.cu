@@ -702,6 +702,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
 // The sums are read and then zeroed, so graw is zero again for the next backward.
 __global__ void k_finalize(const float *__restrict__ params, const PrimRec *__restrict__ rec,
                            float *__restrict__ graw, float *__restrict__ dparams, int32_t N) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const PrimRec r = rec[i];
@@ -818,7 +820,11 @@ cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
 
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
                                  float *dparams, int32_t N, cudaStream_t st) {
-    if (N > 0) k_finalize<<<(N + 255) / 256, 256, 0, st>>>(params, rec, graw, dparams, N);
+    if (N > 0) {
+        const cudaError_t e = launch_pdl(k_finalize, dim3((N + 255) / 256), dim3(256), 0, st, params, rec, graw,
+                                         dparams, N);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
