@@ -30,6 +30,9 @@
  *   - Every call that takes a cudaStream_t only queues work on that stream and
  *     never synchronises it, except where stated (dbmp_status_poll,
  *     dbmp_workspace_create/destroy, dbmp_atlas_create/destroy, dbmp_autotune).
+ *     Some kernels are launched as programmatic dependents of the kernel before
+ *     them in the stream and wait for its completion before their first memory
+ *     access, so stream order holds whatever the caller queued before a call.
  *   - Errors found on the device (tile-list capacity exceeded, degenerate
  *     primitives) are recorded in the workspace's status block; read them with
  *     dbmp_status_poll.  A kernel that finds the capacity error set does nothing.
