@@ -497,3 +497,49 @@ def test_fused_mse_matches_the_separate_passes(tuning):
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)
+
+
+def test_batched_64_canvases_in_the_benchmarked_configuration():
+    """The 64-canvas batch the benchmark times (sides 256..1024, 1k..50k primitives per
+    canvas, 1.03 M in all), planned at tile 32, batch 32, 4 px/lane, T_stop 1e-6, in one
+    binning, one forward and one backward launch.  Four canvases (the cheapest two, the
+    median and the largest) against the oracle: every pixel and T, and the gradients of
+    primitives sampled from each canvas' front quarter under a random upstream gradient."""
+    cuda()
+    scenes = inputs.batched(seed=4)
+    atlas_np = scenes[0].atlas
+    params, bid, off, pix = concat(scenes)
+    N, P = int(off[-1]), int(pix[-1])
+    rng = np.random.default_rng(64)
+    gI = rng.normal(size=3 * P).astype(np.float32) * 1e-3
+    atlas = D.dbmp_atlas_create(to_dev(atlas_np))
+    n_tiles = sum((s.W // 8) * (s.H // 8) for s in scenes)
+    ws = D.dbmp_workspace_create(N, n_tiles, 400 << 20, len(scenes))
+    try:
+        D.dbmp_batch_plan(ws, [s.H for s in scenes], [s.W for s in scenes], off.tolist(), tile=32, batch=32,
+                          ppt=4, ppt_bwd=4)
+        p, b = to_dev(params), to_dev(bid)
+        image = torch.empty(3 * P, device="cuda")
+        T = torch.empty(P, device="cuda")
+        nl = torch.empty(P, dtype=torch.int32, device="cuda")
+        dp = torch.zeros(N, 8, device="cuda")
+        D.dbmp_batch_render(ws, p, b, atlas, 1.0, D.make_background((1.0, 1.0, 1.0)), 1e-6,
+                            D.BATCH_BIN | D.BATCH_FWD | D.BATCH_BWD, image, T, nl, to_dev(gI), dp)
+        assert D.dbmp_status_poll(ws).code == 0
+        torch.cuda.synchronize()
+        img, Tf, g = image.cpu().numpy(), T.cpu().numpy(), dp.cpu().numpy().astype(np.float64)
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+    cost = sorted(range(len(scenes)), key=lambda c: scenes[c].H * scenes[c].W * scenes[c].N)
+    for c in (cost[0], cost[1], cost[len(cost) // 2], cost[-1]):
+        s = scenes[c]
+        ref = oracle.render(s.H, s.W, s.params, s.bitmap_id, atlas_np, background=(1.0, 1.0, 1.0), T_stop=1e-6)
+        got = img[3 * pix[c]: 3 * pix[c + 1]].reshape(3, s.H, s.W)
+        assert np.abs(got - ref["image"]).max() <= IMG_TOL, f"canvas {c}"
+        assert np.abs(Tf[pix[c]: pix[c + 1]].reshape(s.H, s.W) - ref["T_final"]).max() <= IMG_TOL
+        gIc = gI[3 * pix[c]: 3 * pix[c + 1]].reshape(3, s.H, s.W)
+        sel = np.sort(rng.choice(max(4, s.N // 4), 4, replace=False))   # front quarter: visible layers
+        gref = oracle.grad_selected(s.H, s.W, s.params, s.bitmap_id, atlas_np, gIc, sel,
+                                    background=(1.0, 1.0, 1.0), T_stop=1e-6)
+        grad_close(g[off[c] + sel], gref, what=f"canvas {c}")
