@@ -116,10 +116,10 @@ __device__ __forceinline__ ColXf col_xf(const PrimRec &r, float kw, float kv, fl
 }
 
 // The per-pixel half of a sample.  tap_issue transforms the pixel, tests the range
-// and issues the 128-bit tap load; tap_M blends.  Splitting them lets a lane have
-// the loads of all its pixels in flight before it blends.  q keeps its previous
-// contents when no load is issued (ok false); tap_M then returns 0 without
-// reading it, and every other quantity computed from q stays finite.
+// and issues the texture gather of the four taps; tap_M blends.  Splitting them lets
+// a lane have the gathers of all its pixels in flight before it blends.  q keeps its
+// previous contents when no gather is issued (ok false); tap_M then returns 0
+// without reading it, and every other quantity computed from q stays finite.
 struct Tap {
     float4 q;                  // (p00, p01, p10, p11)
     float U, V, wu, wv;        // bitmap coordinates and their fractional parts
