@@ -148,3 +148,36 @@ def test_stress_workload_dense_tiles_and_localized_fd(stress):
         errs.append(np.abs(g[i] - fd) / max(np.abs(fd).max(), 1e-12))
     errs = np.concatenate(errs)
     assert np.median(errs) < 1e-3 and errs.max() < 0.5, errs
+
+
+def test_stress_workload_64_random_tiles_match_oracle(stress):
+    """The 2048^2 x 200k stress canvas (lists above 5 000 primitives) in the launch
+    configuration the benchmark times (tile 32, batch 32, 4 px/lane, T_stop 1e-6):
+    every pixel of 64 random 32 x 32 tiles, image and T, against the oracle."""
+    cuda()
+    sc = stress
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, (sc.W // 8) * (sc.H // 8), 400 << 20, 1)
+    try:
+        D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N], tile=32, batch=32, ppt=4, ppt_bwd=4)
+        image = torch.empty(3, sc.H, sc.W, device="cuda")
+        T = torch.empty(sc.H, sc.W, device="cuda")
+        nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+        D.dbmp_batch_render(ws, to_dev(sc.params), to_dev(sc.bitmap_id), atlas, 1.0,
+                            D.make_background(sc.background), 1e-6, D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
+        assert D.dbmp_status_poll(ws).code == 0
+        torch.cuda.synchronize()
+        img, Tf = image.cpu().numpy(), T.cpu().numpy()
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+    rng = np.random.default_rng(23)
+    ntx = sc.W // 32
+    tiles = rng.choice(ntx * (sc.H // 32), 64, replace=False)
+    ys, xs = np.mgrid[0:32, 0:32]
+    px = np.concatenate([(t % ntx) * 32 + xs.ravel() for t in tiles])
+    py = np.concatenate([(t // ntx) * 32 + ys.ravel() for t in tiles])
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background, T_stop=1e-6,
+                        pixels=(px, py))
+    assert np.abs(img[:, py, px] - ref["image"]).max() <= 1e-5
+    assert np.abs(Tf[py, px] - ref["T_final"]).max() <= 1e-5
