@@ -257,20 +257,21 @@ def binning_hbm(N, K, n_tiles, bin_ms):
     parameters and bitmap ids read (36 B per primitive), the records written for the
     compositors (48 B per primitive), the tile lists (4 B per entry) and the tile
     offsets (8 B per tile)."""
-    peak = hbm_peak_gbs()
+    peak, source = hbm_peak_gbs()
     nbytes = 36 * N + 48 * N + 4 * K + 8 * (n_tiles + 1)
     achieved = nbytes / (bin_ms * 1e-3) / 1e9
     return {"bytes": nbytes, "ms": bin_ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
+            "frac": achieved / peak, "peak_source": source}
 
 
 def hbm_peak_gbs():
-    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    """(GB/s, where it comes from): the measured copy bandwidth, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
-            return float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
     except (OSError, ValueError, KeyError):
-        return 6800.0   # fallback: one earlier measurement on a GB300
+        return 6800.0, "fallback: 6.8 TB/s, one earlier copy measurement on a GB300"   # no measured file
 
 
 def traffic_for(kernel_key, tile, batch, ppt):
