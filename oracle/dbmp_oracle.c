@@ -200,25 +200,28 @@ static orc_prim *make_prims(int32_t N, const float *params, const int32_t *bitma
 /* Renders the pixels (px[i], py[i]), i < n_pix.  If px == NULL, renders the whole
  * H x W canvas in row-major order (n_pix ignored).  Outputs are indexed like the
  * pixel list: image[j * n + i], T_final[i], n_last[i] (index of the last
- * contributing primitive, -1 if none).  Returns the number of sampled pairs. */
+ * contributing primitive, -1 if none).  Returns the number of sampled pairs; if
+ * `contrib` is not NULL it receives the number of contributing pairs: layers with
+ * M > 0 that a pixel composites while its transmittance is still >= T_stop. */
 int64_t oracle_render(int32_t H, int32_t W, int32_t N, const float *params,
                       const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
                       int32_t Wb, double alpha_max, int32_t bg_mode, const double *bg_rgb,
                       const float *bg_buf, double T_stop, int64_t n_pix, const int32_t *px,
-                      const int32_t *py, double *image, double *T_final, int32_t *n_last) {
+                      const int32_t *py, double *image, double *T_final, int32_t *n_last,
+                      int64_t *contrib) {
     (void)n_bmp;
     orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
     int64_t n = px ? n_pix : (int64_t)H * (int64_t)W;
     size_t HW = (size_t)H * (size_t)W;
-    int64_t pairs = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : pairs)
+    int64_t pairs = 0, n_contrib = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : pairs, n_contrib)
     for (int64_t i = 0; i < n; ++i) {
         int32_t x = px ? px[i] : (int32_t)(i % W);
         int32_t y = px ? py[i] : (int32_t)(i / W);
         double C[3], T;
         int32_t last;
         int64_t pr = 0;
-        walk_pixel(P, N, Hb, Wb, (double)x, (double)y, T_stop, NULL, C, &T, &last, &pr);
+        n_contrib += walk_pixel(P, N, Hb, Wb, (double)x, (double)y, T_stop, NULL, C, &T, &last, &pr);
         pairs += pr;
         size_t pix = (size_t)y * (size_t)W + (size_t)x;
         for (int j = 0; j < 3; ++j)
@@ -228,6 +231,7 @@ int64_t oracle_render(int32_t H, int32_t W, int32_t N, const float *params,
         n_last[i] = last;
     }
     free(P);
+    if (contrib) *contrib = n_contrib;
     return pairs;
 }
 

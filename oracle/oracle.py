@@ -36,7 +36,7 @@ def lib():
         L.oracle_render.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p, _i32p,
                                     _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_double, ctypes.c_int32, _f64p, _f32p, ctypes.c_double,
-                                    ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _i32p]
+                                    ctypes.c_int64, _i32p, _i32p, _f64p, _f64p, _i32p, _i64p]
         L.oracle_grad.restype = None
         L.oracle_grad.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p, _i32p,
                                   _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -123,7 +123,8 @@ def render(H, W, params, bitmap_id, atlas, alpha_max=1.0, background=(1.0, 1.0, 
     """Forward (Eqs. 1-5, 8) in FP64.
 
     Returns dict(image (3,H,W) or (3,n), T_final, n_last (index of last contributing
-    primitive, -1 if none), pairs (number of sampled (pixel, primitive) pairs)).
+    primitive, -1 if none), pairs (number of sampled (pixel, primitive) pairs),
+    contrib (contributing pairs: layers with M > 0 composited while T >= T_stop)).
     `pixels` = (px, py) int arrays renders only those pixels."""
     params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
     mode, rgb, buf = _bg(background, H, W)
@@ -137,14 +138,15 @@ def render(H, W, params, bitmap_id, atlas, alpha_max=1.0, background=(1.0, 1.0, 
     image = np.empty((3, n), np.float64)
     T = np.empty(n, np.float64)
     last = np.empty(n, np.int32)
+    contrib = np.zeros(1, np.int64)
     pairs = lib().oracle_render(H, W, N, _p(params, _f32p), _p(bitmap_id, _i32p),
                                 _p(atlas, _f32p), atlas.shape[0], atlas.shape[1], atlas.shape[2],
                                 float(alpha_max), mode, _p(rgb, _f64p), _p(buf, _f32p),
                                 float(T_stop), n, _p(px, _i32p), _p(py, _i32p),
-                                _p(image, _f64p), _p(T, _f64p), _p(last, _i32p))
+                                _p(image, _f64p), _p(T, _f64p), _p(last, _i32p), _p(contrib, _i64p))
     if pixels is None:
         image, T, last = image.reshape(3, H, W), T.reshape(H, W), last.reshape(H, W)
-    return dict(image=image, T_final=T, n_last=last, pairs=int(pairs))
+    return dict(image=image, T_final=T, n_last=last, pairs=int(pairs), contrib=int(contrib[0]))
 
 
 def grad(H, W, params, bitmap_id, atlas, dL_dimage, dL_dalpha=None, alpha_max=1.0,

@@ -428,3 +428,47 @@ def test_adam_matches_torch_optim_adam():
         p, m, v = oracle.adam_step(p, g, m, v, t, lr)
     ref = np.stack([c.detach().numpy() for c in cols], 1)
     np.testing.assert_allclose(p, ref, rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# The contributing-pair count (the work unit of the compositors' roofline)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T_stop", [0.0, 1e-2])
+def test_contributing_pair_count_matches_a_torch_walk(T_stop):
+    """Layers with M > 0 that a pixel composites while T >= T_stop, counted by the
+    oracle's walk, equal the count of Algorithm S3 in torch (grid_sample per layer,
+    a pixel frozen once its T falls below T_stop)."""
+    import torch.nn.functional as F
+    rng = np.random.default_rng(77)
+    H, W, N = 26, 31, 16
+    atlas = inputs.soft_disc_atlas(9, 2, 32)   # solid interiors: pixels saturate
+    params = np.zeros((N, 8), np.float32)
+    params[:, 0] = rng.uniform(0, W, N)
+    params[:, 1] = rng.uniform(0, H, N)
+    params[:, 2] = rng.uniform(8, 18, N)
+    params[:, 3] = rng.uniform(-7, 7, N)
+    params[:, 4] = rng.uniform(3, 8, N)
+    params[:, 5:8] = rng.uniform(-3, 3, (N, 3))
+    bid = rng.integers(0, atlas.shape[0], N).astype(np.int32)
+    A = torch.tensor(atlas.astype(np.float64))
+    p = torch.tensor(params.astype(np.float64))
+    Y, X = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64),
+                          indexing="ij")
+    T = torch.ones(H, W, dtype=torch.float64)
+    count = 0
+    for i in range(N):
+        x, y, s, th, nu = p[i, 0], p[i, 1], p[i, 2], p[i, 3], p[i, 4]
+        u = (torch.cos(th) * (X - x) + torch.sin(th) * (Y - y)) / s
+        v = (-torch.sin(th) * (X - x) + torch.cos(th) * (Y - y)) / s
+        m = F.grid_sample(A[int(bid[i])][None, None], torch.stack([u, v], -1)[None], mode="bilinear",
+                          padding_mode="zeros", align_corners=True)[0, 0]
+        a = torch.sigmoid(nu) * m
+        alive = T >= T_stop
+        count += int(((m > 0) & alive).sum())
+        T = torch.where(alive, T * (1 - a), T)
+    out = oracle.render(H, W, params, bid, atlas, T_stop=T_stop)
+    assert out["contrib"] == count
+    assert 0 < count <= out["pairs"]
+    if T_stop > 0:   # early termination removes work
+        assert count < oracle.render(H, W, params, bid, atlas)["contrib"]
