@@ -38,8 +38,9 @@ def test_binning_bytes_and_peak_source(tmp_path, monkeypatch):
     r = bench.binning_hbm(N=10, K=100, n_tiles=4, bin_ms=1.0)
     assert r["bytes"] == 36 * 10 + 48 * 10 + 4 * 100 + 8 * 5
     assert r["achieved"] == pytest.approx(r["bytes"] / 1e-3 / 1e9)
-    measured = json.load(open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    assert r["peak"] == measured and "measured" in r["peak_source"]
+    peaks = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):   # written per machine, not part of the sources
+        assert r["peak"] == json.load(open(peaks))["hbm_gbs"] and "measured" in r["peak_source"]
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))   # no MEASURED_PEAKS.json there
     peak, src = bench.hbm_peak_gbs()
     assert peak == 6800.0 and src.startswith("fallback")
