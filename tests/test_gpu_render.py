@@ -343,7 +343,8 @@ def test_main_workload_in_the_benchmarked_configuration():
         D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BIN, None, T, nl)
         D.dbmp_batch_render_mse(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_FWD, target, image, T, nl, dL, loss)
         D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BWD, image, T, nl, dL, dp)
-        assert D.dbmp_status_poll(ws).code == 0
+        st = D.dbmp_status_poll(ws)
+        assert st.code == 0
         grad = dp.cpu().numpy().astype(np.float64)
         D.dbmp_adam_step(p, dp, m, v, step, cfg)
         torch.cuda.synchronize()
@@ -352,6 +353,10 @@ def test_main_workload_in_the_benchmarked_configuration():
                             T_stop=1e-6)
         assert np.abs(img - ref["image"]).max() <= IMG_TOL
         assert np.abs(T.cpu().numpy() - ref["T_final"]).max() <= IMG_TOL
+        # the work count behind the roofline: layers with M > 0 composited while
+        # T >= T_stop; fp32 and FP64 part on M > 0 or on the threshold only for pixels
+        # within rounding of the support edge or of T_stop
+        assert abs(st.pairs_contributing - ref["contrib"]) <= 1e-2 * ref["contrib"]
         # the loss of the GPU's own image to summation order; against the oracle's image,
         # |mean(d1^2) - mean(d2^2)| <= max|d1 - d2| * mean|d1 + d2| bounds the difference
         L = loss.item()
