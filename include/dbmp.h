@@ -135,7 +135,8 @@ typedef struct {
     int64_t pairs_required; /* sum_t d_t of the last binning                    */
     int64_t pairs_evaluated;/* (pixel, list entry) pairs the last fwd evaluated  */
     int64_t pairs_evaluated_bwd; /* same for the last bwd                       */
-    int64_t pairs_contributing;  /* pairs with alpha > 0 the last fwd composited  */
+    int64_t pairs_contributing;  /* pairs with alpha > 0 the last fwd composited,
+                                    i.e. layers with M > 0 met while T >= T_stop */
     int64_t warp_steps;          /* list entries walked by warps in the last fwd   */
     int64_t warp_steps_bwd;      /* same for the last bwd                          */
     int64_t survivors;           /* list entries that passed the region test (fwd) */
