@@ -34,6 +34,10 @@ MUTANTS = {
                              "const double d = (double)P[(size_t)yy * W + xx];"),
     "base_probability_dropped": ("const double w = 0.1 + 0.9 * lv[p];", "const double w = lv[p];"),
     "scale_rule_reversed": ("o[2] = s_max - (s_max - s_min) * lv[p];", "o[2] = s_min + (s_max - s_min) * lv[p];"),
+    "grad_selected_clip_off_by_one": ("if (x1 > W - 1) x1 = W - 1;", "if (x1 > W - 2) x1 = W - 2;"),
+    "grad_selected_box_row_dropped": ("y1 = (long)ceil(q->yhi);", "y1 = (long)floor(q->yhi) - 1;"),
+    "grad_selected_row_index": ("pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, sel[t]);",
+                                "pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, t);"),
     "mask_ignored": ("Q[p + 1] = Q[p] + (mask && !(mask[p] > 0.0f) ? 0 : (int64_t)floor(w * 1048576.0));",
                      "Q[p + 1] = Q[p] + (int64_t)floor(w * 1048576.0);"),
 }

@@ -472,3 +472,60 @@ def test_contributing_pair_count_matches_a_torch_walk(T_stop):
     assert 0 < count <= out["pairs"]
     if T_stop > 0:   # early termination removes work
         assert count < oracle.render(H, W, params, bid, atlas)["contrib"]
+
+
+# --------------------------------------------------------------------------
+# The sampled gradient (grad_selected) against the full gradient
+# --------------------------------------------------------------------------
+
+def _edge_scene(seed):
+    """A ragged 37 x 29 canvas of soft discs plus the placements where a support box
+    meets the canvas border or the box rule itself matters: primitives centred past
+    the right and bottom edges and across the top-left corner, rotated ones, a
+    negative scale, a NaN parameter and a zero scale."""
+    H, W = 37, 29
+    sc = inputs.tiny(seed=seed, N=24, H=H, W=W)
+    extra = np.array([
+        [W + 3.0, H / 2, 9.0, 0.4, 0.5, 0.3, -0.2, 1.0],     # past the right edge
+        [W / 2, H + 2.5, 7.5, 2.0, 0.2, -1.0, 0.4, 0.1],     # past the bottom edge
+        [W - 0.5, H - 0.5, 11.0, 0.9, 1.0, 0.6, 0.6, -0.6],  # bottom-right corner
+        [-2.0, -3.0, 8.0, 5.1, 0.7, 0.1, 0.9, -0.3],         # across the top-left corner
+        [10.0, 12.0, -6.0, 1.2, 0.4, -0.4, 0.2, 0.8],        # negative scale
+        [14.0, 20.0, 5.0, float("nan"), 0.0, 0.0, 0.0, 0.0], # NaN angle: no contribution
+        [15.0, 15.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0],          # zero scale: no contribution
+        [W - 1.0, 4.0, 3.2, 0.785, 2.0, 1.5, -1.5, 0.0],     # small, at the last column
+    ], np.float32)
+    params = np.concatenate([sc.params[:12], extra, sc.params[12:]])
+    bid = np.zeros(params.shape[0], np.int32)
+    return H, W, params, bid, sc.atlas
+
+
+@pytest.mark.parametrize("bg", ["const", "none", "buffer"])
+@pytest.mark.parametrize("T_stop", [0.0, 1e-6])
+def test_grad_selected_equals_the_rows_of_the_full_gradient(bg, T_stop):
+    """grad_selected sums each selected primitive's per-pixel terms over its support
+    box clipped to the canvas; every pixel outside the box contributes exactly zero
+    (Eq. 6, Eqs. S4-S5), so its rows must equal those of the full gradient, whatever
+    the selection order, with repeats, on all three backgrounds (Eq. 8), alpha_max < 1
+    and a dL/dI_alpha term."""
+    H, W, params, bid, atlas = _edge_scene(7)
+    rng = np.random.default_rng(3)
+    background = {"const": (0.9, 0.2, 0.5), "none": None,
+                  "buffer": rng.uniform(0, 1, (3, H, W)).astype(np.float32)}[bg]
+    gI = rng.normal(size=(3, H, W)).astype(np.float32)
+    gA = rng.normal(size=(H, W)).astype(np.float32)
+    N = params.shape[0]
+    sel = np.concatenate([rng.permutation(N), [13, 13, 0, N - 1]]).astype(np.int32)
+    for amax, dA in ((1.0, None), (0.65, gA)):
+        full = oracle.grad(H, W, params, bid, atlas, gI.astype(np.float64), dL_dalpha=dA, alpha_max=amax,
+                           background=background, T_stop=T_stop)
+        part = oracle.grad_selected(H, W, params, bid, atlas, gI, sel, dL_dalpha=dA, alpha_max=amax,
+                                    background=background, T_stop=T_stop)
+        scale = np.abs(full).max()
+        assert scale > 0
+        np.testing.assert_allclose(part, full[sel], rtol=0, atol=1e-12 * scale)
+        # the edge primitives do contribute, so the clipped boxes were exercised
+        for i in (12, 13, 14, 15, 16, 19):
+            assert np.abs(full[i]).max() > 1e-6 * scale, i
+        # invalid primitives: zero rows on both sides
+        assert not full[17].any() and not full[18].any()
