@@ -39,10 +39,7 @@ FLOPS_COMPOSITE = 10    # Eqs. 3-5 (alpha, over, transmittance)
 FLOPS_GRAD = 44         # Eq. 6, S4, S5 terms and the reverse recursion
 FLOPS_FWD_PAIR = FLOPS_SAMPLE + FLOPS_COMPOSITE
 FLOPS_BWD_PAIR = FLOPS_SAMPLE + FLOPS_GRAD
-SM_COUNT = 152
-FP32_LANES = 128
-SM_MAX_MHZ = 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP32_LANES = 128        # FP32 multiply-add lanes per SM (4 sub-partitions x 32)
 
 # kernels one step launches (bin: prep, count, colscan, tilescan with the tile ordering, scatter;
 # fwd with the MSE loss in its epilogue; bwd, finalize; adam, step counter)
@@ -274,6 +271,28 @@ def hbm_peak_gbs():
         return 6800.0, "fallback: 6.8 TB/s, one earlier copy measurement on a GB300"   # no measured file
 
 
+def fp32_peak(local):
+    """The FP32 rate the compositors' ALU roofline divides by, measured on this GPU:
+    dbmp_fp32_peak's independent multiply-add chains with scalar FFMA and with packed
+    FP32x2 FMA instructions, clocks sampled meanwhile.  peak = the faster form.  Also
+    the figure derived from the queried SM count, 128 FP32 lanes and the maximum SM
+    clock, for comparison."""
+    import torch
+    from paper_2602_22625_gb300 import microbench
+    with Clocks(local) as clk:
+        r = microbench.fp32(iters=20000, reps=25)
+    c = clk.summary()
+    mx = c.get("sm_max_mhz") or 2070.0
+    derived = r["sms"] * FP32_LANES * 2 * mx * 1e6 / 1e12
+    best = "ffma2" if r["ffma2_tflops"] > r["ffma_tflops"] else "ffma"
+    return {"peak": r[f"{best}_tflops"], "ffma_tflops": r["ffma_tflops"], "ffma2_tflops": r["ffma2_tflops"],
+            "sms": r["sms"], "sm_mhz": c.get("sm_mhz"), "sm_max_mhz": mx, "reasons": c.get("reasons"),
+            "derived_tflops": derived,
+            "source": f"measured: dbmp_fp32_peak ({best}), {r['sms']} SMs x 8 CTAs x 256 threads x 16 "
+                      f"independent chains, median SM clock {c.get('sm_mhz')} MHz",
+            "device": torch.cuda.get_device_name(local)}
+
+
 def traffic_for(kernel_key, tile, batch, ppt):
     """DRAM bytes per launch from the committed ncu summary, if it still matches the
     source and was taken at this tuning (tile, batch, the pass' pixels per lane)."""
@@ -378,7 +397,7 @@ def learned_vs_plain(n_pairs, batch=64, n_targets=8, steps=200):
         scenes.close()
 
 
-def other_workload(name, steps=5, warmup=3):
+def other_workload(name, peak_tflops, steps=5, warmup=3):
     """One optimisation step (bin, forward with the fused MSE, backward, Adam) of the
     batched workload (64 canvases, side U{256..1024}, N log-uniform [1k, 50k], one
     plan and one persistent launch per pass) or the stress workload (2048^2, 200k
@@ -470,7 +489,7 @@ def other_workload(name, steps=5, warmup=3):
                 "breakdown_ms": {"bin": float(ph[:, 0].mean()), "fwd_with_mse": float(ph[:, 1].mean()),
                                  "bwd": bwd, "adam": float(ph[:, 3].mean())},
                 "pairs_contributing": s_.pairs_contributing, "tile_list_entries": s_.pairs_required,
-                "bwd_tflops": bwd_tf, "bwd_frac_of_fp32_peak": bwd_tf / FP32_PEAK_TFLOPS,
+                "bwd_tflops": bwd_tf, "bwd_frac_of_fp32_peak": bwd_tf / peak_tflops,
                 "steps": steps, "l2": "flushed between timed steps"}
     finally:
         D.dbmp_workspace_destroy(ws)
@@ -630,6 +649,7 @@ def run_dbmp(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     D.load()
+    peak = fp32_peak(local)
 
     # inputs: each rank renders its own workload (weak scaling: no exchange)
     seed, tgt_seed = rank_seeds(rank)
@@ -808,7 +828,7 @@ def run_dbmp(args):
     if rank == 0 and world == 1 and not args.no_ablation:
         ablation = blur_ablation()
         constrained = spatial_constraint()
-        others = [other_workload("batched"), other_workload("stress")]
+        others = [other_workload("batched", peak["peak"]), other_workload("stress", peak["peak"])]
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -831,9 +851,9 @@ def run_dbmp(args):
                  "tile_list_entries": pairs_end[3], "warp_steps_fwd": st.warp_steps,
                  "warp_steps_bwd": st.warp_steps_bwd, "survivors_fwd": st.survivors,
                  "survivors_bwd": st.survivors_bwd, "at_warmup_end": list(pairs)},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max clock (derived)",
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak["peak"],
+                     "unit": "TFLOP/s", "frac": achieved / peak["peak"],
+                     "peak_source": peak["source"], "fp32_peak": peak,
                      "unit_of_work": "contributing (pixel, primitive) pair",
                      "flops_per_unit": FLOPS_BWD_PAIR if key == "bwd" else FLOPS_FWD_PAIR,
                      "algorithmic_flops_per_launch": flops, "kernel_ms": dms,

@@ -356,6 +356,20 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
                        int32_t *status_dev, dbmp_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
+/* FP32 issue-rate microbenchmark (measurement aid, not part of the method)    */
+/* ------------------------------------------------------------------------- */
+/* Queues one launch of n_threads / 256 blocks of 256 threads; every thread runs
+ * 16 independent multiply-add chains for iters x 8 steps, with scalar FFMA
+ * (packed = 0) or packed FP32x2 FMA instructions (packed = 1), and stores one
+ * float per thread into sink_dev (float32 [n_threads], device, caller-owned).
+ * *flops (host) receives the launch's floating-point operations (2 per
+ * multiply-add).  Time the launch with events on `stream`: flops / seconds is the
+ * FP32 rate the compositors' ALU roofline is measured against.  n_threads must be
+ * a positive multiple of 256 and iters > 0, else DBMP_ERR_INVALID_ARG. */
+int32_t dbmp_fp32_peak(int32_t packed, int32_t iters, float *sink_dev, int64_t n_threads, double *flops,
+                       dbmp_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
 /* Learned proposal network                                                   */
 /* ------------------------------------------------------------------------- */
 /* A small CNN that maps a target image to initial parameters of 512 primitives,
@@ -473,6 +487,11 @@ int32_t dbmp_structure_reinit(const float *image_dev, const float *mask_dev, int
                               double s_min, double s_max, double sigma_c, double nu, double threshold,
                               void *scratch_dev, float *params_dev, float *adam_m_dev, float *adam_v_dev,
                               int32_t *count_dev, dbmp_stream_t stream);
+
+/* The rendered alpha channel (Sec. 3.3.2): alpha_dev[p] = 1 - T_final_dev[p] for
+ * p < n_pix, from the T_final map of dbmp_render_fwd (float32, device; the two
+ * buffers may be the same).  n_pix >= 0.  Stream-ordered. */
+int32_t dbmp_render_alpha(const float *T_final_dev, float *alpha_dev, int64_t n_pix, dbmp_stream_t stream);
 
 /* Spatially constrained loss (Eq. 9, Sec. 3.3.2), both squared norms read as means:
  *   L = sum_p [a*_p > 0] |I_p - I*_p|^2 / (3 n) + lambda_alpha sum_p (I_alpha,p - a*_p)^2 / n

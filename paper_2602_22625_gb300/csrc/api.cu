@@ -825,6 +825,13 @@ int32_t dbmp_structure_reinit(const float *image_dev, const float *mask_dev, int
     return DBMP_OK;
 }
 
+int32_t dbmp_render_alpha(const float *T_final_dev, float *alpha_dev, int64_t n_pix, dbmp_stream_t stream) {
+    if (n_pix < 0) return fail(DBMP_ERR_INVALID_ARG, "n_pix must be >= 0");
+    if (n_pix > 0 && (!T_final_dev || !alpha_dev)) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    DBMP_CUDA(launch_alpha_from_T(T_final_dev, alpha_dev, n_pix, (cudaStream_t)stream), "alpha launch");
+    return DBMP_OK;
+}
+
 int32_t dbmp_alpha_loss_grad(const float *image_dev, const float *T_final_dev, const float *target_dev,
                              const float *target_alpha_dev, int64_t n_pix, float lambda_alpha, float *dL_dimage_dev,
                              float *dL_dalpha_dev, double *loss_dev, dbmp_stream_t stream) {

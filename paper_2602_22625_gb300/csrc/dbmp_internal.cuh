@@ -279,6 +279,8 @@ cudaError_t launch_structure_init(const float *image, const float *mask, int32_t
                                   double s_max, double sigma_c, double nu, void *scratch, float *params,
                                   double *nlv_out, double reinit_thr, float *adam_m, float *adam_v,
                                   int32_t *count, cudaStream_t st);
+// I_alpha = 1 - T_final (optim.cu).
+cudaError_t launch_alpha_from_T(const float *T_final, float *alpha, int64_t n, cudaStream_t st);
 // Spatially constrained loss, Eq. 9 (optim.cu).
 cudaError_t launch_alpha_loss(const float *image, const float *T_final, const float *target,
                               const float *target_alpha, int64_t n_pix, float lam, float *dL_dimage,

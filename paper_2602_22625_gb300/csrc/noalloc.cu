@@ -88,12 +88,13 @@ int32_t scratch_for_current_device(unsigned char **out) {
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p)
             return fail_static(DBMP_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        // The binning kernels need at most 8 B x 1024 tiles of dynamic shared memory
-        // here, under the default limit, so only the compositors' set-up is needed.
-        e = init_render_kernels();
-        if (e != cudaSuccess) return fail_static(DBMP_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e));
         g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
     }
+    // The binning kernels need at most 8 B x 1024 tiles of dynamic shared memory
+    // here, under the default limit, so only the compositors' set-up (once per
+    // device, inside init_render_kernels) is needed.
+    e = init_render_kernels();
+    if (e != cudaSuccess) return fail_static(DBMP_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e));
     *out = g_scratch_ptr[dev];
     return DBMP_OK;
 }

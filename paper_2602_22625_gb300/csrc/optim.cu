@@ -107,6 +107,12 @@ __global__ void k_mse(const float *__restrict__ I, const float *__restrict__ Tg,
 //   L = sum m_p (I - I*)^2 / n3 + lam sum (I_alpha - alpha*)^2 / n1,  I_alpha = 1 - T_N,
 //   dL/dI = 2 m_p (I - I*) / n3,  dL/dI_alpha = 2 lam (I_alpha - alpha*) / n1.
 // Per-thread sums are compensated (acc_sq), cross-thread sums FP64.
+// The rendered alpha channel I_alpha = 1 - T_N (Sec. 3.3.2) from the forward's T_final.
+__global__ void k_alpha_from_T(const float *__restrict__ T, float *__restrict__ alpha, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        alpha[i] = 1.0f - T[i];
+}
+
 __global__ void k_alpha_loss(const float *__restrict__ I, const float *__restrict__ T, const float *__restrict__ It,
                              const float *__restrict__ at, int64_t n1, float lam, float *__restrict__ dI,
                              float *__restrict__ dA, double *loss) {
@@ -270,6 +276,11 @@ cudaError_t launch_mse_grad(const float *image, const float *target, int64_t n, 
     // four resident blocks per SM: enough loads in flight for HBM with two float4
     // pairs per thread, and half the FP64 atomics of a full grid
     if (n > 0) k_mse<<<grid_for((n + 3) / 4, 256, 4), 256, 0, st>>>(image, target, n, dL, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_from_T(const float *T_final, float *alpha, int64_t n, cudaStream_t st) {
+    if (n > 0) k_alpha_from_T<<<grid_for(n, 256), 256, 0, st>>>(T_final, alpha, n);
     return cudaGetLastError();
 }
 

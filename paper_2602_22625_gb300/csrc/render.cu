@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "dbmp_internal.cuh"
 
 namespace dbmp {
@@ -725,35 +727,54 @@ __global__ void k_finalize(const float *__restrict__ params, const PrimRec *__re
     o[7] += S[7] * r.cb * (1.0f - r.cb);
 }
 
-// Resident CTAs per SM of each instantiation, queried once (init_render_kernels)
-// so that launches inside a CUDA-graph capture make no occupancy queries.
-int g_sms = 0;
+// Resident CTAs per SM of each instantiation and the SM count, queried once per
+// device (init_render_kernels, with that device current) so that launches inside a
+// CUDA-graph capture make no occupancy queries.  Each device's table is filled
+// under its own std::call_once, so concurrent first callers do not race.
+constexpr int kMaxDevices = 64;
+constexpr int kMaxOcc = 64;
 struct OccEntry {
     const void *fn;
     int per_sm;
 };
-OccEntry g_occ[64];
-int g_n_occ = 0;
+struct DeviceKernels {
+    int sms;
+    int n_occ;
+    OccEntry occ[kMaxOcc];
+    cudaError_t err;
+};
+DeviceKernels g_dk[kMaxDevices];
+std::once_flag g_dk_once[kMaxDevices];
 
-int resident_ctas(const void *fn) {
-    for (int i = 0; i < g_n_occ; ++i)
-        if (g_occ[i].fn == fn) return g_occ[i].per_sm;
+// The current device's table (nullptr for a device ordinal beyond the table).
+const DeviceKernels *device_kernels() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    return &g_dk[dev];
+}
+
+int resident_ctas(const DeviceKernels *dk, const void *fn) {
+    if (dk)
+        for (int i = 0; i < dk->n_occ; ++i)
+            if (dk->occ[i].fn == fn) return dk->occ[i].per_sm;
     return 1;
 }
 
 int persistent_grid(const void *kernel, int32_t n_items) {
-    const int full = (g_sms > 0 ? g_sms : 1) * resident_ctas(kernel);
+    const DeviceKernels *dk = device_kernels();
+    const int sms = dk && dk->sms > 0 ? dk->sms : 1;
+    const int full = sms * resident_ctas(dk, kernel);
     const int need = (n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     return need < full ? (need > 0 ? need : 1) : full;
 }
 
 template <int TILE, int PPT, int BATCH>
-void register_occupancy() {
+void register_occupancy(DeviceKernels &dk) {
     const void *fns[2] = {(const void *)k_fwd<TILE, PPT, BATCH>, (const void *)k_bwd<TILE, PPT, BATCH>};
     for (const void *fn : fns) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * kWarpsPerBlock, 0);
-        if (g_n_occ < 64) g_occ[g_n_occ++] = OccEntry{fn, per > 0 ? per : 1};
+        if (dk.n_occ < kMaxOcc) dk.occ[dk.n_occ++] = OccEntry{fn, per > 0 ? per : 1};
     }
 }
 
@@ -786,18 +807,24 @@ cudaError_t dispatch(const RenderArgs &a, const RenderCfg &cfg, bool fwd, cudaSt
 }  // namespace
 
 cudaError_t init_render_kernels() {
-    if (g_sms > 0) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    register_occupancy<8, 1, 32>(); register_occupancy<8, 2, 32>();
-    register_occupancy<8, 1, 64>(); register_occupancy<8, 2, 64>();
-    register_occupancy<16, 1, 32>(); register_occupancy<16, 2, 32>(); register_occupancy<16, 4, 32>();
-    register_occupancy<16, 1, 64>(); register_occupancy<16, 2, 64>(); register_occupancy<16, 4, 64>();
-    register_occupancy<32, 1, 32>(); register_occupancy<32, 2, 32>(); register_occupancy<32, 4, 32>();
-    register_occupancy<32, 1, 64>(); register_occupancy<32, 2, 64>(); register_occupancy<32, 4, 64>();
-    return cudaGetLastError();
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(g_dk_once[dev], [dev]() {
+        DeviceKernels &dk = g_dk[dev];
+        dk.n_occ = 0;
+        dk.err = cudaDeviceGetAttribute(&dk.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (dk.err != cudaSuccess) return;
+        register_occupancy<8, 1, 32>(dk); register_occupancy<8, 2, 32>(dk);
+        register_occupancy<8, 1, 64>(dk); register_occupancy<8, 2, 64>(dk);
+        register_occupancy<16, 1, 32>(dk); register_occupancy<16, 2, 32>(dk); register_occupancy<16, 4, 32>(dk);
+        register_occupancy<16, 1, 64>(dk); register_occupancy<16, 2, 64>(dk); register_occupancy<16, 4, 64>(dk);
+        register_occupancy<32, 1, 32>(dk); register_occupancy<32, 2, 32>(dk); register_occupancy<32, 4, 32>(dk);
+        register_occupancy<32, 1, 64>(dk); register_occupancy<32, 2, 64>(dk); register_occupancy<32, 4, 64>(dk);
+        dk.err = cudaGetLastError();
+    });
+    return g_dk[dev].err;
 }
 
 bool render_cfg_supported(const RenderCfg &cfg) {

@@ -35,7 +35,7 @@ EXPORTS = (
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
     "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
-    "dbmp_workspace_poison", "dbmp_batch_render_mse",
+    "dbmp_workspace_poison", "dbmp_batch_render_mse", "dbmp_fp32_peak", "dbmp_render_alpha",
 )
 
 
@@ -133,6 +133,8 @@ def load(build_if_missing: bool = True):
         "dbmp_autotune": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32, _i32,
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
+        "dbmp_render_alpha": (_i32, [_vp, _vp, _i64, _vp]),
+        "dbmp_fp32_peak": (_i32, [_i32, _i32, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
         "dbmp_gemm_bf16": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _i32,
                                   _vp, _vp]),
         "dbmp_proposer_num_params": (_i64, []),
@@ -356,6 +358,15 @@ def dbmp_gemm_bf16(A, B, M, N, K, mode, Cf=None, Cb=None, ldc=None, bias=None, s
                                  N if ldc is None else ldc, _ptr(bias), split_k, _ptr(status), _stream(stream)))
 
 
+def dbmp_fp32_peak(packed, iters, sink, stream=None):
+    """Queues the FP32 issue-rate microbenchmark (one float per thread of `sink`);
+    returns the launch's floating-point operations."""
+    fl = ctypes.c_double()
+    _check(load().dbmp_fp32_peak(int(packed), int(iters), _ptr(sink), sink.numel(), ctypes.byref(fl),
+                                 _stream(stream)))
+    return fl.value
+
+
 def dbmp_proposer_num_params():
     return int(load().dbmp_proposer_num_params())
 
@@ -426,6 +437,14 @@ def dbmp_structure_reinit(image, u_pos, u_theta, n_color, s_min, s_max, sigma_c,
                                         _ptr(n_color), float(s_min), float(s_max), float(sigma_c), float(nu),
                                         float(threshold), _ptr(scratch), _ptr(params), _ptr(adam_m), _ptr(adam_v),
                                         _ptr(count), _stream(stream)))
+
+
+def dbmp_render_alpha(T_final, alpha, stream=None):
+    """alpha = 1 - T_final (the rendered alpha channel), in the library."""
+    if T_final.numel() != alpha.numel():
+        raise ValueError("T_final and alpha differ in size")
+    _check(load().dbmp_render_alpha(_ptr(T_final), _ptr(alpha), T_final.numel(), _stream(stream)))
+    return alpha
 
 
 def dbmp_alpha_loss_grad(image, T_final, target, target_alpha, lambda_alpha, dL_dimage, dL_dalpha, loss,

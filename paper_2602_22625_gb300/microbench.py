@@ -2,6 +2,7 @@
 
     python -m paper_2602_22625_gb300.microbench gemm 4096     # bf16 GEMM M = N = K = 4096
     python -m paper_2602_22625_gb300.microbench cnn 64        # proposal-network training steps
+    python -m paper_2602_22625_gb300.microbench fp32 20000    # FP32 multiply-add issue rate
 
 Each runs a few warm-up launches, then times repetitions with CUDA events and prints
 one line of JSON (the GEMM also times torch.matmul on the same operands)."""
@@ -57,6 +58,25 @@ def cnn(batch, reps=10):
     return {"cnn_train_batch": batch, "ms": ms, "tflops": proposer.cnn_train_flops(batch) / ms / 1e9}
 
 
+def fp32(iters=20000, reps=20, blocks_per_sm=8):
+    """FP32 multiply-add rate of the whole GPU with scalar FFMA and with packed FP32x2
+    FMA instructions (dbmp_fp32_peak): 8 blocks of 256 threads per SM, 16 independent
+    chains per thread, timed over `reps` launches with CUDA events.  Returns TFLOP/s
+    (2 per multiply-add) of each form and the SM count."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(sms * blocks_per_sm * 256, device="cuda")
+    out = {"sms": sms, "threads": sink.numel(), "iters": iters, "reps": reps}
+    for packed, name in ((0, "ffma"), (1, "ffma2")):
+        fl = D.dbmp_fp32_peak(packed, iters, sink)
+        for _ in range(3):
+            D.dbmp_fp32_peak(packed, iters, sink)
+        ms = _time(lambda: D.dbmp_fp32_peak(packed, iters, sink), reps)
+        out[f"{name}_ms"] = ms
+        out[f"{name}_tflops"] = fl / (ms * 1e-3) / 1e12
+    return out
+
+
 if __name__ == "__main__":
     what, size = sys.argv[1], int(sys.argv[2])
-    print(json.dumps(gemm(size) if what == "gemm" else cnn(size)))
+    fn = {"gemm": gemm, "cnn": cnn, "fp32": fp32}[what]
+    print(json.dumps(fn(size)))

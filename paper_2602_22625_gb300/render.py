@@ -62,13 +62,15 @@ class Renderer:
 
     background: None (Eq. 5), an RGB triple, or a (3, H, W) CUDA tensor (Eq. 8).
     T_stop: early-termination threshold (image error <= T_stop; 0 = exact).
-    check: poll the device status after every binning (one synchronisation) and grow
-    the tile-list capacity when it overflowed; with check=False a capacity overflow
-    is only reported by status().
+    check: False (default) queues work only, so forward and backward never
+    synchronise the host and can be captured in a CUDA graph; a tile-list capacity
+    overflow then leaves the outputs unwritten and is reported by status().  True:
+    poll the device status after every binning (one synchronisation) and grow the
+    tile-list capacity when it overflowed.
     """
 
     def __init__(self, H, W, atlas: Atlas, max_prims, tile=16, alpha_max=1.0,
-                 background=(1.0, 1.0, 1.0), T_stop=1e-6, max_pairs=None, check=True):
+                 background=(1.0, 1.0, 1.0), T_stop=1e-6, max_pairs=None, check=False):
         self.H, self.W, self.tile = int(H), int(W), int(tile)
         self.atlas = atlas
         self.alpha_max = float(alpha_max)
@@ -147,7 +149,7 @@ class RenderFunction(torch.autograd.Function):
         ctx.renderer = renderer
         ctx.gen = renderer.generation
         ctx.save_for_backward(params.detach(), bitmap_id, T_final, n_last)
-        alpha = 1.0 - T_final
+        alpha = D.dbmp_render_alpha(T_final, torch.empty_like(T_final))
         return image, alpha
 
     @staticmethod

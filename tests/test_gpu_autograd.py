@@ -91,7 +91,8 @@ def test_stress_workload_dense_tiles_and_localized_fd(stress):
     changes no other pixel)."""
     cuda()
     sc = stress
-    r = Renderer(sc.H, sc.W, Atlas(to_dev(sc.atlas)), sc.N, tile=32, background=sc.background, T_stop=1e-6)
+    r = Renderer(sc.H, sc.W, Atlas(to_dev(sc.atlas)), sc.N, tile=32, background=sc.background, T_stop=1e-6,
+                 check=True)
     p = to_dev(sc.params).requires_grad_(True)
     bid = to_dev(sc.bitmap_id)
     rng = np.random.default_rng(6)

@@ -17,7 +17,7 @@ IMG_TOL = 1e-5
 def gpu_bin(sc, tile):
     dev = cuda()
     atlas = Atlas(to_dev(sc.atlas))
-    r = Renderer(sc.H, sc.W, atlas, max(sc.N, 1), tile=tile, background=sc.background)
+    r = Renderer(sc.H, sc.W, atlas, max(sc.N, 1), tile=tile, background=sc.background, check=True)
     p = to_dev(sc.params)
     b = to_dev(sc.bitmap_id)
     r.bin(p, b)
@@ -101,7 +101,7 @@ def gpu_forward(sc, tile=16, T_stop=0.0, background="scene", alpha_max=1.0):
     if isinstance(bg, np.ndarray) and bg.size > 3:
         bg = to_dev(bg.astype(np.float32))
     r = Renderer(sc.H, sc.W, atlas, max(sc.N, 1), tile=tile, background=bg, T_stop=T_stop,
-                 alpha_max=alpha_max)
+                 alpha_max=alpha_max, check=True)
     p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
     img, T, nl = r.forward(p, b)
     st = r.status()
