@@ -333,6 +333,47 @@ void oracle_grad_rows(int32_t H, int32_t W, int32_t N, const float *params,
     free(P);
 }
 
+/* The same sum over an explicit set of pixels (px[i], py[i]), i < n (each pixel
+ * counted as often as it is listed): the gradient of a loss that only those pixels
+ * carry, for every primitive at once.  Used for parity on one dense tile of a
+ * canvas too large for oracle_grad.  dL_dimage / dL_dalpha are full-canvas maps. */
+void oracle_grad_pixels(int32_t H, int32_t W, int32_t N, const float *params,
+                        const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
+                        int32_t Wb, double alpha_max, int32_t bg_mode, const double *bg_rgb,
+                        const float *bg_buf, double T_stop, const double *dL_dimage,
+                        const double *dL_dalpha, int64_t n, const int32_t *px, const int32_t *py,
+                        double *dparams) {
+    (void)n_bmp;
+    orc_prim *P = make_prims(N, params, bitmap_id, atlas, Hb, Wb, alpha_max);
+    size_t HW = (size_t)H * (size_t)W;
+    memset(dparams, 0, sizeof(double) * 8 * (size_t)N);
+#pragma omp parallel
+    {
+        double *Gloc = (double *)calloc(8 * (size_t)(N > 0 ? N : 1), sizeof(double));
+        orc_layer *Ls = (orc_layer *)malloc(sizeof(orc_layer) * (size_t)(N > 0 ? N : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            if (px[i] < 0 || px[i] >= W || py[i] < 0 || py[i] >= H) continue;
+            size_t pix = (size_t)py[i] * (size_t)W + (size_t)px[i];
+            double C[3], T, g[3], b[3];
+            int32_t last;
+            int64_t pr = 0;
+            int nl = walk_pixel(P, N, Hb, Wb, (double)px[i], (double)py[i], T_stop, Ls, C, &T, &last, &pr);
+            for (int j = 0; j < 3; ++j) {
+                g[j] = dL_dimage[(size_t)j * HW + pix];
+                b[j] = bg_value(bg_mode, bg_rgb, bg_buf, j, pix, HW);
+            }
+            double gA = dL_dalpha ? dL_dalpha[pix] : 0.0;
+            pixel_grad(P, Hb, Wb, Ls, nl, g, gA, b, Gloc, -1);
+        }
+#pragma omp critical
+        for (size_t t = 0; t < 8 * (size_t)N; ++t) dparams[t] += Gloc[t];
+        free(Gloc);
+        free(Ls);
+    }
+    free(P);
+}
+
 /* Gradient of selected primitives only: for each sel[t], sums the per-pixel
  * contributions over the pixels of its support box (all other pixels contribute
  * exactly zero).  Used for sampled parity on canvases too large for oracle_grad.

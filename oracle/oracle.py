@@ -48,6 +48,12 @@ def lib():
                                        ctypes.c_double, ctypes.c_int32, _f64p, _f32p,
                                        ctypes.c_double, _f64p, _f64p, ctypes.c_int32,
                                        ctypes.c_int32, _f64p]
+        L.oracle_grad_pixels.restype = None
+        L.oracle_grad_pixels.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p, _i32p,
+                                         _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.c_int32, _f64p, _f32p,
+                                         ctypes.c_double, _f64p, _f64p, ctypes.c_int64, _i32p, _i32p,
+                                         _f64p]
         L.oracle_grad_selected.restype = None
         L.oracle_grad_selected.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f32p,
                                            _i32p, _f32p, ctypes.c_int32, ctypes.c_int32,
@@ -178,6 +184,24 @@ def grad_rows(H, W, params, bitmap_id, atlas, dL_dimage, y0, y1, dL_dalpha=None,
                            atlas.shape[0], atlas.shape[1], atlas.shape[2], float(alpha_max), mode,
                            _p(rgb, _f64p), _p(buf, _f32p), float(T_stop), _p(gI, _f64p),
                            _p(gA, _f64p), int(y0), int(y1), _p(out, _f64p))
+    return out
+
+
+def grad_pixels(H, W, params, bitmap_id, atlas, dL_dimage, pixels, dL_dalpha=None, alpha_max=1.0,
+                background=(1.0, 1.0, 1.0), T_stop=0.0):
+    """dL/dparams (N, 8) summed over the pixels (px, py) only (int arrays)."""
+    params, bitmap_id, atlas = _prep(params, bitmap_id, atlas)
+    mode, rgb, buf = _bg(background, H, W)
+    N = params.shape[0]
+    gI = np.ascontiguousarray(dL_dimage, dtype=np.float64).reshape(3, H, W)
+    gA = None if dL_dalpha is None else np.ascontiguousarray(dL_dalpha, np.float64).reshape(H, W)
+    px = np.ascontiguousarray(pixels[0], dtype=np.int32)
+    py = np.ascontiguousarray(pixels[1], dtype=np.int32)
+    out = np.zeros((N, 8), np.float64)
+    lib().oracle_grad_pixels(H, W, N, _p(params, _f32p), _p(bitmap_id, _i32p), _p(atlas, _f32p),
+                             atlas.shape[0], atlas.shape[1], atlas.shape[2], float(alpha_max), mode,
+                             _p(rgb, _f64p), _p(buf, _f32p), float(T_stop), _p(gI, _f64p), _p(gA, _f64p),
+                             px.shape[0], _p(px, _i32p), _p(py, _i32p), _p(out, _f64p))
     return out
 
 

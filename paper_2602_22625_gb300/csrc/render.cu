@@ -111,8 +111,9 @@ __device__ __forceinline__ bool region_hits(const PrimRec &r, const AtlasView &a
     const int v0 = (int)fmaxf(fv0, 0.0f), v1 = (int)fminf(fv1, Hm);
     const int Ws = at.Wb + 1;
     const int32_t *S = at.sat + r.bmp_row * Ws;
-    const int32_t n = __ldg(S + (v1 + 1) * Ws + u1 + 1) - __ldg(S + v0 * Ws + u1 + 1) -
-                      __ldg(S + (v1 + 1) * Ws + u0) + __ldg(S + v0 * Ws + u0);
+    // L2-only loads: a region's four corners are rarely read again from this SM
+    const int32_t n = __ldcg(S + (v1 + 1) * Ws + u1 + 1) - __ldcg(S + v0 * Ws + u1 + 1) -
+                      __ldcg(S + (v1 + 1) * Ws + u0) + __ldcg(S + v0 * Ws + u0);
     return n > 0;
 }
 
@@ -774,6 +775,14 @@ void register_occupancy(DeviceKernels &dk) {
     for (const void *fn : fns) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * kWarpsPerBlock, 0);
+        // the smallest shared-memory carve-out that keeps this occupancy, leaving the
+        // rest of the SM's on-chip memory to L1 (the texel gathers' cache)
+        for (int pct = 0; pct <= 100; pct += 2) {
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            int p2 = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, fn, 32 * kWarpsPerBlock, 0);
+            if (p2 >= per) break;
+        }
         if (dk.n_occ < kMaxOcc) dk.occ[dk.n_occ++] = OccEntry{fn, per > 0 ? per : 1};
     }
 }

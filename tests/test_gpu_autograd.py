@@ -151,6 +151,52 @@ def test_stress_workload_dense_tiles_and_localized_fd(stress):
     assert np.median(errs) < 1e-3 and errs.max() < 0.5, errs
 
 
+def test_stress_workload_gradients_along_the_longest_list(stress):
+    """The reverse walk of the stress canvas' densest 32 x 32 tile (more than 5 000
+    listed primitives) in exact mode (T_stop = 0): every pixel composites until its
+    transmittance falls below the 2^-100 floor, so the backward recovers
+    T_k = T_{k+1} / (1 - alpha_k) (Eq. 6, Eqs. S4-S5) through thousands of divisions.
+    With the upstream gradient random over that tile only, the gradient of every
+    primitive is compared with the oracle's FP64 gradient over the tile's pixels:
+    group-wise, and each primitive that carries gradient above 1e-20 (clear of the
+    floor) on its own scale, at whatever list position it sits."""
+    cuda()
+    sc = stress
+    r = Renderer(sc.H, sc.W, Atlas(to_dev(sc.atlas)), sc.N, tile=32, background=sc.background, T_stop=0.0,
+                 check=True)
+    p = to_dev(sc.params).requires_grad_(True)
+    bid = to_dev(sc.bitmap_id)
+    r.bin(p.detach(), bid)
+    K = r.status().pairs_required
+    ntx = sc.W // 32
+    offs = torch.empty(ntx * (sc.H // 32) + 1, dtype=torch.int64, device="cuda")
+    lst = torch.empty(K, dtype=torch.int32, device="cuda")
+    D.dbmp_get_tile_lists(r.ws.handle, offs, lst)
+    o = offs.cpu().numpy()
+    t = int(np.argmax(np.diff(o)))
+    tile_list = lst.cpu().numpy()[o[t]:o[t + 1]]
+    assert len(tile_list) > 5000
+    tx, ty = (t % ntx) * 32, (t // ntx) * 32
+    wI = np.zeros((3, sc.H, sc.W), np.float32)
+    wI[:, ty:ty + 32, tx:tx + 32] = np.random.default_rng(8).normal(size=(3, 32, 32))
+    img, _ = render(p, bid, r)
+    (img * to_dev(wI)).sum().backward()
+    assert r.status().code == 0
+    g = p.grad.cpu().numpy().astype(np.float64)
+    ys, xs = np.mgrid[ty:ty + 32, tx:tx + 32]
+    ref = oracle.grad_pixels(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, wI, (xs.ravel(), ys.ravel()),
+                             background=sc.background, T_stop=0.0)
+    # only the tile's primitives carry gradient
+    others = np.setdiff1d(np.arange(sc.N), tile_list)
+    assert not ref[others].any() and not g[others].any()
+    grad_close(g[tile_list], ref[tile_list], what="densest tile, exact mode")
+    mag = np.abs(ref[tile_list]).max(axis=1)
+    live = np.nonzero(mag > 1e-20)[0]
+    assert len(live) >= 100 and live.max() > 1000, (len(live), live.max(initial=-1))
+    err = np.abs(g[tile_list[live]] - ref[tile_list[live]]).max(axis=1) / mag[live]
+    assert err.max() <= 2e-3, (live[np.argmax(err)], err.max())
+
+
 def test_stress_workload_64_random_tiles_match_oracle(stress):
     """The 2048^2 x 200k stress canvas (lists above 5 000 primitives) in the launch
     configuration the benchmark times (tile 32, batch 32, 4 px/lane, T_stop 1e-6):

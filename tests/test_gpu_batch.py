@@ -398,8 +398,9 @@ def test_poisoned_single_canvas_workspace_matches_oracle():
 def test_gpu_optimisation_resumes_from_a_checkpoint(tmp_path):
     """Six optimisation steps in one go against three, a checkpoint (parameters, Adam
     moments, step counter) written and read back into fresh device buffers, and three
-    more.  The file is exact; the gradients' float atomics sum in any order, so the two
-    runs agree to rounding, not bit for bit."""
+    more.  The file is exact; the gradients' float atomics sum in any order, so the
+    resumed run agrees with the uninterrupted one as closely as two uninterrupted runs
+    agree with each other, not bit for bit."""
     from paper_2602_22625_gb300 import checkpoint
     cuda()
     sc = inputs.tiny(seed=9, N=60, H=64, W=64)
@@ -436,6 +437,9 @@ def test_gpu_optimisation_resumes_from_a_checkpoint(tmp_path):
         steps(p, m, v, step, 6)
         ref = p.cpu().numpy()
         p, m, v, step = fresh()
+        steps(p, m, v, step, 6)
+        noise = np.abs(p.cpu().numpy() - ref).max()   # two uninterrupted runs (atomics' order)
+        p, m, v, step = fresh()
         steps(p, m, v, step, 3)
         ck = tmp_path / "gpu.ckpt"
         checkpoint.save(ck, {"params": p, "m": m, "v": v, "step": step}, step=int(step.item()))
@@ -445,7 +449,13 @@ def test_gpu_optimisation_resumes_from_a_checkpoint(tmp_path):
         steps(p2, m2, v2, step2, 3)
         assert int(step2.item()) == 6
         got = p2.cpu().numpy()
-        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+        # Adam divides by sqrt(v), so on parameters with near-zero gradients the
+        # atomics' rounding can move a step by a visible amount; a broken resume
+        # (moments, step or parameters not restored) moves every parameter by about
+        # the learning rate instead
+        d = np.abs(got - ref)
+        assert d.max() <= max(20 * noise, 1e-3 * np.abs(ref).max()), (d.max(), noise)
+        assert d.mean() <= 1e-3, d.mean()
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)
@@ -504,7 +514,9 @@ def test_batched_64_canvases_in_the_benchmarked_configuration():
     canvas, 1.03 M in all), planned at tile 32, batch 32, 4 px/lane, T_stop 1e-6, in one
     binning, one forward and one backward launch.  Four canvases (the cheapest two, the
     median and the largest) against the oracle: every pixel and T, and the gradients of
-    primitives sampled from each canvas' front quarter under a random upstream gradient."""
+    primitives sampled from each canvas' front quarter and from its back half under a
+    random upstream gradient (together, and the back half on its own scale wherever its
+    reference is not negligible)."""
     cuda()
     scenes = inputs.batched(seed=4)
     atlas_np = scenes[0].atlas
@@ -539,7 +551,15 @@ def test_batched_64_canvases_in_the_benchmarked_configuration():
         assert np.abs(got - ref["image"]).max() <= IMG_TOL, f"canvas {c}"
         assert np.abs(Tf[pix[c]: pix[c + 1]].reshape(s.H, s.W) - ref["T_final"]).max() <= IMG_TOL
         gIc = gI[3 * pix[c]: 3 * pix[c + 1]].reshape(3, s.H, s.W)
-        sel = np.sort(rng.choice(max(4, s.N // 4), 4, replace=False))   # front quarter: visible layers
+        front = rng.choice(max(4, s.N // 4), 4, replace=False)            # front quarter: visible layers
+        back = s.N // 2 + rng.choice(s.N - s.N // 2, 4, replace=False)    # back half: deep in the lists
+        sel = np.sort(np.concatenate([front, back]))
         gref = oracle.grad_selected(s.H, s.W, s.params, s.bitmap_id, atlas_np, gIc, sel,
                                     background=(1.0, 1.0, 1.0), T_stop=1e-6)
         grad_close(g[off[c] + sel], gref, what=f"canvas {c}")
+        isb = sel >= s.N // 2
+        gb, rb = g[off[c] + sel[isb]], gref[isb]
+        scale = np.abs(gref).max(axis=0)
+        for j in range(8):   # back rows on their own scale, where they carry gradient
+            if np.abs(rb[:, j]).max() > 1e-3 * scale[j]:
+                assert np.abs(gb[:, j] - rb[:, j]).max() <= 1e-2 * np.abs(rb[:, j]).max(), (c, j)

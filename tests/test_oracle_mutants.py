@@ -38,6 +38,8 @@ MUTANTS = {
     "grad_selected_box_row_dropped": ("y1 = (long)ceil(q->yhi);", "y1 = (long)floor(q->yhi) - 1;"),
     "grad_selected_row_index": ("pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, sel[t]);",
                                 "pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, t);"),
+    "grad_pixels_index_transposed": ("size_t pix = (size_t)py[i] * (size_t)W + (size_t)px[i];",
+                                     "size_t pix = (size_t)px[i] * (size_t)W + (size_t)py[i];"),
     "mask_ignored": ("Q[p + 1] = Q[p] + (mask && !(mask[p] > 0.0f) ? 0 : (int64_t)floor(w * 1048576.0));",
                      "Q[p + 1] = Q[p] + (int64_t)floor(w * 1048576.0);"),
 }

@@ -529,3 +529,28 @@ def test_grad_selected_equals_the_rows_of_the_full_gradient(bg, T_stop):
             assert np.abs(full[i]).max() > 1e-6 * scale, i
         # invalid primitives: zero rows on both sides
         assert not full[17].any() and not full[18].any()
+
+
+def test_grad_pixels_equals_rows_and_masked_full_gradients():
+    """The gradient restricted to a pixel set equals grad_rows for whole rows, and
+    the full gradient (Eq. 6, Eqs. S4-S5) of the upstream gradient masked to the set
+    for a scattered set; a listed pixel counts once per listing."""
+    H, W, params, bid, atlas = _edge_scene(9)
+    rng = np.random.default_rng(12)
+    gI = rng.normal(size=(3, H, W))
+    gA = rng.normal(size=(H, W))
+    for T_stop in (0.0, 1e-6):
+        ys, xs = np.mgrid[5:17, 0:W]
+        a = oracle.grad_pixels(H, W, params, bid, atlas, gI, (xs.ravel(), ys.ravel()), dL_dalpha=gA,
+                               alpha_max=0.8, T_stop=T_stop)
+        b = oracle.grad_rows(H, W, params, bid, atlas, gI, 5, 17, dL_dalpha=gA, alpha_max=0.8, T_stop=T_stop)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * np.abs(b).max())
+        mask = rng.uniform(size=(H, W)) < 0.3
+        py, px = np.nonzero(mask)
+        c = oracle.grad_pixels(H, W, params, bid, atlas, gI, (px, py), dL_dalpha=gA, alpha_max=0.8,
+                               T_stop=T_stop)
+        d = oracle.grad(H, W, params, bid, atlas, gI * mask, dL_dalpha=gA * mask, alpha_max=0.8, T_stop=T_stop)
+        np.testing.assert_allclose(c, d, rtol=0, atol=1e-12 * np.abs(d).max())
+    twice = oracle.grad_pixels(H, W, params, bid, atlas, gI, (np.r_[px, px], np.r_[py, py]))
+    once = oracle.grad_pixels(H, W, params, bid, atlas, gI, (px, py))
+    np.testing.assert_allclose(twice, 2 * once, rtol=1e-13, atol=1e-300)
