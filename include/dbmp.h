@@ -408,6 +408,14 @@ int32_t dbmp_proposer_set_params(DbmpProposer *p, const float *host, int64_t n);
 /* Downloads the parameters (which = 0) or the last gradient (which = 1);
  * synchronises the device; DBMP_ERR_TIMEOUT if a tensor-core wait gave up. */
 int32_t dbmp_proposer_get(DbmpProposer *p, int32_t which, float *host, int64_t n);
+/* Testing aid: downloads the activations the last forward (dbmp_propose or
+ * dbmp_proposer_train_step) left on the device, as float32 in host memory:
+ * layer 0 = the packed bf16 input (B x 256 x 256 x 8, NHWC), 1..5 = the bf16
+ * post-ReLU outputs of the five convolutions (B x S x S x C, S = 128, 64, 32, 16, 8,
+ * C = 32, 64, 128, 256, 256), 6 = the head's float32 outputs (B*64 x 64).  n must
+ * be that count for the last forward's batch, else DBMP_ERR_INVALID_ARG;
+ * DBMP_ERR_NOT_READY before the first forward.  Synchronises the device. */
+int32_t dbmp_proposer_activations(DbmpProposer *p, int32_t layer, float *host, int64_t n);
 /* Decoded proposals: params_out_dev float32 B x 512 x 8 (same layout as dbmp_bin's
  * params, primitive order as above).  Stream-ordered. */
 int32_t dbmp_propose(DbmpProposer *p, const float *images_dev, int32_t B, float *params_out_dev,

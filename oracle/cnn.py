@@ -87,20 +87,36 @@ def col2im(dcol, shape, k=4, s=2, p=1):
     return dXp[:, p:p + H, p:p + W]
 
 
-def forward(theta, images, rnd=True):
+def _mm(acc32):
+    """Matrix product with FP64 accumulation, or (acc32 = 1, 2) with the operands and
+    the accumulation in float32, the inner dimension summed forwards (1) or backwards
+    (2).  The fp32 forms are rounding-sensitivity probes, not the reference: the
+    operands are bf16 values, exact in both, so the forms differ only in how the sums
+    are rounded, and their difference shows how far a change of accumulation alone
+    moves each tensor through the bf16 rounding points."""
+    if not acc32:
+        return lambda a, b: a @ b
+    f = np.float32
+    if acc32 == 2:
+        return lambda a, b: (np.asarray(a, f)[:, ::-1] @ np.asarray(b, f)[::-1, :]).astype(np.float64)
+    return lambda a, b: (np.asarray(a, f) @ np.asarray(b, f)).astype(np.float64)
+
+
+def forward(theta, images, rnd=True, acc32=False):
     """Returns (outputs O (B*64, 64), cache for backward)."""
     params = unpack(np.asarray(theta, np.float64))
     R = bf16 if rnd else (lambda a: np.asarray(a, np.float64))
+    mm = _mm(acc32)
     X = pack_input(images, rnd)
     acts, cols = [X], []
     for (cin_pad, _, cout, k), (W, b) in zip(LAYERS[:-1], params[:-1]):
         col, (B, Ho, Wo) = im2col(X)
         cols.append(col)
-        X = R(np.maximum(col @ R(W).T + b, 0.0)).reshape(B, Ho, Wo, cout)
+        X = R(np.maximum(mm(col, R(W).T) + b, 0.0)).reshape(B, Ho, Wo, cout)
         acts.append(X)
     W6, b6 = params[-1]
-    O = X.reshape(-1, 256) @ R(W6).T + b6
-    return O, dict(params=params, acts=acts, cols=cols, rnd=rnd)
+    O = mm(X.reshape(-1, 256), R(W6).T) + b6
+    return O, dict(params=params, acts=acts, cols=cols, rnd=rnd, acc32=acc32)
 
 
 def anchor_bases():
@@ -158,18 +174,19 @@ def backward(dO, cache):
     as the GPU: dZ tensors rounded to bf16 before each product."""
     params, acts, cols, rnd = cache["params"], cache["acts"], cache["cols"], cache["rnd"]
     R = bf16 if rnd else (lambda a: np.asarray(a, np.float64))
+    mm = _mm(cache.get("acc32", False))
     grads = [None] * len(params)
     W6, _ = params[-1]
     X5 = acts[-1].reshape(-1, 256)
     dZ = R(dO)
-    grads[-1] = (dZ.T @ X5, dO.sum(0))
-    dX = (dZ @ R(W6)).reshape(acts[-1].shape)
+    grads[-1] = (mm(dZ.T, X5), dO.sum(0))
+    dX = mm(dZ, R(W6)).reshape(acts[-1].shape)
     for li in range(len(LAYERS) - 2, -1, -1):
         X = acts[li + 1]
         dZ = R(np.where(X > 0, dX, 0.0)).reshape(-1, LAYERS[li][2])
         W, _ = params[li]
-        grads[li] = (dZ.T @ cols[li], dZ.sum(0))
+        grads[li] = (mm(dZ.T, cols[li]), dZ.sum(0))
         if li > 0:
-            dcol = dZ @ R(W)
+            dcol = mm(dZ, R(W))
             dX = col2im(dcol, acts[li].shape)
     return np.concatenate([np.concatenate([g[0].ravel(), g[1]]) for g in grads])

@@ -889,6 +889,7 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
 struct DbmpProposer {
     CnnBuffers c;
     int32_t step = 0;
+    int32_t last_batch = 0;   // batch of the last forward (dbmp_propose / train step)
 };
 
 int64_t dbmp_proposer_num_params(void) { return cnn_num_params(); }
@@ -952,6 +953,18 @@ int32_t dbmp_propose(DbmpProposer *p, const float *images_dev, int32_t B, float 
     cudaStream_t st = (cudaStream_t)stream;
     DBMP_CUDA(cnn_forward(p->c, images_dev, B, st), "proposer forward");
     DBMP_CUDA(cnn_decode(p->c, B, params_out_dev, st), "proposer decode");
+    p->last_batch = B;
+    return DBMP_OK;
+}
+
+int32_t dbmp_proposer_activations(DbmpProposer *p, int32_t layer, float *host, int64_t n) {
+    if (!p || !host) return fail(DBMP_ERR_INVALID_ARG, "NULL argument");
+    if (p->last_batch < 1) return fail(DBMP_ERR_NOT_READY, "no forward of the proposer yet");
+    const int64_t want = cnn_activation_count(layer, p->last_batch);
+    if (want < 0) return fail(DBMP_ERR_INVALID_ARG, "layer %d outside 0..6", layer);
+    if (n != want) return fail(DBMP_ERR_INVALID_ARG, "expected %lld values, got %lld", (long long)want, (long long)n);
+    DBMP_CUDA(cudaDeviceSynchronize(), "sync");
+    DBMP_CUDA(cnn_activation(p->c, layer, p->last_batch, host), "download");
     return DBMP_OK;
 }
 
@@ -964,6 +977,7 @@ int32_t dbmp_proposer_train_step(DbmpProposer *p, const float *images_dev, const
         return fail(DBMP_ERR_INVALID_ARG, "bad Adam settings");
     cudaStream_t st = (cudaStream_t)stream;
     DBMP_CUDA(cnn_forward(p->c, images_dev, B, st), "proposer forward");
+    p->last_batch = B;
     DBMP_CUDA(cnn_backward(p->c, target_params_dev, B, loss_dev, st), "proposer backward");
     if (adam) {
         p->step += 1;

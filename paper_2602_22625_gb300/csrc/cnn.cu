@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "dbmp_internal.cuh"
 
@@ -407,6 +409,29 @@ cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStrea
     if (e == cudaSuccess)
         e = gemm(c.X[5], 256, c.wbf + L[5].w_off, 256, B * 64, 64, 256, GEMM_BIAS_F32, c.O, nullptr, 64,
                  c.theta + L[5].b_off, 1, c.status, st);
+    return e;
+}
+
+int64_t cnn_activation_count(int32_t layer, int32_t B) {
+    if (layer < 0 || layer > 6 || B < 1) return -1;
+    if (layer == 6) return (int64_t)B * 64 * 64;
+    return cnn_sizes(B).X[layer];
+}
+
+cudaError_t cnn_activation(const CnnBuffers &c, int32_t layer, int32_t B, float *host) {
+    const int64_t n = cnn_activation_count(layer, B);
+    if (layer == 6) return cudaMemcpy(host, c.O, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    // bf16 bits are the upper half of the float32 they round to
+    uint16_t *tmp = static_cast<uint16_t *>(malloc(sizeof(uint16_t) * (size_t)n));
+    if (!tmp) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMemcpy(tmp, c.X[layer], sizeof(uint16_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        for (int64_t i = 0; i < n; ++i) {
+            const uint32_t u = (uint32_t)tmp[i] << 16;
+            memcpy(host + i, &u, sizeof u);
+        }
+    }
+    free(tmp);
     return e;
 }
 

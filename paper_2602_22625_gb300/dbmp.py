@@ -35,7 +35,7 @@ EXPORTS = (
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
     "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
-    "dbmp_workspace_poison", "dbmp_batch_render_mse", "dbmp_fp32_peak", "dbmp_render_alpha",
+    "dbmp_workspace_poison", "dbmp_batch_render_mse", "dbmp_fp32_peak", "dbmp_render_alpha", "dbmp_proposer_activations",
 )
 
 
@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True):
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
         "dbmp_render_alpha": (_i32, [_vp, _vp, _i64, _vp]),
+        "dbmp_proposer_activations": (_i32, [_vp, _i32, _vp, _i64]),
         "dbmp_fp32_peak": (_i32, [_i32, _i32, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
         "dbmp_gemm_bf16": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _i32,
                                   _vp, _vp]),
@@ -391,6 +392,17 @@ def dbmp_proposer_get(p, which):
     import numpy as np
     out = np.empty(dbmp_proposer_num_params(), np.float32)
     _check(load().dbmp_proposer_get(p, which, out.ctypes.data, out.size))
+    return out
+
+
+def dbmp_proposer_activations(p, layer, batch):
+    """Activations of layer 0..6 of the last forward (float32 numpy array)."""
+    import numpy as np
+    sides = (256, 128, 64, 32, 16, 8)
+    chans = (8, 32, 64, 128, 256, 256)
+    shape = (batch * 64, 64) if layer == 6 else (batch, sides[layer], sides[layer], chans[layer])
+    out = np.empty(shape, np.float32)
+    _check(load().dbmp_proposer_activations(p, int(layer), out.ctypes.data, out.size))
     return out
 
 

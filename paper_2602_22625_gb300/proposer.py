@@ -67,6 +67,10 @@ class Proposer:
     def grads(self):
         return D.dbmp_proposer_get(self.handle, 1)
 
+    def activations(self, layer, batch):
+        """Layer 0..6 activations of the last forward of `batch` images (testing aid)."""
+        return D.dbmp_proposer_activations(self.handle, layer, batch)
+
     def propose(self, images):
         out = torch.empty(images.shape[0], N_PRIMS, 8, device="cuda")
         D.dbmp_propose(self.handle, images.contiguous(), out)
@@ -114,11 +118,12 @@ def time_to(psnrs, times, goal):
 
 
 def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0, 1.0, 1.0), t0=None,
-           psnr_goal=30.0, bitmap_id=None, log=None):
+           psnr_goal=30.0, bitmap_id=None, log=None, stop_at=None):
     """The plain method: Adam on all primitive parameters of one 256^2 canvas against
     target_image (3, 256, 256).  Returns (psnr per step, seconds per step since t0,
     seconds to reach psnr_goal or None, final params).  With `log` (a writable text
-    file) each step appends one JSON line {"step", "loss", "psnr", "s"}."""
+    file) each step appends one JSON line {"step", "loss", "psnr", "s"}.  With
+    `stop_at` the run ends at the first step whose PSNR reaches it."""
     params = init_params.reshape(N_PRIMS, 8).contiguous().clone()
     bid = torch.zeros(N_PRIMS, dtype=torch.int32, device="cuda") if bitmap_id is None else bitmap_id
     ws = D.dbmp_workspace_create(N_PRIMS, (SIDE // 16) ** 2, N_PRIMS * 256, 1)
@@ -148,7 +153,7 @@ def refine(init_params, target_image, atlas, steps=200, lr=0.1, background=(1.0,
                 log.write(json.dumps({"step": len(psnrs) - 1, "loss": mse, "psnr": ps, "s": times[-1]}) + "\n")
             if hit is None and ps >= psnr_goal:
                 hit = times[-1]
-            if len(psnrs) > steps:
+            if len(psnrs) > steps or (stop_at is not None and ps >= stop_at):
                 break
             D.dbmp_render_bwd(ws, atlas, bg, 1e-6, dL, None, T, nl, g)
             D.dbmp_adam_step(params, g, m, v, step, cfg)

@@ -20,12 +20,12 @@ def test_traffic_record_matches_the_current_sources():
         assert bench.traffic_for(key, 8, e["batch"], e["ppt"]) is None   # another tuning
 
 
-@pytest.mark.parametrize("changed", ["render.cu", "dbmp_internal.cuh"])
+@pytest.mark.parametrize("changed", ["render.cu", "compositor.cuh"])
 def test_traffic_record_is_dropped_when_a_profiled_source_changes(tmp_path, monkeypatch, changed):
     os.makedirs(tmp_path / "profiles")
     os.makedirs(tmp_path / CSRC)
     shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles")
-    for n in ("render.cu", "dbmp_internal.cuh"):
+    for n in ("render.cu", "compositor.cuh"):
         shutil.copy(os.path.join(bench.ROOT, CSRC, n), tmp_path / CSRC / n)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_for("bwd", 32, 32, 4) is not None

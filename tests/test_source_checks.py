@@ -80,6 +80,6 @@ def test_the_check_catches_a_missing_wait():
 
 
 def test_pdl_helpers_are_the_documented_ptx():
-    hdr = sources()["dbmp_internal.cuh"]
-    assert 'asm volatile("griddepcontrol.wait;" ::: "memory")' in hdr
-    assert "cudaLaunchAttributeProgrammaticStreamSerialization" in hdr
+    srcs = sources()
+    assert 'asm volatile("griddepcontrol.wait;" ::: "memory")' in srcs["compositor.cuh"]
+    assert "cudaLaunchAttributeProgrammaticStreamSerialization" in srcs["dbmp_internal.cuh"]
