@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--ppt", type=int, default=2)
     ap.add_argument("--ppt-bwd", type=int, default=0, help="pixels per lane of the backward (0: --ppt)")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "bands"],
+                    help="N > 1: replicas = one canvas per rank (weak scaling, no exchange); bands = one canvas "
+                         "split into bands of tile rows, the gradient summed by one all-reduce per step "
+                         "(strong scaling)")
     return ap.parse_args()
 
 
@@ -697,8 +701,10 @@ def run_dbmp(args):
     D.load()
     peak = fp32_peak(local)
 
-    # inputs: each rank renders its own workload (weak scaling: no exchange)
-    seed, tgt_seed = rank_seeds(rank)
+    # inputs: each rank renders its own workload (weak scaling: no exchange), or with
+    # --shard bands every rank holds the same canvas and renders its band of it
+    bands = args.shard == "bands" and world > 1
+    seed, tgt_seed = rank_seeds(0 if bands else rank)
     sc = inputs.main(seed=seed)
     tgt = inputs.main(seed=tgt_seed)
     atlas_t = torch.from_numpy(sc.atlas).to(dev)
@@ -746,6 +752,9 @@ def run_dbmp(args):
         tuning = {"tile": t, "batch": b, "ppt": pp, "ppt_bwd": pb, "autotuned": True,
                   "autotune_ms_bin_fwd_bwd": ms}
         dparams.zero_()
+    if bands:
+        from paper_2602_22625_gb300 import sharded
+        band = sharded.select_band(ws, H, world, rank, tuning["tile"])
     adam = D.adam_config(lr=0.1, gamma=0.1 ** (1.0 / 500), zero_grad=True)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
@@ -765,6 +774,8 @@ def run_dbmp(args):
             ev[3].record(stream)
         D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BWD, image, T_final, n_last,
                             dL, dparams)
+        if bands:   # the step's one exchange: the bands' gradients summed
+            sharded.sum_gradient_(dparams, world)
         if ev:
             ev[4].record(stream)
         D.dbmp_adam_step(params, dparams, m, v, step, adam)
@@ -798,6 +809,8 @@ def run_dbmp(args):
     # ---- the same step captured once as a CUDA graph and replayed ----
     graph_ms = None
     try:
+        if bands:   # no capture of the NCCL exchange
+            raise RuntimeError("the banded step's all-reduce is not captured")
         cap = torch.cuda.Stream(device=dev)
         cap.wait_stream(stream)
         with torch.cuda.stream(cap):
@@ -882,14 +895,17 @@ def run_dbmp(args):
         return
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "strong" if bands else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config({"tile": tuning["tile"], "batch": tuning["batch"], "ppt": tuning["ppt"],
                           "ppt_bwd": tuning["ppt_bwd"],
                           "autotuned": tuning["autotuned"],
                           "autotune_ms_bin_fwd_bwd": tuning.get("autotune_ms_bin_fwd_bwd"),
                           "loss": "MSE over 3HW, fused into the forward's epilogue (fwd includes it; mse ~ 0)",
-                          "parallelism": f"replicas x{world} (one canvas per GPU, no exchange)"}),
+                          "parallelism": (f"bands x{world} (one canvas, rows {band[0]}..{band[1]} on rank 0; one sum "
+                                          f"all-reduce of the {N}x8 gradient per step)") if bands else
+                                         f"replicas x{world} (one canvas per GPU, no exchange)"}),
         "breakdown_ms": {"bin": float(phase[:, 0].mean()), "fwd": fwd_ms, "mse": float(phase[:, 2].mean()),
                          "bwd": bwd_ms, "adam": float(phase[:, 4].mean()),
                          "step_min": float(step_ms.min()), "step_max": float(step_ms.max())},

@@ -141,7 +141,39 @@ typedef struct {
     int64_t warp_steps_bwd;      /* same for the last bwd                          */
     int64_t survivors;           /* list entries that passed the region test (fwd) */
     int64_t survivors_bwd;       /* same for the last bwd                          */
+    int32_t bad_kind;            /* index-checked build only (dbmp_index_checks):
+                                    the first out-of-range index met since the last
+                                    poll, a DbmpBadIndex; the access was skipped     */
+    int32_t bad_pad;
+    int64_t bad_index;           /* which one: tile id (TILE_RANGE), list position
+                                    (LIST_ENTRY, LIST_WRITE) or primitive (BITMAP_ROW) */
 } DbmpDeviceStatus;
+
+typedef enum {
+    DBMP_BAD_NONE = 0,
+    DBMP_BAD_TILE_RANGE = 1,  /* a tile's list range outside [0, sum_t d_t]: the tile is
+                                 clipped to it (empty if it starts outside)          */
+    DBMP_BAD_LIST_ENTRY = 2,  /* a list entry that is no primitive of the plan: culled */
+    DBMP_BAD_BITMAP_ROW = 3,  /* a record whose bitmap row is not a bitmap's first row:
+                                 culled                                              */
+    DBMP_BAD_LIST_WRITE = 4   /* a binning write outside the lists: dropped          */
+} DbmpBadIndex;
+
+/* 1 if this library was built with device-side index checks (the checked build,
+ * libdbmp_checked.so: the compositors check every tile range, list entry and
+ * bitmap row they read and the binning every list position it writes, record the
+ * first bad one in the status block and skip the access), else 0.  The checks
+ * stand in for a device-assert build, whose failing assert would trap the GPU. */
+int32_t dbmp_index_checks(void);
+
+/* Testing aid for the index checks: overwrites one value of a binned workspace,
+ * stream-ordered, then synchronises `stream`.  what = 0: tile offset `index`
+ * (0..max_tiles); 1: tile-list entry `index` (0..max_pairs-1); 2: the bitmap row of
+ * primitive `index`'s record (0..max_prims-1).  Indices outside the workspace's
+ * allocations are rejected (DBMP_ERR_INVALID_ARG), so the write itself stays inside
+ * them; what a later render then reads is for the caller to keep inside them too. */
+int32_t dbmp_workspace_debug_set(DbmpWorkspace *ws, int32_t what, int64_t index, int64_t value,
+                                 dbmp_stream_t stream);
 
 /* Synchronises `stream`, copies the status block to *out, clears the sticky
  * error code and returns out->code. */
@@ -290,6 +322,19 @@ typedef struct {
 int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, const int32_t *W,
                         const int32_t *prim_offset, const DbmpTuning *tuning,
                         dbmp_stream_t stream);
+
+/* Restricts the forward and backward of the current plan to canvas rows [y0, y1)
+ * of every canvas (binning still lists every tile); y0 = y1 = 0 lifts the
+ * restriction, and dbmp_batch_plan resets it.  Regions outside the window are
+ * skipped: their image, T_final and n_last pixels are left as they were and they
+ * contribute nothing to the loss or the gradient.  The fused MSE keeps its
+ * normalisation over all pixels of the plan, so the losses and gradients of
+ * disjoint windows sum to those of the whole canvas: this is how one canvas is
+ * shared between ranks that hold the same parameters (Sec. 3.1.1, "Parallelization":
+ * tiles are independent; the gradient, Eq. 6, is a sum over pixels).  y0 and y1
+ * must be multiples of the plan's tile size with y0 < y1, else DBMP_ERR_INVALID_ARG;
+ * DBMP_ERR_NOT_READY without a plan.  Host-only: queues nothing. */
+int32_t dbmp_batch_set_rows(DbmpWorkspace *ws, int32_t y0, int32_t y1);
 
 typedef enum { DBMP_BATCH_BIN = 1, DBMP_BATCH_FWD = 2, DBMP_BATCH_BWD = 4 } DbmpBatchMode;
 

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <vector>
 
@@ -75,6 +76,7 @@ struct DbmpWorkspace {
     RenderCfg cfg{16, 32, 2, 2};
     bool persistent = false;
     bool binned = false;
+    int32_t row0 = 0, row1 = 0;   // row window of the plan's renders (row1 0: all rows)
     const float *params = nullptr;  // of the last binning (gradient finalisation)
     int32_t Hb = 0, Wb = 0;
     float alpha_max = 1.0f;
@@ -251,6 +253,9 @@ RenderArgs make_args(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackgr
     a.bg_buf = bg ? bg->buf_dev : nullptr;
     a.T_stop = T_stop;
     a.graw = ws->graw;
+    a.row0 = ws->row0;
+    a.row1 = ws->row1;
+    a.n_prims = ws->N;
     return a;
 }
 
@@ -470,8 +475,15 @@ int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStat
     out->warp_steps_bwd = s.warp_steps_bwd;
     out->survivors = s.survivors_fwd;
     out->survivors_bwd = s.survivors_bwd;
+    out->bad_kind = s.bad_kind;
+    out->bad_pad = 0;
+    out->bad_index = s.bad_index;
     const int32_t zero = 0;
     DBMP_CUDA(cudaMemcpy(&ws->status->code, &zero, sizeof zero, cudaMemcpyHostToDevice), "status clear");
+    if (s.bad_kind) {
+        const int64_t z64[2] = {0, 0};   // bad_kind + pad, bad_index
+        DBMP_CUDA(cudaMemcpy(&ws->status->bad_kind, z64, sizeof z64, cudaMemcpyHostToDevice), "status clear");
+    }
     if (s.code == DBMP_ERR_CAPACITY)
         fail(DBMP_ERR_CAPACITY, "tile lists need %lld entries, workspace holds %lld",
              (long long)s.pairs_required, (long long)ws->lim.max_pairs);
@@ -581,6 +593,7 @@ int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, c
     ws->cfg = cfg;
     ws->persistent = true;
     ws->binned = false;
+    ws->row0 = ws->row1 = 0;
     cudaStream_t st = (cudaStream_t)stream;
     DBMP_CUDA(cudaStreamSynchronize(st), "plan sync");
     DBMP_CUDA(cudaMemcpy(ws->canvas, ws->plan.data(), sizeof(CanvasDesc) * ws->plan.size(),
@@ -661,6 +674,49 @@ int32_t dbmp_batch_render_mse(DbmpWorkspace *ws, const float *params_dev, const 
         return fail(DBMP_ERR_INVALID_ARG, "target / dL_dimage / loss is NULL");
     return batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop, mode, image_dev, T_final_dev,
                         n_last_dev, dL_dimage_dev, dparams_dev, target_dev, dL_dimage_dev, loss_dev, stream);
+}
+
+int32_t dbmp_index_checks(void) { return DBMP_CHECKED; }
+
+int32_t dbmp_workspace_debug_set(DbmpWorkspace *ws, int32_t what, int64_t index, int64_t value,
+                                 dbmp_stream_t stream) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the value is copied from this call's host memory, so the call synchronises
+    // `stream` before returning
+    if (what == 0) {
+        if (index < 0 || index > ws->lim.max_tiles) return fail(DBMP_ERR_INVALID_ARG, "tile offset %lld outside the workspace", (long long)index);
+        DBMP_CUDA(cudaMemcpyAsync(ws->tile_off + index, &value, sizeof(int64_t), cudaMemcpyHostToDevice, st), "poke");
+    } else if (what == 1 || what == 2) {
+        const int64_t cap = what == 1 ? ws->lim.max_pairs : std::max(ws->lim.max_prims, 1);
+        if (index < 0 || index >= cap) return fail(DBMP_ERR_INVALID_ARG, "index %lld outside the workspace", (long long)index);
+        if (value < INT32_MIN || value > INT32_MAX) return fail(DBMP_ERR_INVALID_ARG, "value outside int32");
+        const int32_t v = (int32_t)value;
+        int32_t *dst = what == 1 ? ws->list + index : &ws->rec[index].bmp_row;
+        DBMP_CUDA(cudaMemcpyAsync(dst, &v, sizeof v, cudaMemcpyHostToDevice, st), "poke");
+        DBMP_CUDA(cudaStreamSynchronize(st), "poke sync");
+        return DBMP_OK;
+    } else {
+        return fail(DBMP_ERR_INVALID_ARG, "what must be 0 (tile offset), 1 (list entry) or 2 (bitmap row)");
+    }
+    DBMP_CUDA(cudaStreamSynchronize(st), "poke sync");
+    return DBMP_OK;
+}
+
+int32_t dbmp_batch_set_rows(DbmpWorkspace *ws, int32_t y0, int32_t y1) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    if (!ws->persistent || ws->n_canvas < 1) return fail(DBMP_ERR_NOT_READY, "dbmp_batch_set_rows needs a plan");
+    const int32_t t = ws->cfg.tile;
+    if (y0 == 0 && y1 == 0) {
+        ws->row0 = ws->row1 = 0;
+        return DBMP_OK;
+    }
+    if (y0 < 0 || y1 <= y0 || y0 % t != 0 || y1 % t != 0)
+        return fail(DBMP_ERR_INVALID_ARG, "row window [%d, %d) must be non-empty multiples of the tile size %d", y0,
+                    y1, t);
+    ws->row0 = y0;
+    ws->row1 = y1;
+    return DBMP_OK;
 }
 
 int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,

@@ -457,7 +457,11 @@ __global__ void k_scatter(const int4 *__restrict__ rect, const CanvasDesc *__res
             const int pbase = q0 + bit0;
             while (v) {
                 const int j = __ffs(v) - 1;
-                list[pos++] = pbase + j;
+                if (DBMP_CHECKED && (pos < 0 || pos >= status->pairs_required))
+                    flag_bad(const_cast<DevStatus *>(status), BAD_LIST_WRITE, pos);
+                else
+                    list[pos] = pbase + j;
+                ++pos;
                 v &= v - 1u;
             }
             if (!last && lane == 0) done[t] = prev + total;

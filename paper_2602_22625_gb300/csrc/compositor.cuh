@@ -47,6 +47,10 @@ struct DevStatus {
     int64_t pairs_required;
     int32_t lists_valid;    // 1 after a binning that fit its capacity
     int32_t pad;
+    // first out-of-range index an index-checked build met (BadIndexKind, 0: none)
+    int32_t bad_kind;
+    int32_t pad_bad;
+    int64_t bad_index;
     // forward counters and work queue, reset together before each forward
     int64_t pairs_eval_fwd;
     int64_t pairs_contrib;  // (pixel, layer) pairs with alpha > 0 composited by the last fwd
@@ -66,6 +70,27 @@ constexpr size_t kFwdGroupBytes = offsetof(DevStatus, pairs_eval_bwd) - offsetof
 constexpr size_t kBwdGroupBytes = sizeof(DevStatus) - offsetof(DevStatus, pairs_eval_bwd);
 static_assert(kFwdGroupBytes == 4 * sizeof(int64_t) + 2 * sizeof(uint32_t), "forward group layout");
 static_assert(kBwdGroupBytes == 3 * sizeof(int64_t) + 2 * sizeof(uint32_t), "backward group layout");
+
+// Index checks, compiled into the checked build of the library only (DBMP_CHECKED=1):
+// a kernel that meets a tile range, a list entry, a bitmap row or a list position
+// outside its valid range records the first one in the status block and skips the
+// access (the tile counts as empty, the entry as culled) instead of trapping, so the
+// context stays usable and the status says what was wrong.  The kinds are the ABI's
+// DBMP_BAD_* values.
+#ifndef DBMP_CHECKED
+#define DBMP_CHECKED 0
+#endif
+enum BadIndexKind : int32_t {
+    BAD_NONE = 0,
+    BAD_TILE_RANGE = 1,   // tile offsets outside [0, sum_t d_t]: index = tile id
+    BAD_LIST_ENTRY = 2,   // primitive index outside [0, N): index = list position
+    BAD_BITMAP_ROW = 3,   // record's bitmap row not the start of a bitmap: index = primitive
+    BAD_LIST_WRITE = 4,   // binning write outside [0, sum_t d_t): index = list position
+};
+
+__device__ __forceinline__ void flag_bad(DevStatus *st, int32_t kind, int64_t index) {
+    if (atomicCAS(&st->bad_kind, 0, kind) == 0) st->bad_index = index;
+}
 
 // The bitmap atlas as the kernels see it.  The texels of all bitmaps are stacked in
 // one pitch-linear float plane, bitmap b in rows b (H_b + 1) .. b (H_b + 1) + H_b - 1
@@ -238,6 +263,11 @@ struct RenderArgs {
     const float *dL_dimage;
     const float *dL_dalpha;
     float *graw;                // [N][8] raw per-primitive sums (backward; zero between calls)
+    // rows [row0, row1) of every canvas are composited, regions outside are skipped
+    // (row1 <= 0: all rows); both multiples of the tile size, so that no region
+    // straddles the window
+    int32_t row0, row1;
+    int32_t n_prims;            // primitives of the plan (list entries index [0, n_prims))
     // forward with the MSE loss fused (null target: off): dL/dI = mse_scale (I - I*)
     // into mse_dL, and L = sum (I - I*)^2 / n added into *mse_loss (zeroed by the caller)
     const float *mse_target;

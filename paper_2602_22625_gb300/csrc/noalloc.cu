@@ -231,6 +231,7 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
         }
         a.bg_buf = bg ? bg->buf_dev : nullptr;
         a.T_stop = T_stop;
+        a.n_prims = N;
         a.image = image_dev;
         a.T_final = T_final_dev;
         a.n_last = n_last_dev;
@@ -253,6 +254,9 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
         status_out->warp_steps_bwd = 0;
         status_out->survivors = s.survivors_fwd;
         status_out->survivors_bwd = 0;
+        status_out->bad_kind = s.bad_kind;
+        status_out->bad_pad = 0;
+        status_out->bad_index = s.bad_index;
         if (s.code == DBMP_ERR_CAPACITY)
             return fail_static(DBMP_ERR_CAPACITY, "tile lists need %lld entries, the static scratch holds %lld",
                                (long long)s.pairs_required, (long long)kMaxPairs);

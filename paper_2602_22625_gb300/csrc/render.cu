@@ -58,19 +58,26 @@ __device__ __forceinline__ int find_canvas_tile(const CanvasDesc *cv, int n, int
 template <int RPL>
 struct Prefetch {
     float4 q0[RPL], q1[RPL], q2[RPL];
+    unsigned bad;              // checked build: bit r set for an out-of-range list entry
 };
 
 // Issues the loads of list entries [l0, l0 + n) (lane l: entries l + 32 r).  The
 // loads are consumed by the next compaction, so their latency overlaps with the
 // compositing of the previous batch.
 template <int RPL>
-__device__ __forceinline__ void prefetch(Prefetch<RPL> &pf, const PrimRec *__restrict__ rec,
-                                         const int32_t *__restrict__ list, int64_t l0, int n, int lane) {
+__device__ __forceinline__ void prefetch(Prefetch<RPL> &pf, const RenderArgs &a, int64_t l0, int n, int lane) {
+    pf.bad = 0u;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         const int j = lane + 32 * r;
         if (j < n) {
-            const float4 *p = reinterpret_cast<const float4 *>(rec + __ldg(list + l0 + j));
+            int32_t idx = __ldg(a.list + l0 + j);
+            if (DBMP_CHECKED && (idx < 0 || idx >= a.n_prims)) {
+                flag_bad(a.status, BAD_LIST_ENTRY, l0 + j);
+                pf.bad |= 1u << r;
+                idx = 0;
+            }
+            const float4 *p = reinterpret_cast<const float4 *>(a.rec + idx);
             pf.q0[r] = __ldg(p);
             pf.q1[r] = __ldg(p + 1);
             pf.q2[r] = __ldg(p + 2);
@@ -122,7 +129,7 @@ __device__ __forceinline__ bool region_hits(const PrimRec &r, const AtlasView &a
 // positions in pos[]; returns m (same on every lane).
 template <int RPL>
 __device__ __forceinline__ int compact(const Prefetch<RPL> &pf, int e0, int n, PrimRec *sh, int *pos,
-                                       const AtlasView &at, float x0, float y0, float w, float h,
+                                       const RenderArgs &a, float x0, float y0, float w, float h,
                                        float kw, float kv, int lane) {
     int base = 0;
     const unsigned lt = (1u << lane) - 1u;
@@ -133,7 +140,15 @@ __device__ __forceinline__ int compact(const Prefetch<RPL> &pf, int e0, int n, P
         PrimRec rc;
         if (j < n) {
             rc = as_rec(pf.q0[r], pf.q1[r], pf.q2[r]);
-            keep = region_hits(rc, at, x0, y0, w, h, kw, kv);
+            bool ok = !((pf.bad >> r) & 1u);
+            if (DBMP_CHECKED && ok) {
+                const int stride = a.atlas.Hb + 1;
+                if (rc.bmp_row < 0 || rc.bmp_row > (a.atlas.n_bmp - 1) * stride || rc.bmp_row % stride != 0) {
+                    flag_bad(a.status, BAD_BITMAP_ROW, rc.index);
+                    ok = false;
+                }
+            }
+            keep = ok && region_hits(rc, a.atlas, x0, y0, w, h, kw, kv);
         }
         const unsigned m = __ballot_sync(FULL, keep);
         if (keep) {
@@ -178,6 +193,13 @@ __device__ __forceinline__ Region region_of(const RenderArgs &a, int item) {
     g.y0 = (lt / g.d.ntx) * TILE + (r / RX) * RH;
     g.start = a.tile_off[tile_id];
     g.len = (int)(a.tile_off[tile_id + 1] - g.start);
+    if (DBMP_CHECKED) {
+        const int64_t K = a.status->pairs_required, end = a.tile_off[tile_id + 1];
+        if (g.start < 0 || end < g.start || end > K) {
+            flag_bad(a.status, BAD_TILE_RANGE, tile_id);
+            g.len = g.start < 0 || g.start > K ? 0 : (int)(min(max(end, g.start), K) - g.start);
+        }
+    }
     return g;
 }
 
@@ -231,9 +253,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     __syncwarp();
     float mse_s = 0.0f, mse_c = 0.0f;     // this lane's compensated sum of (I - I*)^2
 
+    const int row1 = a.row1 > 0 ? a.row1 : 0x7fffffff;
     for (int item = next_item(&a.status->queue_fwd, lane); item < n_items;
          item = next_item(&a.status->queue_fwd, lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
+        if (g.y0 < a.row0 || g.y0 >= row1) continue;   // outside the row window
         const int x = g.x0 + lane % RW;
         const float px = (float)x;
         float py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
@@ -255,15 +279,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
         int walked = g.len, sv_it = 0, ct_it = 0;
         if (g.len > 0) {
             Prefetch<RPL> pf;
-            prefetch<RPL>(pf, a.rec, a.list, g.start, min(BATCH, g.len), lane);
+            prefetch<RPL>(pf, a, g.start, min(BATCH, g.len), lane);
             bool alive = __any_sync(FULL, T[0] >= tstop || (PPT > 1 && T[PPT - 1] >= tstop));
             for (int b0 = 0; b0 < g.len && alive; b0 += BATCH) {
                 const int n = min(BATCH, g.len - b0);
-                const int m = compact<RPL>(pf, b0, n, sh, pos, a.atlas, rx0, ry0, rw, rh, kw, kv, lane);
+                const int m = compact<RPL>(pf, b0, n, sh, pos, a, rx0, ry0, rw, rh, kw, kv, lane);
                 sv_it += m;
                 if (b0 + BATCH < g.len)
-                    prefetch<RPL>(pf, a.rec, a.list, g.start + b0 + BATCH, min(BATCH, g.len - b0 - BATCH),
-                                  lane);
+                    prefetch<RPL>(pf, a, g.start + b0 + BATCH, min(BATCH, g.len - b0 - BATCH), lane);
                 for (int t = 0; t < m; ++t) {
                     const PrimRec r = sh[t];
                     const int j = pos[t];
@@ -440,7 +463,12 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
     Tap tp;
     tp.q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int j = 0; j < upto; ++j) {
-        const PrimRec r = a.rec[a.list[g.start + j]];
+        const int32_t idx = a.list[g.start + j];
+        if (DBMP_CHECKED && (idx < 0 || idx >= a.n_prims)) {
+            flag_bad(a.status, BAD_LIST_ENTRY, g.start + j);
+            continue;
+        }
+        const PrimRec r = a.rec[idx];
         tap_issue(r, col_xf(r, kw, kv, px), a.atlas.tex, Wbf, Hbf, py, true, tp);
         T = __fmul_rn(T, __fmaf_rn(-r.a, tap_M(tp), 1.0f));
     }
@@ -467,9 +495,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     if (lane < 4) stats.v[lane] = 0ull;
     __syncwarp();
 
+    const int row1 = a.row1 > 0 ? a.row1 : 0x7fffffff;
     for (int item = next_item(&a.status->queue_bwd, lane); item < n_items;
          item = next_item(&a.status->queue_bwd, lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
+        if (g.y0 < a.row0 || g.y0 >= row1) continue;   // outside the row window
         const int x = g.x0 + lane % RW;
         const float px = (float)x;
         float py[PPT], T[PPT], Y[PPT], g0[PPT], g1[PPT], g2[PPT];
@@ -515,12 +545,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
         int hi = my_max + 1;
         int lo = max(0, hi - BATCH);
         Prefetch<RPL> pf;
-        prefetch<RPL>(pf, a.rec, a.list, g.start + lo, hi - lo, lane);
+        prefetch<RPL>(pf, a, g.start + lo, hi - lo, lane);
         while (hi > 0) {
-            const int m = compact<RPL>(pf, lo, hi - lo, sh, pos, a.atlas, rx0, ry0, rw, rh, kw, kv, lane);
+            const int m = compact<RPL>(pf, lo, hi - lo, sh, pos, a, rx0, ry0, rw, rh, kw, kv, lane);
             sv_it += m;
             const int nlo = max(0, lo - BATCH);
-            if (lo > 0) prefetch<RPL>(pf, a.rec, a.list, g.start + nlo, lo - nlo, lane);
+            if (lo > 0) prefetch<RPL>(pf, a, g.start + nlo, lo - nlo, lane);
             for (int t = m - 1; t >= 0; --t) {
                 const PrimRec r = sh[t];
                 const int j = pos[t];

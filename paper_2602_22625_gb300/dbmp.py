@@ -36,6 +36,7 @@ EXPORTS = (
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
     "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
     "dbmp_workspace_poison", "dbmp_batch_render_mse", "dbmp_fp32_peak", "dbmp_render_alpha", "dbmp_proposer_activations",
+    "dbmp_batch_set_rows", "dbmp_index_checks", "dbmp_workspace_debug_set",
 )
 
 
@@ -66,7 +67,8 @@ class DbmpDeviceStatus(ctypes.Structure):
                 ("pairs_required", ctypes.c_int64), ("pairs_evaluated", ctypes.c_int64),
                 ("pairs_evaluated_bwd", ctypes.c_int64), ("pairs_contributing", ctypes.c_int64),
                 ("warp_steps", ctypes.c_int64), ("warp_steps_bwd", ctypes.c_int64),
-                ("survivors", ctypes.c_int64), ("survivors_bwd", ctypes.c_int64)]
+                ("survivors", ctypes.c_int64), ("survivors_bwd", ctypes.c_int64),
+                ("bad_kind", ctypes.c_int32), ("bad_pad", ctypes.c_int32), ("bad_index", ctypes.c_int64)]
 
 
 class DbmpAdamConfig(ctypes.Structure):
@@ -93,7 +95,9 @@ _f32 = ctypes.c_float
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libdbmp.so, or with DBMP_LIBRARY=checked in the environment the build with
+    device-side index checks (libdbmp_checked.so)."""
+    return _build.LIB_CHECKED if os.environ.get("DBMP_LIBRARY") == "checked" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -103,7 +107,7 @@ def load(build_if_missing: bool = True):
         return _lib
     if build_if_missing and not _build.up_to_date():
         _build.build()
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"libdbmp.so not found at {path}; run paper_2602_22625_gb300._build.build()")
     L = ctypes.CDLL(path)
@@ -134,6 +138,9 @@ def load(build_if_missing: bool = True):
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
         "dbmp_render_alpha": (_i32, [_vp, _vp, _i64, _vp]),
+        "dbmp_batch_set_rows": (_i32, [_vp, _i32, _i32]),
+        "dbmp_index_checks": (_i32, []),
+        "dbmp_workspace_debug_set": (_i32, [_vp, _i32, _i64, _i64, _vp]),
         "dbmp_proposer_activations": (_i32, [_vp, _i32, _vp, _i64]),
         "dbmp_fp32_peak": (_i32, [_i32, _i32, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
         "dbmp_gemm_bf16": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _i32,
@@ -312,6 +319,24 @@ def dbmp_batch_plan(ws, H, W, prim_offset, tile=16, batch=32, ppt=2, ppt_bwd=0, 
     Oa = (_i32 * (n + 1))(*prim_offset)
     t = DbmpTuning(tile, batch, ppt, ppt_bwd)
     _check(load().dbmp_batch_plan(ws, n, Ha, Wa, Oa, ctypes.byref(t), _stream(stream)))
+
+
+BAD_NONE, BAD_TILE_RANGE, BAD_LIST_ENTRY, BAD_BITMAP_ROW, BAD_LIST_WRITE = 0, 1, 2, 3, 4
+
+
+def dbmp_index_checks():
+    """True if the loaded library is the index-checked build."""
+    return bool(load().dbmp_index_checks())
+
+
+def dbmp_workspace_debug_set(ws, what, index, value, stream=None):
+    """Testing aid: overwrites a tile offset (0), list entry (1) or record bitmap row (2)."""
+    _check(load().dbmp_workspace_debug_set(ws, int(what), int(index), int(value), _stream(stream)))
+
+
+def dbmp_batch_set_rows(ws, y0, y1):
+    """Restricts the plan's renders to canvas rows [y0, y1) (0, 0: all rows)."""
+    _check(load().dbmp_batch_set_rows(ws, int(y0), int(y1)))
 
 
 def dbmp_batch_render(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, image=None, T_final=None,

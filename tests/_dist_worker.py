@@ -49,3 +49,38 @@ def reference_arm(rank, world, out_dir):
         f.write(buf.getvalue())
     with open(os.path.join(out_dir, f"ref{rank}.time"), "w") as f:
         f.write(str(__import__("time").perf_counter() - t0))
+
+
+def sharded(rank, world, port, out_dir):
+    """One canvas shared by the ranks: each rank's FP64 oracle gradient over its band
+    of rows (the loss normalised over the whole canvas), summed by the all-reduce of
+    sharded.sum_gradient_, must equal the whole canvas' gradient."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_2602_22625_gb300 import inputs, sharded as S
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sc = inputs.tiny(seed=5, N=80, H=70, W=52)   # 5 tile rows of 16: bands of 3 and 2
+        tg = inputs.tiny(seed=6, N=80, H=70, W=52)
+        img = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)["image"]
+        tgt = oracle.render(tg.H, tg.W, tg.params, tg.bitmap_id, tg.atlas, background=tg.background)["image"]
+        gI = 2.0 * (img - tgt) / img.size                 # MSE over the whole canvas
+        y0, y1 = S.band_rows(sc.H, world, rank, tile=16)
+        g = oracle.grad_rows(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, y0, min(y1, sc.H),
+                             background=sc.background)
+        t = torch.from_numpy(g.copy())
+        S.sum_gradient_(t, world)
+        full = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+        res = {"rows": [y0, y1], "err": float(np.abs(t.numpy() - full).max() / np.abs(full).max()),
+               "own": float(np.abs(g).max() / np.abs(full).max())}
+        with open(os.path.join(out_dir, f"shard{rank}.json"), "w") as f:
+            json.dump(res, f)
+    finally:
+        dist.destroy_process_group()
