@@ -68,6 +68,13 @@ struct DbmpWorkspace {
     CanvasDesc *canvas = nullptr;
     DevStatus *status = nullptr;
     unsigned long long *stats = nullptr;   // scaling statistics counters
+    int32_t *item_cost = nullptr;          // [item_cap] per-region cost of the last forward
+    int32_t *item_order = nullptr;         // [item_cap] regions by decreasing cost
+    int64_t item_cap = 0;                  // regions the two arrays hold
+    int32_t *item_hist = nullptr;          // [2][64] cost buckets and cursors of alternate forwards
+    int32_t hist_half = 0;                 // the half the next forward counts into (zeroed)
+    // the order matches the current plan and the forward's regions (0: none yet)
+    int32_t order_items = 0;
     // host copy of the current plan
     std::vector<CanvasDesc> plan;
     std::vector<int32_t> plan_H, plan_W, plan_off;
@@ -84,6 +91,12 @@ struct DbmpWorkspace {
 
 namespace {
 
+// Regions the per-region cost and order arrays hold: a region covers at least 32
+// pixels (one per lane), so a pass has at most tile^2 / 32 <= 32 regions per tile, at
+// whatever tile size max_tiles was counted.  A pass with more regions than this (more
+// tiles than max_tiles) renders in list-length order without recording costs.
+int64_t item_capacity(const DbmpLimits &l) { return 32 * (int64_t)l.max_tiles; }
+
 size_t ws_bytes(const DbmpLimits &l) {
     size_t b = 0;
     b += sizeof(PrimRec) * (size_t)l.max_prims;
@@ -96,6 +109,7 @@ size_t ws_bytes(const DbmpLimits &l) {
     b += sizeof(CanvasDesc) * (size_t)l.max_canvases;
     b += sizeof(DevStatus);
     b += sizeof(unsigned long long) * kBinStatsWords;
+    b += 2 * sizeof(int32_t) * (size_t)item_capacity(l) + sizeof(int32_t) * 128;
     return b;
 }
 
@@ -286,8 +300,25 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
         a.mse_inv_n = 1.0 / n;
         DBMP_CUDA(cudaMemsetAsync(mse_loss, 0, sizeof(double), st), "loss reset");
     }
+    // regions in the order of the previous forward's costs (when it had the same
+    // regions); this forward records the costs again and the order is re-sorted
+    const int32_t items = render_items(ws->cfg, ws->n_tiles, false);
+    const bool ordered = items <= ws->item_cap;   // the cost and order arrays hold every region
+    int32_t *hist = ws->item_hist + 64 * ws->hist_half, *next = ws->item_hist + 64 * (1 - ws->hist_half);
+    if (ordered) {
+        if (ws->order_items == items) a.item_order = ws->item_order;
+        a.item_cost = ws->item_cost;
+        a.item_hist = hist;
+    }
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, kFwdGroupBytes, st), "status reset");
     DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
+    if (ordered) {
+        DBMP_CUDA(launch_item_order(ws->item_cost, hist, next, ws->item_order, items, st), "region order");
+        ws->order_items = items;
+        ws->hist_half = 1 - ws->hist_half;
+    } else {
+        ws->order_items = 0;
+    }
     return DBMP_OK;
 }
 
@@ -299,6 +330,10 @@ int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     a.n_last = const_cast<int32_t *>(n_last);
     a.dL_dimage = dL_dimage;
     a.dL_dalpha = dL_dalpha;
+    // the forward's regions in decreasing cost, when the backward has the same regions
+    if (ws->order_items > 0 && ws->order_items <= ws->item_cap &&
+        ws->order_items == render_items(ws->cfg, ws->n_tiles, true))
+        a.item_order = ws->item_order;
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, kBwdGroupBytes, st), "status reset");
     DBMP_CUDA(launch_bwd(a, ws->cfg, st), "backward launch");
     DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, st), "gradient finalize");
@@ -391,6 +426,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
     if (int32_t r = check_limits(limits)) return r;
     DbmpWorkspace *ws = new DbmpWorkspace;
     ws->lim = *limits;
+    ws->item_cap = item_capacity(ws->lim);
     const DbmpLimits &l = *limits;
     struct Req {
         void **p;
@@ -406,6 +442,9 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         {(void **)&ws->canvas, sizeof(CanvasDesc) * (size_t)l.max_canvases},
         {(void **)&ws->status, sizeof(DevStatus)},
         {(void **)&ws->stats, sizeof(unsigned long long) * kBinStatsWords},
+        {(void **)&ws->item_cost, sizeof(int32_t) * (size_t)item_capacity(l)},
+        {(void **)&ws->item_order, sizeof(int32_t) * (size_t)item_capacity(l)},
+        {(void **)&ws->item_hist, sizeof(int32_t) * 128},
     };
     for (auto &r : reqs) {
         cudaError_t e = cudaMalloc(r.p, r.n);
@@ -417,6 +456,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
     }
     cudaError_t e = cudaMemset(ws->status, 0, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMemset(ws->graw, 0, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1));
+    if (e == cudaSuccess) e = cudaMemset(ws->item_hist, 0, sizeof(int32_t) * 128);
     if (e == cudaSuccess) e = init_bin_kernels(kMaxTilesPerCanvas);
     if (e == cudaSuccess) e = init_render_kernels();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -444,15 +484,22 @@ int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream) {
         {ws->hist, sizeof(int32_t) * (size_t)kHistCap},
         {ws->canvas, sizeof(CanvasDesc) * (size_t)l.max_canvases},
         {ws->stats, sizeof(unsigned long long) * kBinStatsWords},
+        {ws->item_cost, sizeof(int32_t) * (size_t)item_capacity(l)},
+        {ws->item_order, sizeof(int32_t) * (size_t)item_capacity(l)},
+        {ws->item_hist, sizeof(int32_t) * 128},
     };
     for (auto &b : bufs) DBMP_CUDA(cudaMemsetAsync(b.p, 0xFF, b.n, st), "poison");
+    // the bucket counts are state that must start at zero, not scratch
+    DBMP_CUDA(cudaMemsetAsync(ws->item_hist, 0, sizeof(int32_t) * 128, st), "poison");
+    ws->order_items = 0;
     return DBMP_OK;
 }
 
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws) {
     if (!ws) return DBMP_OK;
-    void *ptrs[] = {ws->rec,  ws->rect, ws->graw,   ws->tile_off, ws->tile_order,
-                    ws->list, ws->hist, ws->canvas, ws->status,   ws->stats};
+    void *ptrs[] = {ws->rec,    ws->rect,   ws->graw,      ws->tile_off,   ws->tile_order, ws->list,
+                    ws->hist,   ws->canvas, ws->status,    ws->stats,      ws->item_cost,  ws->item_order,
+                    ws->item_hist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ws;
@@ -503,7 +550,10 @@ int32_t dbmp_bin(DbmpWorkspace *ws, int32_t H, int32_t W, int32_t tile, const fl
     if (N > 0 && (((uintptr_t)params_dev) & 15))
         return fail(DBMP_ERR_INVALID_ARG, "params_dev must be 16-byte aligned");
     const int32_t off[2] = {0, N};
+    const bool same = !ws->persistent && ws->n_canvas == 1 && ws->plan_H.size() == 1 && ws->plan_H[0] == H &&
+                      ws->plan_W[0] == W && ws->cfg.tile == tile;
     if (int32_t r = build_plan(ws, 1, &H, &W, off, tile)) return r;
+    if (!same) ws->order_items = 0;   // another canvas: the region order no longer applies
     ws->persistent = false;
     cudaStream_t st = (cudaStream_t)stream;
     k_set_canvas<<<1, 1, 0, st>>>(ws->plan[0], ws->canvas);
@@ -594,6 +644,7 @@ int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, c
     ws->persistent = true;
     ws->binned = false;
     ws->row0 = ws->row1 = 0;
+    ws->order_items = 0;
     cudaStream_t st = (cudaStream_t)stream;
     DBMP_CUDA(cudaStreamSynchronize(st), "plan sync");
     DBMP_CUDA(cudaMemcpy(ws->canvas, ws->plan.data(), sizeof(CanvasDesc) * ws->plan.size(),

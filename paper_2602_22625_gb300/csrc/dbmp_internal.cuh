@@ -111,6 +111,11 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
 
 bool render_cfg_supported(const RenderCfg &cfg);
 cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
+// Work items (regions) of a forward (bwd false) or backward pass over n_tiles tiles.
+int32_t render_items(const RenderCfg &cfg, int32_t n_tiles, bool bwd);
+// Region order by decreasing forward cost (counting sort of the forward's buckets).
+cudaError_t launch_item_order(const int32_t *cost, int32_t *hist, int32_t *next_hist, int32_t *order,
+                              int32_t n_items, cudaStream_t st);
 cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
 // dparams += chain rule of the raw sums graw, which are zeroed after reading (graw is
 // zero before every backward: zeroed at workspace creation, left zero by this kernel).

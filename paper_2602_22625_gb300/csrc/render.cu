@@ -166,6 +166,7 @@ __device__ __forceinline__ int compact(const Prefetch<RPL> &pf, int e0, int n, P
 }
 
 struct Region {
+    int raw;          // region id: tile * R + region within the tile
     CanvasDesc d;
     int x0, y0;       // canvas coordinates of the region's top-left pixel
     int64_t start;    // first list entry of the tile
@@ -183,9 +184,16 @@ __device__ __forceinline__ Region region_of(const RenderArgs &a, int item) {
     constexpr int RH = 32 * PPT / RW;             // rows per region
     constexpr int RX = TILE / RW;                 // regions across a tile
     constexpr int R = RX * (TILE / RH);           // regions per tile
-    const int ti = item / R, r = item - ti * R;
-    const int tile_id = a.tile_order ? a.tile_order[ti] : ti;
+    int raw;
+    if (a.item_order) {
+        raw = a.item_order[item];
+    } else {
+        const int ti = item / R;
+        raw = (a.tile_order ? a.tile_order[ti] : ti) * R + (item - ti * R);
+    }
+    const int tile_id = raw / R, r = raw - tile_id * R;
     Region g;
+    g.raw = raw;
     const int c = find_canvas_tile(a.canvas, a.n_canvas, tile_id);
     g.d = a.canvas[c];
     const int lt = tile_id - g.d.tile_base;
@@ -257,7 +265,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     for (int item = next_item(&a.status->queue_fwd, lane); item < n_items;
          item = next_item(&a.status->queue_fwd, lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
-        if (g.y0 < a.row0 || g.y0 >= row1) continue;   // outside the row window
+        if (g.y0 < a.row0 || g.y0 >= row1) {   // outside the row window
+            if (a.item_cost && lane == 0) {
+                a.item_cost[g.raw] = 1;
+                atomicAdd(a.item_hist, 1);
+            }
+            continue;
+        }
         const int x = g.x0 + lane % RW;
         const float px = (float)x;
         float py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
@@ -392,6 +406,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
             stats.v[1] += (unsigned)ct_it;
             stats.v[2] += (unsigned)walked;
             stats.v[3] += (unsigned)sv_it;
+            if (a.item_cost) {   // the region's cost, for the next pass' order
+                const int c = sv_it + 1;
+                a.item_cost[g.raw] = c;
+                atomicAdd(a.item_hist + (31 - __clz(c)), 1);
+            }
         }
     }
     __syncwarp();
@@ -729,6 +748,47 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     }
 }
 
+// Regions sorted by decreasing cost (longest first): a counting sort over the
+// forward's log2 cost buckets.  Within a bucket the order is whatever the atomics
+// give; any order renders the same pixels.  hist[32..63] (the cursors) start at zero.
+// If the buckets do not count every region (a forward that stopped early, e.g. on a
+// tile-list capacity overflow), the order is the identity, so that it always holds
+// every region exactly once.  The counts come in two halves used by alternate
+// forwards: this kernel clears the other half (next_hist) for the next forward, so
+// no separate reset is queued.  Launched as a programmatic dependent of the forward.
+__global__ void k_item_order(const int32_t *__restrict__ cost, int32_t *__restrict__ hist,
+                             int32_t *__restrict__ next_hist, int32_t *__restrict__ order, int32_t n) {
+    pdl_wait();
+    __shared__ int32_t base[32];
+    __shared__ int32_t total;
+    if (blockIdx.x == 0 && threadIdx.x < 64) next_hist[threadIdx.x] = 0;
+    if (threadIdx.x < 32) {
+        // lane l holds bucket 31 - l: an inclusive scan over the lanes counts the
+        // regions of all costlier buckets
+        const int l = threadIdx.x;
+        const int c = hist[31 - l];
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, o);
+            if (l >= o) incl += u;
+        }
+        base[31 - l] = incl - c;
+        if (l == 31) total = incl;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        if (total != n) {
+            order[i] = i;
+            return;
+        }
+        const int c = max(cost[i], 1);
+        const int b = 31 - __clz(c);
+        order[base[b] + atomicAdd(hist + 32 + b, 1)] = i;
+    }
+}
+
 // Per-primitive chain rule from the eight reduced sums to the raw parameters:
 //   x: -(A S0 + C S1)    y: -(B S0 + D S1)    s: -S2 / s    theta: S3
 //   nu: S4 (1 - sigmoid(nu))    c_j: S_{5+j} chat_j (1 - chat_j)
@@ -882,6 +942,21 @@ cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
     RenderCfg b = cfg;
     b.ppt = cfg.bwd_ppt();
     return dispatch(a, b, false, st);
+}
+
+int32_t render_items(const RenderCfg &cfg, int32_t n_tiles, bool bwd) {
+    const int ppt = bwd ? cfg.bwd_ppt() : cfg.ppt;
+    return n_tiles * (cfg.tile * cfg.tile / (32 * ppt));
+}
+
+cudaError_t launch_item_order(const int32_t *cost, int32_t *hist, int32_t *next_hist, int32_t *order,
+                              int32_t n_items, cudaStream_t st) {
+    if (n_items > 0) {
+        const cudaError_t e = launch_pdl(k_item_order, dim3((n_items + 255) / 256), dim3(256), 0, st, cost, hist,
+                                         next_hist, order, n_items);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
