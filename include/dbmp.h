@@ -389,6 +389,7 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
  *   mode 1: Cf[m][n] += acc           (float32 atomics; allows split_k > 1)
  *   mode 2: Cb[m][n] = bf16(max(acc + bias[n], 0))   (bf16, row stride ldc)
  *   mode 3: Cf[m][n] = acc + bias[n]
+ *   mode 4: Cb[m][n] = bf16(acc)      (bf16, row stride ldc)
  *   split_k  number of CTAs sharing the K range of a tile (mode 1 only if > 1)
  *   mode flag 64: failure-detection test only: no operand copy is issued, so the
  *               pipeline's waits run out (2 s each) and status_dev is set to

@@ -978,9 +978,10 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
         (((uintptr_t)B_dev) & 15))
         return fail(DBMP_ERR_INVALID_ARG,
                     "A / B rows must be 16-byte aligned, lda / ldb multiples of 8 and >= the contiguous extent");
-    if (mode < 0 || mode > 3) return fail(DBMP_ERR_INVALID_ARG, "mode must be 0..3 (+ flags 16, 32, 64)");
+    if (mode < 0 || mode > 4) return fail(DBMP_ERR_INVALID_ARG, "mode must be 0..4 (+ flags 16, 32, 64)");
     if (ldc < N) return fail(DBMP_ERR_INVALID_ARG, "ldc < N");
-    if ((mode == 2 && !Cb_dev) || (mode != 2 && !Cf_dev)) return fail(DBMP_ERR_INVALID_ARG, "output is NULL");
+    const bool bf16_out = mode == 2 || mode == 4;
+    if ((bf16_out && !Cb_dev) || (!bf16_out && !Cf_dev)) return fail(DBMP_ERR_INVALID_ARG, "output is NULL");
     if ((mode == 2 || mode == 3) && !bias_dev) return fail(DBMP_ERR_INVALID_ARG, "bias is NULL");
     if (split_k < 1 || (split_k > 1 && mode != 1)) return fail(DBMP_ERR_INVALID_ARG, "split_k > 1 needs mode 1");
     static std::once_flag once;

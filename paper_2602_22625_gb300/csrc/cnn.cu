@@ -72,9 +72,9 @@ __global__ void k_im2col(const uint16_t *__restrict__ X, int32_t B, int32_t lh, 
 }
 
 // dX[b][y][x][c] = sum over (ky, kx) with 2oy-1+ky = y, 2ox-1+kx = x of
-// dcol[(b,oy,ox)][(ky*4+kx)*C + c]; then dZ = X > 0 ? bf16(dX) : 0.  H = W = 2^lh,
-// C = 2^lc (>= 4); four channels per thread (16-byte loads of dcol).
-__global__ void k_col2im_mask(const float *__restrict__ dcol, const uint16_t *__restrict__ X, int32_t B,
+// dcol[(b,oy,ox)][(ky*4+kx)*C + c] (bf16, summed in fp32); then dZ = X > 0 ? bf16(dX) : 0.
+// H = W = 2^lh, C = 2^lc (>= 4); four channels per thread (8-byte loads of dcol).
+__global__ void k_col2im_mask(const uint16_t *__restrict__ dcol, const uint16_t *__restrict__ X, int32_t B,
                               int32_t lh, int32_t lc, uint16_t *__restrict__ dZ) {
     const int lo = lh - 1, Ho = 1 << lo, C = 1 << lc;
     const int64_t n4 = ((int64_t)B << (2 * lh + lc)) >> 2;
@@ -93,12 +93,12 @@ __global__ void k_col2im_mask(const float *__restrict__ dcol, const uint16_t *__
             for (int kx = (x + 1) & 1; kx < 4; kx += 2) {
                 const int ox = (x + 1 - kx) >> 1;
                 if (ox < 0 || ox >= Ho) continue;
-                const float4 d = *reinterpret_cast<const float4 *>(
+                const uint2 d = *reinterpret_cast<const uint2 *>(
                     dcol + ((((b << lo) + oy) << lo) + ox) * ((int64_t)16 << lc) + ((ky * 4 + kx) << lc) + c);
-                acc.x += d.x;
-                acc.y += d.y;
-                acc.z += d.z;
-                acc.w += d.w;
+                acc.x += bf2f((uint16_t)(d.x & 0xffffu));
+                acc.y += bf2f((uint16_t)(d.x >> 16));
+                acc.z += bf2f((uint16_t)(d.y & 0xffffu));
+                acc.w += bf2f((uint16_t)(d.y >> 16));
             }
         }
         const uint2 xv = *reinterpret_cast<const uint2 *>(X + i);
@@ -478,9 +478,11 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
                  K, nullptr, split_for(Co, K, M), c.status, st);
         k_colsum<uint16_t><<<colsum_blocks(M, Co, 2), 256, 0, st>>>(c.dz, M, Co, c.grad + L[l].b_off);
         if (l == 0 || e != cudaSuccess) break;
-        e = gemm(c.dz, Co, c.wbf + L[l].w_off, K, M, K, Co, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, K, nullptr, 1,
+        // the input-gradient columns in bf16 (the product buffer holds twice as many fp32)
+        uint16_t *dcol = reinterpret_cast<uint16_t *>(c.dx);
+        e = gemm(c.dz, Co, c.wbf + L[l].w_off, K, M, K, Co, GEMM_STORE_BF16 | GEMM_B_MN, nullptr, dcol, K, nullptr, 1,
                  c.status, st);
-        k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin / 4), 256, 0, st>>>(c.dx, c.X[l], B, ilog2(H),
+        k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin / 4), 256, 0, st>>>(dcol, c.X[l], B, ilog2(H),
                                                                                    ilog2(L[l].cin), c.dzp);
         uint16_t *t = c.dz;
         c.dz = c.dzp;

@@ -145,7 +145,7 @@ cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32
 // accumulation.  A, B are raw bf16 bits, K-contiguous, 16-byte aligned rows
 // (lda, ldb multiples of 8), K a multiple of 64.
 // ---------------------------------------------------------------------------
-enum GemmMode { GEMM_STORE_F32 = 0, GEMM_ATOMIC_F32 = 1, GEMM_BIAS_RELU_BF16 = 2, GEMM_BIAS_F32 = 3 };
+enum GemmMode { GEMM_STORE_F32 = 0, GEMM_ATOMIC_F32 = 1, GEMM_BIAS_RELU_BF16 = 2, GEMM_BIAS_F32 = 3, GEMM_STORE_BF16 = 4 };
 // Operand layout flags of dbmp_gemm_bf16's mode: A (B) given MN-major, i.e. as the
 // K x M (K x N) matrix with M (N) contiguous.
 constexpr int32_t GEMM_A_MN = 16, GEMM_B_MN = 32;
@@ -159,7 +159,7 @@ struct GemmArgs {
     int32_t mode;       // GemmMode (the epilogue)
     int32_t a_mn, b_mn; // operands MN-major (A: K x M, B: K x N, lda / ldb their row strides)
     float *Cf;          // GEMM_STORE_F32, GEMM_ATOMIC_F32, GEMM_BIAS_F32
-    uint16_t *Cb;       // GEMM_BIAS_RELU_BF16
+    uint16_t *Cb;       // GEMM_BIAS_RELU_BF16, GEMM_STORE_BF16
     const float *bias;  // [N] for the bias modes
     int32_t *status;    // set to DBMP_ERR_TIMEOUT if a bounded wait gives up (may be null)
     int32_t tma_c;      // set by the launcher: C written by TMA tensor stores (aligned C)

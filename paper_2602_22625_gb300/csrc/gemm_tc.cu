@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ---- epilogue ----
         const int q = warp & 3;                   // TMEM lanes 32 q .. 32 q + 31
-        const bool bf = g.mode == GEMM_BIAS_RELU_BF16;
+        const bool bf = g.mode == GEMM_BIAS_RELU_BF16 || g.mode == GEMM_STORE_BF16;
+        const bool relu = g.mode == GEMM_BIAS_RELU_BF16;
         const int ecols = bf ? 64 : 32;           // columns of a 128-byte row piece
         const uint32_t box0 = sbase + S * C::STAGE + (uint32_t)(q * 2 * kStageBox);
         unsigned char *box0p = smem + S * C::STAGE + q * 2 * kStageBox;
@@ -371,10 +372,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
                         }
-                        if (bf) {
+                        if (relu) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i)
                                 w[h / 2 + i] = pack_bf16x2(fmaxf(v[2 * i], 0.0f), fmaxf(v[2 * i + 1], 0.0f));
+                        } else if (bf) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) w[h / 2 + i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
                         } else {
 #pragma unroll
                             for (int i = 0; i < 16; ++i) w[h + i] = __float_as_uint(v[i]);
@@ -427,13 +431,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
                             if (nb + i < g.N) atomicAdd(out + i, v[i]);
-                    } else {  // GEMM_BIAS_RELU_BF16
+                    } else {  // GEMM_BIAS_RELU_BF16, GEMM_STORE_BF16
                         __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + (size_t)row * g.ldc + nb;
                         __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const float bb = nb + i < g.N ? g.bias[nb + i] : 0.0f;
-                            h[i] = __float2bfloat16_rn(fmaxf(v[i] + bb, 0.0f));
+                            if (relu) {
+                                const float bb = nb + i < g.N ? g.bias[nb + i] : 0.0f;
+                                h[i] = __float2bfloat16_rn(fmaxf(v[i] + bb, 0.0f));
+                            } else {
+                                h[i] = __float2bfloat16_rn(v[i]);
+                            }
                         }
                         if (full16 && ((g.ldc & 7) == 0) && ((nb & 7) == 0)) {
                             reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
@@ -484,7 +492,7 @@ bool make_map(CUtensorMap *m, const uint16_t *base, int outer, int inner, int ld
 // under 256 bytes: there one lane per row already stores a warp's rows contiguously,
 // and the staging buffers would only cost resident CTAs.
 bool make_map_c(CUtensorMap *m, const GemmArgs &g) {
-    const bool bf = g.mode == GEMM_BIAS_RELU_BF16;
+    const bool bf = g.mode == GEMM_BIAS_RELU_BF16 || g.mode == GEMM_STORE_BF16;
     const void *base = bf ? (const void *)g.Cb : (const void *)g.Cf;
     const size_t esz = bf ? 2 : 4;
     if (!base || ((uintptr_t)base & 15) || (((size_t)g.ldc * esz) & 15) || g.ldc < g.N) return false;
