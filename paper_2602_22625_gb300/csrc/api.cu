@@ -37,6 +37,10 @@ int32_t cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 constexpr int32_t kMaxTilesPerCanvas = 65536;  // tile index range of one canvas
+// Passes with at most this many regions per SM take their regions in the order of the
+// forward's measured costs (measured: main 1024^2 workload, 54 per SM, backward -10%;
+// 2048^2 stress, 216 per SM, -1%; 64-canvas batch, 1 600 per SM, +3%, so not there).
+constexpr int32_t kOrderMaxRegionsPerSM = 256;
 constexpr int64_t kHistCap = 16 << 20;         // chunk x tile histogram entries
 
 bool tile_ok(int32_t t) { return t == 8 || t == 16 || t == 32; }
@@ -302,8 +306,12 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     }
     // regions in the order of the previous forward's costs (when it had the same
     // regions); this forward records the costs again and the order is re-sorted
+    // Regions in cost order pay off when a pass has few regions per warp, where the
+    // last ones to finish set the pass' time; with many (a large batch of canvases)
+    // there is no tail to shorten and the list-length order keeps a tile's regions
+    // together.  The arrays must also hold every region.
     const int32_t items = render_items(ws->cfg, ws->n_tiles, false);
-    const bool ordered = items <= ws->item_cap;   // the cost and order arrays hold every region
+    const bool ordered = items <= ws->item_cap && items <= kOrderMaxRegionsPerSM * sm_count();
     int32_t *hist = ws->item_hist + 64 * ws->hist_half, *next = ws->item_hist + 64 * (1 - ws->hist_half);
     if (ordered) {
         if (ws->order_items == items) a.item_order = ws->item_order;
