@@ -423,8 +423,8 @@ int32_t dbmp_fp32_peak(int32_t packed, int32_t iters, float *sink_dev, int64_t n
  * learned (autoregressive / RL) initialisation as future work (Sec. S5) and
  * shows that initialisation matters (Sec. 3.2.2); the network here is this
  * library's own design:
- *   input   256 x 256 RGB in [0, 1] -> bf16 NHWC, 2 (I - 0.5), channels padded to 8
- *   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 8 -> 32 -> 64 -> 128 -> 256 -> 256
+ *   input   256 x 256 RGB in [0, 1] -> bf16 NHWC, 2 (I - 0.5), channels padded to 4
+ *   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 4 -> 32 -> 64 -> 128 -> 256 -> 256
  *   head    1x1 conv 256 -> 64 on the 8 x 8 map = 8 slots x 8 outputs per cell
  *   decode  cell (cy, cx), slot k, outputs o: x = 32 cx + 8 (k % 4) + 8 s(o0),
  *           y = 32 cy + 16 (k / 4) + 16 s(o1), s = 6 + 8 s(o2), theta = 0,
@@ -456,7 +456,7 @@ int32_t dbmp_proposer_set_params(DbmpProposer *p, const float *host, int64_t n);
 int32_t dbmp_proposer_get(DbmpProposer *p, int32_t which, float *host, int64_t n);
 /* Testing aid: downloads the activations the last forward (dbmp_propose or
  * dbmp_proposer_train_step) left on the device, as float32 in host memory:
- * layer 0 = the packed bf16 input (B x 256 x 256 x 8, NHWC), 1..5 = the bf16
+ * layer 0 = the packed bf16 input (B x 256 x 256 x 4, NHWC), 1..5 = the bf16
  * post-ReLU outputs of the five convolutions (B x S x S x C, S = 128, 64, 32, 16, 8,
  * C = 32, 64, 128, 256, 256), 6 = the head's float32 outputs (B*64 x 64).  n must
  * be that count for the last forward's batch, else DBMP_ERR_INVALID_ARG;

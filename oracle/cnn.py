@@ -5,8 +5,8 @@ It shares no code with the CUDA library.
 
 The network (a learned initialiser; the paper names learned/AR initialisation as
 future work, Sec. S5, and shows that initialisation matters, Sec. 3.2.2):
-  input   B x 256 x 256 x 8 (NHWC): channels 0-2 = 2 (I - 0.5), 3-7 = 0
-  conv1-5 4x4, stride 2, padding 1, + bias, ReLU: 8(3 used)->32->64->128->256->256,
+  input   B x 256 x 256 x 4 (NHWC): channels 0-2 = 2 (I - 0.5), 3 = 0
+  conv1-5 4x4, stride 2, padding 1, + bias, ReLU: 4(3 used)->32->64->128->256->256,
           spatial 256 -> 128 -> 64 -> 32 -> 16 -> 8
   head    1x1 conv 256 -> 64 (+ bias): 8 slots x 8 outputs per cell of the 8x8 map
 Weights are stored (Cout, K) with K ordered (ky, kx, ci), ci fastest.
@@ -28,7 +28,7 @@ import math
 
 import numpy as np
 
-LAYERS = ((8, 3, 32, 4), (32, 32, 64, 4), (64, 64, 128, 4), (128, 128, 256, 4),
+LAYERS = ((4, 3, 32, 4), (32, 32, 64, 4), (64, 64, 128, 4), (128, 128, 256, 4),
           (256, 256, 256, 4), (256, 256, 64, 1))
 LOSS_W = np.array([1, 1, 1, 0, 1, 1, 1, 1], np.float64)
 
@@ -56,9 +56,9 @@ def unpack(theta):
 
 
 def pack_input(images, rnd=True):
-    """images (B, 3, 256, 256) in [0, 1] -> (B, 256, 256, 8)."""
+    """images (B, 3, 256, 256) in [0, 1] -> (B, 256, 256, 4)."""
     B, _, H, W = images.shape
-    X = np.zeros((B, H, W, 8))
+    X = np.zeros((B, H, W, 4))
     X[..., :3] = (2.0 * (np.asarray(images, np.float32) - np.float32(0.5))).transpose(0, 2, 3, 1)
     return bf16(X) if rnd else X
 

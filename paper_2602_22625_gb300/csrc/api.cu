@@ -7,7 +7,6 @@
 
 #include <algorithm>
 #include <climits>
-#include <mutex>
 #include <vector>
 
 #include "dbmp_internal.cuh"
@@ -992,10 +991,7 @@ int32_t dbmp_gemm_bf16(const uint16_t *A_dev, int32_t lda, const uint16_t *B_dev
     if ((bf16_out && !Cb_dev) || (!bf16_out && !Cf_dev)) return fail(DBMP_ERR_INVALID_ARG, "output is NULL");
     if ((mode == 2 || mode == 3) && !bias_dev) return fail(DBMP_ERR_INVALID_ARG, "bias is NULL");
     if (split_k < 1 || (split_k > 1 && mode != 1)) return fail(DBMP_ERR_INVALID_ARG, "split_k > 1 needs mode 1");
-    static std::once_flag once;
-    static cudaError_t init_err = cudaSuccess;
-    std::call_once(once, [] { init_err = init_gemm_kernels(); });
-    DBMP_CUDA(init_err, "gemm set-up");
+    DBMP_CUDA(init_gemm_kernels(), "gemm set-up");
     GemmArgs g{A_dev, B_dev, M, N, K, lda, ldb, ldc, mode, a_mn, b_mn, Cf_dev, Cb_dev, bias_dev, status_dev};
     g.stall = stall;
     DBMP_CUDA(launch_gemm(g, split_k, (cudaStream_t)stream), "gemm launch");

@@ -33,17 +33,36 @@ __device__ __forceinline__ uint16_t f2bf(float x) {
 }
 __device__ __forceinline__ float bf2f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
+// The input image as the first layer's 4 channels (NHWC bf16): 2 (I - 0.5), and a zero
+// fourth channel (the first layer's K = 16 taps x 4 channels = 64, one GEMM K step).
 __global__ void k_pack_input(const float *__restrict__ img, int32_t B, uint16_t *__restrict__ X0) {
     const int64_t n = (int64_t)B * 65536;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = i >> 16, pix = i & 65535;
         const float *I = img + b * 3 * 65536 + pix;
-        __align__(16) uint16_t h[8];
+        __align__(8) uint16_t h[4];
 #pragma unroll
         for (int c = 0; c < 3; ++c) h[c] = f2bf(2.0f * (I[c * 65536] - 0.5f));
-#pragma unroll
-        for (int c = 3; c < 8; ++c) h[c] = 0;
-        reinterpret_cast<uint4 *>(X0)[i] = *reinterpret_cast<const uint4 *>(h);
+        h[3] = 0;
+        reinterpret_cast<uint2 *>(X0)[i] = *reinterpret_cast<const uint2 *>(h);
+    }
+}
+
+// im2col of the 4-channel input: col[m][(ky*4 + kx)*4 + c] = X[b][2oy-1+ky][2ox-1+kx][c]
+// (0 outside), m = (b, oy, ox), H = W = 2^lh; one 8-byte chunk (4 channels) per thread.
+__global__ void k_im2col4(const uint16_t *__restrict__ X, int32_t B, int32_t lh, uint16_t *__restrict__ col) {
+    const int lo = lh - 1;
+    const int H = 1 << lh;
+    const int64_t n = (int64_t)B << (2 * lo + 4);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(i & 15);
+        const int64_t m = i >> 4;
+        const int ox = (int)(m & ((1 << lo) - 1)), oy = (int)((m >> lo) & ((1 << lo) - 1));
+        const int64_t b = m >> (2 * lo);
+        const int y = 2 * oy - 1 + (kk >> 2), x = 2 * ox - 1 + (kk & 3);
+        uint2 v = make_uint2(0, 0);
+        if (y >= 0 && y < H && x >= 0 && x < H) v = reinterpret_cast<const uint2 *>(X)[(((b << lh) + y) << lh) + x];
+        reinterpret_cast<uint2 *>(col)[i] = v;
     }
 }
 
@@ -278,7 +297,7 @@ struct CnnLayer {
 };
 
 static void layer_table(CnnLayer L[6], int64_t *n_params) {
-    const int cin[6] = {8, 32, 64, 128, 256, 256}, cout[6] = {32, 64, 128, 256, 256, 64};
+    const int cin[6] = {4, 32, 64, 128, 256, 256}, cout[6] = {32, 64, 128, 256, 256, 64};
     const int ks[6] = {4, 4, 4, 4, 4, 1}, hin[6] = {256, 128, 64, 32, 16, 8};
     int64_t o = 0;
     for (int l = 0; l < 6; ++l) {
@@ -312,7 +331,7 @@ static CnnSizes cnn_sizes(int32_t B) {
     int64_t np;
     layer_table(L, &np);
     CnnSizes s{};
-    s.X[0] = (int64_t)B * 256 * 256 * 8;
+    s.X[0] = (int64_t)B * 256 * 256 * 4;
     for (int l = 0; l < 5; ++l) s.X[l + 1] = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2) * L[l].cout;
     s.col = 0;   // all five layers' im2col matrices (kept from the forward for the weight gradients)
     s.dx = (int64_t)B * 64 * 256;
@@ -401,8 +420,11 @@ cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStrea
         const int H = L[l].hin, Ho = H / 2;
         const int M = B * Ho * Ho;
         if (l > 0) col += (int64_t)B * (L[l - 1].hin / 2) * (L[l - 1].hin / 2) * L[l - 1].K;
-        k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, ilog2(H), ilog2(L[l].cin / 8),
-                                                                       col);
+        if (L[l].cin == 4)
+            k_im2col4<<<grid1d((int64_t)M * 16), 256, 0, st>>>(c.X[l], B, ilog2(H), col);
+        else
+            k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, ilog2(H),
+                                                                           ilog2(L[l].cin / 8), col);
         e = gemm(col, (int)L[l].K, c.wbf + L[l].w_off, (int)L[l].K, M, L[l].cout, (int)L[l].K,
                  GEMM_BIAS_RELU_BF16, nullptr, c.X[l + 1], L[l].cout, c.theta + L[l].b_off, 1, c.status, st);
     }

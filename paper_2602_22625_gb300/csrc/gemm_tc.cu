@@ -535,22 +535,36 @@ cudaError_t set_smem() {
 
 }  // namespace
 
+// The driver's tensor-map encoder is looked up once per process; the kernels'
+// shared-memory limits are raised once per device (each under its own
+// std::call_once, with that device current), so repeated and concurrent callers
+// neither race nor repeat the attribute calls.
 cudaError_t init_gemm_kernels() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
+    static std::once_flag encode_once;
+    static cudaError_t encode_err = cudaSuccess;
+    std::call_once(encode_once, [] {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
-        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (err == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn)) err = cudaErrorNotSupported;
+        encode_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (encode_err == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn)) encode_err = cudaErrorNotSupported;
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     });
-    cudaError_t e = err;
-    if (e == cudaSuccess) e = set_smem<32>();
-    if (e == cudaSuccess) e = set_smem<64>();
-    if (e == cudaSuccess) e = set_smem<128>();
-    if (e == cudaSuccess) e = set_smem<256>();
-    return e;
+    if (encode_err != cudaSuccess) return encode_err;
+    constexpr int kMaxDevices = 64;
+    static std::once_flag dev_once[kMaxDevices];
+    static cudaError_t dev_err[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(dev_once[dev], [dev] {
+        cudaError_t r = set_smem<32>();
+        if (r == cudaSuccess) r = set_smem<64>();
+        if (r == cudaSuccess) r = set_smem<128>();
+        if (r == cudaSuccess) r = set_smem<256>();
+        dev_err[dev] = r;
+    });
+    return dev_err[dev];
 }
 
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {

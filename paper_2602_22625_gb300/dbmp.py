@@ -424,7 +424,7 @@ def dbmp_proposer_activations(p, layer, batch):
     """Activations of layer 0..6 of the last forward (float32 numpy array)."""
     import numpy as np
     sides = (256, 128, 64, 32, 16, 8)
-    chans = (8, 32, 64, 128, 256, 256)
+    chans = (4, 32, 64, 128, 256, 256)
     shape = (batch * 64, 64) if layer == 6 else (batch, sides[layer], sides[layer], chans[layer])
     out = np.empty(shape, np.float32)
     _check(load().dbmp_proposer_activations(p, int(layer), out.ctypes.data, out.size))

@@ -279,5 +279,5 @@ def cnn_init(seed: int = 0) -> np.ndarray:
 
 #: (input channels padded, input channels used, output channels, kernel size):
 #: five 4x4 stride-2 convolutions with ReLU, then a 1x1 head (8 slots x 8 outputs)
-CNN_LAYERS = ((8, 3, 32, 4), (32, 32, 64, 4), (64, 64, 128, 4), (128, 128, 256, 4),
+CNN_LAYERS = ((4, 3, 32, 4), (32, 32, 64, 4), (64, 64, 128, 4), (128, 128, 256, 4),
               (256, 256, 256, 4), (256, 256, 64, 1))
