@@ -12,9 +12,10 @@ future work, Sec. S5, and shows that initialisation matters, Sec. 3.2.2):
 Weights are stored (Cout, K) with K ordered (ky, kx, ci), ci fastest.
 
 Mixed precision, mirrored from the GPU path so that both round at the same
-points: inputs, weights, post-ReLU activations, the backward's dZ tensors and the
-convolutions' input-gradient columns (before col2im sums them) are rounded to
-bfloat16 (round to nearest even); everything else is FP64 here.  With round=False
+points: inputs, weights, post-ReLU activations and the backward's dZ tensors are
+rounded to bfloat16 (round to nearest even); a convolution's input gradient is
+summed over all its (tap, channel) terms before the one rounding of the dZ it
+feeds; everything else is FP64 here.  With round=False
 the network is plain FP64 (used by the finite-difference pins).
 
 Output decoding (anchored parameterisation): cell (cy, cx), slot k, outputs o_j:
@@ -188,6 +189,5 @@ def backward(dO, cache):
         W, _ = params[li]
         grads[li] = (mm(dZ.T, cols[li]), dZ.sum(0))
         if li > 0:
-            dcol = R(mm(dZ, R(W)))
-            dX = col2im(dcol, acts[li].shape)
+            dX = col2im(mm(dZ, R(W)), acts[li].shape)
     return np.concatenate([np.concatenate([g[0].ravel(), g[1]]) for g in grads])

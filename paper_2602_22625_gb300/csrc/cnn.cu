@@ -3,16 +3,35 @@
 // optimisation.  (The paper leaves learned initialisation to future work, Sec. S5,
 // and shows that initialisation matters, Sec. 3.2.2.)
 //
-//   input   B x 256 x 256 x 8 bf16 (NHWC; channels 0-2 = 2 (I - 0.5), 3-7 = 0)
-//   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 8 -> 32 -> 64 -> 128 -> 256 -> 256
+//   input   B x 256 x 256 x 4 bf16 (NHWC; channels 0-2 = 2 (I - 0.5), 3 = 0)
+//   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 4 -> 32 -> 64 -> 128 -> 256 -> 256
 //   head    1x1 conv 256 -> 64 on the 8 x 8 map: 8 slots x 8 outputs per cell
 //
-// Every product is the tcgen05 GEMM of gemm_tc.cu (BF16 operands, FP32 accumulation):
-//   forward  X_l = relu(im2col(X_{l-1}) W_l^T + b_l)   (bias + ReLU fused, bf16 out)
-//   wgrad    dW_l = dZ_l^T im2col(X_{l-1})               (both operands read MN-major,
-//                                                          split-K with fp32 atomics)
-//   dgrad    dX_{l-1} = col2im(dZ_l W_l) masked by X_{l-1} > 0   (W_l read MN-major)
-// Weights are FP32 masters with BF16 copies; Adam updates the masters.
+// Every product is the tcgen05 GEMM of gemm_tc.cu (BF16 operands, FP32 accumulation).
+// conv1 runs on an explicit im2col matrix (K = 16 taps x 4 channels = 64).  conv2-5
+// are implicit GEMMs over activations kept in a blocked (space-to-depth) layout:
+//
+//   Xb[b][i][j][(sy*2 + sx)*C + c] = X[b][2i+sy-1][2j+sx-1][c]  (0 outside),
+//   i, j in [0, H/2], sy, sx in {0, 1}
+//
+// Tap (ky, kx) = (2dy + sy, 2dx + sx) of output (oy, ox) reads X[2oy-1+ky][2ox-1+kx] =
+// block (oy+dy, ox+dx), sub-pixel (sy, sx): the 4x4 / stride-2 conv is a 2x2 / stride-1
+// conv over the blocks with 4C channels, so one 64-wide K step is one block tap x 64
+// contiguous channels, read by a 4-D tensor copy (no im2col matrix in HBM; the four
+// reads of each block come from L2).  The previous layer's epilogue writes its output
+// straight into this layout (the padding entries stay zero from allocation).
+//   forward  X_l = relu(conv(X_{l-1}) + b_l)       (A = blocked X_{l-1}, B = W_l in the
+//                                                    blocked tap order; bias + ReLU fused)
+//   wgrad    dW_l = dZ_l^T conv-rows(X_{l-1})       (dZ MN-major, blocked X read MN-major,
+//                                                    split-K; columns written back in the
+//                                                    (ky, kx, c) order)
+//   dgrad    for each parity class (sy, sx): the input pixels (2i+1-sy, 2j+1-sx) get
+//            sum over (dy, dx, co) of dZ[i+1-sy-dy][j+1-sx-dx][co] W[co][2dy+sy][2dx+sx][c],
+//            four GEMMs of K = 4 Co in one launch; the epilogue applies the mask
+//            X_{l-1} > 0 and writes dZ_{l-1} (NHWC, bf16) in place: no column matrix,
+//            no col2im.
+// Weights are FP32 masters with BF16 copies (and the two rearranged copies above);
+// Adam updates the masters.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -68,67 +87,41 @@ __global__ void k_im2col4(const uint16_t *__restrict__ X, int32_t B, int32_t lh,
 
 // The network's sides and channel counts are powers of two; the index arithmetic
 // below uses their log2 (shifts and masks instead of 64-bit divisions).
-//
-// col[m][(ky*4 + kx)*C + c] = X[b][2oy-1+ky][2ox-1+kx][c] (0 outside), m = (b, oy, ox),
-// H = W = 2^lh, C = 8 * 2^lc8; one 16-byte chunk (8 channels) per thread.
-__global__ void k_im2col(const uint16_t *__restrict__ X, int32_t B, int32_t lh, int32_t lc8,
-                         uint16_t *__restrict__ col) {
-    const int lo = lh - 1;   // log2 of the output side
-    const int H = 1 << lh, C8 = 1 << lc8;
-    const int64_t n = ((int64_t)B << (2 * lo + 4 + lc8));
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c8 = (int)(i & (C8 - 1));
-        const int kk = (int)((i >> lc8) & 15);
-        const int64_t m = i >> (lc8 + 4);
-        const int ox = (int)(m & ((1 << lo) - 1)), oy = (int)((m >> lo) & ((1 << lo) - 1));
-        const int64_t b = m >> (2 * lo);
-        const int y = 2 * oy - 1 + (kk >> 2), x = 2 * ox - 1 + (kk & 3);
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (y >= 0 && y < H && x >= 0 && x < H)
-            v = reinterpret_cast<const uint4 *>(X + ((((b << lh) + y) << lh) + x) * (8 << lc8))[c8];
-        reinterpret_cast<uint4 *>(col)[i] = v;
-    }
-}
 
-// dX[b][y][x][c] = sum over (ky, kx) with 2oy-1+ky = y, 2ox-1+kx = x of
-// dcol[(b,oy,ox)][(ky*4+kx)*C + c] (bf16, summed in fp32); then dZ = X > 0 ? bf16(dX) : 0.
-// H = W = 2^lh, C = 2^lc (>= 4); four channels per thread (8-byte loads of dcol).
-__global__ void k_col2im_mask(const uint16_t *__restrict__ dcol, const uint16_t *__restrict__ X, int32_t B,
-                              int32_t lh, int32_t lc, uint16_t *__restrict__ dZ) {
-    const int lo = lh - 1, Ho = 1 << lo, C = 1 << lc;
-    const int64_t n4 = ((int64_t)B << (2 * lh + lc)) >> 2;
-    for (int64_t i4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i4 < n4;
-         i4 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i4 << 2;
-        const int c = (int)(i & (C - 1));
-        const int64_t p = i >> lc;
-        const int x = (int)(p & ((1 << lh) - 1)), y = (int)((p >> lh) & ((1 << lh) - 1));
-        const int64_t b = p >> (2 * lh);
-        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        // ky = y + 1 - 2 oy in [0, 4): two candidates of matching parity
-        for (int ky = (y + 1) & 1; ky < 4; ky += 2) {
-            const int oy = (y + 1 - ky) >> 1;
-            if (oy < 0 || oy >= Ho) continue;
-            for (int kx = (x + 1) & 1; kx < 4; kx += 2) {
-                const int ox = (x + 1 - kx) >> 1;
-                if (ox < 0 || ox >= Ho) continue;
-                const uint2 d = *reinterpret_cast<const uint2 *>(
-                    dcol + ((((b << lo) + oy) << lo) + ox) * ((int64_t)16 << lc) + ((ky * 4 + kx) << lc) + c);
-                acc.x += bf2f((uint16_t)(d.x & 0xffffu));
-                acc.y += bf2f((uint16_t)(d.x >> 16));
-                acc.z += bf2f((uint16_t)(d.y & 0xffffu));
-                acc.w += bf2f((uint16_t)(d.y >> 16));
-            }
+// Rearranged bf16 weights of convs 2-5 (layer table t), from the (ky, kx, c) copies:
+//   wf[co][k'],            k'  = (dy*2 + dx)*4C + (sy*2 + sx)*C + c   (forward, blocked taps)
+//   wd[cls*C + c][k''],    k'' = (dy*2 + dx)*Co + co, cls = sy*2 + sx (input gradient)
+// both = W[co][(2dy+sy)*4 + 2dx+sx][c].
+struct ConvWeightTable {
+    int64_t w_off[4], start[5];
+    int32_t lc[4], lco[4];   // log2 C, log2 Co
+};
+__global__ void k_conv_weights(const uint16_t *__restrict__ wbf, ConvWeightTable t, uint16_t *__restrict__ wf,
+                               uint16_t *__restrict__ wd) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.start[4];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (i >= t.start[1]) + (i >= t.start[2]) + (i >= t.start[3]);
+        const int64_t e = i - t.start[l];
+        const int lc = t.lc[l], lco = t.lco[l];
+        const int C = 1 << lc;
+        const uint16_t *W = wbf + t.w_off[l];
+        // forward copy: e = co * 16C + k'
+        {
+            const int64_t co = e >> (lc + 4);
+            const int kp = (int)(e & ((16 << lc) - 1));
+            const int tap = kp >> (lc + 2), s = (kp >> lc) & 3, c = kp & (C - 1);
+            const int ky = 2 * (tap >> 1) + (s >> 1), kx = 2 * (tap & 1) + (s & 1);
+            wf[t.w_off[l] + e] = W[(co << (lc + 4)) + ((ky * 4 + kx) << lc) + c];
         }
-        const uint2 xv = *reinterpret_cast<const uint2 *>(X + i);
-        const float a[4] = {acc.x, acc.y, acc.z, acc.w};
-        const uint16_t xs[4] = {(uint16_t)(xv.x & 0xffffu), (uint16_t)(xv.x >> 16), (uint16_t)(xv.y & 0xffffu),
-                                (uint16_t)(xv.y >> 16)};
-        uint16_t o[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) o[k] = bf2f(xs[k]) > 0.0f ? f2bf(a[k]) : (uint16_t)0;
-        *reinterpret_cast<uint2 *>(dZ + i) = make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
-                                                        (uint32_t)o[2] | ((uint32_t)o[3] << 16));
+        // input-gradient copy: e = (cls * C + c) * 4Co + k''
+        {
+            const int64_t row = e >> (lco + 2);
+            const int kpp = (int)(e & ((4 << lco) - 1));
+            const int cls = (int)(row >> lc), c = (int)(row & (C - 1));
+            const int tap = kpp >> lco, co = kpp & ((1 << lco) - 1);
+            const int ky = 2 * (tap >> 1) + (cls >> 1), kx = 2 * (tap & 1) + (cls & 1);
+            wd[t.w_off[l] + e] = W[((int64_t)co << (lc + 4)) + ((ky * 4 + kx) << lc) + c];
+        }
     }
 }
 
@@ -326,21 +319,27 @@ struct CnnSizes {
     int64_t X[6], col, dx, dz;
 };
 
+// Images held by the buffers that 4-D tensor copies read: a box may span two images.
+static int32_t held_images(int32_t B) { return B < 2 ? 2 : B; }
+
 static CnnSizes cnn_sizes(int32_t B) {
     CnnLayer L[6];
     int64_t np;
     layer_table(L, &np);
+    const int64_t nb = held_images(B);
     CnnSizes s{};
     s.X[0] = (int64_t)B * 256 * 256 * 4;
-    for (int l = 0; l < 5; ++l) s.X[l + 1] = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2) * L[l].cout;
-    s.col = 0;   // all five layers' im2col matrices (kept from the forward for the weight gradients)
-    s.dx = (int64_t)B * 64 * 256;
-    s.dz = (int64_t)B * 64 * 64;
+    for (int l = 1; l < 5; ++l) {   // blocked: (H/2 + 1)^2 blocks of 4C channels
+        const int64_t hb = L[l].hin / 2 + 1;
+        s.X[l] = nb * hb * hb * 4 * L[l].cin;
+    }
+    s.X[5] = nb * 64 * 256;
+    s.col = (int64_t)B * 128 * 128 * L[0].K;   // the first conv's im2col matrix
+    s.dx = nb * 64 * 256;
+    s.dz = nb * 64 * 64;
     for (int l = 0; l < 5; ++l) {
-        const int64_t M = (int64_t)B * (L[l].hin / 2) * (L[l].hin / 2);
-        s.col += M * L[l].K;
-        if (l > 0) s.dx = s.dx > M * L[l].K ? s.dx : M * L[l].K;
-        s.dz = s.dz > M * L[l].cout ? s.dz : M * L[l].cout;
+        const int64_t Ho = L[l].hin / 2;
+        s.dz = std::max<int64_t>(s.dz, nb * Ho * Ho * L[l].cout);
     }
     return s;
 }
@@ -348,7 +347,7 @@ static CnnSizes cnn_sizes(int32_t B) {
 size_t cnn_bytes(int32_t B) {
     const CnnSizes s = cnn_sizes(B);
     int64_t np = cnn_num_params();
-    size_t b = 4 * sizeof(float) * np + 2 * sizeof(uint16_t) * np;
+    size_t b = 4 * sizeof(float) * np + 3 * sizeof(uint16_t) * np;
     for (int l = 0; l < 6; ++l) b += sizeof(uint16_t) * s.X[l];
     b += 2 * sizeof(float) * (size_t)B * 64 * 64 + sizeof(float) * s.dx;
     b += sizeof(uint16_t) * s.col + 2 * sizeof(uint16_t) * s.dz + sizeof(int32_t) * 4;
@@ -360,6 +359,7 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
     const int64_t np = cnn_num_params();
     c = CnnBuffers{};
     c.max_batch = B;
+    c.nb = held_images(B);
     cudaError_t e = cudaSuccess;
     auto A = [&](void **p, size_t n) {
         if (e == cudaSuccess) e = cudaMalloc(p, n > 0 ? n : 16);
@@ -369,6 +369,8 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
     A((void **)&c.m, sizeof(float) * np);
     A((void **)&c.v, sizeof(float) * np);
     A((void **)&c.wbf, sizeof(uint16_t) * np);
+    A((void **)&c.wf, sizeof(uint16_t) * np);
+    A((void **)&c.wd, sizeof(uint16_t) * np);
     for (int l = 0; l < 6; ++l) A((void **)&c.X[l], sizeof(uint16_t) * s.X[l]);
     A((void **)&c.O, sizeof(float) * B * 64 * 64);
     A((void **)&c.dO, sizeof(float) * B * 64 * 64);
@@ -380,32 +382,61 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
     if (e == cudaSuccess) e = cudaMemset(c.status, 0, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(c.m, 0, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMemset(c.v, 0, sizeof(float) * np);
+    // the blocked activations' padding entries (never written) read as zeros; so do the
+    // images past the batch that a two-image box may touch
+    for (int l = 1; l < 5 && e == cudaSuccess; ++l) e = cudaMemset(c.X[l], 0, sizeof(uint16_t) * s.X[l]);
+    if (e == cudaSuccess) e = cudaMemset(c.X[5], 0, sizeof(uint16_t) * s.X[5]);
+    if (e == cudaSuccess) e = cudaMemset(c.dz, 0, sizeof(uint16_t) * s.dz);
+    if (e == cudaSuccess) e = cudaMemset(c.dzp, 0, sizeof(uint16_t) * s.dz);
     if (e == cudaSuccess) e = init_gemm_kernels();
     return e;
 }
 
 void cnn_free(CnnBuffers &c) {
-    void *ps[] = {c.theta, c.grad, c.m, c.v, c.wbf, c.X[0], c.X[1], c.X[2], c.X[3], c.X[4], c.X[5],
+    void *ps[] = {c.theta, c.grad, c.m, c.v, c.wbf, c.wf, c.wd, c.X[0], c.X[1], c.X[2], c.X[3], c.X[4], c.X[5],
                   c.O, c.dO, c.dx, c.col, c.dz, c.dzp, c.status};
     for (void *p : ps)
         if (p) cudaFree(p);
     c = CnnBuffers{};
 }
 
+// The rearranged weight copies of convs 2-5 from the bf16 copies.
+static cudaError_t conv_weights(CnnBuffers &c, cudaStream_t st) {
+    CnnLayer L[6];
+    int64_t np;
+    layer_table(L, &np);
+    ConvWeightTable t{};
+    t.start[0] = 0;
+    for (int i = 0; i < 4; ++i) {
+        const CnnLayer &l = L[i + 1];
+        t.w_off[i] = l.w_off;
+        t.lc[i] = ilog2(l.cin);
+        t.lco[i] = ilog2(l.cout);
+        t.start[i + 1] = t.start[i] + l.K * l.cout;
+    }
+    k_conv_weights<<<grid1d(t.start[4]), 256, 0, st>>>(c.wbf, t, c.wf, c.wd);
+    return cudaGetLastError();
+}
+
 // After new master weights: bf16 copies for the products.
 cudaError_t cnn_sync_weights(CnnBuffers &c, cudaStream_t st) {
     const int64_t np = cnn_num_params();
     k_to_bf16<<<grid1d(np), 256, 0, st>>>(c.theta, np, c.wbf);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : conv_weights(c, st);
 }
 
 // mode: a GemmMode, plus GEMM_A_MN / GEMM_B_MN when an operand is given MN-major.
+static GemmArgs gemm_args(const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N, int K, int mode,
+                          float *Cf, uint16_t *Cb, int ldc, const float *bias, int32_t *status) {
+    GemmArgs g{A,    B,    M,  N,  K,   lda,  ldb,   ldc, mode & 15, (mode & GEMM_A_MN) != 0, (mode & GEMM_B_MN) != 0,
+               Cf,   Cb,   bias, status};
+    return g;
+}
 static cudaError_t gemm(const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N, int K, int mode,
                         float *Cf, uint16_t *Cb, int ldc, const float *bias, int split, int32_t *status,
                         cudaStream_t st) {
-    GemmArgs g{A,    B,    M,  N,  K,   lda,  ldb,   ldc, mode & 15, (mode & GEMM_A_MN) != 0, (mode & GEMM_B_MN) != 0,
-               Cf,   Cb,   bias, status};
-    return launch_gemm(g, split, st);
+    return launch_gemm(gemm_args(A, lda, B, ldb, M, N, K, mode, Cf, Cb, ldc, bias, status), split, st);
 }
 
 // Forward of B images (fp32, 3 x 256 x 256 each, concatenated) into c.O.
@@ -414,19 +445,26 @@ cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStrea
     int64_t np;
     layer_table(L, &np);
     k_pack_input<<<grid1d((int64_t)B * 65536), 256, 0, st>>>(images, B, c.X[0]);
+    k_im2col4<<<grid1d((int64_t)B * 128 * 128 * 16), 256, 0, st>>>(c.X[0], B, 8, c.col);
     cudaError_t e = cudaGetLastError();
-    uint16_t *col = c.col;
     for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
-        const int H = L[l].hin, Ho = H / 2;
-        const int M = B * Ho * Ho;
-        if (l > 0) col += (int64_t)B * (L[l - 1].hin / 2) * (L[l - 1].hin / 2) * L[l - 1].K;
-        if (L[l].cin == 4)
-            k_im2col4<<<grid1d((int64_t)M * 16), 256, 0, st>>>(c.X[l], B, ilog2(H), col);
-        else
-            k_im2col<<<grid1d((int64_t)M * 16 * (L[l].cin / 8)), 256, 0, st>>>(c.X[l], B, ilog2(H),
-                                                                           ilog2(L[l].cin / 8), col);
-        e = gemm(col, (int)L[l].K, c.wbf + L[l].w_off, (int)L[l].K, M, L[l].cout, (int)L[l].K,
-                 GEMM_BIAS_RELU_BF16, nullptr, c.X[l + 1], L[l].cout, c.theta + L[l].b_off, 1, c.status, st);
+        const int Ho = L[l].hin / 2;
+        const int M = B * Ho * Ho, Co = L[l].cout, K = (int)L[l].K;
+        GemmArgs g = l == 0 ? gemm_args(c.col, K, c.wbf + L[l].w_off, K, M, Co, K, GEMM_BIAS_RELU_BF16, nullptr,
+                                        c.X[1], Co, c.theta + L[l].b_off, c.status)
+                            : gemm_args(c.X[l], 0, c.wf + L[l].w_off, K, M, Co, K, GEMM_BIAS_RELU_BF16, nullptr,
+                                        c.X[l + 1], Co, c.theta + L[l].b_off, c.status);
+        if (l > 0) {
+            g.a_conv = CONV_BLOCKED;
+            g.conv_chan = 4 * L[l].cin;
+            g.conv_side = Ho;
+            g.conv_batch = c.nb;
+        }
+        if (l < 4) {   // the next conv's input, blocked
+            g.out_kind = OUT_BLOCKED;
+            g.out_side = Ho;
+        }
+        e = launch_gemm(g, 1, st);
     }
     if (e == cudaSuccess)
         e = gemm(c.X[5], 256, c.wbf + L[5].w_off, 256, B * 64, 64, 256, GEMM_BIAS_F32, c.O, nullptr, 64,
@@ -437,19 +475,35 @@ cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStrea
 int64_t cnn_activation_count(int32_t layer, int32_t B) {
     if (layer < 0 || layer > 6 || B < 1) return -1;
     if (layer == 6) return (int64_t)B * 64 * 64;
-    return cnn_sizes(B).X[layer];
+    if (layer == 0) return (int64_t)B * 256 * 256 * 4;
+    CnnLayer L[6];
+    int64_t np;
+    layer_table(L, &np);
+    const int64_t H = L[layer - 1].hin / 2;
+    return (int64_t)B * H * H * L[layer - 1].cout;
 }
 
 cudaError_t cnn_activation(const CnnBuffers &c, int32_t layer, int32_t B, float *host) {
     const int64_t n = cnn_activation_count(layer, B);
     if (layer == 6) return cudaMemcpy(host, c.O, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    CnnLayer L[6];
+    int64_t np;
+    layer_table(L, &np);
+    const bool blocked = layer >= 1 && layer <= 4;
+    const int64_t H = layer == 0 ? 256 : L[layer - 1].hin / 2, C = n / ((int64_t)B * H * H), hb = H / 2 + 1;
+    const int64_t stored = blocked ? (int64_t)B * hb * hb * 4 * C : n;
     // bf16 bits are the upper half of the float32 they round to
-    uint16_t *tmp = static_cast<uint16_t *>(malloc(sizeof(uint16_t) * (size_t)n));
+    uint16_t *tmp = static_cast<uint16_t *>(malloc(sizeof(uint16_t) * (size_t)stored));
     if (!tmp) return cudaErrorMemoryAllocation;
-    const cudaError_t e = cudaMemcpy(tmp, c.X[layer], sizeof(uint16_t) * n, cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaMemcpy(tmp, c.X[layer], sizeof(uint16_t) * stored, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) {
         for (int64_t i = 0; i < n; ++i) {
-            const uint32_t u = (uint32_t)tmp[i] << 16;
+            int64_t src = i;
+            if (blocked) {   // NHWC element (b, y, x, ch) from block ((y+1)/2, (x+1)/2)
+                const int64_t ch = i % C, p = i / C, x = p % H, y = (p / H) % H, b = p / (H * H);
+                src = ((b * hb + (y + 1) / 2) * hb + (x + 1) / 2) * 4 * C + (((y + 1) & 1) * 2 + ((x + 1) & 1)) * C + ch;
+            }
+            const uint32_t u = (uint32_t)tmp[src] << 16;
             memcpy(host + i, &u, sizeof u);
         }
     }
@@ -471,7 +525,8 @@ static int split_for(int M, int N, int K) {
 }
 
 // Loss and gradient w.r.t. all parameters into c.grad (overwritten).  Reads the
-// activations and im2col matrices the forward of the same batch left in c.
+// activations and the first conv's im2col matrix that the forward of the same batch
+// left in c.
 cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, double *loss, cudaStream_t st) {
     CnnLayer L[6];
     int64_t np;
@@ -489,23 +544,36 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
         e = gemm(c.dz, 64, c.wbf + L[5].w_off, 256, M6, 256, 64, GEMM_STORE_F32 | GEMM_B_MN, c.dx, nullptr, 256,
                  nullptr, 1, c.status, st);
     k_mask_to_bf16<<<grid1d((int64_t)M6 * 256), 256, 0, st>>>(c.dx, c.X[5], (int64_t)M6 * 256, c.dz);
-    int64_t col_off[5];
-    col_off[0] = 0;
-    for (int l = 1; l < 5; ++l) col_off[l] = col_off[l - 1] + (int64_t)B * (L[l - 1].hin / 2) * (L[l - 1].hin / 2) * L[l - 1].K;
     for (int l = 4; l >= 0 && e == cudaSuccess; --l) {
-        const int H = L[l].hin, Ho = H / 2, M = B * Ho * Ho;
-        const int K = (int)L[l].K, Co = L[l].cout;
-        // the forward of this batch left im2col(X_{l-1}) at col + col_off[l]
-        e = gemm(c.dz, Co, c.col + col_off[l], K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off, nullptr,
-                 K, nullptr, split_for(Co, K, M), c.status, st);
+        const int Ho = L[l].hin / 2, M = B * Ho * Ho;
+        const int K = (int)L[l].K, Co = L[l].cout, C = L[l].cin;
+        if (l == 0) {   // wgrad from the im2col matrix the forward left in c.col
+            e = gemm(c.dz, Co, c.col, K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off,
+                     nullptr, K, nullptr, split_for(Co, K, M), c.status, st);
+        } else {        // wgrad with B = the blocked input, columns back in (ky, kx, c) order
+            GemmArgs g = gemm_args(c.dz, Co, c.X[l], 0, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN,
+                                   c.grad + L[l].w_off, nullptr, K, nullptr, c.status);
+            g.b_conv = CONV_BLOCKED;
+            g.conv_chan = 4 * C;
+            g.conv_side = Ho;
+            g.conv_batch = c.nb;
+            g.col_remap = C;
+            e = launch_gemm(g, split_for(Co, K, M), st);
+        }
         k_colsum<uint16_t><<<colsum_blocks(M, Co, 2), 256, 0, st>>>(c.dz, M, Co, c.grad + L[l].b_off);
         if (l == 0 || e != cudaSuccess) break;
-        // the input-gradient columns in bf16 (the product buffer holds twice as many fp32)
-        uint16_t *dcol = reinterpret_cast<uint16_t *>(c.dx);
-        e = gemm(c.dz, Co, c.wbf + L[l].w_off, K, M, K, Co, GEMM_STORE_BF16 | GEMM_B_MN, nullptr, dcol, K, nullptr, 1,
-                 c.status, st);
-        k_col2im_mask<<<grid1d((int64_t)B * H * H * L[l].cin / 4), 256, 0, st>>>(dcol, c.X[l], B, ilog2(H),
-                                                                                   ilog2(L[l].cin), c.dzp);
+        // dgrad: four parity classes, masked by the layer's input, into dZ_{l-1} (NHWC)
+        GemmArgs g = gemm_args(c.dz, 0, c.wd + L[l].w_off, 4 * Co, M, C, 4 * Co, GEMM_STORE_BF16, nullptr, c.dzp,
+                               C, nullptr, c.status);
+        g.a_conv = CONV_DGRAD;
+        g.conv_chan = Co;
+        g.conv_side = Ho;
+        g.conv_batch = c.nb;
+        g.groups = 4;
+        g.out_kind = OUT_DGRAD;
+        g.out_side = Ho;
+        g.mask = c.X[l];
+        e = launch_gemm(g, 1, st);
         uint16_t *t = c.dz;
         c.dz = c.dzp;
         c.dzp = t;
@@ -517,7 +585,8 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
 cudaError_t cnn_adam(CnnBuffers &c, float lr, float b1, float b2, float eps, int32_t t, cudaStream_t st) {
     const int64_t np = cnn_num_params();
     k_adam_flat<<<grid1d(np), 256, 0, st>>>(c.theta, c.grad, c.m, c.v, np, lr, b1, b2, eps, t, c.wbf);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : conv_weights(c, st);
 }
 
 }  // namespace dbmp

@@ -166,7 +166,38 @@ struct GemmArgs {
     int32_t split;      // set by the launcher: K splits (partial tiles added into C)
     int32_t stall;      // test hook: the producer issues no copies, so the MMA and
                         // epilogue waits run out and status becomes DBMP_ERR_TIMEOUT
+    // Implicit convolution (the proposal network's 4x4 / stride-2 / pad-1 layers).  A
+    // conv operand is read with 4-D tensor copies of an activation tensor instead of
+    // 2-D copies of a matrix; pixel rows m = (b, oy, ox) of the Ho x Ho output grid
+    // (ox fastest), one K step = one tap (dy, dx) of a 2 x 2 stencil x 64 channels:
+    //   CONV_BLOCKED  source Xb [nb][Ho+1][Ho+1][chan] in the blocked layout (below);
+    //                 element (m, tap*chan + q) = Xb[b][oy+dy][ox+dx][q].  As A (K-major)
+    //                 of the forward; as B (MN-major, K = pixels) of the weight gradient.
+    //   CONV_DGRAD    source dZ [nb][Ho][Ho][chan] (NHWC); parity class g = (sy, sx) of
+    //                 the group: element (m, tap*chan + q) = dZ[b][oy+1-sy-dy][ox+1-sx-dx][q]
+    //                 (zero outside).  As A of the input gradient.
+    int32_t a_conv = 0, b_conv = 0;   // ConvKind of the operand (CONV_NONE: a plain matrix)
+    int32_t conv_chan = 0;            // channels of the source tensor (multiple of 64)
+    int32_t conv_side = 0;            // Ho, a power of two >= 8
+    int32_t conv_batch = 0;           // images in the source tensor (>= 2: a box may span two)
+    int32_t groups = 1;               // independent products: tile groups, B rows N apart
+    // Epilogue row placement (per-lane stores; the TMA-store path is plain only):
+    //   OUT_BLOCKED  row m = (b, y, x) of an S x S grid goes to the blocked layout of the
+    //                next layer's input: [nb][S/2+1][S/2+1][4N], element
+    //                ((b, (y+1)/2, (x+1)/2), ((y+1)%2 * 2 + (x+1)%2) * N + n);
+    //   OUT_DGRAD    row m = (b, i, j) of group g = (sy, sx) is pixel (2i+1-sy, 2j+1-sx) of
+    //                the NHWC [nb][2S][2S][N] output; with `mask` (the blocked input of the
+    //                layer), a value whose input element is not > 0 is written as 0.
+    int32_t out_kind = 0;
+    int32_t out_side = 0;             // S
+    const uint16_t *mask = nullptr;
+    // Column placement of a weight gradient computed in the blocked tap order: column
+    // n = tap*4C + (sy*2 + sx)*C + c is written at ((2dy + sy)*4 + 2dx + sx)*C + c
+    // (0: columns in place).
+    int32_t col_remap = 0;            // C
 };
+enum ConvKind { CONV_NONE = 0, CONV_BLOCKED = 1, CONV_DGRAD = 2 };
+enum OutKind { OUT_PLAIN = 0, OUT_BLOCKED = 1, OUT_DGRAD = 2 };
 
 cudaError_t init_gemm_kernels();
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st);
@@ -176,11 +207,15 @@ cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st);
 // ---------------------------------------------------------------------------
 struct CnnBuffers {
     int32_t max_batch;
+    int32_t nb;                    // images the activation buffers hold (max_batch, at least 2)
     float *theta, *grad, *m, *v;   // fp32 master parameters, gradient, Adam moments
-    uint16_t *wbf;                 // bf16 copies of the weights
-    uint16_t *X[6];                // activations (NHWC bf16): input and five conv outputs
-    float *O, *dO, *dx;            // head outputs, their gradient, fp32 product buffer
-    uint16_t *col, *dz, *dzp;      // im2col matrices of the five convs, conv output gradients (two buffers)
+    uint16_t *wbf;                 // bf16 copies of the weights, K in (ky, kx, c) order
+    uint16_t *wf, *wd;             // convs 2-5: forward weights in blocked tap order, and the
+                                   // input-gradient weights per parity class (at wbf's offsets)
+    uint16_t *X[6];                // activations: X[0] the input (NHWC, 4 channels), X[1..4]
+                                   // in the blocked layout, X[5] NHWC
+    float *O, *dO, *dx;            // head outputs, their gradient, the head's input gradient
+    uint16_t *col, *dz, *dzp;      // im2col matrix of the first conv, conv output gradients (two buffers)
     int32_t *status;
 };
 

@@ -115,6 +115,67 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// 4-D tensor copy global -> shared (coordinates innermost first), completing `bar`'s
+// transaction count.  Coordinates outside the tensor read zeros.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Coordinates of the 4-D copy of a conv operand: channel index `chan` (a multiple of
+// 64: tap chan / conv_chan, channels chan % conv_chan ...) and first pixel row `row`
+// (the box covers whole output rows of the Ho x Ho grid), for parity group grp.
+__device__ __forceinline__ void conv_coords(const GemmArgs &g, int kind, int chan, int row, int grp, int &c0,
+                                            int &c1, int &c2, int &c3) {
+    const int tap = chan / g.conv_chan;
+    const int dy = tap >> 1, dx = tap & 1;
+    const int hw = g.conv_side * g.conv_side;
+    const int b = row / hw;
+    const int oy = (row - b * hw) / g.conv_side;
+    c0 = chan - tap * g.conv_chan;
+    c3 = b;
+    if (kind == CONV_BLOCKED) {
+        c1 = dx;
+        c2 = oy + dy;
+    } else {   // CONV_DGRAD: rows and columns one block up and left per parity
+        c1 = 1 - (grp & 1) - dx;
+        c2 = oy + 1 - (grp >> 1) - dy;
+    }
+}
+
+// Column of the weight gradient's canonical (ky, kx, c) order for column n of the
+// blocked tap order (GemmArgs::col_remap); runs of C columns stay contiguous.
+__device__ __forceinline__ int remap_col(int n, int C) {
+    if (C == 0) return n;
+    const int tap = n / (4 * C), r = n - tap * 4 * C;
+    const int s = r / C, c = r - s * C;
+    const int ky = 2 * (tap >> 1) + (s >> 1), kx = 2 * (tap & 1) + (s & 1);
+    return (ky * 4 + kx) * C + c;
+}
+
+// Element offset of output row `row` (column 0) and of its mask row (OUT_DGRAD).
+__device__ __forceinline__ size_t out_row_offset(const GemmArgs &g, int row, int grp, size_t &moff) {
+    moff = 0;
+    if (g.out_kind == OUT_PLAIN) return (size_t)row * g.ldc;
+    const int S = g.out_side;
+    const int xj = row % S, t = row / S;
+    const int yi = t % S, b = t / S;
+    const size_t N = (size_t)g.N;
+    if (g.out_kind == OUT_BLOCKED) {
+        const int hb = S / 2 + 1;
+        return (((size_t)b * hb + ((yi + 1) >> 1)) * hb + ((xj + 1) >> 1)) * 4 * N +
+               (size_t)((((yi + 1) & 1) << 1) + ((xj + 1) & 1)) * N;
+    }
+    const int sy = grp >> 1, sx = grp & 1;
+    const int H = 2 * S, y = 2 * yi + 1 - sy, x = 2 * xj + 1 - sx;
+    moff = (((size_t)b * (S + 1) + yi + 1 - sy) * (S + 1) + xj + 1 - sx) * 4 * N + (size_t)grp * N;
+    return (((size_t)b * H + y) * H + x) * N;
+}
+
 // 2-D tensor store / reduce-add shared -> global of one box (bulk async-group).
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
@@ -226,13 +287,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tiles_m = (g.M + kBM - 1) / kBM, tiles_n = (g.N + BN - 1) / BN;
     const int kt_total = g.K / kBK;
     const int kt_per = (kt_total + g.split - 1) / g.split;
-    const int n_tiles = tiles_m * tiles_n * g.split;
-    // tile t -> output origin (m0, n0) and K steps [kt0, kt0 + T)
-    auto decode = [&](int t, int &m0, int &n0, int &kt0, int &T) {
+    const int n_tiles = tiles_m * tiles_n * g.split * g.groups;
+    // tile t -> output origin (m0, n0), K steps [kt0, kt0 + T) and group grp
+    auto decode = [&](int t, int &m0, int &n0, int &kt0, int &T, int &grp) {
         const int tm = t % tiles_m, r = t / tiles_m;
         m0 = tm * kBM;
         n0 = (r % tiles_n) * BN;
-        kt0 = (r / tiles_n) * kt_per;
+        const int r2 = r / tiles_n;
+        kt0 = (r2 % g.split) * kt_per;
+        grp = r2 / g.split;
         T = max(0, min(kt_per, kt_total - kt0));
     };
 
@@ -269,24 +332,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         int s = 0;
         uint32_t ph = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-            int m0, n0, kt0, T;
-            decode(t, m0, n0, kt0, T);
+            int m0, n0, kt0, T, grp;
+            decode(t, m0, n0, kt0, T, grp);
             for (int i = 0; i < T && !g.stall; ++i) {
                 if (u >= (uint32_t)S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1)) abort_flag = 1;
                 if (*(volatile int *)&abort_flag) break;
                 const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);
                 const int k = (kt0 + i) * kBK;
                 mbar_expect_tx(fb, C::STAGE);
-                if (g.a_mn) {
+                if (g.a_conv) {
+                    int c0, c1, c2, c3;
+                    conv_coords(g, g.a_conv, k, m0, grp, c0, c1, c2, c3);
+                    tma_load_4d(sa, &tmA, c0, c1, c2, c3, fb);
+                } else if (g.a_mn) {
                     for (int j = 0; j < kBM / 64; ++j) tma_load_2d(sa + j * 8192, &tmA, m0 + 64 * j, k, fb);
                 } else {
                     tma_load_2d(sa, &tmA, k, m0, fb);
                 }
-                if (g.b_mn) {
+                if (g.b_conv) {   // MN-major: 64 channels x 64 pixel rows per box
+                    for (int j = 0; j < BN / 64; ++j) {
+                        int c0, c1, c2, c3;
+                        conv_coords(g, g.b_conv, n0 + 64 * j, k, grp, c0, c1, c2, c3);
+                        tma_load_4d(sa + C::A_BYTES + j * 8192, &tmB, c0, c1, c2, c3, fb);
+                    }
+                } else if (g.b_mn) {
                     for (int j = 0; j < BN / 64; ++j)
                         tma_load_2d(sa + C::A_BYTES + j * 8192, &tmB, n0 + 64 * j, k, fb);
                 } else {
-                    tma_load_2d(sa + C::A_BYTES, &tmB, k, n0, fb);
+                    tma_load_2d(sa + C::A_BYTES, &tmB, k, grp * g.N + n0, fb);
                 }
                 ++u;
                 if (++s == S) s = 0, ph ^= 1;
@@ -305,8 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         int s = 0, lt = 0;
         uint32_t ph = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-            int m0, n0, kt0, T;
-            decode(t, m0, n0, kt0, T);
+            int m0, n0, kt0, T, grp;
+            decode(t, m0, n0, kt0, T, grp);
             if (T == 0) continue;
             const int b = lt & 1;
             if (lt >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1)) abort_flag = 1;
@@ -341,8 +414,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         unsigned char *box0p = smem + S * C::STAGE + q * 2 * kStageBox;
         int buf = 0, lt = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-            int m0, n0, kt0, T;
-            decode(t, m0, n0, kt0, T);
+            int m0, n0, kt0, T, grp;
+            decode(t, m0, n0, kt0, T, grp);
             if (T == 0) continue;
             const int b = lt & 1;
             bool ok = mbar_wait(smem_u32(&acc_full[b]), (lt >> 1) & 1);
@@ -395,15 +468,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __syncwarp();
                     if (lane == 0) {
                         const uint32_t src = box0 + (uint32_t)(buf * kStageBox);
+                        const int x = remap_col(n0 + c0, g.col_remap);
                         if (g.mode == GEMM_ATOMIC_F32)
-                            tma_reduce_add_2d(&tmC, n0 + c0, m0 + q * 32, src);
+                            tma_reduce_add_2d(&tmC, x, m0 + q * 32, src);
                         else
-                            tma_store_2d(&tmC, n0 + c0, m0 + q * 32, src);
+                            tma_store_2d(&tmC, x, m0 + q * 32, src);
                         bulk_commit();
                     }
                 }
             } else {
                 const int row = m0 + q * 32 + lane;
+                size_t moff;
+                const size_t ooff = row < g.M ? out_row_offset(g, row, grp, moff) : 0;
                 for (int c0 = 0; c0 < BN; c0 += 16) {
                     float v[16];
                     tmem_ld16(trow + c0, v);
@@ -411,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int nb = n0 + c0;
                     const bool full16 = nb + 16 <= g.N;
                     if (g.mode == GEMM_STORE_F32 || g.mode == GEMM_BIAS_F32) {
-                        float *out = g.Cf + (size_t)row * g.ldc + nb;
+                        float *out = g.Cf + ooff + nb;
                         if (g.mode == GEMM_BIAS_F32) {
 #pragma unroll
                             for (int i = 0; i < 16; ++i) v[i] += nb + i < g.N ? g.bias[nb + i] : 0.0f;
@@ -427,12 +503,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 if (nb + i < g.N) out[i] = v[i];
                         }
                     } else if (g.mode == GEMM_ATOMIC_F32) {
-                        float *out = g.Cf + (size_t)row * g.ldc + nb;
+                        float *out = g.Cf + ooff + remap_col(nb, g.col_remap);
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
                             if (nb + i < g.N) atomicAdd(out + i, v[i]);
                     } else {  // GEMM_BIAS_RELU_BF16, GEMM_STORE_BF16
-                        __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + (size_t)row * g.ldc + nb;
+                        __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + ooff + nb;
                         __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
@@ -443,7 +519,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 h[i] = __float2bfloat16_rn(v[i]);
                             }
                         }
-                        if (full16 && ((g.ldc & 7) == 0) && ((nb & 7) == 0)) {
+                        if (g.mask) {   // OUT_DGRAD: N is a multiple of 16, rows 16-byte aligned
+                            __align__(16) uint16_t mk[16];
+                            const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + moff + nb);
+                            reinterpret_cast<uint4 *>(mk)[0] = mp[0];
+                            reinterpret_cast<uint4 *>(mk)[1] = mp[1];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (!(__bfloat162float(__ushort_as_bfloat16(mk[i])) > 0.0f)) h[i] = __float2bfloat16_rn(0.0f);
+                        }
+                        if (full16 && (((ooff + nb) & 7) == 0)) {
                             reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
                             reinterpret_cast<uint4 *>(out)[1] = reinterpret_cast<const uint4 *>(h)[1];
                         } else {
@@ -486,6 +571,26 @@ bool make_map(CUtensorMap *m, const uint16_t *base, int outer, int inner, int ld
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 4-D tensor map of a conv operand's source [nb][side][side][chan] (bf16, channels
+// contiguous), copied in boxes of 64 channels x `rows` pixel rows of the Ho x Ho output
+// grid (whole rows: Ho columns, rows / Ho grid rows, or whole Ho x Ho images), with the
+// 128-byte swizzle: each pixel row is one 128-byte row of the box, as in a 2-D copy of
+// the equivalent matrix.  Out-of-range coordinates read 0.
+bool make_map_conv(CUtensorMap *m, const uint16_t *base, int chan, int side, int nb, int ho, int rows) {
+    const int bw = ho < rows ? ho : rows;
+    const int bh = ho < rows / bw ? ho : rows / bw;
+    const int bb = rows / (bw * bh);
+    if (bw * bh * bb != rows || bb > nb || chan % 64 != 0) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)chan, (cuuint64_t)side, (cuuint64_t)side, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {(cuuint64_t)chan * 2, (cuuint64_t)side * chan * 2,
+                                   (cuuint64_t)side * side * chan * 2};
+    const cuuint32_t box[4] = {64u, (cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bb};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor map of the output C (M rows of N elements, row stride ldc) for the
 // epilogue's TMA stores: boxes of 128 bytes (32 fp32 or 64 bf16) x 32 rows, 128-byte
 // swizzle.  False when C's base or row stride is not 16-byte aligned, and for rows of
@@ -496,7 +601,7 @@ bool make_map_c(CUtensorMap *m, const GemmArgs &g) {
     const void *base = bf ? (const void *)g.Cb : (const void *)g.Cf;
     const size_t esz = bf ? 2 : 4;
     if (!base || ((uintptr_t)base & 15) || (((size_t)g.ldc * esz) & 15) || g.ldc < g.N) return false;
-    if ((size_t)g.ldc * esz < 256) return false;
+    if ((size_t)g.ldc * esz < 256 || g.out_kind != OUT_PLAIN) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
     const cuuint64_t strides[1] = {(cuuint64_t)g.ldc * esz};
     const cuuint32_t box[2] = {bf ? 64u : 32u, 32u};
@@ -511,13 +616,21 @@ template <int BN>
 cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, int sms, cudaStream_t st) {
     CUtensorMap ta, tb, tc;
     GemmArgs g = g0;
-    const bool ok_a = g.a_mn ? make_map(&ta, g.A, g.K, g.M, g.lda, kBK) : make_map(&ta, g.A, g.M, g.K, g.lda, kBM);
-    const bool ok_b = g.b_mn ? make_map(&tb, g.B, g.K, g.N, g.ldb, kBK) : make_map(&tb, g.B, g.N, g.K, g.ldb, BN);
+    auto conv_map = [&](CUtensorMap *m, const uint16_t *base, int kind, int rows) {
+        const int side = kind == CONV_BLOCKED ? g.conv_side + 1 : g.conv_side;
+        return make_map_conv(m, base, g.conv_chan, side, g.conv_batch, g.conv_side, rows);
+    };
+    const bool ok_a = g.a_conv ? conv_map(&ta, g.A, g.a_conv, kBM)
+                      : g.a_mn ? make_map(&ta, g.A, g.K, g.M, g.lda, kBK)
+                               : make_map(&ta, g.A, g.M, g.K, g.lda, kBM);
+    const bool ok_b = g.b_conv ? conv_map(&tb, g.B, g.b_conv, kBK)
+                      : g.b_mn ? make_map(&tb, g.B, g.K, g.N, g.ldb, kBK)
+                               : make_map(&tb, g.B, g.N * g.groups, g.K, g.ldb, BN);
     if (!ok_a || !ok_b) return cudaErrorInvalidValue;
     memset(&tc, 0, sizeof tc);
     g.tma_c = make_map_c(&tc, g) ? 1 : 0;
     g.split = split_k;
-    const int64_t tiles = (int64_t)((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN) * split_k;
+    const int64_t tiles = (int64_t)((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN) * split_k * g.groups;
     if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
     // One CTA per SM: the ring and the staging boxes take most of the SM's shared
     // memory, the double-buffered accumulator 2 BN of its 512 TMEM columns.  The ring
@@ -569,12 +682,25 @@ cudaError_t init_gemm_kernels() {
 
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
+    if (g.a_conv || g.b_conv) {
+        // whole output rows per box (Ho <= 64), 64-channel K steps, a conv B operand
+        // given MN-major, and room for a box that spans two images
+        const int ho = g.conv_side;
+        if (ho < 8 || ho > 64 || (ho & (ho - 1)) || g.conv_chan % 64 || g.conv_batch < 2 || (g.a_conv && g.a_mn) ||
+            (g.b_conv && !g.b_mn) || (g.a_conv && g.b_conv))
+            return cudaErrorInvalidValue;
+    }
+    if (g.groups != 1 && (g.groups != 4 || g.b_mn || g.b_conv || (g.N & 31))) return cudaErrorInvalidValue;
+    if (g.out_kind != OUT_PLAIN && (g.out_side < 2 || (g.out_side & 1) || (g.N & 15) || g.mode == GEMM_ATOMIC_F32))
+        return cudaErrorInvalidValue;
+    if (g.mask && g.out_kind != OUT_DGRAD) return cudaErrorInvalidValue;
+    if (g.col_remap && (g.col_remap & 31 || g.N != 16 * g.col_remap)) return cudaErrorInvalidValue;
     // tile width: the narrowest of {32 (K-major B only: MN-major boxes are 64 wide), 64,
     // 128, 256} covering N, halved (down to 64) while twice the CTAs still fit one wave
     const int sms = sm_count();
     int bn = g.N <= 32 && !g.b_mn ? 32 : g.N <= 64 ? 64 : g.N <= 128 ? 128 : 256;
     const int64_t rows = (g.M + kBM - 1) / kBM;
-    while (bn > 64 && 2 * rows * ((g.N + bn - 1) / bn) * split_k <= sms) bn /= 2;
+    while (bn > 64 && 2 * rows * ((g.N + bn - 1) / bn) * split_k * g.groups <= sms) bn /= 2;
     if (bn == 32) return launch_gemm_t<32>(g, split_k, sms, st);
     if (bn == 64) return launch_gemm_t<64>(g, split_k, sms, st);
     if (bn == 128) return launch_gemm_t<128>(g, split_k, sms, st);

@@ -24,15 +24,18 @@ def layer_slices():
     return out
 
 
-@pytest.fixture(scope="module")
-def case():
-    rng = np.random.default_rng(0)
+@pytest.fixture(scope="module", params=[2, 3])
+def case(request):
+    """Two images, and three: an odd batch, where a tensor copy of the 8 x 8 layer's
+    128 pixel rows (two whole images) reaches past the last image."""
+    B = request.param
+    rng = np.random.default_rng(B - 2)
     theta = inputs.cnn_init(1)
     # positive biases keep most units active; random ones exercise both ReLU sides
     for w, b in layer_slices():
         theta[b] = rng.normal(0.05, 0.05, theta[b].shape[0])
-    images = rng.uniform(0, 1, (2, 3, 256, 256)).astype(np.float32)
-    tp = inputs.anchored(11, 2)
+    images = rng.uniform(0, 1, (B, 3, 256, 256)).astype(np.float32)
+    tp = inputs.anchored(11, B)
     return theta, images, tp
 
 
@@ -56,13 +59,14 @@ def test_proposer_gradient_matches_oracle(case):
     atom gives errors of order max|ref|.  The norm-wise 2% check stays as a second line."""
     cuda()
     theta, images, tp = case
-    P = proposer.Proposer(max_batch=2)
+    B = images.shape[0]
+    P = proposer.Proposer(max_batch=B)
     try:
         P.set_params(theta)
         loss = P.train_step(to_dev(images), to_dev(tp))
         g = P.grads()
         L = loss.item()
-        acts = [P.activations(l, 2).astype(np.float64) for l in range(7)]
+        acts = [P.activations(l, B).astype(np.float64) for l in range(7)]
     finally:
         P.close()
     O, cache = cnn.forward(theta.astype(np.float64), images)
@@ -106,7 +110,7 @@ def test_proposer_gradient_matches_oracle(case):
 def test_propose_matches_oracle_decode(case):
     cuda()
     theta, images, _ = case
-    P = proposer.Proposer(max_batch=2)
+    P = proposer.Proposer(max_batch=images.shape[0])
     try:
         P.set_params(theta)
         got = P.propose(to_dev(images)).cpu().numpy()
