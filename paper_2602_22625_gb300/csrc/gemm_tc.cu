@@ -7,12 +7,13 @@
 //   warp 0      producer: one thread issues the TMA tensor copies of the A and B
 //               K-slabs (64 wide) into a ring of shared-memory stages, each stage
 //               announced on its `full` mbarrier with the bytes it expects;
-//   warp 1      allocates 2 BN TMEM columns (two accumulators); one thread issues
-//               tcgen05.mma (M = 128, N = BN, K = 16 per instruction) for each stage
-//               and commits it to the stage's `empty` mbarrier, which returns the slot
-//               to the producer; a commit after a tile's last stage marks its
-//               accumulator full;
-//   warps 2-5   epilogue: each reads the TMEM lane quarter it may access
+//   warp 1      allocates NACC BN TMEM columns (NACC accumulators, 2 or 4); one
+//               thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction)
+//               for each stage and commits it to the stage's `empty` mbarrier, which
+//               returns the slot to the producer; a commit after a tile's last stage
+//               marks its accumulator full;
+//   warps 2-5   epilogue (and warps 6-9 for tiles of BN <= 64, taking every other
+//               tile): each reads the TMEM lane quarter it may access
 //               (32 (warp % 4) ...) with tcgen05.ld and applies the mode.  When C's
 //               rows are 16-byte aligned, each warp writes 128-byte row pieces of its
 //               32 rows into a double-buffered shared-memory box in the 128-byte
@@ -51,20 +52,28 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kThreads = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // a wait gives up after 2 s
 
 // Epilogue staging: per epilogue warp two boxes of 32 rows x 128 bytes.
 constexpr int kStageBox = 32 * 128;
-constexpr int kEpiBytes = 4 * 2 * kStageBox;   // 32 KB
+constexpr int kSmemMax = 232448;                 // 227 KB of dynamic shared memory per block
 
+// Per tile width: narrow tiles (BN <= 64) have two epilogue warpgroups taking
+// alternate tiles and four TMEM accumulators, since their epilogue is as long as
+// their MMAs and copies; wider tiles one warpgroup and two accumulators.
 template <int BN>
 struct TileCfg {
+    static constexpr int EPI_GROUPS = BN <= 64 ? 2 : 1;
+    static constexpr int NACC = 2 * EPI_GROUPS;                // accumulators (NACC BN TMEM columns)
+    static constexpr int THREADS = 64 + 128 * EPI_GROUPS;
+    static constexpr int EPI_BYTES = EPI_GROUPS * 4 * 2 * kStageBox;
     static constexpr int A_BYTES = kBM * kBK * 2;   // 16 KB
     static constexpr int B_BYTES = BN * kBK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = 196608 / STAGE > 8 ? 8 : 196608 / STAGE;
-    static constexpr int SMEM = STAGES * STAGE + kEpiBytes + 1024;   // + alignment slack
+    static constexpr int FIT = (kSmemMax - 1024 - EPI_BYTES) / STAGE;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
+    static constexpr int SMEM = STAGES * STAGE + EPI_BYTES + 1024;   // + alignment slack
+    static_assert(SMEM <= kSmemMax && STAGES >= 3, "shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -129,15 +138,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
 // Coordinates of the 4-D copy of a conv operand: channel index `chan` (a multiple of
 // 64: tap chan / conv_chan, channels chan % conv_chan ...) and first pixel row `row`
 // (the box covers whole output rows of the Ho x Ho grid), for parity group grp.
-__device__ __forceinline__ void conv_coords(const GemmArgs &g, int kind, int chan, int row, int grp, int &c0,
-                                            int &c1, int &c2, int &c3) {
-    const int tap = chan / g.conv_chan;
+// conv_chan and Ho are powers of two (lc, lh their log2): shifts and masks only, since
+// one thread issues every copy and its arithmetic sits on the copy pipeline's path.
+__device__ __forceinline__ void conv_coords(int kind, int lc, int lh, int chan, int row, int grp, int &c0, int &c1,
+                                            int &c2, int &c3) {
+    const int tap = chan >> lc;
     const int dy = tap >> 1, dx = tap & 1;
-    const int hw = g.conv_side * g.conv_side;
-    const int b = row / hw;
-    const int oy = (row - b * hw) / g.conv_side;
-    c0 = chan - tap * g.conv_chan;
-    c3 = b;
+    const int oy = (row >> lh) & ((1 << lh) - 1);
+    c0 = chan & ((1 << lc) - 1);
+    c3 = row >> (2 * lh);
     if (kind == CONV_BLOCKED) {
         c1 = dx;
         c2 = oy + dy;
@@ -161,9 +170,9 @@ __device__ __forceinline__ int remap_col(int n, int C) {
 __device__ __forceinline__ size_t out_row_offset(const GemmArgs &g, int row, int grp, size_t &moff) {
     moff = 0;
     if (g.out_kind == OUT_PLAIN) return (size_t)row * g.ldc;
-    const int S = g.out_side;
-    const int xj = row % S, t = row / S;
-    const int yi = t % S, b = t / S;
+    const int S = g.out_side, ls = 31 - __clz(S);   // S a power of two
+    const int xj = row & (S - 1), t = row >> ls;
+    const int yi = t & (S - 1), b = t >> ls;
     const size_t N = (size_t)g.N;
     if (g.out_kind == OUT_BLOCKED) {
         const int hb = S / 2 + 1;
@@ -262,22 +271,58 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
+// The CTA's tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... as mixed-radix digits
+// (tm, tn, sp, grp) of radices (tiles_m, tiles_n, split, groups), stepped by adding the
+// digits of gridDim.x with carries: no division per tile on the roles' issue paths.
+struct TileWalk {
+    int rm, rn, rs;               // radices (the last digit needs none)
+    int dm, dn, ds, dg;           // digits of the stride
+    int tm, tn, sp, grp, t;       // the current tile
+    __device__ TileWalk(int tiles_m, int tiles_n, int split) : rm(tiles_m), rn(tiles_n), rs(split) {
+        digits(gridDim.x, dm, dn, ds, dg);
+        digits(blockIdx.x, tm, tn, sp, grp);
+        t = blockIdx.x;
+    }
+    __device__ void digits(int v, int &a, int &b, int &c, int &d) const {
+        a = v % rm;
+        v /= rm;
+        b = v % rn;
+        v /= rn;
+        c = v % rs;
+        d = v / rs;
+    }
+    __device__ void next() {
+        t += gridDim.x;
+        tm += dm;
+        int c = tm >= rm;
+        tm -= c ? rm : 0;
+        tn += dn + c;
+        c = tn >= rn;
+        tn -= c ? rn : 0;
+        sp += ds + c;
+        c = sp >= rs;
+        sp -= c ? rs : 0;
+        grp += dg + c;
+    }
+};
+
 // Persistent kernel: CTA c takes tiles c, c + gridDim.x, ... of the tiles_m x tiles_n
 // x split schedule (m fastest, so that concurrent CTAs share the B tile).  The stage
 // ring runs across tile boundaries, and the accumulator is double-buffered in TMEM
-// (2 BN columns): the MMA thread fills buffer lt & 1 of the CTA's tile lt while the
+// (NACC BN columns): the MMA thread fills buffer lt % NACC of the CTA's tile lt while the
 // epilogue warps drain the other.
 //   acc_full[b]   completed by the MMA commit after a tile's last K step;
 //   acc_empty[b]  completed when the four epilogue warps have read the buffer.
 // Tiles of a split with no K steps are skipped by every role alike.
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, GemmArgs g) {
     using C = TileCfg<BN>;
     constexpr int S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], drain;
+    constexpr int NACC = C::NACC;
+    __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[NACC], acc_empty[NACC], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -288,14 +333,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int kt_total = g.K / kBK;
     const int kt_per = (kt_total + g.split - 1) / g.split;
     const int n_tiles = tiles_m * tiles_n * g.split * g.groups;
-    // tile t -> output origin (m0, n0), K steps [kt0, kt0 + T) and group grp
-    auto decode = [&](int t, int &m0, int &n0, int &kt0, int &T, int &grp) {
-        const int tm = t % tiles_m, r = t / tiles_m;
-        m0 = tm * kBM;
-        n0 = (r % tiles_n) * BN;
-        const int r2 = r / tiles_n;
-        kt0 = (r2 % g.split) * kt_per;
-        grp = r2 / g.split;
+    // tile -> output origin (m0, n0), K steps [kt0, kt0 + T) and group grp
+    auto decode = [&](const TileWalk &w, int &m0, int &n0, int &kt0, int &T, int &grp) {
+        m0 = w.tm * kBM;
+        n0 = w.tn * BN;
+        kt0 = w.sp * kt_per;
+        grp = w.grp;
         T = max(0, min(kt_per, kt_total - kt0));
     };
 
@@ -305,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), 4);
         }
@@ -317,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                     "r"((uint32_t)(2 * BN))
+                     "r"((uint32_t)(NACC * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -328,12 +371,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0 && lane == 0) {
         // ---- producer ----
+        const int lc = g.conv_chan ? __ffs(g.conv_chan) - 1 : 0, lh = g.conv_side ? __ffs(g.conv_side) - 1 : 0;
         uint32_t u = 0;   // stage uses issued: slot u % S, its (u / S)-th use
         int s = 0;
         uint32_t ph = 0;
-        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        for (TileWalk w(tiles_m, tiles_n, g.split); w.t < n_tiles; w.next()) {
             int m0, n0, kt0, T, grp;
-            decode(t, m0, n0, kt0, T, grp);
+            decode(w, m0, n0, kt0, T, grp);
             for (int i = 0; i < T && !g.stall; ++i) {
                 if (u >= (uint32_t)S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1)) abort_flag = 1;
                 if (*(volatile int *)&abort_flag) break;
@@ -342,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(fb, C::STAGE);
                 if (g.a_conv) {
                     int c0, c1, c2, c3;
-                    conv_coords(g, g.a_conv, k, m0, grp, c0, c1, c2, c3);
+                    conv_coords(g.a_conv, lc, lh, k, m0, grp, c0, c1, c2, c3);
                     tma_load_4d(sa, &tmA, c0, c1, c2, c3, fb);
                 } else if (g.a_mn) {
                     for (int j = 0; j < kBM / 64; ++j) tma_load_2d(sa + j * 8192, &tmA, m0 + 64 * j, k, fb);
@@ -352,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (g.b_conv) {   // MN-major: 64 channels x 64 pixel rows per box
                     for (int j = 0; j < BN / 64; ++j) {
                         int c0, c1, c2, c3;
-                        conv_coords(g, g.b_conv, n0 + 64 * j, k, grp, c0, c1, c2, c3);
+                        conv_coords(g.b_conv, lc, lh, n0 + 64 * j, k, grp, c0, c1, c2, c3);
                         tma_load_4d(sa + C::A_BYTES + j * 8192, &tmB, c0, c1, c2, c3, fb);
                     }
                 } else if (g.b_mn) {
@@ -377,12 +421,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t a_lbo = g.a_mn ? 8192u : 16u, b_lbo = g.b_mn ? 8192u : 16u;
         int s = 0, lt = 0;
         uint32_t ph = 0;
-        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        for (TileWalk w(tiles_m, tiles_n, g.split); w.t < n_tiles; w.next()) {
             int m0, n0, kt0, T, grp;
-            decode(t, m0, n0, kt0, T, grp);
+            decode(w, m0, n0, kt0, T, grp);
             if (T == 0) continue;
-            const int b = lt & 1;
-            if (lt >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1)) abort_flag = 1;
+            const int b = lt % NACC;
+            if (lt >= NACC && !mbar_wait(smem_u32(&acc_empty[b]), ((lt / NACC) & 1) ^ 1)) abort_flag = 1;
             if (*(volatile int *)&abort_flag) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(b * BN);
@@ -391,9 +435,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (*(volatile int *)&abort_flag) break;
                 tc_fence_after();
                 const uint32_t sa = sbase + s * C::STAGE, sb = sa + C::A_BYTES;
+                // a K step of 16 moves the start address field (address >> 4, below
+                // 2^14 for any shared-memory address) without a carry into the rest
+                const uint64_t da = sw128_desc(sa, a_lbo), db = sw128_desc(sb, b_lbo);
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk)
-                    mma_bf16(d, sw128_desc(sa + kk * a_step, a_lbo), sw128_desc(sb + kk * b_step, b_lbo), idesc,
+                    mma_bf16(d, da + (uint64_t)((kk * a_step) >> 4), db + (uint64_t)((kk * b_step) >> 4), idesc,
                              (i > 0 || kk > 0) ? 1u : 0u);
                 mma_commit(smem_u32(&empty[s]));
                 if (++s == S) s = 0, ph ^= 1;
@@ -407,18 +454,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ---- epilogue ----
         const int q = warp & 3;                   // TMEM lanes 32 q .. 32 q + 31
+        const int eg = (warp - 2) >> 2;           // epilogue group: tiles lt with lt % EPI_GROUPS == eg
         const bool bf = g.mode == GEMM_BIAS_RELU_BF16 || g.mode == GEMM_STORE_BF16;
         const bool relu = g.mode == GEMM_BIAS_RELU_BF16;
         const int ecols = bf ? 64 : 32;           // columns of a 128-byte row piece
-        const uint32_t box0 = sbase + S * C::STAGE + (uint32_t)(q * 2 * kStageBox);
-        unsigned char *box0p = smem + S * C::STAGE + q * 2 * kStageBox;
+        const uint32_t box0 = sbase + S * C::STAGE + (uint32_t)((warp - 2) * 2 * kStageBox);
+        unsigned char *box0p = smem + S * C::STAGE + (warp - 2) * 2 * kStageBox;
         int buf = 0, lt = 0;
-        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        for (TileWalk w(tiles_m, tiles_n, g.split); w.t < n_tiles; w.next()) {
             int m0, n0, kt0, T, grp;
-            decode(t, m0, n0, kt0, T, grp);
+            decode(w, m0, n0, kt0, T, grp);
             if (T == 0) continue;
-            const int b = lt & 1;
-            bool ok = mbar_wait(smem_u32(&acc_full[b]), (lt >> 1) & 1);
+            if (lt % C::EPI_GROUPS != eg) {       // the other group's tile
+                ++lt;
+                continue;
+            }
+            const int b = lt % NACC;
+            bool ok = mbar_wait(smem_u32(&acc_full[b]), (lt / NACC) & 1);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) abort_flag = 1;
             ok = ok && !*(volatile int *)&abort_flag;
@@ -510,14 +562,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {  // GEMM_BIAS_RELU_BF16, GEMM_STORE_BF16
                         __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(g.Cb) + ooff + nb;
                         __align__(16) __nv_bfloat16 h[16];
+                        if (relu) {
+                            float bb[16];
+                            if (full16 && (((uintptr_t)(g.bias + nb) & 15) == 0)) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            if (relu) {
-                                const float bb = nb + i < g.N ? g.bias[nb + i] : 0.0f;
-                                h[i] = __float2bfloat16_rn(fmaxf(v[i] + bb, 0.0f));
+                                for (int i = 0; i < 4; ++i)
+                                    *reinterpret_cast<float4 *>(bb + 4 * i) =
+                                        __ldg(reinterpret_cast<const float4 *>(g.bias + nb) + i);
                             } else {
-                                h[i] = __float2bfloat16_rn(v[i]);
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) bb[i] = nb + i < g.N ? g.bias[nb + i] : 0.0f;
                             }
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(fmaxf(v[i] + bb[i], 0.0f));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(v[i]);
                         }
                         if (g.mask) {   // OUT_DGRAD: N is a multiple of 16, rows 16-byte aligned
                             __align__(16) uint16_t mk[16];
@@ -551,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (threadIdx.x == 0 && abort_flag && g.status) atomicExch(g.status, (int)DBMP_ERR_TIMEOUT);
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)(NACC * BN))
                      : "memory");
 }
 
@@ -633,11 +693,11 @@ cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, int sms, cudaStream_t
     const int64_t tiles = (int64_t)((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN) * split_k * g.groups;
     if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
     // One CTA per SM: the ring and the staging boxes take most of the SM's shared
-    // memory, the double-buffered accumulator 2 BN of its 512 TMEM columns.  The ring
+    // memory, the accumulators NACC BN of its 512 TMEM columns.  The ring
     // runs across tiles, so a short-K product still has several tiles' operands in flight.
-    const int smem = TileCfg<BN>::SMEM - (g.tma_c ? 0 : kEpiBytes);
+    const int smem = TileCfg<BN>::SMEM - (g.tma_c ? 0 : TileCfg<BN>::EPI_BYTES);
     const int grid = (int)(tiles < sms ? tiles : sms);
-    k_gemm_tma<BN><<<grid, kThreads, smem, st>>>(ta, tb, tc, g);
+    k_gemm_tma<BN><<<grid, TileCfg<BN>::THREADS, smem, st>>>(ta, tb, tc, g);
     return cudaGetLastError();
 }
 
@@ -686,7 +746,8 @@ cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
         // whole output rows per box (Ho <= 64), 64-channel K steps, a conv B operand
         // given MN-major, and room for a box that spans two images
         const int ho = g.conv_side;
-        if (ho < 8 || ho > 64 || (ho & (ho - 1)) || g.conv_chan % 64 || g.conv_batch < 2 || (g.a_conv && g.a_mn) ||
+        if (ho < 8 || ho > 64 || (ho & (ho - 1)) || g.conv_chan < 64 || (g.conv_chan & (g.conv_chan - 1)) ||
+            g.conv_batch < 2 || (g.a_conv && g.a_mn) ||
             (g.b_conv && !g.b_mn) || (g.a_conv && g.b_conv))
             return cudaErrorInvalidValue;
     }
