@@ -3,13 +3,18 @@
 // optimisation.  (The paper leaves learned initialisation to future work, Sec. S5,
 // and shows that initialisation matters, Sec. 3.2.2.)
 //
-//   input   B x 256 x 256 x 4 bf16 (NHWC; channels 0-2 = 2 (I - 0.5), 3 = 0)
+//   input   B x 256 x 256 x 4 bf16 (NHWC; channels 0-2 = 2 (I - 0.5), 3 = 0), rows padded
+//           by one zero pixel on each side
 //   conv1-5 4x4 / stride 2 / pad 1, bias, ReLU: 4 -> 32 -> 64 -> 128 -> 256 -> 256
 //   head    1x1 conv 256 -> 64 on the 8 x 8 map: 8 slots x 8 outputs per cell
 //
-// Every product is the tcgen05 GEMM of gemm_tc.cu (BF16 operands, FP32 accumulation).
-// conv1 runs on an explicit im2col matrix (K = 16 taps x 4 channels = 64).  conv2-5
-// are implicit GEMMs over activations kept in a blocked (space-to-depth) layout:
+// Every product is the tcgen05 GEMM of gemm_tc.cu (BF16 operands, FP32 accumulation),
+// and every convolution is an implicit GEMM: no im2col matrix is written.  conv1
+// (K = 16 taps x 4 channels = 64) reads its input as 16-byte pixel pairs: for output
+// pixel ox, taps kx = 2p, 2p+1 of tap row ky are padded pixels 2(ox+p), 2(ox+p)+1, so
+// one tensor copy of 128 consecutive pairs is one 16-byte K chunk of 128 output rows
+// (the tensor cores' unswizzled layout), eight copies one K step.  conv2-5 are implicit
+// GEMMs over activations kept in a blocked (space-to-depth) layout:
 //
 //   Xb[b][i][j][(sy*2 + sx)*C + c] = X[b][2i+sy-1][2j+sx-1][c]  (0 outside),
 //   i, j in [0, H/2], sy, sx in {0, 1}
@@ -53,7 +58,8 @@ __device__ __forceinline__ uint16_t f2bf(float x) {
 __device__ __forceinline__ float bf2f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
 // The input image as the first layer's 4 channels (NHWC bf16): 2 (I - 0.5), and a zero
-// fourth channel (the first layer's K = 16 taps x 4 channels = 64, one GEMM K step).
+// fourth channel, in rows of 258 pixels with one zero pixel on each side (written once,
+// at allocation), so that the first conv reads its taps as 16-byte pixel pairs.
 __global__ void k_pack_input(const float *__restrict__ img, int32_t B, uint16_t *__restrict__ X0) {
     const int64_t n = (int64_t)B * 65536;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -63,25 +69,8 @@ __global__ void k_pack_input(const float *__restrict__ img, int32_t B, uint16_t 
 #pragma unroll
         for (int c = 0; c < 3; ++c) h[c] = f2bf(2.0f * (I[c * 65536] - 0.5f));
         h[3] = 0;
-        reinterpret_cast<uint2 *>(X0)[i] = *reinterpret_cast<const uint2 *>(h);
-    }
-}
-
-// im2col of the 4-channel input: col[m][(ky*4 + kx)*4 + c] = X[b][2oy-1+ky][2ox-1+kx][c]
-// (0 outside), m = (b, oy, ox), H = W = 2^lh; one 8-byte chunk (4 channels) per thread.
-__global__ void k_im2col4(const uint16_t *__restrict__ X, int32_t B, int32_t lh, uint16_t *__restrict__ col) {
-    const int lo = lh - 1;
-    const int H = 1 << lh;
-    const int64_t n = (int64_t)B << (2 * lo + 4);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int kk = (int)(i & 15);
-        const int64_t m = i >> 4;
-        const int ox = (int)(m & ((1 << lo) - 1)), oy = (int)((m >> lo) & ((1 << lo) - 1));
-        const int64_t b = m >> (2 * lo);
-        const int y = 2 * oy - 1 + (kk >> 2), x = 2 * ox - 1 + (kk & 3);
-        uint2 v = make_uint2(0, 0);
-        if (y >= 0 && y < H && x >= 0 && x < H) v = reinterpret_cast<const uint2 *>(X)[(((b << lh) + y) << lh) + x];
-        reinterpret_cast<uint2 *>(col)[i] = v;
+        const int64_t y = pix >> 8, x = pix & 255;
+        reinterpret_cast<uint2 *>(X0)[(b * 256 + y) * 258 + x + 1] = *reinterpret_cast<const uint2 *>(h);
     }
 }
 
@@ -316,7 +305,7 @@ int64_t cnn_num_params() {
 
 // sizes in elements for a given max batch
 struct CnnSizes {
-    int64_t X[6], col, dx, dz;
+    int64_t X[6], dx, dz;
 };
 
 // Images held by the buffers that 4-D tensor copies read: a box may span two images.
@@ -328,13 +317,12 @@ static CnnSizes cnn_sizes(int32_t B) {
     layer_table(L, &np);
     const int64_t nb = held_images(B);
     CnnSizes s{};
-    s.X[0] = (int64_t)B * 256 * 256 * 4;
+    s.X[0] = nb * 256 * 258 * 4;   // rows padded by one pixel on each side
     for (int l = 1; l < 5; ++l) {   // blocked: (H/2 + 1)^2 blocks of 4C channels
         const int64_t hb = L[l].hin / 2 + 1;
         s.X[l] = nb * hb * hb * 4 * L[l].cin;
     }
     s.X[5] = nb * 64 * 256;
-    s.col = (int64_t)B * 128 * 128 * L[0].K;   // the first conv's im2col matrix
     s.dx = nb * 64 * 256;
     s.dz = nb * 64 * 64;
     for (int l = 0; l < 5; ++l) {
@@ -350,7 +338,7 @@ size_t cnn_bytes(int32_t B) {
     size_t b = 4 * sizeof(float) * np + 3 * sizeof(uint16_t) * np;
     for (int l = 0; l < 6; ++l) b += sizeof(uint16_t) * s.X[l];
     b += 2 * sizeof(float) * (size_t)B * 64 * 64 + sizeof(float) * s.dx;
-    b += sizeof(uint16_t) * s.col + 2 * sizeof(uint16_t) * s.dz + sizeof(int32_t) * 4;
+    b += 2 * sizeof(uint16_t) * s.dz + sizeof(int32_t) * 4;
     return b;
 }
 
@@ -375,16 +363,15 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
     A((void **)&c.O, sizeof(float) * B * 64 * 64);
     A((void **)&c.dO, sizeof(float) * B * 64 * 64);
     A((void **)&c.dx, sizeof(float) * s.dx);
-    A((void **)&c.col, sizeof(uint16_t) * s.col);
     A((void **)&c.dz, sizeof(uint16_t) * s.dz);
     A((void **)&c.dzp, sizeof(uint16_t) * s.dz);
     A((void **)&c.status, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(c.status, 0, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(c.m, 0, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMemset(c.v, 0, sizeof(float) * np);
-    // the blocked activations' padding entries (never written) read as zeros; so do the
-    // images past the batch that a two-image box may touch
-    for (int l = 1; l < 5 && e == cudaSuccess; ++l) e = cudaMemset(c.X[l], 0, sizeof(uint16_t) * s.X[l]);
+    // the padding entries of the input and of the blocked activations (never written)
+    // read as zeros; so do the images past the batch that a two-image box may touch
+    for (int l = 0; l < 5 && e == cudaSuccess; ++l) e = cudaMemset(c.X[l], 0, sizeof(uint16_t) * s.X[l]);
     if (e == cudaSuccess) e = cudaMemset(c.X[5], 0, sizeof(uint16_t) * s.X[5]);
     if (e == cudaSuccess) e = cudaMemset(c.dz, 0, sizeof(uint16_t) * s.dz);
     if (e == cudaSuccess) e = cudaMemset(c.dzp, 0, sizeof(uint16_t) * s.dz);
@@ -394,7 +381,7 @@ cudaError_t cnn_alloc(CnnBuffers &c, int32_t B) {
 
 void cnn_free(CnnBuffers &c) {
     void *ps[] = {c.theta, c.grad, c.m, c.v, c.wbf, c.wf, c.wd, c.X[0], c.X[1], c.X[2], c.X[3], c.X[4], c.X[5],
-                  c.O, c.dO, c.dx, c.col, c.dz, c.dzp, c.status};
+                  c.O, c.dO, c.dx, c.dz, c.dzp, c.status};
     for (void *p : ps)
         if (p) cudaFree(p);
     c = CnnBuffers{};
@@ -445,21 +432,17 @@ cudaError_t cnn_forward(CnnBuffers &c, const float *images, int32_t B, cudaStrea
     int64_t np;
     layer_table(L, &np);
     k_pack_input<<<grid1d((int64_t)B * 65536), 256, 0, st>>>(images, B, c.X[0]);
-    k_im2col4<<<grid1d((int64_t)B * 128 * 128 * 16), 256, 0, st>>>(c.X[0], B, 8, c.col);
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
         const int Ho = L[l].hin / 2;
         const int M = B * Ho * Ho, Co = L[l].cout, K = (int)L[l].K;
-        GemmArgs g = l == 0 ? gemm_args(c.col, K, c.wbf + L[l].w_off, K, M, Co, K, GEMM_BIAS_RELU_BF16, nullptr,
-                                        c.X[1], Co, c.theta + L[l].b_off, c.status)
-                            : gemm_args(c.X[l], 0, c.wf + L[l].w_off, K, M, Co, K, GEMM_BIAS_RELU_BF16, nullptr,
-                                        c.X[l + 1], Co, c.theta + L[l].b_off, c.status);
-        if (l > 0) {
-            g.a_conv = CONV_BLOCKED;
-            g.conv_chan = 4 * L[l].cin;
-            g.conv_side = Ho;
-            g.conv_batch = c.nb;
-        }
+        // conv1: weights in their (ky, kx, c) order, which the pair chunks follow
+        GemmArgs g = gemm_args(c.X[l], 0, (l == 0 ? c.wbf : c.wf) + L[l].w_off, K, M, Co, K, GEMM_BIAS_RELU_BF16,
+                               nullptr, c.X[l + 1], Co, c.theta + L[l].b_off, c.status);
+        g.a_conv = l == 0 ? CONV_PAIRS : CONV_BLOCKED;
+        g.conv_chan = l == 0 ? 0 : 4 * L[l].cin;
+        g.conv_side = Ho;
+        g.conv_batch = c.nb;
         if (l < 4) {   // the next conv's input, blocked
             g.out_kind = OUT_BLOCKED;
             g.out_side = Ho;
@@ -491,7 +474,7 @@ cudaError_t cnn_activation(const CnnBuffers &c, int32_t layer, int32_t B, float 
     layer_table(L, &np);
     const bool blocked = layer >= 1 && layer <= 4;
     const int64_t H = layer == 0 ? 256 : L[layer - 1].hin / 2, C = n / ((int64_t)B * H * H), hb = H / 2 + 1;
-    const int64_t stored = blocked ? (int64_t)B * hb * hb * 4 * C : n;
+    const int64_t stored = blocked ? (int64_t)B * hb * hb * 4 * C : layer == 0 ? (int64_t)B * 256 * 258 * 4 : n;
     // bf16 bits are the upper half of the float32 they round to
     uint16_t *tmp = static_cast<uint16_t *>(malloc(sizeof(uint16_t) * (size_t)stored));
     if (!tmp) return cudaErrorMemoryAllocation;
@@ -499,10 +482,11 @@ cudaError_t cnn_activation(const CnnBuffers &c, int32_t layer, int32_t B, float 
     if (e == cudaSuccess) {
         for (int64_t i = 0; i < n; ++i) {
             int64_t src = i;
-            if (blocked) {   // NHWC element (b, y, x, ch) from block ((y+1)/2, (x+1)/2)
-                const int64_t ch = i % C, p = i / C, x = p % H, y = (p / H) % H, b = p / (H * H);
+            const int64_t ch = i % C, p = i / C, x = p % H, y = (p / H) % H, b = p / (H * H);
+            if (blocked)   // NHWC element (b, y, x, ch) from block ((y+1)/2, (x+1)/2)
                 src = ((b * hb + (y + 1) / 2) * hb + (x + 1) / 2) * 4 * C + (((y + 1) & 1) * 2 + ((x + 1) & 1)) * C + ch;
-            }
+            else if (layer == 0)   // rows padded by one pixel on each side
+                src = ((b * 256 + y) * 258 + x + 1) * 4 + ch;
             const uint32_t u = (uint32_t)tmp[src] << 16;
             memcpy(host + i, &u, sizeof u);
         }
@@ -525,8 +509,7 @@ static int split_for(int M, int N, int K) {
 }
 
 // Loss and gradient w.r.t. all parameters into c.grad (overwritten).  Reads the
-// activations and the first conv's im2col matrix that the forward of the same batch
-// left in c.
+// activations that the forward of the same batch left in c.
 cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, double *loss, cudaStream_t st) {
     CnnLayer L[6];
     int64_t np;
@@ -547,9 +530,13 @@ cudaError_t cnn_backward(CnnBuffers &c, const float *target_params, int32_t B, d
     for (int l = 4; l >= 0 && e == cudaSuccess; --l) {
         const int Ho = L[l].hin / 2, M = B * Ho * Ho;
         const int K = (int)L[l].K, Co = L[l].cout, C = L[l].cin;
-        if (l == 0) {   // wgrad from the im2col matrix the forward left in c.col
-            e = gemm(c.dz, Co, c.col, K, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN, c.grad + L[l].w_off,
-                     nullptr, K, nullptr, split_for(Co, K, M), c.status, st);
+        if (l == 0) {   // wgrad with B = the padded input's pixel pairs (MN-major)
+            GemmArgs g = gemm_args(c.dz, Co, c.X[0], 0, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN,
+                                   c.grad + L[l].w_off, nullptr, K, nullptr, c.status);
+            g.b_conv = CONV_PAIRS;
+            g.conv_side = Ho;
+            g.conv_batch = c.nb;
+            e = launch_gemm(g, split_for(Co, K, M), st);
         } else {        // wgrad with B = the blocked input, columns back in (ky, kx, c) order
             GemmArgs g = gemm_args(c.dz, Co, c.X[l], 0, Co, K, M, GEMM_ATOMIC_F32 | GEMM_A_MN | GEMM_B_MN,
                                    c.grad + L[l].w_off, nullptr, K, nullptr, c.status);

@@ -196,7 +196,10 @@ struct GemmArgs {
     // (0: columns in place).
     int32_t col_remap = 0;            // C
 };
-enum ConvKind { CONV_NONE = 0, CONV_BLOCKED = 1, CONV_DGRAD = 2 };
+// CONV_PAIRS (the first conv, 4 channels): source = the padded input [nb][2Ho][2Ho+2][4]
+// read as pixel pairs, one 16-byte K chunk (taps kx = 2p, 2p+1 of tap row ky) per copy,
+// unswizzled; K = 64 as A (forward), N = 64 as B (weight gradient, MN-major).
+enum ConvKind { CONV_NONE = 0, CONV_BLOCKED = 1, CONV_DGRAD = 2, CONV_PAIRS = 3 };
 enum OutKind { OUT_PLAIN = 0, OUT_BLOCKED = 1, OUT_DGRAD = 2 };
 
 cudaError_t init_gemm_kernels();
@@ -212,10 +215,11 @@ struct CnnBuffers {
     uint16_t *wbf;                 // bf16 copies of the weights, K in (ky, kx, c) order
     uint16_t *wf, *wd;             // convs 2-5: forward weights in blocked tap order, and the
                                    // input-gradient weights per parity class (at wbf's offsets)
-    uint16_t *X[6];                // activations: X[0] the input (NHWC, 4 channels), X[1..4]
-                                   // in the blocked layout, X[5] NHWC
+    uint16_t *X[6];                // activations: X[0] the input (NHWC, 4 channels, rows padded
+                                   // by one pixel on each side), X[1..4] in the blocked
+                                   // layout, X[5] NHWC
     float *O, *dO, *dx;            // head outputs, their gradient, the head's input gradient
-    uint16_t *col, *dz, *dzp;      // im2col matrix of the first conv, conv output gradients (two buffers)
+    uint16_t *dz, *dzp;            // conv output gradients (two buffers)
     int32_t *status;
 };
 

@@ -71,8 +71,12 @@ struct TileCfg {
     static constexpr int B_BYTES = BN * kBK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int FIT = (kSmemMax - 1024 - EPI_BYTES) / STAGE;
-    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
-    static constexpr int SMEM = STAGES * STAGE + EPI_BYTES + 1024;   // + alignment slack
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;                  // with the staging boxes
+    static constexpr int FIT_ALL = (kSmemMax - 1024) / STAGE;
+    static constexpr int STAGES_MAX = FIT_ALL > 12 ? 12 : FIT_ALL;    // without them
+    static constexpr int SMEM_EPI = STAGES * STAGE + EPI_BYTES + 1024;   // + alignment slack
+    static constexpr int SMEM_NOEPI = STAGES_MAX * STAGE + 1024;
+    static constexpr int SMEM = SMEM_EPI > SMEM_NOEPI ? SMEM_EPI : SMEM_NOEPI;
     static_assert(SMEM <= kSmemMax && STAGES >= 3, "shared memory");
 };
 
@@ -229,6 +233,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t lbo) {
     return d;
 }
 
+// Descriptor of an unswizzled operand (layout type 0): core matrices of eight
+// 16-byte rows, 128 contiguous bytes each.  K-major: lbo = distance between core
+// matrices along K, sbo = along M/N; MN-major: lbo = along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t plain_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: D f32, A and B bf16, M = 128, N = BN; bits 15
 // and 16 mark A / B as MN-major.
 template <int BN>
@@ -319,10 +335,11 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, GemmArgs g) {
     using C = TileCfg<BN>;
-    constexpr int S = C::STAGES;
+    // ring stages: fewer when the epilogue's TMA staging boxes share the shared memory
+    const int S = g.tma_c ? C::STAGES : C::STAGES_MAX;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int NACC = C::NACC;
-    __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[NACC], acc_empty[NACC], drain;
+    __shared__ __align__(8) uint64_t full[C::STAGES_MAX], empty[C::STAGES_MAX], acc_full[NACC], acc_empty[NACC], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -384,7 +401,12 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
                 const uint32_t sa = sbase + s * C::STAGE, fb = smem_u32(&full[s]);
                 const int k = (kt0 + i) * kBK;
                 mbar_expect_tx(fb, C::STAGE);
-                if (g.a_conv) {
+                if (g.a_conv == CONV_PAIRS) {
+                    // chunk kc = (ky, p) of every row: 128 rows x 16 B, 2 KB apart
+                    const int b = m0 >> (2 * lh), oy = (m0 >> lh) & ((1 << lh) - 1), ox = m0 & ((1 << lh) - 1);
+                    for (int kc = 0; kc < 8; ++kc)
+                        tma_load_4d(sa + kc * 2048, &tmA, 0, ox + (kc & 1), 2 * oy - 1 + (kc >> 1), b, fb);
+                } else if (g.a_conv) {
                     int c0, c1, c2, c3;
                     conv_coords(g.a_conv, lc, lh, k, m0, grp, c0, c1, c2, c3);
                     tma_load_4d(sa, &tmA, c0, c1, c2, c3, fb);
@@ -393,7 +415,12 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
                 } else {
                     tma_load_2d(sa, &tmA, k, m0, fb);
                 }
-                if (g.b_conv) {   // MN-major: 64 channels x 64 pixel rows per box
+                if (g.b_conv == CONV_PAIRS) {
+                    // MN-major: chunk kc = (ky, p) of 64 pixel rows, 64 x 16 B, 1 KB apart
+                    const int b = k >> (2 * lh), oy = (k >> lh) & ((1 << lh) - 1), ox = k & ((1 << lh) - 1);
+                    for (int kc = 0; kc < 8; ++kc)
+                        tma_load_4d(sa + C::A_BYTES + kc * 1024, &tmB, 0, ox + (kc & 1), 2 * oy - 1 + (kc >> 1), b, fb);
+                } else if (g.b_conv) {   // MN-major: 64 channels x 64 pixel rows per box
                     for (int j = 0; j < BN / 64; ++j) {
                         int c0, c1, c2, c3;
                         conv_coords(g.b_conv, lc, lh, n0 + 64 * j, k, grp, c0, c1, c2, c3);
@@ -417,8 +444,13 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
         // ---- MMA issuer ----
         const uint32_t idesc = instr_desc<BN>(g.a_mn != 0, g.b_mn != 0);
         // per K step of 16: +32 B (K-major) or +2048 B (MN-major); leading byte offsets
-        const uint32_t a_step = g.a_mn ? 2048u : 32u, b_step = g.b_mn ? 2048u : 32u;
+        const uint32_t a_step = g.a_conv == CONV_PAIRS ? 4096u : g.a_mn ? 2048u : 32u;
+        const uint32_t b_step = g.b_conv == CONV_PAIRS ? 256u : g.b_mn ? 2048u : 32u;
         const uint32_t a_lbo = g.a_mn ? 8192u : 16u, b_lbo = g.b_mn ? 8192u : 16u;
+        // pixel-pair operands are unswizzled: A (K-major) 16-byte chunks 2 KB apart along
+        // K, eight-row groups 128 B apart along M; B (MN-major) eight-pixel groups 128 B
+        // apart along K, 16-byte chunks 1 KB apart along N
+        const bool a_plain = g.a_conv == CONV_PAIRS, b_plain = g.b_conv == CONV_PAIRS;
         int s = 0, lt = 0;
         uint32_t ph = 0;
         for (TileWalk w(tiles_m, tiles_n, g.split); w.t < n_tiles; w.next()) {
@@ -437,7 +469,8 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
                 const uint32_t sa = sbase + s * C::STAGE, sb = sa + C::A_BYTES;
                 // a K step of 16 moves the start address field (address >> 4, below
                 // 2^14 for any shared-memory address) without a carry into the rest
-                const uint64_t da = sw128_desc(sa, a_lbo), db = sw128_desc(sb, b_lbo);
+                const uint64_t da = a_plain ? plain_desc(sa, 2048u, 128u) : sw128_desc(sa, a_lbo);
+                const uint64_t db = b_plain ? plain_desc(sb, 128u, 1024u) : sw128_desc(sb, b_lbo);
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk)
                     mma_bf16(d, da + (uint64_t)((kk * a_step) >> 4), db + (uint64_t)((kk * b_step) >> 4), idesc,
@@ -470,6 +503,19 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
                 continue;
             }
             const int b = lt % NACC;
+            // the per-lane path's row placement and, for OUT_DGRAD tiles of BN <= 64, the
+            // row's mask: loaded before the accumulator wait so that the mask's memory
+            // latency overlaps the tile's MMAs
+            const int row = m0 + q * 32 + lane;
+            size_t moff = 0;
+            const size_t ooff = (!g.tma_c && row < g.M) ? out_row_offset(g, row, grp, moff) : 0;
+            constexpr int MKN = BN <= 64 ? BN / 8 : 1;
+            uint4 mk[MKN];
+            if (BN <= 64 && g.mask && row < g.M) {
+#pragma unroll
+                for (int j = 0; j < MKN; ++j)
+                    if (n0 + 8 * j + 8 <= g.N) mk[j] = __ldg(reinterpret_cast<const uint4 *>(g.mask + moff + n0) + j);
+            }
             bool ok = mbar_wait(smem_u32(&acc_full[b]), (lt / NACC) & 1);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) abort_flag = 1;
@@ -529,9 +575,7 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
                     }
                 }
             } else {
-                const int row = m0 + q * 32 + lane;
-                size_t moff;
-                const size_t ooff = row < g.M ? out_row_offset(g, row, grp, moff) : 0;
+#pragma unroll(BN <= 64 ? BN / 16 : 1)
                 for (int c0 = 0; c0 < BN; c0 += 16) {
                     float v[16];
                     tmem_ld16(trow + c0, v);
@@ -580,13 +624,18 @@ __global__ void __launch_bounds__(TileCfg<BN>::THREADS, 1)
                             for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(v[i]);
                         }
                         if (g.mask) {   // OUT_DGRAD: N is a multiple of 16, rows 16-byte aligned
-                            __align__(16) uint16_t mk[16];
-                            const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + moff + nb);
-                            reinterpret_cast<uint4 *>(mk)[0] = mp[0];
-                            reinterpret_cast<uint4 *>(mk)[1] = mp[1];
+                            __align__(16) uint16_t m16[16];
+                            if (BN <= 64) {
+                                reinterpret_cast<uint4 *>(m16)[0] = mk[(c0 >> 3) % MKN];
+                                reinterpret_cast<uint4 *>(m16)[1] = mk[((c0 >> 3) + 1) % MKN];
+                            } else {
+                                const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + moff + nb);
+                                reinterpret_cast<uint4 *>(m16)[0] = mp[0];
+                                reinterpret_cast<uint4 *>(m16)[1] = mp[1];
+                            }
 #pragma unroll
                             for (int i = 0; i < 16; ++i)
-                                if (!(__bfloat162float(__ushort_as_bfloat16(mk[i])) > 0.0f)) h[i] = __float2bfloat16_rn(0.0f);
+                                if (!(__bfloat162float(__ushort_as_bfloat16(m16[i])) > 0.0f)) h[i] = __float2bfloat16_rn(0.0f);
                         }
                         if (full16 && (((ooff + nb) & 7) == 0)) {
                             reinterpret_cast<uint4 *>(out)[0] = reinterpret_cast<const uint4 *>(h)[0];
@@ -651,6 +700,23 @@ bool make_map_conv(CUtensorMap *m, const uint16_t *base, int chan, int side, int
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 4-D tensor map of the first conv's padded input [nb][2 Ho][2 Ho + 2][4] (bf16, one
+// zero pixel on each side of a row) as pixel pairs: [nb][2 Ho][Ho + 1][8], pair j =
+// padded pixels 2j, 2j + 1.  Boxes of 8 elements (16 bytes) x `rows` pairs of one row,
+// unswizzled: for output pixel ox, tap row ky and pair p = kx / 2, pair ox + p holds
+// taps kx = 2p, 2p + 1 of the 4 x 4 window, so a box starting at pair ox0 + p of row
+// 2 oy - 1 + ky is one 16-byte K chunk of `rows` consecutive output pixels.
+bool make_map_pairs(CUtensorMap *m, const uint16_t *base, int ho, int nb, int rows) {
+    const cuuint64_t pairs = (cuuint64_t)ho + 1, H = 2 * (cuuint64_t)ho, row_bytes = (2 * (cuuint64_t)ho + 2) * 8;
+    const cuuint64_t dims[4] = {8, pairs, H, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {16, row_bytes, H * row_bytes};
+    const cuuint32_t box[4] = {8u, (cuuint32_t)rows, 1u, 1u};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor map of the output C (M rows of N elements, row stride ldc) for the
 // epilogue's TMA stores: boxes of 128 bytes (32 fp32 or 64 bf16) x 32 rows, 128-byte
 // swizzle.  False when C's base or row stride is not 16-byte aligned, and for rows of
@@ -677,6 +743,7 @@ cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, int sms, cudaStream_t
     CUtensorMap ta, tb, tc;
     GemmArgs g = g0;
     auto conv_map = [&](CUtensorMap *m, const uint16_t *base, int kind, int rows) {
+        if (kind == CONV_PAIRS) return make_map_pairs(m, base, g.conv_side, g.conv_batch, rows);
         const int side = kind == CONV_BLOCKED ? g.conv_side + 1 : g.conv_side;
         return make_map_conv(m, base, g.conv_chan, side, g.conv_batch, g.conv_side, rows);
     };
@@ -695,7 +762,7 @@ cudaError_t launch_gemm_t(const GemmArgs &g0, int split_k, int sms, cudaStream_t
     // One CTA per SM: the ring and the staging boxes take most of the SM's shared
     // memory, the accumulators NACC BN of its 512 TMEM columns.  The ring
     // runs across tiles, so a short-K product still has several tiles' operands in flight.
-    const int smem = TileCfg<BN>::SMEM - (g.tma_c ? 0 : TileCfg<BN>::EPI_BYTES);
+    const int smem = g.tma_c ? TileCfg<BN>::SMEM_EPI : TileCfg<BN>::SMEM_NOEPI;
     const int grid = (int)(tiles < sms ? tiles : sms);
     k_gemm_tma<BN><<<grid, TileCfg<BN>::THREADS, smem, st>>>(ta, tb, tc, g);
     return cudaGetLastError();
@@ -742,7 +809,14 @@ cudaError_t init_gemm_kernels() {
 
 cudaError_t launch_gemm(const GemmArgs &g, int split_k, cudaStream_t st) {
     if (g.K % kBK != 0 || g.M <= 0 || g.N <= 0 || split_k < 1 || !g_encode) return cudaErrorInvalidValue;
-    if (g.a_conv || g.b_conv) {
+    if (g.a_conv == CONV_PAIRS || g.b_conv == CONV_PAIRS) {
+        // the first conv: K = 16 taps x 4 channels = 64 (A), or N = 64 (B, MN-major);
+        // boxes of 128 (A) or 64 (B) pixels within one output row
+        const int ho = g.conv_side;
+        if (ho < 128 || (ho & (ho - 1)) || g.conv_batch < 1 || (g.a_conv && g.b_conv) ||
+            (g.a_conv && (g.K != 64 || g.a_mn)) || (g.b_conv && (g.N != 64 || !g.b_mn)))
+            return cudaErrorInvalidValue;
+    } else if (g.a_conv || g.b_conv) {
         // whole output rows per box (Ho <= 64), 64-channel K steps, a conv B operand
         // given MN-major, and room for a box that spans two images
         const int ho = g.conv_side;
