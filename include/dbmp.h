@@ -376,6 +376,18 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
                       int32_t *n_last_dev, const float *dL_dimage_dev, float *dparams_dev,
                       int32_t reps, DbmpTuning *best, float *best_ms, dbmp_stream_t stream);
 
+/* Tile-density-guided autotuning (the scaling statistics of Sec. S4 feeding the
+ * search).  With max_pairs_ratio > 0, dbmp_autotune first bins the plan's scene once
+ * per tile size and reads its tile-density statistics (dbmp_bin_stats: the list
+ * entries pairs = sum over tiles of d_t); it then times only the tile sizes whose
+ * entries are at most max_pairs_ratio times the fewest of any size, in increasing
+ * order of entries (a tile size whose binning overflows the workspace is dropped).
+ * Every tile-list entry is binned, culled per warp region and walked by both
+ * compositors, so a size with several times the entries of another rarely wins.
+ * 0 (the default of a new workspace) times every tile size.  DBMP_ERR_INVALID_ARG
+ * for a negative or non-finite ratio.  Host-only (no device work). */
+int32_t dbmp_autotune_set_prune(DbmpWorkspace *ws, float max_pairs_ratio);
+
 /* ------------------------------------------------------------------------- */
 /* BF16 tensor-core GEMM (tcgen05, FP32 accumulation), used by the proposal    */
 /* network below and exposed for testing                                      */

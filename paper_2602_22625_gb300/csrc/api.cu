@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <vector>
 
 #include "dbmp_internal.cuh"
@@ -87,6 +88,7 @@ struct DbmpWorkspace {
     bool persistent = false;
     bool binned = false;
     int32_t row0 = 0, row1 = 0;   // row window of the plan's renders (row1 0: all rows)
+    float tune_prune = 0.0f;                // dbmp_autotune: tile sizes timed (0: all)
     const float *params = nullptr;  // of the last binning (gradient finalisation)
     int32_t Hb = 0, Wb = 0;
     float alpha_max = 1.0f;
@@ -777,6 +779,14 @@ int32_t dbmp_batch_set_rows(DbmpWorkspace *ws, int32_t y0, int32_t y1) {
     return DBMP_OK;
 }
 
+int32_t dbmp_autotune_set_prune(DbmpWorkspace *ws, float max_pairs_ratio) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "ws is NULL");
+    if (!(max_pairs_ratio >= 0.0f) || !std::isfinite(max_pairs_ratio))
+        return fail(DBMP_ERR_INVALID_ARG, "max_pairs_ratio must be finite and >= 0");
+    ws->tune_prune = max_pairs_ratio;
+    return DBMP_OK;
+}
+
 int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t *bitmap_id_dev,
                       const DbmpAtlas *atlas, float alpha_max, const DbmpBackground *bg, float T_stop,
                       int32_t mode, float *image_dev, float *T_final_dev, int32_t *n_last_dev,
@@ -794,7 +804,43 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
     DBMP_CUDA(cudaEventCreate(&e1), "event");
     float best_t = 1e30f;
     DbmpTuning bt{ws->cfg.tile, ws->cfg.batch, ws->cfg.ppt, ws->cfg.ppt_bwd};
-    const int32_t tiles[] = {8, 16, 32};
+    int32_t tiles[] = {8, 16, 32};
+    int n_tiles_try = 3;
+    if (ws->tune_prune > 0.0f) {
+        // Tile-density guided: the list entries sum_t d_t (Sec. S4) of one binning per
+        // tile size set the order, and sizes above tune_prune x the fewest are not timed.
+        int64_t pairs[3] = {-1, -1, -1};
+        int64_t fewest = -1;
+        for (int i = 0; i < 3; ++i) {
+            DbmpTuning c{tiles[i], 32, 1, 1};
+            if (dbmp_batch_plan(ws, n, H.data(), W.data(), off.data(), &c, stream) != DBMP_OK) continue;
+            if (dbmp_batch_render(ws, params_dev, bitmap_id_dev, atlas, alpha_max, bg, T_stop, DBMP_BATCH_BIN,
+                                  image_dev, T_final_dev, n_last_dev, dL_dimage_dev, dparams_dev, stream) != DBMP_OK)
+                continue;
+            DbmpDeviceStatus s0;
+            DbmpBinStats bs;
+            if (dbmp_status_poll(ws, stream, &s0) != DBMP_OK) continue;   // e.g. capacity: not a candidate
+            if (dbmp_bin_stats(ws, stream, &bs) != DBMP_OK) continue;
+            pairs[i] = bs.pairs;
+            if (fewest < 0 || bs.pairs < fewest) fewest = bs.pairs;
+        }
+        n_tiles_try = 0;
+        int32_t kept[3];
+        int64_t kp[3];
+        for (int i = 0; i < 3; ++i) {
+            if (pairs[i] < 0 || (double)pairs[i] > (double)ws->tune_prune * (double)std::max<int64_t>(fewest, 1))
+                continue;
+            int j = n_tiles_try++;   // insertion by increasing entries
+            while (j > 0 && kp[j - 1] > pairs[i]) {
+                kept[j] = kept[j - 1];
+                kp[j] = kp[j - 1];
+                --j;
+            }
+            kept[j] = tiles[i];
+            kp[j] = pairs[i];
+        }
+        for (int i = 0; i < n_tiles_try; ++i) tiles[i] = kept[i];
+    }
     const int32_t batches[] = {32, 64};
     const int32_t ppts[] = {1, 2, 4};
     const bool want_f = (mode & DBMP_BATCH_FWD) != 0, want_b = (mode & DBMP_BATCH_BWD) != 0;
@@ -815,7 +861,8 @@ int32_t dbmp_autotune(DbmpWorkspace *ws, const float *params_dev, const int32_t 
         cudaEventElapsedTime(&ms, e0, e1);
         return ms / (float)reps;
     };
-    for (int32_t t : tiles) {
+    for (int ti = 0; ti < n_tiles_try; ++ti) {
+        const int32_t t = tiles[ti];
         for (int32_t b : batches) {
             float bin_ms = -1.0f, f_best = 1e30f, g_best = 1e30f;
             int32_t pf = 0, pb = 0;

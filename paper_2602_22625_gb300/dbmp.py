@@ -31,6 +31,7 @@ EXPORTS = (
     "dbmp_atlas_update", "dbmp_workspace_bytes", "dbmp_workspace_create", "dbmp_workspace_destroy",
     "dbmp_status_poll", "dbmp_bin", "dbmp_get_tile_lists", "dbmp_render_fwd", "dbmp_render_bwd",
     "dbmp_mse_grad", "dbmp_adam_step", "dbmp_batch_plan", "dbmp_batch_render", "dbmp_autotune",
+    "dbmp_autotune_set_prune",
     "dbmp_render_fwd_static", "dbmp_gemm_bf16", "dbmp_proposer_num_params", "dbmp_proposer_create",
     "dbmp_proposer_destroy", "dbmp_proposer_set_params", "dbmp_proposer_get", "dbmp_propose",
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
@@ -134,6 +135,7 @@ def load(build_if_missing: bool = True):
                                      _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
         "dbmp_batch_render_mse": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32,
                                          _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "dbmp_autotune_set_prune": (_i32, [_vp, _f32]),
         "dbmp_autotune": (_i32, [_vp, _vp, _vp, _vp, _f32, ctypes.POINTER(DbmpBackground), _f32, _i32,
                                  _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(DbmpTuning),
                                  ctypes.POINTER(_f32), _vp]),
@@ -353,6 +355,12 @@ def dbmp_batch_render_mse(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, m
     _check(load().dbmp_batch_render_mse(ws, _ptr(params), _ptr(bitmap_id), atlas, alpha_max, ctypes.byref(bg),
                                         T_stop, mode, _ptr(target), _ptr(image), _ptr(T_final), _ptr(n_last),
                                         _ptr(dL_dimage), _ptr(dparams), _ptr(loss), _stream(stream)))
+
+
+def dbmp_autotune_set_prune(ws, max_pairs_ratio):
+    """0: dbmp_autotune times every tile size; r > 0: only those whose binning lists at
+    most r x the entries of the sparsest size, in increasing order of entries."""
+    _check(load().dbmp_autotune_set_prune(ws, float(max_pairs_ratio)))
 
 
 def dbmp_autotune(ws, params, bitmap_id, atlas, alpha_max, bg, T_stop, mode, image, T_final, n_last,

@@ -349,6 +349,49 @@ def test_autotune_picks_a_supported_tuning():
         D.dbmp_atlas_destroy(atlas)
 
 
+@pytest.mark.parametrize("which", ["main", "tiny_prims"])
+def test_density_guided_autotune_agrees_with_the_exhaustive_search(which):
+    """The tile-density statistics (Sec. S4) feeding the search: with tile sizes that
+    list more than 2x the entries of the sparsest one left untimed, the autotuner picks
+    the exhaustive search's tile size, at a time within noise of its best.  The main
+    workload's primitives span many tiles (the search keeps tile 32 only); primitives
+    of a few pixels hit one tile at any size, so there every tile size is timed."""
+    cuda()
+    if which == "main":
+        sc = inputs.main()
+    else:
+        p, b = inputs.primitives(77, 20000, 1024, 1024, 16, "uniform", (0.002, 0.004))
+        sc = inputs.Scene("tiny_prims", 1024, 1024, p, b, inputs.strokes16())
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, (sc.H // 8) * (sc.W // 8), 64 << 20, 1)
+    try:
+        p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
+        image = torch.empty(3, sc.H, sc.W, device="cuda")
+        T = torch.empty(sc.H, sc.W, device="cuda")
+        nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+        dL = torch.full((3, sc.H, sc.W), 1e-6, device="cuda")
+        dp = torch.zeros(sc.N, 8, device="cuda")
+        picks = {}
+        for ratio in (0.0, 2.0, 0.0, 2.0):
+            D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N])
+            D.dbmp_autotune_set_prune(ws, ratio)
+            best, ms = D.dbmp_autotune(ws, p, b, atlas, 1.0, D.make_background((1, 1, 1)), 1e-6,
+                                       D.BATCH_FWD | D.BATCH_BWD, image, T, nl, dL, dp, reps=3)
+            picks.setdefault(ratio, []).append((tuple(best), ms))
+        print(which, picks)
+        ex_tiles = {t[0] for t, _ in picks[0.0]}
+        pr_tiles = {t[0] for t, _ in picks[2.0]}
+        best_ex = min(ms for _, ms in picks[0.0])
+        best_pr = min(ms for _, ms in picks[2.0])
+        assert pr_tiles & ex_tiles, picks
+        assert best_pr <= 1.05 * best_ex, picks
+        with pytest.raises(D.DbmpError):
+            D.dbmp_autotune_set_prune(ws, -1.0)
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+
+
 @pytest.mark.parametrize("tuning", [(16, 32, 4), (8, 64, 1), (32, 32, 2)], ids=lambda t: f"t{t[0]}b{t[1]}p{t[2]}")
 def test_poisoned_workspace_changes_nothing(tuning):
     """Every scratch buffer of the workspace filled with NaN / -1 before planning:
