@@ -115,7 +115,9 @@ typedef struct {
 /* Device bytes a workspace with these limits holds. */
 int32_t dbmp_workspace_bytes(const DbmpLimits *limits, size_t *bytes);
 /* Allocates a workspace (device memory: per-primitive records, tile lists,
- * per-chunk histograms, gradient accumulators, status block). */
+ * per-chunk histograms, gradient accumulators, status block, and a record of the
+ * forward's surviving (primitive, list position) pairs for the backward, max_pairs/8
+ * entries of 8 bytes). */
 int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out);
 int32_t dbmp_workspace_destroy(DbmpWorkspace *ws);
 /* Testing aid, in place of a memory sanitizer: fills every scratch buffer of the
@@ -267,6 +269,11 @@ int32_t dbmp_render_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBac
  * shuffles, then added with one atomic per primitive per warp, so dparams is
  * exact up to float32 summation order.  The chain rule to s and nu reads the
  * params_dev given to dbmp_bin: that buffer must still hold the same values.
+ * When the workspace's last forward rendered the same lists with the same region
+ * shape, the backward walks the records that forward kept per region (those that
+ * passed its region test) instead of re-reading and re-testing the tile lists;
+ * a region whose pixels' last layers lie beyond what that forward tested (maps from
+ * another forward with a smaller T_stop) is walked from its list as before.
  *   dparams_dev  float32 [N][8], ACCUMULATED into (zero it first). */
 int32_t dbmp_render_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *bg,
                         float T_stop, const float *dL_dimage_dev, const float *dL_dalpha_dev,

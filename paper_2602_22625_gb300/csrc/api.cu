@@ -79,6 +79,11 @@ struct DbmpWorkspace {
     int32_t hist_half = 0;                 // the half the next forward counts into (zeroed)
     // the order matches the current plan and the forward's regions (0: none yet)
     int32_t order_items = 0;
+    int2 *surv = nullptr;                  // [surv_cap] survivor record of the last forward
+    int4 *surv_tab = nullptr;              // [item_cap] its per-region entries
+    int64_t surv_cap = 0;
+    // regions the last forward recorded survivors for, on the current lists (0: none)
+    int32_t surv_items = 0;
     // host copy of the current plan
     std::vector<CanvasDesc> plan;
     std::vector<int32_t> plan_H, plan_W, plan_off;
@@ -102,6 +107,13 @@ namespace {
 // tiles than max_tiles) renders in list-length order without recording costs.
 int64_t item_capacity(const DbmpLimits &l) { return 32 * (int64_t)l.max_tiles; }
 
+// Entries of the survivor record: one per tile-list entry that passes a region test
+// before its warp saturates, which on the workloads measured is under 1/8 of the list
+// entries (a forward whose warps need more records fewer regions, never fails).
+int64_t surv_capacity(const DbmpLimits &l) {
+    return std::min<int64_t>(std::max<int64_t>(l.max_pairs / 8, 1 << 16), ((int64_t)1 << 31) - 1);
+}
+
 size_t ws_bytes(const DbmpLimits &l) {
     size_t b = 0;
     b += sizeof(PrimRec) * (size_t)l.max_prims;
@@ -115,6 +127,7 @@ size_t ws_bytes(const DbmpLimits &l) {
     b += sizeof(DevStatus);
     b += sizeof(unsigned long long) * kBinStatsWords;
     b += 2 * sizeof(int32_t) * (size_t)item_capacity(l) + sizeof(int32_t) * 128;
+    b += sizeof(int2) * (size_t)surv_capacity(l) + sizeof(int4) * (size_t)item_capacity(l);
     return b;
 }
 
@@ -249,6 +262,7 @@ int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const
     ws->Wb = atlas->Wb;
     ws->alpha_max = alpha_max;
     ws->binned = true;
+    ws->surv_items = 0;   // new lists: the survivor record no longer applies
     return DBMP_OK;
 }
 
@@ -275,6 +289,9 @@ RenderArgs make_args(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackgr
     a.row0 = ws->row0;
     a.row1 = ws->row1;
     a.n_prims = ws->N;
+    a.surv = ws->surv;
+    a.surv_tab = ws->surv_tab;
+    a.surv_cap = ws->surv_cap;
     return a;
 }
 
@@ -320,7 +337,12 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
         a.item_hist = hist;
     }
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, kFwdGroupBytes, st), "status reset");
+    // survivors recorded for the backward when it composites the same regions
+    const bool record = ws->surv && items <= ws->item_cap && ws->cfg.ppt == ws->cfg.bwd_ppt();
+    if (!record) a.surv = nullptr;
+    ws->surv_items = 0;
     DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
+    if (record) ws->surv_items = items;
     if (ordered) {
         DBMP_CUDA(launch_item_order(ws->item_cost, hist, next, ws->item_order, items, st), "region order");
         ws->order_items = items;
@@ -343,9 +365,12 @@ int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     if (ws->order_items > 0 && ws->order_items <= ws->item_cap &&
         ws->order_items == render_items(ws->cfg, ws->n_tiles, true))
         a.item_order = ws->item_order;
+    // the forward's survivors, when it recorded them for these regions on these lists
+    a.surv_use = ws->surv_items > 0 && ws->surv_items == render_items(ws->cfg, ws->n_tiles, true) &&
+                 ws->cfg.ppt == ws->cfg.bwd_ppt();
     DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, kBwdGroupBytes, st), "status reset");
     DBMP_CUDA(launch_bwd(a, ws->cfg, st), "backward launch");
-    DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, st), "gradient finalize");
+    DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, 0.5f * (float)(atlas->Wb - 1), 0.5f * (float)(atlas->Hb - 1), st), "gradient finalize");
     return DBMP_OK;
 }
 
@@ -454,7 +479,10 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         {(void **)&ws->item_cost, sizeof(int32_t) * (size_t)item_capacity(l)},
         {(void **)&ws->item_order, sizeof(int32_t) * (size_t)item_capacity(l)},
         {(void **)&ws->item_hist, sizeof(int32_t) * 128},
+        {(void **)&ws->surv, sizeof(int2) * (size_t)surv_capacity(l)},
+        {(void **)&ws->surv_tab, sizeof(int4) * (size_t)item_capacity(l)},
     };
+    ws->surv_cap = surv_capacity(l);
     for (auto &r : reqs) {
         cudaError_t e = cudaMalloc(r.p, r.n);
         if (e != cudaSuccess) {
@@ -496,11 +524,14 @@ int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream) {
         {ws->item_cost, sizeof(int32_t) * (size_t)item_capacity(l)},
         {ws->item_order, sizeof(int32_t) * (size_t)item_capacity(l)},
         {ws->item_hist, sizeof(int32_t) * 128},
+        {ws->surv, sizeof(int2) * (size_t)surv_capacity(l)},
+        {ws->surv_tab, sizeof(int4) * (size_t)item_capacity(l)},
     };
     for (auto &b : bufs) DBMP_CUDA(cudaMemsetAsync(b.p, 0xFF, b.n, st), "poison");
     // the bucket counts are state that must start at zero, not scratch
     DBMP_CUDA(cudaMemsetAsync(ws->item_hist, 0, sizeof(int32_t) * 128, st), "poison");
     ws->order_items = 0;
+    ws->surv_items = 0;
     return DBMP_OK;
 }
 
@@ -508,7 +539,7 @@ int32_t dbmp_workspace_destroy(DbmpWorkspace *ws) {
     if (!ws) return DBMP_OK;
     void *ptrs[] = {ws->rec,    ws->rect,   ws->graw,      ws->tile_off,   ws->tile_order, ws->list,
                     ws->hist,   ws->canvas, ws->status,    ws->stats,      ws->item_cost,  ws->item_order,
-                    ws->item_hist};
+                    ws->item_hist, ws->surv, ws->surv_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ws;
@@ -562,7 +593,10 @@ int32_t dbmp_bin(DbmpWorkspace *ws, int32_t H, int32_t W, int32_t tile, const fl
     const bool same = !ws->persistent && ws->n_canvas == 1 && ws->plan_H.size() == 1 && ws->plan_H[0] == H &&
                       ws->plan_W[0] == W && ws->cfg.tile == tile;
     if (int32_t r = build_plan(ws, 1, &H, &W, off, tile)) return r;
-    if (!same) ws->order_items = 0;   // another canvas: the region order no longer applies
+    if (!same) {   // another canvas: the region order and the survivor record no longer apply
+        ws->order_items = 0;
+        ws->surv_items = 0;
+    }
     ws->persistent = false;
     cudaStream_t st = (cudaStream_t)stream;
     k_set_canvas<<<1, 1, 0, st>>>(ws->plan[0], ws->canvas);
@@ -654,6 +688,7 @@ int32_t dbmp_batch_plan(DbmpWorkspace *ws, int32_t n_canvas, const int32_t *H, c
     ws->binned = false;
     ws->row0 = ws->row1 = 0;
     ws->order_items = 0;
+    ws->surv_items = 0;
     cudaStream_t st = (cudaStream_t)stream;
     DBMP_CUDA(cudaStreamSynchronize(st), "plan sync");
     DBMP_CUDA(cudaMemcpy(ws->canvas, ws->plan.data(), sizeof(CanvasDesc) * ws->plan.size(),

@@ -284,6 +284,18 @@ struct RenderArgs {
     double *mse_loss;
     float mse_scale;            // float(2 / n)
     double mse_inv_n;           // 1 / n, n = 3 x pixels of all canvases
+    // Survivor record (null: off).  Forward: warp w of the grid appends every batch's
+    // records that passed the region test, as (primitive, list position), to its own
+    // segment surv[w surv_wcap, (w + 1) surv_wcap), and describes region i in
+    // surv_tab[i] = (first entry, count, end of the list range it tested, 0), count -1
+    // when not recorded (segment full, region outside the row window).  Backward
+    // (surv_use): a recorded region whose range covers the pixels' last layers walks its
+    // survivors instead of re-reading and re-testing its tile's list.
+    int2 *surv;
+    int4 *surv_tab;
+    int64_t surv_cap;           // entries of surv (the launch divides them among its warps)
+    int32_t surv_wcap;          // entries per warp (set by the launch)
+    int32_t surv_use;
 };
 
 }  // namespace dbmp

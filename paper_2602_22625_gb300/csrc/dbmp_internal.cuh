@@ -120,7 +120,7 @@ cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t s
 // dparams += chain rule of the raw sums graw, which are zeroed after reading (graw is
 // zero before every backward: zeroed at workspace creation, left zero by this kernel).
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
-                                 float *dparams, int32_t N, cudaStream_t st);
+                                 float *dparams, int32_t N, float kw, float kv, cudaStream_t st);
 // Streaming multiprocessors of the current device (queried once per device).
 int sm_count();
 // Texel plane (row pitch `pitch` floats) and summed-area tables of an atlas from

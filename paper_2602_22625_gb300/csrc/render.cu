@@ -58,6 +58,7 @@ __device__ __forceinline__ int find_canvas_tile(const CanvasDesc *cv, int n, int
 template <int RPL>
 struct Prefetch {
     float4 q0[RPL], q1[RPL], q2[RPL];
+    int pos[RPL];              // list positions (survivor record only)
     unsigned bad;              // checked build: bit r set for an out-of-range list entry
 };
 
@@ -165,6 +166,41 @@ __device__ __forceinline__ int compact(const Prefetch<RPL> &pf, int e0, int n, P
     return base;
 }
 
+// Issues the loads of survivor-record entries [e0, e0 + n) and of their primitives'
+// records (lane l: entries l + 32 r).
+template <int RPL>
+__device__ __forceinline__ void prefetch_rec(Prefetch<RPL> &pf, const RenderArgs &a, int64_t e0, int n, int lane) {
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int j = lane + 32 * r;
+        if (j < n) {
+            const int2 e = __ldg(a.surv + e0 + j);
+            pf.pos[r] = e.y;
+            const float4 *p = reinterpret_cast<const float4 *>(a.rec + e.x);
+            pf.q0[r] = __ldg(p);
+            pf.q1[r] = __ldg(p + 1);
+            pf.q2[r] = __ldg(p + 2);
+        }
+    }
+}
+
+// Writes n prefetched survivor records to sh[0 .. n) with their list positions.
+template <int RPL>
+__device__ __forceinline__ void place(const Prefetch<RPL> &pf, int n, PrimRec *sh, int *pos, int lane) {
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int j = lane + 32 * r;
+        if (j < n) {
+            float4 *d = reinterpret_cast<float4 *>(sh + j);
+            d[0] = pf.q0[r];
+            d[1] = pf.q1[r];
+            d[2] = pf.q2[r];
+            pos[j] = pf.pos[r];
+        }
+    }
+    __syncwarp();
+}
+
 struct Region {
     int raw;          // region id: tile * R + region within the tile
     CanvasDesc d;
@@ -260,18 +296,27 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
     if (lane < 4) stats.v[lane] = 0ull;
     __syncwarp();
     float mse_s = 0.0f, mse_c = 0.0f;     // this lane's compensated sum of (I - I*)^2
+    // this warp's segment of the survivor record and its fill
+    const int64_t sbase = (int64_t)(blockIdx.x * kWarpsPerBlock + warp) * a.surv_wcap;
+    int sfill = 0;
 
     const int row1 = a.row1 > 0 ? a.row1 : 0x7fffffff;
     for (int item = next_item(&a.status->queue_fwd, lane); item < n_items;
          item = next_item(&a.status->queue_fwd, lane)) {
         const Region g = region_of<TILE, PPT>(a, item);
         if (g.y0 < a.row0 || g.y0 >= row1) {   // outside the row window
-            if (a.item_cost && lane == 0) {
-                a.item_cost[g.raw] = 1;
-                atomicAdd(a.item_hist, 1);
+            if (lane == 0) {
+                if (a.item_cost) {
+                    a.item_cost[g.raw] = 1;
+                    atomicAdd(a.item_hist, 1);
+                }
+                if (a.surv) a.surv_tab[g.raw] = make_int4(0, -1, 0, 0);
             }
             continue;
         }
+        const int sfirst = sfill;   // the region's first entry in the segment
+        bool srec = a.surv != nullptr;
+        int tested = 0;             // end of the list range compacted
         const int x = g.x0 + lane % RW;
         const float px = (float)x;
         float py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
@@ -299,6 +344,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
                 const int n = min(BATCH, g.len - b0);
                 const int m = compact<RPL>(pf, b0, n, sh, pos, a, rx0, ry0, rw, rh, kw, kv, lane);
                 sv_it += m;
+                tested = b0 + n;
+                if (srec) {   // append the batch's survivors to the record
+                    if (sfill + m <= a.surv_wcap) {
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r)
+                            if (lane + 32 * r < m)
+                                a.surv[sbase + sfill + lane + 32 * r] =
+                                    make_int2(sh[lane + 32 * r].index, pos[lane + 32 * r]);
+                        sfill += m;
+                    } else {
+                        srec = false;
+                    }
+                }
                 if (b0 + BATCH < g.len)
                     prefetch<RPL>(pf, a, g.start + b0 + BATCH, min(BATCH, g.len - b0 - BATCH), lane);
                 for (int t = 0; t < m; ++t) {
@@ -411,7 +469,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
                 a.item_cost[g.raw] = c;
                 atomicAdd(a.item_hist + (31 - __clz(c)), 1);
             }
+            if (a.surv)
+                a.surv_tab[g.raw] = srec ? make_int4((int)(sbase + sfirst), sfill - sfirst, tested, 0)
+                                         : make_int4(0, -1, 0, 0);
         }
+        if (!srec) sfill = sfirst;   // a region not recorded leaves no entries
     }
     __syncwarp();
     if (a.mse_target) {
@@ -560,19 +622,40 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
         const float rw = (float)(RW - 1), rh = (float)(RH - 1);
 
-        // batches [lo, hi) from the back of the region's walk
-        int hi = my_max + 1;
+        // The forward's survivors of this region, when it recorded them up to beyond
+        // every pixel's last layer: the walk then reads them in batches from the back
+        // (entries behind the last layer are skipped) and tests nothing.  Otherwise
+        // batches [lo, hi) of list positions from the back of the region's walk.
+        int4 rec = make_int4(0, -1, 0, 0);
+        if (a.surv_use) rec = a.surv_tab[g.raw];
+        const bool use_rec = rec.y >= 0 && my_max < rec.z;
+        int hi = use_rec ? rec.y : my_max + 1;
         int lo = max(0, hi - BATCH);
         Prefetch<RPL> pf;
-        prefetch<RPL>(pf, a, g.start + lo, hi - lo, lane);
+        if (use_rec)
+            prefetch_rec<RPL>(pf, a, rec.x + lo, hi - lo, lane);
+        else
+            prefetch<RPL>(pf, a, g.start + lo, hi - lo, lane);
         while (hi > 0) {
-            const int m = compact<RPL>(pf, lo, hi - lo, sh, pos, a, rx0, ry0, rw, rh, kw, kv, lane);
+            int m;
+            if (use_rec) {
+                m = hi - lo;
+                place<RPL>(pf, m, sh, pos, lane);
+            } else {
+                m = compact<RPL>(pf, lo, hi - lo, sh, pos, a, rx0, ry0, rw, rh, kw, kv, lane);
+            }
             sv_it += m;
             const int nlo = max(0, lo - BATCH);
-            if (lo > 0) prefetch<RPL>(pf, a, g.start + nlo, lo - nlo, lane);
+            if (lo > 0) {
+                if (use_rec)
+                    prefetch_rec<RPL>(pf, a, rec.x + nlo, lo - nlo, lane);
+                else
+                    prefetch<RPL>(pf, a, g.start + nlo, lo - nlo, lane);
+            }
             for (int t = m - 1; t >= 0; --t) {
-                const PrimRec r = sh[t];
                 const int j = pos[t];
+                if (j > my_max) continue;   // behind every pixel's last layer (recorded survivors)
+                const PrimRec r = sh[t];
                 const ColXf cx = col_xf(r, kw, kv, px);
                 if constexpr (PPT % 2 == 0) {
 #pragma unroll
@@ -684,12 +767,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                         Y[k] = Yn.x;
                         Y[k + 1] = Yn.y;
                     }
-                    s0 = S0.x + S0.y;
-                    s1 = S1.x + S1.y;
-                    s2 = S2.x + S2.y;
-                    s3u = S3u.x + S3u.y;
-                    s3v = S3v.x + S3v.y;
-                    s4 = S4.x + S4.y;
+                    s0 = -S0.x - S0.y;
+                    s1 = -S1.x - S1.y;
+                    s2 = -S2.x - S2.y;
+                    s3u = -S3u.x - S3u.y;
+                    s3v = -S3v.x - S3v.y;
+                    s4 = -S4.x - S4.y;
                     s5 = -S5.x - S5.y;
                     s6 = -S6.x - S6.y;
                     s7 = -S7.x - S7.y;
@@ -723,11 +806,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                 }
                 {
                     float v[8];
-                    v[0] = ra * s0;
-                    v[1] = ra * s1;
-                    v[2] = ra * fmaf(-kv, s1, fmaf(-kw, s0, s2));
-                    v[3] = ra * (fmaf(rho, s3u, fmaf(-kw, s0, kv * s1)) - irho * s3v);
-                    v[4] = ra * s4;
+                    (void)ra;
+                    v[0] = s0;
+                    v[1] = s1;
+                    v[2] = s2;
+                    v[3] = fmaf(rho, s3u, -irho * s3v);
+                    v[4] = s4;
                     v[5] = s5;
                     v[6] = s6;
                     v[7] = s7;
@@ -794,7 +878,7 @@ __global__ void k_item_order(const int32_t *__restrict__ cost, int32_t *__restri
 //   nu: S4 (1 - sigmoid(nu))    c_j: S_{5+j} chat_j (1 - chat_j)
 // The sums are read and then zeroed, so graw is zero again for the next backward.
 __global__ void k_finalize(const float *__restrict__ params, const PrimRec *__restrict__ rec,
-                           float *__restrict__ graw, float *__restrict__ dparams, int32_t N) {
+                           float *__restrict__ graw, float *__restrict__ dparams, int32_t N, float kw, float kv) {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -803,7 +887,9 @@ __global__ void k_finalize(const float *__restrict__ params, const PrimRec *__re
     float4 *g4 = reinterpret_cast<float4 *>(graw + 8 * (size_t)i);
     const float4 lo = g4[0], hi = g4[1];
     g4[0] = g4[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const float S[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    const float a = r.a;
+    const float S[8] = {a * lo.x, a * lo.y, a * fmaf(-kv, lo.y, fmaf(-kw, lo.x, lo.z)),
+                        a * fmaf(kv, lo.y, fmaf(-kw, lo.x, lo.w)), a * hi.x, hi.y, hi.z, hi.w};
     const float *p = params + 8 * (size_t)i;
     float *o = dparams + 8 * (size_t)i;
     const float s = p[2];
@@ -883,7 +969,13 @@ cudaError_t launch_t(const RenderArgs &a, bool fwd, cudaStream_t st) {
     const int32_t n_items = a.n_tiles * R;
     if (fwd) {
         const int grid = persistent_grid((const void *)k_fwd<TILE, PPT, BATCH>, n_items);
-        k_fwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);
+        RenderArgs b = a;
+        if (b.surv) {   // the survivor record's entries, divided among the grid's warps
+            const int64_t w = b.surv_cap / ((int64_t)grid * kWarpsPerBlock);
+            b.surv_wcap = (int32_t)(w < 0x7fffffff ? w : 0x7fffffff);
+            if (b.surv_wcap < 1) b.surv = nullptr;
+        }
+        k_fwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(b, n_items);
     } else {
         const int grid = persistent_grid((const void *)k_bwd<TILE, PPT, BATCH>, n_items);
         k_bwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);
@@ -960,10 +1052,10 @@ cudaError_t launch_item_order(const int32_t *cost, int32_t *hist, int32_t *next_
 }
 
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,
-                                 float *dparams, int32_t N, cudaStream_t st) {
+                                 float *dparams, int32_t N, float kw, float kv, cudaStream_t st) {
     if (N > 0) {
         const cudaError_t e = launch_pdl(k_finalize, dim3((N + 255) / 256), dim3(256), 0, st, params, rec, graw,
-                                         dparams, N);
+                                         dparams, N, kw, kv);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

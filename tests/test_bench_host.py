@@ -12,11 +12,16 @@ import bench
 CSRC = os.path.join("paper_2602_22625_gb300", "csrc")
 
 
-def test_traffic_record_matches_the_current_sources():
+def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on():
+    import hashlib
     for key in ("fwd", "bwd"):
         e = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))[key]
+        src = b"".join(open(os.path.join(bench.ROOT, CSRC, n), "rb").read() for n in e["sources"])
         got = bench.traffic_for(key, e["tile"], e["batch"], e["ppt"])
-        assert got == e["dram_read_bytes"] + e["dram_write_bytes"] and got > 0
+        if hashlib.sha256(src).hexdigest() == e["sha256"]:
+            assert got == e["dram_read_bytes"] + e["dram_write_bytes"] and got > 0
+        else:   # the kernels changed since the capture: the bench reports no traffic
+            assert got is None
         assert bench.traffic_for(key, 8, e["batch"], e["ppt"]) is None   # another tuning
 
 
@@ -24,9 +29,14 @@ def test_traffic_record_matches_the_current_sources():
 def test_traffic_record_is_dropped_when_a_profiled_source_changes(tmp_path, monkeypatch, changed):
     os.makedirs(tmp_path / "profiles")
     os.makedirs(tmp_path / CSRC)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles")
+    import hashlib
     for n in ("render.cu", "compositor.cuh"):
         shutil.copy(os.path.join(bench.ROOT, CSRC, n), tmp_path / CSRC / n)
+    # a record taken on exactly these sources
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    src = b"".join(open(tmp_path / CSRC / n, "rb").read() for n in rec["bwd"]["sources"])
+    rec["bwd"]["sha256"] = hashlib.sha256(src).hexdigest()
+    json.dump(rec, open(tmp_path / "profiles" / "traffic.json", "w"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_for("bwd", 32, 32, 4) is not None
     with open(tmp_path / CSRC / changed, "a") as f:
