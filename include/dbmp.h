@@ -184,8 +184,12 @@ int32_t dbmp_status_poll(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpDeviceStat
 /* Scaling statistics of the workspace's last binning (Sec. S4, "Additional scaling
  * statistics": normalised footprint A_i / (H W), tile-hit degree tau_i, per-tile
  * density d_t), summed over the plan's canvases.  A_i is the padded box area
- * (2 hx + 2)(2 hy + 2) of the binning specification below (FP64 from its fp32
- * half-extents), normalised by its own canvas.  Histograms have 32 bins:
+ * (2 hx + 2)(2 hy + 2) of the bitmap's whole support rotated and scaled, with
+ * e_u = 1 + 2/(W_b-1), e_v = 1 + 2/(H_b-1), hx = |s| (|cos| e_u + |sin| e_v),
+ * hy = |s| (|sin| e_u + |cos| e_v) and the sine and cosine of the binning
+ * specification below (FP64 from the fp32 half-extents), normalised by its own
+ * canvas; it does not depend on which texels of the bitmap are non-zero.
+ * Histograms have 32 bins:
  *   tau_hist[b]   listed primitives (tau_i >= 1) with floor(log2 tau_i) = b
  *   d_hist[b]     tiles with d_t >= 1 and floor(log2 d_t) = b
  *   foot_hist[b]  listed primitives with A_i / (H W) in [2^-(b+1), 2^-b) (b = 0
@@ -205,17 +209,25 @@ int32_t dbmp_bin_stats(DbmpWorkspace *ws, dbmp_stream_t stream, DbmpBinStats *ou
 /* ------------------------------------------------------------------------- */
 /* Per-primitive preprocessing and tile lists for one canvas H x W split into
  * tile x tile pixel tiles (tile in {8, 16, 32}).  A primitive is listed in
- * every tile its padded bounding box overlaps; each tile's list holds primitive
- * indices in increasing (front-to-back) order.  The bounding box is the fp32
- * specification below, evaluated one IEEE operation at a time (no fused
+ * every tile its bounding box overlaps; each tile's list holds primitive indices
+ * in increasing (front-to-back) order.  The box holds every pixel where the
+ * primitive's sample can be non-zero: with zero padding that needs bitmap
+ * coordinates within one texel of the bitmap's non-zero texels, whose first and
+ * last columns and rows [u0, u1] x [v0, v1] the atlas records per bitmap.  It is
+ * the fp32 specification below, evaluated one IEEE operation at a time (no fused
  * multiply-add), so the lists are bit-exact and reproducible:
- *     (|sin|, |cos|) of theta by Cody-Waite reduction by pi/2 and degree-9/8
- *     Taylor polynomials (|theta| > 65536: both taken as 1);
- *     e_u = 1 + 2/(W_b-1), e_v = 1 + 2/(H_b-1), s' = |s|;
- *     hx = s' (|cos| e_u + |sin| e_v), hy = s' (|sin| e_u + |cos| e_v);
- *     tx0 = floor(((x - hx) - 1) / tile), tx1 = floor(((x + hx) + 1) / tile),
+ *     (sin, cos) of theta by Cody-Waite reduction by pi/2, degree-9/8 Taylor
+ *     polynomials and the quadrant's signs;
+ *     kw = (W_b-1)/2, kv = (H_b-1)/2; uc = ((u0 + u1 - (W_b-1)) / 2) / kw,
+ *     eu = ((u1 - u0 + 2) / 2) / kw, likewise vc, ev with v0, v1, kv;
+ *     dx = s (cos uc - sin vc), dy = s (sin uc + cos vc),
+ *     hx = |s| (|cos| eu + |sin| ev), hy = |s| (|sin| eu + |cos| ev)
+ *     (|theta| > 65536: dx = dy = 0, hx = hy = |s| (((|uc| + eu) + |vc|) + ev));
+ *     m = 1 + |s| 2^-19; cx = x + dx, cy = y + dy;
+ *     tx0 = floor(((cx - hx) - m) / tile), tx1 = floor(((cx + hx) + m) / tile),
  *     likewise ty0, ty1, clipped to the canvas' tiles.
- * Primitives with a non-finite parameter or s == 0 are not listed.
+ * Primitives with a non-finite parameter, s == 0 or an all-zero bitmap are not
+ * listed.
  *   params_dev     float32 [N][8] (x, y, s, theta, nu, c_r, c_g, c_b)
  *   bitmap_id_dev  int32 [N], each in [0, n_bmp); a primitive with an id
  *                  outside the atlas is not listed and is counted in the status
@@ -590,7 +602,7 @@ int32_t dbmp_alpha_loss_grad(const float *image_dev, const float *T_final_dev, c
  * dbmp_render_fwd (default tuning), from the plain atlas texels
  * (float32 [n_bmp][H_b][W_b]), with no DbmpWorkspace and no DbmpAtlas.  All
  * intermediate state lives in one scratch array compiled into the library
- * (about 6.1 MB of device memory).  Every GPU that loads the library holds it
+ * (about 6.3 MB of device memory).  Every GPU that loads the library holds it
  * until the process exits.  Maximum sizes:
  *     H, W <= 512;  N <= 4096;  n_bmp (H_b + 1)(W_b + 1) <= 32768;
  *     tile-list entries (sum_t d_t) <= 1 048 576.

@@ -467,20 +467,33 @@ int32_t oracle_eq_s5_dalpha(int32_t N, const float *params, const int32_t *bitma
  * below, one IEEE single-precision operation at a time (this file is compiled
  * with -ffp-contract=off, so no fused multiply-add).  Its sine and cosine come
  * from Cody-Waite reduction by pi/2 (three-part constant) and the Taylor series
- * of sin and cos to degree 9 / 8 on [-pi/4, pi/4]; they only size the box, which
- * is widened by a one-pixel margin, so the box always contains the support of the
- * primitive (|u| < 1 + 2/(W-1), |v| < 1 + 2/(H-1)).
+ * of sin and cos to degree 9 / 8 on [-pi/4, pi/4].
+ *
+ * The box holds the pixels where the primitive's sample M can be non-zero.  With
+ * zero padding (Sec. S1.1) M > 0 needs a non-zero tap, so only bitmap coordinates
+ * U in (u0 - 1, u1 + 1), V in (v0 - 1, v1 + 1) matter, where [u0, u1] x [v0, v1] are
+ * the first and last columns and rows of the bitmap holding a texel > 0 (an all-zero
+ * bitmap lists the primitive nowhere).  In the normalised coordinates of Eq. 1 that
+ * box has centre (uc, vc) and half-extents (eu, ev); the pixel offsets
+ * (dx, dy) = s (cos u - sin v, sin u + cos v) of its image form a rotated box with
+ * centre s (cos uc - sin vc, sin uc + cos vc) and axis-aligned half-extents
+ * hx = |s| (|cos| eu + |sin| ev), hy = |s| (|sin| eu + |cos| ev).  The margin
+ * m = 1 + |s| 2^-19 pixels exceeds the rounding of these steps and of the
+ * compositors' transform, so the box contains every pixel with M > 0.  For
+ * |theta| > 65536 (outside the reduction's range) the box is centred on (x, y)
+ * with hx = hy = |s| (|uc| + eu + |vc| + ev), which holds every rotation.
  *
  * A primitive is listed in tile (tx, ty) iff tx0 <= tx <= tx1 and ty0 <= ty <= ty1
- * with tx0 = floor((x - hx - 1)/T), tx1 = floor((x + hx + 1)/T) (same for y),
- * clipped to the canvas' tiles.  Lists hold primitive indices in increasing order
- * (front to back). */
+ * with tx0 = floor((cx - hx - m)/T), tx1 = floor((cx + hx + m)/T), cx = x + dx_c
+ * (same for y), clipped to the canvas' tiles.  Lists hold primitive indices in
+ * increasing order (front to back). */
 
-static void spec_abs_sincos(float th, float *as, float *ac) {
-    if (!(fabsf(th) <= 65536.0f)) { /* outside the reduction's exact range: bound by 1 */
-        *as = 1.0f;
-        *ac = 1.0f;
-        return;
+/* sin and cos of the specification; returns 0 (and 1, 1) for |th| > 65536. */
+static int spec_sincos(float th, float *sn, float *cs) {
+    if (!(fabsf(th) <= 65536.0f)) { /* outside the reduction's exact range */
+        *sn = 1.0f;
+        *cs = 1.0f;
+        return 0;
     }
     const float two_over_pi = 0.636619772367581343f;
     const float C1 = 1.5703125f;               /* pi/2 split in three parts */
@@ -501,34 +514,85 @@ static void spec_abs_sincos(float th, float *as, float *ac) {
     cp = cp * r2 + (1.0f / 24.0f);
     cp = cp * r2 + (-0.5f);
     float cr = 1.0f + r2 * cp;
-    long ki = (long)k;
-    if (ki & 1) {
-        *as = fabsf(cr);
-        *ac = fabsf(sr);
+    long q = ((long)k % 4 + 4) % 4; /* quadrant: th = k pi/2 + r */
+    if (q == 0) {
+        *sn = sr;
+        *cs = cr;
+    } else if (q == 1) {
+        *sn = cr;
+        *cs = -sr;
+    } else if (q == 2) {
+        *sn = -sr;
+        *cs = -cr;
     } else {
-        *as = fabsf(sr);
-        *ac = fabsf(cr);
+        *sn = -cr;
+        *cs = sr;
     }
+    return 1;
 }
 
-/* Tile rectangle of one primitive; returns 0 if it touches no tile. */
-static int spec_rect(const float *p, int32_t Hb, int32_t Wb, int32_t tile, int32_t ntx,
-                     int32_t nty, int32_t r[4]) {
+/* |sin|, |cos| of the specification (bounded by 1 outside the reduction's range). */
+static void spec_abs_sincos(float th, float *as, float *ac) {
+    float sn, cs;
+    spec_sincos(th, &sn, &cs);
+    *as = fabsf(sn);
+    *ac = fabsf(cs);
+}
+
+/* First and last column and row of bitmap b holding a texel > 0: box = {u0, u1, v0,
+ * v1}; {W_b, -1, H_b, -1} for an all-zero bitmap. */
+static void spec_nonzero_box(const float *atlas, int32_t b, int32_t Hb, int32_t Wb, int32_t box[4]) {
+    box[0] = Wb;
+    box[1] = -1;
+    box[2] = Hb;
+    box[3] = -1;
+    const float *P = atlas + (size_t)b * Hb * Wb;
+    for (int32_t v = 0; v < Hb; ++v)
+        for (int32_t u = 0; u < Wb; ++u)
+            if (P[(size_t)v * Wb + u] > 0.0f) {
+                if (u < box[0]) box[0] = u;
+                if (u > box[1]) box[1] = u;
+                if (v < box[2]) box[2] = v;
+                if (v > box[3]) box[3] = v;
+            }
+}
+
+/* Tile rectangle of one primitive whose bitmap's non-zero box is `box`; returns 0
+ * if it touches no tile. */
+static int spec_rect(const float *p, const int32_t box[4], int32_t Hb, int32_t Wb, int32_t tile,
+                     int32_t ntx, int32_t nty, int32_t r[4]) {
     for (int j = 0; j < 8; ++j)
         if (!isfinite(p[j])) return 0;
     if (p[2] == 0.0f) return 0;
-    float eu = 1.0f + 2.0f / (float)(Wb - 1);
-    float ev = 1.0f + 2.0f / (float)(Hb - 1);
-    float as, ac;
-    spec_abs_sincos(p[3], &as, &ac);
-    float s = fabsf(p[2]);
-    float hx = s * (ac * eu + as * ev);
-    float hy = s * (as * eu + ac * ev);
+    if (box[0] > box[1]) return 0; /* all-zero bitmap */
+    float kw = (float)(Wb - 1) * 0.5f, kv = (float)(Hb - 1) * 0.5f;
+    /* centre and half-extent of (u0 - 1, u1 + 1) in texels from the bitmap centre (exact) */
+    float cu = ((float)(box[0] + box[1]) - (float)(Wb - 1)) * 0.5f;
+    float hu = (float)(box[1] - box[0] + 2) * 0.5f;
+    float cv = ((float)(box[2] + box[3]) - (float)(Hb - 1)) * 0.5f;
+    float hv = (float)(box[3] - box[2] + 2) * 0.5f;
+    float uc = cu / kw, eu = hu / kw, vc = cv / kv, ev = hv / kv;
+    float sn, cs;
+    float s = p[2], as = fabsf(p[2]);
+    float dxc, dyc, hx, hy;
+    if (spec_sincos(p[3], &sn, &cs)) {
+        dxc = s * (cs * uc - sn * vc);
+        dyc = s * (sn * uc + cs * vc);
+        hx = as * (fabsf(cs) * eu + fabsf(sn) * ev);
+        hy = as * (fabsf(sn) * eu + fabsf(cs) * ev);
+    } else {
+        dxc = 0.0f;
+        dyc = 0.0f;
+        hx = as * (((fabsf(uc) + eu) + fabsf(vc)) + ev);
+        hy = hx;
+    }
+    float m = 1.0f + as * 1.9073486328125e-06f; /* 2^-19 */
+    float cx = p[0] + dxc, cy = p[1] + dyc;
     float inv_t = 1.0f / (float)tile;
-    float fx0 = floorf(((p[0] - hx) - 1.0f) * inv_t);
-    float fx1 = floorf(((p[0] + hx) + 1.0f) * inv_t);
-    float fy0 = floorf(((p[1] - hy) - 1.0f) * inv_t);
-    float fy1 = floorf(((p[1] + hy) + 1.0f) * inv_t);
+    float fx0 = floorf(((cx - hx) - m) * inv_t);
+    float fx1 = floorf(((cx + hx) + m) * inv_t);
+    float fy0 = floorf(((cy - hy) - m) * inv_t);
+    float fy1 = floorf(((cy + hy) + m) * inv_t);
     if (!(fx1 >= 0.0f) || !(fy1 >= 0.0f)) return 0;
     if (!(fx0 <= (float)(ntx - 1)) || !(fy0 <= (float)(nty - 1))) return 0;
     r[0] = fx0 < 0.0f ? 0 : (int32_t)fx0;
@@ -538,9 +602,11 @@ static int spec_rect(const float *p, int32_t Hb, int32_t Wb, int32_t tile, int32
     return 1;
 }
 
-/* Padded screen-space box area of each primitive, (2 hx + 2)(2 hy + 2) in FP64 from
- * the fp32 half-extents of the binning specification (the footprint A_i of the
- * scaling analysis, Sec. S4); -1 for a primitive the binning skips. */
+/* Padded screen-space box area of each primitive, (2 hx + 2)(2 hy + 2) in FP64, from
+ * the fp32 half-extents of the bitmap's whole support with its zero-padding ring
+ * (|u| < 1 + 2/(W-1), |v| < 1 + 2/(H-1)) rotated by theta and scaled by |s|: the
+ * footprint A_i of the scaling analysis (Sec. S4), whatever the bitmap holds; -1 for
+ * a primitive the binning skips as invalid. */
 void oracle_bin_footprint(int32_t N, const float *params, int32_t Hb, int32_t Wb, double *area) {
     for (int32_t i = 0; i < N; ++i) {
         const float *p = params + 8 * (size_t)i;
@@ -563,13 +629,19 @@ void oracle_bin_footprint(int32_t N, const float *params, int32_t Hb, int32_t Wb
 }
 
 /* Per-primitive tile rectangles: rects[4*i] = {tx0, ty0, tx1, ty1} or {0,0,-1,-1}
- * when the primitive touches no tile; tau[i] = number of tiles. */
+ * when the primitive touches no tile; tau[i] = number of tiles.  A primitive whose
+ * bitmap id is outside [0, n_bmp) touches no tile. */
 void oracle_bin_rects(int32_t H, int32_t W, int32_t tile, int32_t N, const float *params,
-                      int32_t Hb, int32_t Wb, int32_t *rects, int64_t *tau) {
+                      const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb,
+                      int32_t Wb, int32_t *rects, int64_t *tau) {
     int32_t ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
+    int32_t *boxes = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n_bmp > 0 ? n_bmp : 1));
+    for (int32_t b = 0; b < n_bmp; ++b) spec_nonzero_box(atlas, b, Hb, Wb, boxes + 4 * (size_t)b);
     for (int32_t i = 0; i < N; ++i) {
         int32_t r[4];
-        if (spec_rect(params + 8 * (size_t)i, Hb, Wb, tile, ntx, nty, r)) {
+        int32_t b = bitmap_id[i];
+        if (b >= 0 && b < n_bmp &&
+            spec_rect(params + 8 * (size_t)i, boxes + 4 * (size_t)b, Hb, Wb, tile, ntx, nty, r)) {
             memcpy(rects + 4 * (size_t)i, r, sizeof r);
             tau[i] = (int64_t)(r[2] - r[0] + 1) * (int64_t)(r[3] - r[1] + 1);
         } else {
@@ -580,6 +652,12 @@ void oracle_bin_rects(int32_t H, int32_t W, int32_t tile, int32_t N, const float
             tau[i] = 0;
         }
     }
+    free(boxes);
+}
+
+/* The non-zero box of each bitmap (testing aid): boxes[4*b] = {u0, u1, v0, v1}. */
+void oracle_nonzero_boxes(const float *atlas, int32_t n_bmp, int32_t Hb, int32_t Wb, int32_t *boxes) {
+    for (int32_t b = 0; b < n_bmp; ++b) spec_nonzero_box(atlas, b, Hb, Wb, boxes + 4 * (size_t)b);
 }
 
 /* The tile lists as a definition: for every tile t (row-major), every primitive
@@ -587,11 +665,12 @@ void oracle_bin_rects(int32_t H, int32_t W, int32_t tile, int32_t N, const float
  * boundaries (offsets[t] .. offsets[t+1]) and, if `list` is not NULL and K fits
  * in `cap`, the concatenated lists.  Returns K = sum_t d_t. */
 int64_t oracle_bin(int32_t H, int32_t W, int32_t tile, int32_t N, const float *params,
-                   int32_t Hb, int32_t Wb, int64_t *offsets, int32_t *list, int64_t cap) {
+                   const int32_t *bitmap_id, const float *atlas, int32_t n_bmp, int32_t Hb, int32_t Wb,
+                   int64_t *offsets, int32_t *list, int64_t cap) {
     int32_t ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
     int32_t *rects = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(N > 0 ? N : 1));
     int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
-    oracle_bin_rects(H, W, tile, N, params, Hb, Wb, rects, tau);
+    oracle_bin_rects(H, W, tile, N, params, bitmap_id, atlas, n_bmp, Hb, Wb, rects, tau);
     int64_t K = 0;
     for (int32_t ty = 0; ty < nty; ++ty)
         for (int32_t tx = 0; tx < ntx; ++tx) {
@@ -707,6 +786,7 @@ int64_t oracle_structure_init(int32_t H, int32_t W, const float *image, const fl
 
 /* The spec's |sin|, |cos| (exported so the tests can bound its error). */
 void oracle_spec_abs_sincos(float th, float *as, float *ac) { spec_abs_sincos(th, as, ac); }
+int oracle_spec_sincos(float th, float *sn, float *cs) { return spec_sincos(th, sn, cs); }
 
 int32_t oracle_num_threads(void) {
 #ifdef _OPENMP

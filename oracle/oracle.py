@@ -66,12 +66,16 @@ def lib():
                                           ctypes.c_int32, _f64p, ctypes.c_double, _f64p, _i32p]
         L.oracle_bin_rects.restype = None
         L.oracle_bin_rects.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, _f32p, ctypes.c_int32, ctypes.c_int32,
-                                       _i32p, _i64p]
+                                       ctypes.c_int32, _f32p, _i32p, _f32p, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, _i32p, _i64p]
         L.oracle_bin.restype = ctypes.c_int64
         L.oracle_bin.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                 _f32p, ctypes.c_int32, ctypes.c_int32, _i64p, _i32p,
-                                 ctypes.c_int64]
+                                 _f32p, _i32p, _f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 _i64p, _i32p, ctypes.c_int64]
+        L.oracle_nonzero_boxes.restype = None
+        L.oracle_nonzero_boxes.argtypes = [_f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p]
+        L.oracle_spec_sincos.restype = ctypes.c_int
+        L.oracle_spec_sincos.argtypes = [ctypes.c_float, _f32p, _f32p]
         L.oracle_spec_abs_sincos.restype = None
         L.oracle_spec_abs_sincos.argtypes = [ctypes.c_float, _f32p, _f32p]
         L.oracle_num_threads.restype = ctypes.c_int32
@@ -236,28 +240,47 @@ def eq_s5_dalpha(params, bitmap_id, atlas, x, y, g, gA=0.0, alpha_max=1.0):
     return out[:n], ks[:n]
 
 
-def bin_rects(H, W, tile, params, Hb, Wb):
-    """Per-primitive tile rectangles (N, 4) {tx0, ty0, tx1, ty1} and tau (N,)."""
+def _bin_inputs(params, bitmap_id, atlas):
     params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    bid = np.ascontiguousarray(np.broadcast_to(np.asarray(bitmap_id, np.int32), (params.shape[0],)))
+    atlas = np.ascontiguousarray(atlas, dtype=np.float32)
+    return params, bid, atlas
+
+
+def bin_rects(H, W, tile, params, bitmap_id, atlas):
+    """Per-primitive tile rectangles (N, 4) {tx0, ty0, tx1, ty1} and tau (N,)."""
+    params, bid, atlas = _bin_inputs(params, bitmap_id, atlas)
     N = params.shape[0]
+    nb, Hb, Wb = atlas.shape
     rects = np.zeros((max(N, 1), 4), np.int32)
     tau = np.zeros(max(N, 1), np.int64)
-    lib().oracle_bin_rects(H, W, tile, N, _p(params, _f32p), Hb, Wb, _p(rects, _i32p),
-                           _p(tau, _i64p))
+    lib().oracle_bin_rects(H, W, tile, N, _p(params, _f32p), _p(bid, _i32p), _p(atlas, _f32p), nb, Hb, Wb,
+                           _p(rects, _i32p), _p(tau, _i64p))
     return rects[:N], tau[:N]
 
 
-def bin(H, W, tile, params, Hb, Wb):
+def bin(H, W, tile, params, bitmap_id, atlas):
     """Tile lists (Sec. 3.1.1): (offsets (n_tiles+1,) int64, list (K,) int32)."""
-    params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    params, bid, atlas = _bin_inputs(params, bitmap_id, atlas)
     N = params.shape[0]
+    nb, Hb, Wb = atlas.shape
     ntx, nty = -(-W // tile), -(-H // tile)
     offsets = np.zeros(ntx * nty + 1, np.int64)
-    K = lib().oracle_bin(H, W, tile, N, _p(params, _f32p), Hb, Wb, _p(offsets, _i64p), None, 0)
+    args = (H, W, tile, N, _p(params, _f32p), _p(bid, _i32p), _p(atlas, _f32p), nb, Hb, Wb)
+    K = lib().oracle_bin(*args, _p(offsets, _i64p), None, 0)
     lst = np.zeros(max(K, 1), np.int32)
-    lib().oracle_bin(H, W, tile, N, _p(params, _f32p), Hb, Wb, _p(offsets, _i64p),
-                     _p(lst, _i32p), K)
+    lib().oracle_bin(*args, _p(offsets, _i64p), _p(lst, _i32p), K)
     return offsets, lst[:K]
+
+
+def nonzero_boxes(atlas):
+    """(n_bmp, 4) {u0, u1, v0, v1}: first and last column and row holding a texel > 0
+    ({W_b, -1, H_b, -1} for an all-zero bitmap)."""
+    atlas = np.ascontiguousarray(atlas, dtype=np.float32)
+    nb, Hb, Wb = atlas.shape
+    out = np.zeros((nb, 4), np.int32)
+    lib().oracle_nonzero_boxes(_p(atlas, _f32p), nb, Hb, Wb, _p(out, _i32p))
+    return out
 
 
 def spec_abs_sincos(theta):
@@ -265,6 +288,14 @@ def spec_abs_sincos(theta):
     b = ctypes.c_float()
     lib().oracle_spec_abs_sincos(float(np.float32(theta)), ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
+
+
+def spec_sincos(theta):
+    """(sin, cos, in range) of the binning specification."""
+    a = ctypes.c_float()
+    b = ctypes.c_float()
+    ok = lib().oracle_spec_sincos(float(np.float32(theta)), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value, bool(ok)
 
 
 # ---------------------------------------------------------------------------
@@ -385,15 +416,16 @@ def _log2_bin(v):
     return np.array([int(x).bit_length() - 1 for x in np.asarray(v).ravel()], np.int64)
 
 
-def bin_stats(H, W, tile, params, Hb, Wb):
+def bin_stats(H, W, tile, params, bitmap_id, atlas):
     """Histograms of one canvas' binning, 32 bins each: tau_hist[b] = listed primitives
     with floor(log2 tau_i) = b; d_hist[b] = tiles with floor(log2 d_t) = b (empty tiles
     counted apart); foot_hist[b] = listed primitives with A_i / (H W) in
     [2^-(b+1), 2^-b) (b = 0 also takes ratios >= 1; b capped at 31)."""
-    params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 8)
+    params, bitmap_id, atlas = _bin_inputs(params, bitmap_id, atlas)
     N = params.shape[0]
-    _, tau = bin_rects(H, W, tile, params, Hb, Wb)
-    offs, _ = bin(H, W, tile, params, Hb, Wb)
+    Hb, Wb = atlas.shape[1:]
+    _, tau = bin_rects(H, W, tile, params, bitmap_id, atlas)
+    offs, _ = bin(H, W, tile, params, bitmap_id, atlas)
     d = np.diff(offs)
     area = np.zeros(max(N, 1))
     lib().oracle_bin_footprint(N, _p(params, _f32p), Hb, Wb, _p(area, _f64p))

@@ -55,8 +55,9 @@ struct DbmpAtlas {
     size_t pitch = 0;
     cudaTextureObject_t tex = 0;
     int32_t *sat = nullptr;
+    int4 *nzbox = nullptr;      // per bitmap: the box of its non-zero texels
     int32_t n_bmp = 0, Hb = 0, Wb = 0;
-    AtlasView view() const { return AtlasView{tex, sat, n_bmp, Hb, Wb}; }
+    AtlasView view() const { return AtlasView{tex, sat, n_bmp, Hb, Wb, nzbox}; }
 };
 
 struct DbmpWorkspace {
@@ -406,8 +407,10 @@ int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
     const size_t cells = rows * (W_b + 1);
     cudaError_t e = cudaMalloc(&a->plane_alloc, a->pitch * rows + kTexAlign);
     if (e == cudaSuccess) e = cudaMalloc(&a->sat, sizeof(int32_t) * cells);
+    if (e == cudaSuccess) e = cudaMalloc(&a->nzbox, sizeof(int4) * (size_t)n_bmp);
     if (e != cudaSuccess) {
         cudaFree(a->plane_alloc);
+        cudaFree(a->sat);
         delete a;
         return fail(DBMP_ERR_NO_MEMORY, "atlas allocation: %s", cudaGetErrorString(e));
     }
@@ -415,8 +418,8 @@ int32_t dbmp_atlas_create(const float *texels_dev, int32_t n_bmp, int32_t H_b, i
     cudaStream_t st = (cudaStream_t)stream;
     e = atlas_texture_create(a->plane, a->pitch, n_bmp, H_b, W_b, &a->tex);
     if (e == cudaSuccess)
-        e = launch_atlas_build(texels_dev, a->plane, (int64_t)(a->pitch / sizeof(float)), a->sat, n_bmp, H_b,
-                               W_b, st);
+        e = launch_atlas_build(texels_dev, a->plane, (int64_t)(a->pitch / sizeof(float)), a->sat, a->nzbox, n_bmp,
+                               H_b, W_b, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         if (a->tex) cudaDestroyTextureObject(a->tex);
@@ -433,7 +436,7 @@ int32_t dbmp_atlas_update(DbmpAtlas *atlas, const float *texels_dev, dbmp_stream
     if (int32_t r = check_atlas(atlas)) return r;
     if (!texels_dev) return fail(DBMP_ERR_INVALID_ARG, "texels_dev is NULL");
     DBMP_CUDA(launch_atlas_build(texels_dev, atlas->plane, (int64_t)(atlas->pitch / sizeof(float)), atlas->sat,
-                                 atlas->n_bmp, atlas->Hb, atlas->Wb, (cudaStream_t)stream),
+                                 atlas->nzbox, atlas->n_bmp, atlas->Hb, atlas->Wb, (cudaStream_t)stream),
               "atlas update");
     return DBMP_OK;
 }
@@ -443,6 +446,7 @@ int32_t dbmp_atlas_destroy(DbmpAtlas *atlas) {
     if (atlas->tex) cudaDestroyTextureObject(atlas->tex);
     cudaFree(atlas->plane_alloc);
     cudaFree(atlas->sat);
+    cudaFree(atlas->nzbox);
     delete atlas;
     return DBMP_OK;
 }

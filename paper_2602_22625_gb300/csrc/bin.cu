@@ -34,14 +34,15 @@ __device__ __forceinline__ int find_canvas_by(const CanvasDesc *cv, int n, int v
     return lo;
 }
 
-// |sin|, |cos| of the binning specification: Cody-Waite reduction by pi/2 with a
+// sin, cos of the binning specification: Cody-Waite reduction by pi/2 with a
 // three-part constant, Taylor polynomials of degree 9 (sin) and 8 (cos) on
-// [-pi/4, pi/4].  Every operation rounds once (explicit intrinsics).
-__device__ __forceinline__ void spec_abs_sincos(float th, float &as, float &ac) {
+// [-pi/4, pi/4], the quadrant's signs.  Every operation rounds once (explicit
+// intrinsics).  False (and 1, 1) for |th| > 65536, outside the reduction's range.
+__device__ __forceinline__ bool spec_sincos(float th, float &sn, float &cs) {
     if (!(fabsf(th) <= 65536.0f)) {
-        as = 1.0f;
-        ac = 1.0f;
-        return;
+        sn = 1.0f;
+        cs = 1.0f;
+        return false;
     }
     const float two_over_pi = 0.636619772367581343f;
     const float C1 = 1.5703125f;
@@ -62,14 +63,17 @@ __device__ __forceinline__ void spec_abs_sincos(float th, float &as, float &ac) 
     cp = __fadd_rn(__fmul_rn(cp, r2), 1.0f / 24.0f);
     cp = __fadd_rn(__fmul_rn(cp, r2), -0.5f);
     const float cr = __fadd_rn(1.0f, __fmul_rn(r2, cp));
-    const int ki = (int)k;
-    if (ki & 1) {
-        as = fabsf(cr);
-        ac = fabsf(sr);
-    } else {
-        as = fabsf(sr);
-        ac = fabsf(cr);
-    }
+    const int q = (((int)k % 4) + 4) % 4;   // quadrant: th = k pi/2 + r
+    sn = q == 0 ? sr : (q == 1 ? cr : (q == 2 ? -sr : -cr));
+    cs = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
+    return true;
+}
+
+__device__ __forceinline__ void spec_abs_sincos(float th, float &as, float &ac) {
+    float sn, cs;
+    spec_sincos(th, sn, cs);
+    as = fabsf(sn);
+    ac = fabsf(cs);
 }
 
 __device__ __forceinline__ bool all_finite8(const float *p) {
@@ -79,9 +83,10 @@ __device__ __forceinline__ bool all_finite8(const float *p) {
     return ok;
 }
 
-// Half-extents of the padded box of the binning specification: the bitmap's
-// support with its zero-padding ring (e_u = 1 + 2/(W_b-1), e_v likewise) rotated by
-// theta and scaled by |s|, one IEEE operation at a time.
+// Half-extents of the padded box of the bitmap's whole support with its zero-padding
+// ring (e_u = 1 + 2/(W_b-1), e_v likewise) rotated by theta and scaled by |s|, one
+// IEEE operation at a time: the footprint A_i = (2 hx + 2)(2 hy + 2) of the scaling
+// statistics (Sec. S4).
 __device__ __forceinline__ void spec_halfext(float s_raw, float theta, int32_t Hb, int32_t Wb, float &hx, float &hy) {
     const float eu = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(Wb - 1)));
     const float ev = __fadd_rn(1.0f, __fdiv_rn(2.0f, (float)(Hb - 1)));
@@ -147,15 +152,44 @@ __global__ void k_prep(const float *__restrict__ params, const int32_t *__restri
     rec[i] = r;
 
     // ---- tile rectangle: the fp32 binning specification ----
+    // The box holds every pixel where M can be non-zero: its bitmap coordinates lie
+    // within one texel of the bitmap's non-zero box [u0, u1] x [v0, v1] (zero padding,
+    // Sec. S1.1).  That texel box (centre (cu, cv), half-extents (hu, hv) from the
+    // bitmap centre, exact) maps to a rotated box of centre s (cos uc - sin vc,
+    // sin uc + cos vc) and axis-aligned half-extents |s| (|cos| eu + |sin| ev),
+    // |s| (|sin| eu + |cos| ev) in normalised coordinates (Eq. 1), widened by the
+    // margin m = 1 + |s| 2^-19 pixels, which exceeds the rounding of these steps and of
+    // the compositors' transform.  An all-zero bitmap lists the primitive nowhere.
     int4 rc = make_int4(0, 0, -1, -1);
-    if (valid) {
-        float hx, hy;
-        spec_halfext(p[2], p[3], atlas.Hb, atlas.Wb, hx, hy);
+    const int4 nz = bid_ok ? atlas.nzbox[bid] : make_int4(1, 0, 1, 0);
+    if (valid && nz.x <= nz.y) {
+        const float kw = __fmul_rn((float)(atlas.Wb - 1), 0.5f), kv = __fmul_rn((float)(atlas.Hb - 1), 0.5f);
+        const float cu = __fmul_rn(__fsub_rn((float)(nz.x + nz.y), (float)(atlas.Wb - 1)), 0.5f);
+        const float hu = __fmul_rn((float)(nz.y - nz.x + 2), 0.5f);
+        const float cv = __fmul_rn(__fsub_rn((float)(nz.z + nz.w), (float)(atlas.Hb - 1)), 0.5f);
+        const float hv = __fmul_rn((float)(nz.w - nz.z + 2), 0.5f);
+        const float uc = __fdiv_rn(cu, kw), eu = __fdiv_rn(hu, kw);
+        const float vc = __fdiv_rn(cv, kv), ev = __fdiv_rn(hv, kv);
+        const float s = p[2], as = fabsf(p[2]);
+        float sn, cs, dxc, dyc, hx, hy;
+        if (spec_sincos(p[3], sn, cs)) {
+            dxc = __fmul_rn(s, __fsub_rn(__fmul_rn(cs, uc), __fmul_rn(sn, vc)));
+            dyc = __fmul_rn(s, __fadd_rn(__fmul_rn(sn, uc), __fmul_rn(cs, vc)));
+            hx = __fmul_rn(as, __fadd_rn(__fmul_rn(fabsf(cs), eu), __fmul_rn(fabsf(sn), ev)));
+            hy = __fmul_rn(as, __fadd_rn(__fmul_rn(fabsf(sn), eu), __fmul_rn(fabsf(cs), ev)));
+        } else {   // rotation unknown: a box about (x, y) that holds every rotation
+            dxc = 0.0f;
+            dyc = 0.0f;
+            hx = __fmul_rn(as, __fadd_rn(__fadd_rn(__fadd_rn(fabsf(uc), eu), fabsf(vc)), ev));
+            hy = hx;
+        }
+        const float m = __fadd_rn(1.0f, __fmul_rn(as, 1.9073486328125e-06f));   // 1 + |s| 2^-19
+        const float cx = __fadd_rn(p[0], dxc), cy = __fadd_rn(p[1], dyc);
         const float inv_t = __fdiv_rn(1.0f, (float)tile);
-        const float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(p[0], hx), 1.0f), inv_t));
-        const float fx1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(p[0], hx), 1.0f), inv_t));
-        const float fy0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(p[1], hy), 1.0f), inv_t));
-        const float fy1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(p[1], hy), 1.0f), inv_t));
+        const float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(cx, hx), m), inv_t));
+        const float fx1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(cx, hx), m), inv_t));
+        const float fy0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(cy, hy), m), inv_t));
+        const float fy1 = floorf(__fmul_rn(__fadd_rn(__fadd_rn(cy, hy), m), inv_t));
         const float mx = (float)(d.ntx - 1), my = (float)(d.nty - 1);
         if (fx1 >= 0.0f && fy1 >= 0.0f && fx0 <= mx && fy0 <= my) {
             rc.x = fx0 < 0.0f ? 0 : (int)fx0;

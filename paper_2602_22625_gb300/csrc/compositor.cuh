@@ -102,6 +102,8 @@ struct AtlasView {
     cudaTextureObject_t tex;  // texel plane
     const int32_t *sat;       // [n_bmp][H_b+1][W_b+1] summed-area table of (texel > 0)
     int32_t n_bmp, Hb, Wb;
+    const int4 *nzbox;        // [n_bmp] first/last column and row holding a texel > 0:
+                              // (u0, u1, v0, v1); (W_b, -1, H_b, -1) for an all-zero bitmap
 };
 
 // Tile size, records per warp staging batch, pixels per lane of the forward and

@@ -125,7 +125,7 @@ cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float 
 int sm_count();
 // Texel plane (row pitch `pitch` floats) and summed-area tables of an atlas from
 // its dense texels [n_bmp][H_b][W_b].
-cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int32_t n_bmp,
+cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int4 *nzbox, int32_t n_bmp,
                                int32_t Hb, int32_t Wb, cudaStream_t st);
 // Row pitch (bytes) of an atlas texel plane, and the texture object over it (the
 // plane's base must be kTexAlign-aligned).

@@ -42,7 +42,9 @@ constexpr size_t kOffList = kOffTileOff + align256(sizeof(int64_t) * (kMaxTiles 
 constexpr size_t kPlaneBytes = 4 * kMaxAtlasCells + 124 * (kMaxAtlasCells / 3 + 1) + kTexAlign;
 constexpr size_t kOffPlane = kOffList + align256(sizeof(int32_t) * kMaxPairs);
 constexpr size_t kOffSat = kOffPlane + align256(kPlaneBytes);
-constexpr size_t kScratchBytes = kOffSat + align256(sizeof(int32_t) * kMaxAtlasCells);  // ~6.1 MB
+// per-bitmap non-zero boxes: n_bmp <= cells / 9 (H_b, W_b >= 2)
+constexpr size_t kOffNzbox = kOffSat + align256(sizeof(int32_t) * kMaxAtlasCells);
+constexpr size_t kScratchBytes = kOffNzbox + align256(sizeof(int4) * (kMaxAtlasCells / 9));  // ~6.2 MB
 
 // The scratch area: every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -177,7 +179,8 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
                                              ~(uintptr_t)(kTexAlign - 1));
     cudaTextureObject_t tex = 0;
     if (int32_t r = scratch_texture(plane, n_bmp, H_b, W_b, &tex)) return r;
-    AtlasView atlas{tex, reinterpret_cast<const int32_t *>(base + kOffSat), n_bmp, H_b, W_b};
+    AtlasView atlas{tex, reinterpret_cast<const int32_t *>(base + kOffSat), n_bmp, H_b, W_b,
+                    reinterpret_cast<const int4 *>(base + kOffNzbox)};
 
     // The previous call's contents are still in the array: the status block (error
     // code, counters, work queues) must start at zero; everything else read later is
@@ -189,7 +192,8 @@ extern "C" int32_t dbmp_render_fwd_static(int32_t H, int32_t W, const float *par
     }
     if (e == cudaSuccess)
         e = launch_atlas_build(texels_dev, plane, (int64_t)(atlas_plane_pitch(W_b) / sizeof(float)),
-                               reinterpret_cast<int32_t *>(base + kOffSat), n_bmp, H_b, W_b, st);
+                               reinterpret_cast<int32_t *>(base + kOffSat), reinterpret_cast<int4 *>(base + kOffNzbox),
+                               n_bmp, H_b, W_b, st);
     if (e == cudaSuccess) {
         BinBuffers b{};
         b.rec = reinterpret_cast<PrimRec *>(base + kOffRec);

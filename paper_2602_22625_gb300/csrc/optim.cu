@@ -22,6 +22,39 @@ __global__ void k_plane(const float *__restrict__ tex, float *__restrict__ plane
     }
 }
 
+// nzbox[b] = (u0, u1, v0, v1): the first and last column and row of bitmap b that
+// hold a texel > 0, the box the binning specification sizes a primitive's tile
+// rectangle from; (W_b, -1, H_b, -1) for an all-zero bitmap.  One CTA per bitmap.
+__global__ void k_nzbox(const float *__restrict__ tex, int4 *__restrict__ nzbox, int32_t Hb, int32_t Wb) {
+    __shared__ int u0, u1, v0, v1;
+    if (threadIdx.x == 0) {
+        u0 = Wb;
+        u1 = -1;
+        v0 = Hb;
+        v1 = -1;
+    }
+    __syncthreads();
+    const float *P = tex + (int64_t)blockIdx.x * Hb * Wb;
+    int a0 = Wb, a1 = -1, b0 = Hb, b1 = -1;
+    for (int64_t i = threadIdx.x; i < (int64_t)Hb * Wb; i += blockDim.x) {
+        if (P[i] > 0.0f) {
+            const int v = (int)(i / Wb), u = (int)(i - (int64_t)v * Wb);
+            a0 = min(a0, u);
+            a1 = max(a1, u);
+            b0 = min(b0, v);
+            b1 = max(b1, v);
+        }
+    }
+    if (a1 >= 0) {
+        atomicMin(&u0, a0);
+        atomicMax(&u1, a1);
+        atomicMin(&v0, b0);
+        atomicMax(&v1, b1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) nzbox[blockIdx.x] = make_int4(u0, u1, v0, v1);
+}
+
 // sat[b][v][u] = number of texels P[v'][u'] > 0 with v' < v and u' < u
 // (v in [0, H_b], u in [0, W_b]); one CTA per bitmap: row prefix sums, then columns.
 __global__ void k_sat(const float *__restrict__ tex, int32_t *__restrict__ sat, int32_t Hb, int32_t Wb) {
@@ -231,11 +264,12 @@ int sm_count() {
     return n;
 }
 
-cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int32_t n_bmp,
+cudaError_t launch_atlas_build(const float *texels, float *plane, int64_t pitch, int32_t *sat, int4 *nzbox, int32_t n_bmp,
                                int32_t Hb, int32_t Wb, cudaStream_t st) {
     const int64_t total = (int64_t)n_bmp * (Hb + 1) * Wb;
     k_plane<<<grid_for(total, 256), 256, 0, st>>>(texels, plane, pitch, n_bmp, Hb, Wb);
     k_sat<<<n_bmp, 256, 0, st>>>(texels, sat, Hb, Wb);
+    k_nzbox<<<n_bmp, 256, 0, st>>>(texels, nzbox, Hb, Wb);
     return cudaGetLastError();
 }
 

@@ -182,11 +182,12 @@ def main(seed: int = 2, N: int = 20000, H: int = 1024, W: int = 1024, atlas_seed
                  recipe=f"16 blurred Bezier strokes 128^2; N={N}; s=LogNormal(-2,0.7)*W; seed={seed}")
 
 
-def stress(seed: int = 3, N: int = 200000, H: int = 2048, W: int = 2048, x_m: float = 0.015,
+def stress(seed: int = 3, N: int = 200000, H: int = 2048, W: int = 2048, x_m: float = 0.035,
            atlas_seed: int = 13) -> Scene:
     """2048^2 canvas, 64 stroke bitmaps, 200k primitives, Pareto(alpha=1.5) scale with
-    x_m = 0.015 of the side (the smallest value tried for which the densest tile lists
-    more than 5000 primitives: 6032 at 32^2 tiles, 5712 at 16^2)."""
+    x_m = 0.035 of the side (the smallest value tried, in steps of 0.005, for which the
+    densest tile lists more than 5000 primitives when tiles list only the part of each
+    primitive its bitmap's non-zero texels can reach: 5427 at 32^2 tiles, 5069 at 16^2)."""
     atlas = stroke_atlas(atlas_seed, 64, 128)
     p, b = primitives(seed, N, H, W, atlas.shape[0], "pareto", (x_m, 1.5))
     return Scene("stress_2048sq_200k", H, W, p, b, atlas,

@@ -41,7 +41,7 @@ def scene_ragged(seed=21, N=60, H=77, W=45):
 def test_bin_bit_exact_tiny(tile):
     sc = inputs.tiny(seed=1)
     offs, lst = gpu_bin(sc, tile)
-    ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, *sc.atlas.shape[1:])
+    ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
     np.testing.assert_array_equal(offs, ro)
     np.testing.assert_array_equal(lst, rl)
 
@@ -55,7 +55,7 @@ def test_bin_bit_exact_ragged_invalid_and_negative_scale():
     p[9, 3] = 1e6  # beyond the reduction range: conservative box
     for tile in (8, 16, 32):
         offs, lst = gpu_bin(sc, tile)
-        ro, rl = oracle.bin(sc.H, sc.W, tile, p, *sc.atlas.shape[1:])
+        ro, rl = oracle.bin(sc.H, sc.W, tile, p, sc.bitmap_id, sc.atlas)
         np.testing.assert_array_equal(offs, ro)
         np.testing.assert_array_equal(lst, rl)
 
@@ -64,7 +64,7 @@ def test_bin_bit_exact_ragged_invalid_and_negative_scale():
 def test_bin_bit_exact_main_workload(tile):
     sc = inputs.main()
     offs, lst = gpu_bin(sc, tile)
-    ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, *sc.atlas.shape[1:])
+    ro, rl = oracle.bin(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
     np.testing.assert_array_equal(offs, ro)
     np.testing.assert_array_equal(lst, rl)
 
@@ -79,7 +79,7 @@ def test_bin_bit_exact_multi_pass_chunks():
     offs, lst = gpu_bin(sc, 8)
     # the oracle's definition tests every primitive against every tile (2e10 tests
     # here); the expected lists come from its rectangles expanded and stably sorted
-    rects, _ = oracle.bin_rects(sc.H, sc.W, 8, sc.params, *sc.atlas.shape[1:])
+    rects, _ = oracle.bin_rects(sc.H, sc.W, 8, sc.params, sc.bitmap_id, sc.atlas)
     ro, rl = lists_from_rects(rects, 256, 256)
     np.testing.assert_array_equal(offs, ro)
     np.testing.assert_array_equal(lst, rl)
@@ -135,7 +135,7 @@ def test_forward_ragged_backgrounds(bg, alpha_max):
     assert np.abs(img.cpu().numpy() - ref["image"]).max() <= IMG_TOL
     assert np.abs(T.cpu().numpy() - ref["T_final"]).max() <= IMG_TOL
     # n_last names the oracle's last contributing primitive
-    offs, lst = oracle.bin(sc.H, sc.W, 16, sc.params, *sc.atlas.shape[1:])
+    offs, lst = oracle.bin(sc.H, sc.W, 16, sc.params, sc.bitmap_id, sc.atlas)
     nl = nl.cpu().numpy()
     ntx = -(-sc.W // 16)
     yy, xx = np.mgrid[0:sc.H, 0:sc.W]
@@ -375,3 +375,50 @@ def test_main_workload_in_the_benchmarked_configuration():
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)
+
+
+def test_backward_with_a_full_survivor_record_matches_a_roomy_workspace():
+    """The workspace's survivor record holds max_pairs / 8 entries (at least 65 536),
+    divided among the forward's warps.  With max_pairs equal to the main workload's
+    list entries, the forward's warps run out of room (the workload keeps about a
+    third of its list entries as survivors), and the regions they could not record
+    are walked from their tile lists by the backward.  The gradient equals that of a
+    workspace with room for every survivor, up to float32 summation order."""
+    cuda()
+    sc = inputs.main()
+    tg = inputs.main(seed=1002)
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    bg = D.make_background(sc.background)
+    p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
+    target = torch.empty(3, sc.H, sc.W, device="cuda")
+    image = torch.empty(3, sc.H, sc.W, device="cuda")
+    T = torch.empty(sc.H, sc.W, device="cuda")
+    nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+    dL = torch.empty(3, sc.H, sc.W, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grads, survivors = [], []
+    K = None
+    try:
+        for roomy in (True, False):
+            ws = D.dbmp_workspace_create(sc.N, (sc.W // 8) * (sc.H // 8), (96 << 20) if roomy else K, 1)
+            try:
+                D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N], tile=32, batch=32, ppt=4, ppt_bwd=4)
+                if roomy:
+                    D.dbmp_batch_render(ws, to_dev(tg.params), to_dev(tg.bitmap_id), atlas, 1.0, bg, 0.0,
+                                        D.BATCH_BIN | D.BATCH_FWD, target, T, nl)
+                dp = torch.zeros(sc.N, 8, device="cuda")
+                D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BIN, None, T, nl)
+                D.dbmp_batch_render_mse(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_FWD, target, image, T, nl, dL,
+                                        loss)
+                D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BWD, image, T, nl, dL, dp)
+                st = D.dbmp_status_poll(ws)
+                assert st.code == 0
+                K = st.pairs_required
+                survivors.append(st.survivors)
+                grads.append(dp.cpu().numpy().astype(np.float64))
+            finally:
+                D.dbmp_workspace_destroy(ws)
+    finally:
+        D.dbmp_atlas_destroy(atlas)
+    assert survivors[1] > max(K // 8, 1 << 16)   # more survivors than the tight record holds
+    grad_close(grads[1], grads[0], rel=1e-4, what="survivor record full")

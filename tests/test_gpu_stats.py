@@ -31,7 +31,7 @@ def test_stats_main_workload(tile):
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)
-    compare(got, oracle.bin_stats(sc.H, sc.W, tile, sc.params, *sc.atlas.shape[1:]))
+    compare(got, oracle.bin_stats(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas))
 
 
 def test_stats_of_a_multi_canvas_plan_sum_the_canvases():
@@ -55,7 +55,7 @@ def test_stats_of_a_multi_canvas_plan_sum_the_canvases():
     finally:
         D.dbmp_workspace_destroy(ws)
         D.dbmp_atlas_destroy(atlas)
-    refs = [oracle.bin_stats(s.H, s.W, 16, s.params, *atlas_np.shape[1:]) for s in scenes]
+    refs = [oracle.bin_stats(s.H, s.W, 16, s.params, s.bitmap_id, atlas_np) for s in scenes]
     ref = {k: sum(r[k] for r in refs) for k in ("n_listed", "pairs", "n_tiles", "empty_tiles",
                                                 "tau_hist", "d_hist", "foot_hist")}
     ref["tau_max"] = max(r["tau_max"] for r in refs)

@@ -25,9 +25,14 @@ MUTANTS = {
                                      "double U = (L->u + 1.0) / 2.0 * (double)(Wb);"),
     "back_product_not_updated": ("B *= (1.0 - L->alpha);\n    }\n}", "}\n}"),
     "transmittance_update": ("T *= (1.0 - L.alpha);", "T *= (1.0 - 0.5 * L.alpha);"),
-    "bin_margin_sign": ("float fx0 = floorf(((p[0] - hx) - 1.0f) * inv_t);",
-                        "float fx0 = floorf(((p[0] - hx) + 1.0f) * inv_t);"),
-    "bin_support_extension_dropped": ("float hx = s * (ac * eu + as * ev);", "float hx = s * (ac + as * ev);"),
+    "bin_margin_sign": ("float fx0 = floorf(((cx - hx) - m) * inv_t);",
+                        "float fx0 = floorf(((cx - hx) + m) * inv_t);"),
+    "bin_support_ring_dropped": ("float hu = (float)(box[1] - box[0] + 2) * 0.5f;",
+                                 "float hu = (float)(box[1] - box[0]) * 0.5f;"),
+    "bin_centre_offset_sign": ("dxc = s * (cs * uc - sn * vc);", "dxc = s * (cs * uc + sn * vc);"),
+    "bin_centre_offset_dropped": ("float cx = p[0] + dxc, cy = p[1] + dyc;", "float cx = p[0], cy = p[1] + dyc;"),
+    "bin_quadrant_sign": ("        *sn = cr;\n        *cs = -sr;", "        *sn = cr;\n        *cs = sr;"),
+    "bin_nonzero_box_row_col_swapped": ("if (u < box[0]) box[0] = u;", "if (v < box[0]) box[0] = v;"),
     "variance_window_5_wide": ("const int32_t x0 = x - 3 < 0 ? 0 : x - 3, x1 = x + 3 > W - 1 ? W - 1 : x + 3;",
                                "const int32_t x0 = x - 2 < 0 ? 0 : x - 2, x1 = x + 2 > W - 1 ? W - 1 : x + 2;"),
     "variance_not_centred": ("const double d = (double)P[(size_t)yy * W + xx] - mean;",

@@ -300,12 +300,30 @@ def test_spec_sincos_error_bound():
     assert err.max() < 2e-5
 
 
+def test_spec_signed_sincos_error_bound_and_range():
+    """The signed sine and cosine (the tile rectangle's centre offset) carry the
+    quadrant's signs: within the same bounds of math.sin / math.cos, their absolute
+    values are spec_abs_sincos's, and outside |theta| <= 65536 the call says so."""
+    th = np.concatenate([np.linspace(-20, 20, 4001), np.random.default_rng(1).uniform(-6e4, 6e4, 2000)])
+    th = th.astype(np.float32)
+    err = []
+    for t in th:
+        sn, cs, ok = oracle.spec_sincos(t)
+        assert ok
+        assert (abs(sn), abs(cs)) == oracle.spec_abs_sincos(t)
+        err.append(max(abs(sn - math.sin(float(t))), abs(cs - math.cos(float(t)))))
+    err = np.array(err)
+    assert err[:4001].max() < 3e-7
+    assert err.max() < 2e-5
+    assert not oracle.spec_sincos(np.float32(70000.0))[2]
+    assert oracle.spec_abs_sincos(np.float32(70000.0)) == (1.0, 1.0)
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_binning_conservation_order_and_rects(tile):
     sc = inputs.tiny(seed=9, N=300, H=200, W=170)
-    Hb, Wb = sc.atlas.shape[1:]
-    offs, lst = oracle.bin(sc.H, sc.W, tile, sc.params, Hb, Wb)
-    rects, tau = oracle.bin_rects(sc.H, sc.W, tile, sc.params, Hb, Wb)
+    offs, lst = oracle.bin(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
+    rects, tau = oracle.bin_rects(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
     ntx, nty = -(-sc.W // tile), -(-sc.H // tile)
     d = np.diff(offs)
     assert d.sum() == tau.sum() == len(lst)  # sum_i tau_i = sum_t d_t (Sec. S4)
@@ -323,42 +341,67 @@ def test_lists_from_rects_reproduce_the_oracle_binning(tile):
     cases too large for the oracle's tile-by-tile definition gives the same lists."""
     from _helpers import lists_from_rects
     sc = inputs.tiny(seed=10, N=500, H=150, W=230)
-    Hb, Wb = sc.atlas.shape[1:]
     sc.params[::7, 2] = 0.0   # unlisted primitives in the mix
-    offs, lst = oracle.bin(sc.H, sc.W, tile, sc.params, Hb, Wb)
-    rects, _ = oracle.bin_rects(sc.H, sc.W, tile, sc.params, Hb, Wb)
+    offs, lst = oracle.bin(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
+    rects, _ = oracle.bin_rects(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
     o2, l2 = lists_from_rects(rects, -(-sc.W // tile), -(-sc.H // tile))
     np.testing.assert_array_equal(o2, offs)
     np.testing.assert_array_equal(l2, lst)
 
 
-def test_binning_rect_is_tight_and_conservative():
-    """The fp32 spec box lies between the exact (FP64) support box widened by
-    0.99 px and by 1.01 px, and every pixel where a primitive is non-zero lies in
-    one of its listed tiles."""
-    sc = inputs.tiny(seed=10, N=120, H=160, W=144)
+def _offcentre_atlas():
+    """Bitmaps whose non-zero texels fill only part of the bitmap, away from its
+    centre: a blob in one corner, a thin bar along one edge, a single texel, and
+    the soft disc (centred) for reference."""
+    a = np.zeros((4, 24, 32), np.float32)
+    yy, xx = np.mgrid[0:24, 0:32]
+    a[0] = np.clip(1.0 - np.hypot(xx - 25.0, yy - 5.0) / 4.0, 0.0, 1.0)   # corner blob
+    a[1, 20:22, 3:29] = 0.7                                                  # bar near the bottom
+    a[2, 2, 30] = 1.0                                                        # one texel
+    a[3] = inputs.soft_disc_atlas(5, 1, 32)[0, 4:28, :]
+    return a
+
+
+@pytest.mark.parametrize("which", ["disc", "offcentre", "strokes"])
+def test_binning_rect_is_tight_and_conservative(which):
+    """The fp32 spec box lies between the exact (FP64) box of the pixels within one
+    texel of the bitmap's non-zero texels, widened by 0.99 px and by 1.01 px plus the
+    margin's |s| 2^-19, and every pixel where a primitive is non-zero lies in one of
+    its listed tiles (a solo FP64 render)."""
     tile = 16
-    Hb, Wb = sc.atlas.shape[1:]
-    rects, tau = oracle.bin_rects(sc.H, sc.W, tile, sc.params, Hb, Wb)
+    if which == "disc":
+        sc = inputs.tiny(seed=10, N=120, H=160, W=144)
+    else:
+        atlas = _offcentre_atlas() if which == "offcentre" else inputs.stroke_atlas(3, 4, 48)
+        p, b = inputs.primitives(17, 96, 160, 144, atlas.shape[0], "uniform", (0.05, 0.3))
+        p[::5, 2] *= -1.0   # mirrored primitives: the centre offset changes sign
+        sc = inputs.Scene(which, 160, 144, p, b, atlas)
+    nb, Hb, Wb = sc.atlas.shape
+    rects, tau = oracle.bin_rects(sc.H, sc.W, tile, sc.params, sc.bitmap_id, sc.atlas)
     ntx, nty = -(-sc.W // tile), -(-sc.H // tile)
-    eu, ev = 1 + 2 / (Wb - 1), 1 + 2 / (Hb - 1)
+    kw, kv = (Wb - 1) / 2, (Hb - 1) / 2
     for i, p in enumerate(sc.params.astype(np.float64)):
-        c, s = abs(math.cos(p[3])), abs(math.sin(p[3]))
-        hx = abs(p[2]) * (c * eu + s * ev)
-        hy = abs(p[2]) * (s * eu + c * ev)
+        ys_, xs_ = np.nonzero(sc.atlas[sc.bitmap_id[i]] > 0)
+        # texel box (u0 - 1, u1 + 1) x (v0 - 1, v1 + 1) in normalised coordinates
+        u_lo, u_hi = (xs_.min() - 1 - kw) / kw, (xs_.max() + 1 - kw) / kw
+        v_lo, v_hi = (ys_.min() - 1 - kv) / kv, (ys_.max() + 1 - kv) / kv
+        c, sn = math.cos(p[3]), math.sin(p[3])
+        dx = [p[2] * (c * u - sn * v) for u in (u_lo, u_hi) for v in (v_lo, v_hi)]
+        dy = [p[2] * (sn * u + c * v) for u in (u_lo, u_hi) for v in (v_lo, v_hi)]
+        ext = 1.01 + abs(p[2]) * 2.0 ** -19
 
         def rect(m):
-            r = [math.floor((p[0] - hx - m) / tile), math.floor((p[1] - hy - m) / tile),
-                 math.floor((p[0] + hx + m) / tile), math.floor((p[1] + hy + m) / tile)]
+            r = [math.floor((p[0] + min(dx) - m) / tile), math.floor((p[1] + min(dy) - m) / tile),
+                 math.floor((p[0] + max(dx) + m) / tile), math.floor((p[1] + max(dy) + m) / tile)]
             if r[2] < 0 or r[3] < 0 or r[0] > ntx - 1 or r[1] > nty - 1:
                 return None
             return [max(r[0], 0), max(r[1], 0), min(r[2], ntx - 1), min(r[3], nty - 1)]
-        lo, hi = rect(0.99), rect(1.01)
+        lo, hi = rect(0.99), rect(ext)
         if tau[i] == 0:
             assert lo is None
             continue
         assert hi is not None
-        assert hi[0] <= rects[i, 0] <= (lo[0] if lo else ntx) and hi[1] <= rects[i, 1]
+        assert hi[0] <= rects[i, 0] and hi[1] <= rects[i, 1]
         assert rects[i, 2] <= hi[2] and rects[i, 3] <= hi[3]
         if lo:
             assert rects[i, 0] <= lo[0] and rects[i, 1] <= lo[1]
@@ -371,15 +414,29 @@ def test_binning_rect_is_tight_and_conservative():
             assert (ys // tile).min() >= rects[i, 1] and (ys // tile).max() <= rects[i, 3]
 
 
+def test_nonzero_boxes_of_the_atlas():
+    a = _offcentre_atlas()
+    boxes = oracle.nonzero_boxes(np.concatenate([a, np.zeros((1, 24, 32), np.float32)]))
+    for b in range(4):
+        ys, xs = np.nonzero(a[b] > 0)
+        assert list(boxes[b]) == [xs.min(), xs.max(), ys.min(), ys.max()]
+    assert list(boxes[2]) == [30, 30, 2, 2]
+    assert list(boxes[4]) == [32, -1, 24, -1]   # all zero
+
+
 def test_binning_skips_invalid_primitives():
     sc = inputs.tiny(seed=11, N=6, H=64, W=64)
     p = sc.params.copy()
     p[1, 2] = 0.0
     p[2, 0] = np.nan
     p[3, 3] = np.inf
-    rects, tau = oracle.bin_rects(64, 64, 16, p, 64, 64)
+    rects, tau = oracle.bin_rects(64, 64, 16, p, sc.bitmap_id, sc.atlas)
     assert tau[1] == tau[2] == tau[3] == 0
     assert tau[0] > 0
+    # an all-zero bitmap and a bitmap id outside the atlas list a primitive nowhere
+    atlas2 = np.concatenate([sc.atlas, np.zeros_like(sc.atlas)])
+    _, tau2 = oracle.bin_rects(64, 64, 16, p[[0, 0, 0]], np.array([0, 1, 2], np.int32), atlas2)
+    assert tau2[0] == tau[0] and tau2[1] == 0 and tau2[2] == 0
     out = oracle.render(64, 64, p, sc.bitmap_id, sc.atlas)
     ref = oracle.render(64, 64, p[[0, 4, 5]], sc.bitmap_id[[0, 4, 5]], sc.atlas)
     np.testing.assert_array_equal(out["image"], ref["image"])

@@ -11,10 +11,9 @@ from paper_2602_22625_gb300 import inputs
 
 def test_conservation_and_brute_force_histograms():
     sc = inputs.tiny(seed=12, N=400, H=150, W=190)
-    Hb, Wb = sc.atlas.shape[1:]
-    st = oracle.bin_stats(sc.H, sc.W, 16, sc.params, Hb, Wb)
-    rects, tau = oracle.bin_rects(sc.H, sc.W, 16, sc.params, Hb, Wb)
-    offs, lst = oracle.bin(sc.H, sc.W, 16, sc.params, Hb, Wb)
+    st = oracle.bin_stats(sc.H, sc.W, 16, sc.params, sc.bitmap_id, sc.atlas)
+    rects, tau = oracle.bin_rects(sc.H, sc.W, 16, sc.params, sc.bitmap_id, sc.atlas)
+    offs, lst = oracle.bin(sc.H, sc.W, 16, sc.params, sc.bitmap_id, sc.atlas)
     d = np.diff(offs)
     assert st["pairs"] == tau.sum() == d.sum() == len(lst)          # sum tau = sum d (Sec. S4)
     assert st["tau_hist"].sum() == st["n_listed"] == (tau > 0).sum()
@@ -26,7 +25,8 @@ def test_conservation_and_brute_force_histograms():
 
 
 def test_footprint_of_axis_aligned_primitives():
-    """theta = 0: hx = s e_u, hy = s e_v (e = 1 + 2/(size-1)), A = (2 hx + 2)(2 hy + 2)."""
+    """theta = 0: hx = s e_u, hy = s e_v (e = 1 + 2/(size-1)), A = (2 hx + 2)(2 hy + 2):
+    the footprint is the whole bitmap's padded box, whatever part of it is non-zero."""
     H = W = 256
     Hb = Wb = 64
     e = 1.0 + 2.0 / 63.0
@@ -35,7 +35,9 @@ def test_footprint_of_axis_aligned_primitives():
     p[:, 0] = 128.0
     p[:, 1] = 128.0
     p[:, 2] = s_vals
-    st = oracle.bin_stats(H, W, 16, p, Hb, Wb)
+    atlas = np.zeros((1, Hb, Wb), np.float32)
+    atlas[0, 20:40, 30:34] = 1.0   # a small non-zero part: the binning box shrinks, the footprint does not
+    st = oracle.bin_stats(H, W, 16, p, np.zeros(len(s_vals), np.int32), atlas)
     want = np.zeros(32, np.int64)
     for s in s_vals:
         a = (2 * s * e + 2) ** 2 / (H * W)
