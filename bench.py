@@ -531,6 +531,9 @@ def other_workload(name, peak_tflops, steps=5, warmup=3):
         torch.cuda.synchronize()
         ph = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(steps)])
         s_ = D.dbmp_status_poll(ws)
+        D.dbmp_workspace_count_pairs(ws, True)   # one counting forward for the work unit
+        D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BIN | D.BATCH_FWD, image, T, nl)
+        s_ = D.dbmp_status_poll(ws)
         bwd = float(ph[:, 2].mean())
         bwd_tf = FLOPS_BWD_PAIR * s_.pairs_contributing / (bwd * 1e-3) / 1e12
         return {"workload": "batched_64_canvases" if name == "batched" else "stress_2048sq_200k",
@@ -782,10 +785,14 @@ def run_dbmp(args):
         if ev:
             ev[5].record(stream)
 
+    # the warm-up steps count the contributing pairs (the work unit; the count is a
+    # separately compiled instance of the forward), the timed steps do not
+    D.dbmp_workspace_count_pairs(ws, True)
     for _ in range(max(args.warmup, 3)):
         one_step()
     st = D.dbmp_status_poll(ws)
     pairs = (st.pairs_evaluated, st.pairs_evaluated_bwd, st.pairs_contributing, st.pairs_required)
+    D.dbmp_workspace_count_pairs(ws, False)
 
     # ---- device-timed steps (inputs resident in HBM) ----
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
@@ -804,7 +811,12 @@ def run_dbmp(args):
     step_ms = phase.sum(1)
     ms = float(step_ms.mean())
     st = D.dbmp_status_poll(ws)
-    pairs_end = (st.pairs_evaluated, st.pairs_evaluated_bwd, st.pairs_contributing, st.pairs_required)
+    # the contributing pairs of the state the timed steps end in: one counting forward
+    D.dbmp_workspace_count_pairs(ws, True)
+    D.dbmp_batch_render(ws, params, bid, atlas, 1.0, bg, T_STOP, D.BATCH_BIN | D.BATCH_FWD, image, T_final, n_last)
+    stc = D.dbmp_status_poll(ws)
+    D.dbmp_workspace_count_pairs(ws, False)
+    pairs_end = (st.pairs_evaluated, st.pairs_evaluated_bwd, stc.pairs_contributing, st.pairs_required)
 
     # ---- the same step captured once as a CUDA graph and replayed ----
     graph_ms = None

@@ -128,6 +128,13 @@ int32_t dbmp_workspace_destroy(DbmpWorkspace *ws);
  * buffer before writing it would then return different results.  Call it before
  * dbmp_batch_plan / dbmp_bin: it also erases a stored plan. */
 int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream);
+/* Measurement aid (the work unit of the compositors' rooflines): with on != 0 the
+ * forwards of this workspace count the pairs they composite with alpha > 0 into
+ * the status block's pairs_contributing; off (the default) they leave it 0.  The
+ * count is a per-pixel increment in the forward's inner loop that costs about a
+ * tenth of its time, so it is compiled into a second instance of the forward that
+ * only this switch selects; images and maps are the same either way. */
+int32_t dbmp_workspace_count_pairs(DbmpWorkspace *ws, int32_t on);
 
 /* Device-side status block, read (and cleared) by dbmp_status_poll. */
 typedef struct {
@@ -138,7 +145,8 @@ typedef struct {
     int64_t pairs_evaluated;/* (pixel, list entry) pairs the last fwd evaluated  */
     int64_t pairs_evaluated_bwd; /* same for the last bwd                       */
     int64_t pairs_contributing;  /* pairs with alpha > 0 the last fwd composited,
-                                    i.e. layers with M > 0 met while T >= T_stop */
+                                    i.e. layers with M > 0 met while T >= T_stop;
+                                    0 unless dbmp_workspace_count_pairs enabled it */
     int64_t warp_steps;          /* list entries walked by warps in the last fwd   */
     int64_t warp_steps_bwd;      /* same for the last bwd                          */
     int64_t survivors;           /* list entries that passed the region test (fwd) */

@@ -85,6 +85,7 @@ struct DbmpWorkspace {
     int64_t surv_cap = 0;
     // regions the last forward recorded survivors for, on the current lists (0: none)
     int32_t surv_items = 0;
+    int32_t count_pairs = 0;               // forwards count the contributing pairs
     // host copy of the current plan
     std::vector<CanvasDesc> plan;
     std::vector<int32_t> plan_H, plan_W, plan_off;
@@ -293,6 +294,7 @@ RenderArgs make_args(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackgr
     a.surv = ws->surv;
     a.surv_tab = ws->surv_tab;
     a.surv_cap = ws->surv_cap;
+    a.count_pairs = ws->count_pairs;
     return a;
 }
 
@@ -536,6 +538,12 @@ int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream) {
     DBMP_CUDA(cudaMemsetAsync(ws->item_hist, 0, sizeof(int32_t) * 128, st), "poison");
     ws->order_items = 0;
     ws->surv_items = 0;
+    return DBMP_OK;
+}
+
+int32_t dbmp_workspace_count_pairs(DbmpWorkspace *ws, int32_t on) {
+    if (!ws) return fail(DBMP_ERR_INVALID_ARG, "workspace is NULL");
+    ws->count_pairs = on != 0;
     return DBMP_OK;
 }
 

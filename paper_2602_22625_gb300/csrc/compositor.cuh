@@ -53,7 +53,7 @@ struct DevStatus {
     int64_t bad_index;
     // forward counters and work queue, reset together before each forward
     int64_t pairs_eval_fwd;
-    int64_t pairs_contrib;  // (pixel, layer) pairs with alpha > 0 composited by the last fwd
+    int64_t pairs_contrib;  // (pixel, layer) pairs with alpha > 0 composited by the last fwd (when counted)
     int64_t warp_steps_fwd; // list entries walked, summed over warps (last fwd)
     int64_t survivors_fwd;  // records that passed the region test (last fwd)
     uint32_t queue_fwd;     // persistent-kernel work counter
@@ -298,6 +298,7 @@ struct RenderArgs {
     int64_t surv_cap;           // entries of surv (the launch divides them among its warps)
     int32_t surv_wcap;          // entries per warp (set by the launch)
     int32_t surv_use;
+    int32_t count_pairs;        // forward: count the contributing pairs (status pairs_contrib)
 };
 
 }  // namespace dbmp

@@ -276,7 +276,10 @@ __device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
-template <int TILE, int PPT, int BATCH>
+// COUNT: also count the contributing pairs (layers with M > 0 composited while
+// T >= T_stop) into the status block; a per-pixel increment that costs about a tenth
+// of the forward's time, so it is compiled in only when asked for.
+template <int TILE, int PPT, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k_fwd(RenderArgs a, int32_t n_items) {
     constexpr int RPL = BATCH / 32;   // records per lane per batch
     constexpr int RW = region_w(TILE);
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
                     for (int k = 0; k < PPT; ++k) {
                         const bool c = M[k] > 0.0f;
                         last[k] = c ? j : last[k];
-                        ct_it += c ? 1 : 0;
+                        if (COUNT) ct_it += c ? 1 : 0;
                         any = any || T[k] >= tstop;
                     }
                     if (!__any_sync(FULL, any)) {
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
         }
         // per item each lane's counts fit 32 bits (<= PPT x list length)
         ev_it = warp_sum(ev_it);
-        ct_it = warp_sum(ct_it);
+        if (COUNT) ct_it = warp_sum(ct_it);
         if (lane == 0) {
             stats.v[0] += (unsigned)ev_it;
             stats.v[1] += (unsigned)ct_it;
@@ -947,7 +950,8 @@ int persistent_grid(const void *kernel, int32_t n_items) {
 
 template <int TILE, int PPT, int BATCH>
 void register_occupancy(DeviceKernels &dk) {
-    const void *fns[2] = {(const void *)k_fwd<TILE, PPT, BATCH>, (const void *)k_bwd<TILE, PPT, BATCH>};
+    const void *fns[3] = {(const void *)k_fwd<TILE, PPT, BATCH, false>, (const void *)k_fwd<TILE, PPT, BATCH, true>,
+                          (const void *)k_bwd<TILE, PPT, BATCH>};
     for (const void *fn : fns) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * kWarpsPerBlock, 0);
@@ -968,14 +972,19 @@ cudaError_t launch_t(const RenderArgs &a, bool fwd, cudaStream_t st) {
     constexpr int R = TILE * TILE / (32 * PPT);   // regions per tile (any region shape)
     const int32_t n_items = a.n_tiles * R;
     if (fwd) {
-        const int grid = persistent_grid((const void *)k_fwd<TILE, PPT, BATCH>, n_items);
+        const void *fn = a.count_pairs ? (const void *)k_fwd<TILE, PPT, BATCH, true>
+                                       : (const void *)k_fwd<TILE, PPT, BATCH, false>;
+        const int grid = persistent_grid(fn, n_items);
         RenderArgs b = a;
         if (b.surv) {   // the survivor record's entries, divided among the grid's warps
             const int64_t w = b.surv_cap / ((int64_t)grid * kWarpsPerBlock);
             b.surv_wcap = (int32_t)(w < 0x7fffffff ? w : 0x7fffffff);
             if (b.surv_wcap < 1) b.surv = nullptr;
         }
-        k_fwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(b, n_items);
+        if (a.count_pairs)
+            k_fwd<TILE, PPT, BATCH, true><<<grid, 32 * kWarpsPerBlock, 0, st>>>(b, n_items);
+        else
+            k_fwd<TILE, PPT, BATCH, false><<<grid, 32 * kWarpsPerBlock, 0, st>>>(b, n_items);
     } else {
         const int grid = persistent_grid((const void *)k_bwd<TILE, PPT, BATCH>, n_items);
         k_bwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);

@@ -37,7 +37,7 @@ EXPORTS = (
     "dbmp_proposer_train_step", "dbmp_structure_init_scratch_bytes", "dbmp_structure_init",
     "dbmp_blur_bitmaps", "dbmp_bin_stats", "dbmp_structure_reinit", "dbmp_alpha_loss_grad",
     "dbmp_workspace_poison", "dbmp_batch_render_mse", "dbmp_fp32_peak", "dbmp_render_alpha", "dbmp_proposer_activations",
-    "dbmp_batch_set_rows", "dbmp_index_checks", "dbmp_workspace_debug_set",
+    "dbmp_batch_set_rows", "dbmp_index_checks", "dbmp_workspace_debug_set", "dbmp_workspace_count_pairs",
 )
 
 
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
         "dbmp_workspace_create": (_i32, [ctypes.POINTER(DbmpLimits), ctypes.POINTER(_vp)]),
         "dbmp_workspace_destroy": (_i32, [_vp]),
         "dbmp_workspace_poison": (_i32, [_vp, _vp]),
+        "dbmp_workspace_count_pairs": (_i32, [_vp, _i32]),
         "dbmp_status_poll": (_i32, [_vp, _vp, ctypes.POINTER(DbmpDeviceStatus)]),
         "dbmp_bin": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _f32, _vp]),
         "dbmp_get_tile_lists": (_i32, [_vp, _vp, _vp, _i64, ctypes.POINTER(_i32), _vp]),
@@ -262,6 +263,11 @@ def dbmp_workspace_destroy(ws):
 
 def dbmp_workspace_poison(ws, stream=None):
     _check(load().dbmp_workspace_poison(ws, _stream(stream)))
+
+
+def dbmp_workspace_count_pairs(ws, on=True):
+    """Forwards of `ws` count the contributing pairs into the status (off by default)."""
+    _check(load().dbmp_workspace_count_pairs(ws, 1 if on else 0))
 
 
 def dbmp_status_poll(ws, stream=None, raise_on_error=True):

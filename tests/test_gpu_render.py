@@ -327,6 +327,7 @@ def test_main_workload_in_the_benchmarked_configuration():
     atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
     ws = D.dbmp_workspace_create(sc.N, (sc.W // 8) * (sc.H // 8), 96 << 20, 1)
     try:
+        D.dbmp_workspace_count_pairs(ws)
         D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N], tile=32, batch=32, ppt=4, ppt_bwd=4)
         bg = D.make_background(sc.background)
         p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
@@ -422,3 +423,32 @@ def test_backward_with_a_full_survivor_record_matches_a_roomy_workspace():
         D.dbmp_atlas_destroy(atlas)
     assert survivors[1] > max(K // 8, 1 << 16)   # more survivors than the tight record holds
     grad_close(grads[1], grads[0], rel=1e-4, what="survivor record full")
+
+
+def test_forward_with_and_without_the_pair_counter_renders_the_same_bits():
+    """The contributing-pair counter is a separately compiled instance of the forward:
+    with it off (the default) the status reports no count, and image, T_final and
+    n_last are bit for bit those of the counting instance."""
+    cuda()
+    sc = inputs.main()
+    atlas = D.dbmp_atlas_create(to_dev(sc.atlas))
+    ws = D.dbmp_workspace_create(sc.N, (sc.W // 8) * (sc.H // 8), 32 << 20, 1)
+    try:
+        D.dbmp_batch_plan(ws, [sc.H], [sc.W], [0, sc.N], tile=32, batch=32, ppt=4, ppt_bwd=4)
+        bg = D.make_background(sc.background)
+        p, b = to_dev(sc.params), to_dev(sc.bitmap_id)
+        out, counts = [], []
+        for on in (False, True):
+            D.dbmp_workspace_count_pairs(ws, on)
+            img = torch.empty(3, sc.H, sc.W, device="cuda")
+            T = torch.empty(sc.H, sc.W, device="cuda")
+            nl = torch.empty(sc.H, sc.W, dtype=torch.int32, device="cuda")
+            D.dbmp_batch_render(ws, p, b, atlas, 1.0, bg, 1e-6, D.BATCH_BIN | D.BATCH_FWD, img, T, nl)
+            counts.append(D.dbmp_status_poll(ws).pairs_contributing)
+            out.append((img.cpu().numpy(), T.cpu().numpy(), nl.cpu().numpy()))
+    finally:
+        D.dbmp_workspace_destroy(ws)
+        D.dbmp_atlas_destroy(atlas)
+    assert counts[0] == 0 and counts[1] > 0
+    for a, c in zip(out[0], out[1]):
+        assert np.array_equal(a, c)
