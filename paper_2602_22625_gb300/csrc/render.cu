@@ -184,9 +184,12 @@ __device__ __forceinline__ void prefetch_rec(Prefetch<RPL> &pf, const RenderArgs
     }
 }
 
-// Writes n prefetched survivor records to sh[0 .. n) with their list positions.
+// Writes n prefetched survivor records to sh[0 .. n) with their list positions and
+// returns how many of them lie at list positions <= limit: a batch's positions
+// increase, so those are the first ones (same on every lane).
 template <int RPL>
-__device__ __forceinline__ void place(const Prefetch<RPL> &pf, int n, PrimRec *sh, int *pos, int lane) {
+__device__ __forceinline__ int place(const Prefetch<RPL> &pf, int n, PrimRec *sh, int *pos, int limit, int lane) {
+    int m = 0;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         const int j = lane + 32 * r;
@@ -197,8 +200,10 @@ __device__ __forceinline__ void place(const Prefetch<RPL> &pf, int n, PrimRec *s
             d[2] = pf.q2[r];
             pos[j] = pf.pos[r];
         }
+        m += __popc(__ballot_sync(FULL, j < n && pf.pos[r] <= limit));
     }
     __syncwarp();
+    return m;
 }
 
 struct Region {
@@ -576,6 +581,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
     const float rho = kw / kv, irho = kv / kw;
     __shared__ WarpStats stats_all[kWarpsPerBlock];
     WarpStats &stats = stats_all[warp];   // pairs evaluated, -, walked, survivors
+    // the region's largest last layer, kept in shared memory: the walk over recorded
+    // survivors reads it once per batch, and a register held across the walk costs spills
+    __shared__ int last_max_all[kWarpsPerBlock];
     if (lane < 4) stats.v[lane] = 0ull;
     __syncwarp();
 
@@ -622,6 +630,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
             stats.v[2] += (unsigned)(my_max + 1);
         }
         if (my_max < 0) continue;
+        if (lane == 0) last_max_all[warp] = my_max;
+        __syncwarp();
         const float rx0 = (float)g.x0, ry0 = (float)g.y0;
         const float rw = (float)(RW - 1), rh = (float)(RH - 1);
 
@@ -641,9 +651,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
             prefetch<RPL>(pf, a, g.start + lo, hi - lo, lane);
         while (hi > 0) {
             int m;
-            if (use_rec) {
-                m = hi - lo;
-                place<RPL>(pf, m, sh, pos, lane);
+            if (use_rec) {   // the entries behind every pixel's last layer are left out
+                m = place<RPL>(pf, hi - lo, sh, pos, last_max_all[warp], lane);
             } else {
                 m = compact<RPL>(pf, lo, hi - lo, sh, pos, a, rx0, ry0, rw, rh, kw, kv, lane);
             }
@@ -657,7 +666,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
             }
             for (int t = m - 1; t >= 0; --t) {
                 const int j = pos[t];
-                if (j > my_max) continue;   // behind every pixel's last layer (recorded survivors)
                 const PrimRec r = sh[t];
                 const ColXf cx = col_xf(r, kw, kv, px);
                 if constexpr (PPT % 2 == 0) {
