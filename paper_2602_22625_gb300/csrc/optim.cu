@@ -215,26 +215,26 @@ __global__ void k_adam8(float4 *__restrict__ p, float4 *__restrict__ g, float4 *
     const float bc1 = 1.0f - powf(c.beta1, (float)t);
     const float bc2 = 1.0f - powf(c.beta2, (float)t);
     const float lr_t = c.lr * powf(c.gamma, (float)(t - 1));
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    // one float4 per thread: half (h) of primitive k / 2's eight parameters
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 2 * (int64_t)N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int h = (int)(k & 1);
+        const float4 g4 = g[k], m4 = m[k], v4 = v[k], p4 = p[k];
+        if (c.zero_grad) g[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float gi[4] = {g4.x, g4.y, g4.z, g4.w}, mo[4] = {m4.x, m4.y, m4.z, m4.w};
+        const float vo[4] = {v4.x, v4.y, v4.z, v4.w}, po[4] = {p4.x, p4.y, p4.z, p4.w};
+        float mn[4], vn[4], pn[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t k = 2 * (int64_t)i + h;
-            const float4 g4 = g[k], m4 = m[k], v4 = v[k], p4 = p[k];
-            if (c.zero_grad) g[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            const float gi[4] = {g4.x, g4.y, g4.z, g4.w}, mo[4] = {m4.x, m4.y, m4.z, m4.w};
-            const float vo[4] = {v4.x, v4.y, v4.z, v4.w}, po[4] = {p4.x, p4.y, p4.z, p4.w};
-            float mn[4], vn[4], pn[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                mn[e] = c.beta1 * mo[e] + (1.0f - c.beta1) * gi[e];
-                vn[e] = c.beta2 * vo[e] + (1.0f - c.beta2) * gi[e] * gi[e];
-                const float mh = mn[e] / bc1, vh = vn[e] / bc2;
-                pn[e] = po[e] - lr_t * c.gains[4 * h + e] * mh / (sqrtf(vh) + c.eps);
-            }
-            m[k] = make_float4(mn[0], mn[1], mn[2], mn[3]);
-            v[k] = make_float4(vn[0], vn[1], vn[2], vn[3]);
-            p[k] = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        for (int e = 0; e < 4; ++e) {
+            mn[e] = c.beta1 * mo[e] + (1.0f - c.beta1) * gi[e];
+            vn[e] = c.beta2 * vo[e] + (1.0f - c.beta2) * gi[e] * gi[e];
+            const float mh = mn[e] / bc1, vh = vn[e] / bc2;
+            const float gain = h ? c.gains[4 + e] : c.gains[e];
+            pn[e] = po[e] - lr_t * gain * mh / (sqrtf(vh) + c.eps);
         }
+        m[k] = make_float4(mn[0], mn[1], mn[2], mn[3]);
+        v[k] = make_float4(vn[0], vn[1], vn[2], vn[3]);
+        p[k] = make_float4(pn[0], pn[1], pn[2], pn[3]);
     }
 }
 
@@ -342,7 +342,7 @@ cudaError_t launch_adam(float *p, float *g, float *m, float *v, int32_t N, int32
     const bool aligned = ((((uintptr_t)p) | ((uintptr_t)g) | ((uintptr_t)m) | ((uintptr_t)v)) & 15) == 0;
     cudaError_t e = cudaSuccess;
     if (n > 0 && aligned)
-        e = launch_pdl(k_adam8, dim3(grid_for(N, 128)), dim3(128), 0, st, reinterpret_cast<float4 *>(p),
+        e = launch_pdl(k_adam8, dim3(grid_for(2 * (int64_t)N, 128)), dim3(128), 0, st, reinterpret_cast<float4 *>(p),
                        reinterpret_cast<float4 *>(g), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), N,
                        static_cast<const int32_t *>(step), c);
     else if (n > 0)

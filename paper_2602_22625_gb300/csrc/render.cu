@@ -873,15 +873,19 @@ __global__ void k_item_order(const int32_t *__restrict__ cost, int32_t *__restri
     }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        if (total != n) {
-            order[i] = i;
-            return;
-        }
-        const int c = max(cost[i], 1);
-        const int b = 31 - __clz(c);
-        order[base[b] + atomicAdd(hist + 32 + b, 1)] = i;
+    if (total != n) {
+        if (i < n) order[i] = i;
+        return;
     }
+    // one atomic per bucket per warp: the lanes of a bucket take consecutive slots
+    const int b = i < n ? 31 - __clz(max(cost[i], 1)) : -1;
+    const unsigned same = __match_any_sync(FULL, b);
+    const int lead = __ffs(same) - 1;
+    const int lane = threadIdx.x & 31;
+    int slot = 0;
+    if (b >= 0 && lane == lead) slot = atomicAdd(hist + 32 + b, __popc(same));
+    slot = __shfl_sync(FULL, slot, lead) + __popc(same & ((1u << lane) - 1u));
+    if (b >= 0) order[base[b] + slot] = i;
 }
 
 // Per-primitive chain rule from the eight reduced sums to the raw parameters:
