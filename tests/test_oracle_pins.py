@@ -611,3 +611,25 @@ def test_grad_pixels_equals_rows_and_masked_full_gradients():
     twice = oracle.grad_pixels(H, W, params, bid, atlas, gI, (np.r_[px, px], np.r_[py, py]))
     once = oracle.grad_pixels(H, W, params, bid, atlas, gI, (px, py))
     np.testing.assert_allclose(twice, 2 * once, rtol=1e-13, atol=1e-300)
+
+
+def test_binning_rect_beyond_the_reduction_range_holds_every_rotation():
+    """For |theta| > 65536 the specification's sine and cosine are not computed; the
+    box is centred on (x, y) with half-extents |s| (|uc| + eu + |vc| + ev), which holds
+    the bitmap's non-zero texels at any rotation: every pixel a solo FP64 render
+    leaves with T < 1 lies in a listed tile."""
+    atlas = _offcentre_atlas()
+    tile = 8
+    rng = np.random.default_rng(23)
+    for b in range(atlas.shape[0]):
+        p = np.zeros((1, 8), np.float32)
+        p[0, :3] = (40.0 + rng.uniform(-3, 3), 44.0 + rng.uniform(-3, 3), 14.0)
+        p[0, 3] = 1.0e6 + rng.uniform(0, 7)   # beyond 65536
+        p[0, 4:] = 2.0
+        bid = np.array([b], np.int32)
+        rects, tau = oracle.bin_rects(96, 96, tile, p, bid, atlas)
+        solo = oracle.render(96, 96, p, bid, atlas, background=None)
+        ys, xs = np.nonzero(solo["T_final"] < 1.0)
+        assert tau[0] > 0 and len(xs) > 0
+        assert (xs // tile).min() >= rects[0, 0] and (xs // tile).max() <= rects[0, 2]
+        assert (ys // tile).min() >= rects[0, 1] and (ys // tile).max() <= rects[0, 3]
