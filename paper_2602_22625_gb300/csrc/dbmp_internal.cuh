@@ -87,6 +87,7 @@ cudaError_t launch_alpha_loss(const float *image, const float *T_final, const fl
 // running count per slab tile (scatter only).
 constexpr int32_t kBinSmemCap = 96 * 1024;
 constexpr int32_t kBinTargetCtas = 8 * 152;   // enough CTAs to fill every SM several times
+constexpr int64_t kBinPairsLarge = (int64_t)1 << 19;   // (chunk, tile) pairs above which chunks hold 1024
 inline int32_t bin_threads(int32_t chunk_log2) { return chunk_log2 >= 10 ? 1024 : (1 << chunk_log2); }
 inline int64_t bin_smem_bytes(int32_t ntx, int32_t rows, int32_t chunk_log2, bool scatter) {
     const int64_t nw = bin_threads(chunk_log2) / 32;
