@@ -76,7 +76,7 @@ struct DbmpWorkspace {
     int32_t *item_cost = nullptr;          // [item_cap] per-region cost of the last forward
     int32_t *item_order = nullptr;         // [item_cap] regions by decreasing cost
     int64_t item_cap = 0;                  // regions the two arrays hold
-    int32_t *item_hist = nullptr;          // [2][64] cost buckets and cursors of alternate forwards
+    int32_t *item_hist = nullptr;          // [2][256] cost buckets and cursors of alternate forwards
     int32_t hist_half = 0;                 // the half the next forward counts into (zeroed)
     // the order matches the current plan and the forward's regions (0: none yet)
     int32_t order_items = 0;
@@ -128,7 +128,7 @@ size_t ws_bytes(const DbmpLimits &l) {
     b += sizeof(CanvasDesc) * (size_t)l.max_canvases;
     b += sizeof(DevStatus);
     b += sizeof(unsigned long long) * kBinStatsWords;
-    b += 2 * sizeof(int32_t) * (size_t)item_capacity(l) + sizeof(int32_t) * 128;
+    b += 2 * sizeof(int32_t) * (size_t)item_capacity(l) + sizeof(int32_t) * 512;
     b += sizeof(int2) * (size_t)surv_capacity(l) + sizeof(int4) * (size_t)item_capacity(l);
     return b;
 }
@@ -342,7 +342,7 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     // together.  The arrays must also hold every region.
     const int32_t items = render_items(ws->cfg, ws->n_tiles, false);
     const bool ordered = items <= ws->item_cap && items <= kOrderMaxRegionsPerSM * sm_count();
-    int32_t *hist = ws->item_hist + 64 * ws->hist_half, *next = ws->item_hist + 64 * (1 - ws->hist_half);
+    int32_t *hist = ws->item_hist + 256 * ws->hist_half, *next = ws->item_hist + 256 * (1 - ws->hist_half);
     if (ordered) {
         if (ws->order_items == items) a.item_order = ws->item_order;
         a.item_cost = ws->item_cost;
@@ -493,7 +493,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
         {(void **)&ws->stats, sizeof(unsigned long long) * kBinStatsWords},
         {(void **)&ws->item_cost, sizeof(int32_t) * (size_t)item_capacity(l)},
         {(void **)&ws->item_order, sizeof(int32_t) * (size_t)item_capacity(l)},
-        {(void **)&ws->item_hist, sizeof(int32_t) * 128},
+        {(void **)&ws->item_hist, sizeof(int32_t) * 512},
         {(void **)&ws->surv, sizeof(int2) * (size_t)surv_capacity(l)},
         {(void **)&ws->surv_tab, sizeof(int4) * (size_t)item_capacity(l)},
     };
@@ -508,7 +508,7 @@ int32_t dbmp_workspace_create(const DbmpLimits *limits, DbmpWorkspace **out) {
     }
     cudaError_t e = cudaMemset(ws->status, 0, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMemset(ws->graw, 0, sizeof(float) * 8 * (size_t)std::max(l.max_prims, 1));
-    if (e == cudaSuccess) e = cudaMemset(ws->item_hist, 0, sizeof(int32_t) * 128);
+    if (e == cudaSuccess) e = cudaMemset(ws->item_hist, 0, sizeof(int32_t) * 512);
     if (e == cudaSuccess) e = init_bin_kernels(kMaxTilesPerCanvas);
     if (e == cudaSuccess) e = init_render_kernels();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -538,13 +538,13 @@ int32_t dbmp_workspace_poison(DbmpWorkspace *ws, dbmp_stream_t stream) {
         {ws->stats, sizeof(unsigned long long) * kBinStatsWords},
         {ws->item_cost, sizeof(int32_t) * (size_t)item_capacity(l)},
         {ws->item_order, sizeof(int32_t) * (size_t)item_capacity(l)},
-        {ws->item_hist, sizeof(int32_t) * 128},
+        {ws->item_hist, sizeof(int32_t) * 512},
         {ws->surv, sizeof(int2) * (size_t)surv_capacity(l)},
         {ws->surv_tab, sizeof(int4) * (size_t)item_capacity(l)},
     };
     for (auto &b : bufs) DBMP_CUDA(cudaMemsetAsync(b.p, 0xFF, b.n, st), "poison");
     // the bucket counts are state that must start at zero, not scratch
-    DBMP_CUDA(cudaMemsetAsync(ws->item_hist, 0, sizeof(int32_t) * 128, st), "poison");
+    DBMP_CUDA(cudaMemsetAsync(ws->item_hist, 0, sizeof(int32_t) * 512, st), "poison");
     ws->order_items = 0;
     ws->surv_items = 0;
     return DBMP_OK;

@@ -274,11 +274,11 @@ struct RenderArgs {
     // item_order set, queue position q takes region item_order[q]; otherwise the
     // regions of tile_order's tiles in turn.  With item_cost set, the forward records
     // each region's cost (surviving records + 1) there and counts it into
-    // item_hist[floor(log2 cost)], from which k_item_order sorts the regions by
-    // decreasing cost for the next pass.
+    // item_hist[cost_bucket(cost)] (four buckets per octave), from which k_item_order
+    // sorts the regions by decreasing cost for the next pass.
     const int32_t *item_order;
     int32_t *item_cost;
-    int32_t *item_hist;         // [32] counts by log2 bucket, then [32] cursors
+    int32_t *item_hist;         // [128] counts by cost bucket, then [128] cursors
     // forward with the MSE loss fused (null target: off): dL/dI = mse_scale (I - I*)
     // into mse_dL, and L = sum (I - I*)^2 / n added into *mse_loss (zeroed by the caller)
     const float *mse_target;

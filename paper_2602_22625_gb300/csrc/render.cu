@@ -206,6 +206,14 @@ __device__ __forceinline__ int place(const Prefetch<RPL> &pf, int n, PrimRec *sh
     return m;
 }
 
+// Bucket of a region cost c >= 1 for the longest-first order: four per octave,
+// 4 floor(log2 c) + the two bits below the leading one (0 .. 127, increasing with c).
+__device__ __forceinline__ int cost_bucket(int c) {
+    const int e = 31 - __clz(c);
+    const int sub = e >= 2 ? (c >> (e - 2)) & 3 : (c << (2 - e)) & 3;
+    return 4 * e + sub;
+}
+
 struct Region {
     int raw;          // region id: tile * R + region within the tile
     CanvasDesc d;
@@ -475,7 +483,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k
             if (a.item_cost) {   // the region's cost, for the next pass' order
                 const int c = sv_it + 1;
                 a.item_cost[g.raw] = c;
-                atomicAdd(a.item_hist + (31 - __clz(c)), 1);
+                atomicAdd(a.item_hist + cost_bucket(c), 1);
             }
             if (a.surv)
                 a.surv_tab[g.raw] = srec ? make_int4((int)(sbase + sfirst), sfill - sfirst, tested, 0)
@@ -844,31 +852,42 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
 }
 
 // Regions sorted by decreasing cost (longest first): a counting sort over the
-// forward's log2 cost buckets.  Within a bucket the order is whatever the atomics
-// give; any order renders the same pixels.  hist[32..63] (the cursors) start at zero.
-// If the buckets do not count every region (a forward that stopped early, e.g. on a
-// tile-list capacity overflow), the order is the identity, so that it always holds
-// every region exactly once.  The counts come in two halves used by alternate
-// forwards: this kernel clears the other half (next_hist) for the next forward, so
-// no separate reset is queued.  Launched as a programmatic dependent of the forward.
+// forward's cost buckets (four per octave, cost_bucket).  Within a bucket the order is
+// whatever the atomics give; any order renders the same pixels.  hist[128..255] (the
+// cursors) start at zero.  If the buckets do not count every region (a forward that
+// stopped early, e.g. on a tile-list capacity overflow), the order is the identity, so
+// that it always holds every region exactly once.  The counts come in two halves used
+// by alternate forwards: this kernel clears the other half (next_hist) for the next
+// forward, so no separate reset is queued.  Launched as a programmatic dependent of the
+// forward, with 256 threads per block.
 __global__ void k_item_order(const int32_t *__restrict__ cost, int32_t *__restrict__ hist,
                              int32_t *__restrict__ next_hist, int32_t *__restrict__ order, int32_t n) {
     pdl_wait();
-    __shared__ int32_t base[32];
+    __shared__ int32_t base[128];
     __shared__ int32_t total;
-    if (blockIdx.x == 0 && threadIdx.x < 64) next_hist[threadIdx.x] = 0;
+    if (blockIdx.x == 0) next_hist[threadIdx.x] = 0;
     if (threadIdx.x < 32) {
-        // lane l holds bucket 31 - l: an inclusive scan over the lanes counts the
-        // regions of all costlier buckets
+        // lane l holds buckets 127 - 4 l ... 124 - 4 l (costliest first): an inclusive
+        // scan over the lanes counts the regions of all costlier buckets
         const int l = threadIdx.x;
-        const int c = hist[31 - l];
-        int incl = c;
+        int c[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c[k] = hist[127 - 4 * l - k];
+            sum += c[k];
+        }
+        int incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(FULL, incl, o);
             if (l >= o) incl += u;
         }
-        base[31 - l] = incl - c;
+        int run = incl - sum;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            base[127 - 4 * l - k] = run;
+            run += c[k];
+        }
         if (l == 31) total = incl;
     }
     __syncthreads();
@@ -878,12 +897,12 @@ __global__ void k_item_order(const int32_t *__restrict__ cost, int32_t *__restri
         return;
     }
     // one atomic per bucket per warp: the lanes of a bucket take consecutive slots
-    const int b = i < n ? 31 - __clz(max(cost[i], 1)) : -1;
+    const int b = i < n ? cost_bucket(max(cost[i], 1)) : -1;
     const unsigned same = __match_any_sync(FULL, b);
     const int lead = __ffs(same) - 1;
     const int lane = threadIdx.x & 31;
     int slot = 0;
-    if (b >= 0 && lane == lead) slot = atomicAdd(hist + 32 + b, __popc(same));
+    if (b >= 0 && lane == lead) slot = atomicAdd(hist + 128 + b, __popc(same));
     slot = __shfl_sync(FULL, slot, lead) + __popc(same & ((1u << lane) - 1u));
     if (b >= 0) order[base[b] + slot] = i;
 }
