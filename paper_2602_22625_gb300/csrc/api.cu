@@ -86,6 +86,10 @@ struct DbmpWorkspace {
     // regions the last forward recorded survivors for, on the current lists (0: none)
     int32_t surv_items = 0;
     int32_t count_pairs = 0;               // forwards count the contributing pairs
+    // the status block's forward / backward group was reset by the last kernel queued
+    // before the next forward / backward (the tile scan / the region sort), which that
+    // pass then follows as a programmatic dependent instead of after a memset
+    bool fwd_group_reset = false, bwd_group_reset = false;
     // host copy of the current plan
     std::vector<CanvasDesc> plan;
     std::vector<int32_t> plan_H, plan_W, plan_off;
@@ -267,7 +271,8 @@ int32_t do_bin(DbmpWorkspace *ws, const float *params, const int32_t *bid, const
                float alpha_max, cudaStream_t st) {
     const BinBuffers b = bin_buffers(ws);
     DBMP_CUDA(cudaMemsetAsync(&ws->status->n_degenerate, 0, sizeof(int32_t), st), "status reset");
-    DBMP_CUDA(launch_bin(b, params, bid, atlas->view(), alpha_max, ws->cfg.tile, st), "bin launch");
+    DBMP_CUDA(launch_bin(b, params, bid, atlas->view(), alpha_max, ws->cfg.tile, st, true), "bin launch");
+    ws->fwd_group_reset = true;
     ws->params = params;
     ws->Hb = atlas->Hb;
     ws->Wb = atlas->Wb;
@@ -348,19 +353,24 @@ int32_t do_fwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
         a.item_cost = ws->item_cost;
         a.item_hist = hist;
     }
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, kFwdGroupBytes, st), "status reset");
+    const bool pdl = ws->fwd_group_reset;
+    if (!pdl) DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_fwd, 0, kFwdGroupBytes, st), "status reset");
+    ws->fwd_group_reset = false;
     // survivors recorded for the backward when it composites the same regions
     const bool record = ws->surv && items <= ws->item_cap && ws->cfg.ppt == ws->cfg.bwd_ppt();
     if (!record) a.surv = nullptr;
     ws->surv_items = 0;
-    DBMP_CUDA(launch_fwd(a, ws->cfg, st), "forward launch");
+    DBMP_CUDA(launch_fwd(a, ws->cfg, st, pdl), "forward launch");
     if (record) ws->surv_items = items;
     if (ordered) {
-        DBMP_CUDA(launch_item_order(ws->item_cost, hist, next, ws->item_order, items, st), "region order");
+        DBMP_CUDA(launch_item_order(ws->item_cost, hist, next, ws->item_order, items, ws->status, st),
+                  "region order");
         ws->order_items = items;
         ws->hist_half = 1 - ws->hist_half;
+        ws->bwd_group_reset = true;
     } else {
         ws->order_items = 0;
+        ws->bwd_group_reset = false;
     }
     return DBMP_OK;
 }
@@ -380,8 +390,10 @@ int32_t do_bwd(DbmpWorkspace *ws, const DbmpAtlas *atlas, const DbmpBackground *
     // the forward's survivors, when it recorded them for these regions on these lists
     a.surv_use = ws->surv_items > 0 && ws->surv_items == render_items(ws->cfg, ws->n_tiles, true) &&
                  ws->cfg.ppt == ws->cfg.bwd_ppt();
-    DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, kBwdGroupBytes, st), "status reset");
-    DBMP_CUDA(launch_bwd(a, ws->cfg, st), "backward launch");
+    const bool pdl = ws->bwd_group_reset;
+    if (!pdl) DBMP_CUDA(cudaMemsetAsync(&ws->status->pairs_eval_bwd, 0, kBwdGroupBytes, st), "status reset");
+    ws->bwd_group_reset = false;
+    DBMP_CUDA(launch_bwd(a, ws->cfg, st, pdl), "backward launch");
     DBMP_CUDA(launch_grad_finalize(ws->params, ws->rec, ws->graw, dparams, ws->N, 0.5f * (float)(atlas->Wb - 1), 0.5f * (float)(atlas->Hb - 1), st), "gradient finalize");
     return DBMP_OK;
 }

@@ -354,7 +354,8 @@ __device__ __forceinline__ int len_bucket(int64_t len) {
 // longest list first (a counting sort on len_bucket; ties in any order) for the
 // persistent compositors.
 __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, int32_t n,
-                                                   int64_t cap, DevStatus *status, int32_t *__restrict__ order) {
+                                                   int64_t cap, DevStatus *status, int32_t *__restrict__ order,
+                                                   int32_t reset_fwd) {
     pdl_wait();
     pdl_trigger();
     __shared__ int64_t warp_sums[32];
@@ -407,6 +408,14 @@ __global__ void __launch_bounds__(1024) k_tilescan(int64_t *__restrict__ off, in
     if (tid == 0) {
         const int64_t K = carry;
         off[n] = K;
+        if (reset_fwd) {   // the forward's status group, for a forward launched as a dependent
+            status->pairs_eval_fwd = 0;
+            status->pairs_contrib = 0;
+            status->warp_steps_fwd = 0;
+            status->survivors_fwd = 0;
+            status->queue_fwd = 0u;
+            status->pad_fwd = 0u;
+        }
         status->pairs_required = K;
         status->lists_valid = K <= cap ? 1 : 0;
         if (K > cap) status->code = (int32_t)DBMP_ERR_CAPACITY;
@@ -591,7 +600,7 @@ cudaError_t init_bin_kernels(int32_t) {
 }
 
 cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,
-                       const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st) {
+                       const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st, bool reset_fwd) {
     if (b.N > 0) {
         k_prep<<<(b.N + 255) / 256, 256, 0, st>>>(params, bitmap_id, b.canvas, b.n_canvas, b.N, atlas,
                                                    alpha_max, tile, b.rec, b.rect, b.status);
@@ -607,7 +616,7 @@ cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *
                                b.n_tiles, b.hist, b.tile_off);
     if (e == cudaSuccess)
         e = launch_pdl(k_tilescan, dim3(1), dim3(1024), 0, st, b.tile_off, b.n_tiles, b.cap, b.status,
-                       b.tile_order);
+                       b.tile_order, (int32_t)(reset_fwd ? 1 : 0));
     if (e == cudaSuccess && b.n_chunks > 0)
         e = launch_pdl(k_scatter, grid_cs, dim3(chunk_threads), b.smem_scatter, st, b.rect, b.canvas, b.n_canvas,
                        b.hist, b.tile_off, b.list, b.status);

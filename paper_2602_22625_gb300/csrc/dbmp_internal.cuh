@@ -106,18 +106,22 @@ inline int32_t bin_slab_rows(int32_t ntx, int32_t nty, int32_t chunk_log2, int64
 }
 cudaError_t init_render_kernels();
 
+// With reset_fwd the binning also resets the status block's forward group (the tile
+// scan does), so that a forward can follow it as a programmatic dependent.
 cudaError_t launch_bin(const BinBuffers &b, const float *params, const int32_t *bitmap_id,
-                       const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st);
+                       const AtlasView &atlas, float alpha_max, int32_t tile, cudaStream_t st,
+                       bool reset_fwd = false);
 
 
 bool render_cfg_supported(const RenderCfg &cfg);
-cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
+cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st, bool pdl = false);
 // Work items (regions) of a forward (bwd false) or backward pass over n_tiles tiles.
 int32_t render_items(const RenderCfg &cfg, int32_t n_tiles, bool bwd);
 // Region order by decreasing forward cost (counting sort of the forward's buckets).
+// With reset_bwd it also resets the backward's status group (see launch_bwd).
 cudaError_t launch_item_order(const int32_t *cost, int32_t *hist, int32_t *next_hist, int32_t *order,
-                              int32_t n_items, cudaStream_t st);
-cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st);
+                              int32_t n_items, DevStatus *reset_bwd, cudaStream_t st);
+cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st, bool pdl = false);
 // dparams += chain rule of the raw sums graw, which are zeroed after reading (graw is
 // zero before every backward: zeroed at workspace creation, left zero by this kernel).
 cudaError_t launch_grad_finalize(const float *params, const PrimRec *rec, float *graw,

@@ -294,6 +294,7 @@ __device__ __forceinline__ int next_item(uint32_t *queue, int lane) {
 // of the forward's time, so it is compiled in only when asked for.
 template <int TILE, int PPT, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, fwd_blocks(PPT, BATCH)) k_fwd(RenderArgs a, int32_t n_items) {
+    pdl_wait();   // launched as a programmatic dependent of the binning when its status group is reset there
     constexpr int RPL = BATCH / 32;   // records per lane per batch
     constexpr int RW = region_w(TILE);
     constexpr int LROWS = 32 / RW;    // rows covered by the 32 lanes in one pass
@@ -574,6 +575,7 @@ __device__ float rewalk_T(const RenderArgs &a, const Region &g, int upto, float 
 
 template <int TILE, int PPT, int BATCH>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k_bwd(RenderArgs a, int32_t n_items) {
+    pdl_wait();   // launched as a programmatic dependent of the region sort when its status group is reset there
     constexpr int RPL = BATCH / 32;
     constexpr int RW = region_w(TILE);
     constexpr int LROWS = 32 / RW;
@@ -859,13 +861,25 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
 // that it always holds every region exactly once.  The counts come in two halves used
 // by alternate forwards: this kernel clears the other half (next_hist) for the next
 // forward, so no separate reset is queued.  Launched as a programmatic dependent of the
-// forward, with 256 threads per block.
+// forward, with 256 threads per block.  With reset_bwd set it also resets the backward's
+// status group, so that the backward can follow as its programmatic dependent with no
+// memset in between.
 __global__ void k_item_order(const int32_t *__restrict__ cost, int32_t *__restrict__ hist,
-                             int32_t *__restrict__ next_hist, int32_t *__restrict__ order, int32_t n) {
+                             int32_t *__restrict__ next_hist, int32_t *__restrict__ order, int32_t n,
+                             DevStatus *reset_bwd) {
     pdl_wait();
+    pdl_trigger();
     __shared__ int32_t base[128];
     __shared__ int32_t total;
     if (blockIdx.x == 0) next_hist[threadIdx.x] = 0;
+    // the backward's status group (counters and work queue), reset for the next backward
+    if (reset_bwd && blockIdx.x == 0 && threadIdx.x == 0) {
+        reset_bwd->pairs_eval_bwd = 0;
+        reset_bwd->warp_steps_bwd = 0;
+        reset_bwd->survivors_bwd = 0;
+        reset_bwd->queue_bwd = 0u;
+        reset_bwd->pad_bwd = 0u;
+    }
     if (threadIdx.x < 32) {
         // lane l holds buckets 127 - 4 l ... 124 - 4 l (costliest first): an inclusive
         // scan over the lanes counts the regions of all costlier buckets
@@ -999,7 +1013,7 @@ void register_occupancy(DeviceKernels &dk) {
 }
 
 template <int TILE, int PPT, int BATCH>
-cudaError_t launch_t(const RenderArgs &a, bool fwd, cudaStream_t st) {
+cudaError_t launch_t(const RenderArgs &a, bool fwd, bool pdl, cudaStream_t st) {
     constexpr int R = TILE * TILE / (32 * PPT);   // regions per tile (any region shape)
     const int32_t n_items = a.n_tiles * R;
     if (fwd) {
@@ -1012,20 +1026,31 @@ cudaError_t launch_t(const RenderArgs &a, bool fwd, cudaStream_t st) {
             b.surv_wcap = (int32_t)(w < 0x7fffffff ? w : 0x7fffffff);
             if (b.surv_wcap < 1) b.surv = nullptr;
         }
-        if (a.count_pairs)
+        if (pdl) {
+            const cudaError_t e =
+                a.count_pairs ? launch_pdl(k_fwd<TILE, PPT, BATCH, true>, dim3(grid), dim3(32 * kWarpsPerBlock), 0, st, b, n_items)
+                              : launch_pdl(k_fwd<TILE, PPT, BATCH, false>, dim3(grid), dim3(32 * kWarpsPerBlock), 0, st, b, n_items);
+            if (e != cudaSuccess) return e;
+        } else if (a.count_pairs) {
             k_fwd<TILE, PPT, BATCH, true><<<grid, 32 * kWarpsPerBlock, 0, st>>>(b, n_items);
-        else
+        } else {
             k_fwd<TILE, PPT, BATCH, false><<<grid, 32 * kWarpsPerBlock, 0, st>>>(b, n_items);
+        }
     } else {
         const int grid = persistent_grid((const void *)k_bwd<TILE, PPT, BATCH>, n_items);
-        k_bwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);
+        if (pdl) {
+            const cudaError_t e = launch_pdl(k_bwd<TILE, PPT, BATCH>, dim3(grid), dim3(32 * kWarpsPerBlock), 0, st, a, n_items);
+            if (e != cudaSuccess) return e;
+        } else {
+            k_bwd<TILE, PPT, BATCH><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a, n_items);
+        }
     }
     return cudaGetLastError();
 }
 
-cudaError_t dispatch(const RenderArgs &a, const RenderCfg &cfg, bool fwd, cudaStream_t st) {
+cudaError_t dispatch(const RenderArgs &a, const RenderCfg &cfg, bool fwd, bool pdl, cudaStream_t st) {
 #define DBMP_CASE(T, P, B) \
-    if (cfg.tile == T && cfg.ppt == P && cfg.batch == B) return launch_t<T, P, B>(a, fwd, st);
+    if (cfg.tile == T && cfg.ppt == P && cfg.batch == B) return launch_t<T, P, B>(a, fwd, pdl, st);
     DBMP_CASE(8, 1, 32) DBMP_CASE(8, 2, 32) DBMP_CASE(8, 1, 64) DBMP_CASE(8, 2, 64)
     DBMP_CASE(16, 1, 32) DBMP_CASE(16, 2, 32) DBMP_CASE(16, 4, 32)
     DBMP_CASE(16, 1, 64) DBMP_CASE(16, 2, 64) DBMP_CASE(16, 4, 64)
@@ -1064,16 +1089,17 @@ bool render_cfg_supported(const RenderCfg &cfg) {
     return tile_ok && ppt_ok(cfg.ppt) && ppt_ok(cfg.bwd_ppt()) && (cfg.batch == 32 || cfg.batch == 64);
 }
 
-// The caller resets the status block's forward (backward) group, work queue included,
-// before each launch.
-cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
-    return dispatch(a, cfg, true, st);
+// The status block's forward (backward) group, work queue included, must be zero at
+// the launch: reset by a memset the caller queues, or by the previous kernel of the
+// stream, which the launch then follows as a programmatic dependent (pdl).
+cudaError_t launch_fwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st, bool pdl) {
+    return dispatch(a, cfg, true, pdl, st);
 }
 
-cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st) {
+cudaError_t launch_bwd(const RenderArgs &a, const RenderCfg &cfg, cudaStream_t st, bool pdl) {
     RenderCfg b = cfg;
     b.ppt = cfg.bwd_ppt();
-    return dispatch(a, b, false, st);
+    return dispatch(a, b, false, pdl, st);
 }
 
 int32_t render_items(const RenderCfg &cfg, int32_t n_tiles, bool bwd) {
@@ -1082,10 +1108,10 @@ int32_t render_items(const RenderCfg &cfg, int32_t n_tiles, bool bwd) {
 }
 
 cudaError_t launch_item_order(const int32_t *cost, int32_t *hist, int32_t *next_hist, int32_t *order,
-                              int32_t n_items, cudaStream_t st) {
+                              int32_t n_items, DevStatus *reset_bwd, cudaStream_t st) {
     if (n_items > 0) {
         const cudaError_t e = launch_pdl(k_item_order, dim3((n_items + 255) / 256), dim3(256), 0, st, cost, hist,
-                                         next_hist, order, n_items);
+                                         next_hist, order, n_items, reset_bwd);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

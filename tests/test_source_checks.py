@@ -21,7 +21,8 @@ def sources():
 
 def kernel_body_start(src, name):
     """Text of kernel `name`'s body from its opening brace (None if not defined here)."""
-    m = re.search(r"__global__\s+void\s+(?:__launch_bounds__\([^)]*\)\s+)?" + re.escape(name) + r"\s*\(", src)
+    m = re.search(r"__global__\s+void\s+(?:__launch_bounds__\((?:[^()]|\([^()]*\))*\)\s+)?" + re.escape(name) + r"\s*\(",
+                  src)
     if not m:
         return None
     depth, i = 0, m.end() - 1
@@ -45,16 +46,16 @@ def first_statement(body):
 def test_pdl_launches_found():
     names = set()
     for src in sources().values():
-        names |= set(re.findall(r"launch_pdl\(\s*(\w+)\s*,", src))
+        names |= set(re.findall(r"launch_pdl\(\s*(\w+)\s*(?:<[^>]*>)?\s*,", src))
     names.discard("kernel")   # the helper's own parameter
     assert {"k_count", "k_colscan", "k_tilescan", "k_scatter", "k_finalize", "k_adam8", "k_adam",
-            "k_step_inc"} <= names
+            "k_step_inc", "k_item_order", "k_fwd", "k_bwd"} <= names
 
 
 def violations(srcs):
     names = set()
     for src in srcs.values():
-        names |= set(re.findall(r"launch_pdl\(\s*(\w+)\s*,", src))
+        names |= set(re.findall(r"launch_pdl\(\s*(\w+)\s*(?:<[^>]*>)?\s*,", src))
     names.discard("kernel")
     bad = []
     for name in sorted(names):
