@@ -144,6 +144,10 @@ typedef struct {
     int64_t pairs_required; /* sum_t d_t of the last binning                    */
     int64_t pairs_evaluated;/* (pixel, list entry) pairs the last fwd evaluated  */
     int64_t pairs_evaluated_bwd; /* same for the last bwd                       */
+    /* (The forward's counters start from zero at each forward, the backward's at each
+     * backward; they are cleared by the binning / the forward's region sort when those
+     * come first, so that the pass can start as their programmatic dependent, and
+     * otherwise by a memset queued with the pass.) */
     int64_t pairs_contributing;  /* pairs with alpha > 0 the last fwd composited,
                                     i.e. layers with M > 0 met while T >= T_stop;
                                     0 unless dbmp_workspace_count_pairs enabled it */
