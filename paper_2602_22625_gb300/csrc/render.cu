@@ -100,8 +100,15 @@ __device__ __forceinline__ PrimRec as_rec(float4 a, float4 b, float4 c) {
 // tap any of its pixels reads; the bitmap's summed-area table of non-zero texels
 // says whether that box holds a non-zero texel.  Never false for a primitive that
 // is non-zero at one of the pixels, so culling with it changes no result.
+// The bounds carry fp32 rounding errors of a few 2^-24 (|A| (|dx| + w) + |B| (|dy| + h))
+// texels (likewise for V).  The region lies in a tile the primitive's box reaches, so
+// |A dx| <= 2 kw + |A| x tile, and while |A| + |B| + |C| + |D| <= 2^12 the errors stay
+// far below the one texel by which the box is widened.  A larger transform (a
+// half-extent below a few hundredths of a pixel) can lose the bitmap's offset kw to
+// cancellation in U0 + A w, so such a primitive is never culled.
 __device__ __forceinline__ bool region_hits(const PrimRec &r, const AtlasView &at, float x0, float y0,
                                             float w, float h, float kw, float kv) {
+    if (fabsf(r.A) + fabsf(r.B) + fabsf(r.C) + fabsf(r.D) > 4096.0f) return true;
     const float dx = x0 - r.x, dy = y0 - r.y;
     const float U0 = fmaf(r.A, dx, r.B * dy) + kw;
     const float V0 = fmaf(r.C, dx, r.D * dy) + kv;

@@ -106,6 +106,48 @@ def test_every_tuning_renders_the_same_bits(T_stop):
         assert np.array_equal(T, first[2]), f"{tuning} vs {first[0]}"
 
 
+def scene_sub_pixel(seed=31, H=48, W=48):
+    """Primitives far smaller than a pixel (s = 1e-9 .. 0.2 px) on integer centres at
+    rotations 0, 45, 90, 180 and 270 degrees, between two groups of ordinary ones.
+    Along the line through a tiny primitive's centre in its u direction, V is within
+    the bitmap while |U| reaches ~1e12 (s = 1e-9): those pixels' taps lie far beyond
+    the bitmap's columns.  Returns the scene and the indices of the tiny primitives."""
+    g = np.random.default_rng(seed)
+    tiny = []
+    for s in (1e-9, 1e-6, 1e-3, 0.2):
+        for th in (0.0, 0.25 * np.pi, 0.5 * np.pi, np.pi, 1.5 * np.pi):
+            x, y = g.integers(4, W - 4), g.integers(4, H - 4)
+            tiny.append([x, y, s, th, g.normal(), *g.normal(size=3)])
+    big = [[g.uniform(0, W), g.uniform(0, H), g.uniform(6, 20), g.uniform(0, 2 * np.pi), g.normal(),
+            *g.normal(size=3)] for _ in range(12)]
+    p = np.array(big[:6] + tiny + big[6:], np.float32)
+    atlas = inputs.tiny(seed=3).atlas[:1]
+    sc = inputs.Scene("sub-pixel", H, W, p, np.zeros(len(p), np.int32), atlas)
+    return sc, np.arange(6, 6 + len(tiny))
+
+
+@pytest.mark.parametrize("tuning", [(16, 32, 2), (32, 32, 4), (8, 32, 1)], ids=lambda t: f"t{t[0]}p{t[2]}")
+def test_sub_pixel_primitives_sample_nothing_beyond_the_bitmap(tuning):
+    """The backward tests only V's range before a gather and relies on the texture's
+    border for U: a footprint in columns < 0 or >= W_b reads zeros, however far out.
+    Each tiny primitive composites only at its own centre pixel (where the atlas is
+    flat, so its geometric gradients are exactly 0); any texel read beyond the bitmap
+    would give it a non-zero geometric gradient, and the deeper layers' recovered
+    transmittance would change.  Image and gradients against the oracle."""
+    sc, tiny = scene_sub_pixel()
+    rng = np.random.default_rng(8)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    img, T, g, st = run_batch([sc], sc.atlas, tuning, gI=gI)
+    assert st.code == 0
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=sc.background)
+    assert np.abs(img.reshape(3, sc.H, sc.W) - ref["image"]).max() <= IMG_TOL
+    gref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=sc.background)
+    assert np.all(gref[tiny, :4] == 0.0) and np.abs(gref[tiny, 4:]).max() > 1e-3
+    grad_close(g[tiny], gref[tiny], what=f"{tuning} sub-pixel")
+    big = np.setdiff1d(np.arange(sc.N), tiny)
+    grad_close(g[big], gref[big], what=f"{tuning} ordinary")
+
+
 @pytest.mark.parametrize("tuning", [(16, 32, 2, 4), (32, 64, 4, 1), (8, 32, 1, 2)],
                          ids=lambda t: f"t{t[0]}b{t[1]}p{t[2]}pb{t[3]}")
 def test_forward_and_backward_at_different_ppt_match_oracle(tuning):
