@@ -178,6 +178,11 @@ __device__ __forceinline__ void tap_issue(const PrimRec &r, const ColXf &c, cuda
 // tap_issue for two pixels of one column (rows py2.x, py2.y), with the transform and
 // the fractional parts in packed FP32x2 instructions.  Lane-wise the roundings are
 // those of tap_issue: a - b is computed as fma(b, -1, a), which rounds a - b once.
+// V_ONLY tests only V's range: for U outside [-1, W_b) the gather's 2 x 2 footprint
+// lies in columns < 0 or >= W_b, where the texture's border gives zeros, so M and both
+// derivatives are exactly 0 as when no gather is issued (the backward's choice: it
+// then issues gathers for pixels beside the bitmap, but tests less).
+template <bool V_ONLY = false>
 __device__ __forceinline__ void tap_issue2(const PrimRec &r, const ColXf &c, cudaTextureObject_t tex, float Wbf,
                                            float Hbf, float2 py2, bool live0, bool live1, Tap &t0, Tap &t1) {
     const float2 m1 = make_float2(-1.0f, -1.0f);
@@ -188,8 +193,13 @@ __device__ __forceinline__ void tap_issue2(const PrimRec &r, const ColXf &c, cud
     const float2 wu = __ffma2_rn(fu, m1, U), wv = __ffma2_rn(fv, m1, V);
     t0.U = U.x; t0.V = V.x; t0.wu = wu.x; t0.wv = wv.x;
     t1.U = U.y; t1.V = V.y; t1.wu = wu.y; t1.wv = wv.y;
-    t0.ok = live0 && U.x >= -1.0f && U.x < Wbf && V.x >= -1.0f && V.x < Hbf;
-    t1.ok = live1 && U.y >= -1.0f && U.y < Wbf && V.y >= -1.0f && V.y < Hbf;
+    if (V_ONLY) {
+        t0.ok = live0 && V.x >= -1.0f && V.x < Hbf;
+        t1.ok = live1 && V.y >= -1.0f && V.y < Hbf;
+    } else {
+        t0.ok = live0 && U.x >= -1.0f && U.x < Wbf && V.x >= -1.0f && V.x < Hbf;
+        t1.ok = live1 && U.y >= -1.0f && U.y < Wbf && V.y >= -1.0f && V.y < Hbf;
+    }
     if (t0.ok) {
         const float4 g = tex2Dgather<float4>(tex, __fadd_rn(fu.x, 1.0f), __fadd_rn(fv.x, c.row), 0);
         t0.q = make_float4(g.w, g.z, g.x, g.y);

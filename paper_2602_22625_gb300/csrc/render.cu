@@ -688,8 +688,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, bwd_blocks(PPT, BATCH)) k
                 if constexpr (PPT % 2 == 0) {
 #pragma unroll
                     for (int k = 0; k < PPT; k += 2)
-                        tap_issue2(r, cx, a.atlas.tex, Wbf, Hbf, make_float2(py[k], py[k + 1]), j <= last[k],
-                                   j <= last[k + 1], tp[k], tp[k + 1]);
+                        tap_issue2<true>(r, cx, a.atlas.tex, Wbf, Hbf, make_float2(py[k], py[k + 1]), j <= last[k],
+                                         j <= last[k + 1], tp[k], tp[k + 1]);
                 } else {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) tap_issue(r, cx, a.atlas.tex, Wbf, Hbf, py[k], j <= last[k], tp[k]);
