@@ -173,6 +173,52 @@ def test_multi_canvas_batch_matches_oracle_per_canvas(tuning):
     assert st.pairs_required > 0
 
 
+def scenes_extreme(seed=61):
+    """A ragged batch of degenerate canvases and extents: 1 x 1, 1 x 37 and 29 x 1
+    canvases, and a 40 x 40 canvas whose primitives include half-extents of 1e3 to
+    1e20 px (the bitmap's centre stretched over the canvas), rotations of 1e30 (beyond
+    the binning's sine/cosine range: a box holding every rotation), centres 1e9 px
+    away with a half-extent that still reaches the canvas, and negative scales; each
+    canvas also has a few ordinary primitives."""
+    g = np.random.default_rng(seed)
+    atlas = inputs.tiny(seed=3).atlas[:1]
+
+    def ordinary(n, H, W):
+        return [[g.uniform(-5, W + 5), g.uniform(-5, H + 5), g.uniform(2, 12) * g.choice([-1, 1]),
+                 g.uniform(0, 2 * np.pi), g.normal(), *g.normal(size=3)] for _ in range(n)]
+
+    scenes = []
+    for H, W in ((1, 1), (1, 37), (29, 1)):
+        p = np.array(ordinary(6, H, W), np.float32)
+        scenes.append(inputs.Scene(f"{H}x{W}", H, W, p, np.zeros(len(p), np.int32), atlas))
+    ext = [[20.0, 20.0, 1e3, 0.3, 0.5, 0.2, -0.4, 0.9],
+           [5.0, 33.0, 1e20, 1.1, -0.5, 1.0, 0.3, -0.2],
+           [17.0, 9.0, 8.0, 1e30, 0.8, -0.6, 0.1, 0.4],
+           [-1e9, 20.0, 1.5e9, 0.0, 0.3, 0.7, -0.9, 0.2],
+           [20.0, 1e9, -1.5e9, 0.5 * np.pi, -0.2, -0.3, 0.6, 0.5],
+           [30.0, 12.0, -6.0, -1e30, 1.2, 0.4, 0.4, -0.7]]
+    p = np.array(ordinary(3, 40, 40) + ext + ordinary(3, 40, 40), np.float32)
+    scenes.append(inputs.Scene("extreme", 40, 40, p, np.zeros(len(p), np.int32), atlas))
+    return scenes, atlas
+
+
+@pytest.mark.parametrize("tuning", [(16, 32, 2), (32, 32, 4), (8, 64, 1)], ids=lambda t: f"t{t[0]}p{t[2]}")
+def test_degenerate_canvases_and_extents_match_oracle(tuning):
+    scenes, atlas = scenes_extreme()
+    params, bid, off, pix = concat(scenes)
+    rng = np.random.default_rng(10)
+    gI = rng.normal(size=3 * int(pix[-1])).astype(np.float32)
+    img, T, g, st = run_batch(scenes, atlas, tuning, gI=gI)
+    assert st.code == 0
+    imgs, Ts, gIs = split(img, scenes, pix, 3), split(T, scenes, pix, 1), split(gI, scenes, pix, 3)
+    for c, s in enumerate(scenes):
+        ref = oracle.render(s.H, s.W, s.params, s.bitmap_id, atlas, background=s.background)
+        assert np.abs(imgs[c] - ref["image"]).max() <= IMG_TOL, s.name
+        assert np.abs(Ts[c].reshape(s.H, s.W) - ref["T_final"]).max() <= IMG_TOL, s.name
+        gref = oracle.grad(s.H, s.W, s.params, s.bitmap_id, atlas, gIs[c], background=s.background)
+        grad_close(g[off[c]:off[c + 1]], gref, what=f"{tuning} {s.name}")
+
+
 def test_batched_workload_sampled_against_oracle():
     """The 64-canvas workload shape (sides 256..1024, 1k..50k primitives), scaled
     down to 12 canvases so the oracle can check sampled pixels of every canvas."""
