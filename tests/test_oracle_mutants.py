@@ -23,6 +23,10 @@ MUTANTS = {
     "theta_gradient_sign": ("Gk[3] += gu * L->v + gv * (-L->u);", "Gk[3] += gu * L->v + gv * (L->u);"),
     "bitmap_scale_W_not_W_minus_1": ("double U = (L->u + 1.0) / 2.0 * (double)(Wb - 1);",
                                      "double U = (L->u + 1.0) / 2.0 * (double)(Wb);"),
+    "bitmap_V_scale_uses_width": ("double V = (L->v + 1.0) / 2.0 * (double)(Hb - 1);",
+                                  "double V = (L->v + 1.0) / 2.0 * (double)(Wb - 1);"),
+    "half_widths_swapped_in_backward": ("double gu = dM * dMdU * kw, gv = dM * dMdV * kv;",
+                                        "double gu = dM * dMdU * kv, gv = dM * dMdV * kw;"),
     "back_product_not_updated": ("B *= (1.0 - L->alpha);\n    }\n}", "}\n}"),
     "transmittance_update": ("T *= (1.0 - L.alpha);", "T *= (1.0 - 0.5 * L.alpha);"),
     "bin_margin_sign": ("float fx0 = floorf(((cx - hx) - m) * inv_t);",
@@ -40,7 +44,9 @@ MUTANTS = {
     "base_probability_dropped": ("const double w = 0.1 + 0.9 * lv[p];", "const double w = lv[p];"),
     "scale_rule_reversed": ("o[2] = s_max - (s_max - s_min) * lv[p];", "o[2] = s_min + (s_max - s_min) * lv[p];"),
     "grad_selected_clip_off_by_one": ("if (x1 > W - 1) x1 = W - 1;", "if (x1 > W - 2) x1 = W - 2;"),
-    "grad_selected_box_row_dropped": ("y1 = (long)ceil(q->yhi);", "y1 = (long)floor(q->yhi) - 1;"),
+    # the support box has a pixel of slack beyond the padding ring, so a box shorter by
+    # one or two rows is still exact (an equivalent mutant); three rows cut into it
+    "grad_selected_box_short_by_three_rows": ("y1 = (long)ceil(q->yhi);", "y1 = (long)ceil(q->yhi) - 3;"),
     "grad_selected_row_index": ("pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, sel[t]);",
                                 "pixel_grad(P, Hb, Wb, Ls, n, g, gA, b, Gl, t);"),
     "grad_pixels_index_transposed": ("size_t pix = (size_t)py[i] * (size_t)W + (size_t)px[i];",
@@ -50,20 +56,34 @@ MUTANTS = {
 }
 
 
+def run_pins(tmp_path, src):
+    """Runs the pin tests against a copy of the oracle built from `src` (the test
+    files and the helpers they import copied beside it); returns the pytest result."""
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("_lib", "__pycache__"))
+    (tmp_path / "oracle" / "dbmp_oracle.c").write_text(src)
+    (tmp_path / "tests").mkdir()
+    for f in ("test_oracle_pins.py", "test_oracle_init.py", "conftest.py", "_helpers.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    os.symlink(os.path.join(ROOT, "paper_2602_22625_gb300"), tmp_path / "paper_2602_22625_gb300")
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           "tests/test_oracle_pins.py", "tests/test_oracle_init.py"], cwd=tmp_path,
+                          capture_output=True, text=True, timeout=300)
+
+
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    """The control: the copied oracle and pins pass as they stand, so a failure
+    below comes from the planted mistake, not from the copy (a missing helper module
+    would make every mutant look caught)."""
+    r = run_pins(tmp_path, open(os.path.join(ROOT, "oracle", "dbmp_oracle.c")).read())
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
     src = open(os.path.join(ROOT, "oracle", "dbmp_oracle.c")).read()
     a, b = MUTANTS[name]
     assert a in src
-    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
-                    ignore=shutil.ignore_patterns("_lib", "__pycache__"))
-    (tmp_path / "oracle" / "dbmp_oracle.c").write_text(src.replace(a, b, 1))
-    (tmp_path / "tests").mkdir()
-    for f in ("test_oracle_pins.py", "test_oracle_init.py", "conftest.py"):
-        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
-    os.symlink(os.path.join(ROOT, "paper_2602_22625_gb300"), tmp_path / "paper_2602_22625_gb300")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_init.py"], cwd=tmp_path,
-                       capture_output=True, text=True, timeout=300)
+    r = run_pins(tmp_path, src.replace(a, b, 1))
     assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
-    assert "failed" in r.stdout
+    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]

@@ -175,13 +175,22 @@ def torch_naive(H, W, params, bid, atlas, amax, bg):
     return p, I, T
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(6))
 def test_oracle_matches_torch_grid_sample_and_autograd(case):
+    """Cases 4 and 5 have non-square bitmaps (24 x 40 and 48 x 28), where Eq. 2's
+    horizontal and vertical half-widths differ: a swap of the two, or of their ratio in
+    the rotation gradient, fails there."""
     rng = np.random.default_rng(100 + case)
-    H, W = [(24, 24), (17, 29), (32, 20), (21, 21)][case]
-    N = [1, 3, 6, 8][case]
-    atlas = inputs.stroke_atlas(7 + case, 3, 24, n_seg=16) if case % 2 else \
-        inputs.soft_disc_atlas(9 + case, 2, 32)
+    H, W = [(24, 24), (17, 29), (32, 20), (21, 21), (26, 31), (30, 22)][case]
+    N = [1, 3, 6, 8, 5, 7][case]
+    if case == 4:
+        atlas = inputs.stroke_atlas(11, 3, 40, n_seg=16)[:, 6:30, :]
+    elif case == 5:
+        atlas = inputs.soft_disc_atlas(13, 2, 48)[:, :, 10:38]
+    else:
+        atlas = inputs.stroke_atlas(7 + case, 3, 24, n_seg=16) if case % 2 else \
+            inputs.soft_disc_atlas(9 + case, 2, 32)
+    atlas = np.ascontiguousarray(atlas)
     params = np.zeros((N, 8), np.float32)
     params[:, 0] = rng.uniform(0, W, N)
     params[:, 1] = rng.uniform(0, H, N)
@@ -190,9 +199,9 @@ def test_oracle_matches_torch_grid_sample_and_autograd(case):
     params[:, 4] = rng.uniform(-2, 3, N)
     params[:, 5:8] = rng.uniform(-3, 3, (N, 3))
     bid = rng.integers(0, atlas.shape[0], N).astype(np.int32)
-    amax = [1.0, 0.7, 0.9, 1.0][case]
+    amax = [1.0, 0.7, 0.9, 1.0, 0.8, 1.0][case]
     bg = [(1.0, 1.0, 1.0), (0.2, 0.5, 0.1), rng.uniform(0, 1, (3, H, W)).astype(np.float32),
-          (0.0, 0.0, 0.0)][case]
+          (0.0, 0.0, 0.0), (0.3, 0.3, 0.9), (1.0, 1.0, 1.0)][case]
     p, I, T = torch_naive(H, W, params, bid, atlas, amax, bg)
     out = oracle.render(H, W, params, bid, atlas, alpha_max=amax, background=bg)
     np.testing.assert_allclose(out["image"], I.detach().numpy(), rtol=0, atol=1e-12)
@@ -536,10 +545,10 @@ def test_contributing_pair_count_matches_a_torch_walk(T_stop):
 # --------------------------------------------------------------------------
 
 def _edge_scene(seed):
-    """A ragged 37 x 29 canvas of soft discs plus the placements where a support box
-    meets the canvas border or the box rule itself matters: primitives centred past
-    the right and bottom edges and across the top-left corner, rotated ones, a
-    negative scale, a NaN parameter and a zero scale."""
+    """A ragged 37 x 29 canvas of soft discs and edge-to-edge bitmaps plus the
+    placements where a support box meets the canvas border or the box rule itself
+    matters: primitives centred past the right and bottom edges and across the
+    top-left corner, rotated ones, a negative scale, a NaN parameter and a zero scale."""
     H, W = 37, 29
     sc = inputs.tiny(seed=seed, N=24, H=H, W=W)
     extra = np.array([
@@ -553,8 +562,15 @@ def _edge_scene(seed):
         [W - 1.0, 4.0, 3.2, 0.785, 2.0, 1.5, -1.5, 0.0],     # small, at the last column
     ], np.float32)
     params = np.concatenate([sc.params[:12], extra, sc.params[12:]])
+    # a second bitmap non-zero up to its edges: its taps in the zero-padding ring
+    # (U or V within one texel outside the bitmap) are non-zero, so the support box
+    # is exercised to its last row and column
+    edge = np.random.default_rng(seed).uniform(0.2, 1.0, (1,) + sc.atlas.shape[1:]).astype(np.float32)
+    atlas = np.concatenate([sc.atlas, edge])
     bid = np.zeros(params.shape[0], np.int32)
-    return H, W, params, bid, sc.atlas
+    bid[::3] = 1
+    bid[12:16] = 1
+    return H, W, params, bid, atlas
 
 
 @pytest.mark.parametrize("bg", ["const", "none", "buffer"])
