@@ -219,6 +219,45 @@ def test_degenerate_canvases_and_extents_match_oracle(tuning):
         grad_close(g[off[c]:off[c + 1]], gref, what=f"{tuning} {s.name}")
 
 
+def scene_non_square(seed=71, H=70, W=90):
+    """Bitmaps of 24 x 40 texels (H_b != W_b: the horizontal and vertical half-widths
+    of Eq. 2 differ, and so do rho and 1/rho in the rotation gradient): two strokes, an
+    all-zero bitmap (never listed) and one whose only non-zero texel is its last
+    corner (the tight binning box and the zero padding at a corner)."""
+    g = np.random.default_rng(seed)
+    strokes = inputs.stroke_atlas(17, 2, 40, n_seg=16)[:, 8:32, :]
+    corner = np.zeros((1, 24, 40), np.float32)
+    corner[0, 23, 39] = 0.9
+    atlas = np.ascontiguousarray(np.concatenate([strokes, np.zeros((1, 24, 40), np.float32), corner]))
+    N = 90
+    p = np.zeros((N, 8), np.float32)
+    p[:, 0] = g.uniform(-5, W + 5, N)
+    p[:, 1] = g.uniform(-5, H + 5, N)
+    p[:, 2] = g.uniform(4, 24, N) * g.choice([1, 1, -1], N)
+    p[:, 3] = g.uniform(-4, 4, N)
+    p[:, 4] = g.uniform(-1, 2, N)
+    p[:, 5:] = g.normal(size=(N, 3))
+    bid = g.choice([0, 1, 2, 3], N, p=[0.4, 0.4, 0.1, 0.1]).astype(np.int32)
+    return inputs.Scene("non-square", H, W, p, bid, atlas)
+
+
+@pytest.mark.parametrize("tuning", [(16, 32, 2), (32, 32, 4), (8, 64, 1)], ids=lambda t: f"t{t[0]}p{t[2]}")
+def test_non_square_bitmaps_match_oracle(tuning):
+    sc = scene_non_square()
+    rng = np.random.default_rng(12)
+    gI = rng.normal(size=(3, sc.H, sc.W)).astype(np.float32)
+    img, T, g, st = run_batch([sc], sc.atlas, tuning, gI=gI, bg=(0.2, 0.4, 0.6))
+    assert st.code == 0
+    ref = oracle.render(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, background=(0.2, 0.4, 0.6))
+    assert np.abs(img.reshape(3, sc.H, sc.W) - ref["image"]).max() <= IMG_TOL
+    assert np.abs(T.reshape(sc.H, sc.W) - ref["T_final"]).max() <= IMG_TOL
+    gref = oracle.grad(sc.H, sc.W, sc.params, sc.bitmap_id, sc.atlas, gI, background=(0.2, 0.4, 0.6))
+    grad_close(g, gref, what=str(tuning))
+    assert not g[sc.bitmap_id == 2].any()   # the all-zero bitmap contributes nothing
+    corner = np.nonzero(sc.bitmap_id == 3)[0]
+    assert np.abs(gref[corner]).max() > 0   # the corner texel is reached
+
+
 def test_batched_workload_sampled_against_oracle():
     """The 64-canvas workload shape (sides 256..1024, 1k..50k primitives), scaled
     down to 12 canvases so the oracle can check sampled pixels of every canvas."""
