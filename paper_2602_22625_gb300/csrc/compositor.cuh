@@ -129,7 +129,9 @@ struct RenderCfg {
 // and each pixel adds its row part:
 //     dy = py - y,   U = B dy + au,    V = D dy + cv             (tap_issue)
 // (U, V) outside (-1, W_b) x (-1, H_b) reads only zero taps; there, and for a
-// pixel that no longer composites, no load is issued and tap_M returns 0.
+// pixel that no longer composites, no load is issued and tap_M returns 0 (the
+// backward's tap_issue2<true> issues the load when only U is outside: the texture's
+// border then supplies the zero taps, and M is 0 all the same).
 // ---------------------------------------------------------------------------
 struct ColXf {
     float au, cv;              // A dx + kw, C dx + kv
