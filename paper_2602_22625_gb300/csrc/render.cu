@@ -102,10 +102,10 @@ __device__ __forceinline__ PrimRec as_rec(float4 a, float4 b, float4 c) {
 // is non-zero at one of the pixels, so culling with it changes no result.
 // The bounds carry fp32 rounding errors of a few 2^-24 (|A| (|dx| + w) + |B| (|dy| + h))
 // texels (likewise for V).  The region lies in a tile the primitive's box reaches, so
-// |A dx| <= 2 kw + |A| x tile, and while |A| + |B| + |C| + |D| <= 2^12 the errors stay
-// far below the one texel by which the box is widened.  A larger transform (a
-// half-extent below a few hundredths of a pixel) can lose the bitmap's offset kw to
-// cancellation in U0 + A w, so such a primitive is never culled.
+// |A dx| is at most about 2 kw + |A| x (tile + margin), and while |A| + |B| + |C| + |D|
+// <= 2^12 the errors stay far below the one texel by which the box is widened.  A larger
+// transform (a half-extent below a few hundredths of a pixel) can lose the bitmap's
+// offset kw to cancellation in U0 + A w, so such a primitive is never culled.
 __device__ __forceinline__ bool region_hits(const PrimRec &r, const AtlasView &at, float x0, float y0,
                                             float w, float h, float kw, float kv) {
     if (fabsf(r.A) + fabsf(r.B) + fabsf(r.C) + fabsf(r.D) > 4096.0f) return true;
