@@ -107,14 +107,15 @@ def test_every_tuning_renders_the_same_bits(T_stop):
 
 
 def scene_sub_pixel(seed=31, H=48, W=48):
-    """Primitives far smaller than a pixel (s = 1e-9 .. 0.2 px) on integer centres at
+    """Primitives far smaller than a pixel (s = 1e-28 .. 0.2 px; at 1e-28 the transform
+    coefficients are ~3e29, within the 2^100 the library accepts) on integer centres at
     rotations 0, 45, 90, 180 and 270 degrees, between two groups of ordinary ones.
     Along the line through a tiny primitive's centre in its u direction, V is within
-    the bitmap while |U| reaches ~1e12 (s = 1e-9): those pixels' taps lie far beyond
-    the bitmap's columns.  Returns the scene and the indices of the tiny primitives."""
+    the bitmap while |U| reaches ~1e31: those pixels' taps lie far beyond the bitmap's
+    columns.  Returns the scene and the indices of the tiny primitives."""
     g = np.random.default_rng(seed)
     tiny = []
-    for s in (1e-9, 1e-6, 1e-3, 0.2):
+    for s in (1e-28, 1e-9, 1e-6, 1e-3, 0.2):
         for th in (0.0, 0.25 * np.pi, 0.5 * np.pi, np.pi, 1.5 * np.pi):
             x, y = g.integers(4, W - 4), g.integers(4, H - 4)
             tiny.append([x, y, s, th, g.normal(), *g.normal(size=3)])
@@ -129,7 +130,8 @@ def scene_sub_pixel(seed=31, H=48, W=48):
 @pytest.mark.parametrize("tuning", [(16, 32, 2), (32, 32, 4), (8, 32, 1)], ids=lambda t: f"t{t[0]}p{t[2]}")
 def test_sub_pixel_primitives_sample_nothing_beyond_the_bitmap(tuning):
     """The backward tests only V's range before a gather and relies on the texture's
-    border for U: a footprint in columns < 0 or >= W_b reads zeros, however far out.
+    border for U: a footprint in columns < 0 or >= W_b reads zeros, however far out
+    (here up to |U| ~ 1e31).
     Each tiny primitive composites only at its own centre pixel (where the atlas is
     flat, so its geometric gradients are exactly 0); any texel read beyond the bitmap
     would give it a non-zero geometric gradient, and the deeper layers' recovered
