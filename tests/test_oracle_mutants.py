@@ -27,6 +27,8 @@ MUTANTS = {
                                   "double V = (L->v + 1.0) / 2.0 * (double)(Wb - 1);"),
     "half_widths_swapped_in_backward": ("double gu = dM * dMdU * kw, gv = dM * dMdV * kv;",
                                         "double gu = dM * dMdU * kv, gv = dM * dMdV * kw;"),
+    "early_termination_dropped": ("        if (T < T_stop) break;\n        orc_layer L;", "        orc_layer L;"),
+    "zero_samples_counted_as_layers": ("        if (L.M == 0.0) continue;\n        L.k = k;", "        L.k = k;"),
     "back_product_not_updated": ("B *= (1.0 - L->alpha);\n    }\n}", "}\n}"),
     "transmittance_update": ("T *= (1.0 - L.alpha);", "T *= (1.0 - 0.5 * L.alpha);"),
     "bin_margin_sign": ("float fx0 = floorf(((cx - hx) - m) * inv_t);",
