@@ -58,12 +58,23 @@ MUTANTS = {
 }
 
 
-def run_pins(tmp_path, src):
-    """Runs the pin tests against a copy of the oracle built from `src` (the test
-    files and the helpers they import copied beside it); returns the pytest result."""
+# mistakes planted in the oracle's Python half (oracle/oracle.py)
+PY_MUTANTS = {
+    "adam_bias_correction_dropped": ("    mh = m / (1.0 - beta1 ** t)\n", "    mh = m\n"),
+    "adam_second_moment_not_squared": ("(1.0 - beta2) * g * g", "(1.0 - beta2) * np.abs(g)"),
+    "mse_grad_factor_two_dropped": ("    return 2.0 * d / d.size", "    return d / d.size"),
+}
+
+
+def run_pins(tmp_path, src, pysrc=None):
+    """Runs the pin tests against a copy of the oracle built from `src` (and, if given,
+    `pysrc` as its oracle.py), with the test files and the helpers they import copied
+    beside it; returns the pytest result."""
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
                     ignore=shutil.ignore_patterns("_lib", "__pycache__"))
     (tmp_path / "oracle" / "dbmp_oracle.c").write_text(src)
+    if pysrc is not None:
+        (tmp_path / "oracle" / "oracle.py").write_text(pysrc)
     (tmp_path / "tests").mkdir()
     for f in ("test_oracle_pins.py", "test_oracle_init.py", "conftest.py", "_helpers.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
@@ -87,5 +98,16 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     a, b = MUTANTS[name]
     assert a in src
     r = run_pins(tmp_path, src.replace(a, b, 1))
+    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_planted_mistake_in_the_python_half(name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "dbmp_oracle.c")).read()
+    py = open(os.path.join(ROOT, "oracle", "oracle.py")).read()
+    a, b = PY_MUTANTS[name]
+    assert a in py
+    r = run_pins(tmp_path, src, py.replace(a, b, 1))
     assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
     assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
