@@ -66,22 +66,35 @@ PY_MUTANTS = {
 }
 
 
-def run_pins(tmp_path, src, pysrc=None):
-    """Runs the pin tests against a copy of the oracle built from `src` (and, if given,
-    `pysrc` as its oracle.py), with the test files and the helpers they import copied
-    beside it; returns the pytest result."""
+# mistakes planted in the proposal network's oracle (oracle/cnn.py), against its pins
+CNN_MUTANTS = {
+    "col2im_taps_transposed": ("+= d[:, :, :, ky, kx, :]", "+= d[:, :, :, kx, ky, :]"),
+    "relu_mask_dropped_in_backward": ("dZ = R(np.where(X > 0, dX, 0.0))", "dZ = R(dX)"),
+    "bias_gradient_dropped": ("grads[li] = (mm(dZ.T, cols[li]), dZ.sum(0))",
+                              "grads[li] = (mm(dZ.T, cols[li]), 0.0 * dZ.sum(0))"),
+    "im2col_padding_misplaced": ("Xp[:, p:p + H, p:p + W] = X", "Xp[:, :H, :W] = X"),
+}
+
+PIN_FILES = ("tests/test_oracle_pins.py", "tests/test_oracle_init.py")
+
+
+def run_pins(tmp_path, src, pysrc=None, files=None, pins=PIN_FILES):
+    """Runs the pin tests `pins` against a copy of the oracle built from `src` (and, if
+    given, `pysrc` as its oracle.py and `files` {name: text} for other oracle files), with
+    the test files and the helpers they import copied beside it; returns the pytest result."""
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
                     ignore=shutil.ignore_patterns("_lib", "__pycache__"))
     (tmp_path / "oracle" / "dbmp_oracle.c").write_text(src)
     if pysrc is not None:
         (tmp_path / "oracle" / "oracle.py").write_text(pysrc)
+    for name, text in (files or {}).items():
+        (tmp_path / "oracle" / name).write_text(text)
     (tmp_path / "tests").mkdir()
-    for f in ("test_oracle_pins.py", "test_oracle_init.py", "conftest.py", "_helpers.py"):
+    for f in [os.path.basename(p) for p in pins] + ["conftest.py", "_helpers.py"]:
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     os.symlink(os.path.join(ROOT, "paper_2602_22625_gb300"), tmp_path / "paper_2602_22625_gb300")
-    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                           "tests/test_oracle_pins.py", "tests/test_oracle_init.py"], cwd=tmp_path,
-                          capture_output=True, text=True, timeout=300)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
+                          cwd=tmp_path, capture_output=True, text=True, timeout=300)
 
 
 def test_unmutated_copy_passes_the_pins(tmp_path):
@@ -109,5 +122,22 @@ def test_pins_catch_planted_mistake_in_the_python_half(name, tmp_path):
     a, b = PY_MUTANTS[name]
     assert a in py
     r = run_pins(tmp_path, src, py.replace(a, b, 1))
+    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
+
+
+def test_unmutated_network_oracle_passes_its_pins(tmp_path):
+    r = run_pins(tmp_path, open(os.path.join(ROOT, "oracle", "dbmp_oracle.c")).read(),
+                 pins=("tests/test_oracle_cnn.py",))
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(CNN_MUTANTS))
+def test_network_pins_catch_planted_mistake(name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "dbmp_oracle.c")).read()
+    cnn = open(os.path.join(ROOT, "oracle", "cnn.py")).read()
+    a, b = CNN_MUTANTS[name]
+    assert a in cnn
+    r = run_pins(tmp_path, src, files={"cnn.py": cnn.replace(a, b, 1)}, pins=("tests/test_oracle_cnn.py",))
     assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
     assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
