@@ -24,6 +24,8 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
+@pytest.mark.skipif(os.environ.get("DBMP_LIBRARY") == "checked",
+                    reason="the suite itself runs on the checked library")
 def test_the_default_build_has_no_checks():
     cuda()
     assert D.dbmp_index_checks() is False
