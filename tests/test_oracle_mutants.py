@@ -35,6 +35,8 @@ MUTANTS = {
                         "float fx0 = floorf(((cx - hx) + m) * inv_t);"),
     "bin_support_ring_dropped": ("float hu = (float)(box[1] - box[0] + 2) * 0.5f;",
                                  "float hu = (float)(box[1] - box[0]) * 0.5f;"),
+    "bin_half_widths_swapped": ("float uc = cu / kw, eu = hu / kw, vc = cv / kv, ev = hv / kv;",
+                                "float uc = cu / kv, eu = hu / kv, vc = cv / kw, ev = hv / kw;"),
     "bin_centre_offset_sign": ("dxc = s * (cs * uc - sn * vc);", "dxc = s * (cs * uc + sn * vc);"),
     "bin_centre_offset_dropped": ("float cx = p[0] + dxc, cy = p[1] + dyc;", "float cx = p[0], cy = p[1] + dyc;"),
     "bin_quadrant_sign": ("        *sn = cr;\n        *cs = -sr;", "        *sn = cr;\n        *cs = sr;"),
