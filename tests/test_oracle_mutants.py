@@ -99,6 +99,12 @@ def run_pins(tmp_path, src, pysrc=None, files=None, pins=PIN_FILES):
                           cwd=tmp_path, capture_output=True, text=True, timeout=300)
 
 
+def assert_caught(r):
+    """A pin failed on an assertion (not on an import or another error)."""
+    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
+
+
 def test_unmutated_copy_passes_the_pins(tmp_path):
     """The control: the copied oracle and pins pass as they stand, so a failure
     below comes from the planted mistake, not from the copy (a missing helper module
@@ -113,8 +119,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     a, b = MUTANTS[name]
     assert a in src
     r = run_pins(tmp_path, src.replace(a, b, 1))
-    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
-    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
+    assert_caught(r)
 
 
 @pytest.mark.parametrize("name", sorted(PY_MUTANTS))
@@ -124,8 +129,7 @@ def test_pins_catch_planted_mistake_in_the_python_half(name, tmp_path):
     a, b = PY_MUTANTS[name]
     assert a in py
     r = run_pins(tmp_path, src, py.replace(a, b, 1))
-    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
-    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
+    assert_caught(r)
 
 
 def test_unmutated_network_oracle_passes_its_pins(tmp_path):
@@ -141,5 +145,4 @@ def test_network_pins_catch_planted_mistake(name, tmp_path):
     a, b = CNN_MUTANTS[name]
     assert a in cnn
     r = run_pins(tmp_path, src, files={"cnn.py": cnn.replace(a, b, 1)}, pins=("tests/test_oracle_cnn.py",))
-    assert r.returncode == 1, r.stdout[-2000:] + r.stderr[-2000:]
-    assert "failed" in r.stdout and "Error" not in r.stdout.replace("AssertionError", ""), r.stdout[-2000:]
+    assert_caught(r)
